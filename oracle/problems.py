@@ -1,0 +1,45 @@
+"""Operator matrices of the two model problems for the oracle (dense, plain numpy).
+
+- Advection u_t + c . grad u = 0 (Section 4.1 with constant coefficients): L = sum_i L_i,
+  L_i = -c_i D on dimension i, D the periodic central difference.  ``advection_A``
+  returns the step matrices dt*L_i used by the RK2 polynomial form.
+- Linearised kinetic equation f_t + v . grad_x f = -nu (f - M(v) rho) (Section 4.2,
+  eq. BGK_LIN; Table tab:ordering lists its separable terms): dimensions
+  (x1, x2, x3, v1, v2, v3) and five terms
+    q = 1..3: alpha = -1,   D on x_i, diag(v) on v_i;
+    q = 4:    alpha = -nu,  identity;
+    q = 5:    alpha = +nu,  (m w^T) on each v dimension (rho = sum_v w^3 f, M = m^{x3}).
+
+Parity: pinned by tests (dense Kronecker operator on tiny grids; exact conservation of
+the weighted mass; the Maxwellian is a fixed point of the collision terms).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .ht import central_diff_matrix
+
+
+def advection_A(case) -> list:
+    D = central_diff_matrix(case.n, case.h)
+    return [case.dt * (-case.c[i]) * D for i in range(case.d)]
+
+
+def kinetic_terms(kc):
+    """(alphas, factors) of the kinetic operator on (x1,x2,x3,v1,v2,v3); None = identity."""
+    n = kc.n
+    D = central_diff_matrix(n, kc.hx)
+    V = np.diag(kc.vgrid())
+    P1 = np.outer(kc.maxwellian(), kc.weights())
+    alphas, factors = [], []
+    for i in range(3):
+        f = [None] * 6
+        f[i] = D
+        f[3 + i] = V
+        alphas.append(-1.0)
+        factors.append(f)
+    alphas.append(-kc.nu)
+    factors.append([None] * 6)
+    alphas.append(kc.nu)
+    factors.append([None, None, None, P1, P1, P1])
+    return alphas, factors

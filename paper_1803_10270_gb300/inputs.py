@@ -1,0 +1,168 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and by the CPU oracle.
+
+This module holds only input generation: random draws, grids and the pointwise
+values of initial conditions and operator coefficients.  None of the method's
+arithmetic (operator application, orthogonalisation, truncation, ALS) lives here,
+so the oracle and the CUDA path can both import it without sharing method code.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014): the state advances by
+0x9E3779B97F4A7C15 and each output is the state passed through two xor-shift-multiply
+rounds.  Larger random arrays (random HT / CP tensors for tests) use numpy's PCG64
+generator seeded from the same integer seed.
+
+Workloads follow the paper's two problem classes:
+- linear advection u_t + c . grad u = 0 on the periodic box [0, 2*pi)^d with a
+  sum of separable products exp(sin(x_i + phi_{m,i})) as initial condition
+  (Section 4.1 studies advection in six dimensions with a separable initial state);
+- the linearised kinetic (BGK-type) equation f_t + v . grad_x f = -nu (f - M(v) rho)
+  (Section 4.2, eq. BGK_LIN and Table tab:ordering give the separable operator).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+SEED_BASE = 0x5EED
+
+
+class SplitMix64:
+    """splitmix64 stream; uniform() in [0,1) from the top 53 bits."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / (1 << 53))
+
+    def uniform_range(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * self.uniform()
+
+    def normal(self) -> float:
+        # Box-Muller on two uniforms (first one shifted away from 0).
+        u1 = 1.0 - self.uniform()
+        u2 = self.uniform()
+        return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+@dataclass
+class AdvectionCase:
+    """Seeded constant-coefficient periodic advection problem.
+
+    Grid: x_j = j*h, h = 2*pi/n (node-centred, periodic).  Velocity c_i ~ U[-1,1].
+    Initial condition u0 = sum_m prod_i exp(sin(x_i + phi_{m,i})), phi ~ U[0, 2*pi).
+    Draw order: c_1..c_d, then phi term by term, dimension by dimension.
+    """
+
+    d: int
+    n: int
+    n_terms: int
+    seed: int
+    c: np.ndarray = field(repr=False)
+    phi: np.ndarray = field(repr=False)
+
+    @property
+    def h(self) -> float:
+        return 2.0 * math.pi / self.n
+
+    @property
+    def dt(self) -> float:
+        return 0.2 * self.h
+
+    def x(self) -> np.ndarray:
+        return np.arange(self.n, dtype=np.float64) * self.h
+
+    def ic_factors(self) -> list[np.ndarray]:
+        """Per dimension an n x n_terms array: column m holds exp(sin(x + phi_{m,i}))."""
+        x = self.x()
+        return [np.stack([np.exp(np.sin(x + self.phi[m, i])) for m in range(self.n_terms)], axis=1)
+                for i in range(self.d)]
+
+
+def advection_case(d: int, n: int, n_terms: int = 2, seed: int | None = None, cfg_index: int = 0) -> AdvectionCase:
+    if seed is None:
+        seed = SEED_BASE + cfg_index
+    g = SplitMix64(seed)
+    c = np.array([g.uniform_range(-1.0, 1.0) for _ in range(d)])
+    phi = np.array([[g.uniform_range(0.0, 2.0 * math.pi) for _ in range(d)] for _ in range(n_terms)])
+    return AdvectionCase(d=d, n=n, n_terms=n_terms, seed=seed, c=c, phi=phi)
+
+
+def normal_array(shape, seed: int, scale: float = 1.0) -> np.ndarray:
+    """N(0, scale^2) array from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return scale * rng.standard_normal(shape)
+
+
+def normal_arrays(shapes, seed: int, scale: float = 1.0) -> list[np.ndarray]:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [scale * rng.standard_normal(s) for s in shapes]
+
+
+def cp_random_factors(ns, rank: int, seed: int) -> list[np.ndarray]:
+    """Random CP factors, one n_i x rank array per dimension."""
+    return normal_arrays([(n, rank) for n in ns], seed)
+
+
+def cp_padding(ns, n_new: int, seed: int, scale: float) -> list[np.ndarray]:
+    """Seeded N(0,1)*scale columns used to pad a CP iterate up to its target rank."""
+    g = SplitMix64(seed)
+    return [np.array([[scale * g.normal() for _ in range(n_new)] for _ in range(n)]).reshape(n, n_new)
+            for n in ns]
+
+
+# ---------------------------------------------------------------------------
+# linearised kinetic equation (x periodic [0,2pi)^3, v in [-6,6]^3)
+# ---------------------------------------------------------------------------
+@dataclass
+class KineticCase:
+    """Grids and coefficient vectors for f_t + v.grad_x f = -nu (f - M(v) rho).
+
+    x grid: x_j = j*h_x, h_x = 2*pi/n.  v grid (cell centred): v_j = -6 + (j+1/2)*12/n.
+    m: 1-D Maxwellian exp(-v^2/2) normalised so that sum_j h_v m_j = 1.
+    w: quadrature weights h_v (rho(x) = sum_v w^3 f).
+    """
+
+    n: int
+    nu: float
+    seed: int
+
+    @property
+    def hx(self) -> float:
+        return 2.0 * math.pi / self.n
+
+    @property
+    def hv(self) -> float:
+        return 12.0 / self.n
+
+    def xgrid(self) -> np.ndarray:
+        return np.arange(self.n, dtype=np.float64) * self.hx
+
+    def vgrid(self) -> np.ndarray:
+        return -6.0 + (np.arange(self.n, dtype=np.float64) + 0.5) * self.hv
+
+    def maxwellian(self) -> np.ndarray:
+        g = np.exp(-0.5 * self.vgrid() ** 2)
+        return g / (self.hv * g.sum())
+
+    def weights(self) -> np.ndarray:
+        return np.full(self.n, self.hv)
+
+    @property
+    def dt(self) -> float:
+        return 0.2 * self.hx / 6.0
+
+
+def kinetic_case(n: int, nu: float = 1.0, seed: int | None = None, cfg_index: int = 2) -> KineticCase:
+    if seed is None:
+        seed = SEED_BASE + cfg_index
+    return KineticCase(n=n, nu=nu, seed=seed)

@@ -1,0 +1,42 @@
+"""Independent closed forms used to pin the oracle (test helpers, not the oracle).
+
+- fully discrete Fourier solution of the central-difference / RK2 scheme;
+- exact characteristic solution of constant-coefficient advection;
+- projector-product form of the root-to-leaves HSVD built from full-matrix SVDs.
+"""
+import numpy as np
+
+
+def fourier_rk2(u0: np.ndarray, c, h: float, dt: float, steps: int) -> np.ndarray:
+    """u_n = IFFT[ R(dt*lam)^n FFT(u0) ], lam(k) = -i sum_j c_j sin(k_j h)/h, R = 1+z+z^2/2.
+
+    The periodic central difference maps e^{i k x} to (i sin(k h)/h) e^{i k x}.
+    """
+    uh = np.fft.fftn(u0)
+    lam = np.zeros(u0.shape, dtype=np.complex128)
+    for j, n in enumerate(u0.shape):
+        k = np.fft.fftfreq(n) * n
+        s = np.sin(k * h) / h
+        shape = [1] * u0.ndim
+        shape[j] = n
+        lam = lam + (-1j * c[j] * s).reshape(shape)
+    z = dt * lam
+    R = 1.0 + z + 0.5 * z * z
+    return np.fft.ifftn(uh * R ** steps).real
+
+
+def matricize(full: np.ndarray, dims: list) -> np.ndarray:
+    rest = [i for i in range(full.ndim) if i not in dims]
+    nr = int(np.prod([full.shape[i] for i in dims]))
+    return full.transpose(dims + rest).reshape(nr, -1, order="F")
+
+
+def apply_node_projector(full: np.ndarray, dims: list, P: np.ndarray) -> np.ndarray:
+    """Apply P (N_t x N_t) to the node matricisation rows and fold back."""
+    rest = [i for i in range(full.ndim) if i not in dims]
+    perm = dims + rest
+    shp = [full.shape[i] for i in perm]
+    M = matricize(full, dims)
+    Y = (P @ M).reshape(shp, order="F")
+    inv = np.argsort(perm)
+    return Y.transpose(inv)

@@ -1,0 +1,79 @@
+"""Pins for the CP / ALS oracle."""
+import numpy as np
+import pytest
+
+from oracle import cp as C
+from oracle import fullgrid as FG
+from oracle import ht as H
+from paper_1803_10270_gb300.inputs import advection_case, cp_random_factors
+from tests.closed_forms import fourier_rk2
+
+
+def test_cp_apply_matches_fourier():
+    d, n = 3, 6
+    case = advection_case(d, n, seed=3)
+    x = C.CP(np.array([1.0, -0.4]), cp_random_factors([n] * d, 2, seed=1))
+    A = [case.dt * (-case.c[i]) * H.central_diff_matrix(n, case.h) for i in range(d)]
+    y = C.apply_kron_sum_rk2(x, A)
+    assert y.rank == 2 * (1 + 2 * d + d * (d - 1) // 2)
+    ref = fourier_rk2(C.to_full(x), case.c, case.h, case.dt, 1)
+    assert np.abs(C.to_full(y) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_mode_update_is_bruteforce_least_squares():
+    d, n, r = 3, 4, 2
+    rng = np.random.default_rng(0)
+    y = C.CP(rng.uniform(0.5, 1.5, 5), [rng.standard_normal((n, 5)) for _ in range(d)])
+    xf = [rng.standard_normal((n, r)) for _ in range(d)]
+    Yfull = C.to_full(y)
+    for k in range(d):
+        Xk = C._mode_solve(y, xf, k)
+        # unfold: Yfull[..] = sum_l X_k[i_k, l] prod_{j != k} X_j[i_j, l]
+        others = [j for j in range(d) if j != k]
+        Z = np.ones((1, r))
+        for j in others:
+            Z = np.einsum("al,bl->abl", Z, xf[j]).reshape(-1, r)
+        # Z rows ordered with the earlier 'other' index slowest; match by transposing Yfull
+        Yk = np.moveaxis(Yfull, k, 0).reshape(n, -1)
+        sol, *_ = np.linalg.lstsq(Z, Yk.T, rcond=None)
+        assert np.abs(sol.T - Xk).max() < 1e-10 * np.abs(sol).max()
+
+
+def test_gs_residual_monotone_and_fixed_point():
+    d, n = 4, 6
+    rng = np.random.default_rng(2)
+    y = C.CP(rng.uniform(0.5, 1.5, 7), [rng.standard_normal((n, 7)) for _ in range(d)])
+    x0 = C.CP(np.ones(3), [rng.standard_normal((n, 3)) for _ in range(d)])
+    prev = C.residual(y, x0)
+    x = x0
+    for _ in range(6):
+        x, _ = C.als_sweeps(y, x, 1)
+        cur = C.residual(y, x)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+    # exact rank-3 target, init = truth: fixed point
+    z = C.CP(np.array([2.0, 1.0, 0.5]), [rng.standard_normal((n, 3)) for _ in range(d)])
+    xz, eps = C.als_sweeps(z, z, 2)
+    assert np.abs(C.to_full(xz) - C.to_full(z)).max() < 1e-10 * np.abs(C.to_full(z)).max()
+    assert eps[-1] < 1e-10
+
+
+@pytest.mark.parametrize("variant", ["gs", "jacobi_damped"])
+def test_rank1_target_recovered(variant):
+    d, n = 3, 5
+    rng = np.random.default_rng(4)
+    truth = C.CP(np.array([3.0]), [rng.standard_normal((n, 1)) for _ in range(d)])
+    init = C.CP(np.array([1.0]), [f + 0.3 * rng.standard_normal(f.shape) for f in truth.factors])
+    sweeps = 30 if variant == "gs" else 200
+    x, eps = C.als_sweeps(truth, init, sweeps, variant)
+    ft = C.to_full(truth)
+    assert np.linalg.norm(C.to_full(x) - ft) < 1e-8 * np.linalg.norm(ft)
+    assert eps[-1] < eps[0]
+
+
+def test_pad_keeps_tensor_when_padding_zero():
+    d, n = 3, 4
+    x = C.CP(np.array([1.0, 2.0]), cp_random_factors([n] * d, 2, seed=5))
+    p = C.pad(x, 5, [np.zeros((n, 3))] * d)
+    assert p.rank == 5
+    assert np.abs(C.to_full(p) - C.to_full(x)).max() < 1e-12 * np.abs(C.to_full(x)).max()
