@@ -1,0 +1,217 @@
+/*
+ * htgpu.h -- C ABI of the GB300 (sm_103a) library for explicit time steps of
+ * d-dimensional linear PDEs u_t = L u whose solution is held in hierarchical Tucker
+ * (HT) format on a balanced binary dimension tree, or in canonical (CP) format.
+ *
+ * Method (arXiv:1803.10270):
+ *  - HT format, Section 2.2, eqs. HTD / coreT: leaf bases U_i (n_i x k) and transfer
+ *    tensors B_t (k_t1 x k_t2 x k_t), root B (k_t1 x k_t2).
+ *  - Separable operator, Section 3, eq. Lz: L = sum_q alpha_q L_1^q ... L_d^q.
+ *  - Explicit stepping with rank reduction, Section 3.2 (eq. AB2_ and the text after
+ *    it): the step needs operator application, addition and rank reduction by the
+ *    hierarchical SVD (HT) or by alternating least squares (CP).
+ *  - CP format and ALS, Section 2.1, eqs. functional-SSE, als, SSYSTEM, A^{ln}_{jhp}.
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments named "device" are device pointers owned by the caller.
+ *    The library owns only the workspace inside an ht_ctx.
+ *  - Every call is asynchronous on the given CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and never synchronises the host, so a
+ *    sequence of calls can be captured in a CUDA graph.  Ranks stay in device memory.
+ *  - Floating-point data are FP64 in memory in every precision mode.
+ *  - Return value: HT_OK (0) or a negative ht_status.  Argument errors are detected on
+ *    the host before anything is launched.  Numerical problems found on the device
+ *    (non-finite values, a bounded wait that gave up) set a device error word that
+ *    ht_ctx_check() reads (synchronising) and clears.
+ *
+ * Tree and node numbering
+ *  The dimension range [a, b) of a node splits at a + floor((b-a)/2); for d = 6 this is
+ *  {1,2,3}|{4,5,6}, then {1}|{2,3} and {4}|{5,6} (Section 2.2, eq. HTD).  Nodes are
+ *  numbered breadth first from the root (node 0); 2d-1 nodes, d leaves.  ht_tree_info()
+ *  returns the numbering.
+ *
+ * Storage of an HT tensor (packed with the CURRENT ranks, first index fastest)
+ *  leaf t of dimension i:  U[j + n_i * a],             0 <= a < k_t
+ *  interior t (t1, t2):    B[a + k_t1 * (b + k_t2 * c)]
+ *  root (t1, t2):          B[a + k_t1 * b]
+ *  Buffers are sized for the capacity cap: n_i*cap, cap^3 and cap^2 doubles.
+ */
+#ifndef HTGPU_H
+#define HTGPU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HT_MAXD 16
+#define HT_MAXNODES (2 * HT_MAXD - 1)
+#define HT_MAXTERMS 8
+#define HT_MAXSTENCIL 9
+
+typedef enum ht_status {
+  HT_OK = 0,
+  HT_ERR_ARG = -1,        /* bad argument: d, n, ranks, pointers, modes */
+  HT_ERR_CAPACITY = -2,   /* a result rank could exceed a buffer or workspace capacity */
+  HT_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+  HT_ERR_NONFINITE = -4,  /* NaN/Inf met on the device (reported by ht_ctx_check) */
+  HT_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up (reported by ht_ctx_check) */
+  HT_ERR_NOMEM = -6       /* workspace allocation failed */
+} ht_status;
+
+typedef enum ht_precision {
+  HT_PREC_FP64 = 0,   /* every operation in FP64 */
+  HT_PREC_MIXED = 1   /* contractions and QR in FP32, node SVDs and thresholds in FP64 */
+} ht_precision;
+
+/* ---------------------------------------------------------------- tensors ---- */
+typedef struct ht_tensor {
+  int d;                          /* number of dimensions, 2 <= d <= HT_MAXD */
+  int n[HT_MAXD];                 /* grid points per dimension, 1 <= n_i */
+  int cap;                        /* rank capacity of every non-root node */
+  double* node[HT_MAXNODES];      /* device buffers per node (see storage above) */
+  int* rank;                      /* device, HT_MAXNODES ints; rank[0] = 1 */
+} ht_tensor;
+
+typedef struct cp_tensor {
+  int d;                          /* number of dimensions */
+  int n[HT_MAXD];                 /* grid points per dimension */
+  int rank;                       /* current rank r (host value) */
+  int cap;                        /* column capacity of every factor buffer */
+  double* factor[HT_MAXD];        /* device, n_k x cap column-major, first r columns used */
+  double* weight;                 /* device, cap values lambda_l */
+} cp_tensor;
+
+/* ------------------------------------------------------------- operators ---- */
+typedef enum ht_factor_kind {
+  HT_F_IDENTITY = 0,   /* identity */
+  HT_F_STENCIL = 1,    /* periodic constant band: (A u)_j = sum_{s=-w}^{w} c_{s+w} u_{j+s mod n} */
+  HT_F_DIAG = 2,       /* (A u)_j = v_j u_j, v a device vector of n values */
+  HT_F_RANK1 = 3       /* (A u)_j = m_j sum_l w_l u_l, m and w device vectors of n values */
+} ht_factor_kind;
+
+typedef struct ht_factor {
+  int kind;                        /* ht_factor_kind */
+  int half_width;                  /* STENCIL: w, 0 <= w <= (HT_MAXSTENCIL-1)/2 */
+  double stencil[HT_MAXSTENCIL];   /* STENCIL: 2w+1 coefficients (host values) */
+  const double* v;                 /* DIAG: device values; RANK1: device m */
+  const double* w;                 /* RANK1: device w */
+} ht_factor;
+
+/* Separable operator L = sum_q alpha_q A_1^q x ... x A_d^q  (eq. Lz).
+ * kron_sum = 1 declares that term q acts on dimension q only (n_terms = d,
+ * f[q][i] = identity for i != q), i.e. L = sum_i L_i; this enables the exact
+ * rank-3k form of the RK2 polynomial p(dt L) = 1 + dt L + dt^2 L^2 / 2. */
+typedef struct ht_op {
+  int d;
+  int n_terms;                             /* 1 <= n_terms <= HT_MAXTERMS */
+  int kron_sum;
+  double alpha[HT_MAXTERMS];
+  ht_factor f[HT_MAXTERMS][HT_MAXD];
+} ht_op;
+
+/* ---------------------------------------------------------------- context --- */
+typedef struct ht_ctx ht_ctx;
+
+typedef struct ht_config {
+  int d;                   /* dimensions of the tensors this context serves */
+  int n[HT_MAXD];          /* grid points per dimension */
+  int cap;                 /* largest input rank capacity */
+  int max_terms;           /* largest operator term count used with ht_step/ht_apply */
+  int precision;           /* ht_precision */
+  int device;              /* CUDA device ordinal */
+} ht_config;
+
+/* Workspace bytes a context with this configuration allocates (0 on bad config). */
+size_t ht_workspace_bytes(const ht_config* cfg);
+
+/* Create a context: allocates the workspace on cfg->device with cudaMalloc.
+ * *out receives the context.  Errors: HT_ERR_ARG, HT_ERR_NOMEM, HT_ERR_CUDA. */
+int ht_ctx_create(ht_ctx** out, const ht_config* cfg);
+
+/* Free the workspace and the context (NULL is accepted). */
+void ht_ctx_destroy(ht_ctx* ctx);
+
+/* Synchronise the context's last stream, read and clear the device error word.
+ * Returns HT_OK, HT_ERR_NONFINITE or HT_ERR_TIMEOUT. */
+int ht_ctx_check(ht_ctx* ctx, void* stream);
+
+/* Number of kernel launches the context issued since creation (host counter). */
+long long ht_ctx_launches(const ht_ctx* ctx);
+
+/* Human-readable name of a status code. */
+const char* ht_status_string(int status);
+
+/* Node numbering of the balanced tree for d dimensions.  Each output array holds
+ * 2d-1 ints: lo/hi = dimension range [lo, hi), c1/c2 = children (-1 for leaves),
+ * parent (-1 for the root), depth.  Returns HT_ERR_ARG for d outside [2, HT_MAXD]. */
+int ht_tree_info(int d, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth);
+
+/* ------------------------------------------------------------- HT calls ----- */
+typedef enum ht_apply_mode {
+  HT_APPLY_L = 0,          /* v = L u                        rank n_terms * k */
+  HT_APPLY_EULER = 1,      /* v = u + dt L u                 rank (n_terms+1) * k */
+  HT_APPLY_RK2POLY = 2     /* v = (1 + dt L + dt^2 L^2 / 2) u, kron_sum operators only, rank 3k */
+} ht_apply_mode;
+
+/* Operator application (eq. Lz; Section 3.2).  The result is exact (no truncation):
+ * leaves [A_i^q U_i]_q, block-structured transfer tensors.  v->cap must hold the
+ * raised rank of every node (checked against u->cap on the host).  u and v must not
+ * alias.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
+int ht_apply(ht_ctx* ctx, const ht_tensor* u, const ht_op* L, double dt, int mode,
+             ht_tensor* v, void* stream);
+
+/* HSVD truncation T(u) (root-to-leaves hierarchical SVD; Section 2.2 and 3.2).
+ * Rank of node t: the smallest k whose discarded singular-value energy is at most
+ * (rel_tol * |u|)^2 / (2d-3), then min(k, rmax); both root children share the rank.
+ * Writes T(u) into out (out->cap >= rmax; out may equal u).  sigma_dev (device,
+ * HT_MAXNODES * sig_stride doubles, or NULL) receives each node's singular values
+ * (descending, zero padded; sig_stride >= the node's input rank).  norm_dev (device,
+ * 1 double, or NULL) receives |u|.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
+int ht_truncate(ht_ctx* ctx, const ht_tensor* u, double rel_tol, int rmax, ht_tensor* out,
+                double* sigma_dev, int sig_stride, double* norm_dev, void* stream);
+
+typedef enum ht_scheme {
+  HT_SCHEME_RK2POLY = 0,   /* u <- T(p(dt L) u), kron_sum operators */
+  HT_SCHEME_HEUN2 = 1      /* u* = T(u + dt L u); u <- T(u/2 + (u* + dt L u*)/2) */
+} ht_scheme;
+
+/* One explicit time step in place (Section 3.2).  Errors as ht_apply/ht_truncate. */
+int ht_step(ht_ctx* ctx, ht_tensor* u, const ht_op* L, double dt, double rel_tol, int rmax,
+            int scheme, void* stream);
+
+/* Exact HT form of a CP tensor (footnote to eq. HTD: a CP tensor is the diagonal case):
+ * leaves = factors, interior B = delta_abc, root = diag(weights).  out->cap >= x->rank. */
+int ht_from_cp(ht_ctx* ctx, const cp_tensor* x, ht_tensor* out, void* stream);
+
+/* Scalars: sum of all entries (discrete mass) and <u, w>, written to device doubles. */
+int ht_mass(ht_ctx* ctx, const ht_tensor* u, double* out_dev, void* stream);
+int ht_inner(ht_ctx* ctx, const ht_tensor* u, const ht_tensor* w, double* out_dev, void* stream);
+
+/* ------------------------------------------------------------- CP calls ----- */
+typedef enum cp_variant {
+  CP_ALS_GS = 0,              /* Gauss-Seidel over k = 1..d (Section 3.1) */
+  CP_ALS_JACOBI_DAMPED = 1    /* all modes from one iterate, increment / 4 (Appendix B, Alg. 1) */
+} cp_variant;
+
+/* ALS rank reduction (eqs. SSYSTEM, A^{ln}_{jhp}): x <- argmin |y - x| by `sweeps`
+ * sweeps from the initial x (rank x->rank).  Mode update: X_k Gamma_k = Y_k diag(mu) H_k
+ * with Gamma_k = hadamard_{j!=k} X_j^T X_j and H_k = hadamard_{j!=k} Y_j^T X_j, solved by
+ * an FP64 Cholesky factorisation.  Factor columns are normalised into x->weight after
+ * each mode solve.  eps_dev (device, `sweeps` doubles, or NULL) receives Algorithm 5's
+ * max_k |X_k^new - X_k^old| / |X_k^old| per sweep.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY. */
+int cp_als_sweep(ht_ctx* ctx, const cp_tensor* y, cp_tensor* x, int sweeps, int variant,
+                 double* eps_dev, void* stream);
+
+/* y = p(dt L) x exactly in CP form for a kron_sum operator: 1 + 2d + d(d-1)/2 rank-1
+ * terms per term of x (identity, dt A_i, dt^2 A_i^2 / 2, dt^2 A_i A_j for i < j).
+ * y->cap >= x->rank * (1 + 2d + d(d-1)/2).  Sets y->rank on the host. */
+int cp_apply_rk2(ht_ctx* ctx, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y,
+                 void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTGPU_H */

@@ -1,0 +1,96 @@
+// Internal declarations shared by the translation units of the htgpu library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/htgpu.h"
+
+#define HTG_WARP 32
+
+// ------------------------------------------------------------------ tree ----
+struct TreeInfo {
+  int d;
+  int nn;                        // 2d - 1
+  int lo[HT_MAXNODES], hi[HT_MAXNODES];
+  int c1[HT_MAXNODES], c2[HT_MAXNODES];
+  int parent[HT_MAXNODES], depth[HT_MAXNODES];
+  int max_depth;
+};
+void htg_build_tree(int d, TreeInfo* t);
+
+// --------------------------------------------------------- work descriptors --
+// Batched GEMM: C[b] = alpha * op(A[b]) * op(B[b]) * diag(colscale) + beta * C[b],
+// op(A) is m x k, op(B) is k x n, column-major; b = 0..batch-1 with strides sA/sB/sC.
+struct GemmDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  const double* colscale;   // n values or nullptr
+  long long sA, sB, sC;
+  int m, n, k;
+  int lda, ldb, ldc;
+  int batch;
+  int tA, tB;
+  double alpha, beta;
+};
+
+// Householder QR, R factor only.  Input op(A) is m x k (tA: A stored k x m, lda between
+// columns of the stored array).  Output R is min(m,k) x k upper trapezoidal written to
+// R (ldr); with tR the transpose R^T (k x min(m,k)) is written instead.  scratch holds
+// m*k values.  rows_out (optional) receives min(m,k).
+struct QrDesc {
+  const double* A;
+  double* scratch;
+  double* R;
+  int* rows_out;
+  int m, k, lda, ldr;
+  int tA, tR;
+};
+
+// One-sided Jacobi SVD of M = P^T where P (p x q, ldp) is given.  Rows of M beyond q
+// (when q < p) are treated as zero.  Outputs: sigma (p, descending), V (p x p, ldv = p)
+// = left singular vectors of P, U (q x p, ldu = q) = right singular vectors of P with
+// unit columns (zero for sigma = 0).  work: (max(p,q) + p) * p values.
+struct SvdDesc {
+  const double* P;
+  double* sigma;
+  double* V;
+  double* U;
+  double* work;
+  int p, q, ldp;
+};
+
+// ------------------------------------------------------------ launchers -----
+// All launchers return cudaGetLastError() of their launch.
+cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s);
+cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s);
+cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
+                           cudaStream_t s);
+
+// ------------------------------------------------------------ helpers -------
+__host__ __device__ inline int htg_min(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int htg_max(int a, int b) { return a > b ? a : b; }
+__host__ __device__ inline int htg_cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// ------------------------------------------------------------ context access ---
+// CP-ALS workspace inside an ht_ctx (sized from the context configuration).
+struct CpWs {
+  double* G;       // d x rcap^2         factor Grams X_j^T X_j
+  double* H;       // d x rycap x rcap   cross Grams Y_j^T X_j
+  double* Hh;      // rycap x rcap       diag(mu) * hadamard_{j != k} H_j
+  double* Gam;     // rcap^2             hadamard_{j != k} G_j
+  double* RHS;     // nmax x rcap        Y_k Hh
+  double* Xold;    // HT_MAXD x nmax x rcap   iterate copy (Jacobi variant / eps)
+  double* wold;    // rcap
+  double* epsacc;  // 64 (per-sweep accumulators)
+  GemmDesc* descs; // 4 * HT_MAXD
+  int rcap, rycap, nmax;
+};
+CpWs* htg_ctx_cp(ht_ctx* c);
+int htg_ctx_d(const ht_ctx* c);
+const int* htg_ctx_n(const ht_ctx* c);
+int* htg_ctx_err(ht_ctx* c);
+int htg_ctx_grid(const ht_ctx* c);
+void htg_ctx_count(ht_ctx* c, int launches, cudaStream_t s);
+int htg_cp_terms(int d);   // 1 + 2d + d(d-1)/2

@@ -1,0 +1,1106 @@
+// HT apply, HSVD truncation and explicit steps: context, workspace, device planner,
+// apply / rank-selection kernels and the C entry points of include/htgpu.h.
+//
+// Truncation T(u) (root-to-leaves hierarchical SVD; Section 2.2 cites it as the HT rank
+// reduction, Section 3.2 uses it after each explicit step) is computed without ever
+// forming orthonormal bases:
+//   bottom-up  R_leaf = qr_R(U_leaf);  interior: C_t = B_t x1 R_t1 x2 R_t2,  R_t = qr_R(C_t)
+//   root       E_t1 = B R_t2^T,  E_t2 = B^T R_t1^T        (square-root factors of the
+//                                                          complement Gramians)
+//   top-down   P_t = R_t E_t (its SVD gives the singular values of the t-matricisation);
+//              children: E_t1 = lq([B_t x2 R_t2 x3 E_t^T]_(1)), E_t2 likewise
+//   ranks      smallest k with discarded energy <= (tol |u|)^2 / (2d-3), capped
+//   project    X_t = W_k^T R_t,  Y_t = E_t Z_k S_k^{-1}  (P_t = W S Z^T)
+//              leaf U <- U Y;  B_t <- B_t x1 X_t1 x2 X_t2 x3 Y_t^T;  root B <- X_t1 B X_t2^T
+// With U_t = Q_t R_t this is exactly Q_t W_k (the leading left singular vectors) at every
+// node, i.e. the HSVD projections, expressed through R_t, E_t and the small SVDs only.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+// ------------------------------------------------------------------- tree -----
+void htg_build_tree(int d, TreeInfo* t) {
+  memset(t, 0, sizeof(*t));
+  t->d = d;
+  int n = 1;
+  t->lo[0] = 0; t->hi[0] = d; t->parent[0] = -1; t->depth[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    const int a = t->lo[i], b = t->hi[i];
+    if (b - a > 1) {
+      const int m = a + (b - a) / 2;
+      t->c1[i] = n; t->c2[i] = n + 1;
+      t->lo[n] = a; t->hi[n] = m; t->lo[n + 1] = m; t->hi[n + 1] = b;
+      t->parent[n] = t->parent[n + 1] = i;
+      t->depth[n] = t->depth[n + 1] = t->depth[i] + 1;
+      t->c1[n] = t->c2[n] = t->c1[n + 1] = t->c2[n + 1] = -1;
+      n += 2;
+    } else {
+      t->c1[i] = t->c2[i] = -1;
+    }
+  }
+  t->nn = n;
+  int md = 0;
+  for (int i = 0; i < n; ++i) md = htg_max(md, t->depth[i]);
+  t->max_depth = md;
+}
+
+namespace {
+
+constexpr int NN = HT_MAXNODES;
+constexpr int MAXLEV = 6;
+
+// Device-side plan: dimensions derived from the device-resident ranks, plus every work
+// descriptor of one truncation.  Slots per level follow the host's level lists.
+struct Plan {
+  int K[NN], Rp[NN], mE[NN], knew[NN];
+  QrDesc qr_leaf[HT_MAXD];
+  QrDesc qr_orth[MAXLEV][NN];
+  QrDesc qr_comp[MAXLEV][2 * NN];
+  GemmDesc g_abs1[MAXLEV][NN];
+  GemmDesc g_abs2[MAXLEV][NN];
+  GemmDesc g_rootE[2];
+  GemmDesc g_P[MAXLEV][NN];
+  SvdDesc svd[MAXLEV][NN];
+  GemmDesc g_T1[MAXLEV][NN];
+  GemmDesc g_Epre[MAXLEV][2 * NN];
+  GemmDesc g_XY[2 * NN];
+  GemmDesc g_proj1[NN];
+  GemmDesc g_proj2[NN];
+  GemmDesc g_proj3[NN];
+  double norm;
+};
+
+// Static level lists (host computed, passed by value to the planner).
+struct Levels {
+  int n_all[MAXLEV];          // non-root nodes per depth
+  int all[MAXLEV][NN];
+  int n_int[MAXLEV];          // interior non-root nodes per depth
+  int inter[MAXLEV][NN];
+  int n_leaf;
+  int leaf[HT_MAXD];          // leaf nodes in dimension order
+  int n_proj1, proj1[NN];     // leaves + interior + root
+  int n_proj2, proj2[NN];     // interior + root
+  int n_proj3, proj3[NN];     // interior
+};
+
+// Workspace pointers per node (capacity sized).
+struct WsNode {
+  double* Rf;     // R factor          Kc x Kc (leaves: min(n,Kc) x Kc)
+  double* Tabs;   // absorb temp / projection T2 / root TR       Kc^3
+  double* Cabs;   // absorbed transfer / projection T3           Kc^3
+  double* S;      // QR scratch                                   Kc^3
+  double* Epre;   // uncompressed complement factor               Kc^3
+  double* T1;     // B x3 E^T                                     Kc^3
+  double* E;      // compressed complement factor                 Kc x Kc
+  double* P;      // R E                                          Kc x Kc
+  double* sig;    // singular values                              Kc
+  double* W;      // left singular vectors of P                   Kc x Kc
+  double* Z;      // right singular vectors of P                  Kc x Kc
+  double* SW;     // SVD work                                     2 Kc^2 + Kc
+  double* X;      // W_k^T R                                      Kc x Kc
+  double* Y;      // E Z_k / s                                    Kc x Kc
+  double* invsig; // 1/s_k                                        Kc
+};
+
+struct HtView {           // a tensor as the kernels see it
+  double* node[NN];
+  int* rank;
+  int n[HT_MAXD];
+};
+
+}  // namespace
+
+struct ht_ctx {
+  ht_config cfg;
+  TreeInfo tree;
+  Levels lev;
+  int Kc;                 // largest truncation input rank
+  int cap;                // largest stored rank
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  Plan* plan = nullptr;   // device
+  int* err = nullptr;     // device error word
+  WsNode wn[NN];
+  // applied-tensor area (truncation input of ht_step): packed at rank <= Kc
+  double* app[NN];
+  int* app_rank;
+  // second tensor area for HEUN2 (u* and the stage sum), rank <= Kc
+  double* stage[NN];
+  int* stage_rank;
+  WsNode* wn_dev = nullptr;   // device copy of wn[]
+  const double** ptr_tbl = nullptr;   // device table of caller pointers (CP factors)
+  CpWs cp;
+  long long launches = 0;
+  int svd_smem = 0;
+  int gemm_grid = 0;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- planner -----
+__device__ void fill_gemm(GemmDesc& g, const double* A, int lda, int tA, const double* B, int ldb,
+                          int tB, double* C, int ldc, int m, int n, int k) {
+  g.A = A; g.B = B; g.C = C; g.colscale = nullptr;
+  g.lda = lda; g.ldb = ldb; g.ldc = ldc;
+  g.m = m; g.n = n; g.k = k;
+  g.tA = tA; g.tB = tB;
+  g.sA = g.sB = g.sC = 0;
+  g.batch = 1;
+  g.alpha = 1.0; g.beta = 0.0;
+}
+
+__global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const WsNode* wn, int cap_in,
+                                int* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  // device-resident ranks are validated against the input capacity: out-of-range ranks are
+  // clamped (every later access stays inside the buffers) and reported as HT_ERR_CAPACITY
+  bool bad = false;
+  for (int t = 0; t < T.nn; ++t) {
+    int k = (t == 0) ? 1 : in.rank[t];
+    if (k < 1 || k > cap_in) {
+      bad = true;
+      k = k < 1 ? 1 : cap_in;
+    }
+    P->K[t] = k;
+  }
+  if (bad && err) atomicCAS(err, 0, (int)HT_ERR_CAPACITY);
+  // R-factor row counts bottom-up
+  for (int dep = T.max_depth; dep >= 1; --dep) {
+    for (int t = 1; t < T.nn; ++t) {
+      if (T.depth[t] != dep) continue;
+      if (T.c1[t] < 0) P->Rp[t] = htg_min(in.n[T.lo[t]], P->K[t]);
+      else P->Rp[t] = htg_min(P->Rp[T.c1[t]] * P->Rp[T.c2[t]], P->K[t]);
+    }
+  }
+  const int ra = T.c1[0], rb = T.c2[0];
+  P->mE[ra] = P->Rp[rb];
+  P->mE[rb] = P->Rp[ra];
+  for (int dep = 1; dep < T.max_depth; ++dep) {
+    for (int t = 1; t < T.nn; ++t) {
+      if (T.depth[t] != dep || T.c1[t] < 0) continue;
+      const int a = T.c1[t], b = T.c2[t];
+      P->mE[a] = htg_min(P->K[a], P->Rp[b] * P->mE[t]);
+      P->mE[b] = htg_min(P->K[b], P->Rp[a] * P->mE[t]);
+    }
+  }
+  // leaf QR
+  for (int s = 0; s < L.n_leaf; ++s) {
+    const int t = L.leaf[s];
+    QrDesc& q = P->qr_leaf[s];
+    q.A = in.node[t]; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr;
+    q.m = in.n[T.lo[t]]; q.k = P->K[t]; q.lda = q.m; q.ldr = P->Rp[t]; q.tA = 0; q.tR = 0;
+  }
+  // bottom-up absorb + orthogonalisation QR
+  for (int dep = 1; dep < MAXLEV; ++dep) {
+    for (int s = 0; s < L.n_int[dep]; ++s) {
+      const int t = L.inter[dep][s], a = T.c1[t], b = T.c2[t];
+      const int K1 = P->K[a], K2 = P->K[b], K = P->K[t];
+      fill_gemm(P->g_abs1[dep][s], wn[a].Rf, P->Rp[a], 0, in.node[t], K1, 0, wn[t].Tabs, P->Rp[a],
+                P->Rp[a], K2 * K, K1);
+      GemmDesc& g2 = P->g_abs2[dep][s];
+      fill_gemm(g2, wn[t].Tabs, P->Rp[a], 0, wn[b].Rf, P->Rp[b], 1, wn[t].Cabs, P->Rp[a],
+                P->Rp[a], P->Rp[b], K2);
+      g2.batch = K; g2.sA = (long long)P->Rp[a] * K2; g2.sB = 0; g2.sC = (long long)P->Rp[a] * P->Rp[b];
+      QrDesc& q = P->qr_orth[dep][s];
+      q.A = wn[t].Cabs; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr;
+      q.m = P->Rp[a] * P->Rp[b]; q.k = K; q.lda = q.m; q.ldr = P->Rp[t]; q.tA = 0; q.tR = 0;
+    }
+  }
+  // root complement factors
+  {
+    const int K1 = P->K[ra], K2 = P->K[rb];
+    fill_gemm(P->g_rootE[0], in.node[0], K1, 0, wn[rb].Rf, P->Rp[rb], 1, wn[ra].E, K1, K1, P->Rp[rb], K2);
+    fill_gemm(P->g_rootE[1], in.node[0], K1, 1, wn[ra].Rf, P->Rp[ra], 1, wn[rb].E, K2, K2, P->Rp[ra], K1);
+  }
+  // top-down
+  for (int dep = 1; dep < MAXLEV; ++dep) {
+    for (int s = 0; s < L.n_all[dep]; ++s) {
+      const int t = L.all[dep][s];
+      fill_gemm(P->g_P[dep][s], wn[t].Rf, P->Rp[t], 0, wn[t].E, P->K[t], 0, wn[t].P, P->Rp[t],
+                P->Rp[t], P->mE[t], P->K[t]);
+      SvdDesc& v = P->svd[dep][s];
+      v.P = wn[t].P; v.p = P->Rp[t]; v.q = P->mE[t]; v.ldp = P->Rp[t];
+      v.sigma = wn[t].sig; v.V = wn[t].W; v.U = wn[t].Z; v.work = wn[t].SW;
+    }
+    for (int s = 0; s < L.n_int[dep]; ++s) {
+      const int t = L.inter[dep][s], a = T.c1[t], b = T.c2[t];
+      const int K1 = P->K[a], K2 = P->K[b], K = P->K[t], mE = P->mE[t];
+      fill_gemm(P->g_T1[dep][s], in.node[t], K1 * K2, 0, wn[t].E, K, 0, wn[t].T1, K1 * K2, K1 * K2, mE, K);
+      GemmDesc& ga = P->g_Epre[dep][2 * s];
+      fill_gemm(ga, wn[t].T1, K1, 0, wn[b].Rf, P->Rp[b], 1, wn[a].Epre, K1, K1, P->Rp[b], K2);
+      ga.batch = mE; ga.sA = (long long)K1 * K2; ga.sC = (long long)K1 * P->Rp[b];
+      GemmDesc& gb = P->g_Epre[dep][2 * s + 1];
+      fill_gemm(gb, wn[t].T1, K1, 1, wn[a].Rf, P->Rp[a], 1, wn[b].Epre, K2, K2, P->Rp[a], K1);
+      gb.batch = mE; gb.sA = (long long)K1 * K2; gb.sC = (long long)K2 * P->Rp[a];
+      QrDesc& qa = P->qr_comp[dep][2 * s];
+      qa.A = wn[a].Epre; qa.scratch = wn[a].S; qa.R = wn[a].E; qa.rows_out = nullptr;
+      qa.m = P->Rp[b] * mE; qa.k = K1; qa.lda = K1; qa.ldr = K1; qa.tA = 1; qa.tR = 1;
+      QrDesc& qb = P->qr_comp[dep][2 * s + 1];
+      qb.A = wn[b].Epre; qb.scratch = wn[b].S; qb.R = wn[b].E; qb.rows_out = nullptr;
+      qb.m = P->Rp[a] * mE; qb.k = K2; qb.lda = K2; qb.ldr = K2; qb.tA = 1; qb.tR = 1;
+    }
+  }
+}
+
+// Rank selection (one CTA) + projection descriptors.
+__global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtView out,
+                                   const WsNode* wn, double rel_tol, int rmax, double* sigma_out,
+                                   int sig_stride, double* norm_out, int* err) {
+  __shared__ double s_thr2;
+  const int ra = T.c1[0], rb = T.c2[0];
+  if (threadIdx.x == 0) {
+    const double* sa = wn[ra].sig;
+    double nrm2 = 0.0;
+    for (int j = 0; j < P->Rp[ra]; ++j) nrm2 += sa[j] * sa[j];
+    if (!isfinite(nrm2) && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
+    P->norm = sqrt(nrm2);
+    if (norm_out) *norm_out = P->norm;
+    const int edges = htg_max(2 * T.d - 3, 1);
+    s_thr2 = rel_tol * rel_tol * nrm2 / (double)edges;
+  }
+  __syncthreads();
+  const double thr2 = s_thr2;
+  for (int t = 1 + threadIdx.x; t < T.nn; t += blockDim.x) {
+    const int src = (t == rb) ? ra : t;
+    const double* s = wn[src].sig;
+    const int p = P->Rp[src];
+    double tail = 0.0;
+    int k = p;
+    // tail(kk) = sum_{j >= kk} s_j^2; smallest kk >= 1 with tail <= thr2
+    for (int kk = p; kk >= 1; --kk) {
+      if (tail <= thr2) k = kk;
+      else break;
+      tail += s[kk - 1] * s[kk - 1];
+    }
+    // (loop above walks kk downward while tail(kk) <= thr2)
+    k = htg_max(1, htg_min(k, rmax));
+    k = htg_min(k, P->Rp[t]);
+    P->knew[t] = k;
+    out.rank[t] = k;
+    for (int j = 0; j < P->Rp[t]; ++j) {
+      const double sj = wn[t].sig[j];
+      wn[t].invsig[j] = (j < k && sj > 0.0) ? 1.0 / sj : 0.0;
+    }
+    if (sigma_out) {
+      for (int j = 0; j < sig_stride; ++j)
+        sigma_out[(long long)t * sig_stride + j] = (j < P->Rp[t]) ? wn[t].sig[j] : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) out.rank[0] = 1;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // root children share one rank
+  {
+    const int k = htg_min(P->knew[ra], P->knew[rb]);
+    P->knew[ra] = P->knew[rb] = k;
+    out.rank[ra] = out.rank[rb] = k;
+    if (sigma_out) {
+      for (int j = 0; j < sig_stride; ++j) sigma_out[j] = 0.0;
+    }
+  }
+  // X_t, Y_t
+  int i = 0;
+  for (int t = 1; t < T.nn; ++t) {
+    const int k = P->knew[t];
+    fill_gemm(P->g_XY[i++], wn[t].W, P->Rp[t], 1, wn[t].Rf, P->Rp[t], 0, wn[t].X, k, k, P->K[t], P->Rp[t]);
+    GemmDesc& y = P->g_XY[i++];
+    fill_gemm(y, wn[t].E, P->K[t], 0, wn[t].Z, P->mE[t], 0, wn[t].Y, P->K[t], P->K[t], k, P->mE[t]);
+    y.colscale = wn[t].invsig;
+  }
+  // projection
+  for (int s = 0; s < L.n_proj1; ++s) {
+    const int t = L.proj1[s];
+    GemmDesc& g = P->g_proj1[s];
+    if (t == 0) {
+      fill_gemm(g, wn[ra].X, P->knew[ra], 0, in.node[0], P->K[ra], 0, wn[0].Tabs, P->knew[ra],
+                P->knew[ra], P->K[rb], P->K[ra]);
+    } else if (T.c1[t] < 0) {
+      const int n = in.n[T.lo[t]];
+      fill_gemm(g, in.node[t], n, 0, wn[t].Y, P->K[t], 0, out.node[t], n, n, P->knew[t], P->K[t]);
+    } else {
+      const int a = T.c1[t], b = T.c2[t];
+      const int K12 = P->K[a] * P->K[b];
+      fill_gemm(g, in.node[t], K12, 0, wn[t].Y, P->K[t], 0, wn[t].Tabs, K12, K12, P->knew[t], P->K[t]);
+    }
+  }
+  for (int s = 0; s < L.n_proj2; ++s) {
+    const int t = L.proj2[s];
+    GemmDesc& g = P->g_proj2[s];
+    if (t == 0) {
+      fill_gemm(g, wn[0].Tabs, P->knew[ra], 0, wn[rb].X, P->knew[rb], 1, out.node[0], P->knew[ra],
+                P->knew[ra], P->knew[rb], P->K[rb]);
+    } else {
+      const int a = T.c1[t], b = T.c2[t];
+      fill_gemm(g, wn[a].X, P->knew[a], 0, wn[t].Tabs, P->K[a], 0, wn[t].Cabs, P->knew[a],
+                P->knew[a], P->K[b] * P->knew[t], P->K[a]);
+    }
+  }
+  for (int s = 0; s < L.n_proj3; ++s) {
+    const int t = L.proj3[s];
+    const int a = T.c1[t], b = T.c2[t];
+    GemmDesc& g = P->g_proj3[s];
+    fill_gemm(g, wn[t].Cabs, P->knew[a], 0, wn[b].X, P->knew[b], 1, out.node[t], P->knew[a],
+              P->knew[a], P->knew[b], P->K[b]);
+    g.batch = P->knew[t];
+    g.sA = (long long)P->knew[a] * P->K[b];
+    g.sC = (long long)P->knew[a] * P->knew[b];
+  }
+}
+
+// ------------------------------------------------------------ apply kernels ---
+struct ApplyFactor {   // one 1-D factor as the apply kernel sees it
+  int kind, hw;
+  double c[HT_MAXSTENCIL];
+  const double* v;
+  const double* w;
+};
+constexpr int MAXBLK = HT_MAXTERMS + 2;
+// Block-diagonal assembly: block b of the result is F_b applied to source tensor src[b]
+// (0 or 1) with root weight coef[b].  RK2POLY instead uses the binomial block pattern of
+// a single source with factor f[0][dim] = dt * L_dim.
+struct ApplyOp {
+  int nb;                            // number of blocks
+  int mode;                          // HT_APPLY_RK2POLY or blockdiag (any other value)
+  int src[MAXBLK];
+  double coef[MAXBLK];
+  ApplyFactor f[MAXBLK][HT_MAXD];
+};
+
+// y = A x for one factor on a column of length n; x in shared memory
+__device__ double apply_factor_at(const ApplyFactor& F, const double* x, int n, int j, double xsum) {
+  switch (F.kind) {
+    case HT_F_IDENTITY: return x[j];
+    case HT_F_STENCIL: {
+      double s = 0.0;
+      for (int o = -F.hw; o <= F.hw; ++o) {
+        int jj = (j + o) % n;
+        if (jj < 0) jj += n;
+        s = fma(F.c[o + F.hw], x[jj], s);
+      }
+      return s;
+    }
+    case HT_F_DIAG: return F.v[j] * x[j];
+    case HT_F_RANK1: return F.v[j] * xsum;
+  }
+  return 0.0;
+}
+
+// Leaves: for each leaf (blockIdx.y), every input column (blockIdx.x-strided) of every block
+// is loaded to shared memory and the block's 1-D factor is applied to it.
+// RK2POLY: [U, A U, A^2 U] with A = dt * L_i.
+__global__ void apply_leaf_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+  extern __shared__ double sh[];
+  const int leaf = L.leaf[blockIdx.y];
+  const int dim = T.lo[leaf];
+  const int n = out.n[dim];
+  double* x = sh;          // n
+  double* y = sh + n;      // n
+  __shared__ double red[32];
+  if (op.mode == HT_APPLY_RK2POLY) {
+    const int K = in0.rank[leaf];
+    const ApplyFactor& F = op.f[0][dim];
+    for (int c = blockIdx.x; c < K; c += gridDim.x) {
+      const double* src = in0.node[leaf] + (long long)n * c;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = src[j];
+      __syncthreads();
+      double* o0 = out.node[leaf] + (long long)n * c;
+      double* o1 = out.node[leaf] + (long long)n * (K + c);
+      double* o2 = out.node[leaf] + (long long)n * (2 * K + c);
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = apply_factor_at(F, x, n, j, 0.0);
+        y[j] = v;
+        o0[j] = x[j];
+        o1[j] = v;
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) o2[j] = apply_factor_at(F, y, n, j, 0.0);
+      __syncthreads();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out.rank[leaf] = 3 * K;
+    return;
+  }
+  int off = 0;
+  for (int b = 0; b < op.nb; ++b) {
+    const HtView& sv = op.src[b] == 0 ? in0 : in1;
+    const int K = sv.rank[leaf];
+    const ApplyFactor& F = op.f[b][dim];
+    for (int c = blockIdx.x; c < K; c += gridDim.x) {
+      const double* src = sv.node[leaf] + (long long)n * c;
+      for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = src[j];
+      __syncthreads();
+      double xsum = 0.0;
+      if (F.kind == HT_F_RANK1) {
+        double s = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) s = fma(F.w[j], x[j], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        double tt = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tt += red[w];
+        xsum = tt;
+      }
+      double* o = out.node[leaf] + (long long)n * (off + c);
+      for (int j = threadIdx.x; j < n; j += blockDim.x) o[j] = apply_factor_at(F, x, n, j, xsum);
+      __syncthreads();
+    }
+    off += K;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out.rank[leaf] = off;
+}
+
+__device__ inline double binom3(int j, int j1) {   // C(j, j1) for j <= 2
+  return (j == 2 && j1 == 1) ? 2.0 : 1.0;
+}
+
+// Transfer tensors: binomial block pattern (RK2POLY) or block diagonal (other modes).
+__device__ inline int find_block(const int* offs, int nb, int i, int* local) {
+  int b = 0;
+  while (b + 1 < nb && offs[b + 1] <= i) ++b;
+  *local = i - offs[b];
+  return b;
+}
+
+__global__ void apply_xfer_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+  const int t = L.proj2[blockIdx.y];   // interior nodes and the root
+  const int a = T.c1[t], b = T.c2[t];
+  int oa[MAXBLK + 1], ob[MAXBLK + 1], ot[MAXBLK + 1];
+  int nb = op.nb;
+  if (op.mode == HT_APPLY_RK2POLY) {
+    nb = 3;
+    for (int j = 0; j <= 3; ++j) {
+      oa[j] = j * in0.rank[a];
+      ob[j] = j * in0.rank[b];
+      ot[j] = (t == 0) ? j : j * in0.rank[t];
+    }
+  } else {
+    oa[0] = ob[0] = ot[0] = 0;
+    for (int j = 0; j < nb; ++j) {
+      const HtView& sv = op.src[j] == 0 ? in0 : in1;
+      oa[j + 1] = oa[j] + sv.rank[a];
+      ob[j + 1] = ob[j] + sv.rank[b];
+      ot[j + 1] = ot[j] + (t == 0 ? 1 : sv.rank[t]);
+    }
+  }
+  const int M1 = oa[nb], M2 = ob[nb], M3 = (t == 0) ? 1 : ot[nb];
+  const long long total = (long long)M1 * M2 * M3;
+  double* O = out.node[t];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i1 = (int)(e % M1);
+    const int i2 = (int)((e / M1) % M2);
+    const int i3 = (int)(e / ((long long)M1 * M2));
+    int aa, bb, cc = 0;
+    const int j1 = find_block(oa, nb, i1, &aa);
+    const int j2 = find_block(ob, nb, i2, &bb);
+    double v = 0.0;
+    if (op.mode == HT_APPLY_RK2POLY) {
+      const int K1 = in0.rank[a], K2 = in0.rank[b];
+      if (t == 0) {
+        const int j = j1 + j2;
+        if (j <= 2) v = (j == 2 ? 0.5 : 1.0) * binom3(j, j1) * in0.node[0][aa + (long long)K1 * bb];
+      } else {
+        const int j3 = find_block(ot, nb, i3, &cc);
+        if (j1 + j2 == j3)
+          v = binom3(j3, j1) * in0.node[t][aa + (long long)K1 * (bb + (long long)K2 * cc)];
+      }
+    } else if (j1 == j2) {
+      const HtView& sv = op.src[j1] == 0 ? in0 : in1;
+      const int K1 = sv.rank[a], K2 = sv.rank[b];
+      if (t == 0) {
+        v = op.coef[j1] * sv.node[0][aa + (long long)K1 * bb];
+      } else {
+        const int j3 = find_block(ot, nb, i3, &cc);
+        if (j3 == j1) v = sv.node[t][aa + (long long)K1 * (bb + (long long)K2 * cc)];
+      }
+    }
+    O[e] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && t != 0) out.rank[t] = ot[nb];
+}
+
+// ------------------------------------------------------------ misc kernels ----
+__global__ void from_cp_kernel(TreeInfo T, HtView out, const double* const* fac, const double* w, int r) {
+  const int t = blockIdx.y;
+  double* O = out.node[t];
+  if (T.c1[t] < 0) {
+    const int n = out.n[T.lo[t]];
+    const double* F = fac[T.lo[t]];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * r;
+         e += (long long)gridDim.x * blockDim.x)
+      O[e] = F[e];
+  } else if (t == 0) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)r * r;
+         e += (long long)gridDim.x * blockDim.x)
+      O[e] = (e % r == e / r) ? w[e % r] : 0.0;
+  } else {
+    const long long r2 = (long long)r * r;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < r2 * r;
+         e += (long long)gridDim.x * blockDim.x) {
+      const long long a = e % r, b = (e / r) % r, c = e / r2;
+      O[e] = (a == b && b == c) ? 1.0 : 0.0;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out.rank[t] = (t == 0) ? 1 : r;
+}
+
+// <u, w> (or the mass when w == nullptr: contraction with all-ones vectors), one CTA.
+// G_leaf = U^T W; G_t[k,l] = sum B_u[a,b,k] G_a[a,a'] G_b[b,b'] B_w[a',b',l]; root likewise.
+__global__ void inner_kernel(TreeInfo T, HtView u, HtView w, int use_ones, double* gbuf, long long gstride,
+                             double* tmp, double* out) {
+  for (int dep = T.max_depth; dep >= 0; --dep) {
+    for (int t = 0; t < T.nn; ++t) {
+      if (T.depth[t] != dep) continue;
+      double* G = gbuf + gstride * t;
+      const int ku = (t == 0) ? 1 : u.rank[t];
+      const int kw = use_ones ? 1 : ((t == 0) ? 1 : w.rank[t]);
+      if (T.c1[t] < 0) {
+        const int n = u.n[T.lo[t]];
+        for (int e = threadIdx.x; e < ku * kw; e += blockDim.x) {
+          const int k = e % ku, l = e / ku;
+          double s = 0.0;
+          for (int j = 0; j < n; ++j)
+            s += u.node[t][j + (long long)n * k] * (use_ones ? 1.0 : w.node[t][j + (long long)n * l]);
+          G[e] = s;
+        }
+      } else {
+        const int a = T.c1[t], b = T.c2[t];
+        const int A1 = u.rank[a], A2 = u.rank[b];
+        const int W1 = use_ones ? 1 : w.rank[a], W2 = use_ones ? 1 : w.rank[b];
+        const double* Ga = gbuf + gstride * a;
+        const double* Gb = gbuf + gstride * b;
+        const double* Bu = u.node[t];
+        const double* Bw = use_ones ? nullptr : w.node[t];
+        // tmp[a', b', k] = sum_{a,b} Ga[a,a'] Gb[b,b'] Bu[a,b,k]
+        for (long long e = threadIdx.x; e < (long long)W1 * W2 * ku; e += blockDim.x) {
+          const int ap = (int)(e % W1), bp = (int)((e / W1) % W2), k = (int)(e / ((long long)W1 * W2));
+          double s = 0.0;
+          for (int bb = 0; bb < A2; ++bb) {
+            double sa = 0.0;
+            for (int aa = 0; aa < A1; ++aa)
+              sa += Ga[aa + (long long)A1 * ap] * Bu[aa + (long long)A1 * (bb + (long long)A2 * k)];
+            s += Gb[bb + (long long)A2 * bp] * sa;
+          }
+          tmp[e] = s;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < ku * kw; e += blockDim.x) {
+          const int k = e % ku, l = e / ku;
+          double s = 0.0;
+          for (int ap = 0; ap < W1; ++ap)
+            for (int bp = 0; bp < W2; ++bp) {
+              const double bw = use_ones ? 1.0 : Bw[ap + (long long)W1 * (bp + (long long)W2 * l)];
+              s += tmp[ap + (long long)W1 * (bp + (long long)W2 * k)] * bw;
+            }
+          G[e] = s;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) *out = gbuf[0];
+}
+
+}  // namespace
+
+// ================================================================ host side =====
+#define HTG_CHECK_LAUNCH(ctx, expr)            \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    (ctx)->launches++;                         \
+    if (_e != cudaSuccess) return HT_ERR_CUDA; \
+  } while (0)
+
+static void build_levels(const TreeInfo& T, Levels* L) {
+  memset(L, 0, sizeof(*L));
+  for (int dep = 1; dep <= T.max_depth; ++dep) {
+    for (int t = 1; t < T.nn; ++t) {
+      if (T.depth[t] != dep) continue;
+      L->all[dep][L->n_all[dep]++] = t;
+      if (T.c1[t] >= 0) L->inter[dep][L->n_int[dep]++] = t;
+    }
+  }
+  for (int i = 0; i < T.d; ++i)
+    for (int t = 0; t < T.nn; ++t)
+      if (T.c1[t] < 0 && T.lo[t] == i) L->leaf[L->n_leaf++] = t;
+  for (int t = 0; t < T.nn; ++t) L->proj1[L->n_proj1++] = t;
+  for (int t = 0; t < T.nn; ++t)
+    if (T.c1[t] >= 0) L->proj2[L->n_proj2++] = t;
+  for (int t = 1; t < T.nn; ++t)
+    if (T.c1[t] >= 0) L->proj3[L->n_proj3++] = t;
+}
+
+static bool cfg_valid(const ht_config* c) {
+  if (!c || c->d < 2 || c->d > HT_MAXD || c->cap < 1 || c->max_terms < 1 || c->max_terms > HT_MAXTERMS)
+    return false;
+  for (int i = 0; i < c->d; ++i)
+    if (c->n[i] < 1) return false;
+  return c->precision == HT_PREC_FP64 || c->precision == HT_PREC_MIXED;
+}
+
+static int trunc_input_cap(const ht_config* c) {
+  // RK2POLY raises ranks by 3; HEUN2 stage sums reach (terms + 2) * cap
+  return htg_max(3, c->max_terms + 2) * c->cap;
+}
+
+struct WsLayout {
+  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[9];
+  size_t node_off[NN][16];
+  size_t app_off[NN], stage_off[NN];
+  size_t total;
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
+  const size_t Kc = (size_t)trunc_input_cap(c);
+  size_t off = 0;
+  W->off_plan = off; off = align_up(off + sizeof(Plan));
+  W->off_err = off; off = align_up(off + 64);
+  W->off_app_rank = off; off = align_up(off + NN * sizeof(int));
+  W->off_stage_rank = off; off = align_up(off + NN * sizeof(int));
+  W->off_wn = off; off = align_up(off + NN * sizeof(WsNode));
+  W->off_ptrs = off; off = align_up(off + 4 * HT_MAXD * sizeof(void*));
+  {
+    const size_t rc = (size_t)c->cap, ry = rc * (size_t)htg_cp_terms(c->d);
+    size_t nmax = 1;
+    for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
+    const size_t cps[9] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
+                           HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1};
+    for (int j = 0; j < 9; ++j) {
+      W->off_cp[j] = off;
+      off = align_up(off + cps[j] * sizeof(double));
+    }
+  }
+  size_t nmax = 1;
+  for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
+  size_t K3 = Kc * Kc * Kc;
+  if (K3 < nmax * Kc) K3 = nmax * Kc;             // leaf QR scratch (n x Kc)
+  if (K3 < (size_t)NN * Kc * Kc) K3 = (size_t)NN * Kc * Kc;   // per-node Grams of ht_inner
+  const size_t K2 = Kc * Kc;
+  const size_t sizes[15] = {K2, K3, K3, K3, K3, K3, K2, K2, Kc, K2, K2, 2 * K2 + Kc, K2, K2, Kc};
+  for (int t = 0; t < T.nn; ++t) {
+    for (int j = 0; j < 15; ++j) {
+      W->node_off[t][j] = off;
+      off = align_up(off + sizes[j] * sizeof(double));
+    }
+  }
+  for (int t = 0; t < T.nn; ++t) {
+    size_t sz = (T.c1[t] < 0) ? (size_t)c->n[T.lo[t]] * Kc : (t == 0 ? K2 : K3);
+    W->app_off[t] = off; off = align_up(off + sz * sizeof(double));
+    W->stage_off[t] = off; off = align_up(off + sz * sizeof(double));
+  }
+  W->total = off;
+}
+
+extern "C" size_t ht_workspace_bytes(const ht_config* cfg) {
+  if (!cfg_valid(cfg)) return 0;
+  TreeInfo T;
+  htg_build_tree(cfg->d, &T);
+  WsLayout W;
+  layout(cfg, T, &W);
+  return W.total;
+}
+
+extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
+  if (!out) return HT_ERR_ARG;
+  *out = nullptr;
+  if (!cfg_valid(cfg)) return HT_ERR_ARG;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return HT_ERR_CUDA;
+  ht_ctx* c = new ht_ctx();
+  c->cfg = *cfg;
+  htg_build_tree(cfg->d, &c->tree);
+  build_levels(c->tree, &c->lev);
+  c->Kc = trunc_input_cap(cfg);
+  c->cap = cfg->cap;
+  if (c->Kc > 4096) { delete c; return HT_ERR_CAPACITY; }
+  WsLayout W;
+  layout(cfg, c->tree, &W);
+  c->ws_bytes = W.total;
+  if (cudaMalloc(&c->ws, W.total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return HT_ERR_NOMEM;
+  }
+  char* base = (char*)c->ws;
+  c->plan = (Plan*)(base + W.off_plan);
+  c->err = (int*)(base + W.off_err);
+  c->app_rank = (int*)(base + W.off_app_rank);
+  c->stage_rank = (int*)(base + W.off_stage_rank);
+  for (int t = 0; t < c->tree.nn; ++t) {
+    double** f[15] = {&c->wn[t].Rf, &c->wn[t].Tabs, &c->wn[t].Cabs, &c->wn[t].S, &c->wn[t].Epre,
+                      &c->wn[t].T1, &c->wn[t].E, &c->wn[t].P, &c->wn[t].sig, &c->wn[t].W,
+                      &c->wn[t].Z, &c->wn[t].SW, &c->wn[t].X, &c->wn[t].Y, &c->wn[t].invsig};
+    for (int j = 0; j < 15; ++j) *f[j] = (double*)(base + W.node_off[t][j]);
+    c->app[t] = (double*)(base + W.app_off[t]);
+    c->stage[t] = (double*)(base + W.stage_off[t]);
+  }
+  c->wn_dev = (WsNode*)(base + W.off_wn);
+  c->ptr_tbl = (const double**)(base + W.off_ptrs);
+  {
+    double** cpf[8] = {&c->cp.G, &c->cp.H, &c->cp.Hh, &c->cp.Gam, &c->cp.RHS, &c->cp.Xold, &c->cp.wold, &c->cp.epsacc};
+    for (int j = 0; j < 8; ++j) *cpf[j] = (double*)(base + W.off_cp[j]);
+    c->cp.descs = (GemmDesc*)(base + W.off_cp[8]);
+    c->cp.rcap = cfg->cap;
+    c->cp.rycap = cfg->cap * htg_cp_terms(cfg->d);
+    int nmax = 1;
+    for (int i = 0; i < cfg->d; ++i) nmax = htg_max(nmax, cfg->n[i]);
+    c->cp.nmax = nmax;
+  }
+  if (cudaMemset(c->err, 0, 64) != cudaSuccess ||
+      cudaMemcpy(c->wn_dev, c->wn, sizeof(WsNode) * NN, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return HT_ERR_CUDA;
+  }
+  // SVD working copy in shared memory when the capacity allows
+  const size_t Kc = (size_t)c->Kc;
+  c->svd_smem = ((2 * Kc * Kc + Kc) * sizeof(double) <= 200 * 1024) ? 1 : 0;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
+  c->gemm_grid = htg_max(1, sms) * 4;
+  *out = c;
+  return HT_OK;
+}
+
+extern "C" void ht_ctx_destroy(ht_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->ws) cudaFree(ctx->ws);
+  delete ctx;
+}
+
+extern "C" long long ht_ctx_launches(const ht_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int ht_ctx_check(ht_ctx* ctx, void* stream) {
+  if (!ctx) return HT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HT_ERR_CUDA;
+  if (h != 0) cudaMemsetAsync(ctx->err, 0, sizeof(int), s);
+  return h;
+}
+
+extern "C" const char* ht_status_string(int s) {
+  switch (s) {
+    case HT_OK: return "HT_OK";
+    case HT_ERR_ARG: return "HT_ERR_ARG";
+    case HT_ERR_CAPACITY: return "HT_ERR_CAPACITY";
+    case HT_ERR_CUDA: return "HT_ERR_CUDA";
+    case HT_ERR_NONFINITE: return "HT_ERR_NONFINITE";
+    case HT_ERR_TIMEOUT: return "HT_ERR_TIMEOUT";
+    case HT_ERR_NOMEM: return "HT_ERR_NOMEM";
+  }
+  return "HT_ERR_UNKNOWN";
+}
+
+extern "C" int ht_tree_info(int d, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth) {
+  if (d < 2 || d > HT_MAXD) return HT_ERR_ARG;
+  TreeInfo T;
+  htg_build_tree(d, &T);
+  for (int t = 0; t < T.nn; ++t) {
+    if (lo) lo[t] = T.lo[t];
+    if (hi) hi[t] = T.hi[t];
+    if (c1) c1[t] = T.c1[t];
+    if (c2) c2[t] = T.c2[t];
+    if (parent) parent[t] = T.parent[t];
+    if (depth) depth[t] = T.depth[t];
+  }
+  return HT_OK;
+}
+
+static bool tensor_matches(const ht_ctx* c, const ht_tensor* u) {
+  if (!u || u->d != c->cfg.d || !u->rank || u->cap < 1) return false;
+  for (int i = 0; i < u->d; ++i)
+    if (u->n[i] != c->cfg.n[i]) return false;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (!u->node[t]) return false;
+  return true;
+}
+
+static HtView view_of(const ht_tensor* u) {
+  HtView v;
+  memset(&v, 0, sizeof(v));
+  for (int t = 0; t < HT_MAXNODES; ++t) v.node[t] = u->node[t];
+  v.rank = u->rank;
+  for (int i = 0; i < HT_MAXD; ++i) v.n[i] = u->n[i];
+  return v;
+}
+
+static HtView view_ws(ht_ctx* c, double* const* nodes, int* rank) {
+  HtView v;
+  memset(&v, 0, sizeof(v));
+  for (int t = 0; t < c->tree.nn; ++t) v.node[t] = nodes[t];
+  v.rank = rank;
+  for (int i = 0; i < c->cfg.d; ++i) v.n[i] = c->cfg.n[i];
+  return v;
+}
+
+
+// ---------------------------------------------------------------- truncation --
+static int run_truncate(ht_ctx* c, const HtView& in, int cap_in, const HtView& out, double rel_tol, int rmax,
+                        double* sigma_dev, int sig_stride, double* norm_dev, cudaStream_t s) {
+  const TreeInfo& T = c->tree;
+  const Levels& L = c->lev;
+  Plan* P = c->plan;
+  const WsNode* wn = c->wn_dev;
+  const int g = c->gemm_grid;
+  HTG_CHECK_LAUNCH(c, (plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, c->err), cudaGetLastError()));
+  HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_leaf, L.n_leaf, s));
+  for (int dep = T.max_depth - 1; dep >= 1; --dep) {
+    if (L.n_int[dep] == 0) continue;
+    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s));
+    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s));
+    HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s));
+  }
+  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_rootE, 2, g, s));
+  for (int dep = 1; dep <= T.max_depth; ++dep) {
+    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_P[dep], L.n_all[dep], g, s));
+    HTG_CHECK_LAUNCH(c, htg_launch_svd(P->svd[dep], L.n_all[dep], c->svd_smem, c->Kc, c->Kc, s));
+    if (L.n_int[dep] == 0) continue;
+    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s));
+    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s));
+    HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s));
+  }
+  HTG_CHECK_LAUNCH(c, (rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev,
+                                                          sig_stride, norm_dev, c->err),
+                       cudaGetLastError()));
+  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s));
+  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s));
+  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s));
+  if (L.n_proj3 > 0) HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s));
+  c->last_stream = s;
+  return HT_OK;
+}
+
+static int copy_tensor_to(ht_ctx* c, const ht_tensor* u, double* const* dst, int* dst_rank, cudaStream_t s) {
+  const TreeInfo& T = c->tree;
+  for (int t = 0; t < T.nn; ++t) {
+    size_t sz;
+    if (T.c1[t] < 0) sz = (size_t)u->n[T.lo[t]] * u->cap;
+    else if (t == 0) sz = (size_t)u->cap * u->cap;
+    else sz = (size_t)u->cap * u->cap * u->cap;
+    if (cudaMemcpyAsync(dst[t], u->node[t], sz * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return HT_ERR_CUDA;
+  }
+  if (cudaMemcpyAsync(dst_rank, u->rank, NN * sizeof(int), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return HT_ERR_CUDA;
+  return HT_OK;
+}
+
+extern "C" int ht_truncate(ht_ctx* c, const ht_tensor* u, double rel_tol, int rmax, ht_tensor* out,
+                           double* sigma_dev, int sig_stride, double* norm_dev, void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, out)) return HT_ERR_ARG;
+  if (rmax < 1 || !(rel_tol >= 0.0) || (sigma_dev && sig_stride < 1)) return HT_ERR_ARG;
+  if (u->cap > c->Kc || out->cap < rmax) return HT_ERR_CAPACITY;
+  if (sigma_dev && sig_stride < htg_min(u->cap, c->Kc)) return HT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  bool alias = false;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (u->node[t] == out->node[t]) alias = true;
+  HtView in = view_of(u);
+  if (alias) {
+    int st = copy_tensor_to(c, u, c->stage, c->stage_rank, s);
+    if (st != HT_OK) return st;
+    in = view_ws(c, c->stage, c->stage_rank);
+  }
+  return run_truncate(c, in, u->cap, view_of(out), rel_tol, rmax, sigma_dev, sig_stride, norm_dev, s);
+}
+
+// ---------------------------------------------------------------- apply -------
+static bool build_apply(const ht_ctx* c, const ht_op* L, double dt, int mode, ApplyOp* op) {
+  memset(op, 0, sizeof(*op));
+  const int d = c->cfg.d;
+  if (!L || L->d != d || L->n_terms < 1 || L->n_terms > HT_MAXTERMS) return false;
+  auto conv = [&](const ht_factor& f, double scale, ApplyFactor* o) -> bool {
+    o->kind = f.kind;
+    o->hw = 0;
+    if (f.kind == HT_F_IDENTITY) {
+      o->kind = HT_F_STENCIL;   // identity as a width-0 stencil carrying the scale
+      o->c[0] = scale;
+      return true;
+    }
+    if (f.kind == HT_F_STENCIL) {
+      if (f.half_width < 0 || 2 * f.half_width + 1 > HT_MAXSTENCIL) return false;
+      o->hw = f.half_width;
+      for (int j = 0; j < 2 * f.half_width + 1; ++j) o->c[j] = scale * f.stencil[j];
+      return true;
+    }
+    if (f.kind == HT_F_DIAG || f.kind == HT_F_RANK1) {
+      if (!f.v || (f.kind == HT_F_RANK1 && !f.w)) return false;
+      if (scale != 1.0) return false;   // scales of DIAG/RANK1 factors go into alpha
+      o->v = f.v;
+      o->w = f.w;
+      return true;
+    }
+    return false;
+  };
+  op->mode = mode;
+  if (mode == HT_APPLY_RK2POLY) {
+    if (!L->kron_sum || L->n_terms != d) return false;
+    for (int i = 0; i < d; ++i) {
+      if (L->f[i][i].kind != HT_F_STENCIL) return false;
+      for (int j = 0; j < d; ++j)
+        if (j != i && L->f[i][j].kind != HT_F_IDENTITY) return false;
+      if (!conv(L->f[i][i], dt * L->alpha[i], &op->f[0][i])) return false;
+    }
+    op->nb = 3;
+    return true;
+  }
+  int b = 0;
+  ht_factor ident;
+  memset(&ident, 0, sizeof(ident));
+  if (mode == HT_APPLY_EULER) {
+    op->src[b] = 0;
+    op->coef[b] = 1.0;
+    for (int i = 0; i < d; ++i) conv(ident, 1.0, &op->f[b][i]);
+    ++b;
+  }
+  const double sc = (mode == HT_APPLY_EULER) ? dt : 1.0;
+  for (int q = 0; q < L->n_terms; ++q) {
+    op->src[b] = 0;
+    op->coef[b] = sc * L->alpha[q];
+    for (int i = 0; i < d; ++i)
+      if (!conv(L->f[q][i], 1.0, &op->f[b][i])) return false;
+    ++b;
+  }
+  op->nb = b;
+  return true;
+}
+
+static int launch_apply(ht_ctx* c, const ApplyOp& op, const HtView& in0, const HtView& in1,
+                        const HtView& out, int max_cols, cudaStream_t s) {
+  const TreeInfo& T = c->tree;
+  const Levels& L = c->lev;
+  int nmax = 1;
+  for (int i = 0; i < c->cfg.d; ++i) nmax = htg_max(nmax, c->cfg.n[i]);
+  dim3 gl(htg_max(1, htg_min(max_cols, 64)), L.n_leaf);
+  const size_t smem = 2 * (size_t)nmax * sizeof(double);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(apply_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return HT_ERR_CUDA;
+  }
+  HTG_CHECK_LAUNCH(c, (apply_leaf_kernel<<<gl, 128, smem, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
+  dim3 gx(c->gemm_grid, L.n_proj2);
+  HTG_CHECK_LAUNCH(c, (apply_xfer_kernel<<<gx, 256, 0, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
+  c->last_stream = s;
+  return HT_OK;
+}
+
+extern "C" int ht_apply(ht_ctx* c, const ht_tensor* u, const ht_op* L, double dt, int mode, ht_tensor* v,
+                        void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, v)) return HT_ERR_ARG;
+  if (mode < HT_APPLY_L || mode > HT_APPLY_RK2POLY) return HT_ERR_ARG;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (u->node[t] == v->node[t]) return HT_ERR_ARG;
+  ApplyOp op;
+  if (!build_apply(c, L, dt, mode, &op)) return HT_ERR_ARG;
+  const int mult = (mode == HT_APPLY_RK2POLY) ? 3 : op.nb;
+  if ((long long)mult * u->cap > v->cap) return HT_ERR_CAPACITY;
+  HtView in = view_of(u);
+  return launch_apply(c, op, in, in, view_of(v), u->cap, (cudaStream_t)stream);
+}
+
+extern "C" int ht_step(ht_ctx* c, ht_tensor* u, const ht_op* L, double dt, double rel_tol, int rmax,
+                       int scheme, void* stream) {
+  if (!c || !tensor_matches(c, u)) return HT_ERR_ARG;
+  if (rmax < 1 || rmax > u->cap || !(rel_tol >= 0.0)) return HT_ERR_ARG;
+  if (u->cap > c->cap) return HT_ERR_CAPACITY;
+  cudaStream_t s = (cudaStream_t)stream;
+  HtView uv = view_of(u);
+  HtView app = view_ws(c, c->app, c->app_rank);
+  if (scheme == HT_SCHEME_RK2POLY) {
+    ApplyOp op;
+    if (!build_apply(c, L, dt, HT_APPLY_RK2POLY, &op)) return HT_ERR_ARG;
+    int st = launch_apply(c, op, uv, uv, app, u->cap, s);
+    if (st != HT_OK) return st;
+    return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
+  }
+  if (scheme == HT_SCHEME_HEUN2) {
+    ApplyOp op;
+    if (!build_apply(c, L, dt, HT_APPLY_EULER, &op)) return HT_ERR_ARG;
+    if ((long long)(op.nb + 1) * u->cap > c->Kc) return HT_ERR_CAPACITY;
+    HtView stg = view_ws(c, c->stage, c->stage_rank);
+    // u* = T(u + dt L u) into the stage area
+    int st = launch_apply(c, op, uv, uv, app, u->cap, s);
+    if (st != HT_OK) return st;
+    st = run_truncate(c, app, c->Kc, stg, rel_tol, rmax, nullptr, 0, nullptr, s);
+    if (st != HT_OK) return st;
+    // u <- T(u/2 + (u* + dt L u*)/2): blocks [u | u* | A^q u*]
+    ApplyOp op2;
+    memset(&op2, 0, sizeof(op2));
+    op2.mode = HT_APPLY_EULER;
+    op2.nb = op.nb + 1;
+    op2.src[0] = 0;
+    op2.coef[0] = 0.5;
+    for (int i = 0; i < c->cfg.d; ++i) op2.f[0][i] = op.f[0][i];   // identity
+    for (int b = 0; b < op.nb; ++b) {
+      op2.src[b + 1] = 1;
+      op2.coef[b + 1] = 0.5 * op.coef[b];
+      for (int i = 0; i < c->cfg.d; ++i) op2.f[b + 1][i] = op.f[b][i];
+    }
+    st = launch_apply(c, op2, uv, stg, app, u->cap, s);
+    if (st != HT_OK) return st;
+    return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
+  }
+  return HT_ERR_ARG;
+}
+
+// ---------------------------------------------------------------- misc --------
+extern "C" int ht_from_cp(ht_ctx* c, const cp_tensor* x, ht_tensor* out, void* stream) {
+  if (!c || !x || !tensor_matches(c, out) || x->d != c->cfg.d || x->rank < 1 || !x->weight) return HT_ERR_ARG;
+  if (x->rank > out->cap) return HT_ERR_CAPACITY;
+  for (int i = 0; i < x->d; ++i)
+    if (x->n[i] != c->cfg.n[i] || !x->factor[i]) return HT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* fp[HT_MAXD];
+  for (int i = 0; i < HT_MAXD; ++i) fp[i] = (i < x->d) ? x->factor[i] : nullptr;
+  const double** tbl = c->ptr_tbl;
+  if (cudaMemcpyAsync((void*)tbl, fp, sizeof(fp), cudaMemcpyHostToDevice, s) != cudaSuccess) return HT_ERR_CUDA;
+  dim3 g(64, c->tree.nn);
+  HTG_CHECK_LAUNCH(c, (from_cp_kernel<<<g, 256, 0, s>>>(c->tree, view_of(out), tbl, x->weight, x->rank),
+                       cudaGetLastError()));
+  c->last_stream = s;
+  return HT_OK;
+}
+
+static int run_inner(ht_ctx* c, const ht_tensor* u, const ht_tensor* w, double* out_dev, cudaStream_t s) {
+  // Grams per node in the workspace's per-node E buffers (Kc x Kc), temp in T1 of the root
+  double* gbuf = c->wn[0].Epre;   // nn * Kc^2 fits in Kc^3 for Kc >= 2d - 1
+  const long long gstride = (long long)c->Kc * c->Kc;
+  if ((long long)c->tree.nn * gstride > (long long)c->Kc * c->Kc * c->Kc) return HT_ERR_CAPACITY;
+  HtView uw = view_of(u);
+  HtView ww = w ? view_of(w) : uw;
+  HTG_CHECK_LAUNCH(c, (inner_kernel<<<1, 256, 0, s>>>(c->tree, uw, ww, w ? 0 : 1, gbuf, gstride, c->wn[0].T1, out_dev),
+                       cudaGetLastError()));
+  c->last_stream = s;
+  return HT_OK;
+}
+
+extern "C" int ht_mass(ht_ctx* c, const ht_tensor* u, double* out_dev, void* stream) {
+  if (!c || !tensor_matches(c, u) || !out_dev) return HT_ERR_ARG;
+  if (u->cap > c->Kc) return HT_ERR_CAPACITY;
+  return run_inner(c, u, nullptr, out_dev, (cudaStream_t)stream);
+}
+
+extern "C" int ht_inner(ht_ctx* c, const ht_tensor* u, const ht_tensor* w, double* out_dev, void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, w) || !out_dev) return HT_ERR_ARG;
+  if (u->cap > c->Kc || w->cap > c->Kc) return HT_ERR_CAPACITY;
+  return run_inner(c, u, w, out_dev, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- accessors -----
+CpWs* htg_ctx_cp(ht_ctx* c) { return &c->cp; }
+int htg_ctx_d(const ht_ctx* c) { return c->cfg.d; }
+const int* htg_ctx_n(const ht_ctx* c) { return c->cfg.n; }
+int* htg_ctx_err(ht_ctx* c) { return c->err; }
+int htg_ctx_grid(const ht_ctx* c) { return c->gemm_grid; }
+void htg_ctx_count(ht_ctx* c, int launches, cudaStream_t s) {
+  c->launches += launches;
+  c->last_stream = s;
+}
+int htg_cp_terms(int d) { return 1 + 2 * d + d * (d - 1) / 2; }

@@ -1,0 +1,102 @@
+// Batched small GEMMs for the HT contractions (mode products of transfer tensors,
+// leaf projections, factor products).  Sizes are read from device descriptors, so one
+// launch serves every node of a tree level whatever the ranks chosen on the device.
+//
+// Work decomposition: every descriptor contributes batch * tiles(m) * tiles(n) work items
+// of a 32 x 32 output tile; a fixed grid walks the items with a grid-stride loop.
+// FP64 on the CUDA cores (GB300 has no FP64 tensor-core path worth using).
+#include "common.cuh"
+
+namespace {
+
+constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
+constexpr int MAXD = 64;
+
+__global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc) {
+  __shared__ long long prefix[MAXD + 1];
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    long long acc = 0;
+    prefix[0] = 0;
+    for (int i = 0; i < ndesc; ++i) {
+      const GemmDesc& g = descs[i];
+      long long items = 0;
+      if (g.m > 0 && g.n > 0 && g.batch > 0)
+        items = (long long)g.batch * htg_cdiv(g.m, BM) * htg_cdiv(g.n, BN);
+      acc += items;
+      prefix[i + 1] = acc;
+    }
+  }
+  __syncthreads();
+  const long long total = prefix[ndesc];
+  const int tx = tid % 16, ty = tid / 16;
+  for (long long w = blockIdx.x; w < total; w += gridDim.x) {
+    int di = 0;
+    while (prefix[di + 1] <= w) ++di;
+    const GemmDesc g = descs[di];
+    long long loc = w - prefix[di];
+    const int tm = htg_cdiv(g.m, BM), tn = htg_cdiv(g.n, BN);
+    const int tile = (int)(loc % ((long long)tm * tn));
+    const int b = (int)(loc / ((long long)tm * tn));
+    const int i0 = (tile % tm) * BM, j0 = (tile / tm) * BN;
+    const double* A = g.A + (long long)b * g.sA;
+    const double* B = g.B + (long long)b * g.sB;
+    double* C = g.C + (long long)b * g.sC;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int l0 = 0; l0 < g.k; l0 += BK) {
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int e = tid + NT * p;
+        int i, l;
+        if (!g.tA) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
+        const int gi = i0 + i, gl = l0 + l;
+        double v = 0.0;
+        if (gi < g.m && gl < g.k) v = g.tA ? A[gl + (long long)g.lda * gi] : A[gi + (long long)g.lda * gl];
+        As[l][i] = v;
+        int j, l2;
+        if (!g.tB) { l2 = e % BK; j = e / BK; } else { j = e % BN; l2 = e / BN; }
+        const int gj = j0 + j, gl2 = l0 + l2;
+        double u = 0.0;
+        if (gj < g.n && gl2 < g.k) u = g.tB ? B[gj + (long long)g.ldb * gl2] : B[gl2 + (long long)g.ldb * gj];
+        Bs[l2][j] = u;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < BK; ++l) {
+        const double a0 = As[l][ty], a1 = As[l][ty + 16];
+        const double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+        acc[0][0] = fma(a0, b0, acc[0][0]);
+        acc[0][1] = fma(a0, b1, acc[0][1]);
+        acc[1][0] = fma(a1, b0, acc[1][0]);
+        acc[1][1] = fma(a1, b1, acc[1][1]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+        if (gi < g.m && gj < g.n) {
+          double v = g.alpha * acc[r][c];
+          if (g.colscale) v *= g.colscale[gj];
+          double* cp = C + gi + (long long)g.ldc * gj;
+          if (g.beta != 0.0) v += g.beta * *cp;
+          *cp = v;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s) {
+  if (ndesc <= 0) return cudaSuccess;
+  if (ndesc > MAXD) return cudaErrorInvalidValue;
+  if (grid < 1) grid = 1;
+  gemm_kernel<<<grid, NT, 0, s>>>(descs_dev, ndesc);
+  return cudaGetLastError();
+}
