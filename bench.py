@@ -1,0 +1,382 @@
+"""Benchmark: explicit time steps of 6-D advection held in HT and CP format on GB300.
+
+Workload (BASELINE config 2): u_t + c.grad u = 0 on [0,2pi)^6, n = 64 points per
+dimension, central differences, RK2 with dt = 0.2 h, initial condition
+sum_{m=1,2} prod_i exp(sin(x_i + phi_{m,i})) (c, phi seeded).  One step runs the whole hot
+path once:
+  HT route: ht_step = exact rank-3r RK2-polynomial apply + root-to-leaves HSVD truncation
+            (tol 1e-8, r_max 32);
+  CP route: cp_apply_rk2 (exact, rank 28 r) + cp_als_sweep (5 Gauss-Seidel sweeps, rank 24).
+value = steps/s with all inputs resident in HBM (CUDA events on the launching stream, L2
+flushed between timed steps).  e2e = the same through host buffers (pinned host -> device
+copy of the state, step, device -> host copy, every step).
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the method) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HT steps/s (apply+truncate) vs FP64 plain form at rel err ≤1e-6; % roofline"
+WORKLOAD = ("6-D advection n=64 (cfg2): HT r_max=32 tol=1e-8 + CP rank<=24 with 5 ALS sweeps, "
+            "RK2 dt=0.2h; one step = HT apply+HSVD truncate and CP apply+ALS")
+D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ oracle legs ----
+def oracle_sample(seconds: float) -> dict:
+    """Time the CPU oracle's HT + CP step on the same workload for about `seconds`."""
+    import numpy as np
+
+    from oracle import cp as OC
+    from oracle import ht as OH
+    from oracle.problems import advection_A
+    from paper_1803_10270_gb300.inputs import advection_case, cp_padding
+
+    case = advection_case(D, N, cfg_index=1)
+    A = advection_A(case)
+    u = OH.from_cp(np.ones(2), case.ic_factors())
+    x = OC.CP(np.ones(2), case.ic_factors())
+    pad = cp_padding([N] * D, CP_R - 2, seed=0x5EED + 1, scale=1e-3)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        u, _ = OH.step_rk2_poly(u, A, TOL, RMAX)
+        x, _ = OC.step_rk2(x, A, CP_R, pad, SWEEPS)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or steps >= 200:
+            break
+    return {"steps": steps, "seconds": el, "value": steps / el}
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """Run the oracle sample in a fresh single-threaded process (BLAS pinned to 1 thread)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--cpu-seconds", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=seconds * 10 + 120)
+    if r.returncode != 0:
+        return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": res["value"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{res['steps']} consecutive steps of the same workload from t=0 "
+                      f"(HT + CP routes) in {res['seconds']:.1f} s, FP64 numpy, 1 thread"}
+
+
+# ------------------------------------------------------------------ clocks ---------
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [l.strip().split(",") for l in self.f.read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU workload ---
+class Workload:
+    def __init__(self, G, device: int, precision: int):
+        import numpy as np
+        import torch
+
+        from paper_1803_10270_gb300.inputs import advection_case, cp_padding
+
+        self.G = G
+        self.case = advection_case(D, N, cfg_index=1)
+        self.ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=D, precision=precision, device=device)
+        self.op = G.advection_op(self.case.c, self.case.h)
+        self.u = G.HTTensor(D, [N] * D, RMAX)
+        self.X = G.CPTensor(D, [N] * D, CP_R)
+        self.Y = G.CPTensor(D, [N] * D, CP_R * (1 + 2 * D + D * (D - 1) // 2))
+        self.pad = cp_padding([N] * D, CP_R - 2, seed=0x5EED + 1, scale=1e-3)
+        self.np = np
+        self.torch = torch
+        self.reset()
+
+    def reset(self):
+        np = self.np
+        fac = self.case.ic_factors()
+        tr = self.u.tree
+        nodes = {}
+        for t in range(tr.n_nodes):
+            if tr.is_leaf(t):
+                nodes[t] = fac[tr.lo[t]]
+            elif t == 0:
+                nodes[t] = np.eye(2)
+            else:
+                B = np.zeros((2, 2, 2))
+                B[0, 0, 0] = B[1, 1, 1] = 1.0
+                nodes[t] = B
+        self.u.upload(nodes)
+        self.X.upload(np.ones(2), fac)
+        self.padded = False
+
+    def _pad_cp(self):
+        """First CP step: append the seeded padding columns (weight 1) up to rank 24."""
+        np = self.np
+        w, f = self.X.download()
+        nw = np.linalg.norm
+        # normalised columns, norms into the weights (as the oracle's pad does)
+        f2, w2 = [], w.copy()
+        for F in f:
+            nr = nw(F, axis=0)
+            f2.append(F / nr)
+            w2 = w2 * nr
+        self.X.upload(np.concatenate([w2, np.ones(CP_R - 2)]), [np.hstack([F, p]) for F, p in zip(f2, self.pad)])
+        self.padded = True
+
+    def step(self, stream=None):
+        G = self.G
+        G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=stream)
+        G.cp_apply_rk2(self.ctx, self.X, self.op, self.case.dt, self.Y, stream=stream)
+        G.cp_als_sweep(self.ctx, self.Y, self.X, SWEEPS, stream=stream)
+
+    def first_step(self):
+        """Step 1 builds y from the rank-2 state, then pads the iterate to rank 24."""
+        G = self.G
+        G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX)
+        X2 = G.CPTensor(D, [N] * D, 2)
+        w, f = self.X.download()
+        X2.upload(w, f)
+        G.cp_apply_rk2(self.ctx, X2, self.op, self.case.dt, self.Y)
+        self._pad_cp()
+        G.cp_als_sweep(self.ctx, self.Y, self.X, SWEEPS)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_1803_10270_gb300 import build as B
+    from paper_1803_10270_gb300 import htgpu as G
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    G.load()
+    prec = G.HT_PREC_FP64 if args.precision == "fp64" else G.HT_PREC_MIXED
+    W = Workload(G, local, prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    # warm-up (the first step pads the CP iterate to its target rank)
+    W.first_step()
+    for _ in range(max(args.warmup - 1, 0)):
+        W.step()
+    torch.cuda.synchronize()
+    W.ctx.check()
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = W.ctx.launches()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        W.step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = W.ctx.launches() - l0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    W.ctx.check()
+    t = torch.tensor([ms], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    value = world * args.steps / (ms_max * 1e-3)
+
+    # ---- e2e: state from pinned host memory each step, result back to the host
+    e2e = run_e2e(W, G, torch, min(args.steps, 50))
+    ranks = W.u.ranks()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic (seeded advection, BASELINE config 2)",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "ht_ranks_final": ranks,
+                       "cp_rank": CP_R, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(W, G, torch, steps: int) -> dict:
+    """Per step: pinned host -> device copy of the HT and CP state, ht_step + CP step, copy back."""
+    np = W.np
+    ubufs = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True) for b in W.u.bufs]
+    urank = torch.empty(W.u.rank_buf.numel(), dtype=torch.int32, pin_memory=True)
+    xbufs = [torch.empty(f.numel(), dtype=torch.float64, pin_memory=True) for f in W.X.factors]
+    xw = torch.empty(W.X.weight.numel(), dtype=torch.float64, pin_memory=True)
+    for h, d in zip(ubufs, W.u.bufs):
+        h.copy_(d)
+    urank.copy_(W.u.rank_buf)
+    for h, d in zip(xbufs, W.X.factors):
+        h.copy_(d)
+    xw.copy_(W.X.weight)
+    tr = W.u.tree
+
+    def used_sizes(rk):
+        sz = []
+        for t in range(tr.n_nodes):
+            if tr.is_leaf(t):
+                sz.append(N * rk[t])
+            else:
+                k1, k2 = rk[tr.c1[t]], rk[tr.c2[t]]
+                sz.append(k1 * k2 * (1 if t == 0 else rk[t]))
+        return sz
+
+    torch.cuda.synchronize()
+    rk = [int(v) for v in urank[: tr.n_nodes]]
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sz = used_sizes(rk)
+        W.u.rank_buf.copy_(urank, non_blocking=True)
+        h2d += urank.numel() * 4
+        for t, (h, d) in enumerate(zip(ubufs, W.u.bufs)):
+            d[: sz[t]].copy_(h[: sz[t]], non_blocking=True)
+            h2d += sz[t] * 8
+        for h, d in zip(xbufs, W.X.factors):
+            d.copy_(h, non_blocking=True)
+            h2d += h.numel() * 8
+        W.X.weight.copy_(xw, non_blocking=True)
+        h2d += xw.numel() * 8
+        W.step()
+        urank.copy_(W.u.rank_buf)       # synchronising: the new ranks size the copies below
+        d2h += urank.numel() * 4
+        rk = [int(v) for v in urank[: tr.n_nodes]]
+        sz = used_sizes(rk)
+        for t, (h, d) in enumerate(zip(ubufs, W.u.bufs)):
+            h[: sz[t]].copy_(d[: sz[t]], non_blocking=True)
+            d2h += sz[t] * 8
+        for h, d in zip(xbufs, W.X.factors):
+            h.copy_(d, non_blocking=True)
+            d2h += h.numel() * 8
+        xw.copy_(W.X.weight, non_blocking=True)
+        d2h += xw.numel() * 8
+        torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": steps / el, "unit": "steps/s", "h2d_bytes_per_step": h2d // steps,
+            "d2h_bytes_per_step": d2h // steps, "steps": steps}
+
+
+def run_reference(args):
+    """The oracle on the host cores, on the same config, metric and unit."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    per = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(per / 4)
+    vals = []
+    total_steps, total_s = 0, 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(per)
+        vals.append(r["value"])
+        total_steps += r["steps"]
+        total_s += r["seconds"]
+    v = total_steps / total_s
+    out = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": 0, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded advection, BASELINE config 2)",
+           "impl": "reference",
+           "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)"},
+           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{args.steps} samples of up to {per:.1f} s, each from t=0, "
+                                      f"FP64 numpy oracle ({total_steps} steps)"},
+           "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.cpu_seconds)))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -105,7 +105,11 @@ def _mode_solve(y: CP, x_factors: list, k: int):
         Gam *= x_factors[j].T @ x_factors[j]
         H *= y.factors[j].T @ x_factors[j]
     rhs = y.factors[k] @ (y.weights[:, None] * H)          # n_k x r
-    L = np.linalg.cholesky(Gam)                              # Gam = L L^T
+    try:
+        L = np.linalg.cholesky(Gam)                          # Gam = L L^T
+    except np.linalg.LinAlgError:
+        # Section 2.1: poorly conditioned ALS matrices are regularised; shift only on failure
+        L = np.linalg.cholesky(Gam + (1e-14 * np.trace(Gam) / r) * np.eye(r))
     Z = np.linalg.solve(L, rhs.T)                            # forward substitution
     return np.linalg.solve(L.T, Z).T                         # back substitution
 
