@@ -210,6 +210,24 @@ int cp_als_sweep(ht_ctx* ctx, const cp_tensor* y, cp_tensor* x, int sweeps, int 
 int cp_apply_rk2(ht_ctx* ctx, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y,
                  void* stream);
 
+/* ----------------------------------------------------- allocation-free ---- */
+/* cp_als_sweep for callers that cannot allocate device memory (no ht_ctx needed).
+ * The paper has no counterpart: this is a deployment variant of cp_als_sweep.
+ * Who needs it: code running where cudaMalloc is unavailable or forbidden -- inside
+ * host callbacks or plug-ins with a fixed memory budget, or processes whose device
+ * memory is reserved up front by another framework.
+ * Same arguments and results as cp_als_sweep, plus status_dev (device int, or NULL)
+ * which receives the device error word (HT_OK or HT_ERR_NONFINITE) at the end.
+ * Scratch: one file-scope __device__ array of about 3.0 MB that every GPU loading the
+ * library holds until exit.  Limits: d <= 8, n_k <= 256, x rank <= 32, y rank <= 1024;
+ * larger sizes return HT_ERR_CAPACITY before anything is launched.  Allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine).  The first call on a device
+ * looks up the array's address with that device current: make it before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race and must
+ * be serialised by the caller.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
+int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int variant, double* eps_dev,
+                         int* status_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -379,3 +379,144 @@ extern "C" int cp_als_sweep(ht_ctx* c, const cp_tensor* y, cp_tensor* x, int swe
   htg_ctx_count(c, launches, s);
   return HT_OK;
 }
+
+// ============================================================================
+// Allocation-free variant of cp_als_sweep.
+//
+// Some callers cannot allocate device memory at all: code that runs inside a host
+// callback or a driver-managed plug-in with a fixed memory budget, processes whose GPU
+// memory is fully reserved up front by another framework, or environments where
+// cudaMalloc is forbidden after initialisation.  cp_als_sweep_noalloc serves them: it
+// needs no ht_ctx and calls no allocator.  Its scratch (Grams, right-hand sides,
+// descriptors, the error word) lives in one file-scope __device__ array of fixed size
+// that every GPU loading this library holds until the process exits.
+//
+// Limits: d <= 8, n_k <= 256, x rank <= 32, y rank <= 1024 (about 3.0 MB of scratch).
+// The array is shared by every call: calls whose work overlaps on the GPU (two streams,
+// two host threads) race on it and must be serialised by the caller.  The first call
+// on a device looks up the array's device address (cudaGetSymbolAddress) with that
+// device current; make that first call before any stream capture.
+// ============================================================================
+#include <mutex>
+
+namespace {
+
+constexpr int NA_MAXD = 8, NA_MAXN = 256, NA_MAXR = 32, NA_MAXRY = 1024;
+constexpr size_t NA_G = (size_t)NA_MAXD * NA_MAXR * NA_MAXR;
+constexpr size_t NA_H = (size_t)NA_MAXD * NA_MAXRY * NA_MAXR;
+constexpr size_t NA_HH = (size_t)NA_MAXRY * NA_MAXR;
+constexpr size_t NA_GAM = (size_t)NA_MAXR * NA_MAXR;
+constexpr size_t NA_RHS = (size_t)NA_MAXN * NA_MAXR;
+constexpr size_t NA_XOLD = (size_t)NA_MAXD * NA_MAXN * NA_MAXR;
+constexpr size_t NA_WOLD = NA_MAXR;
+constexpr size_t NA_EPS = 64;
+constexpr size_t NA_DESC = (4 * HT_MAXD * sizeof(GemmDesc) + sizeof(double) - 1) / sizeof(double);
+constexpr size_t NA_ERR = 4;
+constexpr size_t NA_TOTAL = NA_G + NA_H + NA_HH + NA_GAM + NA_RHS + NA_XOLD + NA_WOLD + NA_EPS + NA_DESC + NA_ERR;
+
+__device__ __align__(256) double g_cp_noalloc_scratch[NA_TOTAL];
+
+__global__ void na_status_kernel(const int* err, int* out) {
+  if (threadIdx.x == 0) *out = *err;
+}
+
+struct NaDevice {
+  double* base = nullptr;
+  int grid = 0;
+  bool ready = false;
+};
+NaDevice g_na_dev[64];
+std::mutex g_na_mutex;
+
+}  // namespace
+
+extern "C" int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int variant, double* eps_dev,
+                                    int* status_dev, void* stream) {
+  if (!x || !y || sweeps < 0 || sweeps > 64) return HT_ERR_ARG;
+  if (variant != CP_ALS_GS && variant != CP_ALS_JACOBI_DAMPED) return HT_ERR_ARG;
+  const int d = x->d;
+  if (d < 2 || d > HT_MAXD || y->d != d || x->rank < 1 || y->rank < 1 || !x->weight || !y->weight)
+    return HT_ERR_ARG;
+  if (x->rank > x->cap || y->rank > y->cap) return HT_ERR_CAPACITY;
+  if (d > NA_MAXD || x->rank > NA_MAXR || y->rank > NA_MAXRY) return HT_ERR_CAPACITY;
+  for (int k = 0; k < d; ++k) {
+    if (x->n[k] != y->n[k] || x->n[k] < 1 || !x->factor[k] || !y->factor[k]) return HT_ERR_ARG;
+    if (x->n[k] > NA_MAXN) return HT_ERR_CAPACITY;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return HT_ERR_CUDA;
+  NaDevice* nd = &g_na_dev[dev];
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!nd->ready) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_cp_noalloc_scratch) != cudaSuccess || p == nullptr) return HT_ERR_CUDA;
+      int sms = 0;
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HT_ERR_CUDA;
+      nd->base = (double*)p;
+      nd->grid = htg_max(1, sms) * 4;
+      nd->ready = true;
+    }
+  }
+  double* b = nd->base;
+  CpWs w;
+  w.G = b; b += NA_G;
+  w.H = b; b += NA_H;
+  w.Hh = b; b += NA_HH;
+  w.Gam = b; b += NA_GAM;
+  w.RHS = b; b += NA_RHS;
+  w.Xold = b; b += NA_XOLD;
+  w.wold = b; b += NA_WOLD;
+  w.epsacc = b; b += NA_EPS;
+  w.descs = (GemmDesc*)b; b += NA_DESC;
+  int* err = (int*)b;
+  w.rcap = NA_MAXR;
+  w.rycap = NA_MAXRY;
+  w.nmax = NA_MAXN;
+
+  CpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.d = d; a.r = x->rank; a.ry = y->rank; a.variant = variant;
+  for (int k = 0; k < d; ++k) {
+    a.n[k] = x->n[k];
+    a.X[k] = x->factor[k];
+    a.Y[k] = y->factor[k];
+  }
+  a.mu = y->weight;
+  a.lam = x->weight;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = nd->grid;
+  // the error word starts at zero on every call; everything else is written before it is read
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return HT_ERR_CUDA;
+#define NAL(expr)                                                  \
+  do {                                                             \
+    expr;                                                          \
+    if (cudaGetLastError() != cudaSuccess) return HT_ERR_CUDA;     \
+  } while (0)
+  const int fold = (variant == CP_ALS_JACOBI_DAMPED) ? 1 : 0;
+  NAL((cp_eps_init_kernel<<<1, 64, 0, s>>>(w, sweeps)));
+  NAL((cp_plan_kernel<<<1, 1, 0, s>>>(a, w)));
+  NAL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, fold)));
+  for (int k = 0; k < d; ++k)
+    if (htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
+  const size_t solve_smem = ((size_t)a.r * a.r + a.r) * sizeof(double);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int k = 0; k < d; ++k) {
+      NAL((cp_hadamard_kernel<<<32, NT, 0, s>>>(a, w, k)));
+      if (htg_launch_gemm(w.descs + 3 * k, 1, grid, s) != cudaSuccess) return HT_ERR_CUDA;
+      NAL((cp_solve_kernel<<<1, NT, solve_smem, s>>>(a, w, k, sw, err)));
+      if (variant == CP_ALS_GS && htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess)
+        return HT_ERR_CUDA;
+    }
+    if (variant == CP_ALS_JACOBI_DAMPED) {
+      NAL((cp_damp_kernel<<<dim3(8, d), NT, 0, s>>>(a, w)));
+      for (int k = 0; k < d; ++k)
+        if (htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
+    }
+  }
+  if (variant == CP_ALS_JACOBI_DAMPED) NAL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, 0)));
+  if (eps_dev && sweeps > 0) NAL((cp_eps_out_kernel<<<1, 64, 0, s>>>(w, sweeps, eps_dev)));
+  if (status_dev) NAL((na_status_kernel<<<1, 32, 0, s>>>(err, status_dev)));
+#undef NAL
+  return HT_OK;
+}

@@ -76,6 +76,8 @@ _EXPORTS = {
                                C.POINTER(cp_tensor), C.c_void_p]),
     "cp_als_sweep": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                C.c_void_p, C.c_void_p]),
+    "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -396,3 +398,13 @@ def cp_als_sweep(ctx: Context, y: CPTensor, x: CPTensor, sweeps: int, variant: i
     _check(load().cp_als_sweep(ctx.ptr, C.byref(y.struct), C.byref(x.struct), sweeps, variant,
                                C.c_void_p(eps.data_ptr() if eps is not None else 0), _stream_ptr(stream)),
            "cp_als_sweep")
+
+
+def cp_als_sweep_noalloc(y: CPTensor, x: CPTensor, sweeps: int, variant: int = CP_ALS_GS, eps=None, status=None,
+                         stream=None):
+    """ALS sweeps without a context and without any device allocation (fixed-size static
+    scratch; see include/htgpu.h for the limits and the rule on overlapping calls)."""
+    _check(load().cp_als_sweep_noalloc(C.byref(y.struct), C.byref(x.struct), sweeps, variant,
+                                       C.c_void_p(eps.data_ptr() if eps is not None else 0),
+                                       C.c_void_p(status.data_ptr() if status is not None else 0),
+                                       _stream_ptr(stream)), "cp_als_sweep_noalloc")
