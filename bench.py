@@ -6,7 +6,8 @@ sum_{m=1,2} prod_i exp(sin(x_i + phi_{m,i})) (c, phi seeded).  One step runs the
 path once:
   HT route: ht_step = exact rank-3r RK2-polynomial apply + root-to-leaves HSVD truncation
             (tol 1e-8, r_max 32);
-  CP route: cp_apply_rk2 (exact, rank 28 r) + cp_als_sweep (5 Gauss-Seidel sweeps, rank 24).
+  CP route: cp_als_sweep_rk2 = 5 Gauss-Seidel ALS sweeps (rank 24) towards the exact
+            y = p(dt L) x_n (rank 28 r), with y represented by its factor powers.
 value = steps/s with all inputs resident in HBM (CUDA events on the launching stream, L2
 flushed between timed steps).  e2e = the same through host buffers (pinned host -> device
 copy of the state, step, device -> host copy, every step).
@@ -34,6 +35,12 @@ METRIC = "HT steps/s (apply+truncate) vs FP64 plain form at rel err ≤1e-6; % r
 WORKLOAD = ("6-D advection n=64 (cfg2): HT r_max=32 tol=1e-8 + CP rank<=24 with 5 ALS sweeps, "
             "RK2 dt=0.2h; one step = HT apply+HSVD truncate and CP apply+ALS")
 D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
+# FP64 peak of GB300 derived from the nominal 1.25 TFLOP/s: 152 SMs x 2070 MHz x 4 FP64
+# flop/clk/SM (2 FMA/clk/SM).  An FMA-chain probe measured 1.196 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel", "qr": "qr_r_kernel",
+                "svd": "svd_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
+                "cp_small": "cp_hadamard_rk2_kernel/cp_normalize_kernel/...", "cp_solve": "cp_solve_kernel"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -47,6 +54,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="launch every kernel per step instead of a CUDA graph")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
@@ -142,11 +150,11 @@ class Workload:
 
         self.G = G
         self.case = advection_case(D, N, cfg_index=1)
-        self.ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=D, precision=precision, device=device)
+        # Kronecker-sum RK2 steps raise ranks by 3: max_terms=1 sizes the workspace for that
+        self.ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=1, precision=precision, device=device)
         self.op = G.advection_op(self.case.c, self.case.h)
         self.u = G.HTTensor(D, [N] * D, RMAX)
         self.X = G.CPTensor(D, [N] * D, CP_R)
-        self.Y = G.CPTensor(D, [N] * D, CP_R * (1 + 2 * D + D * (D - 1) // 2))
         self.pad = cp_padding([N] * D, CP_R - 2, seed=0x5EED + 1, scale=1e-3)
         self.np = np
         self.torch = torch
@@ -187,19 +195,18 @@ class Workload:
     def step(self, stream=None):
         G = self.G
         G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=stream)
-        G.cp_apply_rk2(self.ctx, self.X, self.op, self.case.dt, self.Y, stream=stream)
-        G.cp_als_sweep(self.ctx, self.Y, self.X, SWEEPS, stream=stream)
+        # CP route: ALS towards y = p(dt L) x_n with x_n as warm start (y never formed)
+        G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=stream)
 
     def first_step(self):
-        """Step 1 builds y from the rank-2 state, then pads the iterate to rank 24."""
+        """Step 1: the rank-2 state defines y; the iterate is that state padded to rank 24."""
         G = self.G
         G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX)
+        self._pad_cp()
         X2 = G.CPTensor(D, [N] * D, 2)
         w, f = self.X.download()
-        X2.upload(w, f)
-        G.cp_apply_rk2(self.ctx, X2, self.op, self.case.dt, self.Y)
-        self._pad_cp()
-        G.cp_als_sweep(self.ctx, self.Y, self.X, SWEEPS)
+        X2.upload(w[:2], [F[:, :2] for F in f])
+        G.cp_als_sweep_rk2(self.ctx, X2, self.op, self.case.dt, self.X, SWEEPS)
 
 
 def run_gpu(args):
@@ -231,6 +238,19 @@ def run_gpu(args):
     torch.cuda.synchronize()
     W.ctx.check()
 
+    # ---- one step captured as a CUDA graph (ranks live on the device, no host sync inside)
+    graph = None
+    per_step_launches = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        l0 = W.ctx.launches()
+        with torch.cuda.graph(graph):
+            W.step()
+        per_step_launches = W.ctx.launches() - l0
+        torch.cuda.synchronize()
+        graph.replay()          # one more warm-up step through the graph
+        torch.cuda.synchronize()
+
     # ---- timed region: device-resident inputs, L2 flushed between steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -241,10 +261,13 @@ def run_gpu(args):
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        W.step()
+        if graph is not None:
+            graph.replay()
+        else:
+            W.step()
         ev[i][1].record(stream)
     torch.cuda.synchronize()
-    launches = W.ctx.launches() - l0
+    launches = (W.ctx.launches() - l0) if graph is None else per_step_launches * args.steps
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -255,6 +278,10 @@ def run_gpu(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t[0])
     value = world * args.steps / (ms_max * 1e-3)
+
+    # ---- roofline: per-kernel-class CUDA-event time on the launching stream over a second
+    #      timed region (same steps, L2 flushed, no graph so each launch can be bracketed)
+    roof, shares = profile_pass(W, torch, flush, min(args.steps, 50))
 
     # ---- e2e: state from pinned host memory each step, result back to the host
     e2e = run_e2e(W, G, torch, min(args.steps, 50))
@@ -268,14 +295,57 @@ def run_gpu(args):
             "data": "synthetic (seeded advection, BASELINE config 2)",
             "config": {"workload": WORKLOAD, "precision": args.precision, "ht_ranks_final": ranks,
                        "cp_rank": CP_R, "l2": "flushed between timed steps (256 MB write)",
+                       "cuda_graph": graph is not None,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roof, "kernel_shares": shares,
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def load_traffic() -> dict:
+    """DRAM bytes per launch per kernel from the committed ncu summary (profiles/traffic.json)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def profile_pass(W, torch, flush, steps: int):
+    """Event-time every kernel class over `steps` steps; roofline of the dominant class."""
+    W.ctx.profile(True)
+    for _ in range(steps):
+        flush.zero_()
+        W.step()
+    torch.cuda.synchronize()
+    prof = W.ctx.profile_read()
+    W.ctx.profile(False)
+    total = sum(v["ms"] for v in prof.values()) or 1.0
+    shares = {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
+                  "share": v["ms"] / total} for k, v in prof.items() if v["launches"]}
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    v = prof[dom]
+    roof = {"kernel": KERNEL_NAMES.get(dom, dom), "class": dom, "bound": "alu", "unit": "TFLOP/s",
+            "peak": FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM)",
+            "achieved": None, "frac": None, "traffic": None, "avg_launch_us": None, "steps": steps}
+    if v["launches"]:
+        per_launch_s = v["ms"] * 1e-3 / v["launches"]
+        roof["avg_launch_us"] = per_launch_s * 1e6
+        if v["flops"] > 0:
+            ach = v["flops"] / v["launches"] / per_launch_s / 1e12
+            roof["achieved"] = ach
+            roof["frac"] = ach / FP64_PEAK_TFLOPS
+            roof["flops_per_launch"] = v["flops"] / v["launches"]
+    tr = load_traffic().get(roof["kernel"].split("/")[0])
+    if tr is not None:
+        roof["traffic"] = tr
+    return roof, shares
 
 
 def run_e2e(W, G, torch, steps: int) -> dict:

@@ -140,6 +140,17 @@ int ht_ctx_check(ht_ctx* ctx, void* stream);
 /* Number of kernel launches the context issued since creation (host counter). */
 long long ht_ctx_launches(const ht_ctx* ctx);
 
+/* Opt-in event profiler (off by default).  on = 1 clears the accumulators and starts
+ * recording a CUDA event pair on the launching stream around every kernel launch of the
+ * context; the FP64-bound kernels also add the FP64 flops they execute to a device
+ * counter per kernel class.  on = 0 stops recording.  Not for use inside stream capture. */
+int ht_ctx_profile(ht_ctx* ctx, int on);
+
+/* Per kernel class (7 classes: apply, gemm, qr, svd, plan/rank, cp small kernels,
+ * cp solve) the summed event time in ms, the launch count and the counted FP64 flops.
+ * Synchronises on the recorded events.  Any output pointer may be NULL. */
+int ht_ctx_profile_read(ht_ctx* ctx, double* ms, long long* launches, double* flops);
+
 /* Human-readable name of a status code. */
 const char* ht_status_string(int status);
 
@@ -209,6 +220,16 @@ int cp_als_sweep(ht_ctx* ctx, const cp_tensor* y, cp_tensor* x, int sweeps, int 
  * y->cap >= x->rank * (1 + 2d + d(d-1)/2).  Sets y->rank on the host. */
 int cp_apply_rk2(ht_ctx* ctx, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y,
                  void* stream);
+
+/* ALS rank reduction towards the implicit y = p(dt L) x_old (kron_sum L), without forming y:
+ * the same result as cp_apply_rk2 followed by cp_als_sweep (Section 3.2: explicit step
+ * then ALS rank reduction; Section 2.1 normal equations).  The factors of y are built
+ * from the powers A_j^p X_old,j (p <= 2), so the right-hand side of mode k contracts
+ * over 3 r0 columns instead of r0 (1 + 2d + d(d-1)/2).  x holds the initial iterate
+ * (rank x->rank) and receives the fit; x_old (rank r0) may alias x (it is read first).
+ * Errors: HT_ERR_ARG, HT_ERR_CAPACITY (x rank > 64 or above the context capacity). */
+int cp_als_sweep_rk2(ht_ctx* ctx, const cp_tensor* x_old, const ht_op* L, double dt, cp_tensor* x,
+                     int sweeps, int variant, double* eps_dev, void* stream);
 
 /* ----------------------------------------------------- allocation-free ---- */
 /* cp_als_sweep for callers that cannot allocate device memory (no ht_ctx needed).

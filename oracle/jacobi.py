@@ -6,7 +6,8 @@ SVD of an m x k matrix A (m >= k after the caller's QR) by orthogonalising its
 columns with plane rotations:
 
   for a column pair (p, q): alpha = |a_p|^2, beta = |a_q|^2, gamma = a_p . a_q;
-  if |gamma| > tol * sqrt(alpha beta): zeta = (beta - alpha) / (2 gamma),
+  if |gamma| > tol * sqrt(alpha beta) (tol = eps * max(m, 8), the rounding level of a
+  length-m dot product): zeta = (beta - alpha) / (2 gamma),
   t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
   [a_p, a_q] <- [c a_p - s a_q, s a_p + c a_q]  (same rotation on V).
 
@@ -39,10 +40,12 @@ def _round_robin(k: int):
     return rounds
 
 
-def jacobi_svd(A: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
+def jacobi_svd(A: np.ndarray, tol: float | None = None, max_sweeps: int = 60):
     """Return (U, s, V) with A = U diag(s) V^T, s descending; A is m x k with m >= k."""
     A = np.array(A, dtype=np.float64, copy=True)
     m, k = A.shape
+    if tol is None:
+        tol = np.finfo(np.float64).eps * max(m, 8)
     if m < k:
         raise ValueError("jacobi_svd expects m >= k (QR-reduce wide matrices first)")
     V = np.eye(k)

@@ -90,25 +90,39 @@ __global__ void cp_apply_kernel(StencilArgs a) {
 }
 
 // Unit columns, norms into the weights (GS) or folded into factor 0 (Jacobi variant).
+// One CTA: column norms of every factor (one warp per (dim, column)), then the scaling.
 __global__ void cp_normalize_kernel(CpArgs a, int fold) {
-  for (int l = threadIdx.x; l < a.r; l += blockDim.x) {
+  __shared__ double nrm[HT_MAXD * 64];
+  __shared__ double wfin[64];
+  const int tid = threadIdx.x, lane = tid & 31, nw = blockDim.x >> 5;
+  if (a.r > 64) return;   // callers keep r <= 64 (checked on the host)
+  for (int p = tid >> 5; p < a.d * a.r; p += nw) {
+    const int k = p / a.r, l = p % a.r;
+    const double* col = a.X[k] + (long long)a.n[k] * l;
+    double s = 0.0;
+    for (int j = lane; j < a.n[k]; j += 32) s = fma(col[j], col[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[p] = sqrt(s);
+  }
+  __syncthreads();
+  for (int l = tid; l < a.r; l += blockDim.x) {
     double w = a.lam[l];
     for (int k = 0; k < a.d; ++k) {
-      double* col = a.X[k] + (long long)a.n[k] * l;
-      double s = 0.0;
-      for (int j = 0; j < a.n[k]; ++j) s = fma(col[j], col[j], s);
-      const double nr = sqrt(s);
-      if (nr > 0.0) {
-        for (int j = 0; j < a.n[k]; ++j) col[j] /= nr;
-        w *= nr;
-      }
+      const double nr = nrm[k * a.r + l];
+      if (nr > 0.0) w *= nr;
+      nrm[k * a.r + l] = nr > 0.0 ? 1.0 / nr : 1.0;
     }
-    if (fold) {
-      double* col = a.X[0] + (long long)a.n[0] * l;
-      for (int j = 0; j < a.n[0]; ++j) col[j] *= w;
-      a.lam[l] = 1.0;
-    } else {
-      a.lam[l] = w;
+    wfin[l] = w;
+    a.lam[l] = fold ? 1.0 : w;
+  }
+  __syncthreads();
+  for (int k = 0; k < a.d; ++k) {
+    const int n = a.n[k];
+    for (long long e = tid; e < (long long)n * a.r; e += blockDim.x) {
+      const int l = (int)(e / n);
+      double v = a.X[k][e] * nrm[k * a.r + l];
+      if (fold && k == 0) v *= wfin[l];
+      a.X[k][e] = v;
     }
   }
 }
@@ -136,69 +150,80 @@ __global__ void cp_hadamard_kernel(CpArgs a, CpWs w, int k) {
 
 // Cholesky of Gamma (FP64), X~ = RHS Gamma^{-1}; then either (GS) normalise into X_k and
 // lam, or (Jacobi) store X~ into Xold slot k.  Records |X~ - X_old lam_old| / |X_old lam_old|.
-__global__ void cp_solve_kernel(CpArgs a, CpWs w, int k, int sweep, int* err) {
+// The factorisation is right-looking and column parallel; every division is replaced by a
+// multiplication with a reciprocal computed once (FP64 divides are long instruction
+// sequences and each FP64 warp instruction holds the FP64 pipe for the whole warp).
+__global__ void cp_solve_kernel(CpArgs a, CpWs w, int k, int sweep, int* err, double* flops) {
   extern __shared__ double sh[];
   const int r = a.r, n = a.n[k];
-  double* Lm = sh;               // r x r
-  double* nrm = sh + r * r;      // r
+  double* Lm = sh;               // r x r (lower triangle used)
+  double* rinv = sh + r * r;     // r reciprocals of the diagonal, later of the column norms
+  double* Xs = rinv + r;         // n x r staged rows
   __shared__ int ok;
   __shared__ double red_num[NT / 32], red_den[NT / 32];
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Lm[e] = w.Gam[e];
-  __syncthreads();
+  const int tid = threadIdx.x;
   for (int attempt = 0; attempt < 2; ++attempt) {
-    if (threadIdx.x == 0) {
-      ok = 1;
-      if (attempt == 1) {
-        double tr = 0.0;
-        for (int i = 0; i < r; ++i) tr += w.Gam[i + r * i];
-        for (int e = 0; e < r * r; ++e) Lm[e] = w.Gam[e];
-        const double sh_ = 1e-14 * tr / r;
-        for (int i = 0; i < r; ++i) Lm[i + r * i] += sh_;
-      }
-      // column-oriented Cholesky, lower triangle: Gamma = L L^T
-      for (int j = 0; j < r && ok; ++j) {
-        double dj = Lm[j + r * j];
-        for (int p = 0; p < j; ++p) dj -= Lm[j + r * p] * Lm[j + r * p];
-        if (!(dj > 0.0)) { ok = 0; break; }
-        dj = sqrt(dj);
-        Lm[j + r * j] = dj;
-        for (int i = j + 1; i < r; ++i) {
-          double v = Lm[i + r * j];
-          for (int p = 0; p < j; ++p) v -= Lm[i + r * p] * Lm[j + r * p];
-          Lm[i + r * j] = v / dj;
-        }
-      }
+    double shift = 0.0;
+    if (attempt == 1) {
+      double tr = 0.0;
+      for (int i = 0; i < r; ++i) tr += w.Gam[i + r * i];
+      shift = 1e-14 * tr / r;
     }
+    for (int e = tid; e < r * r; e += blockDim.x) Lm[e] = w.Gam[e] + ((e % r == e / r) ? shift : 0.0);
+    if (tid == 0) ok = 1;
     __syncthreads();
+    for (int j = 0; j < r; ++j) {
+      if (tid == 0) {
+        const double dj = Lm[j + r * j];
+        if (!(dj > 0.0)) ok = 0;
+        const double sq = ok ? sqrt(dj) : 1.0;
+        Lm[j + r * j] = sq;
+        rinv[j] = 1.0 / sq;
+      }
+      __syncthreads();
+      if (!ok) break;
+      const double inv = rinv[j];
+      for (int i = j + 1 + tid; i < r; i += blockDim.x) Lm[i + r * j] *= inv;
+      __syncthreads();
+      // trailing update of the lower triangle: L[i][c] -= L[i][j] L[c][j], j < c <= i
+      const int m = r - j - 1;
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = j + 1 + e % m, cc = j + 1 + e / m;
+        if (cc <= i) Lm[i + r * cc] -= Lm[i + r * j] * Lm[cc + r * j];
+      }
+      __syncthreads();
+    }
     const int good = ok;
     __syncthreads();
     if (good) break;
   }
   if (!ok) {
-    if (threadIdx.x == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
+    if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
     return;
   }
-  // rows: solve L L^T x = rhs, x^T is row i of X~ (stored into RHS in place)
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double* row = w.RHS + i;   // stride n between columns
+  // rows: solve L L^T x = rhs, x^T is row i of X~
+  for (long long e = tid; e < (long long)n * r; e += blockDim.x) Xs[e] = w.RHS[e];
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) {
+    double* row = Xs + i;   // stride n between columns
     for (int j = 0; j < r; ++j) {
       double v = row[(long long)n * j];
       for (int p = 0; p < j; ++p) v -= Lm[j + r * p] * row[(long long)n * p];
-      row[(long long)n * j] = v / Lm[j + r * j];
+      row[(long long)n * j] = v * rinv[j];
     }
     for (int j = r - 1; j >= 0; --j) {
       double v = row[(long long)n * j];
       for (int p = j + 1; p < r; ++p) v -= Lm[p + r * j] * row[(long long)n * p];
-      row[(long long)n * j] = v / Lm[j + r * j];
+      row[(long long)n * j] = v * rinv[j];
     }
   }
   __syncthreads();
-  // convergence measure against the old (scaled) factor, then store
+  // convergence measure against the old (scaled) factor
   double num = 0.0, den = 0.0;
-  for (long long e = threadIdx.x; e < (long long)n * r; e += blockDim.x) {
+  for (long long e = tid; e < (long long)n * r; e += blockDim.x) {
     const int l = (int)(e / n);
     const double old = a.X[k][e] * (a.variant == CP_ALS_GS ? a.lam[l] : 1.0);
-    const double df = w.RHS[e] - old;
+    const double df = Xs[e] - old;
     num = fma(df, df, num);
     den = fma(old, old, den);
   }
@@ -206,28 +231,36 @@ __global__ void cp_solve_kernel(CpArgs a, CpWs w, int k, int sweep, int* err) {
     num += __shfl_xor_sync(0xffffffffu, num, o);
     den += __shfl_xor_sync(0xffffffffu, den, o);
   }
-  if ((threadIdx.x & 31) == 0) { red_num[threadIdx.x >> 5] = num; red_den[threadIdx.x >> 5] = den; }
-  for (int l = threadIdx.x; l < r; l += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) s = fma(w.RHS[j + (long long)n * l], w.RHS[j + (long long)n * l], s);
-    nrm[l] = sqrt(s);
-  }
+  if ((tid & 31) == 0) { red_num[tid >> 5] = num; red_den[tid >> 5] = den; }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // column norms: one warp per column
+  for (int l = tid >> 5; l < r; l += blockDim.x >> 5) {
+    double s2 = 0.0;
+    for (int j = tid & 31; j < n; j += 32) s2 = fma(Xs[j + (long long)n * l], Xs[j + (long long)n * l], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if ((tid & 31) == 0) {
+      const double nr = sqrt(s2);
+      a.lam[l] = (a.variant == CP_ALS_GS) ? nr : a.lam[l];
+      rinv[l] = nr > 0.0 ? 1.0 / nr : 1.0;
+    }
+  }
+  if (tid == 0 && flops) {
+    // Cholesky (r^3/3 multiply-adds), two triangular solves per row, measure and norms
+    const double rr = (double)r;
+    atomicAdd(flops, 2.0 * rr * rr * rr / 3.0 + 2.0 * n * rr * rr + 6.0 * n * rr);
+  }
+  if (tid == 0) {
     double tn = 0.0, td = 0.0;
     for (int q = 0; q < NT / 32; ++q) { tn += red_num[q]; td += red_den[q]; }
     const double ek = td > 0.0 ? sqrt(tn / td) : sqrt(tn);
     if (ek > w.epsacc[sweep]) w.epsacc[sweep] = ek;
   }
+  __syncthreads();
   if (a.variant == CP_ALS_GS) {
-    for (long long e = threadIdx.x; e < (long long)n * r; e += blockDim.x) {
-      const int l = (int)(e / n);
-      a.X[k][e] = nrm[l] > 0.0 ? w.RHS[e] / nrm[l] : w.RHS[e];
-    }
-    for (int l = threadIdx.x; l < r; l += blockDim.x) a.lam[l] = nrm[l] > 0.0 ? nrm[l] : 0.0;
+    for (long long e = tid; e < (long long)n * r; e += blockDim.x) a.X[k][e] = Xs[e] * rinv[e / n];
   } else {
     double* dst = w.Xold + (long long)k * w.nmax * w.rcap;
-    for (long long e = threadIdx.x; e < (long long)n * r; e += blockDim.x) dst[e] = w.RHS[e];
+    for (long long e = tid; e < (long long)n * r; e += blockDim.x) dst[e] = Xs[e];
   }
 }
 
@@ -280,6 +313,306 @@ __global__ void cp_plan_kernel(CpArgs a, CpWs w) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// ALS against the implicit y = p(dt L) x_old (Kronecker-sum L): the factors of y are
+// built from the three powers Z_j^(p) = A_j^p X_old,j (p = 0, 1, 2), so with
+// M_j^(p) = Z_j^(p)T X_j (r0 x r) the mode-k system becomes
+//   RHS = sum_p Z_k^(p) Hs_p,  Hs_p = sum_{tau : p_tau(k) = p} c_tau diag(mu) hadamard_{j!=k} M_j^(p_tau(j))
+// with the column types tau of cp_apply_rk2.  Same result as cp_als_sweep on the formed y.
+// ---------------------------------------------------------------------------
+struct PowArgs {
+  int d, r0;
+  int n[HT_MAXD];
+  int hw[HT_MAXD];
+  double c[HT_MAXD][HT_MAXSTENCIL];
+  const double* X[HT_MAXD];
+};
+
+__global__ void cp_powers_kernel(PowArgs a, CpWs w) {
+  extern __shared__ double sh[];
+  const int k = blockIdx.y, l = blockIdx.x;
+  const int n = a.n[k];
+  double* x = sh;
+  double* ax = sh + n;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = a.X[k][j + (long long)n * l];
+  __syncthreads();
+  double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;   // n x 3 r0, ld n
+  const int hw = a.hw[k];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s = 0.0;
+    for (int o = -hw; o <= hw; ++o) {
+      int jj = (j + o) % n;
+      if (jj < 0) jj += n;
+      s = fma(a.c[k][o + hw], x[jj], s);
+    }
+    ax[j] = s;
+    Zk[j + (long long)n * l] = x[j];
+    Zk[j + (long long)n * (a.r0 + l)] = s;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    double s = 0.0;
+    for (int o = -hw; o <= hw; ++o) {
+      int jj = (j + o) % n;
+      if (jj < 0) jj += n;
+      s = fma(a.c[k][o + hw], ax[jj], s);
+    }
+    Zk[j + (long long)n * (2 * a.r0 + l)] = s;
+  }
+}
+
+// Gamma = hadamard_{j!=k} G_j ; Hs (3 r0 x r) as above.  M_j lives in w.H (3 r0 x r, ld 3 r0).
+__global__ void cp_hadamard_rk2_kernel(CpArgs a, CpWs w, int k, int r0, const double* mu) {
+  const int d = a.d, r = a.r;
+  const long long nh = (long long)r0 * r, ng = (long long)r * r;
+  const int nt = 1 + 2 * d + d * (d - 1) / 2;
+  // type table: power of A_j in column type tau (<= 1 + 2*16 + 120 types, d <= 16)
+  __shared__ unsigned char pw[153][HT_MAXD];
+  __shared__ double cf[153];
+  for (int e = threadIdx.x; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
+  for (int e = threadIdx.x; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
+  __syncthreads();
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nh + ng;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < nh) {
+      const int lp = (int)(e % r0), l = (int)(e / r0);
+      const double* Hb = w.H + (lp + (long long)3 * r0 * l);
+      double hs[3] = {0.0, 0.0, 0.0};
+      for (int ti = 0; ti < nt; ++ti) {
+        double v = cf[ti];
+        for (int j = 0; j < d; ++j) {
+          if (j == k) continue;
+          v *= Hb[(long long)j * w.rycap * w.rcap + pw[ti][j] * r0];
+        }
+        hs[pw[ti][k]] += v;
+      }
+      const double m = mu[lp];
+      for (int pp = 0; pp < 3; ++pp) w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = m * hs[pp];
+    } else {
+      const long long g = e - nh;
+      double v = 1.0;
+      for (int j = 0; j < d; ++j)
+        if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + g];
+      w.Gam[g] = v;
+    }
+  }
+}
+
+// Mode update of the structured ALS, part 1 (one CTA per row index lp of the r0 x r block):
+//   hs_p[l] = mu_lp sum_{tau: p_tau(k) = p} c_tau prod_{j != k} M_j^(p_tau(j))[lp, l]   (p = 0,1,2)
+//   Gamma = hadamard_{j != k} G_j, Gamma = L L^T (FP64 Cholesky, shifted only on failure)
+//   W[p r0 + lp, :] = hs_p Gamma^{-1}    (forward and back substitution)
+// Then X~_k = Z_k W (a GEMM over all SMs) equals RHS Gamma^{-1} of the normal equations.
+// The M_j operands of a thread are loaded into registers before any product (an L2 latency
+// chain otherwise), and each CTA repeats the small Cholesky so no grid-wide sync is needed.
+constexpr int MODE_MAXR = 64;
+constexpr int MODE_MAXD = 16;
+
+__global__ void cp_mode_prep_kernel(CpArgs a, CpWs w, int k, int r0, const double* mu, int* err) {
+  extern __shared__ double sh[];
+  const int d = a.d, r = a.r, lp = blockIdx.x, tid = threadIdx.x;
+  double* Lm = sh;              // r x r
+  double* hs = Lm + r * r;      // 3 x r
+  double* rinv = hs + 3 * r;    // r
+  __shared__ unsigned char pw[153][MODE_MAXD];
+  __shared__ double cf[153];
+  __shared__ int ok;
+  const int nt = 1 + 2 * d + d * (d - 1) / 2;
+  for (int e = tid; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
+  for (int e = tid; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
+  __syncthreads();
+  // hs: thread per column l, operands in registers
+  for (int l = tid; l < r; l += blockDim.x) {
+    double mv[MODE_MAXD][3];
+    for (int j = 0; j < d; ++j) {
+      if (j == k) continue;
+      const double* Mj = w.H + (long long)j * w.rycap * w.rcap + lp + (long long)3 * r0 * l;
+      mv[j][0] = Mj[0];
+      mv[j][1] = Mj[r0];
+      mv[j][2] = Mj[2 * r0];
+    }
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int ti = 0; ti < nt; ++ti) {
+      double v = cf[ti];
+      for (int j = 0; j < d; ++j)
+        if (j != k) v *= mv[j][pw[ti][j]];
+      acc[pw[ti][k]] += v;
+    }
+    const double m = mu[lp];
+    hs[l] = m * acc[0];
+    hs[r + l] = m * acc[1];
+    hs[2 * r + l] = m * acc[2];
+  }
+  // Gamma
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    double v = 1.0;
+    for (int j = 0; j < d; ++j)
+      if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+    Lm[e] = v;
+  }
+  __syncthreads();
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (attempt == 1) {
+      double tr = 0.0;
+      for (int i = 0; i < r; ++i) {
+        double v = 1.0;
+        for (int j = 0; j < d; ++j)
+          if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
+        tr += v;
+      }
+      const double shift = 1e-14 * tr / r;
+      for (int e = tid; e < r * r; e += blockDim.x) {
+        double v = 1.0;
+        for (int j = 0; j < d; ++j)
+          if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+        Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
+      }
+    }
+    if (tid == 0) ok = 1;
+    __syncthreads();
+    for (int j = 0; j < r; ++j) {
+      if (tid == 0) {
+        const double dj = Lm[j + r * j];
+        if (!(dj > 0.0)) ok = 0;
+        const double ri = ok ? htg_rsqrt_fast(dj) : 1.0;
+        Lm[j + r * j] = ok ? dj * ri : 1.0;
+        rinv[j] = ri;
+      }
+      __syncthreads();
+      if (!ok) break;
+      const double inv = rinv[j];
+      for (int i = j + 1 + tid; i < r; i += blockDim.x) Lm[i + r * j] *= inv;
+      __syncthreads();
+      const int m = r - j - 1;
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = j + 1 + e % m, cc = j + 1 + e / m;
+        if (cc <= i) Lm[i + r * cc] -= Lm[i + r * j] * Lm[cc + r * j];
+      }
+      __syncthreads();
+    }
+    const int good = ok;
+    __syncthreads();
+    if (good) break;
+  }
+  if (!ok) {
+    if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
+    return;
+  }
+  // L L^T w = hs_p for the three vectors, column oriented (short dependency chains):
+  // forward  v_j <- v_j / L_jj, then v_i -= L_ij v_j (i > j);
+  // backward v_j <- v_j / L_jj, then v_i -= L_ji v_j (i < j)
+  for (int j = 0; j < r; ++j) {
+    if (tid < 3) hs[tid * r + j] *= rinv[j];
+    __syncthreads();
+    for (int e = tid; e < 3 * (r - j - 1); e += blockDim.x) {
+      const int pv = e / (r - j - 1), i = j + 1 + e % (r - j - 1);
+      hs[pv * r + i] -= Lm[i + r * j] * hs[pv * r + j];
+    }
+    __syncthreads();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    if (tid < 3) hs[tid * r + j] *= rinv[j];
+    __syncthreads();
+    for (int e = tid; e < 3 * j; e += blockDim.x) {
+      const int pv = e / j, i = e % j;
+      hs[pv * r + i] -= Lm[j + r * i] * hs[pv * r + j];
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < 3 * r; e += blockDim.x) {
+    const int pp = e / r, l = e % r;
+    w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = hs[e];
+  }
+}
+
+// Part 3: convergence measure, column norms, X_k (GS) or the Jacobi slot.  X~ is in w.RHS.
+__global__ void cp_mode_finish_kernel(CpArgs a, CpWs w, int k, int sweep, double* flops) {
+  const int r = a.r, n = a.n[k], tid = threadIdx.x;
+  __shared__ double rinv[MODE_MAXR];
+  __shared__ double red_num[NT / 32], red_den[NT / 32];
+  double num = 0.0, den = 0.0;
+  for (long long e = tid; e < (long long)n * r; e += blockDim.x) {
+    const int l = (int)(e / n);
+    const double old = a.X[k][e] * (a.variant == CP_ALS_GS ? a.lam[l] : 1.0);
+    const double df = w.RHS[e] - old;
+    num = fma(df, df, num);
+    den = fma(old, old, den);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    num += __shfl_xor_sync(0xffffffffu, num, o);
+    den += __shfl_xor_sync(0xffffffffu, den, o);
+  }
+  if ((tid & 31) == 0) { red_num[tid >> 5] = num; red_den[tid >> 5] = den; }
+  __syncthreads();
+  for (int l = tid >> 5; l < r; l += blockDim.x >> 5) {
+    double s2 = 0.0;
+    for (int j = tid & 31; j < n; j += 32) s2 = fma(w.RHS[j + (long long)n * l], w.RHS[j + (long long)n * l], s2);
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    if ((tid & 31) == 0) {
+      const double nr = sqrt(s2);
+      if (a.variant == CP_ALS_GS) a.lam[l] = nr;
+      rinv[l] = nr > 0.0 ? 1.0 / nr : 1.0;
+    }
+  }
+  if (tid == 0) {
+    double tn = 0.0, td = 0.0;
+    for (int q = 0; q < NT / 32; ++q) { tn += red_num[q]; td += red_den[q]; }
+    const double ek = td > 0.0 ? sqrt(tn / td) : sqrt(tn);
+    if (ek > w.epsacc[sweep]) w.epsacc[sweep] = ek;
+    if (flops) atomicAdd(flops, 8.0 * n * r);
+  }
+  __syncthreads();
+  if (a.variant == CP_ALS_GS) {
+    for (long long e = tid; e < (long long)n * r; e += blockDim.x) a.X[k][e] = w.RHS[e] * rinv[e / n];
+  } else {
+    double* dst = w.Xold + (long long)k * w.nmax * w.rcap;
+    for (long long e = tid; e < (long long)n * r; e += blockDim.x) dst[e] = w.RHS[e];
+  }
+}
+
+// descriptors per mode k: [RHS_k = Z_k (n x 3r0) Hs (3r0 x r), G_k = X_k^T X_k, M_k = Z_k^T X_k]
+__global__ void cp_plan_rk2_kernel(CpArgs a, CpWs w, int r0) {
+  if (threadIdx.x != 0) return;
+  for (int k = 0; k < a.d; ++k) {
+    GemmDesc* g = w.descs + 3 * k;
+    const int n = a.n[k];
+    const double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
+    for (int q = 0; q < 3; ++q) {
+      g[q].colscale = nullptr;
+      g[q].sA = g[q].sB = g[q].sC = 0;
+      g[q].batch = 1;
+      g[q].alpha = 1.0;
+      g[q].beta = 0.0;
+    }
+    g[0].A = Zk; g[0].lda = n; g[0].tA = 0;
+    g[0].B = w.Hh; g[0].ldb = 3 * r0; g[0].tB = 0;
+    g[0].C = w.RHS; g[0].ldc = n;
+    g[0].m = n; g[0].n = a.r; g[0].k = 3 * r0;
+    g[1].A = a.X[k]; g[1].lda = n; g[1].tA = 1;
+    g[1].B = a.X[k]; g[1].ldb = n; g[1].tB = 0;
+    g[1].C = w.G + (long long)k * w.rcap * w.rcap; g[1].ldc = a.r;
+    g[1].m = a.r; g[1].n = a.r; g[1].k = n;
+    g[2].A = Zk; g[2].lda = n; g[2].tA = 1;
+    g[2].B = a.X[k]; g[2].ldb = n; g[2].tB = 0;
+    g[2].C = w.H + (long long)k * w.rycap * w.rcap; g[2].ldc = 3 * r0;
+    g[2].m = 3 * r0; g[2].n = a.r; g[2].k = n;
+  }
+}
+
+__global__ void cp_copy_weights_kernel(const double* src, double* dst, int r) {
+  for (int i = threadIdx.x; i < r; i += blockDim.x) dst[i] = src[i];
+}
+
+// dynamic shared memory of cp_solve_kernel: L (r x r), norms (r), staged rows (n x r)
+static cudaError_t solve_smem_for(int r, const int* n, int d, size_t* out) {
+  int nmax = 1;
+  for (int k = 0; k < d; ++k) nmax = htg_max(nmax, n[k]);
+  const size_t sm = ((size_t)r * r + r + (size_t)nmax * r) * sizeof(double);
+  *out = sm;
+  if (sm > 48 * 1024) return cudaFuncSetAttribute(cp_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" int cp_apply_rk2(ht_ctx* c, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y, void* stream) {
@@ -306,7 +639,9 @@ extern "C" int cp_apply_rk2(ht_ctx* c, const cp_tensor* x, const ht_op* L, doubl
   a.w = x->weight;
   a.wy = y->weight;
   cudaStream_t s = (cudaStream_t)stream;
+  htg_prof_begin(c, s);
   cp_apply_kernel<<<dim3(x->rank, d), 128, 3 * nmax * sizeof(double), s>>>(a);
+  htg_prof_end(c, KC_APPLY, s);
   htg_ctx_count(c, 1, s);
   if (cudaGetLastError() != cudaSuccess) return HT_ERR_CUDA;
   y->rank = x->rank * nt;
@@ -320,7 +655,8 @@ extern "C" int cp_als_sweep(ht_ctx* c, const cp_tensor* y, cp_tensor* x, int swe
   const int d = htg_ctx_d(c);
   CpWs* w = htg_ctx_cp(c);
   if (x->d != d || y->d != d || x->rank < 1 || y->rank < 1 || !x->weight || !y->weight) return HT_ERR_ARG;
-  if (x->rank > w->rcap || y->rank > w->rycap || x->rank > x->cap || y->rank > y->cap) return HT_ERR_CAPACITY;
+  if (x->rank > w->rcap || y->rank > w->rycap || x->rank > x->cap || y->rank > y->cap || x->rank > 64)
+    return HT_ERR_CAPACITY;
   CpArgs a;
   memset(&a, 0, sizeof(a));
   a.d = d; a.r = x->rank; a.ry = y->rank; a.variant = variant;
@@ -335,47 +671,143 @@ extern "C" int cp_als_sweep(ht_ctx* c, const cp_tensor* y, cp_tensor* x, int swe
   cudaStream_t s = (cudaStream_t)stream;
   const int grid = htg_ctx_grid(c);
   int launches = 0;
-#define CPL(expr)                                              \
+#define CPL(cls, expr)                                         \
   do {                                                         \
+    htg_prof_begin(c, s);                                      \
     expr;                                                      \
+    htg_prof_end(c, (cls), s);                                 \
     ++launches;                                                \
     if (cudaGetLastError() != cudaSuccess) {                   \
       htg_ctx_count(c, launches, s);                           \
       return HT_ERR_CUDA;                                      \
     }                                                          \
   } while (0)
+#define CPG(descs, nd)                                                                    \
+  do {                                                                                    \
+    htg_prof_begin(c, s);                                                                 \
+    cudaError_t _e = htg_launch_gemm((descs), (nd), grid, s, htg_prof_flops(c, KC_GEMM)); \
+    htg_prof_end(c, KC_GEMM, s);                                                          \
+    ++launches;                                                                           \
+    if (_e != cudaSuccess) {                                                              \
+      htg_ctx_count(c, launches, s);                                                      \
+      return HT_ERR_CUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
   const int fold = (variant == CP_ALS_JACOBI_DAMPED) ? 1 : 0;
-  CPL((cp_eps_init_kernel<<<1, 64, 0, s>>>(*w, sweeps)));
-  CPL((cp_plan_kernel<<<1, 1, 0, s>>>(a, *w)));
-  CPL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, fold)));
+  CPL(KC_CPSMALL, (cp_eps_init_kernel<<<1, 64, 0, s>>>(*w, sweeps)));
+  CPL(KC_CPSMALL, (cp_plan_kernel<<<1, 1, 0, s>>>(a, *w)));
+  CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, fold)));
   // all G_k, H_k: descriptors 1,2 of every mode; launch each mode's pair (small)
   for (int k = 0; k < d; ++k) {
-    if (htg_launch_gemm(w->descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-    ++launches;
+    CPG(w->descs + 3 * k + 1, 2);
   }
-  const size_t solve_smem = ((size_t)a.r * a.r + a.r) * sizeof(double);
+  size_t solve_smem = 0;
+  if (solve_smem_for(a.r, a.n, d, &solve_smem) != cudaSuccess) return HT_ERR_CUDA;
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int k = 0; k < d; ++k) {
-      CPL((cp_hadamard_kernel<<<32, NT, 0, s>>>(a, *w, k)));
-      if (htg_launch_gemm(w->descs + 3 * k, 1, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-      ++launches;
-      CPL((cp_solve_kernel<<<1, NT, solve_smem, s>>>(a, *w, k, sw, htg_ctx_err(c))));
-      if (variant == CP_ALS_GS) {
-        if (htg_launch_gemm(w->descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-        ++launches;
-      }
+      CPL(KC_CPSMALL, (cp_hadamard_kernel<<<32, NT, 0, s>>>(a, *w, k)));
+      CPG(w->descs + 3 * k, 1);
+      CPL(KC_CPSOLVE, (cp_solve_kernel<<<1, NT, solve_smem, s>>>(a, *w, k, sw, htg_ctx_err(c), htg_prof_flops(c, KC_CPSOLVE))));
+      if (variant == CP_ALS_GS) CPG(w->descs + 3 * k + 1, 2);
     }
     if (variant == CP_ALS_JACOBI_DAMPED) {
-      CPL((cp_damp_kernel<<<dim3(8, d), NT, 0, s>>>(a, *w)));
-      for (int k = 0; k < d; ++k) {
-        if (htg_launch_gemm(w->descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-        ++launches;
-      }
+      CPL(KC_CPSMALL, (cp_damp_kernel<<<dim3(8, d), NT, 0, s>>>(a, *w)));
+      for (int k = 0; k < d; ++k) CPG(w->descs + 3 * k + 1, 2);
     }
   }
-  if (variant == CP_ALS_JACOBI_DAMPED) CPL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, 0)));
-  if (eps_dev && sweeps > 0) CPL((cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev)));
+  if (variant == CP_ALS_JACOBI_DAMPED) CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, 0)));
+  if (eps_dev && sweeps > 0) CPL(KC_CPSMALL, (cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev)));
 #undef CPL
+#undef CPG
+  htg_ctx_count(c, launches, s);
+  return HT_OK;
+}
+
+extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* L, double dt, cp_tensor* x,
+                                int sweeps, int variant, double* eps_dev, void* stream) {
+  if (!c || !x || !x_old || !L || sweeps < 0 || sweeps > 64) return HT_ERR_ARG;
+  if (variant != CP_ALS_GS && variant != CP_ALS_JACOBI_DAMPED) return HT_ERR_ARG;
+  const int d = htg_ctx_d(c);
+  CpWs* w = htg_ctx_cp(c);
+  if (x->d != d || x_old->d != d || L->d != d || !L->kron_sum || L->n_terms != d) return HT_ERR_ARG;
+  if (x->rank < 1 || x_old->rank < 1 || !x->weight || !x_old->weight) return HT_ERR_ARG;
+  if (x->rank > w->rcap || x_old->rank > w->rcap || 3 * x_old->rank > w->rycap || x->rank > x->cap ||
+      x_old->rank > x_old->cap || x->rank > 64)
+    return HT_ERR_CAPACITY;
+  CpArgs a;
+  memset(&a, 0, sizeof(a));
+  PowArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  a.d = d; a.r = x->rank; a.ry = 3 * x_old->rank; a.variant = variant;
+  pa.d = d; pa.r0 = x_old->rank;
+  int nmax = 1;
+  for (int k = 0; k < d; ++k) {
+    if (x->n[k] != x_old->n[k] || x->n[k] != htg_ctx_n(c)[k] || !x->factor[k] || !x_old->factor[k]) return HT_ERR_ARG;
+    const ht_factor& f = L->f[k][k];
+    if (f.kind != HT_F_STENCIL || 2 * f.half_width + 1 > HT_MAXSTENCIL) return HT_ERR_ARG;
+    a.n[k] = x->n[k];
+    a.X[k] = x->factor[k];
+    pa.n[k] = x->n[k];
+    pa.hw[k] = f.half_width;
+    for (int j = 0; j < 2 * f.half_width + 1; ++j) pa.c[k][j] = dt * L->alpha[k] * f.stencil[j];
+    pa.X[k] = x_old->factor[k];
+    nmax = htg_max(nmax, x->n[k]);
+  }
+  a.lam = x->weight;
+  a.mu = w->wold;
+  const int r0 = x_old->rank;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int grid = htg_ctx_grid(c);
+  int launches = 0;
+#define CPL(cls, expr)                                         \
+  do {                                                         \
+    htg_prof_begin(c, s);                                      \
+    expr;                                                      \
+    htg_prof_end(c, (cls), s);                                 \
+    ++launches;                                                \
+    if (cudaGetLastError() != cudaSuccess) {                   \
+      htg_ctx_count(c, launches, s);                           \
+      return HT_ERR_CUDA;                                      \
+    }                                                          \
+  } while (0)
+#define CPG(descs, nd)                                                                    \
+  do {                                                                                    \
+    htg_prof_begin(c, s);                                                                 \
+    cudaError_t _e = htg_launch_gemm((descs), (nd), grid, s, htg_prof_flops(c, KC_GEMM)); \
+    htg_prof_end(c, KC_GEMM, s);                                                          \
+    ++launches;                                                                           \
+    if (_e != cudaSuccess) {                                                              \
+      htg_ctx_count(c, launches, s);                                                      \
+      return HT_ERR_CUDA;                                                                 \
+    }                                                                                     \
+  } while (0)
+  // the step input is read first (powers, weights), so x_old may alias x
+  CPL(KC_CPSMALL, (cp_powers_kernel<<<dim3(r0, d), 128, 2 * nmax * sizeof(double), s>>>(pa, *w)));
+  CPL(KC_CPSMALL, (cp_copy_weights_kernel<<<1, 64, 0, s>>>(x_old->weight, w->wold, r0)));
+  const int fold = (variant == CP_ALS_JACOBI_DAMPED) ? 1 : 0;
+  CPL(KC_CPSMALL, (cp_eps_init_kernel<<<1, 64, 0, s>>>(*w, sweeps)));
+  CPL(KC_CPSMALL, (cp_plan_rk2_kernel<<<1, 1, 0, s>>>(a, *w, r0)));
+  CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, fold)));
+  for (int k = 0; k < d; ++k) {
+    CPG(w->descs + 3 * k + 1, 2);
+  }
+  const size_t prep_smem = ((size_t)a.r * a.r + 4 * (size_t)a.r) * sizeof(double);
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int k = 0; k < d; ++k) {
+      CPL(KC_CPSOLVE, (cp_mode_prep_kernel<<<r0, 64, prep_smem, s>>>(a, *w, k, r0, w->wold, htg_ctx_err(c))));
+      CPG(w->descs + 3 * k, 1);
+      CPL(KC_CPSMALL, (cp_mode_finish_kernel<<<1, NT, 0, s>>>(a, *w, k, sw, htg_prof_flops(c, KC_CPSMALL))));
+      if (variant == CP_ALS_GS) CPG(w->descs + 3 * k + 1, 2);
+    }
+    if (variant == CP_ALS_JACOBI_DAMPED) {
+      CPL(KC_CPSMALL, (cp_damp_kernel<<<dim3(8, d), NT, 0, s>>>(a, *w)));
+      for (int k = 0; k < d; ++k) CPG(w->descs + 3 * k + 1, 2);
+    }
+  }
+  if (variant == CP_ALS_JACOBI_DAMPED) CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, 0)));
+  if (eps_dev && sweeps > 0) CPL(KC_CPSMALL, (cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev)));
+#undef CPL
+#undef CPG
   htg_ctx_count(c, launches, s);
   return HT_OK;
 }
@@ -496,15 +928,16 @@ extern "C" int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps
   const int fold = (variant == CP_ALS_JACOBI_DAMPED) ? 1 : 0;
   NAL((cp_eps_init_kernel<<<1, 64, 0, s>>>(w, sweeps)));
   NAL((cp_plan_kernel<<<1, 1, 0, s>>>(a, w)));
-  NAL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, fold)));
+  NAL((cp_normalize_kernel<<<1, NT, 0, s>>>(a, fold)));
   for (int k = 0; k < d; ++k)
     if (htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-  const size_t solve_smem = ((size_t)a.r * a.r + a.r) * sizeof(double);
+  size_t solve_smem = 0;
+  if (solve_smem_for(a.r, a.n, d, &solve_smem) != cudaSuccess) return HT_ERR_CUDA;
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int k = 0; k < d; ++k) {
       NAL((cp_hadamard_kernel<<<32, NT, 0, s>>>(a, w, k)));
       if (htg_launch_gemm(w.descs + 3 * k, 1, grid, s) != cudaSuccess) return HT_ERR_CUDA;
-      NAL((cp_solve_kernel<<<1, NT, solve_smem, s>>>(a, w, k, sw, err)));
+      NAL((cp_solve_kernel<<<1, NT, solve_smem, s>>>(a, w, k, sw, err, nullptr)));
       if (variant == CP_ALS_GS && htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess)
         return HT_ERR_CUDA;
     }
@@ -514,7 +947,7 @@ extern "C" int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps
         if (htg_launch_gemm(w.descs + 3 * k + 1, 2, grid, s) != cudaSuccess) return HT_ERR_CUDA;
     }
   }
-  if (variant == CP_ALS_JACOBI_DAMPED) NAL((cp_normalize_kernel<<<1, 64, 0, s>>>(a, 0)));
+  if (variant == CP_ALS_JACOBI_DAMPED) NAL((cp_normalize_kernel<<<1, NT, 0, s>>>(a, 0)));
   if (eps_dev && sweeps > 0) NAL((cp_eps_out_kernel<<<1, 64, 0, s>>>(w, sweeps, eps_dev)));
   if (status_dev) NAL((na_status_kernel<<<1, 32, 0, s>>>(err, status_dev)));
 #undef NAL

@@ -135,6 +135,12 @@ struct ht_ctx {
   const double** ptr_tbl = nullptr;   // device table of caller pointers (CP factors)
   CpWs cp;
   long long launches = 0;
+  // opt-in event profiler
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_cls;        // class of record i (events 2i, 2i+1)
+  size_t prof_n = 0;
+  double* prof_flops = nullptr;     // device, KC_COUNT counters
   int svd_smem = 0;
   int gemm_grid = 0;
   cudaStream_t last_stream = nullptr;
@@ -608,9 +614,11 @@ __global__ void inner_kernel(TreeInfo T, HtView u, HtView w, int use_ones, doubl
 }  // namespace
 
 // ================================================================ host side =====
-#define HTG_CHECK_LAUNCH(ctx, expr)            \
+#define HTG_LAUNCH(ctx, cls, s, expr)          \
   do {                                         \
+    htg_prof_begin((ctx), (s));                \
     cudaError_t _e = (expr);                   \
+    htg_prof_end((ctx), (cls), (s));           \
     (ctx)->launches++;                         \
     if (_e != cudaSuccess) return HT_ERR_CUDA; \
   } while (0)
@@ -648,7 +656,7 @@ static int trunc_input_cap(const ht_config* c) {
 }
 
 struct WsLayout {
-  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[9];
+  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[10], off_prof;
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
   size_t total;
@@ -664,14 +672,16 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   W->off_app_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_stage_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_wn = off; off = align_up(off + NN * sizeof(WsNode));
+  W->off_prof = off; off = align_up(off + KC_COUNT * sizeof(double));
   W->off_ptrs = off; off = align_up(off + 4 * HT_MAXD * sizeof(void*));
   {
     const size_t rc = (size_t)c->cap, ry = rc * (size_t)htg_cp_terms(c->d);
     size_t nmax = 1;
     for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
-    const size_t cps[9] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
-                           HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1};
-    for (int j = 0; j < 9; ++j) {
+    const size_t cps[10] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
+                            HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1,
+                            HT_MAXD * nmax * 3 * rc};
+    for (int j = 0; j < 10; ++j) {
       W->off_cp[j] = off;
       off = align_up(off + cps[j] * sizeof(double));
     }
@@ -740,11 +750,13 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->stage[t] = (double*)(base + W.stage_off[t]);
   }
   c->wn_dev = (WsNode*)(base + W.off_wn);
+  c->prof_flops = (double*)(base + W.off_prof);
   c->ptr_tbl = (const double**)(base + W.off_ptrs);
   {
     double** cpf[8] = {&c->cp.G, &c->cp.H, &c->cp.Hh, &c->cp.Gam, &c->cp.RHS, &c->cp.Xold, &c->cp.wold, &c->cp.epsacc};
     for (int j = 0; j < 8; ++j) *cpf[j] = (double*)(base + W.off_cp[j]);
     c->cp.descs = (GemmDesc*)(base + W.off_cp[8]);
+    c->cp.Z = (double*)(base + W.off_cp[9]);
     c->cp.rcap = cfg->cap;
     c->cp.rycap = cfg->cap * htg_cp_terms(cfg->d);
     int nmax = 1;
@@ -769,6 +781,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
 
 extern "C" void ht_ctx_destroy(ht_ctx* ctx) {
   if (!ctx) return;
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
   delete ctx;
 }
@@ -849,30 +862,30 @@ static int run_truncate(ht_ctx* c, const HtView& in, int cap_in, const HtView& o
   Plan* P = c->plan;
   const WsNode* wn = c->wn_dev;
   const int g = c->gemm_grid;
-  HTG_CHECK_LAUNCH(c, (plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, c->err), cudaGetLastError()));
-  HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_leaf, L.n_leaf, s));
+  HTG_LAUNCH(c, KC_PLAN, s, (plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, c->err), cudaGetLastError()));
+  HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_leaf, L.n_leaf, s, htg_prof_flops(c, KC_QR)));
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s));
-    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s));
-    HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
   }
-  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_rootE, 2, g, s));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM)));
   for (int dep = 1; dep <= T.max_depth; ++dep) {
-    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_P[dep], L.n_all[dep], g, s));
-    HTG_CHECK_LAUNCH(c, htg_launch_svd(P->svd[dep], L.n_all[dep], c->svd_smem, c->Kc, c->Kc, s));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_P[dep], L.n_all[dep], g, s, htg_prof_flops(c, KC_GEMM)));
+    HTG_LAUNCH(c, KC_SVD, s, htg_launch_svd(P->svd[dep], L.n_all[dep], c->svd_smem, c->Kc, c->Kc, s, htg_prof_flops(c, KC_SVD)));
     if (L.n_int[dep] == 0) continue;
-    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s));
-    HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s));
-    HTG_CHECK_LAUNCH(c, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
   }
-  HTG_CHECK_LAUNCH(c, (rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev,
+  HTG_LAUNCH(c, KC_PLAN, s, (rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev,
                                                           sig_stride, norm_dev, c->err),
                        cudaGetLastError()));
-  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s));
-  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s));
-  HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s));
-  if (L.n_proj3 > 0) HTG_CHECK_LAUNCH(c, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM)));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM)));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM)));
+  if (L.n_proj3 > 0) HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s, htg_prof_flops(c, KC_GEMM)));
   c->last_stream = s;
   return HT_OK;
 }
@@ -984,9 +997,9 @@ static int launch_apply(ht_ctx* c, const ApplyOp& op, const HtView& in0, const H
     if (cudaFuncSetAttribute(apply_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HT_ERR_CUDA;
   }
-  HTG_CHECK_LAUNCH(c, (apply_leaf_kernel<<<gl, 128, smem, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
+  HTG_LAUNCH(c, KC_APPLY, s, (apply_leaf_kernel<<<gl, 128, smem, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
   dim3 gx(c->gemm_grid, L.n_proj2);
-  HTG_CHECK_LAUNCH(c, (apply_xfer_kernel<<<gx, 256, 0, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
+  HTG_LAUNCH(c, KC_APPLY, s, (apply_xfer_kernel<<<gx, 256, 0, s>>>(op, T, L, in0, in1, out), cudaGetLastError()));
   c->last_stream = s;
   return HT_OK;
 }
@@ -1062,7 +1075,7 @@ extern "C" int ht_from_cp(ht_ctx* c, const cp_tensor* x, ht_tensor* out, void* s
   const double** tbl = c->ptr_tbl;
   if (cudaMemcpyAsync((void*)tbl, fp, sizeof(fp), cudaMemcpyHostToDevice, s) != cudaSuccess) return HT_ERR_CUDA;
   dim3 g(64, c->tree.nn);
-  HTG_CHECK_LAUNCH(c, (from_cp_kernel<<<g, 256, 0, s>>>(c->tree, view_of(out), tbl, x->weight, x->rank),
+  HTG_LAUNCH(c, KC_APPLY, s, (from_cp_kernel<<<g, 256, 0, s>>>(c->tree, view_of(out), tbl, x->weight, x->rank),
                        cudaGetLastError()));
   c->last_stream = s;
   return HT_OK;
@@ -1075,7 +1088,7 @@ static int run_inner(ht_ctx* c, const ht_tensor* u, const ht_tensor* w, double* 
   if ((long long)c->tree.nn * gstride > (long long)c->Kc * c->Kc * c->Kc) return HT_ERR_CAPACITY;
   HtView uw = view_of(u);
   HtView ww = w ? view_of(w) : uw;
-  HTG_CHECK_LAUNCH(c, (inner_kernel<<<1, 256, 0, s>>>(c->tree, uw, ww, w ? 0 : 1, gbuf, gstride, c->wn[0].T1, out_dev),
+  HTG_LAUNCH(c, KC_PLAN, s, (inner_kernel<<<1, 256, 0, s>>>(c->tree, uw, ww, w ? 0 : 1, gbuf, gstride, c->wn[0].T1, out_dev),
                        cudaGetLastError()));
   c->last_stream = s;
   return HT_OK;
@@ -1104,3 +1117,60 @@ void htg_ctx_count(ht_ctx* c, int launches, cudaStream_t s) {
   c->last_stream = s;
 }
 int htg_cp_terms(int d) { return 1 + 2 * d + d * (d - 1) / 2; }
+
+// ---------------------------------------------------------------- profiler ------
+void htg_prof_begin(ht_ctx* c, cudaStream_t s) {
+  if (!c || !c->prof_on) return;
+  if (c->prof_pool.size() < 2 * (c->prof_n + 1)) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { c->prof_on = false; return; }
+      c->prof_pool.push_back(e);
+    }
+  }
+  cudaEventRecord(c->prof_pool[2 * c->prof_n], s);
+}
+
+void htg_prof_end(ht_ctx* c, int cls, cudaStream_t s) {
+  if (!c || !c->prof_on) return;
+  cudaEventRecord(c->prof_pool[2 * c->prof_n + 1], s);
+  if (c->prof_cls.size() <= c->prof_n) c->prof_cls.push_back(cls);
+  else c->prof_cls[c->prof_n] = cls;
+  c->prof_n++;
+}
+
+double* htg_prof_flops(ht_ctx* c, int cls) {
+  return (c && c->prof_on && cls >= 0 && cls < KC_COUNT) ? c->prof_flops + cls : nullptr;
+}
+
+extern "C" int ht_ctx_profile(ht_ctx* c, int on) {
+  if (!c) return HT_ERR_ARG;
+  if (cudaSetDevice(c->cfg.device) != cudaSuccess) return HT_ERR_CUDA;
+  if (on) {
+    if (cudaMemset(c->prof_flops, 0, KC_COUNT * sizeof(double)) != cudaSuccess) return HT_ERR_CUDA;
+    c->prof_n = 0;
+  }
+  c->prof_on = on != 0;
+  return HT_OK;
+}
+
+extern "C" int ht_ctx_profile_read(ht_ctx* c, double* ms, long long* launches, double* flops) {
+  if (!c) return HT_ERR_ARG;
+  double tms[KC_COUNT] = {0};
+  long long cnt[KC_COUNT] = {0};
+  for (size_t i = 0; i < c->prof_n; ++i) {
+    if (cudaEventSynchronize(c->prof_pool[2 * i + 1]) != cudaSuccess) return HT_ERR_CUDA;
+    float e = 0.f;
+    if (cudaEventElapsedTime(&e, c->prof_pool[2 * i], c->prof_pool[2 * i + 1]) != cudaSuccess) return HT_ERR_CUDA;
+    tms[c->prof_cls[i]] += e;
+    cnt[c->prof_cls[i]] += 1;
+  }
+  double fl[KC_COUNT] = {0};
+  if (cudaMemcpy(fl, c->prof_flops, sizeof(fl), cudaMemcpyDeviceToHost) != cudaSuccess) return HT_ERR_CUDA;
+  for (int k = 0; k < KC_COUNT; ++k) {
+    if (ms) ms[k] = tms[k];
+    if (launches) launches[k] = cnt[k];
+    if (flops) flops[k] = fl[k];
+  }
+  return HT_OK;
+}

@@ -3,16 +3,18 @@
 // launch serves every node of a tree level whatever the ranks chosen on the device.
 //
 // Work decomposition: every descriptor contributes batch * tiles(m) * tiles(n) work items
-// of a 32 x 32 output tile; a fixed grid walks the items with a grid-stride loop.
-// FP64 on the CUDA cores (GB300 has no FP64 tensor-core path worth using).
+// of a 16 x 16 output tile computed by 64 threads (2 x 2 outputs each); a fixed grid walks
+// the items with a grid-stride loop.  FP64 on the CUDA cores: on GB300 the FP64 pipe of an
+// SM retires about 2 FMA per clock, so the contractions of these small ranks are bound by
+// how many SMs take part; small tiles spread a product over as many SMs as possible.
 #include "common.cuh"
 
 namespace {
 
-constexpr int BM = 32, BN = 32, BK = 16, NT = 256;
+constexpr int BM = 16, BN = 16, BK = 16, NT = 64;
 constexpr int MAXD = 64;
 
-__global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc) {
+__global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc, double* flops) {
   __shared__ long long prefix[MAXD + 1];
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
   }
   __syncthreads();
   const long long total = prefix[ndesc];
-  const int tx = tid % 16, ty = tid / 16;
+  const int tx = tid % 8, ty = tid / 8;
   for (long long w = blockIdx.x; w < total; w += gridDim.x) {
     int di = 0;
     while (prefix[di + 1] <= w) ++di;
@@ -41,13 +43,15 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     const int tile = (int)(loc % ((long long)tm * tn));
     const int b = (int)(loc / ((long long)tm * tn));
     const int i0 = (tile % tm) * BM, j0 = (tile / tm) * BN;
+    if (flops && tid == 0)
+      atomicAdd(flops, 2.0 * htg_min(BM, g.m - i0) * htg_min(BN, g.n - j0) * (double)g.k);
     const double* A = g.A + (long long)b * g.sA;
     const double* B = g.B + (long long)b * g.sB;
     double* C = g.C + (long long)b * g.sC;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     for (int l0 = 0; l0 < g.k; l0 += BK) {
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
+      for (int p = 0; p < (BM * BK) / NT; ++p) {
         const int e = tid + NT * p;
         int i, l;
         if (!g.tA) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
@@ -65,8 +69,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
       __syncthreads();
 #pragma unroll
       for (int l = 0; l < BK; ++l) {
-        const double a0 = As[l][ty], a1 = As[l][ty + 16];
-        const double b0 = Bs[l][tx], b1 = Bs[l][tx + 16];
+        const double a0 = As[l][ty], a1 = As[l][ty + 8];
+        const double b0 = Bs[l][tx], b1 = Bs[l][tx + 8];
         acc[0][0] = fma(a0, b0, acc[0][0]);
         acc[0][1] = fma(a0, b1, acc[0][1]);
         acc[1][0] = fma(a1, b0, acc[1][0]);
@@ -78,7 +82,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     for (int r = 0; r < 2; ++r) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * c;
+        const int gi = i0 + ty + 8 * r, gj = j0 + tx + 8 * c;
         if (gi < g.m && gj < g.n) {
           double v = g.alpha * acc[r][c];
           if (g.colscale) v *= g.colscale[gj];
@@ -93,10 +97,11 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
 
 }  // namespace
 
-cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s) {
+cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops) {
   if (ndesc <= 0) return cudaSuccess;
   if (ndesc > MAXD) return cudaErrorInvalidValue;
   if (grid < 1) grid = 1;
-  gemm_kernel<<<grid, NT, 0, s>>>(descs_dev, ndesc);
+  grid = grid / 2;   // 2 x SMs 64-thread CTAs: the grid-stride loop covers any item count
+  gemm_kernel<<<grid, NT, 0, s>>>(descs_dev, ndesc, flops);
   return cudaGetLastError();
 }

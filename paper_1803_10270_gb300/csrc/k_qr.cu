@@ -24,14 +24,19 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs) {
+constexpr int QR_MAX_COLS = 4096;
+
+__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long smem_doubles,
+                                                 double* flops) {
   const QrDesc q = descs[blockIdx.x];
   const int m = q.m, k = q.k;
-  if (m <= 0 || k <= 0) {
+  if (m <= 0 || k <= 0 || k > QR_MAX_COLS) {
     if (threadIdx.x == 0 && q.rows_out) *q.rows_out = 0;
     return;
   }
-  double* S = q.scratch;
+  extern __shared__ double diag[];   // min(m,k) values, then the matrix when it fits
+  const long long need = (long long)m * k;
+  double* S = (need <= smem_doubles - QR_MAX_COLS) ? diag + QR_MAX_COLS : q.scratch;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
   // copy op(A) into S (m x k, column major)
   const long long mk = (long long)m * k;
@@ -41,7 +46,6 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
   }
   __shared__ double red[NT / 32];
   __shared__ double sh_alpha, sh_tau;
-  extern __shared__ double diag[];   // min(m,k) values
   __syncthreads();
   const int rmax = htg_min(m, k);
   for (int j = 0; j < rmax; ++j) {
@@ -55,13 +59,15 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
       double t = 0.0;
       for (int w = 0; w < nw; ++w) t += red[w];
       const double x0 = col[j];
-      const double nrm = sqrt(x0 * x0 + t);
+      const double n2 = fma(x0, x0, t);
       double alpha = 0.0, tau = 0.0;
-      if (nrm > 0.0) {
+      if (n2 > 0.0) {
+        const double ri = htg_rsqrt_fast(n2);
+        const double nrm = n2 * ri;
         alpha = x0 > 0.0 ? -nrm : nrm;
         const double v0 = x0 - alpha;
-        const double vv = v0 * v0 + t;
-        tau = vv > 0.0 ? 2.0 / vv : 0.0;
+        const double vv = fma(v0, v0, t);
+        tau = vv > 0.0 ? 2.0 * htg_rcp_fast(vv) : 0.0;
         col[j] = v0;
       }
       sh_alpha = alpha;
@@ -92,14 +98,27 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     else q.R[r + (long long)q.ldr * c] = v;
   }
   if (tid == 0 && q.rows_out) *q.rows_out = rmax;
+  if (tid == 0 && flops) {
+    // norm of the sub-column (2 per entry) + dot and update of every trailing column (4 per entry)
+    double f = 0.0;
+    for (int j = 0; j < rmax; ++j) f += 2.0 * (m - j) + 4.0 * (double)(m - j) * (k - j - 1);
+    atomicAdd(flops, f);
+  }
 }
 
 }  // namespace
 
-cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s) {
+cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops) {
   if (ndesc <= 0) return cudaSuccess;
-  // diag[] holds min(m,k) <= HT_MAX_QR_COLS values; 4096 columns is far above any capacity
-  const size_t smem = 4096 * sizeof(double);
-  qr_r_kernel<<<ndesc, NT, smem, s>>>(descs_dev);
+  static bool attr[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(qr_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HTG_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr[dev] = true;
+  }
+  // diag[] (QR_MAX_COLS values) followed by the staged matrix when it fits
+  qr_r_kernel<<<ndesc, NT, HTG_SMEM_BYTES, s>>>(descs_dev, (long long)(HTG_SMEM_BYTES / sizeof(double)), flops);
   return cudaGetLastError();
 }

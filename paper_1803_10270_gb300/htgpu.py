@@ -62,6 +62,9 @@ _EXPORTS = {
     "ht_ctx_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ht_ctx_launches": (C.c_longlong, [C.c_void_p]),
     "ht_status_string": (C.c_char_p, [C.c_int]),
+    "ht_ctx_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "ht_ctx_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double)]),
     "ht_tree_info": (C.c_int, [C.c_int] + [C.POINTER(C.c_int)] * 6),
     "ht_apply": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_op), C.c_double, C.c_int,
                            C.POINTER(ht_tensor), C.c_void_p]),
@@ -76,6 +79,8 @@ _EXPORTS = {
                                C.POINTER(cp_tensor), C.c_void_p]),
     "cp_als_sweep": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                C.c_void_p, C.c_void_p]),
+    "cp_als_sweep_rk2": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
+                                   C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -176,6 +181,19 @@ class Context:
 
     def launches(self) -> int:
         return int(load().ht_ctx_launches(self.ptr))
+
+    KERNEL_CLASSES = ["apply", "gemm", "qr", "svd", "plan", "cp_small", "cp_solve"]
+
+    def profile(self, on: bool):
+        _check(load().ht_ctx_profile(self.ptr, 1 if on else 0), "ht_ctx_profile")
+
+    def profile_read(self) -> dict:
+        n = len(self.KERNEL_CLASSES)
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        fl = (C.c_double * n)()
+        _check(load().ht_ctx_profile_read(self.ptr, ms, cnt, fl), "ht_ctx_profile_read")
+        return {k: {"ms": ms[i], "launches": cnt[i], "flops": fl[i]} for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def check(self, stream=None):
         _check(load().ht_ctx_check(self.ptr, _stream_ptr(stream)), "device error word")
@@ -398,6 +416,13 @@ def cp_als_sweep(ctx: Context, y: CPTensor, x: CPTensor, sweeps: int, variant: i
     _check(load().cp_als_sweep(ctx.ptr, C.byref(y.struct), C.byref(x.struct), sweeps, variant,
                                C.c_void_p(eps.data_ptr() if eps is not None else 0), _stream_ptr(stream)),
            "cp_als_sweep")
+
+
+def cp_als_sweep_rk2(ctx: Context, x_old: CPTensor, op: ht_op, dt: float, x: CPTensor, sweeps: int,
+                     variant: int = CP_ALS_GS, eps=None, stream=None):
+    _check(load().cp_als_sweep_rk2(ctx.ptr, C.byref(x_old.struct), C.byref(op), dt, C.byref(x.struct), sweeps,
+                                   variant, C.c_void_p(eps.data_ptr() if eps is not None else 0),
+                                   _stream_ptr(stream)), "cp_als_sweep_rk2")
 
 
 def cp_als_sweep_noalloc(y: CPTensor, x: CPTensor, sweeps: int, variant: int = CP_ALS_GS, eps=None, status=None,

@@ -102,3 +102,47 @@ def test_cp_step_config2_shape(G):
     got = OC.CP(w, f)
     num = gram(got, got) - 2 * gram(got, ref) + gram(ref, ref)
     assert num <= (1e-7 * np.sqrt(gram(ref, ref))) ** 2   # Gram identity resolves ~1e-8 relative
+
+
+@pytest.mark.parametrize("variant", ["gs", "jacobi_damped"])
+def test_structured_rk2_als_matches_oracle_step(G, variant):
+    """cp_als_sweep_rk2 (y never formed) == oracle: ALS on y = p(dt L) x from the padded x."""
+    import torch
+    d, n, r = 5, 7, 6
+    case = advection_case(d, n, seed=21)
+    A = advection_A(case)
+    x = OC.CP(np.array([1.3, -0.4]), cp_random_factors([n] * d, 2, seed=4))
+    pad = cp_padding([n] * d, r - 2, seed=5, scale=1e-3)
+    ref, eps = OC.step_rk2(x, A, r, pad, 3, variant)
+    xi = OC.pad(x, r, pad)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    X = G.CPTensor(d, [n] * d, r)
+    X.upload(xi.weights, xi.factors)
+    Xold = G.CPTensor(d, [n] * d, r)
+    Xold.upload(xi.weights[:2], [f[:, :2] for f in xi.factors])   # the normalised rank-2 state
+    e = torch.zeros(3, dtype=torch.float64, device="cuda")
+    v = G.CP_ALS_GS if variant == "gs" else G.CP_ALS_JACOBI_DAMPED
+    G.cp_als_sweep_rk2(ctx, Xold, G.advection_op(case.c, case.h), case.dt, X, 3, v, eps=e)
+    sync()
+    ctx.check()
+    w, f = X.download()
+    assert full_rel(OC.CP(w, f), ref) < 1e-10
+    np.testing.assert_allclose(e.cpu().numpy(), eps, rtol=1e-6, atol=1e-14)
+
+
+def test_structured_rk2_als_aliased_state(G):
+    """x_old aliasing x (the steady-state call of a time loop): two steps vs the oracle."""
+    d, n, r = 4, 6, 4
+    case = advection_case(d, n, seed=33)
+    A = advection_A(case)
+    x = OC.CP(np.ones(r), cp_random_factors([n] * d, r, seed=6))
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    X = G.CPTensor(d, [n] * d, r)
+    X.upload(x.weights, x.factors)
+    op = G.advection_op(case.c, case.h)
+    for _ in range(2):
+        x, _ = OC.step_rk2(x, A, r, [np.zeros((n, 0))] * d, 2)
+        G.cp_als_sweep_rk2(ctx, X, op, case.dt, X, 2)
+    sync()
+    w, f = X.download()
+    assert full_rel(OC.CP(w, f), x) < 1e-10
