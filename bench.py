@@ -158,6 +158,9 @@ class Workload:
         self.pad = cp_padding([N] * D, CP_R - 2, seed=0x5EED + 1, scale=1e-3)
         self.np = np
         self.torch = torch
+        self.side = torch.cuda.Stream()
+        self.ev_fork = torch.cuda.Event()
+        self.ev_join = torch.cuda.Event()
         self.reset()
 
     def reset(self):
@@ -193,10 +196,17 @@ class Workload:
         self.padded = True
 
     def step(self, stream=None):
-        G = self.G
-        G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=stream)
+        """HT route on the current stream, CP route on a side stream (independent data),
+        forked and joined with events so the pair also captures into one CUDA graph."""
+        G, torch = self.G, self.torch
+        main = stream if stream is not None else torch.cuda.current_stream()
+        self.ev_fork.record(main)
+        self.side.wait_event(self.ev_fork)
+        G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=main)
         # CP route: ALS towards y = p(dt L) x_n with x_n as warm start (y never formed)
-        G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=stream)
+        G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=self.side)
+        self.ev_join.record(self.side)
+        main.wait_event(self.ev_join)
 
     def first_step(self):
         """Step 1: the rank-2 state defines y; the iterate is that state padded to rank 24."""
@@ -294,6 +304,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic (seeded advection, BASELINE config 2)",
             "config": {"workload": WORKLOAD, "precision": args.precision, "ht_ranks_final": ranks,
+                       "streams": "HT route and CP route on two streams (independent data)",
                        "cp_rank": CP_R, "l2": "flushed between timed steps (256 MB write)",
                        "cuda_graph": graph is not None,
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -7,7 +7,10 @@ columns with plane rotations:
 
   for a column pair (p, q): alpha = |a_p|^2, beta = |a_q|^2, gamma = a_p . a_q;
   if |gamma| > tol * sqrt(alpha beta) (tol = eps * max(m, 8), the rounding level of a
-  length-m dot product): zeta = (beta - alpha) / (2 gamma),
+  length-m dot product) and both columns are above the rounding floor eps * |A|_F (a
+  column below it carries no information, and rotating it only reshuffles rounding noise,
+  which would keep the sweeps from terminating on rank-deficient matrices):
+  zeta = (beta - alpha) / (2 gamma),
   t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
   [a_p, a_q] <- [c a_p - s a_q, s a_p + c a_q]  (same rotation on V).
 
@@ -49,6 +52,7 @@ def jacobi_svd(A: np.ndarray, tol: float | None = None, max_sweeps: int = 60):
     if m < k:
         raise ValueError("jacobi_svd expects m >= k (QR-reduce wide matrices first)")
     V = np.eye(k)
+    floor2 = (np.finfo(np.float64).eps ** 2) * float(np.sum(A * A))
     if k > 1:
         rounds = _round_robin(k)
         for _ in range(max_sweeps):
@@ -62,6 +66,7 @@ def jacobi_svd(A: np.ndarray, tol: float | None = None, max_sweeps: int = 60):
                 gamma = np.einsum("ij,ij->j", ap, aq)
                 act = np.abs(gamma) > tol * np.sqrt(alpha * beta)
                 act &= gamma != 0.0
+                act &= (alpha > floor2) & (beta > floor2)
                 if not act.any():
                     continue
                 rotated = True

@@ -9,6 +9,9 @@
 #define HTG_WARP 32
 // dynamic shared memory a single-CTA-per-matrix kernel may request (sm_103a allows 227 KB)
 #define HTG_SMEM_BYTES (200 * 1024)
+// largest number of column pairs in one Jacobi round (node factors up to 2 * HTG_SVD_MAXP
+// columns); their rotation parameters live in static shared memory next to the dynamic part
+#define HTG_SVD_MAXP 1024
 
 // ------------------------------------------------------------------ tree ----
 struct TreeInfo {
@@ -53,7 +56,7 @@ struct QrDesc {
 // One-sided Jacobi SVD of M = P^T where P (p x q, ldp) is given.  Rows of M beyond q
 // (when q < p) are treated as zero.  Outputs: sigma (p, descending), V (p x p, ldv = p)
 // = left singular vectors of P, U (q x p, ldu = q) = right singular vectors of P with
-// unit columns (zero for sigma = 0).  work: (max(p,q) + p) * p values.
+// unit columns (zero for sigma = 0).  work: 2.5 max(p,q) p + 3.5 p^2 + p + 2 values.
 struct SvdDesc {
   const double* P;
   double* sigma;
@@ -77,22 +80,71 @@ __host__ __device__ inline int htg_max(int a, int b) { return a > b ? a : b; }
 __host__ __device__ inline int htg_cdiv(int a, int b) { return (a + b - 1) / b; }
 
 // ------------------------------------------------------- FP64 special values ---
-// On GB300 a dependent FP64 operation costs about 64 cycles and an FP64 sqrt / divide
-// several hundred, against 4.5 / 50-70 cycles in FP32.  These helpers take an FP32 seed
-// and refine it with one Newton-Raphson step in FP64 (relative error ~ 1.5 e0^2, e0 the
-// seed's error of about 6e-8, i.e. ~1e-14).  Outside the FP32 normal range they fall
-// back to the FP64 library functions.
+// Measured on GB300 (dependent chains): FP64 FMA 64 cycles, FP64 sqrt 674, divide / rsqrt
+// 429, a double<->float conversion about 400 and an FP64 compare-and-select about 800,
+// against 4.5 - 70 cycles for their FP32 and integer counterparts.  The helpers below keep
+// FP64 compares and conversions out of hot loops: comparisons act on the IEEE bit patterns
+// (ordered 64-bit integers), conversions move exponent and mantissa bits with integer
+// instructions, and reciprocal (square) roots take an FP32 seed refined by two FP64
+// Newton-Raphson steps (each squares the relative error; 2e-7 -> 6e-14 -> rounding level).
+
+// a > 0 (and not -0, NaN counts as positive)
+__device__ inline bool htg_dpos(double a) { return __double_as_longlong(a) > 0; }
+// a > b for a, b >= 0
+__device__ inline bool htg_dgt_nn(double a, double b) { return __double_as_longlong(a) > __double_as_longlong(b); }
+// 0 < a < inf (false for NaN, zero, negative)
+__device__ inline bool htg_dpos_finite(double a) {
+  const long long b = __double_as_longlong(a);
+  return b > 0 && b < 0x7FF0000000000000ll;
+}
+// a != 0 (either sign)
+__device__ inline bool htg_dnz(double a) { return (__double_as_longlong(a) << 1) != 0; }
+__device__ inline double htg_dabs(double a) { return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll); }
+// |a| > |b|
+__device__ inline bool htg_dabs_gt(double a, double b) {
+  return (__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFll) > (__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFll);
+}
+__device__ inline double htg_dmax_nn(double a, double b) { return htg_dgt_nn(a, b) ? a : b; }
+
+// double -> float by truncating the mantissa; |x| outside the FP32 normal range gives +-0 / +-inf
+__device__ inline float htg_d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (e <= 0) return __int_as_float((int)sign);
+  if (e >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+  return __int_as_float((int)(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu)));
+}
+// float -> double, exact for normal floats and zero (FP32 denormals become 0)
+__device__ inline double htg_f2d(float f) {
+  const unsigned int u = (unsigned int)__float_as_int(f);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  const unsigned long long ee = (e == 255) ? 0x7FF0000000000000ull : (unsigned long long)(e - 127 + 1023) << 52;
+  return __longlong_as_double((long long)(sign | ee | m));
+}
+// exponent test without FP64 compares: 2^-120 <= |x| < 2^120
+__device__ inline bool htg_in_f32_range(double x) {
+  const int e = (int)((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7FF) - 1023;
+  return e > -120 && e < 120;
+}
 __device__ inline double htg_rsqrt_fast(double x) {
-  if (!(x > 1e-36 && x < 1e36)) return rsqrt(x);
-  const double y = (double)rsqrtf((float)x);
-  const double h = x * y;               // Newton for f(y) = 1/y^2 - x:  y <- y (3 - x y^2) / 2
+  if (!htg_in_f32_range(x) || !htg_dpos(x)) return rsqrt(x);
+  double y = htg_f2d(rsqrtf(htg_d2f(x)));
+  // two Newton steps for f(y) = 1/y^2 - x, y <- y (3 - x y^2) / 2: seed error ~2e-7 (truncated
+  // conversion) -> 6e-14 -> rounding level; Jacobi rotations need c^2 + s^2 = 1 to rounding
+  double h = x * y;
+  y = fma(0.5 * y, fma(-h, y, 1.0), y);
+  h = x * y;
   return fma(0.5 * y, fma(-h, y, 1.0), y);
 }
 __device__ inline double htg_rcp_fast(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-36 && ax < 1e36)) return 1.0 / x;
-  const double y = (double)(1.0f / (float)x);
-  return fma(y, fma(-x, y, 1.0), y);    // Newton for f(y) = 1/y - x:  y <- y (2 - x y)
+  if (!htg_in_f32_range(x)) return 1.0 / x;
+  double y = htg_f2d(1.0f / htg_d2f(x));
+  y = fma(y, fma(-x, y, 1.0), y);       // Newton for f(y) = 1/y - x:  y <- y (2 - x y), twice
+  return fma(y, fma(-x, y, 1.0), y);
 }
 
 // ------------------------------------------------------------ context access ---
@@ -108,6 +160,8 @@ struct CpWs {
   double* epsacc;  // 64 (per-sweep accumulators)
   GemmDesc* descs; // 4 * HT_MAXD
   double* Z;       // HT_MAXD x nmax x 3 rcap   powers [X, A X, A^2 X] of the step's input
+  double* acc2;    // 2 doubles: per-mode sums of the convergence measure (persistent kernel)
+  unsigned int* bar;   // 2 words: grid barrier arrival count and generation
   int rcap, rycap, nmax;
 };
 CpWs* htg_ctx_cp(ht_ctx* c);

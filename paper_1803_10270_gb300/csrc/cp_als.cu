@@ -109,8 +109,9 @@ __global__ void cp_normalize_kernel(CpArgs a, int fold) {
     double w = a.lam[l];
     for (int k = 0; k < a.d; ++k) {
       const double nr = nrm[k * a.r + l];
-      if (nr > 0.0) w *= nr;
-      nrm[k * a.r + l] = nr > 0.0 ? 1.0 / nr : 1.0;
+      const bool pos = htg_dpos_finite(nr);
+      if (pos) w *= nr;
+      nrm[k * a.r + l] = pos ? htg_rcp_fast(nr) : 1.0;
     }
     wfin[l] = w;
     a.lam[l] = fold ? 1.0 : w;
@@ -175,7 +176,7 @@ __global__ void cp_solve_kernel(CpArgs a, CpWs w, int k, int sweep, int* err, do
     for (int j = 0; j < r; ++j) {
       if (tid == 0) {
         const double dj = Lm[j + r * j];
-        if (!(dj > 0.0)) ok = 0;
+        if (!htg_dpos_finite(dj)) ok = 0;
         const double sq = ok ? sqrt(dj) : 1.0;
         Lm[j + r * j] = sq;
         rinv[j] = 1.0 / sq;
@@ -241,7 +242,7 @@ __global__ void cp_solve_kernel(CpArgs a, CpWs w, int k, int sweep, int* err, do
     if ((tid & 31) == 0) {
       const double nr = sqrt(s2);
       a.lam[l] = (a.variant == CP_ALS_GS) ? nr : a.lam[l];
-      rinv[l] = nr > 0.0 ? 1.0 / nr : 1.0;
+      rinv[l] = htg_dpos_finite(nr) ? htg_rcp_fast(nr) : 1.0;
     }
   }
   if (tid == 0 && flops) {
@@ -473,7 +474,7 @@ __global__ void cp_mode_prep_kernel(CpArgs a, CpWs w, int k, int r0, const doubl
     for (int j = 0; j < r; ++j) {
       if (tid == 0) {
         const double dj = Lm[j + r * j];
-        if (!(dj > 0.0)) ok = 0;
+        if (!htg_dpos_finite(dj)) ok = 0;
         const double ri = ok ? htg_rsqrt_fast(dj) : 1.0;
         Lm[j + r * j] = ok ? dj * ri : 1.0;
         rinv[j] = ri;
@@ -551,7 +552,7 @@ __global__ void cp_mode_finish_kernel(CpArgs a, CpWs w, int k, int sweep, double
     if ((tid & 31) == 0) {
       const double nr = sqrt(s2);
       if (a.variant == CP_ALS_GS) a.lam[l] = nr;
-      rinv[l] = nr > 0.0 ? 1.0 / nr : 1.0;
+      rinv[l] = htg_dpos_finite(nr) ? htg_rcp_fast(nr) : 1.0;
     }
   }
   if (tid == 0) {
@@ -601,6 +602,359 @@ __global__ void cp_plan_rk2_kernel(CpArgs a, CpWs w, int r0) {
 
 __global__ void cp_copy_weights_kernel(const double* src, double* dst, int r) {
   for (int i = threadIdx.x; i < r; i += blockDim.x) dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form of cp_als_sweep_rk2: one cooperative launch runs every sweep.  CTA b owns
+// factor column b (row b of the r0 x r blocks in the solve phase); phases are separated by
+// a grid barrier:
+//   0a  powers Z_j^(p) of x_old (CTA b < r0), mu <- weights of x_old, normalise column b of x
+//   0b  column b of G_j = X_j^T X_j and M_j = Z_j^T X_j for every j
+//   per mode k:  A  Gamma_k (Cholesky) and row b of W = Hs Gamma_k^-1      (CTA b < r0)
+//                B  column b of X~_k = Z_k W, convergence sums, X_k[:, b] and lam_b
+//                C  column b of G_k and M_k; CTA 0 records the mode's convergence measure
+// The launch is cooperative (all CTAs resident), and every barrier wait is bounded: past the
+// limit the kernel records HT_ERR_TIMEOUT in the error word and returns.
+// ---------------------------------------------------------------------------
+constexpr long long BARRIER_TIMEOUT_CYCLES = 400000000LL;   // about 0.2 s
+
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
+    int ok = 1;
+    if (arrived == nblocks) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > BARRIER_TIMEOUT_CYCLES) {
+          ok = 0;
+          if (err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// column b of G_j (r values) and, when withM, of M_j (3 r0 values); X_j[:, b] staged in xs
+__device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool withM, double* xs) {
+  const int n = a.n[j], r = a.r;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = a.X[j][i + (long long)n * b];
+  __syncthreads();
+  const double* Zj = w.Z + (long long)j * w.nmax * 3 * w.rcap;
+  const int nout = r + (withM ? 3 * r0 : 0);
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const double* src = (o < r) ? a.X[j] + (long long)n * o : Zj + (long long)n * (o - r);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 3 < n; i += 4) {
+      s0 = fma(src[i], xs[i], s0);
+      s1 = fma(src[i + 1], xs[i + 1], s1);
+      s2 = fma(src[i + 2], xs[i + 2], s2);
+      s3 = fma(src[i + 3], xs[i + 3], s3);
+    }
+    for (; i < n; ++i) s0 = fma(src[i], xs[i], s0);
+    const double v = (s0 + s1) + (s2 + s3);
+    if (o < r) w.G[(long long)j * w.rcap * w.rcap + o + (long long)r * b] = v;
+    else w.H[(long long)j * w.rycap * w.rcap + (o - r) + (long long)3 * r0 * b] = v;
+  }
+  __syncthreads();
+}
+
+// unit columns across all dimensions for column b (norms into lam_b, or folded into X_0 when fold)
+__device__ void normalise_column(const CpArgs& a, int b, bool fold, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = wid; k < a.d; k += blockDim.x >> 5) {
+    const double* col = a.X[k] + (long long)a.n[k] * b;
+    double s = 0.0;
+    for (int j = lane; j < a.n[k]; j += 32) s = fma(col[j], col[j], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[k] = sqrt(s);
+  }
+  __syncthreads();
+  __shared__ double wfin;
+  if (threadIdx.x == 0) {
+    double wv = a.lam[b];
+    for (int k = 0; k < a.d; ++k) {
+      const double nr = red[k];
+      const bool pos = htg_dpos_finite(nr);
+      if (pos) wv *= nr;
+      red[k] = pos ? htg_rcp_fast(nr) : 1.0;
+    }
+    wfin = wv;
+    a.lam[b] = fold ? 1.0 : wv;
+  }
+  __syncthreads();
+  for (int k = 0; k < a.d; ++k) {
+    double* col = a.X[k] + (long long)a.n[k] * b;
+    const double sc = red[k] * ((fold && k == 0) ? wfin : 1.0);
+    for (int j = threadIdx.x; j < a.n[k]; j += blockDim.x) col[j] *= sc;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
+                                                            int sweeps, int* err) {
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const unsigned int nb = gridDim.x;
+  const int d = a.d, r = a.r, r0 = pa.r0;
+  extern __shared__ double sh[];
+  double* Lm = sh;                    // r x r
+  double* hs = Lm + r * r;            // 3 r
+  double* rinv = hs + 3 * r;          // r
+  double* xs = rinv + r;              // nmax
+  double* ys = xs + w.nmax;           // nmax
+  __shared__ unsigned char pw[153][MODE_MAXD];
+  __shared__ double cf[153];
+  __shared__ double red[HT_MAXD + 32];
+  __shared__ int ok;
+  const int nt = 1 + 2 * d + d * (d - 1) / 2;
+  for (int e = tid; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
+  for (int e = tid; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
+  const bool gs = (a.variant == CP_ALS_GS);
+  // ---------------- 0a
+  if (b < r0) {
+    for (int k = 0; k < d; ++k) {
+      const int n = pa.n[k], hw = pa.hw[k];
+      for (int j = tid; j < n; j += blockDim.x) xs[j] = pa.X[k][j + (long long)n * b];
+      __syncthreads();
+      double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
+      for (int j = tid; j < n; j += blockDim.x) {
+        double s = 0.0;
+        for (int o = -hw; o <= hw; ++o) {
+          int jj = (j + o) % n;
+          if (jj < 0) jj += n;
+          s = fma(pa.c[k][o + hw], xs[jj], s);
+        }
+        ys[j] = s;
+        Zk[j + (long long)n * b] = xs[j];
+        Zk[j + (long long)n * (r0 + b)] = s;
+      }
+      __syncthreads();
+      for (int j = tid; j < n; j += blockDim.x) {
+        double s = 0.0;
+        for (int o = -hw; o <= hw; ++o) {
+          int jj = (j + o) % n;
+          if (jj < 0) jj += n;
+          s = fma(pa.c[k][o + hw], ys[jj], s);
+        }
+        Zk[j + (long long)n * (2 * r0 + b)] = s;
+      }
+      __syncthreads();
+    }
+  }
+  if (b == 0) {
+    for (int i = tid; i < r0; i += blockDim.x) w.wold[i] = mu_src[i];
+    for (int i = tid; i < sweeps && i < 64; i += blockDim.x) w.epsacc[i] = 0.0;
+  }
+  // the iterate's column b may alias x_old: everything of x_old is read above, before the barrier
+  if (!grid_barrier(w.bar, nb, err)) return;
+  if (b < r) normalise_column(a, b, !gs, red);
+  if (!grid_barrier(w.bar, nb, err)) return;
+  // ---------------- 0b
+  if (b < r)
+    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs);
+  if (!grid_barrier(w.bar, nb, err)) return;
+  const double* mu = w.wold;
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int k = 0; k < d; ++k) {
+      // ---------------- A: Gamma_k, Cholesky, row b of W
+      if (b == 0 && tid == 0) { w.acc2[0] = 0.0; w.acc2[1] = 0.0; }
+      if (b < r0) {
+        const int lp = b;
+        for (int l = tid; l < r; l += blockDim.x) {
+          double mv[MODE_MAXD][3];
+          for (int j = 0; j < d; ++j) {
+            if (j == k) continue;
+            const double* Mj = w.H + (long long)j * w.rycap * w.rcap + lp + (long long)3 * r0 * l;
+            mv[j][0] = Mj[0];
+            mv[j][1] = Mj[r0];
+            mv[j][2] = Mj[2 * r0];
+          }
+          double acc[3] = {0.0, 0.0, 0.0};
+          for (int ti = 0; ti < nt; ++ti) {
+            double v = cf[ti];
+            for (int j = 0; j < d; ++j)
+              if (j != k) v *= mv[j][pw[ti][j]];
+            acc[pw[ti][k]] += v;
+          }
+          const double m = mu[lp];
+          hs[l] = m * acc[0];
+          hs[r + l] = m * acc[1];
+          hs[2 * r + l] = m * acc[2];
+        }
+        for (int e = tid; e < r * r; e += blockDim.x) {
+          double v = 1.0;
+          for (int j = 0; j < d; ++j)
+            if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+          Lm[e] = v;
+        }
+        __syncthreads();
+        for (int attempt = 0; attempt < 2; ++attempt) {
+          if (attempt == 1) {
+            double tr = 0.0;
+            for (int i = 0; i < r; ++i) {
+              double v = 1.0;
+              for (int j = 0; j < d; ++j)
+                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
+              tr += v;
+            }
+            const double shift = 1e-14 * tr / r;
+            for (int e = tid; e < r * r; e += blockDim.x) {
+              double v = 1.0;
+              for (int j = 0; j < d; ++j)
+                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+              Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
+            }
+          }
+          if (tid == 0) ok = 1;
+          __syncthreads();
+          for (int j = 0; j < r; ++j) {
+            if (tid == 0) {
+              const double dj = Lm[j + r * j];
+              if (!htg_dpos_finite(dj)) ok = 0;
+              const double ri = ok ? htg_rsqrt_fast(dj) : 1.0;
+              Lm[j + r * j] = ok ? dj * ri : 1.0;
+              rinv[j] = ri;
+            }
+            __syncthreads();
+            if (!ok) break;
+            const double inv = rinv[j];
+            for (int i = j + 1 + tid; i < r; i += blockDim.x) Lm[i + r * j] *= inv;
+            __syncthreads();
+            const int m = r - j - 1;
+            for (int e = tid; e < m * m; e += blockDim.x) {
+              const int i = j + 1 + e % m, cc = j + 1 + e / m;
+              if (cc <= i) Lm[i + r * cc] -= Lm[i + r * j] * Lm[cc + r * j];
+            }
+            __syncthreads();
+          }
+          const int good = ok;
+          __syncthreads();
+          if (good) break;
+        }
+        if (!ok) {
+          if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
+        } else {
+          for (int j = 0; j < r; ++j) {
+            if (tid < 3) hs[tid * r + j] *= rinv[j];
+            __syncthreads();
+            for (int e = tid; e < 3 * (r - j - 1); e += blockDim.x) {
+              const int pv = e / (r - j - 1), i = j + 1 + e % (r - j - 1);
+              hs[pv * r + i] -= Lm[i + r * j] * hs[pv * r + j];
+            }
+            __syncthreads();
+          }
+          for (int j = r - 1; j >= 0; --j) {
+            if (tid < 3) hs[tid * r + j] *= rinv[j];
+            __syncthreads();
+            for (int e = tid; e < 3 * j; e += blockDim.x) {
+              const int pv = e / j, i = e % j;
+              hs[pv * r + i] -= Lm[j + r * i] * hs[pv * r + j];
+            }
+            __syncthreads();
+          }
+        }
+        for (int e = tid; e < 3 * r; e += blockDim.x) {
+          const int pp = e / r, l = e % r;
+          w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = hs[e];
+        }
+      }
+      if (!grid_barrier(w.bar, nb, err)) return;
+      // ---------------- B: column b of X~_k = Z_k W
+      if (b < r) {
+        const int n = a.n[k];
+        const double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
+        const double* Wb = w.Hh + (long long)3 * r0 * b;
+        const double lam_old = a.lam[b];
+        double* col = a.X[k] + (long long)n * b;
+        double num = 0.0, den = 0.0, nrm2 = 0.0;
+        for (int row = tid; row < n; row += blockDim.x) {
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int i = 0;
+          const int K = 3 * r0;
+          for (; i + 3 < K; i += 4) {
+            s0 = fma(Zk[row + (long long)n * i], Wb[i], s0);
+            s1 = fma(Zk[row + (long long)n * (i + 1)], Wb[i + 1], s1);
+            s2 = fma(Zk[row + (long long)n * (i + 2)], Wb[i + 2], s2);
+            s3 = fma(Zk[row + (long long)n * (i + 3)], Wb[i + 3], s3);
+          }
+          for (; i < K; ++i) s0 = fma(Zk[row + (long long)n * i], Wb[i], s0);
+          const double v = (s0 + s1) + (s2 + s3);
+          xs[row] = v;
+          const double old = col[row] * (gs ? lam_old : 1.0);
+          const double df = v - old;
+          num = fma(df, df, num);
+          den = fma(old, old, den);
+          nrm2 = fma(v, v, nrm2);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          num += __shfl_xor_sync(0xffffffffu, num, o);
+          den += __shfl_xor_sync(0xffffffffu, den, o);
+          nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+        }
+        __shared__ double r3[3][NT / 32];
+        if ((tid & 31) == 0) { r3[0][tid >> 5] = num; r3[1][tid >> 5] = den; r3[2][tid >> 5] = nrm2; }
+        __syncthreads();
+        __shared__ double scol;
+        if (tid == 0) {
+          double tn = 0.0, td = 0.0, t2 = 0.0;
+          for (int q = 0; q < NT / 32; ++q) { tn += r3[0][q]; td += r3[1][q]; t2 += r3[2][q]; }
+          atomicAdd(&w.acc2[0], tn);
+          atomicAdd(&w.acc2[1], td);
+          const double nr = sqrt(t2);
+          if (gs) a.lam[b] = nr;
+          scol = htg_dpos_finite(nr) ? htg_rcp_fast(nr) : 1.0;
+        }
+        __syncthreads();
+        if (gs) {
+          for (int row = tid; row < n; row += blockDim.x) col[row] = xs[row] * scol;
+        } else {
+          double* dst = w.Xold + (long long)k * w.nmax * w.rcap + (long long)n * b;
+          for (int row = tid; row < n; row += blockDim.x) dst[row] = xs[row];
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(w.bar, nb, err)) return;
+      // ---------------- C: refresh column b of G_k, M_k; record the mode's measure
+      if (gs && b < r) gram_column(a, w, k, b, r0, true, xs);
+      if (b == 0 && tid == 0) {
+        const double tn = w.acc2[0], td = w.acc2[1];
+        const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
+        if (htg_dgt_nn(ek, w.epsacc[sweep])) w.epsacc[sweep] = ek;
+      }
+      if (!grid_barrier(w.bar, nb, err)) return;
+    }
+    if (!gs) {
+      // damped Jacobi update of every factor column b, then refresh the Grams
+      if (b < r) {
+        for (int k = 0; k < d; ++k) {
+          const int n = a.n[k];
+          const double* src = w.Xold + (long long)k * w.nmax * w.rcap + (long long)n * b;
+          double* col = a.X[k] + (long long)n * b;
+          for (int row = tid; row < n; row += blockDim.x) col[row] += 0.25 * (src[row] - col[row]);
+        }
+      }
+      if (!grid_barrier(w.bar, nb, err)) return;
+      if (b < r)
+        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs);
+      if (!grid_barrier(w.bar, nb, err)) return;
+    }
+  }
+  if (!gs && b < r) normalise_column(a, b, false, red);
 }
 
 // dynamic shared memory of cp_solve_kernel: L (r x r), norms (r), staged rows (n x r)
@@ -757,57 +1111,43 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   a.mu = w->wold;
   const int r0 = x_old->rank;
   cudaStream_t s = (cudaStream_t)stream;
-  const int grid = htg_ctx_grid(c);
+  (void)nmax;
+  // one cooperative launch: CTA b owns factor column b (and row b of the solve)
+  const int nblk = htg_max(a.r, r0);
+  const size_t smem = ((size_t)a.r * a.r + 4 * (size_t)a.r + 2 * (size_t)w->nmax) * sizeof(double);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(cp_als_rk2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return HT_ERR_CUDA;
+  }
   int launches = 0;
-#define CPL(cls, expr)                                         \
-  do {                                                         \
-    htg_prof_begin(c, s);                                      \
-    expr;                                                      \
-    htg_prof_end(c, (cls), s);                                 \
-    ++launches;                                                \
-    if (cudaGetLastError() != cudaSuccess) {                   \
-      htg_ctx_count(c, launches, s);                           \
-      return HT_ERR_CUDA;                                      \
-    }                                                          \
-  } while (0)
-#define CPG(descs, nd)                                                                    \
-  do {                                                                                    \
-    htg_prof_begin(c, s);                                                                 \
-    cudaError_t _e = htg_launch_gemm((descs), (nd), grid, s, htg_prof_flops(c, KC_GEMM)); \
-    htg_prof_end(c, KC_GEMM, s);                                                          \
-    ++launches;                                                                           \
-    if (_e != cudaSuccess) {                                                              \
-      htg_ctx_count(c, launches, s);                                                      \
-      return HT_ERR_CUDA;                                                                 \
-    }                                                                                     \
-  } while (0)
-  // the step input is read first (powers, weights), so x_old may alias x
-  CPL(KC_CPSMALL, (cp_powers_kernel<<<dim3(r0, d), 128, 2 * nmax * sizeof(double), s>>>(pa, *w)));
-  CPL(KC_CPSMALL, (cp_copy_weights_kernel<<<1, 64, 0, s>>>(x_old->weight, w->wold, r0)));
-  const int fold = (variant == CP_ALS_JACOBI_DAMPED) ? 1 : 0;
-  CPL(KC_CPSMALL, (cp_eps_init_kernel<<<1, 64, 0, s>>>(*w, sweeps)));
-  CPL(KC_CPSMALL, (cp_plan_rk2_kernel<<<1, 1, 0, s>>>(a, *w, r0)));
-  CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, fold)));
-  for (int k = 0; k < d; ++k) {
-    CPG(w->descs + 3 * k + 1, 2);
+  htg_prof_begin(c, s);
+  cudaError_t e0 = cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned int), s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblk);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_persistent, a, pa, *w, (const double*)x_old->weight, sweeps,
+                                      htg_ctx_err(c));
+  htg_prof_end(c, KC_CPSOLVE, s);
+  ++launches;
+  if (e0 != cudaSuccess || e1 != cudaSuccess) {
+    htg_ctx_count(c, launches, s);
+    return HT_ERR_CUDA;
   }
-  const size_t prep_smem = ((size_t)a.r * a.r + 4 * (size_t)a.r) * sizeof(double);
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int k = 0; k < d; ++k) {
-      CPL(KC_CPSOLVE, (cp_mode_prep_kernel<<<r0, 64, prep_smem, s>>>(a, *w, k, r0, w->wold, htg_ctx_err(c))));
-      CPG(w->descs + 3 * k, 1);
-      CPL(KC_CPSMALL, (cp_mode_finish_kernel<<<1, NT, 0, s>>>(a, *w, k, sw, htg_prof_flops(c, KC_CPSMALL))));
-      if (variant == CP_ALS_GS) CPG(w->descs + 3 * k + 1, 2);
-    }
-    if (variant == CP_ALS_JACOBI_DAMPED) {
-      CPL(KC_CPSMALL, (cp_damp_kernel<<<dim3(8, d), NT, 0, s>>>(a, *w)));
-      for (int k = 0; k < d; ++k) CPG(w->descs + 3 * k + 1, 2);
+  if (eps_dev && sweeps > 0) {
+    cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev);
+    ++launches;
+    if (cudaGetLastError() != cudaSuccess) {
+      htg_ctx_count(c, launches, s);
+      return HT_ERR_CUDA;
     }
   }
-  if (variant == CP_ALS_JACOBI_DAMPED) CPL(KC_CPSMALL, (cp_normalize_kernel<<<1, NT, 0, s>>>(a, 0)));
-  if (eps_dev && sweeps > 0) CPL(KC_CPSMALL, (cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev)));
-#undef CPL
-#undef CPG
   htg_ctx_count(c, launches, s);
   return HT_OK;
 }
@@ -902,6 +1242,9 @@ extern "C" int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps
   w.epsacc = b; b += NA_EPS;
   w.descs = (GemmDesc*)b; b += NA_DESC;
   int* err = (int*)b;
+  w.Z = nullptr;
+  w.acc2 = nullptr;
+  w.bar = nullptr;
   w.rcap = NA_MAXR;
   w.rycap = NA_MAXRY;
   w.nmax = NA_MAXN;

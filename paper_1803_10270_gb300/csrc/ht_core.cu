@@ -63,8 +63,8 @@ struct Plan {
   GemmDesc g_abs1[MAXLEV][NN];
   GemmDesc g_abs2[MAXLEV][NN];
   GemmDesc g_rootE[2];
-  GemmDesc g_P[MAXLEV][NN];
-  SvdDesc svd[MAXLEV][NN];
+  GemmDesc g_Pall[NN];        // P_t = R_t E_t for every non-root node (slot t-1)
+  SvdDesc svd_all[NN];
   GemmDesc g_T1[MAXLEV][NN];
   GemmDesc g_Epre[MAXLEV][2 * NN];
   GemmDesc g_XY[2 * NN];
@@ -100,7 +100,7 @@ struct WsNode {
   double* sig;    // singular values                              Kc
   double* W;      // left singular vectors of P                   Kc x Kc
   double* Z;      // right singular vectors of P                  Kc x Kc
-  double* SW;     // SVD work                                     2 Kc^2 + Kc
+  double* SW;     // SVD work                                     6 Kc^2 + Kc + 2
   double* X;      // W_k^T R                                      Kc x Kc
   double* Y;      // E Z_k / s                                    Kc x Kc
   double* invsig; // 1/s_k                                        Kc
@@ -227,9 +227,9 @@ __global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const 
   for (int dep = 1; dep < MAXLEV; ++dep) {
     for (int s = 0; s < L.n_all[dep]; ++s) {
       const int t = L.all[dep][s];
-      fill_gemm(P->g_P[dep][s], wn[t].Rf, P->Rp[t], 0, wn[t].E, P->K[t], 0, wn[t].P, P->Rp[t],
+      fill_gemm(P->g_Pall[t - 1], wn[t].Rf, P->Rp[t], 0, wn[t].E, P->K[t], 0, wn[t].P, P->Rp[t],
                 P->Rp[t], P->mE[t], P->K[t]);
-      SvdDesc& v = P->svd[dep][s];
+      SvdDesc& v = P->svd_all[t - 1];
       v.P = wn[t].P; v.p = P->Rp[t]; v.q = P->mE[t]; v.ldp = P->Rp[t];
       v.sigma = wn[t].sig; v.V = wn[t].W; v.U = wn[t].Z; v.work = wn[t].SW;
     }
@@ -279,9 +279,9 @@ __global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtV
     int k = p;
     // tail(kk) = sum_{j >= kk} s_j^2; smallest kk >= 1 with tail <= thr2
     for (int kk = p; kk >= 1; --kk) {
-      if (tail <= thr2) k = kk;
+      if (!htg_dgt_nn(tail, thr2)) k = kk;   // tail <= thr2 (both >= 0), as a bit compare
       else break;
-      tail += s[kk - 1] * s[kk - 1];
+      tail = fma(s[kk - 1], s[kk - 1], tail);
     }
     // (loop above walks kk downward while tail(kk) <= thr2)
     k = htg_max(1, htg_min(k, rmax));
@@ -290,7 +290,7 @@ __global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtV
     out.rank[t] = k;
     for (int j = 0; j < P->Rp[t]; ++j) {
       const double sj = wn[t].sig[j];
-      wn[t].invsig[j] = (j < k && sj > 0.0) ? 1.0 / sj : 0.0;
+      wn[t].invsig[j] = (j < k && htg_dpos_finite(sj)) ? 1.0 / sj : 0.0;
     }
     if (sigma_out) {
       for (int j = 0; j < sig_stride; ++j)
@@ -656,7 +656,7 @@ static int trunc_input_cap(const ht_config* c) {
 }
 
 struct WsLayout {
-  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[10], off_prof;
+  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
   size_t total;
@@ -678,10 +678,10 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
     const size_t rc = (size_t)c->cap, ry = rc * (size_t)htg_cp_terms(c->d);
     size_t nmax = 1;
     for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
-    const size_t cps[10] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
+    const size_t cps[11] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
                             HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1,
-                            HT_MAXD * nmax * 3 * rc};
-    for (int j = 0; j < 10; ++j) {
+                            HT_MAXD * nmax * 3 * rc, 8};
+    for (int j = 0; j < 11; ++j) {
       W->off_cp[j] = off;
       off = align_up(off + cps[j] * sizeof(double));
     }
@@ -692,7 +692,7 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   if (K3 < nmax * Kc) K3 = nmax * Kc;             // leaf QR scratch (n x Kc)
   if (K3 < (size_t)NN * Kc * Kc) K3 = (size_t)NN * Kc * Kc;   // per-node Grams of ht_inner
   const size_t K2 = Kc * Kc;
-  const size_t sizes[15] = {K2, K3, K3, K3, K3, K3, K2, K2, Kc, K2, K2, 2 * K2 + Kc, K2, K2, Kc};
+  const size_t sizes[15] = {K2, K3, K3, K3, K3, K3, K2, K2, Kc, K2, K2, 6 * K2 + Kc + 8, K2, K2, Kc};
   for (int t = 0; t < T.nn; ++t) {
     for (int j = 0; j < 15; ++j) {
       W->node_off[t][j] = off;
@@ -727,7 +727,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   build_levels(c->tree, &c->lev);
   c->Kc = trunc_input_cap(cfg);
   c->cap = cfg->cap;
-  if (c->Kc > 4096) { delete c; return HT_ERR_CAPACITY; }
+  if (c->Kc > 2 * HTG_SVD_MAXP) { delete c; return HT_ERR_CAPACITY; }
   WsLayout W;
   layout(cfg, c->tree, &W);
   c->ws_bytes = W.total;
@@ -757,6 +757,8 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     for (int j = 0; j < 8; ++j) *cpf[j] = (double*)(base + W.off_cp[j]);
     c->cp.descs = (GemmDesc*)(base + W.off_cp[8]);
     c->cp.Z = (double*)(base + W.off_cp[9]);
+    c->cp.acc2 = (double*)(base + W.off_cp[10]);
+    c->cp.bar = (unsigned int*)(base + W.off_cp[10] + 4 * sizeof(double));
     c->cp.rcap = cfg->cap;
     c->cp.rycap = cfg->cap * htg_cp_terms(cfg->d);
     int nmax = 1;
@@ -871,14 +873,16 @@ static int run_truncate(ht_ctx* c, const HtView& in, int cap_in, const HtView& o
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
   }
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM)));
-  for (int dep = 1; dep <= T.max_depth; ++dep) {
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_P[dep], L.n_all[dep], g, s, htg_prof_flops(c, KC_GEMM)));
-    HTG_LAUNCH(c, KC_SVD, s, htg_launch_svd(P->svd[dep], L.n_all[dep], c->svd_smem, c->Kc, c->Kc, s, htg_prof_flops(c, KC_SVD)));
+  // top-down complement factors: E of a child needs only E, B and R of its parent, never the
+  // parent's SVD, so every node SVD runs afterwards in a single launch
+  for (int dep = 1; dep < T.max_depth; ++dep) {
     if (L.n_int[dep] == 0) continue;
     HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
     HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
   }
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM)));
+  HTG_LAUNCH(c, KC_SVD, s, htg_launch_svd(P->svd_all, T.nn - 1, c->svd_smem, c->Kc, c->Kc, s, htg_prof_flops(c, KC_SVD)));
   HTG_LAUNCH(c, KC_PLAN, s, (rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev,
                                                           sig_stride, norm_dev, c->err),
                        cudaGetLastError()));

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     const double* B = g.B + (long long)b * g.sB;
     double* C = g.C + (long long)b * g.sC;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const bool has_beta = htg_dnz(g.beta);   // bit test: an FP64 compare costs ~800 cycles here
     for (int l0 = 0; l0 < g.k; l0 += BK) {
 #pragma unroll
       for (int p = 0; p < (BM * BK) / NT; ++p) {
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
           double v = g.alpha * acc[r][c];
           if (g.colscale) v *= g.colscale[gj];
           double* cp = C + gi + (long long)g.ldc * gj;
-          if (g.beta != 0.0) v += g.beta * *cp;
+          if (has_beta) v += g.beta * *cp;
           *cp = v;
         }
       }

@@ -61,13 +61,13 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
       const double x0 = col[j];
       const double n2 = fma(x0, x0, t);
       double alpha = 0.0, tau = 0.0;
-      if (n2 > 0.0) {
+      if (htg_dpos(n2)) {
         const double ri = htg_rsqrt_fast(n2);
         const double nrm = n2 * ri;
-        alpha = x0 > 0.0 ? -nrm : nrm;
+        alpha = htg_dpos(x0) ? -nrm : nrm;
         const double v0 = x0 - alpha;
         const double vv = fma(v0, v0, t);
-        tau = vv > 0.0 ? 2.0 * htg_rcp_fast(vv) : 0.0;
+        tau = htg_dpos(vv) ? 2.0 * htg_rcp_fast(vv) : 0.0;
         col[j] = v0;
       }
       sh_alpha = alpha;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     }
     __syncthreads();
     const double tau = sh_tau;
-    if (tau != 0.0) {
+    if (htg_dnz(tau)) {
       for (int c = j + 1 + wid; c < k; c += nw) {
         double* cc = S + (long long)m * c;
         double dot = 0.0;

@@ -30,11 +30,50 @@ __device__ inline int rr_player(int pos, int round, int p2) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (p2 - 1));
 }
 
-// FP64 cost model of this kernel: each FP64 warp instruction occupies the SM's FP64 pipe
-// for the whole warp whatever the number of active lanes.  A column pair is therefore
-// handled by a group of L lanes (L a power of two chosen from the column length): the
-// lanes split the rows, reduce their partial dot products with log2(L) shuffles, and every
-// group computes its own rotation parameters in the same instructions as the others.
+// Cost model: a dependent FP64 operation costs ~64 cycles on GB300 (FP32: 4.5), FP64 sqrt /
+// divide several hundred, and every FP64 warp instruction holds the SM's FP64 pipe for the
+// whole warp.  The SVD therefore runs in two phases:
+//  1. one-sided Jacobi entirely in FP32 on a scaled copy of M, accumulating V32 (cheap
+//     sweeps until |a.b| <= tol32 |a||b|);
+//  2. V32 is made orthogonal to FP64 accuracy by two Newton-Schulz steps
+//     V <- V (3 I - V^T V) / 2, then G = (M V)^T (M V) is formed in FP64; its off-diagonal
+//     part is now ~tol32 relative, so two-sided Jacobi on G (rotations applied to rows, then
+//     columns, of G and to V) converges in two or three FP64 sweeps while every entry keeps
+//     its relative accuracy (no cancellation with small rotation angles);
+//  3. U S = M V in FP64, S = column norms, sorted descending.
+// Rotation parameters: angle from an FP32 evaluation, c = (1 + t^2)^(-1/2) by an FP64 Newton
+// step and s = c t, so each FP64 rotation is orthogonal to FP64 accuracy.
+
+// round-robin pair (a < b) of position pi in a round, or a = -1 for a dummy player
+__device__ inline void rr_pair(int pi, int round, int p, int p2, int* a, int* b) {
+  int x = rr_player(pi, round, p2), y = rr_player(p2 - 1 - pi, round, p2);
+  if (x > y) { int t = x; x = y; y = t; }
+  *a = (y >= p) ? -1 : x;
+  *b = y;
+}
+
+// dst (r x c, ld r) = A (r x k, ld lda) * B (k x c, ld ldb), FP64, whole CTA
+__device__ void cta_gemm(double* dst, const double* A, int lda, const double* B, int ldb, int r, int c, int k,
+                         bool transA) {
+  for (int e = threadIdx.x; e < r * c; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int l = 0;
+    for (; l + 3 < k; l += 4) {
+      const double a0 = transA ? A[l + lda * i] : A[i + lda * l];
+      const double a1 = transA ? A[l + 1 + lda * i] : A[i + lda * (l + 1)];
+      const double a2 = transA ? A[l + 2 + lda * i] : A[i + lda * (l + 2)];
+      const double a3 = transA ? A[l + 3 + lda * i] : A[i + lda * (l + 3)];
+      s0 = fma(a0, B[l + ldb * j], s0);
+      s1 = fma(a1, B[l + 1 + ldb * j], s1);
+      s2 = fma(a2, B[l + 2 + ldb * j], s2);
+      s3 = fma(a3, B[l + 3 + ldb * j], s3);
+    }
+    for (; l < k; ++l) s0 = fma(transA ? A[l + lda * i] : A[i + lda * l], B[l + ldb * j], s0);
+    dst[i + r * j] = (s0 + s1) + (s2 + s3);
+  }
+}
+
 __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ descs, long long smem_doubles,
                                                 double* flops) {
   const SvdDesc D = descs[blockIdx.x];
@@ -42,88 +81,107 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   if (p <= 0) return;
   const int mr = htg_max(p, q);
   extern __shared__ double smem[];
-  // working copy in shared memory when the ACTUAL sizes fit, else in the global work buffer
-  const long long need = (long long)mr * p + (long long)p * p + p;
-  double* M = (need <= smem_doubles) ? smem : D.work;
-  double* V = M + (long long)mr * p;
+  // layout (doubles): M64 mr*p | N mr*p | G p*p | V p*p | T p*p | nrm p | M32 mr*p/2 | V32 p*p/2
+  const long long mp = (long long)mr * p, pp = (long long)p * p;
+  const long long need = 2 * mp + 3 * pp + p + (mp + 1) / 2 + (pp + 1) / 2 + 2;
+  double* base = (need <= smem_doubles) ? smem : D.work;
+  double* M = base;
+  double* N = M + mp;
+  double* G = N + mp;
+  double* V = G + pp;
+  double* T = V + pp;
+  double* nrm = T + pp;
+  float* M32 = (float*)(nrm + p);
+  float* V32 = M32 + mp + 1;
   const int tid = threadIdx.x;
-  for (long long e = tid; e < (long long)mr * p; e += NT) {
+  __shared__ int rotated;
+  __shared__ double red[NT / 32];
+  __shared__ double sc_[HTG_SVD_MAXP];
+  __shared__ double ss_[HTG_SVD_MAXP];
+  __shared__ int act_[HTG_SVD_MAXP];
+  for (long long e = tid; e < mp; e += NT) {
     const int i = (int)(e % mr), c = (int)(e / mr);
     M[e] = (i < q) ? D.P[c + (long long)D.ldp * i] : 0.0;
   }
-  for (int e = tid; e < p * p; e += NT) V[e] = (e % p == e / p) ? 1.0 : 0.0;
-  __shared__ int rotated;
+  // scale of the FP32 copy: 2^-e with 2^e about max |M| (keeps FP32 far from over/underflow)
+  double amax = 0.0, fro = 0.0;
+  for (long long e = tid; e < mp; e += NT) {
+    amax = htg_dmax_nn(amax, htg_dabs(M[e]));
+    fro = fma(M[e], M[e], fro);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    amax = htg_dmax_nn(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    fro += __shfl_xor_sync(0xffffffffu, fro, o);
+  }
+  __shared__ double red2[NT / 32];
+  if ((tid & 31) == 0) { red[tid >> 5] = amax; red2[tid >> 5] = fro; }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, f = 0.0;
+    for (int w = 0; w < NT / 32; ++w) { a = htg_dmax_nn(a, red[w]); f += red2[w]; }
+    red[0] = (a > 0.0) ? ldexp(1.0, -ilogb(a)) : 1.0;
+    red2[0] = f;
+  }
+  __syncthreads();
+  const double scale = red[0];
+  // rounding floor: columns with |col|^2 <= eps^2 |M|_F^2 carry no information and are not
+  // rotated (rotating them only reshuffles rounding noise and keeps the sweeps going)
+  const double floor2 = EPS * EPS * red2[0];
+  const float floor2_32 = htg_d2f(16.0 * 3.55e-15 * red2[0] * scale * scale);   // (4 eps32)^2 |M s|_F^2
+  for (long long e = tid; e < mp; e += NT) M32[e] = htg_d2f(M[e] * scale);
+  for (long long e = tid; e < pp; e += NT) V32[e] = (e % p == e / p) ? 1.0f : 0.0f;
   const int p2 = p + (p & 1);
   const int npairs = p2 / 2;
-  // lanes per pair: about 8 rows per lane, at most 32, and all pairs of a round in one pass
   int L = 1;
   while (L < 32 && L * 8 < htg_max(mr, p)) L <<= 1;
   while (L > 1 && npairs * L > NT) L >>= 1;
   const int gid = tid / L, gl = tid % L, ngroups = NT / L;
   const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((tid & 31) & ~(L - 1)));
   double myflops = 0.0;
-  const double TOL = EPS * (double)htg_max(mr, 8);
   __syncthreads();
+  // ---------------- phase 1: FP32 one-sided Jacobi
+  const float TOL32 = 4.0f * 5.96e-8f * (float)htg_max(mr, 8);
   if (p > 1) {
-    for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+    for (int sweep = 0; sweep < 20; ++sweep) {
       if (tid == 0) rotated = 0;
       __syncthreads();
       for (int round = 0; round < p2 - 1; ++round) {
         for (int pi = gid; pi < npairs; pi += ngroups) {
-          int a = rr_player(pi, round, p2), b = rr_player(p2 - 1 - pi, round, p2);
-          if (a >= p || b >= p) continue;
-          if (a > b) { int t = a; a = b; b = t; }
-          double* ca = M + (long long)mr * a;
-          double* cb = M + (long long)mr * b;
-          double al = 0.0, be = 0.0, ga = 0.0;
+          int a, b;
+          rr_pair(pi, round, p, p2, &a, &b);
+          if (a < 0) continue;
+          float* ca = M32 + (long long)mr * a;
+          float* cb = M32 + (long long)mr * b;
+          float al = 0.f, be = 0.f, ga = 0.f;
           for (int i = gl; i < mr; i += L) {
-            const double x = ca[i], y = cb[i];
-            al = fma(x, x, al);
-            be = fma(y, y, be);
-            ga = fma(x, y, ga);
+            const float x = ca[i], y = cb[i];
+            al = fmaf(x, x, al);
+            be = fmaf(y, y, be);
+            ga = fmaf(x, y, ga);
           }
           for (int o = L >> 1; o > 0; o >>= 1) {
             al += __shfl_xor_sync(gmask, al, o);
             be += __shfl_xor_sync(gmask, be, o);
             ga += __shfl_xor_sync(gmask, ga, o);
           }
-          if (gl == 0) myflops += 6.0 * mr;
-          if (ga != 0.0 && ga * ga > TOL * TOL * al * be) {
-            // tan of the rotation angle from an FP32 evaluation of
-            // zeta = (be - al) / (2 ga), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); the angle
-            // only steers the iteration, while c = (1 + t^2)^(-1/2) (FP64 Newton) and s = c t keep
-            // every rotation orthogonal to FP64 accuracy
-            const double diff = be - al;
-            double t;
-            const double ag = fabs(ga), ad = fabs(diff);
-            if (ag > 1e-30 && ag < 1e30 && ad < 1e30) {
-              const float zf = (float)diff / (2.0f * (float)ga);
-              const float azf = fabsf(zf);
-              const float tf = (azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f)));
-              t = (double)tf;
-            } else {
-              const double zeta = diff / (2.0 * ga);
-              const double az = fabs(zeta);
-              t = (az > 1e150) ? 0.5 / zeta : (zeta >= 0.0 ? 1.0 : -1.0) / (az + sqrt(fma(zeta, zeta, 1.0)));
-            }
-            const double c = htg_rsqrt_fast(fma(t, t, 1.0));
-            const double s = c * t;
+          if (ga != 0.f && al > floor2_32 && be > floor2_32 && fabsf(ga) > TOL32 * sqrtf(al) * sqrtf(be)) {
+            const float zf = (be - al) / (2.0f * ga);
+            const float azf = fabsf(zf);
+            const float t = (azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f)));
+            const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
             for (int i = gl; i < mr; i += L) {
-              const double x = ca[i], y = cb[i];
-              ca[i] = c * x - s * y;
-              cb[i] = s * x + c * y;
+              const float x = ca[i], y = cb[i];
+              ca[i] = c * x - sn * y;
+              cb[i] = sn * x + c * y;
             }
-            double* va = V + (long long)p * a;
-            double* vb = V + (long long)p * b;
+            float* va = V32 + (long long)p * a;
+            float* vb = V32 + (long long)p * b;
             for (int i = gl; i < p; i += L) {
-              const double x = va[i], y = vb[i];
-              va[i] = c * x - s * y;
-              vb[i] = s * x + c * y;
+              const float x = va[i], y = vb[i];
+              va[i] = c * x - sn * y;
+              vb[i] = sn * x + c * y;
             }
-            if (gl == 0) {
-              rotated = 1;
-              myflops += 6.0 * mr + 6.0 * p;
-            }
+            if (gl == 0) rotated = 1;
           }
         }
         __syncthreads();
@@ -133,29 +191,137 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
       if (!any) break;
     }
   }
-  if (flops && gl == 0 && myflops > 0.0) atomicAdd(flops, myflops);
-  // column norms, then descending order (ties by index)
+  // ---------------- phase 2: orthogonal V in FP64, G = (M V)^T (M V)
+  for (long long e = tid; e < pp; e += NT) V[e] = htg_f2d(V32[e]);
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    cta_gemm(T, V, p, V, p, p, p, p, true);                 // T = V^T V
+    __syncthreads();
+    for (long long e = tid; e < pp; e += NT) T[e] = ((e % p == e / p) ? 1.5 : 0.0) - 0.5 * T[e];
+    __syncthreads();
+    cta_gemm(N, V, p, T, p, p, p, p, false);                // N(p x p) = V (3I - V^T V)/2
+    __syncthreads();
+    for (long long e = tid; e < pp; e += NT) V[e] = N[e];
+    __syncthreads();
+  }
+  cta_gemm(N, M, mr, V, p, mr, p, p, false);                // N = M V
+  __syncthreads();
+  cta_gemm(G, N, mr, N, mr, p, p, mr, true);                // G = N^T N
+  __syncthreads();
+  if (gl == 0 && gid == 0) myflops += 4.0 * p * p * p + 2.0 * mr * p * p + 2.0 * mr * p * p;
+  // ---------------- phase 3: FP64 two-sided Jacobi on G (rotations also applied to V)
+  const double TOL = EPS * (double)htg_max(mr, 8);
+  const float TOL32G = htg_d2f(TOL * TOL);
+  const double scale2 = scale * scale;
+  if (p > 1) {
+    for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+      if (tid == 0) rotated = 0;
+      __syncthreads();
+      for (int round = 0; round < p2 - 1; ++round) {
+        for (int pi = tid; pi < npairs; pi += NT) {
+          int a, b;
+          rr_pair(pi, round, p, p2, &a, &b);
+          int act = 0;
+          double c = 1.0, sn = 0.0;
+          if (a >= 0) {
+            const double al = G[a + (long long)p * a], be = G[b + (long long)p * b], ga = G[a + (long long)p * b];
+            // test and angle in FP32 on Gram entries scaled by s^2 (|s M| <= 2): a threshold
+            // test and a steering angle need no more; only c is refined in FP64.  When a scaled
+            // entry leaves the FP32 normal range (tiny columns) both are taken in FP64, so a
+            // rotation is never flagged without moving anything.
+            const double als = al * scale2, bes = be * scale2, gas = ga * scale2;
+            const bool f32 = htg_in_f32_range(als) && htg_in_f32_range(bes) && htg_in_f32_range(gas);
+            bool big;
+            float zf = 0.0f;
+            if (f32) {
+              const float alf = htg_d2f(als), bef = htg_d2f(bes), gaf = htg_d2f(gas);
+              const float g2 = gaf * gaf, ab = TOL32G * alf * bef;
+              big = (g2 > 0.0f && ab > 0.0f) ? (g2 > ab) : (ga * ga > TOL * TOL * al * be);
+              zf = htg_d2f((be - al) * scale2) / (2.0f * gaf);
+            } else {
+              big = htg_dnz(ga) && (ga * ga > TOL * TOL * al * be);
+            }
+            if (htg_dnz(ga) && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) && big) {
+              double t;
+              if (f32) {
+                const float azf = fabsf(zf);
+                t = htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
+              } else {
+                const double zeta = (be - al) / (2.0 * ga);
+                const double az = fabs(zeta);
+                t = (az > 1e150) ? 0.5 / zeta : (zeta >= 0.0 ? 1.0 : -1.0) / (az + sqrt(fma(zeta, zeta, 1.0)));
+              }
+              c = htg_rsqrt_fast(fma(t, t, 1.0));
+              sn = c * t;
+              act = 1;
+              rotated = 1;
+              myflops += 12.0 * p;
+            }
+          }
+          sc_[pi] = c;
+          ss_[pi] = sn;
+          act_[pi] = act;
+        }
+        __syncthreads();
+        // rows a, b of G
+        for (int e = tid; e < npairs * p; e += NT) {
+          const int pi = e / p, k = e % p;
+          if (!act_[pi]) continue;
+          int a, b;
+          rr_pair(pi, round, p, p2, &a, &b);
+          const double c = sc_[pi], sn = ss_[pi];
+          const double x = G[a + (long long)p * k], y = G[b + (long long)p * k];
+          G[a + (long long)p * k] = c * x - sn * y;
+          G[b + (long long)p * k] = sn * x + c * y;
+        }
+        __syncthreads();
+        // columns a, b of G and of V
+        for (int e = tid; e < npairs * p; e += NT) {
+          const int pi = e / p, k = e % p;
+          if (!act_[pi]) continue;
+          int a, b;
+          rr_pair(pi, round, p, p2, &a, &b);
+          const double c = sc_[pi], sn = ss_[pi];
+          double x = G[k + (long long)p * a], y = G[k + (long long)p * b];
+          G[k + (long long)p * a] = c * x - sn * y;
+          G[k + (long long)p * b] = sn * x + c * y;
+          x = V[k + (long long)p * a];
+          y = V[k + (long long)p * b];
+          V[k + (long long)p * a] = c * x - sn * y;
+          V[k + (long long)p * b] = sn * x + c * y;
+        }
+        __syncthreads();
+      }
+      const int any = rotated;
+      __syncthreads();
+      if (!any) break;
+    }
+  }
+  // ---------------- phase 4: U S = M V, sorted by S
+  cta_gemm(N, M, mr, V, p, mr, p, p, false);
+  if (gl == 0 && gid == 0) myflops += 2.0 * mr * p * p;
+  __syncthreads();
   const int lane = tid & 31, wid = tid >> 5, nw = NT / 32;
-  double* nrm = V + (long long)p * p;   // p scratch values after V
   for (int c = wid; c < p; c += nw) {
-    const double* cc = M + (long long)mr * c;
+    const double* cc = N + (long long)mr * c;
     double s = 0.0;
     for (int i = lane; i < mr; i += 32) s = fma(cc[i], cc[i], s);
     s = warp_sum(s);
     if (lane == 0) nrm[c] = sqrt(s);
   }
   __syncthreads();
+  if (flops && myflops > 0.0) atomicAdd(flops, myflops);
   for (int c = wid; c < p; c += nw) {
     const double sc = nrm[c];
     int rank = 0;
     for (int o = 0; o < p; ++o) {
       const double so = nrm[o];
-      rank += (so > sc) || (so == sc && o < c);
+      rank += htg_dgt_nn(so, sc) || (__double_as_longlong(so) == __double_as_longlong(sc) && o < c);
     }
     if (lane == 0) D.sigma[rank] = sc;
     for (int i = lane; i < p; i += 32) D.V[i + (long long)p * rank] = V[i + (long long)p * c];
-    const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-    for (int i = lane; i < q; i += 32) D.U[i + (long long)q * rank] = M[i + (long long)mr * c] * inv;
+    const double inv = htg_dpos_finite(sc) ? 1.0 / sc : 0.0;
+    for (int i = lane; i < q; i += 32) D.U[i + (long long)q * rank] = N[i + (long long)mr * c] * inv;
   }
 }
 
@@ -166,7 +332,8 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
   if (ndesc <= 0) return cudaSuccess;
   (void)use_smem;
   const int mr = htg_max(pmax, qmax);
-  size_t smem = ((size_t)mr * pmax + (size_t)pmax * pmax + pmax) * sizeof(double);
+  const size_t mp = (size_t)mr * pmax, pp = (size_t)pmax * pmax;
+  size_t smem = (2 * mp + 3 * pp + pmax + (mp + 1) / 2 + (pp + 1) / 2 + 2) * sizeof(double);
   if (smem > HTG_SMEM_BYTES) smem = HTG_SMEM_BYTES;
   static bool attr[64] = {false};
   int dev = 0;
