@@ -649,15 +649,40 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) 
   return ok_sh != 0;
 }
 
+// Copy count doubles global -> shared with 8 independent loads in flight per thread (a plain
+// copy loop waits out the full L2 latency on every element).  Plain (coherent) loads: the
+// sources are written by other CTAs of the same launch before a grid barrier.
+__device__ void stage_copy(double* dst, const double* src, long long count) {
+  const int T = blockDim.x;
+  long long base = 0;
+  for (; base + 8LL * T <= count; base += 8LL * T) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = src[base + (long long)u * T + threadIdx.x];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) dst[base + (long long)u * T + threadIdx.x] = v[u];
+  }
+  for (long long e = base + threadIdx.x; e < count; e += T) dst[e] = src[e];
+}
+
 // column b of G_j (r values) and, when withM, of M_j (3 r0 values); X_j[:, b] staged in xs
-__device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool withM, double* xs) {
+__device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool withM, double* xs,
+                            double* stage = nullptr) {
   const int n = a.n[j], r = a.r;
   for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = a.X[j][i + (long long)n * b];
-  __syncthreads();
   const double* Zj = w.Z + (long long)j * w.nmax * 3 * w.rcap;
+  const double* Xsrc = a.X[j];
+  const double* Zsrc = Zj;
+  if (stage) {   // [X_j | Z_j] (n x (r + 3 r0)) in shared memory
+    stage_copy(stage, a.X[j], (long long)n * r);
+    if (withM) stage_copy(stage + (long long)n * r, Zj, (long long)n * 3 * r0);
+    Xsrc = stage;
+    Zsrc = stage + (long long)n * r;
+  }
+  __syncthreads();
   const int nout = r + (withM ? 3 * r0 : 0);
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const double* src = (o < r) ? a.X[j] + (long long)n * o : Zj + (long long)n * (o - r);
+    const double* src = (o < r) ? Xsrc + (long long)n * o : Zsrc + (long long)n * (o - r);
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     int i = 0;
     for (; i + 3 < n; i += 4) {
@@ -706,17 +731,30 @@ __device__ void normalise_column(const CpArgs& a, int b, bool fold, double* red)
   __syncthreads();
 }
 
+// one Newton step on an FP32 seed: relative error ~1e-13, ample for a Cholesky pivot
+__device__ inline double rsqrt_pivot(double x) {
+  if (!htg_in_f32_range(x) || !htg_dpos(x)) return rsqrt(x);
+  const double y = htg_f2d(rsqrtf(htg_d2f(x)));
+  const double h = x * y;
+  return fma(0.5 * y, fma(-h, y, 1.0), y);
+}
+
 __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
-                                                            int sweeps, int* err) {
+                                                            int sweeps, int* err, int zs_smem) {
   const int b = blockIdx.x, tid = threadIdx.x;
   const unsigned int nb = gridDim.x;
   const int d = a.d, r = a.r, r0 = pa.r0;
+  const int nmax = w.nmax;
   extern __shared__ double sh[];
-  double* Lm = sh;                    // r x r
-  double* hs = Lm + r * r;            // 3 r
-  double* rinv = hs + 3 * r;          // r
-  double* xs = rinv + r;              // nmax
-  double* ys = xs + w.nmax;           // nmax
+  double* Lm = sh;                         // r x r
+  double* hs = Lm + r * r;                 // 3 r
+  double* rinv = hs + 3 * r;               // r
+  double* xs = rinv + r;                   // nmax
+  double* ys = xs + nmax;                  // nmax
+  double* Mv = ys + nmax;                  // d x 3 x r   (M_j rows of this CTA's lp)
+  const int nt_ = 1 + 2 * d + d * (d - 1) / 2;
+  double* Xs = Mv + 3 * d * r;             // max(nmax, types) x r: a staged factor, or type products
+  double* Zs = Xs + (long long)htg_max(nmax, nt_) * r;   // nmax x 3 r0 (Z_k, when zs_smem)
   __shared__ unsigned char pw[153][MODE_MAXD];
   __shared__ double cf[153];
   __shared__ double red[HT_MAXD + 32];
@@ -725,13 +763,13 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   for (int e = tid; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
   for (int e = tid; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
   const bool gs = (a.variant == CP_ALS_GS);
-  // ---------------- 0a
+  // ---------------- 0a: powers of x_old (CTA b < r0), weights, normalisation of column b
   if (b < r0) {
     for (int k = 0; k < d; ++k) {
       const int n = pa.n[k], hw = pa.hw[k];
       for (int j = tid; j < n; j += blockDim.x) xs[j] = pa.X[k][j + (long long)n * b];
       __syncthreads();
-      double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
+      double* Zk = w.Z + (long long)k * nmax * 3 * w.rcap;
       for (int j = tid; j < n; j += blockDim.x) {
         double s = 0.0;
         for (int o = -hw; o <= hw; ++o) {
@@ -760,42 +798,54 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
     for (int i = tid; i < r0; i += blockDim.x) w.wold[i] = mu_src[i];
     for (int i = tid; i < sweeps && i < 64; i += blockDim.x) w.epsacc[i] = 0.0;
   }
-  // the iterate's column b may alias x_old: everything of x_old is read above, before the barrier
+  // the iterate may alias x_old: everything of x_old is read above, before the barrier
   if (!grid_barrier(w.bar, nb, err)) return;
   if (b < r) normalise_column(a, b, !gs, red);
   if (!grid_barrier(w.bar, nb, err)) return;
-  // ---------------- 0b
+  // ---------------- 0b: column b of G_j and M_j for every j
   if (b < r)
-    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs);
+    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, zs_smem ? Xs : nullptr);
   if (!grid_barrier(w.bar, nb, err)) return;
   const double* mu = w.wold;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int k = 0; k < d; ++k) {
-      // ---------------- A: Gamma_k, Cholesky, row b of W
-      if (b == 0 && tid == 0) { w.acc2[0] = 0.0; w.acc2[1] = 0.0; }
+      const bool record = !(sweep == 0 && k == 0);  // the previous mode's sums are complete
+      // ---------------- A: Gamma_k (Cholesky) and row lp = b of W = Hs Gamma_k^-1
       if (b < r0) {
         const int lp = b;
-        for (int l = tid; l < r; l += blockDim.x) {
-          double mv[MODE_MAXD][3];
-          for (int j = 0; j < d; ++j) {
-            if (j == k) continue;
-            const double* Mj = w.H + (long long)j * w.rycap * w.rcap + lp + (long long)3 * r0 * l;
-            mv[j][0] = Mj[0];
-            mv[j][1] = Mj[r0];
-            mv[j][2] = Mj[2 * r0];
-          }
-          double acc[3] = {0.0, 0.0, 0.0};
-          for (int ti = 0; ti < nt; ++ti) {
-            double v = cf[ti];
-            for (int j = 0; j < d; ++j)
-              if (j != k) v *= mv[j][pw[ti][j]];
-            acc[pw[ti][k]] += v;
-          }
-          const double m = mu[lp];
-          hs[l] = m * acc[0];
-          hs[r + l] = m * acc[1];
-          hs[2 * r + l] = m * acc[2];
+        if (b == 0 && tid == 0 && record) {
+          // record the previous mode's convergence measure (its sums are complete)
+          const double tn = w.acc2[0], td = w.acc2[1];
+          const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
+          const int sw = (k == 0) ? sweep - 1 : sweep;
+          if (htg_dgt_nn(ek, w.epsacc[sw])) w.epsacc[sw] = ek;
         }
+        // M_j operands of row lp (j != k), and the factor updated last, into shared memory
+        for (int e = tid; e < 3 * d * r; e += blockDim.x) {
+          const int j = e / (3 * r), rem = e % (3 * r), pp = rem / r, l = rem % r;
+          Mv[e] = (j == k) ? 0.0 : w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)3 * r0 * l];
+        }
+        __syncthreads();
+        if (b == 0 && tid == 0) { w.acc2[0] = 0.0; w.acc2[1] = 0.0; }
+        // hs_p[l] = mu_lp sum_{tau: p_tau(k) = p} c_tau prod_{j != k} M_j^(p_tau(j))[lp, l]:
+        // every (type, l) product by its own thread into Xs, then sums per (p, l) in type order
+        for (int e = tid; e < nt * r; e += blockDim.x) {
+          const int ti = e / r, l = e % r;
+          double v = cf[ti];
+          for (int j = 0; j < d; ++j)
+            if (j != k) v *= Mv[(j * 3 + pw[ti][j]) * r + l];
+          Xs[e] = v;
+        }
+        __syncthreads();
+        for (int e = tid; e < 3 * r; e += blockDim.x) {
+          const int pp = e / r, l = e % r;
+          double acc0 = 0.0;
+          for (int ti = 0; ti < nt; ++ti)
+            if (pw[ti][k] == pp) acc0 += Xs[ti * r + l];
+          hs[e] = mu[lp] * acc0;
+        }
+        __syncthreads();
+        // Gamma_k = hadamard_{j != k} G_j
         for (int e = tid; e < r * r; e += blockDim.x) {
           double v = 1.0;
           for (int j = 0; j < d; ++j)
@@ -805,40 +855,72 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         __syncthreads();
         for (int attempt = 0; attempt < 2; ++attempt) {
           if (attempt == 1) {
-            double tr = 0.0;
-            for (int i = 0; i < r; ++i) {
-              double v = 1.0;
-              for (int j = 0; j < d; ++j)
-                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
-              tr += v;
+            // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation
+            __shared__ double shift;
+            if (tid == 0) {
+              double tr = 0.0;
+              for (int i = 0; i < r; ++i) {
+                double v = 1.0;
+                for (int j = 0; j < d; ++j)
+                  if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
+                tr += v;
+              }
+              shift = 1e-14 * tr / r;
             }
-            const double shift = 1e-14 * tr / r;
+            __syncthreads();
             for (int e = tid; e < r * r; e += blockDim.x) {
               double v = 1.0;
               for (int j = 0; j < d; ++j)
                 if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
               Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
             }
+            // the forward solve below overwrote hs: rebuild it (products still in Xs)
+            for (int e = tid; e < 3 * r; e += blockDim.x) {
+              const int pp = e / r, l = e % r;
+              double acc0 = 0.0;
+              for (int ti = 0; ti < nt; ++ti)
+                if (pw[ti][k] == pp) acc0 += Xs[ti * r + l];
+              hs[e] = mu[lp] * acc0;
+            }
           }
-          if (tid == 0) ok = 1;
+          if (tid == 0) {
+            ok = 1;
+            const double d0 = Lm[0];
+            ok = htg_dpos_finite(d0);
+            rinv[0] = ok ? rsqrt_pivot(d0) : 1.0;
+          }
           __syncthreads();
-          for (int j = 0; j < r; ++j) {
-            if (tid == 0) {
-              const double dj = Lm[j + r * j];
-              if (!htg_dpos_finite(dj)) ok = 0;
-              const double ri = ok ? htg_rsqrt_fast(dj) : 1.0;
-              Lm[j + r * j] = ok ? dj * ri : 1.0;
-              rinv[j] = ri;
+          // right-looking Cholesky, forward substitution fused in: step j scales column j
+          // (L_ij = a_ij / L_jj) and y_j, then applies the rank-1 updates with one FMA each; the
+          // thread that finishes pivot j+1 computes its reciprocal root at once
+          for (int j = 0; j < r && ok; ++j) {
+            const double rj = rinv[j];
+            for (int e = tid; e < r - j; e += blockDim.x) {
+              if (e == 0) {
+                for (int pv = 0; pv < 3; ++pv) hs[pv * r + j] *= rj;
+                Lm[j + r * j] *= rj;       // d_j / sqrt(d_j)
+              } else {
+                Lm[j + e + r * j] *= rj;
+              }
             }
             __syncthreads();
-            if (!ok) break;
-            const double inv = rinv[j];
-            for (int i = j + 1 + tid; i < r; i += blockDim.x) Lm[i + r * j] *= inv;
-            __syncthreads();
             const int m = r - j - 1;
-            for (int e = tid; e < m * m; e += blockDim.x) {
-              const int i = j + 1 + e % m, cc = j + 1 + e / m;
-              if (cc <= i) Lm[i + r * cc] -= Lm[i + r * j] * Lm[cc + r * j];
+            for (int e = tid; e < m * m + 3 * m; e += blockDim.x) {
+              if (e < m * m) {
+                const int i = j + 1 + e % m, cc = j + 1 + e / m;
+                if (cc <= i) {
+                  const double v = fma(-Lm[i + r * j], Lm[cc + r * j], Lm[i + r * cc]);
+                  Lm[i + r * cc] = v;
+                  if (i == j + 1 && cc == j + 1) {
+                    const bool good = htg_dpos_finite(v);
+                    if (!good) ok = 0;
+                    rinv[j + 1] = good ? rsqrt_pivot(v) : 1.0;
+                  }
+                }
+              } else {
+                const int f = e - m * m, pv = f / m, i = j + 1 + f % m;
+                hs[pv * r + i] = fma(-Lm[i + r * j], hs[pv * r + j], hs[pv * r + i]);
+              }
             }
             __syncthreads();
           }
@@ -849,15 +931,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         if (!ok) {
           if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
         } else {
-          for (int j = 0; j < r; ++j) {
-            if (tid < 3) hs[tid * r + j] *= rinv[j];
-            __syncthreads();
-            for (int e = tid; e < 3 * (r - j - 1); e += blockDim.x) {
-              const int pv = e / (r - j - 1), i = j + 1 + e % (r - j - 1);
-              hs[pv * r + i] -= Lm[i + r * j] * hs[pv * r + j];
-            }
-            __syncthreads();
-          }
+          // back substitution L^T w = y (y already in hs, columns of L scaled)
           for (int j = r - 1; j >= 0; --j) {
             if (tid < 3) hs[tid * r + j] *= rinv[j];
             __syncthreads();
@@ -874,25 +948,32 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         }
       }
       if (!grid_barrier(w.bar, nb, err)) return;
-      // ---------------- B: column b of X~_k = Z_k W
+      // ---------------- B: column b of X~_k = Z_k W, X_k[:, b], lam_b, and M_k[:, b]
       if (b < r) {
         const int n = a.n[k];
-        const double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
-        const double* Wb = w.Hh + (long long)3 * r0 * b;
+        const int K = 3 * r0;
+        const double* Zg = w.Z + (long long)k * nmax * 3 * w.rcap;
+        const double* Zk = Zg;
+        if (zs_smem) {
+          stage_copy(Zs, Zg, (long long)n * K);
+          Zk = Zs;
+        }
+        const double* Wb = w.Hh + (long long)K * b;
+        for (int i = tid; i < K; i += blockDim.x) ys[i] = Wb[i];
+        __syncthreads();
         const double lam_old = a.lam[b];
         double* col = a.X[k] + (long long)n * b;
         double num = 0.0, den = 0.0, nrm2 = 0.0;
         for (int row = tid; row < n; row += blockDim.x) {
           double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
           int i = 0;
-          const int K = 3 * r0;
           for (; i + 3 < K; i += 4) {
-            s0 = fma(Zk[row + (long long)n * i], Wb[i], s0);
-            s1 = fma(Zk[row + (long long)n * (i + 1)], Wb[i + 1], s1);
-            s2 = fma(Zk[row + (long long)n * (i + 2)], Wb[i + 2], s2);
-            s3 = fma(Zk[row + (long long)n * (i + 3)], Wb[i + 3], s3);
+            s0 = fma(Zk[row + (long long)n * i], ys[i], s0);
+            s1 = fma(Zk[row + (long long)n * (i + 1)], ys[i + 1], s1);
+            s2 = fma(Zk[row + (long long)n * (i + 2)], ys[i + 2], s2);
+            s3 = fma(Zk[row + (long long)n * (i + 3)], ys[i + 3], s3);
           }
-          for (; i < K; ++i) s0 = fma(Zk[row + (long long)n * i], Wb[i], s0);
+          for (; i < K; ++i) s0 = fma(Zk[row + (long long)n * i], ys[i], s0);
           const double v = (s0 + s1) + (s2 + s3);
           xs[row] = v;
           const double old = col[row] * (gs ? lam_old : 1.0);
@@ -921,38 +1002,77 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         }
         __syncthreads();
         if (gs) {
-          for (int row = tid; row < n; row += blockDim.x) col[row] = xs[row] * scol;
+          for (int row = tid; row < n; row += blockDim.x) {
+            const double v = xs[row] * scol;
+            xs[row] = v;
+            col[row] = v;
+          }
+          __syncthreads();
+          // M_k[:, b] = Z_k^T X_k[:, b]
+          for (int o = tid; o < K; o += blockDim.x) {
+            const double* zc = Zk + (long long)n * o;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int q = 0;
+            for (; q + 3 < n; q += 4) {
+              s0 = fma(zc[q], xs[q], s0);
+              s1 = fma(zc[q + 1], xs[q + 1], s1);
+              s2 = fma(zc[q + 2], xs[q + 2], s2);
+              s3 = fma(zc[q + 3], xs[q + 3], s3);
+            }
+            for (; q < n; ++q) s0 = fma(zc[q], xs[q], s0);
+            w.H[(long long)k * w.rycap * w.rcap + o + (long long)K * b] = (s0 + s1) + (s2 + s3);
+          }
         } else {
-          double* dst = w.Xold + (long long)k * w.nmax * w.rcap + (long long)n * b;
+          double* dst = w.Xold + (long long)k * nmax * w.rcap + (long long)n * b;
           for (int row = tid; row < n; row += blockDim.x) dst[row] = xs[row];
         }
         __syncthreads();
       }
       if (!grid_barrier(w.bar, nb, err)) return;
-      // ---------------- C: refresh column b of G_k, M_k; record the mode's measure
-      if (gs && b < r) gram_column(a, w, k, b, r0, true, xs);
-      if (b == 0 && tid == 0) {
-        const double tn = w.acc2[0], td = w.acc2[1];
-        const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
-        if (htg_dgt_nn(ek, w.epsacc[sweep])) w.epsacc[sweep] = ek;
+      // ---------------- C: column b of G_k = X_k^T X_k (all columns of X_k are final)
+      if (gs && b < r) {
+        const int n = a.n[k];
+        stage_copy(Xs, a.X[k], (long long)n * r);
+        __syncthreads();
+        const double* xb = Xs + (long long)n * b;
+        for (int o = tid; o < r; o += blockDim.x) {
+          const double* xo = Xs + (long long)n * o;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int q = 0;
+          for (; q + 3 < n; q += 4) {
+            s0 = fma(xo[q], xb[q], s0);
+            s1 = fma(xo[q + 1], xb[q + 1], s1);
+            s2 = fma(xo[q + 2], xb[q + 2], s2);
+            s3 = fma(xo[q + 3], xb[q + 3], s3);
+          }
+          for (; q < n; ++q) s0 = fma(xo[q], xb[q], s0);
+          w.G[(long long)k * w.rcap * w.rcap + o + (long long)r * b] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
       }
-      if (!grid_barrier(w.bar, nb, err)) return;
+      if (gs && !grid_barrier(w.bar, nb, err)) return;
     }
     if (!gs) {
-      // damped Jacobi update of every factor column b, then refresh the Grams
+      // damped Jacobi update of every column b, then refresh all Grams
       if (b < r) {
         for (int k = 0; k < d; ++k) {
           const int n = a.n[k];
-          const double* src = w.Xold + (long long)k * w.nmax * w.rcap + (long long)n * b;
+          const double* src = w.Xold + (long long)k * nmax * w.rcap + (long long)n * b;
           double* col = a.X[k] + (long long)n * b;
           for (int row = tid; row < n; row += blockDim.x) col[row] += 0.25 * (src[row] - col[row]);
         }
       }
       if (!grid_barrier(w.bar, nb, err)) return;
       if (b < r)
-        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs);
+        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, zs_smem ? Xs : nullptr);
       if (!grid_barrier(w.bar, nb, err)) return;
     }
+  }
+  // the last mode's measure
+  if (b == 0 && tid == 0 && sweeps > 0) {
+    const double tn = w.acc2[0], td = w.acc2[1];
+    const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
+    if (htg_dgt_nn(ek, w.epsacc[sweeps - 1])) w.epsacc[sweeps - 1] = ek;
   }
   if (!gs && b < r) normalise_column(a, b, false, red);
 }
@@ -1114,7 +1234,12 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   (void)nmax;
   // one cooperative launch: CTA b owns factor column b (and row b of the solve)
   const int nblk = htg_max(a.r, r0);
-  const size_t smem = ((size_t)a.r * a.r + 4 * (size_t)a.r + 2 * (size_t)w->nmax) * sizeof(double);
+  const size_t rr = (size_t)a.r, nm = (size_t)w->nmax;
+  const size_t ntypes = (size_t)htg_cp_terms(d);
+  size_t smem = (rr * rr + 4 * rr + 2 * nm + 3 * (size_t)d * rr + (nm > ntypes ? nm : ntypes) * rr) * sizeof(double);
+  const size_t zbytes = nm * 3 * (size_t)r0 * sizeof(double);
+  const int zs_smem = (smem + zbytes <= 160 * 1024) ? 1 : 0;   // stage Z_k in shared memory when it fits
+  if (zs_smem) smem += zbytes;
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(cp_als_rk2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HT_ERR_CUDA;
@@ -1133,7 +1258,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_persistent, a, pa, *w, (const double*)x_old->weight, sweeps,
-                                      htg_ctx_err(c));
+                                      htg_ctx_err(c), zs_smem);
   htg_prof_end(c, KC_CPSOLVE, s);
   ++launches;
   if (e0 != cudaSuccess || e1 != cudaSuccess) {
