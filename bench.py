@@ -283,11 +283,7 @@ def run_gpu(args):
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     W.ctx.check()
-    t = torch.tensor([ms], dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t[0])
-    value = world * args.steps / (ms_max * 1e-3)
+    ms_max, value = aggregate_replicas(ms, args.steps)
 
     # ---- roofline: per-kernel-class CUDA-event time on the launching stream over a second
     #      timed region (same steps, L2 flushed, no graph so each launch can be bracketed)
@@ -316,6 +312,19 @@ def run_gpu(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def aggregate_replicas(ms_local: float, steps: int):
+    """Replicas (one independent copy of the workload per rank, no data-path collective):
+    the job time is the slowest rank's, the throughput counts every rank's steps."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([ms_local], dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t[0])
+    return ms_max, world * steps / (ms_max * 1e-3)
 
 
 def load_traffic() -> dict:

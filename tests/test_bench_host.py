@@ -1,0 +1,65 @@
+"""Host-side logic of bench.py on CPU: replica aggregation over gloo ranks and the reference
+arm's rank gating (no GPU involved)."""
+import os
+import socket
+import sys
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms_max, value = bench.aggregate_replicas(100.0 * (rank + 1), steps=50)
+    q.put((rank, ms_max, value))
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms_max, value in res:
+        assert ms_max == 200.0                      # the slowest rank sets the job time
+        assert abs(value - 2 * 50 / 0.2) < 1e-9      # every rank's steps count
+
+
+def test_single_process_aggregation():
+    sys.path.insert(0, ROOT)
+    import bench
+    ms, v = bench.aggregate_replicas(250.0, steps=10)
+    assert ms == 250.0 and abs(v - 40.0) < 1e-12
+
+
+def test_reference_arm_only_rank0_works(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0))
+    assert capsys.readouterr().out == ""

@@ -1,0 +1,129 @@
+"""GPU parity at the shapes of the other configurations and at edge cases (FP64 form)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ht as OH
+from oracle.problems import advection_A
+from oracle.tree import build_tree
+from paper_1803_10270_gb300.inputs import advection_case, cp_random_factors
+from tests.helpers import min_gap, random_ht, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1803_10270_gb300 import build as B
+    B.build()
+    from paper_1803_10270_gb300 import htgpu
+    htgpu.load()
+    return htgpu
+
+
+def sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def to_gpu(G, u, cap):
+    t = G.HTTensor(u.tree.d, u.n, cap)
+    t.upload(u.node)
+    return t
+
+
+def from_gpu(t, tree):
+    return OH.HT(tree, list(t.n), t.download())
+
+
+def test_twelve_dim_depth4_tree_steps(G):
+    """12-D advection (the shape of the 12-D configuration: depth-4 tree, separable rank-3
+    initial condition), n = 6, r_max 6, 3 RK2 steps against the oracle."""
+    d, n = 12, 6
+    case = advection_case(d, n, n_terms=3, cfg_index=4)
+    A = advection_A(case)
+    tree = build_tree(d)
+    assert max(tree.depth) == 4
+    u = OH.from_cp(np.ones(3), case.ic_factors())
+    ctx = G.Context(d, [n] * d, cap=6, max_terms=1)
+    g = to_gpu(G, u, 6)
+    op = G.advection_op(case.c, case.h)
+    for step in range(3):
+        u, rep = OH.step_rk2_poly(u, A, 1e-6, 6)
+        G.ht_step(ctx, g, op, case.dt, 1e-6, 6)
+        sync()
+        ctx.check()
+        assert g.ranks() == rep.ranks, f"step {step}"
+        assert rel_err(from_gpu(g, u.tree), u) < TOL64
+
+
+def test_two_dim_steps_and_rank_cap_one(G):
+    d, n = 2, 24
+    case = advection_case(d, n, seed=3)
+    A = advection_A(case)
+    u = random_ht(d, n, 4, seed=2, scale_decay=0.3)
+    for rmax in (1, 4):
+        uo = u
+        ctx = G.Context(d, [n] * d, cap=4, max_terms=1)
+        g = to_gpu(G, u, 4)
+        op = G.advection_op(case.c, case.h)
+        for step in range(3):
+            uo, rep = OH.step_rk2_poly(uo, A, 1e-9, rmax)
+            G.ht_step(ctx, g, op, case.dt, 1e-9, rmax)
+            sync()
+            assert g.ranks() == rep.ranks
+            assert rel_err(from_gpu(g, uo.tree), uo) < TOL64
+
+
+def test_zero_tensor_and_zero_tolerance(G):
+    import torch
+    d, n = 4, 5
+    z = random_ht(d, n, 2, seed=4)
+    for t in z.node:
+        z.node[t] = np.zeros_like(z.node[t])
+    ctx = G.Context(d, [n] * d, cap=6, max_terms=1)
+    g = to_gpu(G, z, 6)
+    out = G.HTTensor(d, [n] * d, 6)
+    G.ht_truncate(ctx, g, 1e-8, 6, out)
+    sync()
+    ctx.check()
+    assert out.ranks()[1:] == [1] * (2 * d - 2)
+    assert all(np.abs(a).max() == 0.0 for a in out.download().values())
+    # tol 0 keeps every nonzero direction up to the cap
+    u = random_ht(d, n, 3, seed=5, scale_decay=0.5)
+    ref, rep = OH.truncate(u, 0.0, 6)
+    g2 = to_gpu(G, u, 6)
+    G.ht_truncate(ctx, g2, 0.0, 6, out)
+    sync()
+    assert out.ranks() == rep.ranks
+    assert rel_err(from_gpu(out, u.tree), ref) < TOL64
+    assert rel_err(ref, u) < 1e-12        # nothing was cut
+
+
+def test_config2_full_size_mass_bound(G):
+    """n=64, d=6 (64^6 grid points): the apply conserves the discrete mass exactly, the HSVD
+    changes it by at most sqrt(N) |v - T(v)| <= sqrt(N) tol |v|; checked over 5 steps."""
+    import torch
+    case = advection_case(6, 64, cfg_index=1)
+    u = OH.from_cp(np.ones(2), case.ic_factors())
+    ctx = G.Context(6, [64] * 6, cap=32, max_terms=1)
+    g = to_gpu(G, u, 32)
+    op = G.advection_op(case.c, case.h)
+    m = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G.ht_mass(ctx, g, m)
+    sync()
+    m0 = float(m[0])
+    assert abs(m0 - OH.mass(u)) < 1e-12 * abs(m0)
+    nrm = OH.norm(u)
+    for _ in range(5):
+        G.ht_step(ctx, g, op, case.dt, 1e-8, 32)
+        G.ht_mass(ctx, g, m)
+        sync()
+        m1 = float(m[0])
+        assert abs(m1 - m0) <= math.sqrt(64.0 ** 6) * 1e-8 * nrm * 1.01
+        m0 = m1
