@@ -40,7 +40,7 @@ D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel", "qr": "qr_r_kernel",
                 "svd": "svd_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
-                "cp_small": "cp_hadamard_rk2_kernel/cp_normalize_kernel/...", "cp_solve": "cp_solve_kernel"}
+                "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...", "cp_solve": "cp_als_rk2_persistent"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

@@ -47,7 +47,8 @@ extern "C" {
 
 #define HT_MAXD 16
 #define HT_MAXNODES (2 * HT_MAXD - 1)
-#define HT_MAXTERMS 8
+#define HT_MAXTERMS 16   /* a Kronecker-sum operator has one term per dimension */
+#define HT_MAXBLOCKTERMS 8   /* terms of a general (block-diagonal) application */
 #define HT_MAXSTENCIL 9
 
 typedef enum ht_status {
@@ -105,7 +106,8 @@ typedef struct ht_factor {
  * rank-3k form of the RK2 polynomial p(dt L) = 1 + dt L + dt^2 L^2 / 2. */
 typedef struct ht_op {
   int d;
-  int n_terms;                             /* 1 <= n_terms <= HT_MAXTERMS */
+  int n_terms;                             /* 1 <= n_terms <= HT_MAXTERMS; the general (block-
+                                              diagonal) forms take at most HT_MAXBLOCKTERMS */
   int kron_sum;
   double alpha[HT_MAXTERMS];
   ht_factor f[HT_MAXTERMS][HT_MAXD];

@@ -321,6 +321,8 @@ __global__ void cp_plan_kernel(CpArgs a, CpWs w) {
 //   RHS = sum_p Z_k^(p) Hs_p,  Hs_p = sum_{tau : p_tau(k) = p} c_tau diag(mu) hadamard_{j!=k} M_j^(p_tau(j))
 // with the column types tau of cp_apply_rk2.  Same result as cp_als_sweep on the formed y.
 // ---------------------------------------------------------------------------
+constexpr int MODE_MAXD = 16;   // largest d of the structured ALS (unrolled Gram loads)
+
 struct PowArgs {
   int d, r0;
   int n[HT_MAXD];
@@ -329,290 +331,16 @@ struct PowArgs {
   const double* X[HT_MAXD];
 };
 
-__global__ void cp_powers_kernel(PowArgs a, CpWs w) {
-  extern __shared__ double sh[];
-  const int k = blockIdx.y, l = blockIdx.x;
-  const int n = a.n[k];
-  double* x = sh;
-  double* ax = sh + n;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = a.X[k][j + (long long)n * l];
-  __syncthreads();
-  double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;   // n x 3 r0, ld n
-  const int hw = a.hw[k];
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double s = 0.0;
-    for (int o = -hw; o <= hw; ++o) {
-      int jj = (j + o) % n;
-      if (jj < 0) jj += n;
-      s = fma(a.c[k][o + hw], x[jj], s);
-    }
-    ax[j] = s;
-    Zk[j + (long long)n * l] = x[j];
-    Zk[j + (long long)n * (a.r0 + l)] = s;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double s = 0.0;
-    for (int o = -hw; o <= hw; ++o) {
-      int jj = (j + o) % n;
-      if (jj < 0) jj += n;
-      s = fma(a.c[k][o + hw], ax[jj], s);
-    }
-    Zk[j + (long long)n * (2 * a.r0 + l)] = s;
-  }
-}
-
-// Gamma = hadamard_{j!=k} G_j ; Hs (3 r0 x r) as above.  M_j lives in w.H (3 r0 x r, ld 3 r0).
-__global__ void cp_hadamard_rk2_kernel(CpArgs a, CpWs w, int k, int r0, const double* mu) {
-  const int d = a.d, r = a.r;
-  const long long nh = (long long)r0 * r, ng = (long long)r * r;
-  const int nt = 1 + 2 * d + d * (d - 1) / 2;
-  // type table: power of A_j in column type tau (<= 1 + 2*16 + 120 types, d <= 16)
-  __shared__ unsigned char pw[153][HT_MAXD];
-  __shared__ double cf[153];
-  for (int e = threadIdx.x; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
-  for (int e = threadIdx.x; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nh + ng;
-       e += (long long)gridDim.x * blockDim.x) {
-    if (e < nh) {
-      const int lp = (int)(e % r0), l = (int)(e / r0);
-      const double* Hb = w.H + (lp + (long long)3 * r0 * l);
-      double hs[3] = {0.0, 0.0, 0.0};
-      for (int ti = 0; ti < nt; ++ti) {
-        double v = cf[ti];
-        for (int j = 0; j < d; ++j) {
-          if (j == k) continue;
-          v *= Hb[(long long)j * w.rycap * w.rcap + pw[ti][j] * r0];
-        }
-        hs[pw[ti][k]] += v;
-      }
-      const double m = mu[lp];
-      for (int pp = 0; pp < 3; ++pp) w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = m * hs[pp];
-    } else {
-      const long long g = e - nh;
-      double v = 1.0;
-      for (int j = 0; j < d; ++j)
-        if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + g];
-      w.Gam[g] = v;
-    }
-  }
-}
-
-// Mode update of the structured ALS, part 1 (one CTA per row index lp of the r0 x r block):
-//   hs_p[l] = mu_lp sum_{tau: p_tau(k) = p} c_tau prod_{j != k} M_j^(p_tau(j))[lp, l]   (p = 0,1,2)
-//   Gamma = hadamard_{j != k} G_j, Gamma = L L^T (FP64 Cholesky, shifted only on failure)
-//   W[p r0 + lp, :] = hs_p Gamma^{-1}    (forward and back substitution)
-// Then X~_k = Z_k W (a GEMM over all SMs) equals RHS Gamma^{-1} of the normal equations.
-// The M_j operands of a thread are loaded into registers before any product (an L2 latency
-// chain otherwise), and each CTA repeats the small Cholesky so no grid-wide sync is needed.
-constexpr int MODE_MAXR = 64;
-constexpr int MODE_MAXD = 16;
-
-__global__ void cp_mode_prep_kernel(CpArgs a, CpWs w, int k, int r0, const double* mu, int* err) {
-  extern __shared__ double sh[];
-  const int d = a.d, r = a.r, lp = blockIdx.x, tid = threadIdx.x;
-  double* Lm = sh;              // r x r
-  double* hs = Lm + r * r;      // 3 x r
-  double* rinv = hs + 3 * r;    // r
-  __shared__ unsigned char pw[153][MODE_MAXD];
-  __shared__ double cf[153];
-  __shared__ int ok;
-  const int nt = 1 + 2 * d + d * (d - 1) / 2;
-  for (int e = tid; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
-  for (int e = tid; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
-  __syncthreads();
-  // hs: thread per column l, operands in registers
-  for (int l = tid; l < r; l += blockDim.x) {
-    double mv[MODE_MAXD][3];
-    for (int j = 0; j < d; ++j) {
-      if (j == k) continue;
-      const double* Mj = w.H + (long long)j * w.rycap * w.rcap + lp + (long long)3 * r0 * l;
-      mv[j][0] = Mj[0];
-      mv[j][1] = Mj[r0];
-      mv[j][2] = Mj[2 * r0];
-    }
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int ti = 0; ti < nt; ++ti) {
-      double v = cf[ti];
-      for (int j = 0; j < d; ++j)
-        if (j != k) v *= mv[j][pw[ti][j]];
-      acc[pw[ti][k]] += v;
-    }
-    const double m = mu[lp];
-    hs[l] = m * acc[0];
-    hs[r + l] = m * acc[1];
-    hs[2 * r + l] = m * acc[2];
-  }
-  // Gamma
-  for (int e = tid; e < r * r; e += blockDim.x) {
-    double v = 1.0;
-    for (int j = 0; j < d; ++j)
-      if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
-    Lm[e] = v;
-  }
-  __syncthreads();
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (attempt == 1) {
-      double tr = 0.0;
-      for (int i = 0; i < r; ++i) {
-        double v = 1.0;
-        for (int j = 0; j < d; ++j)
-          if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
-        tr += v;
-      }
-      const double shift = 1e-14 * tr / r;
-      for (int e = tid; e < r * r; e += blockDim.x) {
-        double v = 1.0;
-        for (int j = 0; j < d; ++j)
-          if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
-        Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
-      }
-    }
-    if (tid == 0) ok = 1;
-    __syncthreads();
-    for (int j = 0; j < r; ++j) {
-      if (tid == 0) {
-        const double dj = Lm[j + r * j];
-        if (!htg_dpos_finite(dj)) ok = 0;
-        const double ri = ok ? htg_rsqrt_fast(dj) : 1.0;
-        Lm[j + r * j] = ok ? dj * ri : 1.0;
-        rinv[j] = ri;
-      }
-      __syncthreads();
-      if (!ok) break;
-      const double inv = rinv[j];
-      for (int i = j + 1 + tid; i < r; i += blockDim.x) Lm[i + r * j] *= inv;
-      __syncthreads();
-      const int m = r - j - 1;
-      for (int e = tid; e < m * m; e += blockDim.x) {
-        const int i = j + 1 + e % m, cc = j + 1 + e / m;
-        if (cc <= i) Lm[i + r * cc] -= Lm[i + r * j] * Lm[cc + r * j];
-      }
-      __syncthreads();
-    }
-    const int good = ok;
-    __syncthreads();
-    if (good) break;
-  }
-  if (!ok) {
-    if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
-    return;
-  }
-  // L L^T w = hs_p for the three vectors, column oriented (short dependency chains):
-  // forward  v_j <- v_j / L_jj, then v_i -= L_ij v_j (i > j);
-  // backward v_j <- v_j / L_jj, then v_i -= L_ji v_j (i < j)
-  for (int j = 0; j < r; ++j) {
-    if (tid < 3) hs[tid * r + j] *= rinv[j];
-    __syncthreads();
-    for (int e = tid; e < 3 * (r - j - 1); e += blockDim.x) {
-      const int pv = e / (r - j - 1), i = j + 1 + e % (r - j - 1);
-      hs[pv * r + i] -= Lm[i + r * j] * hs[pv * r + j];
-    }
-    __syncthreads();
-  }
-  for (int j = r - 1; j >= 0; --j) {
-    if (tid < 3) hs[tid * r + j] *= rinv[j];
-    __syncthreads();
-    for (int e = tid; e < 3 * j; e += blockDim.x) {
-      const int pv = e / j, i = e % j;
-      hs[pv * r + i] -= Lm[j + r * i] * hs[pv * r + j];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < 3 * r; e += blockDim.x) {
-    const int pp = e / r, l = e % r;
-    w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = hs[e];
-  }
-}
-
-// Part 3: convergence measure, column norms, X_k (GS) or the Jacobi slot.  X~ is in w.RHS.
-__global__ void cp_mode_finish_kernel(CpArgs a, CpWs w, int k, int sweep, double* flops) {
-  const int r = a.r, n = a.n[k], tid = threadIdx.x;
-  __shared__ double rinv[MODE_MAXR];
-  __shared__ double red_num[NT / 32], red_den[NT / 32];
-  double num = 0.0, den = 0.0;
-  for (long long e = tid; e < (long long)n * r; e += blockDim.x) {
-    const int l = (int)(e / n);
-    const double old = a.X[k][e] * (a.variant == CP_ALS_GS ? a.lam[l] : 1.0);
-    const double df = w.RHS[e] - old;
-    num = fma(df, df, num);
-    den = fma(old, old, den);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    num += __shfl_xor_sync(0xffffffffu, num, o);
-    den += __shfl_xor_sync(0xffffffffu, den, o);
-  }
-  if ((tid & 31) == 0) { red_num[tid >> 5] = num; red_den[tid >> 5] = den; }
-  __syncthreads();
-  for (int l = tid >> 5; l < r; l += blockDim.x >> 5) {
-    double s2 = 0.0;
-    for (int j = tid & 31; j < n; j += 32) s2 = fma(w.RHS[j + (long long)n * l], w.RHS[j + (long long)n * l], s2);
-    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    if ((tid & 31) == 0) {
-      const double nr = sqrt(s2);
-      if (a.variant == CP_ALS_GS) a.lam[l] = nr;
-      rinv[l] = htg_dpos_finite(nr) ? htg_rcp_fast(nr) : 1.0;
-    }
-  }
-  if (tid == 0) {
-    double tn = 0.0, td = 0.0;
-    for (int q = 0; q < NT / 32; ++q) { tn += red_num[q]; td += red_den[q]; }
-    const double ek = td > 0.0 ? sqrt(tn / td) : sqrt(tn);
-    if (ek > w.epsacc[sweep]) w.epsacc[sweep] = ek;
-    if (flops) atomicAdd(flops, 8.0 * n * r);
-  }
-  __syncthreads();
-  if (a.variant == CP_ALS_GS) {
-    for (long long e = tid; e < (long long)n * r; e += blockDim.x) a.X[k][e] = w.RHS[e] * rinv[e / n];
-  } else {
-    double* dst = w.Xold + (long long)k * w.nmax * w.rcap;
-    for (long long e = tid; e < (long long)n * r; e += blockDim.x) dst[e] = w.RHS[e];
-  }
-}
-
-// descriptors per mode k: [RHS_k = Z_k (n x 3r0) Hs (3r0 x r), G_k = X_k^T X_k, M_k = Z_k^T X_k]
-__global__ void cp_plan_rk2_kernel(CpArgs a, CpWs w, int r0) {
-  if (threadIdx.x != 0) return;
-  for (int k = 0; k < a.d; ++k) {
-    GemmDesc* g = w.descs + 3 * k;
-    const int n = a.n[k];
-    const double* Zk = w.Z + (long long)k * w.nmax * 3 * w.rcap;
-    for (int q = 0; q < 3; ++q) {
-      g[q].colscale = nullptr;
-      g[q].sA = g[q].sB = g[q].sC = 0;
-      g[q].batch = 1;
-      g[q].alpha = 1.0;
-      g[q].beta = 0.0;
-    }
-    g[0].A = Zk; g[0].lda = n; g[0].tA = 0;
-    g[0].B = w.Hh; g[0].ldb = 3 * r0; g[0].tB = 0;
-    g[0].C = w.RHS; g[0].ldc = n;
-    g[0].m = n; g[0].n = a.r; g[0].k = 3 * r0;
-    g[1].A = a.X[k]; g[1].lda = n; g[1].tA = 1;
-    g[1].B = a.X[k]; g[1].ldb = n; g[1].tB = 0;
-    g[1].C = w.G + (long long)k * w.rcap * w.rcap; g[1].ldc = a.r;
-    g[1].m = a.r; g[1].n = a.r; g[1].k = n;
-    g[2].A = Zk; g[2].lda = n; g[2].tA = 1;
-    g[2].B = a.X[k]; g[2].ldb = n; g[2].tB = 0;
-    g[2].C = w.H + (long long)k * w.rycap * w.rcap; g[2].ldc = 3 * r0;
-    g[2].m = 3 * r0; g[2].n = a.r; g[2].k = n;
-  }
-}
-
-__global__ void cp_copy_weights_kernel(const double* src, double* dst, int r) {
-  for (int i = threadIdx.x; i < r; i += blockDim.x) dst[i] = src[i];
-}
-
 // ---------------------------------------------------------------------------
 // Persistent form of cp_als_sweep_rk2: one cooperative launch runs every sweep.  CTA b owns
 // factor column b (row b of the r0 x r blocks in the solve phase); phases are separated by
 // a grid barrier:
 //   0a  powers Z_j^(p) of x_old (CTA b < r0), mu <- weights of x_old, normalise column b of x
 //   0b  column b of G_j = X_j^T X_j and M_j = Z_j^T X_j for every j
-//   per mode k:  A  Gamma_k (Cholesky) and row b of W = Hs Gamma_k^-1      (CTA b < r0)
-//                B  column b of X~_k = Z_k W, convergence sums, X_k[:, b] and lam_b
-//                C  column b of G_k and M_k; CTA 0 records the mode's convergence measure
+//   per mode k:  A  Gamma_k (LDL^T) and row b of W = Hs Gamma_k^-1; CTA 0 records the
+//                   previous mode's convergence measure                      (CTA b < r0)
+//                B  column b of X~_k = Z_k W, convergence sums, X_k[:, b], lam_b and M_k[:, b]
+//                C  column b of G_k
 // The launch is cooperative (all CTAs resident), and every barrier wait is bounded: past the
 // limit the kernel records HT_ERR_TIMEOUT in the error word and returns.
 // ---------------------------------------------------------------------------
@@ -649,54 +377,118 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) 
   return ok_sh != 0;
 }
 
-// Copy count doubles global -> shared with 8 independent loads in flight per thread (a plain
-// copy loop waits out the full L2 latency on every element).  Plain (coherent) loads: the
-// sources are written by other CTAs of the same launch before a grid barrier.
-__device__ void stage_copy(double* dst, const double* src, long long count) {
-  const int T = blockDim.x;
-  long long base = 0;
-  for (; base + 8LL * T <= count; base += 8LL * T) {
+// Odd leading dimension for a staged n-row matrix: lanes that walk its columns (stride ld)
+// then hit distinct shared-memory banks with their 8-byte words.
+__device__ inline int odd_ld(int n) { return n | 1; }
+
+// Copy an n x cols column-major matrix (leading dimension lds) to dst (leading dimension ldd),
+// 8 independent loads in flight per thread (a plain copy loop waits out the full L2 latency on
+// every element).  Plain (coherent) loads: the sources are written by other CTAs of the same
+// launch before a grid barrier.
+__device__ void stage_pad(double* dst, int ldd, const double* src, int lds, int n, int cols) {
+  const unsigned int total = (unsigned int)n * (unsigned int)cols, un = (unsigned int)n;
+  const unsigned int T = blockDim.x;
+  unsigned int base = 0;
+  for (; base + 8u * T <= total; base += 8u * T) {
     double v[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = src[base + (long long)u * T + threadIdx.x];
+    for (int u = 0; u < 8; ++u) {
+      const unsigned int e = base + u * T + threadIdx.x;
+      v[u] = src[(e % un) + (long long)lds * (e / un)];
+    }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) dst[base + (long long)u * T + threadIdx.x] = v[u];
+    for (int u = 0; u < 8; ++u) {
+      const unsigned int e = base + u * T + threadIdx.x;
+      dst[(e % un) + (long long)ldd * (e / un)] = v[u];
+    }
   }
-  for (long long e = base + threadIdx.x; e < count; e += T) dst[e] = src[e];
+  for (unsigned int e = base + threadIdx.x; e < total; e += T)
+    dst[(e % un) + (long long)ldd * (e / un)] = src[(e % un) + (long long)lds * (e / un)];
 }
 
-// column b of G_j (r values) and, when withM, of M_j (3 r0 values); X_j[:, b] staged in xs
-__device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool withM, double* xs,
-                            double* stage = nullptr) {
-  const int n = a.n[j], r = a.r;
+// Parts per output of a split dot product: as many as fill the CTA, at most 8.
+__device__ inline int dot_parts(int nout) { return (nout <= NT) ? htg_max(1, htg_min(NT / htg_max(nout, 1), 8)) : 1; }
+
+// out_o = col(o) . x (length n) for o < nout: consecutive lanes take consecutive outputs, each
+// output is split into P chunks whose partial sums (pb, nout * P <= max(NT, nout) values) are
+// added in chunk order; store(o, value) receives the result.  Two CTA barriers.
+template <class Col, class Store>
+__device__ void cols_dot(Col col, const double* x, int n, int nout, double* pb, Store store) {
+  const int P = dot_parts(nout);
+  const int chunk = (n + P - 1) / P;
+  for (int e = threadIdx.x; e < nout * P; e += NT) {
+    const int o = e % nout, part = e / nout;
+    const int q0 = part * chunk, q1 = htg_min(n, q0 + chunk);
+    const double* src = col(o);
+    double s0 = 0.0, s1 = 0.0;
+    int q = q0;
+    for (; q + 1 < q1; q += 2) {
+      s0 = fma(src[q], x[q], s0);
+      s1 = fma(src[q + 1], x[q + 1], s1);
+    }
+    if (q < q1) s0 = fma(src[q], x[q], s0);
+    pb[e] = s0 + s1;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nout; o += NT) {
+    double v = pb[o];
+    for (int part = 1; part < P; ++part) v += pb[o + nout * part];
+    store(o, v);
+  }
+  __syncthreads();
+}
+
+// out[row] = sum_i S[row + ld i] y[i] for row < n, i < m: consecutive lanes take consecutive
+// rows, P chunks of the m terms per row, partial sums added in chunk order.  Two CTA barriers.
+__device__ void rows_dot(const double* S, int ld, const double* y, int n, int m, double* pb, double* out) {
+  const int P = dot_parts(n);
+  const int chunk = (m + P - 1) / P;
+  for (int e = threadIdx.x; e < n * P; e += NT) {
+    const int row = e % n, part = e / n;
+    const int i0 = part * chunk, i1 = htg_min(m, i0 + chunk);
+    double s0 = 0.0, s1 = 0.0;
+    int i = i0;
+    for (; i + 1 < i1; i += 2) {
+      s0 = fma(S[row + (long long)ld * i], y[i], s0);
+      s1 = fma(S[row + (long long)ld * (i + 1)], y[i + 1], s1);
+    }
+    if (i < i1) s0 = fma(S[row + (long long)ld * i], y[i], s0);
+    pb[e] = s0 + s1;
+  }
+  __syncthreads();
+  for (int row = threadIdx.x; row < n; row += NT) {
+    double v = pb[row];
+    for (int part = 1; part < P; ++part) v += pb[row + n * part];
+    out[row] = v;
+  }
+  __syncthreads();
+}
+
+// column b of G_j (r values) and, when withM, of M_j (3 r0 values); X_j[:, b] staged in xs.
+// With stage, [X_j | Z_j] is copied to shared memory with an odd leading dimension first.
+__device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool withM, double* xs, double* pb,
+                            double* stage) {
+  const int n = a.n[j], r = a.r, K = 3 * r0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = a.X[j][i + (long long)n * b];
   const double* Zj = w.Z + (long long)j * w.nmax * 3 * w.rcap;
   const double* Xsrc = a.X[j];
   const double* Zsrc = Zj;
-  if (stage) {   // [X_j | Z_j] (n x (r + 3 r0)) in shared memory
-    stage_copy(stage, a.X[j], (long long)n * r);
-    if (withM) stage_copy(stage + (long long)n * r, Zj, (long long)n * 3 * r0);
+  int ld = n;
+  if (stage) {
+    ld = odd_ld(n);
+    stage_pad(stage, ld, a.X[j], n, n, r);
+    if (withM) stage_pad(stage + (long long)ld * r, ld, Zj, n, n, K);
     Xsrc = stage;
-    Zsrc = stage + (long long)n * r;
+    Zsrc = stage + (long long)ld * r;
   }
   __syncthreads();
-  const int nout = r + (withM ? 3 * r0 : 0);
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const double* src = (o < r) ? Xsrc + (long long)n * o : Zsrc + (long long)n * (o - r);
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int i = 0;
-    for (; i + 3 < n; i += 4) {
-      s0 = fma(src[i], xs[i], s0);
-      s1 = fma(src[i + 1], xs[i + 1], s1);
-      s2 = fma(src[i + 2], xs[i + 2], s2);
-      s3 = fma(src[i + 3], xs[i + 3], s3);
-    }
-    for (; i < n; ++i) s0 = fma(src[i], xs[i], s0);
-    const double v = (s0 + s1) + (s2 + s3);
-    if (o < r) w.G[(long long)j * w.rcap * w.rcap + o + (long long)r * b] = v;
-    else w.H[(long long)j * w.rycap * w.rcap + (o - r) + (long long)3 * r0 * b] = v;
-  }
-  __syncthreads();
+  double* Gc = w.G + (long long)j * w.rcap * w.rcap + (long long)r * b;
+  double* Hc = w.H + (long long)j * w.rycap * w.rcap + (long long)K * b;
+  cols_dot([&](int o) { return (o < r) ? Xsrc + (long long)ld * o : Zsrc + (long long)ld * (o - r); }, xs, n,
+           r + (withM ? K : 0), pb, [&](int o, double v) {
+             if (o < r) Gc[o] = v;
+             else Hc[o - r] = v;
+           });
 }
 
 // unit columns across all dimensions for column b (norms into lam_b, or folded into X_0 when fold)
@@ -731,37 +523,140 @@ __device__ void normalise_column(const CpArgs& a, int b, bool fold, double* red)
   __syncthreads();
 }
 
-// one Newton step on an FP32 seed: relative error ~1e-13, ample for a Cholesky pivot
-__device__ inline double rsqrt_pivot(double x) {
-  if (!htg_in_f32_range(x) || !htg_dpos(x)) return rsqrt(x);
-  const double y = htg_f2d(rsqrtf(htg_d2f(x)));
-  const double h = x * y;
-  return fma(0.5 * y, fma(-h, y, 1.0), y);
+// Right-hand sides of row lp for mode k, one per power p of A_k, from the products
+// m_p,j = M_j^(p)[lp, l] staged in Mv.  The column types of y = p(dt L) x_old are the monomials
+// of p(z_1 + ... + z_d), p(z) = 1 + z + z^2 / 2, each with coefficient 1 / alpha!; grouped by
+// the power of z_k they read p(z_k + s) = (1 + s + s^2/2) + z_k (1 + s) + z_k^2 / 2 with
+// s = sum_{j != k} z_j.  The truncated product f(e) = prod_{j != k} (m_0,j + m_1,j e + m_2,j e^2 / 2)
+// mod e^3 = f0 + f1 e + f2 e^2 holds the degree sums, so
+//   hs_0 = mu (f0 + f1 + f2),   hs_1 = mu (f0 + f1),   hs_2 = mu f0 / 2.
+__device__ void rk2_rhs_row(const double* Mv, int d, int k, int r, double mu, double* hs) {
+  for (int l = threadIdx.x; l < r; l += blockDim.x) {
+    double f0 = 1.0, f1 = 0.0, f2 = 0.0;
+    for (int j = 0; j < d; ++j) {
+      if (j == k) continue;
+      const double m0 = Mv[(j * 3) * r + l], m1 = Mv[(j * 3 + 1) * r + l];
+      const double m2h = 0.5 * Mv[(j * 3 + 2) * r + l];
+      f2 = fma(f2, m0, fma(f1, m1, f0 * m2h));
+      f1 = fma(f1, m0, f0 * m1);
+      f0 *= m0;
+    }
+    hs[l] = mu * ((f0 + f1) + f2);
+    hs[r + l] = mu * (f0 + f1);
+    hs[2 * r + l] = 0.5 * mu * f0;
+  }
+}
+
+constexpr int TRI_MAX = 64 * 65 / 2;   // lower-triangle pairs of the largest rank (64)
+
+// offset of column c in the column-ordered lower-triangle pair list of an r x r matrix
+__device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 2; }
+
+// LDL^T factorisation (D diagonal, L unit lower) of the SPD r x r matrix in Lm (column-major,
+// lower part) with the unit-lower forward solve of the three right-hand sides in hs fused in.
+// Right-looking, one CTA barrier per pivot: step j applies a_ic -= (a_ij / d_j) a_cj to the
+// trailing lower triangle (pairs from tri, i >= c > j) and z_i -= (a_ij / d_j) z_j to the
+// right-hand sides; the thread that updates a_{j+1,j+1} (the first pair of the step) forms
+// 1/d_{j+1} at once.  Column j keeps a_ij = L_ij d_j.  A pivot that is not positive and finite
+// leaves dinv = 0 there; every thread sees it after the barrier and the result is false.
+__device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigned short* tri, int r) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    const double d0 = Lm[0];
+    dinv[0] = htg_dpos_finite(d0) ? htg_rcp_fast(d0) : 0.0;
+  }
+  __syncthreads();
+  const int T = r * (r + 1) / 2;
+  for (int j = 0; j < r; ++j) {
+    const double dj = dinv[j];
+    if (!htg_dnz(dj)) return false;   // uniform: written before the last barrier
+    const int m = r - 1 - j;
+    const int s0 = tri_offset(j + 1, r);
+    const int ntri = T - s0;
+    const int nall = ntri + 3 * m;
+    for (int e = tid; e < nall; e += NT) {
+      if (e < ntri) {
+        const unsigned int pr = tri[s0 + e];
+        const int i = pr & 0xff, c = pr >> 8;
+        const double v = fma(-(Lm[i + r * j] * dj), Lm[c + r * j], Lm[i + r * c]);
+        Lm[i + r * c] = v;
+        if (e == 0) dinv[j + 1] = htg_dpos_finite(v) ? htg_rcp_fast(v) : 0.0;
+      } else {
+        const int f = e - ntri, p = f / m, i = j + 1 + f % m;
+        hs[p * r + i] = fma(-(Lm[i + r * j] * dj), hs[p * r + j], hs[p * r + i]);
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// Back substitution D L^T w = z for the three right-hand sides (z in hs, overwritten by w):
+// w_i = (z_i - sum_{c > i} a_ci w_c) / d_i.  For r <= 32 warp p takes side p with lane i holding
+// z_i and the scaled column a_ci / d_c (c > i) in registers: no CTA barrier inside.
+__device__ void ldlt_back(const double* Lm, double* hs, const double* dinv, int r) {
+  const int tid = threadIdx.x;
+  if (r <= 32) {
+    const int wp = tid >> 5, lane = tid & 31;
+    if (wp < 3) {
+      double s = (lane < r) ? hs[wp * r + lane] : 0.0;
+      double col[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) col[c] = (c < r && lane < c) ? Lm[c + r * lane] * dinv[c] : 0.0;
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < r) {
+          const double uc = __shfl_sync(0xffffffffu, s, c);
+          if (lane < c) s = fma(-col[c], uc, s);
+        }
+      }
+      if (lane < r) hs[wp * r + lane] = s * dinv[lane];
+    }
+    __syncthreads();
+    return;
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    if (tid < 3) hs[tid * r + j] *= dinv[j];
+    __syncthreads();
+    for (int e = tid; e < 3 * j; e += NT) {
+      const int p = e / j, i = e % j;
+      hs[p * r + i] = fma(-Lm[j + r * i], hs[p * r + j], hs[p * r + i]);
+    }
+    __syncthreads();
+  }
+}
+
+// Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage is optional.
+__host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z) {
+  const long long ld = nmax | 1, K = 3LL * r0;
+  const long long base = (long long)r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
+                         (nmax > NT ? nmax : NT) + ld * r;
+  return base + (with_z ? ld * K : 0);
 }
 
 __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
-                                                            int sweeps, int* err, int zs_smem) {
+                                                            int sweeps, int* err, int zs_smem, double* flops) {
   const int b = blockIdx.x, tid = threadIdx.x;
   const unsigned int nb = gridDim.x;
-  const int d = a.d, r = a.r, r0 = pa.r0;
+  const int d = a.d, r = a.r, r0 = pa.r0, K = 3 * r0;
   const int nmax = w.nmax;
   extern __shared__ double sh[];
-  double* Lm = sh;                         // r x r
-  double* hs = Lm + r * r;                 // 3 r
-  double* rinv = hs + 3 * r;               // r
-  double* xs = rinv + r;                   // nmax
-  double* ys = xs + nmax;                  // nmax
-  double* Mv = ys + nmax;                  // d x 3 x r   (M_j rows of this CTA's lp)
-  const int nt_ = 1 + 2 * d + d * (d - 1) / 2;
-  double* Xs = Mv + 3 * d * r;             // max(nmax, types) x r: a staged factor, or type products
-  double* Zs = Xs + (long long)htg_max(nmax, nt_) * r;   // nmax x 3 r0 (Z_k, when zs_smem)
-  __shared__ unsigned char pw[153][MODE_MAXD];
-  __shared__ double cf[153];
+  double* Lm = sh;                           // r x r: Gamma_k, then its LDL^T factor
+  double* hs = Lm + r * r;                   // 3 r: right-hand sides, then row lp of W
+  double* dinv = hs + 3 * r;                 // r: reciprocal pivots
+  double* xs = dinv + r;                     // nmax
+  double* ys = xs + nmax;                    // max(nmax, 3 r0)
+  double* Mv = ys + htg_max(nmax, K);        // d x 3 x r: M_j^(p) rows of this CTA's lp
+  double* pb = Mv + 3 * d * r;               // max(NT, nmax): partial sums of split dot products
+  double* Xs = pb + htg_max(NT, nmax);       // odd_ld(nmax) x r: a staged factor
+  double* Zs = Xs + (long long)odd_ld(nmax) * r;   // odd_ld(nmax) x 3 r0: Z_k (when zs_smem)
+  __shared__ unsigned short tri[TRI_MAX];
   __shared__ double red[HT_MAXD + 32];
-  __shared__ int ok;
-  const int nt = 1 + 2 * d + d * (d - 1) / 2;
-  for (int e = tid; e < nt * d; e += blockDim.x) pw[e / d][e % d] = (unsigned char)type_power(e / d, d, e % d);
-  for (int e = tid; e < nt; e += blockDim.x) cf[e] = (e > d && e <= 2 * d) ? 0.5 : 1.0;
+  // lower-triangle pairs (i, c), i >= c, ordered by column then row
+  for (int c = tid; c < r; c += blockDim.x) {
+    const int o = tri_offset(c, r);
+    for (int i = c; i < r; ++i) tri[o + i - c] = (unsigned short)(i | (c << 8));
+  }
   const bool gs = (a.variant == CP_ALS_GS);
   // ---------------- 0a: powers of x_old (CTA b < r0), weights, normalisation of column b
   if (b < r0) {
@@ -804,13 +699,13 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   if (!grid_barrier(w.bar, nb, err)) return;
   // ---------------- 0b: column b of G_j and M_j for every j
   if (b < r)
-    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, zs_smem ? Xs : nullptr);
+    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
   if (!grid_barrier(w.bar, nb, err)) return;
   const double* mu = w.wold;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int k = 0; k < d; ++k) {
       const bool record = !(sweep == 0 && k == 0);  // the previous mode's sums are complete
-      // ---------------- A: Gamma_k (Cholesky) and row lp = b of W = Hs Gamma_k^-1
+      // ---------------- A: Gamma_k (LDL^T) and row lp = b of W = Hs Gamma_k^-1
       if (b < r0) {
         const int lp = b;
         if (b == 0 && tid == 0 && record) {
@@ -819,163 +714,89 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
           const int sw = (k == 0) ? sweep - 1 : sweep;
           if (htg_dgt_nn(ek, w.epsacc[sw])) w.epsacc[sw] = ek;
+          w.acc2[0] = 0.0;
+          w.acc2[1] = 0.0;
+        } else if (b == 0 && tid == 0) {
+          w.acc2[0] = 0.0;
+          w.acc2[1] = 0.0;
         }
-        // M_j operands of row lp (j != k), and the factor updated last, into shared memory
+        // M_j operands of row lp (j != k) into shared memory
         for (int e = tid; e < 3 * d * r; e += blockDim.x) {
           const int j = e / (3 * r), rem = e % (3 * r), pp = rem / r, l = rem % r;
-          Mv[e] = (j == k) ? 0.0 : w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)3 * r0 * l];
+          Mv[e] = (j == k) ? 0.0 : w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)K * l];
         }
-        __syncthreads();
-        if (b == 0 && tid == 0) { w.acc2[0] = 0.0; w.acc2[1] = 0.0; }
-        // hs_p[l] = mu_lp sum_{tau: p_tau(k) = p} c_tau prod_{j != k} M_j^(p_tau(j))[lp, l]:
-        // every (type, l) product by its own thread into Xs, then sums per (p, l) in type order
-        for (int e = tid; e < nt * r; e += blockDim.x) {
-          const int ti = e / r, l = e % r;
-          double v = cf[ti];
-          for (int j = 0; j < d; ++j)
-            if (j != k) v *= Mv[(j * 3 + pw[ti][j]) * r + l];
-          Xs[e] = v;
-        }
-        __syncthreads();
-        for (int e = tid; e < 3 * r; e += blockDim.x) {
-          const int pp = e / r, l = e % r;
-          double acc0 = 0.0;
-          for (int ti = 0; ti < nt; ++ti)
-            if (pw[ti][k] == pp) acc0 += Xs[ti * r + l];
-          hs[e] = mu[lp] * acc0;
-        }
-        __syncthreads();
-        // Gamma_k = hadamard_{j != k} G_j
+        // Gamma_k = hadamard_{j != k} G_j (all loads of an entry issued before the products)
         for (int e = tid; e < r * r; e += blockDim.x) {
+          double g[MODE_MAXD];
+#pragma unroll
+          for (int j = 0; j < MODE_MAXD; ++j)
+            g[j] = (j < d && j != k) ? w.G[(long long)j * w.rcap * w.rcap + e] : 1.0;
           double v = 1.0;
-          for (int j = 0; j < d; ++j)
-            if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+#pragma unroll
+          for (int j = 0; j < MODE_MAXD; ++j)
+            if (j < d && j != k) v *= g[j];
           Lm[e] = v;
         }
         __syncthreads();
-        for (int attempt = 0; attempt < 2; ++attempt) {
-          if (attempt == 1) {
-            // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation
-            __shared__ double shift;
-            if (tid == 0) {
-              double tr = 0.0;
-              for (int i = 0; i < r; ++i) {
-                double v = 1.0;
-                for (int j = 0; j < d; ++j)
-                  if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
-                tr += v;
-              }
-              shift = 1e-14 * tr / r;
-            }
-            __syncthreads();
-            for (int e = tid; e < r * r; e += blockDim.x) {
+        rk2_rhs_row(Mv, d, k, r, mu[lp], hs);
+        __syncthreads();
+        bool ok = ldlt_forward(Lm, hs, dinv, tri, r);
+        if (!ok) {
+          // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation (Section 2.1
+          // regularisation of ill-conditioned ALS systems), and start over
+          __shared__ double shift;
+          if (tid == 0) {
+            double tr = 0.0;
+            for (int i = 0; i < r; ++i) {
               double v = 1.0;
               for (int j = 0; j < d; ++j)
-                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
-              Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
+                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
+              tr += v;
             }
-            // the forward solve below overwrote hs: rebuild it (products still in Xs)
-            for (int e = tid; e < 3 * r; e += blockDim.x) {
-              const int pp = e / r, l = e % r;
-              double acc0 = 0.0;
-              for (int ti = 0; ti < nt; ++ti)
-                if (pw[ti][k] == pp) acc0 += Xs[ti * r + l];
-              hs[e] = mu[lp] * acc0;
-            }
-          }
-          if (tid == 0) {
-            ok = 1;
-            const double d0 = Lm[0];
-            ok = htg_dpos_finite(d0);
-            rinv[0] = ok ? rsqrt_pivot(d0) : 1.0;
+            shift = 1e-14 * tr / r;
           }
           __syncthreads();
-          // right-looking Cholesky, forward substitution fused in: step j scales column j
-          // (L_ij = a_ij / L_jj) and y_j, then applies the rank-1 updates with one FMA each; the
-          // thread that finishes pivot j+1 computes its reciprocal root at once
-          for (int j = 0; j < r && ok; ++j) {
-            const double rj = rinv[j];
-            for (int e = tid; e < r - j; e += blockDim.x) {
-              if (e == 0) {
-                for (int pv = 0; pv < 3; ++pv) hs[pv * r + j] *= rj;
-                Lm[j + r * j] *= rj;       // d_j / sqrt(d_j)
-              } else {
-                Lm[j + e + r * j] *= rj;
-              }
-            }
-            __syncthreads();
-            const int m = r - j - 1;
-            for (int e = tid; e < m * m + 3 * m; e += blockDim.x) {
-              if (e < m * m) {
-                const int i = j + 1 + e % m, cc = j + 1 + e / m;
-                if (cc <= i) {
-                  const double v = fma(-Lm[i + r * j], Lm[cc + r * j], Lm[i + r * cc]);
-                  Lm[i + r * cc] = v;
-                  if (i == j + 1 && cc == j + 1) {
-                    const bool good = htg_dpos_finite(v);
-                    if (!good) ok = 0;
-                    rinv[j + 1] = good ? rsqrt_pivot(v) : 1.0;
-                  }
-                }
-              } else {
-                const int f = e - m * m, pv = f / m, i = j + 1 + f % m;
-                hs[pv * r + i] = fma(-Lm[i + r * j], hs[pv * r + j], hs[pv * r + i]);
-              }
-            }
-            __syncthreads();
+          for (int e = tid; e < r * r; e += blockDim.x) {
+            double v = 1.0;
+            for (int j = 0; j < d; ++j)
+              if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+            Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
           }
-          const int good = ok;
+          rk2_rhs_row(Mv, d, k, r, mu[lp], hs);
           __syncthreads();
-          if (good) break;
+          ok = ldlt_forward(Lm, hs, dinv, tri, r);
         }
         if (!ok) {
           if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
         } else {
-          // back substitution L^T w = y (y already in hs, columns of L scaled)
-          for (int j = r - 1; j >= 0; --j) {
-            if (tid < 3) hs[tid * r + j] *= rinv[j];
-            __syncthreads();
-            for (int e = tid; e < 3 * j; e += blockDim.x) {
-              const int pv = e / j, i = e % j;
-              hs[pv * r + i] -= Lm[j + r * i] * hs[pv * r + j];
-            }
-            __syncthreads();
-          }
+          ldlt_back(Lm, hs, dinv, r);
         }
         for (int e = tid; e < 3 * r; e += blockDim.x) {
           const int pp = e / r, l = e % r;
-          w.Hh[(pp * r0 + lp) + (long long)3 * r0 * l] = hs[e];
+          w.Hh[(pp * r0 + lp) + (long long)K * l] = hs[e];
         }
       }
       if (!grid_barrier(w.bar, nb, err)) return;
       // ---------------- B: column b of X~_k = Z_k W, X_k[:, b], lam_b, and M_k[:, b]
       if (b < r) {
         const int n = a.n[k];
-        const int K = 3 * r0;
         const double* Zg = w.Z + (long long)k * nmax * 3 * w.rcap;
         const double* Zk = Zg;
+        int ldz = n;
         if (zs_smem) {
-          stage_copy(Zs, Zg, (long long)n * K);
+          ldz = odd_ld(n);
+          stage_pad(Zs, ldz, Zg, n, n, K);
           Zk = Zs;
         }
         const double* Wb = w.Hh + (long long)K * b;
         for (int i = tid; i < K; i += blockDim.x) ys[i] = Wb[i];
         __syncthreads();
+        rows_dot(Zk, ldz, ys, n, K, pb, xs);
         const double lam_old = a.lam[b];
         double* col = a.X[k] + (long long)n * b;
         double num = 0.0, den = 0.0, nrm2 = 0.0;
         for (int row = tid; row < n; row += blockDim.x) {
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          int i = 0;
-          for (; i + 3 < K; i += 4) {
-            s0 = fma(Zk[row + (long long)n * i], ys[i], s0);
-            s1 = fma(Zk[row + (long long)n * (i + 1)], ys[i + 1], s1);
-            s2 = fma(Zk[row + (long long)n * (i + 2)], ys[i + 2], s2);
-            s3 = fma(Zk[row + (long long)n * (i + 3)], ys[i + 3], s3);
-          }
-          for (; i < K; ++i) s0 = fma(Zk[row + (long long)n * i], ys[i], s0);
-          const double v = (s0 + s1) + (s2 + s3);
-          xs[row] = v;
+          const double v = xs[row];
           const double old = col[row] * (gs ? lam_old : 1.0);
           const double df = v - old;
           num = fma(df, df, num);
@@ -1009,46 +830,25 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           }
           __syncthreads();
           // M_k[:, b] = Z_k^T X_k[:, b]
-          for (int o = tid; o < K; o += blockDim.x) {
-            const double* zc = Zk + (long long)n * o;
-            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int q = 0;
-            for (; q + 3 < n; q += 4) {
-              s0 = fma(zc[q], xs[q], s0);
-              s1 = fma(zc[q + 1], xs[q + 1], s1);
-              s2 = fma(zc[q + 2], xs[q + 2], s2);
-              s3 = fma(zc[q + 3], xs[q + 3], s3);
-            }
-            for (; q < n; ++q) s0 = fma(zc[q], xs[q], s0);
-            w.H[(long long)k * w.rycap * w.rcap + o + (long long)K * b] = (s0 + s1) + (s2 + s3);
-          }
+          double* Hc = w.H + (long long)k * w.rycap * w.rcap + (long long)K * b;
+          cols_dot([&](int o) { return Zk + (long long)ldz * o; }, xs, n, K, pb,
+                   [&](int o, double v) { Hc[o] = v; });
         } else {
           double* dst = w.Xold + (long long)k * nmax * w.rcap + (long long)n * b;
           for (int row = tid; row < n; row += blockDim.x) dst[row] = xs[row];
+          __syncthreads();
         }
-        __syncthreads();
       }
       if (!grid_barrier(w.bar, nb, err)) return;
       // ---------------- C: column b of G_k = X_k^T X_k (all columns of X_k are final)
       if (gs && b < r) {
         const int n = a.n[k];
-        stage_copy(Xs, a.X[k], (long long)n * r);
+        const int ld = odd_ld(n);
+        stage_pad(Xs, ld, a.X[k], n, n, r);
         __syncthreads();
-        const double* xb = Xs + (long long)n * b;
-        for (int o = tid; o < r; o += blockDim.x) {
-          const double* xo = Xs + (long long)n * o;
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          int q = 0;
-          for (; q + 3 < n; q += 4) {
-            s0 = fma(xo[q], xb[q], s0);
-            s1 = fma(xo[q + 1], xb[q + 1], s1);
-            s2 = fma(xo[q + 2], xb[q + 2], s2);
-            s3 = fma(xo[q + 3], xb[q + 3], s3);
-          }
-          for (; q < n; ++q) s0 = fma(xo[q], xb[q], s0);
-          w.G[(long long)k * w.rcap * w.rcap + o + (long long)r * b] = (s0 + s1) + (s2 + s3);
-        }
-        __syncthreads();
+        const double* xb = Xs + (long long)ld * b;
+        double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
+        cols_dot([&](int o) { return Xs + (long long)ld * o; }, xb, n, r, pb, [&](int o, double v) { Gc[o] = v; });
       }
       if (gs && !grid_barrier(w.bar, nb, err)) return;
     }
@@ -1064,9 +864,21 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
       }
       if (!grid_barrier(w.bar, nb, err)) return;
       if (b < r)
-        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, zs_smem ? Xs : nullptr);
+        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
       if (!grid_barrier(w.bar, nb, err)) return;
     }
+  }
+  if (flops && b == 0 && tid == 0) {
+    // FP64 work of the structured algorithm per mode (each item once): Gram of the new factor
+    // 2 n r^2, Z_k W and M_k 2 x 2 n (3 r0) r, right-hand sides 10 (d-1) r0 r, Gamma (d-2) r^2,
+    // LDL^T r^3 / 3, forward and back substitution for 3 r0 vectors 6 r0 r^2
+    double f = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double n = a.n[k], rr = r, q0 = r0;
+      f += 2.0 * n * rr * rr + 12.0 * n * q0 * rr + 10.0 * (d - 1) * q0 * rr + (d - 2) * rr * rr +
+           rr * rr * rr / 3.0 + 6.0 * q0 * rr * rr;
+    }
+    atomicAdd(flops, f * sweeps);
   }
   // the last mode's measure
   if (b == 0 && tid == 0 && sweeps > 0) {
@@ -1234,12 +1046,11 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   (void)nmax;
   // one cooperative launch: CTA b owns factor column b (and row b of the solve)
   const int nblk = htg_max(a.r, r0);
-  const size_t rr = (size_t)a.r, nm = (size_t)w->nmax;
-  const size_t ntypes = (size_t)htg_cp_terms(d);
-  size_t smem = (rr * rr + 4 * rr + 2 * nm + 3 * (size_t)d * rr + (nm > ntypes ? nm : ntypes) * rr) * sizeof(double);
-  const size_t zbytes = nm * 3 * (size_t)r0 * sizeof(double);
-  const int zs_smem = (smem + zbytes <= 160 * 1024) ? 1 : 0;   // stage Z_k in shared memory when it fits
-  if (zs_smem) smem += zbytes;
+  const size_t nm = (size_t)w->nmax;
+  // stage Z_k in shared memory when it fits
+  const size_t with_z = (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, true) * sizeof(double);
+  const int zs_smem = (with_z <= 160 * 1024) ? 1 : 0;
+  const size_t smem = zs_smem ? with_z : (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, false) * sizeof(double);
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(cp_als_rk2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HT_ERR_CUDA;
@@ -1258,7 +1069,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_persistent, a, pa, *w, (const double*)x_old->weight, sweeps,
-                                      htg_ctx_err(c), zs_smem);
+                                      htg_ctx_err(c), zs_smem, htg_prof_flops(c, KC_CPSOLVE));
   htg_prof_end(c, KC_CPSOLVE, s);
   ++launches;
   if (e0 != cudaSuccess || e1 != cudaSuccess) {

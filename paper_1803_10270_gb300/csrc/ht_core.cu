@@ -365,7 +365,7 @@ struct ApplyFactor {   // one 1-D factor as the apply kernel sees it
   const double* v;
   const double* w;
 };
-constexpr int MAXBLK = HT_MAXTERMS + 2;
+constexpr int MAXBLK = HT_MAXBLOCKTERMS + 2;   // identity + terms (+ the stage block of HEUN2)
 // Block-diagonal assembly: block b of the result is F_b applied to source tensor src[b]
 // (0 or 1) with root weight coef[b].  RK2POLY instead uses the binomial block pattern of
 // a single source with factor f[0][dim] = dt * L_dim.
@@ -968,6 +968,7 @@ static bool build_apply(const ht_ctx* c, const ht_op* L, double dt, int mode, Ap
     op->nb = 3;
     return true;
   }
+  if (L->n_terms > HT_MAXBLOCKTERMS) return false;
   int b = 0;
   ht_factor ident;
   memset(&ident, 0, sizeof(ident));

@@ -17,7 +17,8 @@ import numpy as np
 
 HT_MAXD = 16
 HT_MAXNODES = 2 * HT_MAXD - 1
-HT_MAXTERMS = 8
+HT_MAXTERMS = 16
+HT_MAXBLOCKTERMS = 8
 HT_MAXSTENCIL = 9
 
 HT_OK, HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA, HT_ERR_NONFINITE, HT_ERR_TIMEOUT, HT_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
@@ -159,7 +160,7 @@ def tree_info(d: int) -> TreeInfo:
 class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
-    def __init__(self, d: int, n, cap: int, max_terms: int = HT_MAXTERMS - 2, precision: int = HT_PREC_FP64,
+    def __init__(self, d: int, n, cap: int, max_terms: int = HT_MAXBLOCKTERMS - 2, precision: int = HT_PREC_FP64,
                  device: int = 0):
         lib = load()
         cfg = ht_config()
