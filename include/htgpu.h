@@ -194,6 +194,32 @@ typedef enum ht_scheme {
 int ht_step(ht_ctx* ctx, ht_tensor* u, const ht_op* L, double dt, double rel_tol, int rmax,
             int scheme, void* stream);
 
+/* ---------------------------------------------------------- batched steps -- */
+/* Many independent instances of the explicit step (Section 3.2, one per instance), each with
+ * its own context (grid sizes, rank capacity and workspace may differ) and its own tensor, all
+ * with the same d and so the same dimension tree.  Every launch of a batched step covers all
+ * instances: the planner, each level's QRs and contractions, the node SVDs, the rank choice and
+ * the projections run once per step for the whole batch (instance = a grid dimension), so the
+ * per-instance results are those of ht_step on that instance.
+ *
+ * ht_batch_create binds count contexts and tensors (caller-owned, distinct, same d and device;
+ * us[i] must fit ctxs[i] as for ht_step).  A bound context's device plan lives in the batch
+ * until ht_batch_destroy; the context may still be used alone in between, but not concurrently
+ * with a batched step.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_NOMEM, HT_ERR_CUDA. */
+typedef struct ht_batch ht_batch;
+int ht_batch_create(ht_batch** out, int count, ht_ctx* const* ctxs, ht_tensor* const* us);
+void ht_batch_destroy(ht_batch* b);
+
+/* One step of every bound instance in place: u_i <- step(u_i; Ls[i], dts[i], rel_tols[i],
+ * rmaxs[i]) with the scheme of ht_step (HT_SCHEME_RK2POLY or HT_SCHEME_HEUN2).  Operators and
+ * scalars are copied to the device only when they differ from the previous call's (the first
+ * call always copies; the copy is ordered on the stream); a call that needs such a copy while
+ * the stream is being captured returns HT_ERR_ARG, so make one call before capturing a graph.
+ * Device errors of instance i are reported by ht_ctx_check(ctxs[i]).  Errors: HT_ERR_ARG,
+ * HT_ERR_CAPACITY, HT_ERR_CUDA. */
+int ht_batch_step(ht_batch* b, const ht_op* const* Ls, const double* dts, const double* rel_tols,
+                  const int* rmaxs, int scheme, void* stream);
+
 /* Exact HT form of a CP tensor (footnote to eq. HTD: a CP tensor is the diagonal case):
  * leaves = factors, interior B = delta_abc, root = diag(weights).  out->cap >= x->rank. */
 int ht_from_cp(ht_ctx* ctx, const cp_tensor* x, ht_tensor* out, void* stream);

@@ -69,10 +69,14 @@ struct SvdDesc {
 // ------------------------------------------------------------ launchers -----
 // All launchers return cudaGetLastError() of their launch.
 // flops (device double, or nullptr): the kernels add the FP64 flops they execute.
-cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr);
-cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops = nullptr);
+// Batched form (count > 1): instance i (blockIdx.y) reads its ndesc descriptors at
+// descs_dev + i * inst_stride bytes.
+cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr,
+                            int count = 1, long long inst_stride = 0);
+cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops = nullptr, int count = 1,
+                          long long inst_stride = 0);
 cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
-                           cudaStream_t s, double* flops = nullptr);
+                           cudaStream_t s, double* flops = nullptr, int count = 1, long long inst_stride = 0);
 
 // ------------------------------------------------------------ helpers -------
 __host__ __device__ inline int htg_min(int a, int b) { return a < b ? a : b; }

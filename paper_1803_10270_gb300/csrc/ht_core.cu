@@ -112,6 +112,22 @@ struct HtView {           // a tensor as the kernels see it
   int n[HT_MAXD];
 };
 
+struct ApplyOp;
+
+// One instance of a batched step as the batched kernels see it (device array, one entry per
+// instance): its plan, workspace nodes, views and operators.
+enum { VIEW_U = 0, VIEW_APP = 1, VIEW_STAGE = 2, NVIEW = 3 };
+struct Inst {
+  Plan* P;
+  const WsNode* wn;
+  HtView view[NVIEW];      // the caller's tensor, the applied-tensor area, the HEUN2 stage area
+  const ApplyOp* op[2];    // RK2POLY or EULER operator; HEUN2 second-stage operator
+  int* err;
+  int cap_in;              // capacity of the truncation input (the applied-tensor area)
+  int rmax;
+  double rel_tol;
+};
+
 }  // namespace
 
 struct ht_ctx {
@@ -144,6 +160,7 @@ struct ht_ctx {
   int svd_smem = 0;
   int gemm_grid = 0;
   cudaStream_t last_stream = nullptr;
+  ht_batch* batch = nullptr;   // the batch this context is bound to, if any
 };
 
 namespace {
@@ -160,9 +177,9 @@ __device__ void fill_gemm(GemmDesc& g, const double* A, int lda, int tA, const d
   g.alpha = 1.0; g.beta = 0.0;
 }
 
-__global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const WsNode* wn, int cap_in,
-                                int* err) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const HtView& in, const WsNode* wn,
+                              int cap_in, int* err) {
+  if (threadIdx.x != 0) return;
   // device-resident ranks are validated against the input capacity: out-of-range ranks are
   // clamped (every later access stays inside the buffers) and reported as HT_ERR_CAPACITY
   bool bad = false;
@@ -253,10 +270,19 @@ __global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const 
   }
 }
 
+__global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const WsNode* wn, int cap_in, int* err) {
+  plan_pre_body(P, T, L, in, wn, cap_in, err);
+}
+
+__global__ void plan_pre_batch_kernel(const Inst* I, TreeInfo T, Levels L, int in_sel) {
+  const Inst& x = I[blockIdx.x];
+  plan_pre_body(x.P, T, L, x.view[in_sel], x.wn, x.cap_in, x.err);
+}
+
 // Rank selection (one CTA) + projection descriptors.
-__global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtView out,
-                                   const WsNode* wn, double rel_tol, int rmax, double* sigma_out,
-                                   int sig_stride, double* norm_out, int* err) {
+__device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, const HtView& in, const HtView& out,
+                                 const WsNode* wn, double rel_tol, int rmax, double* sigma_out, int sig_stride,
+                                 double* norm_out, int* err) {
   __shared__ double s_thr2;
   const int ra = T.c1[0], rb = T.c2[0];
   if (threadIdx.x == 0) {
@@ -358,6 +384,17 @@ __global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtV
   }
 }
 
+__global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtView out, const WsNode* wn,
+                                   double rel_tol, int rmax, double* sigma_out, int sig_stride, double* norm_out,
+                                   int* err) {
+  rank_select_body(P, T, L, in, out, wn, rel_tol, rmax, sigma_out, sig_stride, norm_out, err);
+}
+
+__global__ void rank_select_batch_kernel(const Inst* I, TreeInfo T, Levels L, int in_sel, int out_sel) {
+  const Inst& x = I[blockIdx.x];
+  rank_select_body(x.P, T, L, x.view[in_sel], x.view[out_sel], x.wn, x.rel_tol, x.rmax, nullptr, 0, nullptr, x.err);
+}
+
 // ------------------------------------------------------------ apply kernels ---
 struct ApplyFactor {   // one 1-D factor as the apply kernel sees it
   int kind, hw;
@@ -399,7 +436,8 @@ __device__ double apply_factor_at(const ApplyFactor& F, const double* x, int n, 
 // Leaves: for each leaf (blockIdx.y), every input column (blockIdx.x-strided) of every block
 // is loaded to shared memory and the block's 1-D factor is applied to it.
 // RK2POLY: [U, A U, A^2 U] with A = dt * L_i.
-__global__ void apply_leaf_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+__device__ void apply_leaf_body(const ApplyOp& op, const TreeInfo& T, const Levels& L, const HtView& in0,
+                                const HtView& in1, const HtView& out) {
   extern __shared__ double sh[];
   const int leaf = L.leaf[blockIdx.y];
   const int dim = T.lo[leaf];
@@ -471,7 +509,8 @@ __device__ inline int find_block(const int* offs, int nb, int i, int* local) {
   return b;
 }
 
-__global__ void apply_xfer_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+__device__ void apply_xfer_body(const ApplyOp& op, const TreeInfo& T, const Levels& L, const HtView& in0,
+                                const HtView& in1, const HtView& out) {
   const int t = L.proj2[blockIdx.y];   // interior nodes and the root
   const int a = T.c1[t], b = T.c2[t];
   int oa[MAXBLK + 1], ob[MAXBLK + 1], ot[MAXBLK + 1];
@@ -527,6 +566,27 @@ __global__ void apply_xfer_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, 
     O[e] = v;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && t != 0) out.rank[t] = ot[nb];
+}
+
+__global__ void apply_leaf_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+  apply_leaf_body(op, T, L, in0, in1, out);
+}
+
+__global__ void apply_xfer_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
+  apply_xfer_body(op, T, L, in0, in1, out);
+}
+
+// batched forms: instance blockIdx.z, its operator op_sel and views in0_sel, in1_sel, out_sel
+__global__ void apply_leaf_batch_kernel(const Inst* I, TreeInfo T, Levels L, int op_sel, int in0_sel, int in1_sel,
+                                        int out_sel) {
+  const Inst& x = I[blockIdx.z];
+  apply_leaf_body(*x.op[op_sel], T, L, x.view[in0_sel], x.view[in1_sel], x.view[out_sel]);
+}
+
+__global__ void apply_xfer_batch_kernel(const Inst* I, TreeInfo T, Levels L, int op_sel, int in0_sel, int in1_sel,
+                                        int out_sel) {
+  const Inst& x = I[blockIdx.z];
+  apply_xfer_body(*x.op[op_sel], T, L, x.view[in0_sel], x.view[in1_sel], x.view[out_sel]);
 }
 
 // ------------------------------------------------------------ misc kernels ----
@@ -857,41 +917,62 @@ static HtView view_ws(ht_ctx* c, double* const* nodes, int* rank) {
 
 
 // ---------------------------------------------------------------- truncation --
+// Launch sequence of one truncation (the HSVD of Section 2.2 in R-factor form) for `count`
+// instances: instance i's descriptors sit in plan P + i.  pre() and sel() launch the planner and
+// the rank selection (single-instance or batched kernels).
+template <class Pre, class Sel>
+static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem, Pre pre, Sel sel, cudaStream_t s) {
+  const TreeInfo& T = c->tree;
+  const Levels& L = c->lev;
+  const int g = c->gemm_grid;
+  const long long st = (long long)sizeof(Plan);
+  HTG_LAUNCH(c, KC_PLAN, s, pre());
+  HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_leaf, L.n_leaf, s, htg_prof_flops(c, KC_QR), count, st));
+  for (int dep = T.max_depth - 1; dep >= 1; --dep) {
+    if (L.n_int[dep] == 0) continue;
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st));
+  }
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  // top-down complement factors: E of a child needs only E, B and R of its parent, never the
+  // parent's SVD, so every node SVD runs afterwards in a single launch
+  for (int dep = 1; dep < T.max_depth; ++dep) {
+    if (L.n_int[dep] == 0) continue;
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_GEMM, s,
+               htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st));
+  }
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_SVD, s,
+             htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st));
+  HTG_LAUNCH(c, KC_PLAN, s, sel());
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  if (L.n_proj3 > 0)
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  c->last_stream = s;
+  return HT_OK;
+}
+
 static int run_truncate(ht_ctx* c, const HtView& in, int cap_in, const HtView& out, double rel_tol, int rmax,
                         double* sigma_dev, int sig_stride, double* norm_dev, cudaStream_t s) {
   const TreeInfo& T = c->tree;
   const Levels& L = c->lev;
   Plan* P = c->plan;
   const WsNode* wn = c->wn_dev;
-  const int g = c->gemm_grid;
-  HTG_LAUNCH(c, KC_PLAN, s, (plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, c->err), cudaGetLastError()));
-  HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_leaf, L.n_leaf, s, htg_prof_flops(c, KC_QR)));
-  for (int dep = T.max_depth - 1; dep >= 1; --dep) {
-    if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
-    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
-  }
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM)));
-  // top-down complement factors: E of a child needs only E, B and R of its parent, never the
-  // parent's SVD, so every node SVD runs afterwards in a single launch
-  for (int dep = 1; dep < T.max_depth; ++dep) {
-    if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM)));
-    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR)));
-  }
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM)));
-  HTG_LAUNCH(c, KC_SVD, s, htg_launch_svd(P->svd_all, T.nn - 1, c->svd_smem, c->Kc, c->Kc, s, htg_prof_flops(c, KC_SVD)));
-  HTG_LAUNCH(c, KC_PLAN, s, (rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev,
-                                                          sig_stride, norm_dev, c->err),
-                       cudaGetLastError()));
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM)));
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM)));
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM)));
-  if (L.n_proj3 > 0) HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s, htg_prof_flops(c, KC_GEMM)));
-  c->last_stream = s;
-  return HT_OK;
+  int* err = c->err;
+  auto pre = [&]() {
+    plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, err);
+    return cudaGetLastError();
+  };
+  auto sel = [&]() {
+    rank_select_kernel<<<1, 32, 0, s>>>(P, T, L, in, out, wn, rel_tol, rmax, sigma_dev, sig_stride, norm_dev, err);
+    return cudaGetLastError();
+  };
+  return truncate_launches(c, P, 1, c->Kc, c->svd_smem, pre, sel, s);
 }
 
 static int copy_tensor_to(ht_ctx* c, const ht_tensor* u, double* const* dst, int* dst_rank, cudaStream_t s) {
@@ -1066,6 +1147,203 @@ extern "C" int ht_step(ht_ctx* c, ht_tensor* u, const ht_op* L, double dt, doubl
     return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
   }
   return HT_ERR_ARG;
+}
+
+// ---------------------------------------------------------------- batches -----
+struct ht_batch {
+  int count = 0;
+  std::vector<ht_ctx*> ctx;
+  std::vector<Plan*> own_plan;     // each context's own plan, restored by ht_batch_destroy
+  void* mem = nullptr;             // device: plans | instances | operators (2 per instance)
+  Plan* plans = nullptr;
+  Inst* inst = nullptr;
+  ApplyOp* ops = nullptr;
+  void* host = nullptr;            // pinned staging of instances and operators
+  Inst* inst_h = nullptr;
+  ApplyOp* ops_h = nullptr;
+  cudaEvent_t up_done = nullptr;   // the last upload from the staging buffers
+  bool uploaded = false;
+  std::vector<Inst> inst_new;
+  std::vector<ApplyOp> ops_new;
+  std::vector<int> ucap;           // rank capacity of each bound tensor
+  int Kc = 0, nmax = 1, max_cols = 1;
+};
+
+static void batch_free(ht_batch* b) {
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    if (i < b->own_plan.size() && b->own_plan[i]) b->ctx[i]->plan = b->own_plan[i];
+    b->ctx[i]->batch = nullptr;
+  }
+  if (b->up_done) cudaEventDestroy(b->up_done);
+  if (b->host) cudaFreeHost(b->host);
+  if (b->mem) cudaFree(b->mem);
+  delete b;
+}
+
+extern "C" int ht_batch_create(ht_batch** out, int count, ht_ctx* const* ctxs, ht_tensor* const* us) {
+  if (!out) return HT_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || count > 65535 || !ctxs || !us) return HT_ERR_ARG;
+  const int d = ctxs[0] ? ctxs[0]->cfg.d : 0;
+  const int dev = ctxs[0] ? ctxs[0]->cfg.device : 0;
+  for (int i = 0; i < count; ++i) {
+    ht_ctx* c = ctxs[i];
+    if (!c || c->cfg.d != d || c->cfg.device != dev || c->batch || !tensor_matches(c, us[i])) return HT_ERR_ARG;
+    if (us[i]->cap > c->cap) return HT_ERR_CAPACITY;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return HT_ERR_ARG;   // each instance needs its own workspace
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) return HT_ERR_CUDA;
+  ht_batch* b = new ht_batch();
+  b->count = count;
+  const size_t plan_b = align_up((size_t)count * sizeof(Plan));
+  const size_t inst_b = align_up((size_t)count * sizeof(Inst));
+  const size_t ops_b = align_up(2 * (size_t)count * sizeof(ApplyOp));
+  if (cudaMalloc(&b->mem, plan_b + inst_b + ops_b) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return HT_ERR_NOMEM;
+  }
+  char* base = (char*)b->mem;
+  b->plans = (Plan*)base;
+  b->inst = (Inst*)(base + plan_b);
+  b->ops = (ApplyOp*)(base + plan_b + inst_b);
+  if (cudaMallocHost(&b->host, inst_b + ops_b) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(b->mem);
+    delete b;
+    return HT_ERR_NOMEM;
+  }
+  b->inst_h = (Inst*)b->host;
+  b->ops_h = (ApplyOp*)((char*)b->host + inst_b);
+  if (cudaEventCreateWithFlags(&b->up_done, cudaEventDisableTiming) != cudaSuccess) {
+    b->up_done = nullptr;
+    batch_free(b);
+    return HT_ERR_CUDA;
+  }
+  b->inst_new.resize(count);
+  b->ops_new.resize(2 * (size_t)count);
+  for (int i = 0; i < count; ++i) {
+    ht_ctx* c = ctxs[i];
+    b->ctx.push_back(c);
+    b->own_plan.push_back(c->plan);
+    c->plan = b->plans + i;
+    c->batch = b;
+    Inst& x = b->inst_new[i];
+    memset(&x, 0, sizeof(x));
+    x.P = b->plans + i;
+    x.wn = c->wn_dev;
+    x.view[VIEW_U] = view_of(us[i]);
+    x.view[VIEW_APP] = view_ws(c, c->app, c->app_rank);
+    x.view[VIEW_STAGE] = view_ws(c, c->stage, c->stage_rank);
+    x.op[0] = b->ops + 2 * i;
+    x.op[1] = b->ops + 2 * i + 1;
+    x.err = c->err;
+    x.cap_in = c->Kc;
+    b->Kc = htg_max(b->Kc, c->Kc);
+    b->ucap.push_back(us[i]->cap);
+    b->max_cols = htg_max(b->max_cols, us[i]->cap);
+    for (int k = 0; k < d; ++k) b->nmax = htg_max(b->nmax, c->cfg.n[k]);
+  }
+  *out = b;
+  return HT_OK;
+}
+
+extern "C" void ht_batch_destroy(ht_batch* b) {
+  if (!b) return;
+  if (!b->ctx.empty()) cudaSetDevice(b->ctx[0]->cfg.device);
+  batch_free(b);
+}
+
+extern "C" int ht_batch_step(ht_batch* b, const ht_op* const* Ls, const double* dts, const double* rel_tols,
+                             const int* rmaxs, int scheme, void* stream) {
+  if (!b || !Ls || !dts || !rel_tols || !rmaxs) return HT_ERR_ARG;
+  if (scheme != HT_SCHEME_RK2POLY && scheme != HT_SCHEME_HEUN2) return HT_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cnt = b->count;
+  // operators and scalars of this call
+  for (int i = 0; i < cnt; ++i) {
+    ht_ctx* c = b->ctx[i];
+    Inst& x = b->inst_new[i];
+    const int ucap = b->ucap[i];
+    if (rmaxs[i] < 1 || rmaxs[i] > ucap || !(rel_tols[i] >= 0.0)) return HT_ERR_ARG;
+    x.rmax = rmaxs[i];
+    x.rel_tol = rel_tols[i];
+    ApplyOp& op = b->ops_new[2 * i];
+    ApplyOp& op2 = b->ops_new[2 * i + 1];
+    memset(&op2, 0, sizeof(op2));
+    if (scheme == HT_SCHEME_RK2POLY) {
+      if (!build_apply(c, Ls[i], dts[i], HT_APPLY_RK2POLY, &op)) return HT_ERR_ARG;
+    } else {
+      if (!build_apply(c, Ls[i], dts[i], HT_APPLY_EULER, &op)) return HT_ERR_ARG;
+      if ((long long)(op.nb + 1) * ucap > c->Kc) return HT_ERR_CAPACITY;
+      // second stage blocks [u | u* | A^q u*], as in ht_step
+      op2.mode = HT_APPLY_EULER;
+      op2.nb = op.nb + 1;
+      op2.src[0] = 0;
+      op2.coef[0] = 0.5;
+      for (int k = 0; k < c->cfg.d; ++k) op2.f[0][k] = op.f[0][k];
+      for (int q = 0; q < op.nb; ++q) {
+        op2.src[q + 1] = 1;
+        op2.coef[q + 1] = 0.5 * op.coef[q];
+        for (int k = 0; k < c->cfg.d; ++k) op2.f[q + 1][k] = op.f[q][k];
+      }
+    }
+  }
+  const size_t ib = (size_t)cnt * sizeof(Inst), ob = 2 * (size_t)cnt * sizeof(ApplyOp);
+  const bool same = b->uploaded && memcmp(b->inst_h, b->inst_new.data(), ib) == 0 &&
+                    memcmp(b->ops_h, b->ops_new.data(), ob) == 0;
+  if (!same) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return HT_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return HT_ERR_ARG;
+    // the staging buffers are rewritten only after the previous upload has run
+    if (cudaEventSynchronize(b->up_done) != cudaSuccess) return HT_ERR_CUDA;
+    memcpy(b->inst_h, b->inst_new.data(), ib);
+    memcpy(b->ops_h, b->ops_new.data(), ob);
+    if (cudaMemcpyAsync(b->inst, b->inst_h, ib, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(b->ops, b->ops_h, ob, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(b->up_done, s) != cudaSuccess)
+      return HT_ERR_CUDA;
+    b->uploaded = true;
+  }
+  ht_ctx* c0 = b->ctx[0];
+  const TreeInfo& T = c0->tree;
+  const Levels& L = c0->lev;
+  const Inst* I = b->inst;
+  const size_t smem = 2 * (size_t)b->nmax * sizeof(double);
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(apply_leaf_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HT_ERR_CUDA;
+  const dim3 gl(htg_max(1, htg_min(b->max_cols, 64)), L.n_leaf, cnt);
+  const dim3 gx(htg_max(1, c0->gemm_grid / cnt), L.n_proj2, cnt);
+  auto apply = [&](int op_sel, int in0, int in1, int outv) -> int {
+    HTG_LAUNCH(c0, KC_APPLY, s, (apply_leaf_batch_kernel<<<gl, 128, smem, s>>>(I, T, L, op_sel, in0, in1, outv),
+                                 cudaGetLastError()));
+    HTG_LAUNCH(c0, KC_APPLY, s, (apply_xfer_batch_kernel<<<gx, 256, 0, s>>>(I, T, L, op_sel, in0, in1, outv),
+                                 cudaGetLastError()));
+    return HT_OK;
+  };
+  auto truncate = [&](int inv, int outv) -> int {
+    auto pre = [&]() {
+      plan_pre_batch_kernel<<<cnt, 1, 0, s>>>(I, T, L, inv);
+      return cudaGetLastError();
+    };
+    auto sel = [&]() {
+      rank_select_batch_kernel<<<cnt, 32, 0, s>>>(I, T, L, inv, outv);
+      return cudaGetLastError();
+    };
+    return truncate_launches(c0, b->plans, cnt, b->Kc, c0->svd_smem, pre, sel, s);
+  };
+  int st;
+  if (scheme == HT_SCHEME_RK2POLY) {
+    if ((st = apply(0, VIEW_U, VIEW_U, VIEW_APP)) != HT_OK) return st;
+    return truncate(VIEW_APP, VIEW_U);
+  }
+  if ((st = apply(0, VIEW_U, VIEW_U, VIEW_APP)) != HT_OK) return st;
+  if ((st = truncate(VIEW_APP, VIEW_STAGE)) != HT_OK) return st;
+  if ((st = apply(1, VIEW_U, VIEW_STAGE, VIEW_APP)) != HT_OK) return st;
+  return truncate(VIEW_APP, VIEW_U);
 }
 
 // ---------------------------------------------------------------- misc --------

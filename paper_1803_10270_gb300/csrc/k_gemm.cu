@@ -14,7 +14,10 @@ namespace {
 constexpr int BM = 16, BN = 16, BK = 16, NT = 64;
 constexpr int MAXD = 64;
 
-__global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs, int ndesc, double* flops) {
+__global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs0, long long inst_stride, int ndesc,
+                                                  double* flops) {
+  // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
+  const GemmDesc* __restrict__ descs = (const GemmDesc*)((const char*)descs0 + inst_stride * blockIdx.y);
   __shared__ long long prefix[MAXD + 1];
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -98,11 +101,13 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
 
 }  // namespace
 
-cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops) {
-  if (ndesc <= 0) return cudaSuccess;
-  if (ndesc > MAXD) return cudaErrorInvalidValue;
-  if (grid < 1) grid = 1;
-  grid = grid / 2;   // 2 x SMs 64-thread CTAs: the grid-stride loop covers any item count
-  gemm_kernel<<<grid, NT, 0, s>>>(descs_dev, ndesc, flops);
+cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops, int count,
+                            long long inst_stride) {
+  if (ndesc <= 0 || count <= 0) return cudaSuccess;
+  if (ndesc > MAXD || count > 65535) return cudaErrorInvalidValue;
+  // 2 x SMs 64-thread CTAs in all (split over the instances of a batch): the grid-stride
+  // loop covers any item count
+  const int gx = htg_max(1, (grid / 2 + count - 1) / count);
+  gemm_kernel<<<dim3(gx, count), NT, 0, s>>>(descs_dev, inst_stride, ndesc, flops);
   return cudaGetLastError();
 }

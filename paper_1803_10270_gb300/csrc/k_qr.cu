@@ -26,9 +26,10 @@ __device__ inline double warp_sum(double v) {
 
 constexpr int QR_MAX_COLS = 4096;
 
-__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long smem_doubles,
-                                                 double* flops) {
-  const QrDesc q = descs[blockIdx.x];
+__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long inst_stride,
+                                                 long long smem_doubles, double* flops) {
+  // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
+  const QrDesc q = ((const QrDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
   const int m = q.m, k = q.k;
   if (m <= 0 || k <= 0 || k > QR_MAX_COLS) {
     if (threadIdx.x == 0 && q.rows_out) *q.rows_out = 0;
@@ -108,8 +109,10 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
 
 }  // namespace
 
-cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops) {
-  if (ndesc <= 0) return cudaSuccess;
+cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops, int count,
+                          long long inst_stride) {
+  if (ndesc <= 0 || count <= 0) return cudaSuccess;
+  if (count > 65535) return cudaErrorInvalidValue;
   static bool attr[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -119,6 +122,7 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
   // diag[] (QR_MAX_COLS values) followed by the staged matrix when it fits
-  qr_r_kernel<<<ndesc, NT, HTG_SMEM_BYTES, s>>>(descs_dev, (long long)(HTG_SMEM_BYTES / sizeof(double)), flops);
+  qr_r_kernel<<<dim3(ndesc, count), NT, HTG_SMEM_BYTES, s>>>(descs_dev, inst_stride,
+                                                               (long long)(HTG_SMEM_BYTES / sizeof(double)), flops);
   return cudaGetLastError();
 }

@@ -74,9 +74,10 @@ __device__ void cta_gemm(double* dst, const double* A, int lda, const double* B,
   }
 }
 
-__global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ descs, long long smem_doubles,
-                                                double* flops) {
-  const SvdDesc D = descs[blockIdx.x];
+__global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ descs, long long inst_stride,
+                                                long long smem_doubles, double* flops) {
+  // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
+  const SvdDesc D = ((const SvdDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
   const int p = D.p, q = D.q;
   if (p <= 0) return;
   const int mr = htg_max(p, q);
@@ -328,8 +329,9 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
 }  // namespace
 
 cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
-                           cudaStream_t s, double* flops) {
-  if (ndesc <= 0) return cudaSuccess;
+                           cudaStream_t s, double* flops, int count, long long inst_stride) {
+  if (ndesc <= 0 || count <= 0) return cudaSuccess;
+  if (count > 65535) return cudaErrorInvalidValue;
   (void)use_smem;
   const int mr = htg_max(pmax, qmax);
   const size_t mp = (size_t)mr * pmax, pp = (size_t)pmax * pmax;
@@ -343,6 +345,6 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  svd_kernel<<<ndesc, NT, smem, s>>>(descs_dev, (long long)(smem / sizeof(double)), flops);
+  svd_kernel<<<dim3(ndesc, count), NT, smem, s>>>(descs_dev, inst_stride, (long long)(smem / sizeof(double)), flops);
   return cudaGetLastError();
 }

@@ -73,6 +73,10 @@ _EXPORTS = {
                               C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "ht_step": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_op), C.c_double, C.c_double,
                           C.c_int, C.c_int, C.c_void_p]),
+    "ht_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]),
+    "ht_batch_destroy": (None, [C.c_void_p]),
+    "ht_batch_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                C.POINTER(C.c_int), C.c_int, C.c_void_p]),
     "ht_from_cp": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_tensor), C.c_void_p]),
     "ht_mass": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
     "ht_inner": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
@@ -392,6 +396,40 @@ def ht_step(ctx: Context, u: HTTensor, op: ht_op, dt: float, rel_tol: float, rma
             scheme: int = HT_SCHEME_RK2POLY, stream=None):
     _check(load().ht_step(ctx.ptr, C.byref(u.struct), C.byref(op), dt, rel_tol, rmax, scheme,
                           _stream_ptr(stream)), "ht_step")
+
+
+class Batch:
+    """Owns an ht_batch: independent instances (one context and one tensor each, same d) stepped
+    together, every launch covering all instances."""
+
+    def __init__(self, ctxs, tensors):
+        if len(ctxs) != len(tensors) or not ctxs:
+            raise ValueError("one tensor per context")
+        self.ctxs, self.tensors = list(ctxs), list(tensors)
+        n = len(ctxs)
+        cp = (C.c_void_p * n)(*[c.ptr.value for c in ctxs])
+        self._tptr = (C.c_void_p * n)(*[C.cast(C.pointer(t.struct), C.c_void_p).value for t in tensors])
+        self.ptr = C.c_void_p()
+        _check(load().ht_batch_create(C.byref(self.ptr), n, cp, self._tptr), "ht_batch_create")
+
+    def step(self, ops, dts, rel_tols, rmaxs, scheme: int = HT_SCHEME_RK2POLY, stream=None):
+        n = len(self.ctxs)
+        self._ops = list(ops)   # the structs must outlive the call
+        opp = (C.c_void_p * n)(*[C.cast(C.pointer(o), C.c_void_p).value for o in self._ops])
+        _check(load().ht_batch_step(self.ptr, opp, (C.c_double * n)(*map(float, dts)),
+                                    (C.c_double * n)(*map(float, rel_tols)), (C.c_int * n)(*map(int, rmaxs)),
+                                    scheme, _stream_ptr(stream)), "ht_batch_step")
+
+    def close(self):
+        if self.ptr:
+            load().ht_batch_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ht_from_cp(ctx: Context, x: CPTensor, out: HTTensor, stream=None):
