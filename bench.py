@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="launch every kernel per step instead of a CUDA graph")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -293,6 +294,10 @@ def run_gpu(args):
     e2e = run_e2e(W, G, torch, min(args.steps, 50))
     ranks = W.u.ranks()
 
+    # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
+    batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
+        if args.batched > 0 else None
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -307,11 +312,89 @@ def run_gpu(args):
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_shares": shares,
         }
+        if batched is not None:
+            out["batched"] = batched
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("ragged batch (cfg4): independent 6-D advection instances, n in {32,48,64,96,128}, "
+                  "HT r_max in 8..48, seeded velocities, RK2 dt=0.2h, tol 1e-8, FP64; "
+                  "one step = every instance's HT apply+HSVD truncate, each launch covering all instances")
+
+
+def ic_nodes(tree, fac, np):
+    """Exact rank-2 HT form of the two-term separable initial condition."""
+    nodes = {}
+    for t in range(tree.n_nodes):
+        if tree.is_leaf(t):
+            nodes[t] = fac[tree.lo[t]]
+        elif t == 0:
+            nodes[t] = np.eye(2)
+        else:
+            B = np.zeros((2, 2, 2))
+            B[0, 0, 0] = B[1, 1, 1] = 1.0
+            nodes[t] = B
+    return nodes
+
+
+def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:
+    """Throughput of ht_batch_step on a ragged batch: instance-steps/s over a graph-captured
+    step, L2 flushed between timed steps, slowest rank's time for replicas."""
+    import numpy as np
+    from paper_1803_10270_gb300.inputs import batched_advection_cases
+    cases = batched_advection_cases(count, D)
+    ctxs, tens, ops = [], [], []
+    ws = 0
+    for n, rmax, case in cases:
+        c = G.Context(D, [n] * D, cap=rmax, max_terms=1)
+        ws += c.workspace_bytes
+        t = G.HTTensor(D, [n] * D, rmax)
+        t.upload(ic_nodes(t.tree, case.ic_factors(), np))
+        ctxs.append(c)
+        tens.append(t)
+        ops.append(G.advection_op(case.c, case.h))
+    b = G.Batch(ctxs, tens)
+    dts = [case.dt for _, _, case in cases]
+    tols = [TOL] * count
+    rmaxs = [r for _, r, _ in cases]
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        b.step(ops, dts, tols, rmaxs, stream=stream)
+    torch.cuda.synchronize()
+    l0 = ctxs[0].launches()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        b.step(ops, dts, tols, rmaxs, stream=torch.cuda.current_stream())
+    per_step = ctxs[0].launches() - l0
+    graph.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(x) for a, x in ev)
+    for c in ctxs:
+        c.check()
+    ms_max, steps_per_s = aggregate_replicas(ms, steps)
+    rk = [max(t.ranks()[1:]) for t in tens]
+    ns = [n for n, _, _ in cases]
+    b.close()
+    del graph
+    for c in ctxs:
+        c.close()
+    return {"workload": BATCH_WORKLOAD, "instances": count, "value": steps_per_s * count,
+            "unit": "instance-steps/s", "ms_per_step": ms_max / steps, "steps": steps, "warmup": warmup,
+            "gpu_launches_per_step": per_step, "grids": {str(v): ns.count(v) for v in sorted(set(ns))},
+            "rank_max_final": max(rk), "rank_mean_final": sum(rk) / len(rk),
+            "workspace_gb": ws / 1e9, "l2": "flushed between timed steps (256 MB write)", "cuda_graph": True}
 
 
 def aggregate_replicas(ms_local: float, steps: int):

@@ -755,8 +755,11 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   const size_t sizes[15] = {K2, K3, K3, K3, K3, K3, K2, K2, Kc, K2, K2, 6 * K2 + Kc + 8, K2, K2, Kc};
   for (int t = 0; t < T.nn; ++t) {
     for (int j = 0; j < 15; ++j) {
+      // leaves never hold an absorbed transfer (Tabs, Cabs) or B x3 E^T (T1); the root has no
+      // QR and no absorbed transfer (Cabs, S)
+      const bool unused = (T.c1[t] < 0 && (j == 1 || j == 2 || j == 5)) || (t == 0 && (j == 2 || j == 3));
       W->node_off[t][j] = off;
-      off = align_up(off + sizes[j] * sizeof(double));
+      off = align_up(off + (unused ? 8 : sizes[j]) * sizeof(double));
     }
   }
   for (int t = 0; t < T.nn; ++t) {

@@ -97,6 +97,23 @@ def advection_case(d: int, n: int, n_terms: int = 2, seed: int | None = None, cf
     return AdvectionCase(d=d, n=n, n_terms=n_terms, seed=seed, c=c, phi=phi)
 
 
+BATCH_GRIDS = (32, 48, 64, 96, 128)
+
+
+def batched_advection_cases(count: int, d: int = 6, cfg_index: int = 3):
+    """A ragged batch of independent advection problems: per instance (n, r_max, case) with n
+    drawn from BATCH_GRIDS and r_max from 8..48 (one splitmix64 stream, seed 0x5EED + cfg_index,
+    two draws per instance), and the velocity and phases of instance i from its own seed
+    0x5EED + 1000 + i."""
+    g = SplitMix64(SEED_BASE + cfg_index)
+    out = []
+    for i in range(count):
+        n = BATCH_GRIDS[int(g.uniform_range(0.0, float(len(BATCH_GRIDS)))) % len(BATCH_GRIDS)]
+        rmax = 8 + int(g.uniform_range(0.0, 41.0)) % 41
+        out.append((n, rmax, advection_case(d, n, seed=SEED_BASE + 1000 + i)))
+    return out
+
+
 def normal_array(shape, seed: int, scale: float = 1.0) -> np.ndarray:
     """N(0, scale^2) array from PCG64(seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))
