@@ -64,6 +64,11 @@ struct SvdDesc {
   double* U;
   double* work;
   int p, q, ldp;
+  // Pairs of columns whose squared norms are both below skip2 |P|_F^2 are not rotated against
+  // each other.  With skip2 |P|_F^2 p <= the truncation threshold (tol |u|)^2 / (2d-3) every such
+  // column is discarded by the rank rule, and the tail sums it enters are traces of that block,
+  // which rotations within the block do not change.  0: rotate every pair.
+  double skip2;
 };
 
 // ------------------------------------------------------------ launchers -----
@@ -136,19 +141,40 @@ __device__ inline bool htg_in_f32_range(double x) {
 }
 __device__ inline double htg_rsqrt_fast(double x) {
   if (!htg_in_f32_range(x) || !htg_dpos(x)) return rsqrt(x);
-  double y = htg_f2d(rsqrtf(htg_d2f(x)));
-  // two Newton steps for f(y) = 1/y^2 - x, y <- y (3 - x y^2) / 2: seed error ~2e-7 (truncated
-  // conversion) -> 6e-14 -> rounding level; Jacobi rotations need c^2 + s^2 = 1 to rounding
-  double h = x * y;
-  y = fma(0.5 * y, fma(-h, y, 1.0), y);
-  h = x * y;
-  return fma(0.5 * y, fma(-h, y, 1.0), y);
+  const double y = htg_f2d(rsqrtf(htg_d2f(x)));
+  // with e = 1 - x y^2 (|e| <~ 2^-21 from the FP32 seed of the truncated input):
+  // x^-1/2 = y (1 - e)^-1/2 = y (1 + e/2 + 3 e^2/8 + O(e^3)); the O(e^3) term is below 2^-62,
+  // so five dependent FP64 operations give the result to rounding (Jacobi rotations need
+  // c^2 + s^2 = 1 to rounding)
+  const double h = x * y;
+  const double e = fma(-h, y, 1.0);
+  const double q = fma(0.375, e, 0.5) * e;
+  return fma(y, q, y);
+}
+// float of x 2^k (truncated mantissa) when x 2^k lies in the normal FP32 range, for a power-of-
+// two rescaling without an FP64 multiply; *ok = false (and 0 returned) otherwise, x = 0 included
+__device__ inline float htg_d2f_shift(double x, int k, bool* ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023 + k + 127;
+  if ((b << 1) == 0 || e <= 8 || e >= 247) {   // zero, or outside [2^-118, 2^119]
+    *ok = false;
+    return 0.0f;
+  }
+  *ok = true;
+  return __int_as_float((int)(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu)));
 }
 __device__ inline double htg_rcp_fast(double x) {
   if (!htg_in_f32_range(x)) return 1.0 / x;
-  double y = htg_f2d(1.0f / htg_d2f(x));
-  y = fma(y, fma(-x, y, 1.0), y);       // Newton for f(y) = 1/y - x:  y <- y (2 - x y), twice
-  return fma(y, fma(-x, y, 1.0), y);
+  // seed: the approximate FP32 reciprocal (one special-function instruction, relative error
+  // about 2^-23 on normal inputs; the range test keeps the input and its reciprocal normal)
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(htg_d2f(x)));
+  const double y = htg_f2d(yf);
+  // with e = 1 - x y (|e| <~ 2^-22): 1/x = y / (1 - e) = y (1 + e + e^2 + O(e^3)); the O(e^3)
+  // term is below 2^-64, so three dependent FP64 operations give the reciprocal to rounding
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // ------------------------------------------------------------ context access ---

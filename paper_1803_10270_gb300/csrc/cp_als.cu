@@ -361,13 +361,12 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) 
       atomicAdd(bar + 1, 1u);
     } else {
       const long long t0 = clock64();
-      while (*vgen == g) {
+      while (*vgen == g) {   // one polling thread per CTA: spin on the L2 line, no back-off
         if (clock64() - t0 > BARRIER_TIMEOUT_CYCLES) {
           ok = 0;
           if (err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
           break;
         }
-        __nanosleep(32);
       }
     }
     __threadfence();
@@ -556,11 +555,17 @@ __device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 
 // lower part) with the unit-lower forward solve of the three right-hand sides in hs fused in.
 // Right-looking, one CTA barrier per pivot: step j applies a_ic -= (a_ij / d_j) a_cj to the
 // trailing lower triangle (pairs from tri, i >= c > j) and z_i -= (a_ij / d_j) z_j to the
-// right-hand sides; the thread that updates a_{j+1,j+1} (the first pair of the step) forms
-// 1/d_{j+1} at once.  Column j keeps a_ij = L_ij d_j.  A pivot that is not positive and finite
-// leaves dinv = 0 there; every thread sees it after the barrier and the result is false.
+// right-hand sides.  The next pivot a_{j+1,j+1} and its reciprocal are formed by one thread of
+// the last warp, and the warps on that warp's SM partition (warp index 3 mod 4) take no other
+// work: the pivot chain (two FP64 operations, the reciprocal's seed and its correction) then
+// never waits behind other warps' FP64 instructions.  Column j keeps a_ij = L_ij d_j.  A pivot
+// that is not positive and finite leaves dinv = 0 there; every thread sees it after the
+// barrier and the result is false.
 __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigned short* tri, int r) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5;
+  constexpr int PIV = NT - 32;              // the pivot thread: lane 0 of the last warp
+  constexpr int NE = (NT / 32) * 3 / 4 * 32;   // element threads: the warps with wid % 4 != 3
+  const int et = (wid % 4 != 3) ? (wid - wid / 4) * 32 + (tid & 31) : -1;
   if (tid == 0) {
     const double d0 = Lm[0];
     dinv[0] = htg_dpos_finite(d0) ? htg_rcp_fast(d0) : 0.0;
@@ -571,20 +576,26 @@ __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigne
     const double dj = dinv[j];
     if (!htg_dnz(dj)) return false;   // uniform: written before the last barrier
     const int m = r - 1 - j;
-    const int s0 = tri_offset(j + 1, r);
+    const int s0 = tri_offset(j + 1, r) + 1;   // the pairs after (j+1, j+1)
     const int ntri = T - s0;
     const int nall = ntri + 3 * m;
-    for (int e = tid; e < nall; e += NT) {
-      if (e < ntri) {
-        const unsigned int pr = tri[s0 + e];
-        const int i = pr & 0xff, c = pr >> 8;
-        const double v = fma(-(Lm[i + r * j] * dj), Lm[c + r * j], Lm[i + r * c]);
-        Lm[i + r * c] = v;
-        if (e == 0) dinv[j + 1] = htg_dpos_finite(v) ? htg_rcp_fast(v) : 0.0;
-      } else {
-        const int f = e - ntri, p = f / m, i = j + 1 + f % m;
-        hs[p * r + i] = fma(-(Lm[i + r * j] * dj), hs[p * r + j], hs[p * r + i]);
+    if (et >= 0) {
+      for (int e = et; e < nall; e += NE) {
+        if (e < ntri) {
+          const unsigned int pr = tri[s0 + e];
+          const int i = pr & 0xff, c = pr >> 8;
+          Lm[i + r * c] = fma(-(Lm[i + r * j] * dj), Lm[c + r * j], Lm[i + r * c]);
+        } else {
+          const int f = e - ntri, p = f / m, i = j + 1 + f % m;
+          hs[p * r + i] = fma(-(Lm[i + r * j] * dj), hs[p * r + j], hs[p * r + i]);
+        }
       }
+    } else if (tid == PIV && m > 0) {
+      const int i = j + 1;
+      const double a = Lm[i + r * j];
+      const double v = fma(-(a * dj), a, Lm[i + r * i]);
+      Lm[i + r * i] = v;
+      dinv[i] = htg_dpos_finite(v) ? htg_rcp_fast(v) : 0.0;
     }
     __syncthreads();
   }
@@ -630,7 +641,7 @@ __device__ void ldlt_back(const double* Lm, double* hs, const double* dinv, int 
 __host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z) {
   const long long ld = nmax | 1, K = 3LL * r0;
   const long long base = (long long)r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
-                         (nmax > NT ? nmax : NT) + ld * r;
+                         (nmax > NT ? nmax : NT) + (long long)d * r * r + ld * r;
   return base + (with_z ? ld * K : 0);
 }
 
@@ -646,9 +657,10 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   double* dinv = hs + 3 * r;                 // r: reciprocal pivots
   double* xs = dinv + r;                     // nmax
   double* ys = xs + nmax;                    // max(nmax, 3 r0)
-  double* Mv = ys + htg_max(nmax, K);        // d x 3 x r: M_j^(p) rows of this CTA's lp
+  double* Mv = ys + htg_max(nmax, K);        // d x 3 x r: copy of the M_j^(p) rows of this CTA's lp
   double* pb = Mv + 3 * d * r;               // max(NT, nmax): partial sums of split dot products
-  double* Xs = pb + htg_max(NT, nmax);       // odd_ld(nmax) x r: a staged factor
+  double* Gs = pb + htg_max(NT, nmax);       // d x r x r: copy of the Grams G_j
+  double* Xs = Gs + (long long)d * r * r;    // odd_ld(nmax) x r: a staged factor
   double* Zs = Xs + (long long)odd_ld(nmax) * r;   // odd_ld(nmax) x 3 r0: Z_k (when zs_smem)
   __shared__ unsigned short tri[TRI_MAX];
   __shared__ double red[HT_MAXD + 32];
@@ -720,21 +732,28 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           w.acc2[0] = 0.0;
           w.acc2[1] = 0.0;
         }
-        // M_j operands of row lp (j != k) into shared memory
-        for (int e = tid; e < 3 * d * r; e += blockDim.x) {
-          const int j = e / (3 * r), rem = e % (3 * r), pp = rem / r, l = rem % r;
-          Mv[e] = (j == k) ? 0.0 : w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)K * l];
+        // refresh the shared copies of G_j and of the rows lp of M_j^(p) that changed since
+        // this CTA last read them: all at the start and after a damped Jacobi sweep, else those
+        // of the mode updated last (Gauss-Seidel)
+        int j0 = 0, j1 = 0;
+        if (k == 0 && (sweep == 0 || !gs)) j1 = d;
+        else if (gs) { j0 = (k + d - 1) % d; j1 = j0 + 1; }
+        const int nG = r * r, nM = 3 * r;
+        for (int e = tid; e < (j1 - j0) * (nG + nM); e += blockDim.x) {
+          const int j = j0 + e / (nG + nM), f = e % (nG + nM);
+          if (f < nG) {
+            Gs[j * nG + f] = w.G[(long long)j * w.rcap * w.rcap + f];
+          } else {
+            const int pp = (f - nG) / r, l = (f - nG) % r;
+            Mv[(j * 3 + pp) * r + l] = w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)K * l];
+          }
         }
-        // Gamma_k = hadamard_{j != k} G_j (all loads of an entry issued before the products)
-        for (int e = tid; e < r * r; e += blockDim.x) {
-          double g[MODE_MAXD];
-#pragma unroll
-          for (int j = 0; j < MODE_MAXD; ++j)
-            g[j] = (j < d && j != k) ? w.G[(long long)j * w.rcap * w.rcap + e] : 1.0;
+        __syncthreads();
+        // Gamma_k = hadamard_{j != k} G_j
+        for (int e = tid; e < nG; e += blockDim.x) {
           double v = 1.0;
-#pragma unroll
-          for (int j = 0; j < MODE_MAXD; ++j)
-            if (j < d && j != k) v *= g[j];
+          for (int j = 0; j < d; ++j)
+            if (j != k) v *= Gs[j * nG + e];
           Lm[e] = v;
         }
         __syncthreads();
@@ -750,16 +769,16 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
             for (int i = 0; i < r; ++i) {
               double v = 1.0;
               for (int j = 0; j < d; ++j)
-                if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + i + r * i];
+                if (j != k) v *= Gs[j * nG + i + r * i];
               tr += v;
             }
             shift = 1e-14 * tr / r;
           }
           __syncthreads();
-          for (int e = tid; e < r * r; e += blockDim.x) {
+          for (int e = tid; e < nG; e += blockDim.x) {
             double v = 1.0;
             for (int j = 0; j < d; ++j)
-              if (j != k) v *= w.G[(long long)j * w.rcap * w.rcap + e];
+              if (j != k) v *= Gs[j * nG + e];
             Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
           }
           rk2_rhs_row(Mv, d, k, r, mu[lp], hs);
@@ -803,23 +822,33 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           den = fma(old, old, den);
           nrm2 = fma(v, v, nrm2);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          num += __shfl_xor_sync(0xffffffffu, num, o);
-          den += __shfl_xor_sync(0xffffffffu, den, o);
-          nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
-        }
+        // only the warps that hold rows reduce (every FP64 warp instruction costs the same)
+        const int wr = htg_min(NT / 32, (n + 31) / 32);
         __shared__ double r3[3][NT / 32];
-        if ((tid & 31) == 0) { r3[0][tid >> 5] = num; r3[1][tid >> 5] = den; r3[2][tid >> 5] = nrm2; }
+        if ((tid >> 5) < wr) {
+          for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+            nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+          }
+          if ((tid & 31) == 0) { r3[0][tid >> 5] = num; r3[1][tid >> 5] = den; r3[2][tid >> 5] = nrm2; }
+        }
         __syncthreads();
         __shared__ double scol;
         if (tid == 0) {
           double tn = 0.0, td = 0.0, t2 = 0.0;
-          for (int q = 0; q < NT / 32; ++q) { tn += r3[0][q]; td += r3[1][q]; t2 += r3[2][q]; }
+          for (int q = 0; q < wr; ++q) { tn += r3[0][q]; td += r3[1][q]; t2 += r3[2][q]; }
           atomicAdd(&w.acc2[0], tn);
           atomicAdd(&w.acc2[1], td);
-          const double nr = sqrt(t2);
+          double nr = 0.0, inv = 1.0;
+          if (htg_dpos_finite(t2)) {
+            inv = htg_rsqrt_fast(t2);
+            nr = t2 * inv;
+          } else {
+            nr = sqrt(t2);
+          }
           if (gs) a.lam[b] = nr;
-          scol = htg_dpos_finite(nr) ? htg_rcp_fast(nr) : 1.0;
+          scol = inv;
         }
         __syncthreads();
         if (gs) {

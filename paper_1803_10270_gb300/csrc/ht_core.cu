@@ -177,8 +177,10 @@ __device__ void fill_gemm(GemmDesc& g, const double* A, int lda, int tA, const d
   g.alpha = 1.0; g.beta = 0.0;
 }
 
+// skip_tol: the relative tolerance that sets the SVD discard level (SvdDesc::skip2), 0 when every
+// singular value is to be resolved (they are reported to the caller)
 __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const HtView& in, const WsNode* wn,
-                              int cap_in, int* err) {
+                              int cap_in, double skip_tol, int* err) {
   if (threadIdx.x != 0) return;
   // device-resident ranks are validated against the input capacity: out-of-range ranks are
   // clamped (every later access stays inside the buffers) and reported as HT_ERR_CAPACITY
@@ -249,6 +251,9 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
       SvdDesc& v = P->svd_all[t - 1];
       v.P = wn[t].P; v.p = P->Rp[t]; v.q = P->mE[t]; v.ldp = P->Rp[t];
       v.sigma = wn[t].sig; v.V = wn[t].W; v.U = wn[t].Z; v.work = wn[t].SW;
+      // |P_t|_F = |u|: columns with sigma^2 below 1e-6 (tol |u|)^2 / (2d-3) are discarded by
+      // the rank rule whatever their mutual rotation (see SvdDesc::skip2)
+      v.skip2 = 1e-6 * skip_tol * skip_tol / (double)htg_max(2 * T.d - 3, 1);
     }
     for (int s = 0; s < L.n_int[dep]; ++s) {
       const int t = L.inter[dep][s], a = T.c1[t], b = T.c2[t];
@@ -270,13 +275,14 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
   }
 }
 
-__global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const WsNode* wn, int cap_in, int* err) {
-  plan_pre_body(P, T, L, in, wn, cap_in, err);
+__global__ void plan_pre_kernel(Plan* P, TreeInfo T, Levels L, HtView in, const WsNode* wn, int cap_in,
+                                double skip_tol, int* err) {
+  plan_pre_body(P, T, L, in, wn, cap_in, skip_tol, err);
 }
 
 __global__ void plan_pre_batch_kernel(const Inst* I, TreeInfo T, Levels L, int in_sel) {
   const Inst& x = I[blockIdx.x];
-  plan_pre_body(x.P, T, L, x.view[in_sel], x.wn, x.cap_in, x.err);
+  plan_pre_body(x.P, T, L, x.view[in_sel], x.wn, x.cap_in, x.rel_tol, x.err);
 }
 
 // Rank selection (one CTA) + projection descriptors.
@@ -968,7 +974,7 @@ static int run_truncate(ht_ctx* c, const HtView& in, int cap_in, const HtView& o
   const WsNode* wn = c->wn_dev;
   int* err = c->err;
   auto pre = [&]() {
-    plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, err);
+    plan_pre_kernel<<<1, 1, 0, s>>>(P, T, L, in, wn, cap_in, sigma_dev ? 0.0 : rel_tol, err);
     return cudaGetLastError();
   };
   auto sel = [&]() {

@@ -30,16 +30,16 @@ __device__ inline int rr_player(int pos, int round, int p2) {
   return pos == 0 ? 0 : 1 + ((pos - 1 + round) % (p2 - 1));
 }
 
-// Cost model: a dependent FP64 operation costs ~64 cycles on GB300 (FP32: 4.5), FP64 sqrt /
-// divide several hundred, and every FP64 warp instruction holds the SM's FP64 pipe for the
-// whole warp.  The SVD therefore runs in two phases:
+// Cost model (measured on GB300): every FP64 warp instruction holds its SM partition's FP64
+// pipe for 64 cycles whatever the number of active lanes (FP32: 4.5 cycles latency, 32 lanes
+// per clock), FP64 sqrt / divide several hundred.  The SVD therefore runs in phases:
 //  1. one-sided Jacobi entirely in FP32 on a scaled copy of M, accumulating V32 (cheap
 //     sweeps until |a.b| <= tol32 |a||b|);
 //  2. V32 is made orthogonal to FP64 accuracy by two Newton-Schulz steps
 //     V <- V (3 I - V^T V) / 2, then G = (M V)^T (M V) is formed in FP64; its off-diagonal
 //     part is now ~tol32 relative, so two-sided Jacobi on G (rotations applied to rows, then
-//     columns, of G and to V) converges in two or three FP64 sweeps while every entry keeps
-//     its relative accuracy (no cancellation with small rotation angles);
+//     columns, of G and to V) converges in a few FP64 sweeps while every entry keeps its
+//     relative accuracy (no cancellation with small rotation angles);
 //  3. U S = M V in FP64, S = column norms, sorted descending.
 // Rotation parameters: angle from an FP32 evaluation, c = (1 + t^2)^(-1/2) by an FP64 Newton
 // step and s = c t, so each FP64 rotation is orthogonal to FP64 accuracy.
@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   float* V32 = M32 + mp + 1;
   const int tid = threadIdx.x;
   __shared__ int rotated;
+  __shared__ int sh_e;        // scale = 2^sh_e
+  __shared__ int ract;        // id of the last round with a rotation
   __shared__ double red[NT / 32];
   __shared__ double sc_[HTG_SVD_MAXP];
   __shared__ double ss_[HTG_SVD_MAXP];
@@ -120,21 +122,27 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   if (tid == 0) {
     double a = 0.0, f = 0.0;
     for (int w = 0; w < NT / 32; ++w) { a = htg_dmax_nn(a, red[w]); f += red2[w]; }
-    red[0] = (a > 0.0) ? ldexp(1.0, -ilogb(a)) : 1.0;
+    sh_e = (a > 0.0) ? -ilogb(a) : 0;
+    red[0] = ldexp(1.0, sh_e);
     red2[0] = f;
   }
   __syncthreads();
   const double scale = red[0];
+  const int sh2 = 2 * sh_e;   // Gram entries scale by 2^sh2
   // rounding floor: columns with |col|^2 <= eps^2 |M|_F^2 carry no information and are not
   // rotated (rotating them only reshuffles rounding noise and keeps the sweeps going)
   const double floor2 = EPS * EPS * red2[0];
+  // pairs of columns both below the discard level stay unrotated (see SvdDesc::skip2)
+  const double skip_abs = D.skip2 * red2[0];
+  const float skip32 = htg_d2f(skip_abs * scale * scale);
   const float floor2_32 = htg_d2f(16.0 * 3.55e-15 * red2[0] * scale * scale);   // (4 eps32)^2 |M s|_F^2
   for (long long e = tid; e < mp; e += NT) M32[e] = htg_d2f(M[e] * scale);
   for (long long e = tid; e < pp; e += NT) V32[e] = (e % p == e / p) ? 1.0f : 0.0f;
   const int p2 = p + (p & 1);
   const int npairs = p2 / 2;
+  // lanes per pair: enough for one row per lane, as many pairs as fit the CTA
   int L = 1;
-  while (L < 32 && L * 8 < htg_max(mr, p)) L <<= 1;
+  while (L < 32 && L < mr) L <<= 1;
   while (L > 1 && npairs * L > NT) L >>= 1;
   const int gid = tid / L, gl = tid % L, ngroups = NT / L;
   const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << ((tid & 31) & ~(L - 1)));
@@ -165,7 +173,8 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
             be += __shfl_xor_sync(gmask, be, o);
             ga += __shfl_xor_sync(gmask, ga, o);
           }
-          if (ga != 0.f && al > floor2_32 && be > floor2_32 && fabsf(ga) > TOL32 * sqrtf(al) * sqrtf(be)) {
+          if (ga != 0.f && al > floor2_32 && be > floor2_32 && (al > skip32 || be > skip32) &&
+              fabsf(ga) > TOL32 * sqrtf(al) * sqrtf(be)) {
             const float zf = (be - al) / (2.0f * ga);
             const float azf = fabsf(zf);
             const float t = (azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f)));
@@ -212,13 +221,15 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   if (gl == 0 && gid == 0) myflops += 4.0 * p * p * p + 2.0 * mr * p * p + 2.0 * mr * p * p;
   // ---------------- phase 3: FP64 two-sided Jacobi on G (rotations also applied to V)
   const double TOL = EPS * (double)htg_max(mr, 8);
-  const float TOL32G = htg_d2f(TOL * TOL);
-  const double scale2 = scale * scale;
+  const float TOL64F = htg_d2f(TOL);
+  if (tid == 0) ract = 0;
+  __syncthreads();
   if (p > 1) {
     for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
       if (tid == 0) rotated = 0;
       __syncthreads();
       for (int round = 0; round < p2 - 1; ++round) {
+        const int rid = sweep * p2 + round + 1;
         for (int pi = tid; pi < npairs; pi += NT) {
           int a, b;
           rr_pair(pi, round, p, p2, &a, &b);
@@ -226,36 +237,30 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
           double c = 1.0, sn = 0.0;
           if (a >= 0) {
             const double al = G[a + (long long)p * a], be = G[b + (long long)p * b], ga = G[a + (long long)p * b];
-            // test and angle in FP32 on Gram entries scaled by s^2 (|s M| <= 2): a threshold
-            // test and a steering angle need no more; only c is refined in FP64.  When a scaled
-            // entry leaves the FP32 normal range (tiny columns) both are taken in FP64, so a
-            // rotation is never flagged without moving anything.
-            const double als = al * scale2, bes = be * scale2, gas = ga * scale2;
-            const bool f32 = htg_in_f32_range(als) && htg_in_f32_range(bes) && htg_in_f32_range(gas);
-            bool big;
-            float zf = 0.0f;
-            if (f32) {
-              const float alf = htg_d2f(als), bef = htg_d2f(bes), gaf = htg_d2f(gas);
-              const float g2 = gaf * gaf, ab = TOL32G * alf * bef;
-              big = (g2 > 0.0f && ab > 0.0f) ? (g2 > ab) : (ga * ga > TOL * TOL * al * be);
-              zf = htg_d2f((be - al) * scale2) / (2.0f * gaf);
-            } else {
-              big = htg_dnz(ga) && (ga * ga > TOL * TOL * al * be);
-            }
-            if (htg_dnz(ga) && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) && big) {
-              double t;
-              if (f32) {
-                const float azf = fabsf(zf);
-                t = htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
-              } else {
-                const double zeta = (be - al) / (2.0 * ga);
-                const double az = fabs(zeta);
-                t = (az > 1e150) ? 0.5 / zeta : (zeta >= 0.0 ? 1.0 : -1.0) / (az + sqrt(fma(zeta, zeta, 1.0)));
-              }
+            // test and angle in FP32 on the entries scaled by 2^sh2 (|s M| <= 2), rescaled by
+            // exponent arithmetic; only c is refined in FP64, so each rotation is orthogonal to
+            // FP64 accuracy.  An entry outside the FP32 range means a column below the rounding
+            // floor (|s a|^2 < 2^-118, far below eps^2 |s M|_F^2) or a coupling below 2^-118:
+            // neither is rotated.
+            bool oka, okb, okg;
+            const float alf = htg_d2f_shift(al, sh2, &oka), bef = htg_d2f_shift(be, sh2, &okb);
+            const float gaf = htg_d2f_shift(ga, sh2, &okg);
+            // |ga| > TOL sqrt(al be), with the product formed so that it cannot underflow
+            // before the floor test below rejects the pair
+            const bool big = oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef);
+            if (big && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
+                (htg_dgt_nn(al, skip_abs) || htg_dgt_nn(be, skip_abs))) {
+              bool okd;
+              const float df = htg_d2f_shift(be - al, sh2, &okd);   // 0 when below the range
+              const float zf = df / (2.0f * gaf);
+              const float azf = fabsf(zf);
+              const double t =
+                  htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
               c = htg_rsqrt_fast(fma(t, t, 1.0));
               sn = c * t;
               act = 1;
               rotated = 1;
+              ract = rid;
               myflops += 12.0 * p;
             }
           }
@@ -264,6 +269,7 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
           act_[pi] = act;
         }
         __syncthreads();
+        if (ract != rid) continue;   // no rotation in this round (uniform after the barrier)
         // rows a, b of G
         for (int e = tid; e < npairs * p; e += NT) {
           const int pi = e / p, k = e % p;
@@ -276,20 +282,19 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
           G[b + (long long)p * k] = sn * x + c * y;
         }
         __syncthreads();
-        // columns a, b of G and of V
-        for (int e = tid; e < npairs * p; e += NT) {
-          const int pi = e / p, k = e % p;
+        // columns a, b of G (items e < npairs p) and of V (the rest), one rotation each
+        for (int e = tid; e < 2 * npairs * p; e += NT) {
+          const int isV = e >= npairs * p;
+          const int f = isV ? e - npairs * p : e;
+          const int pi = f / p, k = f % p;
           if (!act_[pi]) continue;
           int a, b;
           rr_pair(pi, round, p, p2, &a, &b);
           const double c = sc_[pi], sn = ss_[pi];
-          double x = G[k + (long long)p * a], y = G[k + (long long)p * b];
-          G[k + (long long)p * a] = c * x - sn * y;
-          G[k + (long long)p * b] = sn * x + c * y;
-          x = V[k + (long long)p * a];
-          y = V[k + (long long)p * b];
-          V[k + (long long)p * a] = c * x - sn * y;
-          V[k + (long long)p * b] = sn * x + c * y;
+          double* X = isV ? V : G;
+          const double x = X[k + (long long)p * a], y = X[k + (long long)p * b];
+          X[k + (long long)p * a] = c * x - sn * y;
+          X[k + (long long)p * b] = sn * x + c * y;
         }
         __syncthreads();
       }
