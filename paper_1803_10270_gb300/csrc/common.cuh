@@ -191,7 +191,7 @@ struct CpWs {
   GemmDesc* descs; // 4 * HT_MAXD
   double* Z;       // HT_MAXD x nmax x 3 rcap   powers [X, A X, A^2 X] of the step's input
   double* acc2;    // 2 doubles: per-mode sums of the convergence measure (persistent kernel)
-  unsigned int* bar;   // 2 words: grid barrier arrival count and generation
+  unsigned int* bar;   // 64 words: grid barrier arrival sequence numbers, one per CTA
   int rcap, rycap, nmax;
 };
 CpWs* htg_ctx_cp(ht_ctx* c);

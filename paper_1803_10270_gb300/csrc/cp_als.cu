@@ -346,31 +346,34 @@ struct PowArgs {
 // ---------------------------------------------------------------------------
 constexpr long long BARRIER_TIMEOUT_CYCLES = 400000000LL;   // about 0.2 s
 
-__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) {
+// Grid barrier by per-CTA arrival words: CTA b publishes the barrier's sequence number seq in
+// flags[b] (no atomics); warp 0 of every CTA polls all words, one lane each, until every one has
+// reached seq.  Sequence numbers grow by one per barrier of the launch; the words are zeroed
+// before the launch.  The wait is bounded: past the limit the kernel records HT_ERR_TIMEOUT and
+// every barrier after it returns false.
+__device__ bool grid_barrier(unsigned int* flags, unsigned int nblocks, unsigned int seq, int* err) {
   __shared__ int ok_sh;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = bar + 1;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(bar, 1u) + 1u;
-    int ok = 1;
-    if (arrived == nblocks) {
-      atomicExch(bar, 0u);
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {   // one polling thread per CTA: spin on the L2 line, no back-off
+      *(volatile unsigned int*)(flags + blockIdx.x) = seq;
+    }
+    __syncwarp();
+    int ok = 1;
+    const long long t0 = clock64();
+    for (unsigned int i = threadIdx.x; i < nblocks && ok; i += 32) {
+      while (*(volatile unsigned int*)(flags + i) < seq) {
         if (clock64() - t0 > BARRIER_TIMEOUT_CYCLES) {
           ok = 0;
-          if (err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
           break;
         }
       }
     }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && threadIdx.x == 0 && err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
     __threadfence();
-    ok_sh = ok;
+    if (threadIdx.x == 0) ok_sh = ok;
   }
   __syncthreads();
   return ok_sh != 0;
@@ -529,8 +532,8 @@ __device__ void normalise_column(const CpArgs& a, int b, bool fold, double* red)
 // s = sum_{j != k} z_j.  The truncated product f(e) = prod_{j != k} (m_0,j + m_1,j e + m_2,j e^2 / 2)
 // mod e^3 = f0 + f1 e + f2 e^2 holds the degree sums, so
 //   hs_0 = mu (f0 + f1 + f2),   hs_1 = mu (f0 + f1),   hs_2 = mu f0 / 2.
-__device__ void rk2_rhs_row(const double* Mv, int d, int k, int r, double mu, double* hs) {
-  for (int l = threadIdx.x; l < r; l += blockDim.x) {
+__device__ void rk2_rhs_row(const double* Mv, int d, int k, int r, double mu, double* hs, int t0, int nthr) {
+  for (int l = t0; l < r; l += nthr) {
     double f0 = 1.0, f1 = 0.0, f2 = 0.0;
     for (int j = 0; j < d; ++j) {
       if (j == k) continue;
@@ -558,9 +561,9 @@ __device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 
 // right-hand sides.  The next pivot a_{j+1,j+1} and its reciprocal are formed by one thread of
 // the last warp, and the warps on that warp's SM partition (warp index 3 mod 4) take no other
 // work: the pivot chain (two FP64 operations, the reciprocal's seed and its correction) then
-// never waits behind other warps' FP64 instructions.  Column j keeps a_ij = L_ij d_j.  A pivot
-// that is not positive and finite leaves dinv = 0 there; every thread sees it after the
-// barrier and the result is false.
+// never waits behind other warps' FP64 instructions (anything else that runs meanwhile, even
+// loads, lengthens the steps).  Column j keeps a_ij = L_ij d_j.  A pivot that is not positive and
+// finite leaves dinv = 0 there; every thread sees it after the barrier and the result is false.
 __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigned short* tri, int r) {
   const int tid = threadIdx.x, wid = tid >> 5;
   constexpr int PIV = NT - 32;              // the pivot thread: lane 0 of the last warp
@@ -670,6 +673,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
     for (int i = c; i < r; ++i) tri[o + i - c] = (unsigned short)(i | (c << 8));
   }
   const bool gs = (a.variant == CP_ALS_GS);
+  unsigned int bseq = 0;   // sequence number of the last grid barrier
   // ---------------- 0a: powers of x_old (CTA b < r0), weights, normalisation of column b
   if (b < r0) {
     for (int k = 0; k < d; ++k) {
@@ -706,13 +710,13 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
     for (int i = tid; i < sweeps && i < 64; i += blockDim.x) w.epsacc[i] = 0.0;
   }
   // the iterate may alias x_old: everything of x_old is read above, before the barrier
-  if (!grid_barrier(w.bar, nb, err)) return;
+  if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
   if (b < r) normalise_column(a, b, !gs, red);
-  if (!grid_barrier(w.bar, nb, err)) return;
+  if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
   // ---------------- 0b: column b of G_j and M_j for every j
   if (b < r)
     for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
-  if (!grid_barrier(w.bar, nb, err)) return;
+  if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
   const double* mu = w.wold;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int k = 0; k < d; ++k) {
@@ -720,18 +724,6 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
       // ---------------- A: Gamma_k (LDL^T) and row lp = b of W = Hs Gamma_k^-1
       if (b < r0) {
         const int lp = b;
-        if (b == 0 && tid == 0 && record) {
-          // record the previous mode's convergence measure (its sums are complete)
-          const double tn = w.acc2[0], td = w.acc2[1];
-          const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
-          const int sw = (k == 0) ? sweep - 1 : sweep;
-          if (htg_dgt_nn(ek, w.epsacc[sw])) w.epsacc[sw] = ek;
-          w.acc2[0] = 0.0;
-          w.acc2[1] = 0.0;
-        } else if (b == 0 && tid == 0) {
-          w.acc2[0] = 0.0;
-          w.acc2[1] = 0.0;
-        }
         // refresh the shared copies of G_j and of the rows lp of M_j^(p) that changed since
         // this CTA last read them: all at the start and after a damped Jacobi sweep, else those
         // of the mode updated last (Gauss-Seidel)
@@ -739,25 +731,43 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         if (k == 0 && (sweep == 0 || !gs)) j1 = d;
         else if (gs) { j0 = (k + d - 1) % d; j1 = j0 + 1; }
         const int nG = r * r, nM = 3 * r;
-        for (int e = tid; e < (j1 - j0) * (nG + nM); e += blockDim.x) {
-          const int j = j0 + e / (nG + nM), f = e % (nG + nM);
-          if (f < nG) {
-            Gs[j * nG + f] = w.G[(long long)j * w.rcap * w.rcap + f];
-          } else {
-            const int pp = (f - nG) / r, l = (f - nG) % r;
-            Mv[(j * 3 + pp) * r + l] = w.H[(long long)j * w.rycap * w.rcap + (pp * r0 + lp) + (long long)K * l];
+        for (int j = j0; j < j1; ++j) {
+          const double* Gg = w.G + (long long)j * w.rcap * w.rcap;
+          const double* Hg = w.H + (long long)j * w.rycap * w.rcap + lp;
+          for (int e = tid; e < nG + nM; e += blockDim.x) {
+            if (e < nG) {
+              Gs[j * nG + e] = Gg[e];
+            } else {
+              const int f = e - nG, pp = f / r, l = f - pp * r;
+              Mv[(j * 3 + pp) * r + l] = Hg[pp * r0 + (long long)K * l];
+            }
           }
         }
         __syncthreads();
-        // Gamma_k = hadamard_{j != k} G_j
-        for (int e = tid; e < nG; e += blockDim.x) {
-          double v = 1.0;
-          for (int j = 0; j < d; ++j)
-            if (j != k) v *= Gs[j * nG + e];
-          Lm[e] = v;
+        // side by side: Gamma_k = hadamard_{j != k} G_j (warps with index != 3 mod 4 but the
+        // last), the right-hand sides (the last warp), and in CTA 0 the convergence measure of
+        // the previous mode (its sums are complete), recorded off the critical path (warp 3)
+        const int wid = tid >> 5;
+        if (wid == NT / 32 - 1) {
+          rk2_rhs_row(Mv, d, k, r, mu[lp], hs, tid - (NT - 32), 32);
+        } else if (wid % 4 != 3) {
+          const int gt = (wid - wid / 4) * 32 + (tid & 31);
+          for (int e = gt; e < nG; e += (NT / 32 - 2) * 32) {
+            double v = 1.0;
+            for (int j = 0; j < d; ++j)
+              if (j != k) v *= Gs[j * nG + e];
+            Lm[e] = v;
+          }
+        } else if (b == 0 && tid == 96) {
+          if (record) {
+            const double tn = w.acc2[0], td = w.acc2[1];
+            const double ek = htg_dpos_finite(td) ? sqrt(tn / td) : sqrt(tn);
+            const int sw = (k == 0) ? sweep - 1 : sweep;
+            if (htg_dgt_nn(ek, w.epsacc[sw])) w.epsacc[sw] = ek;
+          }
+          w.acc2[0] = 0.0;
+          w.acc2[1] = 0.0;
         }
-        __syncthreads();
-        rk2_rhs_row(Mv, d, k, r, mu[lp], hs);
         __syncthreads();
         bool ok = ldlt_forward(Lm, hs, dinv, tri, r);
         if (!ok) {
@@ -781,7 +791,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
               if (j != k) v *= Gs[j * nG + e];
             Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
           }
-          rk2_rhs_row(Mv, d, k, r, mu[lp], hs);
+          rk2_rhs_row(Mv, d, k, r, mu[lp], hs, tid, blockDim.x);
           __syncthreads();
           ok = ldlt_forward(Lm, hs, dinv, tri, r);
         }
@@ -795,7 +805,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           w.Hh[(pp * r0 + lp) + (long long)K * l] = hs[e];
         }
       }
-      if (!grid_barrier(w.bar, nb, err)) return;
+      if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
       // ---------------- B: column b of X~_k = Z_k W, X_k[:, b], lam_b, and M_k[:, b]
       if (b < r) {
         const int n = a.n[k];
@@ -868,7 +878,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           __syncthreads();
         }
       }
-      if (!grid_barrier(w.bar, nb, err)) return;
+      if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
       // ---------------- C: column b of G_k = X_k^T X_k (all columns of X_k are final)
       if (gs && b < r) {
         const int n = a.n[k];
@@ -879,7 +889,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
         cols_dot([&](int o) { return Xs + (long long)ld * o; }, xb, n, r, pb, [&](int o, double v) { Gc[o] = v; });
       }
-      if (gs && !grid_barrier(w.bar, nb, err)) return;
+      if (gs && !grid_barrier(w.bar, nb, ++bseq, err)) return;
     }
     if (!gs) {
       // damped Jacobi update of every column b, then refresh all Grams
@@ -891,10 +901,10 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           for (int row = tid; row < n; row += blockDim.x) col[row] += 0.25 * (src[row] - col[row]);
         }
       }
-      if (!grid_barrier(w.bar, nb, err)) return;
+      if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
       if (b < r)
         for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
-      if (!grid_barrier(w.bar, nb, err)) return;
+      if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
     }
   }
   if (flops && b == 0 && tid == 0) {
@@ -1047,7 +1057,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   if (x->d != d || x_old->d != d || L->d != d || !L->kron_sum || L->n_terms != d) return HT_ERR_ARG;
   if (x->rank < 1 || x_old->rank < 1 || !x->weight || !x_old->weight) return HT_ERR_ARG;
   if (x->rank > w->rcap || x_old->rank > w->rcap || 3 * x_old->rank > w->rycap || x->rank > x->cap ||
-      x_old->rank > x_old->cap || x->rank > 64)
+      x_old->rank > x_old->cap || x->rank > 64 || x_old->rank > 64)
     return HT_ERR_CAPACITY;
   CpArgs a;
   memset(&a, 0, sizeof(a));
@@ -1086,7 +1096,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   }
   int launches = 0;
   htg_prof_begin(c, s);
-  cudaError_t e0 = cudaMemsetAsync(w->bar, 0, 2 * sizeof(unsigned int), s);
+  cudaError_t e0 = cudaMemsetAsync(w->bar, 0, 64 * sizeof(unsigned int), s);   // barrier words, one per CTA
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nblk);
   cfg.blockDim = dim3(NT);

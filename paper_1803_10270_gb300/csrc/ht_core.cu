@@ -746,7 +746,7 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
     for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
     const size_t cps[11] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
                             HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1,
-                            HT_MAXD * nmax * 3 * rc, 8};
+                            HT_MAXD * nmax * 3 * rc, 4 + 32};   // acc2 (4 doubles) + 64 barrier words
     for (int j = 0; j < 11; ++j) {
       W->off_cp[j] = off;
       off = align_up(off + cps[j] * sizeof(double));
