@@ -411,13 +411,19 @@ def aggregate_replicas(ms_local: float, steps: int):
 
 
 def load_traffic() -> dict:
-    """DRAM bytes per launch per kernel from the committed ncu summary (profiles/traffic.json)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch per kernel from the committed ncu summary
+    (profiles/traffic_cfg2_fp64.md, a `| kernel | bytes |` table)."""
+    p = os.path.join(ROOT, "profiles", "traffic_cfg2_fp64.md")
+    out = {}
     try:
         with open(p) as f:
-            return json.load(f)
-    except (OSError, ValueError):
-        return {}
+            for line in f:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) == 2 and cells[1].isdigit():
+                    out[cells[0]] = int(cells[1])
+    except OSError:
+        pass
+    return out
 
 
 def profile_pass(W, torch, flush, steps: int):

@@ -63,7 +63,8 @@ typedef enum ht_status {
 
 typedef enum ht_precision {
   HT_PREC_FP64 = 0,   /* every operation in FP64 */
-  HT_PREC_MIXED = 1   /* contractions and QR in FP32, node SVDs and thresholds in FP64 */
+  HT_PREC_MIXED = 1   /* accepted; runs the FP64 kernels (an FP32-contraction form drifted past a
+                         1e-6 relative error over 200 steps of the 6-D advection workload) */
 } ht_precision;
 
 /* ---------------------------------------------------------------- tensors ---- */
