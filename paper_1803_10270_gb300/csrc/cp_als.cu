@@ -408,6 +408,32 @@ __device__ void stage_pad(double* dst, int ldd, const double* src, int lds, int 
     dst[(e % un) + (long long)ldd * (e / un)] = src[(e % un) + (long long)lds * (e / un)];
 }
 
+// The same copy by asynchronous 8-byte copies (all in flight at once, no register staging);
+// row and column advance incrementally (no divisions).  Every thread must call stage_wait()
+// before the CTA barrier that publishes dst.  Reads through L1 are safe here: the grid barrier
+// ends with a device-scope fence on every SM before anything staged is read.
+__device__ void stage_pad_async(double* dst, int ldd, const double* src, int lds, int n, int cols) {
+  const int T = blockDim.x;
+  int row = threadIdx.x % n, col = threadIdx.x / n;
+  const int dr = T % n, dc = T / n;
+  while (col < cols) {
+    const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst + row + (long long)ldd * col);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + row + (long long)lds * col) : "memory");
+    row += dr;
+    col += dc;
+    if (row >= n) {
+      row -= n;
+      ++col;
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ inline void stage_async1(double* dst, const double* src) {
+  const unsigned int d = (unsigned int)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ inline void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Parts per output of a split dot product: as many as fill the CTA, at most 8.
 __device__ inline int dot_parts(int nout) { return (nout <= NT) ? htg_max(1, htg_min(NT / htg_max(nout, 1), 8)) : 1; }
 
@@ -478,8 +504,9 @@ __device__ void gram_column(const CpArgs& a, CpWs& w, int j, int b, int r0, bool
   int ld = n;
   if (stage) {
     ld = odd_ld(n);
-    stage_pad(stage, ld, a.X[j], n, n, r);
-    if (withM) stage_pad(stage + (long long)ld * r, ld, Zj, n, n, K);
+    stage_pad_async(stage, ld, a.X[j], n, n, r);
+    if (withM) stage_pad_async(stage + (long long)ld * r, ld, Zj, n, n, K);
+    stage_wait();
     Xsrc = stage;
     Zsrc = stage + (long long)ld * r;
   }
@@ -562,9 +589,9 @@ __device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 
 // the last warp, and the warps on that warp's SM partition (warp index 3 mod 4) take no other
 // work: the pivot chain (two FP64 operations, the reciprocal's seed and its correction) then
 // never waits behind other warps' FP64 instructions (anything else that runs meanwhile, even
-// loads, lengthens the steps).  Column j keeps a_ij = L_ij d_j.  A pivot that is not positive and
+// loads, lengthens the steps).  Column j keeps a_ij = L_ij d_j, Lsc receives L_ij.  A pivot that is not positive and
 // finite leaves dinv = 0 there; every thread sees it after the barrier and the result is false.
-__device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigned short* tri, int r) {
+__device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, const unsigned short* tri, int r) {
   const int tid = threadIdx.x, wid = tid >> 5;
   constexpr int PIV = NT - 32;              // the pivot thread: lane 0 of the last warp
   constexpr int NE = (NT / 32) * 3 / 4 * 32;   // element threads: the warps with wid % 4 != 3
@@ -587,7 +614,9 @@ __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigne
         if (e < ntri) {
           const unsigned int pr = tri[s0 + e];
           const int i = pr & 0xff, c = pr >> 8;
-          Lm[i + r * c] = fma(-(Lm[i + r * j] * dj), Lm[c + r * j], Lm[i + r * c]);
+          const double t = Lm[i + r * j] * dj;   // L_ij
+          Lm[i + r * c] = fma(-t, Lm[c + r * j], Lm[i + r * c]);
+          if (e < m - 1) Lsc[i + r * j] = t;    // the pairs of column j+1 come first
         } else {
           const int f = e - ntri, p = f / m, i = j + 1 + f % m;
           hs[p * r + i] = fma(-(Lm[i + r * j] * dj), hs[p * r + j], hs[p * r + i]);
@@ -596,7 +625,9 @@ __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigne
     } else if (tid == PIV && m > 0) {
       const int i = j + 1;
       const double a = Lm[i + r * j];
-      const double v = fma(-(a * dj), a, Lm[i + r * i]);
+      const double t = a * dj;
+      Lsc[i + r * j] = t;
+      const double v = fma(-t, a, Lm[i + r * i]);
       Lm[i + r * i] = v;
       dinv[i] = htg_dpos_finite(v) ? htg_rcp_fast(v) : 0.0;
     }
@@ -606,25 +637,26 @@ __device__ bool ldlt_forward(double* Lm, double* hs, double* dinv, const unsigne
 }
 
 // Back substitution D L^T w = z for the three right-hand sides (z in hs, overwritten by w):
-// w_i = (z_i - sum_{c > i} a_ci w_c) / d_i.  For r <= 32 warp p takes side p with lane i holding
-// z_i and the scaled column a_ci / d_c (c > i) in registers: no CTA barrier inside.
-__device__ void ldlt_back(const double* Lm, double* hs, const double* dinv, int r) {
+// w_i = z_i / d_i - sum_{c > i} L_ci w_c.  For r <= 32 warp p takes side p with lane i holding
+// w_i's running value and column i of L (from Lsc) in registers: no CTA barrier inside.
+// Otherwise a CTA-wide substitution on the unscaled columns: w_i = (z_i - sum a_ci w_c) / d_i.
+__device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const double* dinv, int r) {
   const int tid = threadIdx.x;
   if (r <= 32) {
     const int wp = tid >> 5, lane = tid & 31;
     if (wp < 3) {
-      double s = (lane < r) ? hs[wp * r + lane] : 0.0;
+      double s = (lane < r) ? hs[wp * r + lane] * dinv[lane] : 0.0;
       double col[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) col[c] = (c < r && lane < c) ? Lm[c + r * lane] * dinv[c] : 0.0;
+      for (int c = 0; c < 32; ++c) col[c] = (c < r && lane < c) ? Lsc[c + r * lane] : 0.0;
 #pragma unroll
       for (int c = 31; c >= 0; --c) {
         if (c < r) {
-          const double uc = __shfl_sync(0xffffffffu, s, c);
-          if (lane < c) s = fma(-col[c], uc, s);
+          const double wc = __shfl_sync(0xffffffffu, s, c);
+          if (lane < c) s = fma(-col[c], wc, s);
         }
       }
-      if (lane < r) hs[wp * r + lane] = s * dinv[lane];
+      if (lane < r) hs[wp * r + lane] = s;
     }
     __syncthreads();
     return;
@@ -643,7 +675,7 @@ __device__ void ldlt_back(const double* Lm, double* hs, const double* dinv, int 
 // Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage is optional.
 __host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z) {
   const long long ld = nmax | 1, K = 3LL * r0;
-  const long long base = (long long)r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
+  const long long base = 2LL * r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
                          (nmax > NT ? nmax : NT) + (long long)d * r * r + ld * r;
   return base + (with_z ? ld * K : 0);
 }
@@ -656,7 +688,8 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   const int nmax = w.nmax;
   extern __shared__ double sh[];
   double* Lm = sh;                           // r x r: Gamma_k, then its LDL^T factor
-  double* hs = Lm + r * r;                   // 3 r: right-hand sides, then row lp of W
+  double* Lsc = Lm + r * r;                  // r x r: L of the LDL^T factorisation
+  double* hs = Lsc + r * r;                  // 3 r: right-hand sides, then row lp of W
   double* dinv = hs + 3 * r;                 // r: reciprocal pivots
   double* xs = dinv + r;                     // nmax
   double* ys = xs + nmax;                    // max(nmax, 3 r0)
@@ -736,13 +769,15 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           const double* Hg = w.H + (long long)j * w.rycap * w.rcap + lp;
           for (int e = tid; e < nG + nM; e += blockDim.x) {
             if (e < nG) {
-              Gs[j * nG + e] = Gg[e];
+              stage_async1(Gs + j * nG + e, Gg + e);
             } else {
               const int f = e - nG, pp = f / r, l = f - pp * r;
-              Mv[(j * 3 + pp) * r + l] = Hg[pp * r0 + (long long)K * l];
+              stage_async1(Mv + (j * 3 + pp) * r + l, Hg + pp * r0 + (long long)K * l);
             }
           }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        stage_wait();
         __syncthreads();
         // side by side: Gamma_k = hadamard_{j != k} G_j (warps with index != 3 mod 4 but the
         // last), the right-hand sides (the last warp), and in CTA 0 the convergence measure of
@@ -769,7 +804,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           w.acc2[1] = 0.0;
         }
         __syncthreads();
-        bool ok = ldlt_forward(Lm, hs, dinv, tri, r);
+        bool ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r);
         if (!ok) {
           // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation (Section 2.1
           // regularisation of ill-conditioned ALS systems), and start over
@@ -793,12 +828,12 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           }
           rk2_rhs_row(Mv, d, k, r, mu[lp], hs, tid, blockDim.x);
           __syncthreads();
-          ok = ldlt_forward(Lm, hs, dinv, tri, r);
+          ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r);
         }
         if (!ok) {
           if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
         } else {
-          ldlt_back(Lm, hs, dinv, r);
+          ldlt_back(Lm, Lsc, hs, dinv, r);
         }
         for (int e = tid; e < 3 * r; e += blockDim.x) {
           const int pp = e / r, l = e % r;
@@ -814,19 +849,23 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         int ldz = n;
         if (zs_smem) {
           ldz = odd_ld(n);
-          stage_pad(Zs, ldz, Zg, n, n, K);
+          stage_pad_async(Zs, ldz, Zg, n, n, K);
           Zk = Zs;
         }
         const double* Wb = w.Hh + (long long)K * b;
-        for (int i = tid; i < K; i += blockDim.x) ys[i] = Wb[i];
+        for (int i = tid; i < K; i += blockDim.x) stage_async1(ys + i, Wb + i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // the old column (convergence sums) is fetched now, consumed after the contraction
+        double* col = a.X[k] + (long long)n * b;
+        const double old_pre = (tid < n) ? col[tid] : 0.0;
+        stage_wait();
         __syncthreads();
         rows_dot(Zk, ldz, ys, n, K, pb, xs);
         const double lam_old = a.lam[b];
-        double* col = a.X[k] + (long long)n * b;
         double num = 0.0, den = 0.0, nrm2 = 0.0;
         for (int row = tid; row < n; row += blockDim.x) {
           const double v = xs[row];
-          const double old = col[row] * (gs ? lam_old : 1.0);
+          const double old = (row == tid ? old_pre : col[row]) * (gs ? lam_old : 1.0);
           const double df = v - old;
           num = fma(df, df, num);
           den = fma(old, old, den);
@@ -883,7 +922,8 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
       if (gs && b < r) {
         const int n = a.n[k];
         const int ld = odd_ld(n);
-        stage_pad(Xs, ld, a.X[k], n, n, r);
+        stage_pad_async(Xs, ld, a.X[k], n, n, r);
+        stage_wait();
         __syncthreads();
         const double* xb = Xs + (long long)ld * b;
         double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
