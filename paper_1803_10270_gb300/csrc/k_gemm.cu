@@ -71,14 +71,27 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
         Bs[l2][j] = u;
       }
       __syncthreads();
+      if (l0 + BK <= g.k) {
 #pragma unroll
-      for (int l = 0; l < BK; ++l) {
-        const double a0 = As[l][ty], a1 = As[l][ty + 8];
-        const double b0 = Bs[l][tx], b1 = Bs[l][tx + 8];
-        acc[0][0] = fma(a0, b0, acc[0][0]);
-        acc[0][1] = fma(a0, b1, acc[0][1]);
-        acc[1][0] = fma(a1, b0, acc[1][0]);
-        acc[1][1] = fma(a1, b1, acc[1][1]);
+        for (int l = 0; l < BK; ++l) {
+          const double a0 = As[l][ty], a1 = As[l][ty + 8];
+          const double b0 = Bs[l][tx], b1 = Bs[l][tx + 8];
+          acc[0][0] = fma(a0, b0, acc[0][0]);
+          acc[0][1] = fma(a0, b1, acc[0][1]);
+          acc[1][0] = fma(a1, b0, acc[1][0]);
+          acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
+      } else {
+        // the ragged last slice: only its k - l0 terms (every FP64 warp instruction costs the
+        // same, padded or not)
+        for (int l = 0; l < g.k - l0; ++l) {
+          const double a0 = As[l][ty], a1 = As[l][ty + 8];
+          const double b0 = Bs[l][tx], b1 = Bs[l][tx + 8];
+          acc[0][0] = fma(a0, b0, acc[0][0]);
+          acc[0][1] = fma(a0, b1, acc[0][1]);
+          acc[1][0] = fma(a1, b0, acc[1][0]);
+          acc[1][1] = fma(a1, b1, acc[1][1]);
+        }
       }
       __syncthreads();
     }
@@ -105,9 +118,10 @@ cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cuda
                             long long inst_stride) {
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (ndesc > MAXD || count > 65535) return cudaErrorInvalidValue;
-  // 2 x SMs 64-thread CTAs in all (split over the instances of a batch): the grid-stride
-  // loop covers any item count
-  const int gx = htg_max(1, (grid / 2 + count - 1) / count);
+  // One instance: 2 x SMs 64-thread CTAs (grid = 4 x SMs), the grid-stride loop covers any
+  // item count.  A batch: instances differ in size, so each gets up to 16 CTAs, as many as
+  // stay resident together (32 CTAs of 64 threads per SM)
+  const int gx = (count == 1) ? htg_max(1, grid / 2) : htg_max(2, htg_min(16, (grid * 8 + count - 1) / count));
   gemm_kernel<<<dim3(gx, count), NT, 0, s>>>(descs_dev, inst_stride, ndesc, flops);
   return cudaGetLastError();
 }

@@ -24,7 +24,9 @@ __device__ inline double warp_sum(double v) {
   return v;
 }
 
-constexpr int QR_MAX_COLS = 4096;
+// Dynamic shared memory per CTA: 96 KB, so that two CTAs share an SM in batched launches; a
+// matrix that does not fit is reduced in its global scratch buffer (L2 resident).
+constexpr int QR_SMEM_BYTES = 96 * 1024;
 
 // Householder reflector of column j from x0 = S[j, j] and t = sum_{i > j} S[i, j]^2 (lane 0):
 // v = x - alpha e1 with alpha = -sign(x0) |x| stored over S[j, j], alpha into diag[j], and
@@ -56,13 +58,14 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
   // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
   const QrDesc q = ((const QrDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
   const int m = q.m, k = q.k;
-  if (m <= 0 || k <= 0 || k > QR_MAX_COLS) {
+  const int kd = (k + 1) & ~1;   // diagonal entries, rounded to keep the matrix 16-byte aligned
+  if (m <= 0 || k <= 0 || kd > smem_doubles) {
     if (threadIdx.x == 0 && q.rows_out) *q.rows_out = 0;
     return;
   }
-  extern __shared__ double diag[];   // min(m,k) values, then the matrix when it fits
+  extern __shared__ double diag[];   // the k diagonal entries of R, then the matrix when it fits
   const long long need = (long long)m * k;
-  double* S = (need <= smem_doubles - QR_MAX_COLS) ? diag + QR_MAX_COLS : q.scratch;
+  double* S = (need <= smem_doubles - kd) ? diag + kd : q.scratch;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
   // copy op(A) into S (m x k, column major)
   const long long mk = (long long)m * k;
@@ -137,12 +140,11 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(qr_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HTG_SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(qr_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  // diag[] (QR_MAX_COLS values) followed by the staged matrix when it fits
-  qr_r_kernel<<<dim3(ndesc, count), NT, HTG_SMEM_BYTES, s>>>(descs_dev, inst_stride,
-                                                               (long long)(HTG_SMEM_BYTES / sizeof(double)), flops);
+  qr_r_kernel<<<dim3(ndesc, count), NT, QR_SMEM_BYTES, s>>>(descs_dev, inst_stride,
+                                                              (long long)(QR_SMEM_BYTES / sizeof(double)), flops);
   return cudaGetLastError();
 }

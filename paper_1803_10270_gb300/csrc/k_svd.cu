@@ -338,6 +338,10 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (count > 65535) return cudaErrorInvalidValue;
   (void)use_smem;
+  // shared memory sized for p, q <= 40 (about 77 KB dynamic + 21 KB static: two CTAs per SM in
+  // batched launches); larger node factors work in their global buffers
+  pmax = htg_min(pmax, 40);
+  qmax = htg_min(qmax, 40);
   const int mr = htg_max(pmax, qmax);
   const size_t mp = (size_t)mr * pmax, pp = (size_t)pmax * pmax;
   size_t smem = (2 * mp + 3 * pp + pmax + (mp + 1) / 2 + (pp + 1) / 2 + 2) * sizeof(double);
