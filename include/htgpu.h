@@ -282,6 +282,15 @@ int cp_als_sweep_rk2(ht_ctx* ctx, const cp_tensor* x_old, const ht_op* L, double
 int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int variant, double* eps_dev,
                          int* status_dev, void* stream);
 
+/* ------------------------------------------------------------ diagnostics -- */
+/* Self-test of the bounded grid barrier that the persistent ALS kernel (cp_als_sweep_rk2) uses
+ * between its phases.  The paper has no counterpart.  Launches nblocks (1..64) cooperative CTAs
+ * on `device` that meet at one barrier; CTA `absent` (or none when absent < 0) skips it, so the
+ * others wait out the bounded limit (about 0.2 s of SM clock) and report instead of hanging.
+ * Synchronising (allocates and frees its own 2 KB).  Returns HT_OK when every CTA passed, the
+ * device-reported HT_ERR_TIMEOUT when the barrier gave up, or HT_ERR_ARG / HT_ERR_CUDA. */
+int ht_selftest_grid_barrier(int nblocks, int absent, int device);
+
 #ifdef __cplusplus
 }
 #endif

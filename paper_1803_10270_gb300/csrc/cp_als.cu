@@ -1217,6 +1217,44 @@ std::mutex g_na_mutex;
 
 }  // namespace
 
+namespace {
+// every CTA but `absent` meets at one grid barrier (sequence number 1)
+__global__ void selftest_barrier_kernel(unsigned int* flags, int absent, int* err) {
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(flags, gridDim.x, 1u, err);
+}
+}  // namespace
+
+extern "C" int ht_selftest_grid_barrier(int nblocks, int absent, int device) {
+  if (nblocks < 1 || nblocks > 64 || absent >= nblocks) return HT_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return HT_ERR_CUDA;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 2048) != cudaSuccess) return HT_ERR_CUDA;
+  unsigned int* flags = (unsigned int*)mem;
+  int* err = (int*)((char*)mem + 1024);
+  int st = HT_OK;
+  if (cudaMemset(mem, 0, 2048) != cudaSuccess) st = HT_ERR_CUDA;
+  if (st == HT_OK) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = 0;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, selftest_barrier_kernel, flags, absent, err) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      st = HT_ERR_CUDA;
+  }
+  int h = 0;
+  if (st == HT_OK && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) st = HT_ERR_CUDA;
+  cudaFree(mem);
+  return st != HT_OK ? st : h;
+}
+
 extern "C" int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int variant, double* eps_dev,
                                     int* status_dev, void* stream) {
   if (!x || !y || sweeps < 0 || sweeps > 64) return HT_ERR_ARG;

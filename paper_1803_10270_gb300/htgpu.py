@@ -88,6 +88,7 @@ _EXPORTS = {
                                    C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
 }
 
 _lib = None
@@ -472,3 +473,8 @@ def cp_als_sweep_noalloc(y: CPTensor, x: CPTensor, sweeps: int, variant: int = C
                                        C.c_void_p(eps.data_ptr() if eps is not None else 0),
                                        C.c_void_p(status.data_ptr() if status is not None else 0),
                                        _stream_ptr(stream)), "cp_als_sweep_noalloc")
+
+
+def selftest_grid_barrier(nblocks: int, absent: int = -1, device: int = 0) -> int:
+    """Status of one bounded grid barrier over nblocks CTAs with CTA `absent` missing (-1: none)."""
+    return int(load().ht_selftest_grid_barrier(nblocks, absent, device))
