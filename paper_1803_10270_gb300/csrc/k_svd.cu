@@ -98,6 +98,8 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   __shared__ int rotated;
   __shared__ int sh_e;        // scale = 2^sh_e
   __shared__ int ract;        // id of the last round with a rotation
+  __shared__ int nact;        // active rotations of the round (packed form)
+  int nrot = 0;               // rotations applied by this thread (flop count)
   __shared__ double red[NT / 32];
   __shared__ double sc_[HTG_SVD_MAXP];
   __shared__ double ss_[HTG_SVD_MAXP];
@@ -230,67 +232,92 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
       __syncthreads();
       for (int round = 0; round < p2 - 1; ++round) {
         const int rid = sweep * p2 + round + 1;
-        for (int pi = tid; pi < npairs; pi += NT) {
-          int a, b;
-          rr_pair(pi, round, p, p2, &a, &b);
-          int act = 0;
-          double c = 1.0, sn = 0.0;
-          if (a >= 0) {
-            const double al = G[a + (long long)p * a], be = G[b + (long long)p * b], ga = G[a + (long long)p * b];
-            // test and angle in FP32 on the entries scaled by 2^sh2 (|s M| <= 2), rescaled by
-            // exponent arithmetic; only c is refined in FP64, so each rotation is orthogonal to
-            // FP64 accuracy.  An entry outside the FP32 range means a column below the rounding
-            // floor (|s a|^2 < 2^-118, far below eps^2 |s M|_F^2) or a coupling below 2^-118:
-            // neither is rotated.
-            bool oka, okb, okg;
-            const float alf = htg_d2f_shift(al, sh2, &oka), bef = htg_d2f_shift(be, sh2, &okb);
-            const float gaf = htg_d2f_shift(ga, sh2, &okg);
-            // |ga| > TOL sqrt(al be), with the product formed so that it cannot underflow
-            // before the floor test below rejects the pair
-            const bool big = oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef);
-            if (big && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
-                (htg_dgt_nn(al, skip_abs) || htg_dgt_nn(be, skip_abs))) {
-              bool okd;
-              const float df = htg_d2f_shift(be - al, sh2, &okd);   // 0 when below the range
-              const float zf = df / (2.0f * gaf);
-              const float azf = fabsf(zf);
-              const double t =
-                  htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
-              c = htg_rsqrt_fast(fma(t, t, 1.0));
-              sn = c * t;
-              act = 1;
-              rotated = 1;
-              ract = rid;
-              myflops += 12.0 * p;
+        // angles: one thread per pair; with at most 32 pairs the active ones are packed into the
+        // first nact slots (warp ballot), so the update passes touch only their rows/columns
+        const bool packed = npairs <= 32;
+        if (!packed || tid < 32) {
+          for (int pi = tid; pi < (packed ? 32 : npairs); pi += NT) {
+            int a = -1, b = 0;
+            if (pi < npairs) rr_pair(pi, round, p, p2, &a, &b);
+            int act = 0;
+            double c = 1.0, sn = 0.0;
+            if (a >= 0) {
+              const double al = G[a + (long long)p * a], be = G[b + (long long)p * b], ga = G[a + (long long)p * b];
+              // test and angle in FP32 on the entries scaled by 2^sh2 (|s M| <= 2), rescaled by
+              // exponent arithmetic; only c is refined in FP64, so each rotation is orthogonal
+              // to FP64 accuracy.  An entry outside the FP32 range means a column below the
+              // rounding floor (|s a|^2 < 2^-118, far below eps^2 |s M|_F^2) or a coupling
+              // below 2^-118: neither is rotated.
+              bool oka, okb, okg;
+              const float alf = htg_d2f_shift(al, sh2, &oka), bef = htg_d2f_shift(be, sh2, &okb);
+              const float gaf = htg_d2f_shift(ga, sh2, &okg);
+              // |ga| > TOL sqrt(al be), with the product formed so that it cannot underflow
+              // before the floor test below rejects the pair
+              const bool big = oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef);
+              if (big && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
+                  (htg_dgt_nn(al, skip_abs) || htg_dgt_nn(be, skip_abs))) {
+                bool okd;
+                const float df = htg_d2f_shift(be - al, sh2, &okd);   // 0 when below the range
+                const float zf = df / (2.0f * gaf);
+                const float azf = fabsf(zf);
+                const double t =
+                    htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
+                c = htg_rsqrt_fast(fma(t, t, 1.0));
+                sn = c * t;
+                act = 1;
+                ++nrot;
+              }
+            }
+            if (packed) {
+              const unsigned int m = __ballot_sync(0xffffffffu, act);
+              if (act) {
+                const int pos = __popc(m & ((1u << tid) - 1u));
+                sc_[pos] = c;
+                ss_[pos] = sn;
+                act_[pos] = a | (b << 16);
+              }
+              if (tid == 0) {
+                nact = __popc(m);
+                if (m) {
+                  rotated = 1;
+                  ract = rid;
+                }
+              }
+            } else {
+              sc_[pi] = c;
+              ss_[pi] = sn;
+              act_[pi] = act ? (a | (b << 16)) : -1;
+              if (act) {
+                rotated = 1;
+                ract = rid;
+              }
             }
           }
-          sc_[pi] = c;
-          ss_[pi] = sn;
-          act_[pi] = act;
         }
         __syncthreads();
         if (ract != rid) continue;   // no rotation in this round (uniform after the barrier)
+        const int ns = packed ? nact : npairs;   // rotation slots
         // rows a, b of G
-        for (int e = tid; e < npairs * p; e += NT) {
-          const int pi = e / p, k = e % p;
-          if (!act_[pi]) continue;
-          int a, b;
-          rr_pair(pi, round, p, p2, &a, &b);
-          const double c = sc_[pi], sn = ss_[pi];
+        for (int e = tid; e < ns * p; e += NT) {
+          const int q = e / p, k = e - q * p;
+          const int ab = act_[q];
+          if (ab < 0) continue;
+          const int a = ab & 0xffff, b = ab >> 16;
+          const double c = sc_[q], sn = ss_[q];
           const double x = G[a + (long long)p * k], y = G[b + (long long)p * k];
           G[a + (long long)p * k] = c * x - sn * y;
           G[b + (long long)p * k] = sn * x + c * y;
         }
         __syncthreads();
-        // columns a, b of G (items e < npairs p) and of V (the rest), one rotation each
-        for (int e = tid; e < 2 * npairs * p; e += NT) {
-          const int isV = e >= npairs * p;
-          const int f = isV ? e - npairs * p : e;
-          const int pi = f / p, k = f % p;
-          if (!act_[pi]) continue;
-          int a, b;
-          rr_pair(pi, round, p, p2, &a, &b);
-          const double c = sc_[pi], sn = ss_[pi];
+        // columns a, b of G (items e < ns p) and of V (the rest), one rotation each
+        for (int e = tid; e < 2 * ns * p; e += NT) {
+          const int isV = e >= ns * p;
+          const int f = isV ? e - ns * p : e;
+          const int q = f / p, k = f - q * p;
+          const int ab = act_[q];
+          if (ab < 0) continue;
+          const int a = ab & 0xffff, b = ab >> 16;
+          const double c = sc_[q], sn = ss_[q];
           double* X = isV ? V : G;
           const double x = X[k + (long long)p * a], y = X[k + (long long)p * b];
           X[k + (long long)p * a] = c * x - sn * y;
@@ -316,6 +343,7 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
     if (lane == 0) nrm[c] = sqrt(s);
   }
   __syncthreads();
+  myflops += 12.0 * p * nrot;
   if (flops && myflops > 0.0) atomicAdd(flops, myflops);
   for (int c = wid; c < p; c += nw) {
     const double sc = nrm[c];
