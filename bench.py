@@ -288,10 +288,21 @@ def run_gpu(args):
 
     # ---- roofline: per-kernel-class CUDA-event time on the launching stream over a second
     #      timed region (same steps, L2 flushed, no graph so each launch can be bracketed)
-    roof, shares = profile_pass(W, torch, flush, min(args.steps, 50))
+    # the passes below replay the same stretch of the run as the timed region (the step
+    # cost changes as the solution's ranks evolve): restart from t = 0 before each
+    def restart():
+        W.reset()
+        W.first_step()
+        for _ in range(max(args.warmup - 1, 0)):
+            W.step()
+        torch.cuda.synchronize()
+
+    restart()
+    roof, shares = profile_pass(W, torch, flush, args.steps)
 
     # ---- e2e: state from pinned host memory each step, result back to the host
-    e2e = run_e2e(W, G, torch, min(args.steps, 50))
+    restart()
+    e2e = run_e2e(W, G, torch, args.steps)
     ranks = W.u.ranks()
 
     # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
@@ -458,63 +469,40 @@ def profile_pass(W, torch, flush, steps: int):
 
 
 def run_e2e(W, G, torch, steps: int) -> dict:
-    """Per step: pinned host -> device copy of the HT and CP state, ht_step + CP step, copy back."""
-    np = W.np
-    ubufs = [torch.empty(b.numel(), dtype=torch.float64, pin_memory=True) for b in W.u.bufs]
-    urank = torch.empty(W.u.rank_buf.numel(), dtype=torch.int32, pin_memory=True)
-    xbufs = [torch.empty(f.numel(), dtype=torch.float64, pin_memory=True) for f in W.X.factors]
-    xw = torch.empty(W.X.weight.numel(), dtype=torch.float64, pin_memory=True)
-    for h, d in zip(ubufs, W.u.bufs):
-        h.copy_(d)
-    urank.copy_(W.u.rank_buf)
-    for h, d in zip(xbufs, W.X.factors):
-        h.copy_(d)
-    xw.copy_(W.X.weight)
-    tr = W.u.tree
-
-    def used_sizes(rk):
-        sz = []
-        for t in range(tr.n_nodes):
-            if tr.is_leaf(t):
-                sz.append(N * rk[t])
-            else:
-                k1, k2 = rk[tr.c1[t]], rk[tr.c2[t]]
-                sz.append(k1 * k2 * (1 if t == 0 else rk[t]))
-        return sz
-
+    """Per step, through the same public calls: the HT and CP state (one contiguous buffer each,
+    at capacity, plus the HT ranks) copied from pinned host memory to the device, the step, and
+    the new state copied back to pinned host memory; the host waits for it every step.  The
+    copies and the step are captured together in one CUDA graph."""
+    hu = torch.empty(W.u.blob.numel(), dtype=torch.float64, pin_memory=True)
+    hr = torch.empty(W.u.rank_buf.numel(), dtype=torch.int32, pin_memory=True)
+    hx = torch.empty(W.X.blob.numel(), dtype=torch.float64, pin_memory=True)
+    hu.copy_(W.u.blob)
+    hr.copy_(W.u.rank_buf)
+    hx.copy_(W.X.blob)
     torch.cuda.synchronize()
-    rk = [int(v) for v in urank[: tr.n_nodes]]
-    h2d = d2h = 0
+
+    def one():
+        W.u.blob.copy_(hu, non_blocking=True)
+        W.u.rank_buf.copy_(hr, non_blocking=True)
+        W.X.blob.copy_(hx, non_blocking=True)
+        W.step()
+        hu.copy_(W.u.blob, non_blocking=True)
+        hr.copy_(W.u.rank_buf, non_blocking=True)
+        hx.copy_(W.X.blob, non_blocking=True)
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        one()
+    graph.replay()
+    torch.cuda.synchronize()
+    nbytes = hu.numel() * 8 + hr.numel() * 4 + hx.numel() * 8
     t0 = time.perf_counter()
     for _ in range(steps):
-        sz = used_sizes(rk)
-        W.u.rank_buf.copy_(urank, non_blocking=True)
-        h2d += urank.numel() * 4
-        for t, (h, d) in enumerate(zip(ubufs, W.u.bufs)):
-            d[: sz[t]].copy_(h[: sz[t]], non_blocking=True)
-            h2d += sz[t] * 8
-        for h, d in zip(xbufs, W.X.factors):
-            d.copy_(h, non_blocking=True)
-            h2d += h.numel() * 8
-        W.X.weight.copy_(xw, non_blocking=True)
-        h2d += xw.numel() * 8
-        W.step()
-        urank.copy_(W.u.rank_buf)       # synchronising: the new ranks size the copies below
-        d2h += urank.numel() * 4
-        rk = [int(v) for v in urank[: tr.n_nodes]]
-        sz = used_sizes(rk)
-        for t, (h, d) in enumerate(zip(ubufs, W.u.bufs)):
-            h[: sz[t]].copy_(d[: sz[t]], non_blocking=True)
-            d2h += sz[t] * 8
-        for h, d in zip(xbufs, W.X.factors):
-            h.copy_(d, non_blocking=True)
-            d2h += h.numel() * 8
-        xw.copy_(W.X.weight, non_blocking=True)
-        d2h += xw.numel() * 8
+        graph.replay()
         torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    return {"value": steps / el, "unit": "steps/s", "h2d_bytes_per_step": h2d // steps,
-            "d2h_bytes_per_step": d2h // steps, "steps": steps}
+    return {"value": steps / el, "unit": "steps/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": steps, "cuda_graph": True}
 
 
 def run_reference(args):

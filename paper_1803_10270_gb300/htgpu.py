@@ -224,15 +224,22 @@ class HTTensor:
         import torch
         self.d, self.n, self.cap = d, list(n), cap
         self.tree = tree_info(d)
-        self.bufs = []
+        # one device allocation (`blob`) holds every node buffer at 256-byte aligned offsets, so
+        # the whole state moves between host and device in one copy
+        sizes = []
         for t in range(self.tree.n_nodes):
             if self.tree.is_leaf(t):
-                sz = self.n[self.tree.lo[t]] * cap
+                sizes.append(self.n[self.tree.lo[t]] * cap)
             elif t == 0:
-                sz = cap * cap
+                sizes.append(cap * cap)
             else:
-                sz = cap ** 3
-            self.bufs.append(torch.zeros(sz, dtype=torch.float64, device=device))
+                sizes.append(cap ** 3)
+        offs, off = [], 0
+        for sz in sizes:
+            offs.append(off)
+            off += (sz + 31) // 32 * 32
+        self.blob = torch.zeros(off, dtype=torch.float64, device=device)
+        self.bufs = [self.blob[o:o + sz] for o, sz in zip(offs, sizes)]
         self.rank_buf = torch.ones(HT_MAXNODES, dtype=torch.int32, device=device)
         s = ht_tensor()
         s.d = d
@@ -282,8 +289,15 @@ class CPTensor:
     def __init__(self, d: int, n, cap: int, device="cuda"):
         import torch
         self.d, self.n, self.cap = d, list(n), cap
-        self.factors = [torch.zeros(v * cap, dtype=torch.float64, device=device) for v in self.n]
-        self.weight = torch.zeros(cap, dtype=torch.float64, device=device)
+        # factors and weights in one device allocation (`blob`), 256-byte aligned views
+        sizes = [v * cap for v in self.n] + [cap]
+        offs, off = [], 0
+        for sz in sizes:
+            offs.append(off)
+            off += (sz + 31) // 32 * 32
+        self.blob = torch.zeros(off, dtype=torch.float64, device=device)
+        views = [self.blob[o:o + sz] for o, sz in zip(offs, sizes)]
+        self.factors, self.weight = views[:-1], views[-1]
         s = cp_tensor()
         s.d = d
         for i, v in enumerate(self.n):
