@@ -184,8 +184,9 @@ int ht_apply(ht_ctx* ctx, const ht_tensor* u, const ht_op* L, double dt, int mod
  * (descending, zero padded; sig_stride >= the node's input rank).  norm_dev (device,
  * 1 double, or NULL) receives |u|.  When sigma_dev is NULL (and in ht_step / ht_batch_step)
  * the node SVDs leave unrotated any pair of columns whose squared norms are both below
- * 1e-6 (rel_tol |u|)^2 / (2d-3): every such column is discarded, and the discarded energy is
- * the trace of that block, which such rotations do not change, so ranks and T(u) are those of
+ * (rel_tol |u|)^2 / (2 p (2d-3)) (p columns in the node factor): together such columns hold at
+ * most half the truncation threshold, so all of them are discarded, and the discarded energy
+ * is the trace of that block, which such rotations do not change; ranks and T(u) are those of
  * the fully resolved SVDs.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
 int ht_truncate(ht_ctx* ctx, const ht_tensor* u, double rel_tol, int rmax, ht_tensor* out,
                 double* sigma_dev, int sig_stride, double* norm_dev, void* stream);

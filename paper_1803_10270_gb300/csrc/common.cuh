@@ -64,10 +64,11 @@ struct SvdDesc {
   double* U;
   double* work;
   int p, q, ldp;
-  // Pairs of columns whose squared norms are both below skip2 |P|_F^2 are not rotated against
-  // each other.  With skip2 |P|_F^2 p <= the truncation threshold (tol |u|)^2 / (2d-3) every such
-  // column is discarded by the rank rule, and the tail sums it enters are traces of that block,
-  // which rotations within the block do not change.  0: rotate every pair.
+  // Pairs of columns whose squared norms are both below skip2 |P|_F^2 / p are not rotated
+  // against each other.  With skip2 |P|_F^2 <= half the truncation threshold (tol |u|)^2 / (2d-3)
+  // those columns hold at most half the threshold together, so the rank rule discards all of
+  // them, and the tail sums they enter are traces of that block, which rotations within the
+  // block do not change.  0: rotate every pair.
   double skip2;
 };
 

@@ -251,9 +251,9 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
       SvdDesc& v = P->svd_all[t - 1];
       v.P = wn[t].P; v.p = P->Rp[t]; v.q = P->mE[t]; v.ldp = P->Rp[t];
       v.sigma = wn[t].sig; v.V = wn[t].W; v.U = wn[t].Z; v.work = wn[t].SW;
-      // |P_t|_F = |u|: columns with sigma^2 below 1e-6 (tol |u|)^2 / (2d-3) are discarded by
-      // the rank rule whatever their mutual rotation (see SvdDesc::skip2)
-      v.skip2 = 1e-6 * skip_tol * skip_tol / (double)htg_max(2 * T.d - 3, 1);
+      // |P_t|_F = |u|: with p columns, those with sigma^2 below (tol |u|)^2 / (2p (2d-3)) are
+      // discarded by the rank rule whatever their mutual rotation (see SvdDesc::skip2)
+      v.skip2 = 0.5 * skip_tol * skip_tol / (double)htg_max(2 * T.d - 3, 1);
     }
     for (int s = 0; s < L.n_int[dep]; ++s) {
       const int t = L.inter[dep][s], a = T.c1[t], b = T.c2[t];

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   // rotated (rotating them only reshuffles rounding noise and keeps the sweeps going)
   const double floor2 = EPS * EPS * red2[0];
   // pairs of columns both below the discard level stay unrotated (see SvdDesc::skip2)
-  const double skip_abs = D.skip2 * red2[0];
+  const double skip_abs = D.skip2 * red2[0] / (double)p;
   const float skip32 = htg_d2f(skip_abs * scale * scale);
   const float floor2_32 = htg_d2f(16.0 * 3.55e-15 * red2[0] * scale * scale);   // (4 eps32)^2 |M s|_F^2
   for (long long e = tid; e < mp; e += NT) M32[e] = htg_d2f(M[e] * scale);
