@@ -40,6 +40,11 @@ def rk2_steps(u: np.ndarray, c, h, dt: float, steps: int) -> np.ndarray:
     return u
 
 
+def ab2_step(u: np.ndarray, u_prev: np.ndarray, c, h, dt: float) -> np.ndarray:
+    """The two-step Adams-Bashforth scheme of eq. AB2_: u + dt (3/2 L u - 1/2 L u_prev)."""
+    return u + dt * (1.5 * apply_L(u, c, h) - 0.5 * apply_L(u_prev, c, h))
+
+
 def cp_to_full(weights, factors) -> np.ndarray:
     """sum_l w_l prod_k X_k[:, l] on the full grid (eq. functional-SSE)."""
     shape = tuple(f.shape[0] for f in factors)

@@ -130,43 +130,56 @@ _BINOM = [[1], [1, 1], [1, 2, 1]]
 _POLY = [1.0, 1.0, 0.5]   # p(z) = 1 + z + z^2/2
 
 
-def apply_kron_sum_rk2(ht: HT, A: list) -> HT:
-    """v = p(S) u with S = sum_i A_i (A_i acts on dimension i only), p(z)=1+z+z^2/2.
+def apply_kron_sum_poly(ht: HT, A: list, coeffs) -> HT:
+    """v = q(S) u with S = sum_i A_i (A_i acts on dimension i only) and
+    q(z) = sum_{j <= D} coeffs[j] z^j, D = len(coeffs) - 1 <= 2.
 
-    A[i] is the n_i x n_i matrix dt*L_i.  With S_t = sum_{i in t} A_i the node basis
-    of v is [U_t, S_t U_t, S_t^2 U_t]; since S_t = S_t1 + S_t2 with commuting summands,
+    A[i] is the n_i x n_i matrix dt*L_i.  With S_t = sum_{i in t} A_i the node basis of v is
+    [U_t, S_t U_t, .., S_t^D U_t]; since S_t = S_t1 + S_t2 with commuting summands,
     S_t^j U_t = sum_{j1+j2=j} C(j,j1) (S_t2^{j2} U_t2 kron S_t1^{j1} U_t1) B_t, so
-      leaf:     U'_i = [U_i, A_i U_i, A_i^2 U_i]                       (n_i x 3k)
-      interior: B'[(j1,a),(j2,b),(j,c)] = C(j,j1) [j = j1+j2] B[a,b,c]  (3k1 x 3k2 x 3k)
-      root:     B'[(j1,a),(j2,b)] = p_{j1+j2} C(j1+j2,j1) [j1+j2 <= 2] B[a,b]
-    with block index (j, c) -> j*k + c.  This is the structured sum of Section 3.2
-    (sums of HT tensors have block structure), taken exactly with no truncation.
+      leaf:     U'_i = [U_i, A_i U_i, .., A_i^D U_i]                      (n_i x (D+1)k)
+      interior: B'[(j1,a),(j2,b),(j,c)] = C(j,j1) [j = j1+j2] B[a,b,c]
+      root:     B'[(j1,a),(j2,b)] = coeffs[j1+j2] C(j1+j2,j1) [j1+j2 <= D] B[a,b]
+    with block index (j, c) -> j*k + c.  This is the structured sum of Section 3.2 (sums of HT
+    tensors have block structure), taken exactly with no truncation.
     """
+    D = len(coeffs) - 1
+    if not 0 <= D <= 2:
+        raise ValueError("degree 0..2")
+    nb = D + 1
     tr = ht.tree
     out = HT(tr, list(ht.n))
     for t in range(tr.n_nodes):
         X = ht.node[t]
         if tr.is_leaf(t):
             Ai = A[tr.lo[t]]
-            AX = Ai @ X
-            out.node[t] = np.hstack([X, AX, Ai @ AX])
+            cols = [X]
+            for _ in range(D):
+                cols.append(Ai @ cols[-1])
+            out.node[t] = np.hstack(cols)
         elif t == 0:
             k1, k2 = X.shape
-            Bn = np.zeros((3 * k1, 3 * k2))
-            for j1 in range(3):
-                for j2 in range(3 - j1):
+            Bn = np.zeros((nb * k1, nb * k2))
+            for j1 in range(nb):
+                for j2 in range(nb - j1):
                     j = j1 + j2
-                    Bn[j1 * k1:(j1 + 1) * k1, j2 * k2:(j2 + 1) * k2] = _POLY[j] * _BINOM[j][j1] * X
+                    Bn[j1 * k1:(j1 + 1) * k1, j2 * k2:(j2 + 1) * k2] = coeffs[j] * _BINOM[j][j1] * X
             out.node[t] = Bn
         else:
             k1, k2, k = X.shape
-            Bn = np.zeros((3 * k1, 3 * k2, 3 * k))
-            for j1 in range(3):
-                for j2 in range(3 - j1):
+            Bn = np.zeros((nb * k1, nb * k2, nb * k))
+            for j1 in range(nb):
+                for j2 in range(nb - j1):
                     j = j1 + j2
                     Bn[j1 * k1:(j1 + 1) * k1, j2 * k2:(j2 + 1) * k2, j * k:(j + 1) * k] = _BINOM[j][j1] * X
             out.node[t] = Bn
     return out
+
+
+def apply_kron_sum_rk2(ht: HT, A: list) -> HT:
+    """v = p(S) u with p(z) = 1 + z + z^2/2 (every two-stage order-2 Runge-Kutta method on a
+    linear ODE): apply_kron_sum_poly with coefficients (1, 1, 1/2), rank 3k."""
+    return apply_kron_sum_poly(ht, A, _POLY)
 
 
 def apply_separable(ht: HT, alphas: list, factors: list) -> HT:
@@ -415,6 +428,14 @@ def norm(u: HT) -> float:
 def step_rk2_poly(u: HT, A: list, rel_tol: float, rmax: int):
     """One step u <- T(p(dt L) u) for a Kronecker-sum operator (single truncation)."""
     return truncate(apply_kron_sum_rk2(u, A), rel_tol, rmax)
+
+
+def step_ab2(u: HT, u_prev: HT, A: list, rel_tol: float, rmax: int):
+    """The paper's explicit two-step scheme (eq. AB2_, Section 3.2) for a Kronecker-sum operator:
+    u_next = T(u + dt (3/2 L u - 1/2 L u_prev)) = T((1 + 3/2 S) u + (-1/2 S) u_prev) with
+    S = dt L, the sum formed exactly (ranks add, block-diagonal transfers) and truncated once."""
+    v = add(1.0, apply_kron_sum_poly(u, A, (1.0, 1.5)), 1.0, apply_kron_sum_poly(u_prev, A, (0.0, -0.5)))
+    return truncate(v, rel_tol, rmax)
 
 
 def step_heun2(u: HT, alphas: list, factors: list, dt: float, rel_tol: float, rmax: int):

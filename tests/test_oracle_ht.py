@@ -9,7 +9,8 @@ from oracle import fullgrid as FG
 from oracle import ht as H
 from oracle.tree import build_tree
 from paper_1803_10270_gb300.inputs import advection_case, normal_arrays
-from tests.closed_forms import apply_node_projector, fourier_rk2, matricize
+from oracle.problems import advection_A
+from tests.closed_forms import apply_node_projector, fourier_ab2, fourier_rk2, matricize
 
 
 def random_ht(d, n, rank, seed, leaf_rank=None):
@@ -234,3 +235,53 @@ def test_heun2_matches_full_grid_rk2_without_truncation():
 
 def _ht_of(f, like):
     return like
+
+
+def test_apply_poly_matches_full_grid_polynomial():
+    """apply_kron_sum_poly == q(dt L) on the full grid for degree 0, 1, 2 coefficient sets."""
+    d, n = 4, 6
+    case = advection_case(d, n, seed=51)
+    A = advection_A(case)
+    u = random_ht(d, n, 3, seed=52)
+    full = H.to_full(u)
+    Lu = FG.apply_L(full, case.c, case.h)
+    LLu = FG.apply_L(Lu, case.c, case.h)
+    for q in [(0.7,), (1.0, 1.5), (0.0, -0.5), (1.0, 1.0, 0.5), (0.3, -2.0, 0.25)]:
+        want = q[0] * full
+        if len(q) > 1:
+            want = want + q[1] * case.dt * Lu
+        if len(q) > 2:
+            want = want + q[2] * case.dt ** 2 * LLu
+        got = H.to_full(H.apply_kron_sum_poly(u, A, q))
+        assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_ab2_full_grid_matches_fourier_recurrence():
+    """The full-grid AB2 stepper reproduces the per-mode two-step recurrence (eq. AB2_)."""
+    d, n = 3, 8
+    case = advection_case(d, n, seed=53)
+    u0 = H.to_full(H.from_cp(np.ones(2), case.ic_factors()))
+    u1 = FG.rk2_step(u0, case.c, case.h, case.dt)
+    a, b = u0, u1
+    for _ in range(5):
+        a, b = b, FG.ab2_step(b, a, case.c, case.h, case.dt)
+    want = fourier_ab2(u0, u1, case.c, case.h, case.dt, 5)
+    assert np.abs(b - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_ab2_ht_step_untruncated_matches_full_grid():
+    """step_ab2 with tol 0 and a rank cap above the exact rank equals the full-grid AB2 step;
+    with a tolerance it stays within the HSVD bound of the exact sum."""
+    d, n = 4, 6
+    case = advection_case(d, n, seed=54)
+    A = advection_A(case)
+    u0 = H.from_cp(np.ones(2), case.ic_factors())
+    u1, _ = H.step_rk2_poly(u0, A, 0.0, 64)
+    u2, rep = H.step_ab2(u1, u0, A, 0.0, 64)
+    want = FG.ab2_step(H.to_full(u1), H.to_full(u0), case.c, case.h, case.dt)
+    got = H.to_full(u2)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+    tol = 1e-4
+    u2t, rep = H.step_ab2(u1, u0, A, tol, 64)
+    err = np.linalg.norm(H.to_full(u2t) - want)
+    assert err <= tol * np.linalg.norm(want) * (1 + 1e-9)
