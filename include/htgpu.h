@@ -226,6 +226,15 @@ void ht_batch_destroy(ht_batch* b);
 int ht_batch_step(ht_batch* b, const ht_op* const* Ls, const double* dts, const double* rel_tols,
                   const int* rmaxs, int scheme, void* stream);
 
+/* The paper's two-step explicit scheme (eq. AB2_, Section 3.2) for Kronecker-sum operators:
+ * u_next = T(u + dt (3/2 L u - 1/2 L u_prev)) = T((1 + 3/2 dt L) u + (-1/2 dt L) u_prev), the sum
+ * formed exactly (rank 2k + 2k_prev, block-diagonal transfers) and truncated once as in
+ * ht_truncate; then u_prev <- u and u <- u_next, in place.  u and u_prev: distinct buffers
+ * and rank arrays, equal capacity.  Start a run with u_prev = u_0 and u = one ht_step of u_0.
+ * The context needs a truncation input of 4 cap (max_terms >= 2).  Errors as ht_step. */
+int ht_step_ab2(ht_ctx* ctx, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, double dt, double rel_tol,
+                int rmax, void* stream);
+
 /* Exact HT form of a CP tensor (footnote to eq. HTD: a CP tensor is the diagonal case):
  * leaves = factors, interior B = delta_abc, root = diag(weights).  out->cap >= x->rank. */
 int ht_from_cp(ht_ctx* ctx, const cp_tensor* x, ht_tensor* out, void* stream);

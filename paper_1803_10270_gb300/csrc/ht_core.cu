@@ -303,6 +303,7 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
   }
   __syncthreads();
   const double thr2 = s_thr2;
+  const double sfloor = 64.0 * 2.220446049250313e-16 * P->norm;
   for (int t = 1 + threadIdx.x; t < T.nn; t += blockDim.x) {
     const int src = (t == rb) ? ra : t;
     const double* s = wn[src].sig;
@@ -316,6 +317,13 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
       tail = fma(s[kk - 1], s[kk - 1], tail);
     }
     // (loop above walks kk downward while tail(kk) <= thr2)
+    // singular values at the rounding level of |u| are never kept, whatever the tolerance:
+    // their vectors are rounding noise, which Y = E Z S^-1 would amplify (dropping them changes
+    // T(u) at that level only)
+    int knz = 0;
+    for (int j = 0; j < p; ++j)
+      if (htg_dgt_nn(s[j], sfloor)) knz = j + 1;
+    k = htg_min(k, htg_max(1, knz));
     k = htg_max(1, htg_min(k, rmax));
     k = htg_min(k, P->Rp[t]);
     P->knew[t] = k;
@@ -412,11 +420,18 @@ constexpr int MAXBLK = HT_MAXBLOCKTERMS + 2;   // identity + terms (+ the stage 
 // Block-diagonal assembly: block b of the result is F_b applied to source tensor src[b]
 // (0 or 1) with root weight coef[b].  RK2POLY instead uses the binomial block pattern of
 // a single source with factor f[0][dim] = dt * L_dim.
+// mode APPLY_POLY: sum over npoly sources s of q_s(S) u_s, q_s(z) = sum_{j <= deg[s]} pc[s][j] z^j,
+// S = sum_i f[0][i] (a Kronecker sum, the 1-D factors dt L_i): the exact form with the binomial
+// block pattern (HT_APPLY_RK2POLY is the one-source case with q = 1 + z + z^2/2).
+constexpr int APPLY_POLY = 100;
 struct ApplyOp {
-  int nb;                            // number of blocks
-  int mode;                          // HT_APPLY_RK2POLY or blockdiag (any other value)
+  int nb;                            // number of blocks (block-diagonal modes)
+  int mode;                          // APPLY_POLY or block diagonal (any other value)
   int src[MAXBLK];
   double coef[MAXBLK];
+  int npoly;                         // APPLY_POLY: sources (1 or 2, views in0 / in1)
+  int deg[2];
+  double pc[2][3];
   ApplyFactor f[MAXBLK][HT_MAXD];
 };
 
@@ -451,27 +466,36 @@ __device__ void apply_leaf_body(const ApplyOp& op, const TreeInfo& T, const Leve
   double* x = sh;          // n
   double* y = sh + n;      // n
   __shared__ double red[32];
-  if (op.mode == HT_APPLY_RK2POLY) {
-    const int K = in0.rank[leaf];
+  if (op.mode == APPLY_POLY) {
+    // columns [U_s, A U_s, .., A^deg_s U_s] of every source s, one after the other
     const ApplyFactor& F = op.f[0][dim];
-    for (int c = blockIdx.x; c < K; c += gridDim.x) {
-      const double* src = in0.node[leaf] + (long long)n * c;
-      for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = src[j];
-      __syncthreads();
-      double* o0 = out.node[leaf] + (long long)n * c;
-      double* o1 = out.node[leaf] + (long long)n * (K + c);
-      double* o2 = out.node[leaf] + (long long)n * (2 * K + c);
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const double v = apply_factor_at(F, x, n, j, 0.0);
-        y[j] = v;
-        o0[j] = x[j];
-        o1[j] = v;
+    int off = 0;
+    for (int sidx = 0; sidx < op.npoly; ++sidx) {
+      const HtView& sv = sidx == 0 ? in0 : in1;
+      const int K = sv.rank[leaf], dg = op.deg[sidx];
+      for (int c = blockIdx.x; c < K; c += gridDim.x) {
+        const double* src = sv.node[leaf] + (long long)n * c;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = src[j];
+        __syncthreads();
+        double* o0 = out.node[leaf] + (long long)n * (off + c);
+        double* o1 = out.node[leaf] + (long long)n * (off + K + c);
+        double* o2 = out.node[leaf] + (long long)n * (off + 2 * K + c);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          o0[j] = x[j];
+          if (dg >= 1) {
+            const double v = apply_factor_at(F, x, n, j, 0.0);
+            y[j] = v;
+            o1[j] = v;
+          }
+        }
+        __syncthreads();
+        if (dg >= 2)
+          for (int j = threadIdx.x; j < n; j += blockDim.x) o2[j] = apply_factor_at(F, y, n, j, 0.0);
+        __syncthreads();
       }
-      __syncthreads();
-      for (int j = threadIdx.x; j < n; j += blockDim.x) o2[j] = apply_factor_at(F, y, n, j, 0.0);
-      __syncthreads();
+      off += (dg + 1) * K;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out.rank[leaf] = 3 * K;
+    if (blockIdx.x == 0 && threadIdx.x == 0) out.rank[leaf] = off;
     return;
   }
   int off = 0;
@@ -520,13 +544,21 @@ __device__ void apply_xfer_body(const ApplyOp& op, const TreeInfo& T, const Leve
   const int t = L.proj2[blockIdx.y];   // interior nodes and the root
   const int a = T.c1[t], b = T.c2[t];
   int oa[MAXBLK + 1], ob[MAXBLK + 1], ot[MAXBLK + 1];
+  int bs[MAXBLK], bj[MAXBLK];   // APPLY_POLY: source and power of each block
   int nb = op.nb;
-  if (op.mode == HT_APPLY_RK2POLY) {
-    nb = 3;
-    for (int j = 0; j <= 3; ++j) {
-      oa[j] = j * in0.rank[a];
-      ob[j] = j * in0.rank[b];
-      ot[j] = (t == 0) ? j : j * in0.rank[t];
+  if (op.mode == APPLY_POLY) {
+    nb = 0;
+    oa[0] = ob[0] = ot[0] = 0;
+    for (int sidx = 0; sidx < op.npoly; ++sidx) {
+      const HtView& sv = sidx == 0 ? in0 : in1;
+      for (int j = 0; j <= op.deg[sidx]; ++j) {
+        bs[nb] = sidx;
+        bj[nb] = j;
+        oa[nb + 1] = oa[nb] + sv.rank[a];
+        ob[nb + 1] = ob[nb] + sv.rank[b];
+        ot[nb + 1] = ot[nb] + (t == 0 ? 1 : sv.rank[t]);
+        ++nb;
+      }
     }
   } else {
     oa[0] = ob[0] = ot[0] = 0;
@@ -549,15 +581,21 @@ __device__ void apply_xfer_body(const ApplyOp& op, const TreeInfo& T, const Leve
     const int j1 = find_block(oa, nb, i1, &aa);
     const int j2 = find_block(ob, nb, i2, &bb);
     double v = 0.0;
-    if (op.mode == HT_APPLY_RK2POLY) {
-      const int K1 = in0.rank[a], K2 = in0.rank[b];
-      if (t == 0) {
-        const int j = j1 + j2;
-        if (j <= 2) v = (j == 2 ? 0.5 : 1.0) * binom3(j, j1) * in0.node[0][aa + (long long)K1 * bb];
-      } else {
-        const int j3 = find_block(ot, nb, i3, &cc);
-        if (j1 + j2 == j3)
-          v = binom3(j3, j1) * in0.node[t][aa + (long long)K1 * (bb + (long long)K2 * cc)];
+    if (op.mode == APPLY_POLY) {
+      // blocks j1, j2 (j3) are (source, power) pairs: nonzero only within one source, with
+      // power(j3) = power(j1) + power(j2) (root: the polynomial coefficient of that power)
+      const int sidx = bs[j1];
+      if (bs[j2] == sidx) {
+        const HtView& sv = sidx == 0 ? in0 : in1;
+        const int K1 = sv.rank[a], K2 = sv.rank[b];
+        const int p1 = bj[j1], p2 = bj[j2], pw = p1 + p2;
+        if (t == 0) {
+          if (pw <= op.deg[sidx]) v = op.pc[sidx][pw] * binom3(pw, p1) * sv.node[0][aa + (long long)K1 * bb];
+        } else {
+          const int j3 = find_block(ot, nb, i3, &cc);
+          if (bs[j3] == sidx && bj[j3] == pw)
+            v = binom3(pw, p1) * sv.node[t][aa + (long long)K1 * (bb + (long long)K2 * cc)];
+        }
       }
     } else if (j1 == j2) {
       const HtView& sv = op.src[j1] == 0 ? in0 : in1;
@@ -1055,6 +1093,13 @@ static bool build_apply(const ht_ctx* c, const ht_op* L, double dt, int mode, Ap
         if (j != i && L->f[i][j].kind != HT_F_IDENTITY) return false;
       if (!conv(L->f[i][i], dt * L->alpha[i], &op->f[0][i])) return false;
     }
+    // p(z) = 1 + z + z^2/2 of one source
+    op->mode = APPLY_POLY;
+    op->npoly = 1;
+    op->deg[0] = 2;
+    op->pc[0][0] = 1.0;
+    op->pc[0][1] = 1.0;
+    op->pc[0][2] = 0.5;
     op->nb = 3;
     return true;
   }
@@ -1156,6 +1201,34 @@ extern "C" int ht_step(ht_ctx* c, ht_tensor* u, const ht_op* L, double dt, doubl
     return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
   }
   return HT_ERR_ARG;
+}
+
+extern "C" int ht_step_ab2(ht_ctx* c, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, double dt, double rel_tol,
+                           int rmax, void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, u_prev) || u->cap != u_prev->cap) return HT_ERR_ARG;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (u->node[t] == u_prev->node[t]) return HT_ERR_ARG;
+  if (u->rank == u_prev->rank) return HT_ERR_ARG;
+  if (rmax < 1 || rmax > u->cap || !(rel_tol >= 0.0)) return HT_ERR_ARG;
+  if (u->cap > c->cap || 4LL * u->cap > c->Kc) return HT_ERR_CAPACITY;
+  ApplyOp op;
+  if (!build_apply(c, L, dt, HT_APPLY_RK2POLY, &op)) return HT_ERR_ARG;   // the factors dt L_i
+  // (1 + 3/2 S) u + (-1/2 S) u_prev, S = dt L (eq. AB2_)
+  op.npoly = 2;
+  op.deg[0] = op.deg[1] = 1;
+  op.pc[0][0] = 1.0;
+  op.pc[0][1] = 1.5;
+  op.pc[1][0] = 0.0;
+  op.pc[1][1] = -0.5;
+  op.pc[0][2] = op.pc[1][2] = 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  HtView uv = view_of(u);
+  HtView app = view_ws(c, c->app, c->app_rank);
+  int st = launch_apply(c, op, uv, view_of(u_prev), app, u->cap, s);
+  if (st != HT_OK) return st;
+  st = copy_tensor_to(c, u, u_prev->node, u_prev->rank, s);   // u_prev <- u (u is read no more)
+  if (st != HT_OK) return st;
+  return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
 }
 
 // ---------------------------------------------------------------- batches -----

@@ -77,6 +77,8 @@ _EXPORTS = {
     "ht_batch_destroy": (None, [C.c_void_p]),
     "ht_batch_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+    "ht_step_ab2": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.POINTER(ht_op), C.c_double,
+                              C.c_double, C.c_int, C.c_void_p]),
     "ht_from_cp": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_tensor), C.c_void_p]),
     "ht_mass": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
     "ht_inner": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
@@ -445,6 +447,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def ht_step_ab2(ctx: Context, u: HTTensor, u_prev: HTTensor, op: ht_op, dt: float, rel_tol: float, rmax: int,
+                stream=None):
+    _check(load().ht_step_ab2(ctx.ptr, C.byref(u.struct), C.byref(u_prev.struct), C.byref(op), dt, rel_tol, rmax,
+                              _stream_ptr(stream)), "ht_step_ab2")
 
 
 def ht_from_cp(ctx: Context, x: CPTensor, out: HTTensor, stream=None):
