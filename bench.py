@@ -305,6 +305,9 @@ def run_gpu(args):
     e2e = run_e2e(W, G, torch, args.steps)
     ranks = W.u.ranks()
 
+    # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
+    ab2 = run_ab2(G, torch, flush, args.steps, args.warmup)
+
     # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
     batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
         if args.batched > 0 else None
@@ -323,6 +326,7 @@ def run_gpu(args):
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_shares": shares,
         }
+        out["ab2"] = ab2
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -350,6 +354,45 @@ def ic_nodes(tree, fac, np):
             B[0, 0, 0] = B[1, 1, 1] = 1.0
             nodes[t] = B
     return nodes
+
+
+def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
+    """HT steps/s of the AB2 scheme (ht_step_ab2) on the configuration-2 advection workload: an
+    RK2 start step, then AB2 steps, the timed ones graph-captured with L2 flushed between them."""
+    import numpy as np
+    from paper_1803_10270_gb300.inputs import advection_case
+    case = advection_case(D, N, cfg_index=1)
+    ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=2)
+    u = G.HTTensor(D, [N] * D, RMAX)
+    up = G.HTTensor(D, [N] * D, RMAX)
+    nodes = ic_nodes(u.tree, case.ic_factors(), np)
+    u.upload(nodes)
+    up.upload(nodes)
+    op = G.advection_op(case.c, case.h)
+    G.ht_step(ctx, u, op, case.dt, TOL, RMAX)       # u_1; u_prev = u_0
+    for _ in range(max(warmup - 1, 0)):
+        G.ht_step_ab2(ctx, u, up, op, case.dt, TOL, RMAX)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        G.ht_step_ab2(ctx, u, up, op, case.dt, TOL, RMAX, stream=torch.cuda.current_stream())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max, value = aggregate_replicas(ms, steps)
+    ranks = u.ranks()
+    del graph
+    ctx.close()
+    return {"workload": "6-D advection n=64 (cfg2) HT route, AB2 (eq. AB2_) after one RK2 start step, "
+                        "r_max 32, tol 1e-8", "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+            "steps": steps, "ht_ranks_final": ranks, "cuda_graph": True}
 
 
 def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:
