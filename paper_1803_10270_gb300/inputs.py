@@ -179,6 +179,35 @@ class KineticCase:
         return 0.2 * self.hx / 6.0
 
 
+def kinetic_ic(kc: "KineticCase", seed: int | None = None, n_pert: int = 4, amp: float = 1e-2):
+    """CP form (weights, factors) of the kinetic initial condition on (x1,x2,x3,v1,v2,v3):
+    f0 = M(v) (1 + 0.1 prod_i sin(x_i)) plus a seeded rank-n_pert perturbation whose x-factors
+    are band-limited (Fourier modes |k| <= 2) and whose v-factors are m(v) times a polynomial of
+    degree <= 2 (splitmix64 coefficients in [-1, 1]); each perturbation term is scaled to
+    max-norm amp.  M = m^(x3) with the case's discretely normalised Maxwellian m."""
+    g = SplitMix64(kc.seed + 7 if seed is None else seed)
+    x, v, m = kc.xgrid(), kc.vgrid(), kc.maxwellian()
+    ones = np.ones_like(x)
+    weights = [1.0, 0.1]
+    factors = [[ones, ones, ones, m, m, m], [np.sin(x), np.sin(x), np.sin(x), m, m, m]]
+    for _ in range(n_pert):
+        fs = []
+        for _i in range(3):
+            f = np.zeros_like(x)
+            for k in range(3):
+                a, b = g.uniform_range(-1.0, 1.0), g.uniform_range(-1.0, 1.0)
+                f = f + a * np.cos(k * x) + b * np.sin(k * x)
+            fs.append(f)
+        for _i in range(3):
+            c0, c1, c2 = (g.uniform_range(-1.0, 1.0) for _ in range(3))
+            fs.append(m * (c0 + c1 * v + c2 * v * v))
+        scale = float(np.prod([np.abs(f).max() for f in fs]))
+        weights.append(amp / scale if scale > 0 else 0.0)
+        factors.append(fs)
+    F = [np.stack([t[i] for t in factors], axis=1) for i in range(6)]
+    return np.array(weights), F
+
+
 def kinetic_case(n: int, nu: float = 1.0, seed: int | None = None, cfg_index: int = 2) -> KineticCase:
     if seed is None:
         seed = SEED_BASE + cfg_index

@@ -127,3 +127,25 @@ def test_config2_full_size_mass_bound(G):
         m1 = float(m[0])
         assert abs(m1 - m0) <= math.sqrt(64.0 ** 6) * 1e-8 * nrm * 1.01
         m0 = m1
+
+
+def test_kinetic_config3_shape_heun2(G):
+    """Linearised 6-D kinetic equation (x periodic, v in [-6, 6]) with its initial condition
+    M(v)(1 + 0.1 prod sin x_i) plus a seeded rank-4 perturbation, n = 12, HEUN2 with a
+    truncation after each stage, r_max 12, tol 1e-6: three steps against the oracle."""
+    from oracle.problems import kinetic_terms
+    from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+    kc = kinetic_case(12)
+    w, F = kinetic_ic(kc)
+    u = OH.from_cp(w, F)
+    alphas, factors = kinetic_terms(kc)
+    kop = G.KineticOp(kc)
+    ctx = G.Context(6, [12] * 6, cap=12, max_terms=5)
+    g = to_gpu(G, u, 12)
+    for step in range(3):
+        u, reps = OH.step_heun2(u, alphas, factors, kc.dt, 1e-6, 12)
+        G.ht_step(ctx, g, kop.op, kc.dt, 1e-6, 12, scheme=G.HT_SCHEME_HEUN2)
+        sync()
+        ctx.check()
+        assert g.ranks() == reps[1].ranks, f"step {step}"
+        assert rel_err(from_gpu(g, u.tree), u) < TOL64, f"step {step}"
