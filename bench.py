@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--no-graph", action="store_true", help="launch every kernel per step instead of a CUDA graph")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
+    p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -308,6 +309,9 @@ def run_gpu(args):
     # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
     ab2 = run_ab2(G, torch, flush, args.steps, args.warmup)
 
+    # ---- the 12-D workload (n = 128, r_max 64, depth-4 tree), HT route alone, 100 RK2 steps
+    d12 = run_d12(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
+
     # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
     batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
         if args.batched > 0 else None
@@ -327,6 +331,8 @@ def run_gpu(args):
             "roofline": roof, "kernel_shares": shares,
         }
         out["ab2"] = ab2
+        if d12 is not None:
+            out["d12"] = d12
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -342,16 +348,18 @@ BATCH_WORKLOAD = ("ragged batch (cfg4): independent 6-D advection instances, n i
 
 
 def ic_nodes(tree, fac, np):
-    """Exact rank-2 HT form of the two-term separable initial condition."""
+    """Exact rank-R HT form of an R-term separable initial condition (fac[i] is n x R)."""
+    R = fac[0].shape[1]
     nodes = {}
     for t in range(tree.n_nodes):
         if tree.is_leaf(t):
             nodes[t] = fac[tree.lo[t]]
         elif t == 0:
-            nodes[t] = np.eye(2)
+            nodes[t] = np.eye(R)
         else:
-            B = np.zeros((2, 2, 2))
-            B[0, 0, 0] = B[1, 1, 1] = 1.0
+            B = np.zeros((R, R, R))
+            for m in range(R):
+                B[m, m, m] = 1.0
             nodes[t] = B
     return nodes
 
@@ -393,6 +401,48 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
     return {"workload": "6-D advection n=64 (cfg2) HT route, AB2 (eq. AB2_) after one RK2 start step, "
                         "r_max 32, tol 1e-8", "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
             "steps": steps, "ht_ranks_final": ranks, "cuda_graph": True}
+
+
+D12_WORKLOAD = ("12-D advection n=128 (cfg5): depth-4 tree, seeded separable rank-3 initial condition, "
+                "HT r_max 64, tol 1e-8, RK2 dt=0.2h, FP64 throughout")
+
+
+def run_d12(G, torch, flush, steps: int, warmup: int) -> dict:
+    """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
+    64): the timed steps graph-captured, L2 flushed between them."""
+    import numpy as np
+    from paper_1803_10270_gb300.inputs import advection_case
+    d, n, cap = 12, 128, 64
+    case = advection_case(d, n, n_terms=3, cfg_index=4)
+    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1)
+    u = G.HTTensor(d, [n] * d, cap)
+    u.upload(ic_nodes(u.tree, case.ic_factors(), np))
+    op = G.advection_op(case.c, case.h)
+    for _ in range(warmup):
+        G.ht_step(ctx, u, op, case.dt, TOL, cap)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    l0 = ctx.launches()
+    with torch.cuda.graph(graph):
+        G.ht_step(ctx, u, op, case.dt, TOL, cap, stream=torch.cuda.current_stream())
+    per_step = ctx.launches() - l0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max, value = aggregate_replicas(ms, steps)
+    ranks = u.ranks()
+    del graph
+    ctx.close()
+    return {"workload": D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step,
+            "ht_ranks_final": ranks, "cuda_graph": True}
 
 
 def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:

@@ -206,7 +206,10 @@ int ht_step(ht_ctx* ctx, ht_tensor* u, const ht_op* L, double dt, double rel_tol
  * with the same d and so the same dimension tree.  Every launch of a batched step covers all
  * instances: the planner, each level's QRs and contractions, the node SVDs, the rank choice and
  * the projections run once per step for the whole batch (instance = a grid dimension), so the
- * per-instance results are those of ht_step on that instance.
+ * per-instance results are those of ht_step on that instance: bit for bit while a launch's
+ * matrices (instances x matrices of a tree level) are fewer than the SMs; a larger batch keeps
+ * every QR in one CTA where a lone step may reduce a large one in row blocks (the same R up to
+ * rounding and an orthogonal factor the truncation does not see).
  *
  * ht_batch_create binds count contexts and tensors (caller-owned, distinct, same d and device;
  * us[i] must fit ctxs[i] as for ht_step).  A bound context's device plan lives in the batch

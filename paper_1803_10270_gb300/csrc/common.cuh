@@ -43,12 +43,14 @@ struct GemmDesc {
 // Householder QR, R factor only.  Input op(A) is m x k (tA: A stored k x m, lda between
 // columns of the stored array).  Output R is min(m,k) x k upper trapezoidal written to
 // R (ldr); with tR the transpose R^T (k x min(m,k)) is written instead.  scratch holds
-// m*k values.  rows_out (optional) receives min(m,k).
+// m*k values.  rows_out (optional) receives min(m,k).  With a ticket, tall matrices are
+// reduced in row blocks by several CTAs and a combine step (the launch resets the ticket).
 struct QrDesc {
   const double* A;
   double* scratch;
   double* R;
   int* rows_out;
+  unsigned* ticket;   // zero-initialised counter of the two-stage form (null: one CTA per matrix)
   int m, k, lda, ldr;
   int tA, tR;
 };

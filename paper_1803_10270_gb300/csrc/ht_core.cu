@@ -104,6 +104,7 @@ struct WsNode {
   double* X;      // W_k^T R                                      Kc x Kc
   double* Y;      // E Z_k / s                                    Kc x Kc
   double* invsig; // 1/s_k                                        Kc
+  unsigned* tick; // QR tickets: [0] basis (leaf / orthogonalisation), [1] complement factor
 };
 
 struct HtView {           // a tensor as the kernels see it
@@ -217,7 +218,7 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
   for (int s = 0; s < L.n_leaf; ++s) {
     const int t = L.leaf[s];
     QrDesc& q = P->qr_leaf[s];
-    q.A = in.node[t]; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr;
+    q.A = in.node[t]; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr; q.ticket = wn[t].tick;
     q.m = in.n[T.lo[t]]; q.k = P->K[t]; q.lda = q.m; q.ldr = P->Rp[t]; q.tA = 0; q.tR = 0;
   }
   // bottom-up absorb + orthogonalisation QR
@@ -232,7 +233,7 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
                 P->Rp[a], P->Rp[b], K2);
       g2.batch = K; g2.sA = (long long)P->Rp[a] * K2; g2.sB = 0; g2.sC = (long long)P->Rp[a] * P->Rp[b];
       QrDesc& q = P->qr_orth[dep][s];
-      q.A = wn[t].Cabs; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr;
+      q.A = wn[t].Cabs; q.scratch = wn[t].S; q.R = wn[t].Rf; q.rows_out = nullptr; q.ticket = wn[t].tick;
       q.m = P->Rp[a] * P->Rp[b]; q.k = K; q.lda = q.m; q.ldr = P->Rp[t]; q.tA = 0; q.tR = 0;
     }
   }
@@ -266,10 +267,10 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
       fill_gemm(gb, wn[t].T1, K1, 1, wn[a].Rf, P->Rp[a], 1, wn[b].Epre, K2, K2, P->Rp[a], K1);
       gb.batch = mE; gb.sA = (long long)K1 * K2; gb.sC = (long long)K2 * P->Rp[a];
       QrDesc& qa = P->qr_comp[dep][2 * s];
-      qa.A = wn[a].Epre; qa.scratch = wn[a].S; qa.R = wn[a].E; qa.rows_out = nullptr;
+      qa.A = wn[a].Epre; qa.scratch = wn[a].S; qa.R = wn[a].E; qa.rows_out = nullptr; qa.ticket = wn[a].tick + 1;
       qa.m = P->Rp[b] * mE; qa.k = K1; qa.lda = K1; qa.ldr = K1; qa.tA = 1; qa.tR = 1;
       QrDesc& qb = P->qr_comp[dep][2 * s + 1];
-      qb.A = wn[b].Epre; qb.scratch = wn[b].S; qb.R = wn[b].E; qb.rows_out = nullptr;
+      qb.A = wn[b].Epre; qb.scratch = wn[b].S; qb.R = wn[b].E; qb.rows_out = nullptr; qb.ticket = wn[b].tick + 1;
       qb.m = P->Rp[a] * mE; qb.k = K2; qb.lda = K2; qb.ldr = K2; qb.tA = 1; qb.tR = 1;
     }
   }
@@ -760,7 +761,7 @@ static int trunc_input_cap(const ht_config* c) {
 }
 
 struct WsLayout {
-  size_t off_plan, off_err, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
+  size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
   size_t total;
@@ -773,6 +774,7 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   size_t off = 0;
   W->off_plan = off; off = align_up(off + sizeof(Plan));
   W->off_err = off; off = align_up(off + 64);
+  W->off_tick = off; off = align_up(off + 2 * NN * sizeof(unsigned));
   W->off_app_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_stage_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_wn = off; off = align_up(off + NN * sizeof(WsNode));
@@ -853,6 +855,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
                       &c->wn[t].T1, &c->wn[t].E, &c->wn[t].P, &c->wn[t].sig, &c->wn[t].W,
                       &c->wn[t].Z, &c->wn[t].SW, &c->wn[t].X, &c->wn[t].Y, &c->wn[t].invsig};
     for (int j = 0; j < 15; ++j) *f[j] = (double*)(base + W.node_off[t][j]);
+    c->wn[t].tick = (unsigned*)(base + W.off_tick) + 2 * t;
     c->app[t] = (double*)(base + W.app_off[t]);
     c->stage[t] = (double*)(base + W.stage_off[t]);
   }
@@ -873,6 +876,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->cp.nmax = nmax;
   }
   if (cudaMemset(c->err, 0, 64) != cudaSuccess ||
+      cudaMemset(base + W.off_tick, 0, 2 * NN * sizeof(unsigned)) != cudaSuccess ||
       cudaMemcpy(c->wn_dev, c->wn, sizeof(WsNode) * NN, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(c->ws);
     delete c;

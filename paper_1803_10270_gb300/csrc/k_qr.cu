@@ -8,10 +8,12 @@
 // inputs (leaf bases [U, A U, A^2 U] with more columns than grid points are exactly
 // rank deficient), where Cholesky-based QR would break down.
 //
-// One CTA per matrix; the matrix is copied into shared memory (or a scratch buffer, L2
-// resident, when it does not fit) and reduced in place.  For column j the reflector
-// v = x - alpha e1 (alpha = -sign(x0)|x|) is formed in place and every trailing column (one
-// warp each) gets c <- c - tau (v.c) v with tau = 2 / (v.v).
+// For column j the reflector v = x - alpha e1 (alpha = -sign(x0)|x|) is formed in place and
+// every trailing column (one warp each) gets c <- c - tau (v.c) v with tau = 2 / (v.v).  A
+// matrix is reduced by one CTA, or, when it is tall (m >= 3k) and its row blocks fit in shared
+// memory, in two stages (tall-skinny QR): row blocks by separate CTAs, then their stacked
+// triangular factors by the last CTA to finish.  An FP64 Householder sweep is bound by the SM's
+// FP64 pipe, so the split buys SMs for the few large matrices of a tree level.
 #include "common.cuh"
 
 namespace {
@@ -27,6 +29,9 @@ __device__ inline double warp_sum(double v) {
 // Dynamic shared memory per CTA: 96 KB, so that two CTAs share an SM in batched launches; a
 // matrix that does not fit is reduced in its global scratch buffer (L2 resident).
 constexpr int QR_SMEM_BYTES = 96 * 1024;
+
+// Largest number of row blocks (CTAs) per matrix in the two-stage form.
+constexpr int QR_MAXSPLIT = 8;
 
 // Householder reflector of column j from x0 = S[j, j] and t = sum_{i > j} S[i, j]^2 (lane 0):
 // v = x - alpha e1 with alpha = -sign(x0) |x| stored over S[j, j], alpha into diag[j], and
@@ -48,38 +53,29 @@ __device__ inline double reflector(double* colj, int j, double t, double* diag) 
   return tau;
 }
 
-// Warp w owns the columns c = w (mod number of warps).  Step j applies reflector j to every
-// trailing column c > j (dot product over rows >= j, warp reduction, rank-1 update); the owner
-// of column j+1 updates it first and forms reflector j+1 at once (look-ahead), while the other
-// warps are still updating their columns, so the reflector's serial FP64 chain (norm, square
-// root, reciprocal) stays off the critical path.  One CTA barrier per step.
-__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long inst_stride,
-                                                 long long smem_doubles, double* flops) {
-  // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
-  const QrDesc q = ((const QrDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
-  const int m = q.m, k = q.k;
-  const int kd = (k + 1) & ~1;   // diagonal entries, rounded to keep the matrix 16-byte aligned
-  if (m <= 0 || k <= 0 || kd > smem_doubles) {
-    if (threadIdx.x == 0 && q.rows_out) *q.rows_out = 0;
-    return;
-  }
-  extern __shared__ double diag[];   // the k diagonal entries of R, then the matrix when it fits
-  const long long need = (long long)m * k;
-  double* S = (need <= smem_doubles - kd) ? diag + kd : q.scratch;
+// Householder reduction of the m x k column-major matrix S (in shared memory or scratch) to its
+// R factor: diag receives the diagonal, the strict upper triangle stays in S.  Warp w owns the
+// columns c = w (mod number of warps).  Step j applies reflector j to every trailing column
+// c > j (dot product, warp reduction, rank-1 update); the owner of column j+1 updates it first
+// and forms reflector j+1 at once (look-ahead), while the other warps are still updating their
+// columns, so the reflector's serial FP64 chain (norm, square root, reciprocal) stays off the
+// critical path.  One CTA barrier per step.
+//
+// band > 0 declares that column c is zero below row (c+1) band - 1 (the interleaved stack of
+// triangular factors in the combine stage); reflectors then keep that pattern, and step j works
+// on rows [j, min(m, (j+1) band)) only.
+__device__ inline int band_rows(int m, int band, int j) {
+  return band > 0 ? htg_min(m, (j + 1) * band) : m;
+}
+
+__device__ void householder_r(double* S, int m, int k, int band, double* diag, double* tau_sh) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
-  // copy op(A) into S (m x k, column major)
-  const long long mk = (long long)m * k;
-  for (long long e = tid; e < mk; e += NT) {
-    const int i = (int)(e % m), c = (int)(e / m);
-    S[e] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
-  }
-  __shared__ double tau_sh[2];
-  __syncthreads();
   const int rmax = htg_min(m, k);
   // reflector 0 by the owner of column 0
-  if (wid == 0) {
+  if (wid == 0 && rmax > 0) {
+    const int m0 = band_rows(m, band, 0);
     double s = 0.0;
-    for (int i = 1 + lane; i < m; i += 32) s = fma(S[i], S[i], s);
+    for (int i = 1 + lane; i < m0; i += 32) s = fma(S[i], S[i], s);
     s = warp_sum(s);
     if (lane == 0) tau_sh[0] = reflector(S, 0, s, diag);
   }
@@ -87,18 +83,24 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
   for (int j = 0; j < rmax; ++j) {
     const double tau = tau_sh[j & 1];
     const double* v = S + (long long)m * j;
+    const int mj = band_rows(m, band, j);
     const int c0 = j + 1 + ((wid - (j + 1)) % nw + nw) % nw;   // this warp's first column > j
     for (int c = c0; c < k; c += nw) {
       double* cc = S + (long long)m * c;
       double dot = 0.0;
-      for (int i = j + lane; i < m; i += 32) dot = fma(v[i], cc[i], dot);
+      for (int i = j + lane; i < mj; i += 32) dot = fma(v[i], cc[i], dot);
       const double wgt = warp_sum(dot) * tau;
       if (c == j + 1 && j + 1 < rmax) {
-        // update column j+1 and form reflector j+1 from its new entries
+        // update column j+1 and form reflector j+1 from its new entries (with band > 0 its
+        // support reaches rows [mj, m_{j+1}) that reflector j left untouched)
+        const int mj1 = band_rows(m, band, j + 1);
         double ss = 0.0;
-        for (int i = j + lane; i < m; i += 32) {
-          const double x = fma(-wgt, v[i], cc[i]);
-          cc[i] = x;
+        for (int i = j + lane; i < mj1; i += 32) {
+          double x = cc[i];
+          if (i < mj) {
+            x = fma(-wgt, v[i], x);
+            cc[i] = x;
+          }
           if (i > j + 1) ss = fma(x, x, ss);
         }
         ss = warp_sum(ss);
@@ -106,28 +108,131 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
         if (lane == 0) tau_sh[(j + 1) & 1] = reflector(cc, j + 1, ss, diag);
         __syncwarp();
       } else {
-        for (int i = j + lane; i < m; i += 32) cc[i] = fma(-wgt, v[i], cc[i]);
+        for (int i = j + lane; i < mj; i += 32) cc[i] = fma(-wgt, v[i], cc[i]);
       }
     }
     __syncthreads();
   }
+}
+
+// Flops of householder_r: the sub-column norm (2 per entry) and the dot and update of every
+// trailing column (4 per entry), over the rows each step touches.
+__device__ double householder_flops(int m, int k, int band) {
+  double f = 0.0;
+  const int rmax = htg_min(m, k);
+  for (int j = 0; j < rmax; ++j) {
+    const double rows = (double)(band_rows(m, band, j) - j);
+    f += 2.0 * rows + 4.0 * rows * (k - j - 1);
+  }
+  return f;
+}
+
+// Row blocks of the two-stage form: ns blocks for a matrix that does not fit in shared memory
+// (one CTA would sweep it in its L2-resident scratch buffer) when the blocks and the stack of
+// their triangular factors do fit and there are at least three rows per column.  A matrix that
+// fits stays whole: its sweep is latency bound, and two stages double the serial steps.
+// Stage 1 costs about (m / ns) k^2 / 2 and the banded combine about ns k^3 / 6 element
+// updates, balanced at ns^2 = 3 m / k.
+__device__ inline int qr_splits(int m, int k, int gsplit, long long room) {
+  if (gsplit < 2 || m < 3 * k || (long long)m * k <= room) return 1;
+  int ns = 1;
+  while (ns < gsplit && (long long)(ns + 1) * (ns + 1) * k <= 3LL * m) ++ns;
+  while (ns > 1 && (long long)ns * k * k > room) --ns;                 // stack in shared memory
+  if (ns > 1 && (long long)((m + ns - 1) / ns) * k > room) ns = 1;     // row block in shared memory
+  return ns;
+}
+
+// One matrix per CTA (gsplit = 1, or a matrix the split rule keeps whole): the matrix is copied
+// into shared memory (or its scratch buffer, L2 resident, when it does not fit) and reduced in
+// place.  Two-stage form (TSQR, ns > 1): CTA s of the matrix reduces the row block
+// [s mb, (s+1) mb) in shared memory and stores its k x k triangular factor R_s into the scratch
+// buffer, interleaved (row r of R_s at stack row r ns + s); the last CTA to finish (a ticket
+// counter, no waiting) reduces the ns k x k stack, whose column c is zero below row
+// (c+1) ns - 1, with the banded sweep, and writes R.  Q = diag(Q_s) Q_stack, so R is the R
+// factor of op(A) up to an orthogonal factor on the left, which the truncation never sees.
+__global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long inst_stride,
+                                                 long long smem_doubles, int gsplit, double* flops) {
+  // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
+  const QrDesc q = ((const QrDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x / gsplit];
+  const int part = blockIdx.x % gsplit;
+  const int m = q.m, k = q.k;
+  const int kd = (k + 1) & ~1;   // diagonal entries, rounded to keep the matrix 16-byte aligned
+  if (m <= 0 || k <= 0 || kd > smem_doubles) {
+    if (threadIdx.x == 0 && part == 0 && q.rows_out) *q.rows_out = 0;
+    return;
+  }
+  const long long room = smem_doubles - kd;
+  const int ns = q.ticket ? qr_splits(m, k, gsplit, room) : 1;
+  if (part >= ns) return;
+  extern __shared__ double diag[];   // the k diagonal entries of R, then the matrix when it fits
+  __shared__ double tau_sh[2];
+  __shared__ int last_sh;
+  const int tid = threadIdx.x;
+  double* S;
+  int mw;                            // rows of the matrix this CTA reduces
+  int band = 0;
+  double f = 0.0;
+  if (ns == 1) {
+    mw = m;
+    S = ((long long)m * k <= room) ? diag + kd : q.scratch;
+    for (long long e = tid; e < (long long)m * k; e += NT) {
+      const int i = (int)(e % m), c = (int)(e / m);
+      S[e] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
+    }
+    __syncthreads();
+  } else {
+    // ---- stage 1: the row block of this CTA
+    const int mb = (m + ns - 1) / ns;
+    const int r0 = part * mb;
+    const int ms = htg_max(0, htg_min(mb, m - r0));
+    S = diag + kd;
+    for (long long e = tid; e < (long long)ms * k; e += NT) {
+      const int i = (int)(e % ms), c = (int)(e / ms);
+      const long long ig = r0 + i;
+      S[e] = q.tA ? q.A[c + (long long)q.lda * ig] : q.A[ig + (long long)q.lda * c];
+    }
+    __syncthreads();
+    householder_r(S, ms, k, 0, diag, tau_sh);
+    if (tid == 0 && flops) f += householder_flops(ms, k, 0);
+    // R_s into the interleaved stack (rows beyond min(ms, k) are zero)
+    const int M2 = ns * k, rs = htg_min(ms, k);
+    double* stack = q.scratch;
+    for (int e = tid; e < k * k; e += NT) {
+      const int r = e % k, c = e / k;
+      double val = 0.0;
+      if (r < rs) val = (c == r) ? diag[r] : (c > r ? S[r + (long long)ms * c] : 0.0);
+      stack[(long long)(r * ns + part) + (long long)M2 * c] = val;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last_sh = (atomicAdd(q.ticket, 1u) == (unsigned)(ns - 1));
+    __syncthreads();
+    if (!last_sh) {
+      if (tid == 0 && flops && f > 0.0) atomicAdd(flops, f);
+      return;
+    }
+    // ---- stage 2 (last CTA): the banded stack
+    __threadfence();
+    if (tid == 0) *q.ticket = 0u;    // ready for the next launch (stream ordered)
+    for (int e = tid; e < M2 * k; e += NT) S[e] = __ldcg(stack + e);
+    __syncthreads();
+    mw = M2;
+    band = ns;
+  }
+  householder_r(S, mw, k, band, diag, tau_sh);
   // write R (rmax x k upper trapezoidal) or its transpose
+  const int rmax = htg_min(mw, k);
   const long long rk = (long long)rmax * k;
   for (long long e = tid; e < rk; e += NT) {
     const int r = (int)(e % rmax), c = (int)(e / rmax);
     double val = 0.0;
     if (c == r) val = diag[r];
-    else if (c > r) val = S[r + (long long)m * c];
+    else if (c > r) val = S[r + (long long)mw * c];
     if (q.tR) q.R[c + (long long)q.ldr * r] = val;
     else q.R[r + (long long)q.ldr * c] = val;
   }
   if (tid == 0 && q.rows_out) *q.rows_out = rmax;
-  if (tid == 0 && flops) {
-    // norm of the sub-column (2 per entry) + dot and update of every trailing column (4 per entry)
-    double f = 0.0;
-    for (int j = 0; j < rmax; ++j) f += 2.0 * (m - j) + 4.0 * (double)(m - j) * (k - j - 1);
-    atomicAdd(flops, f);
-  }
+  if (tid == 0 && flops) atomicAdd(flops, f + householder_flops(mw, k, band));
 }
 
 }  // namespace
@@ -144,7 +249,12 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  qr_r_kernel<<<dim3(ndesc, count), NT, QR_SMEM_BYTES, s>>>(descs_dev, inst_stride,
-                                                              (long long)(QR_SMEM_BYTES / sizeof(double)), flops);
+  // the split buys idle SMs: a launch whose matrices already outnumber the SMs keeps them whole
+  static int sms[64] = {0};
+  if (dev >= 0 && dev < 64 && sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  const int nsm = (dev >= 0 && dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
+  const int gsplit = ((long long)ndesc * count < nsm) ? QR_MAXSPLIT : 1;
+  qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, QR_SMEM_BYTES, s>>>(
+      descs_dev, inst_stride, (long long)(QR_SMEM_BYTES / sizeof(double)), gsplit, flops);
   return cudaGetLastError();
 }

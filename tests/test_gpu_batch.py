@@ -1,6 +1,7 @@
 """Batched steps (ht_batch_step): every instance of a batch equals ht_step on that instance
 alone, bit for bit (the same kernels on the same descriptors, one launch covering all
-instances), and so the FP64 oracle's step (Section 3.2) within the FP64 bound.  Instances
+instances; these batches are small enough that the QR launches split large matrices as a lone
+step does), and so the FP64 oracle's step (Section 3.2) within the FP64 bound.  Instances
 differ in grid size, rank capacity, velocity and cap, as in a ragged batch of advection
 problems."""
 import math
