@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
+    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched"],
+                   help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -239,8 +241,21 @@ def run_gpu(args):
         dist.barrier()
     G.load()
     prec = G.HT_PREC_FP64 if args.precision == "fp64" else G.HT_PREC_MIXED
-    W = Workload(G, local, prec)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
+    if args.line != "all":
+        warm = max(args.warmup, 3)
+        if args.line == "d12":
+            res = run_d12(G, torch, flush, args.steps, warm)
+        elif args.line == "ab2":
+            res = run_ab2(G, torch, flush, args.steps, warm)
+        else:
+            res = run_batched(G, torch, flush, args.batched, args.steps, warm)
+        if rank == 0:
+            print(json.dumps({"line": args.line, **res}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    W = Workload(G, local, prec)
     stream = torch.cuda.current_stream()
 
     # warm-up (the first step pads the CP iterate to its target rank)
