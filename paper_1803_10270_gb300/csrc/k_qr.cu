@@ -53,13 +53,17 @@ __device__ inline double reflector(double* colj, int j, double t, double* diag) 
   return tau;
 }
 
-// Householder reduction of the m x k column-major matrix S (in shared memory or scratch) to its
-// R factor: diag receives the diagonal, the strict upper triangle stays in S.  Warp w owns the
-// columns c = w (mod number of warps).  Step j applies reflector j to every trailing column
-// c > j (dot product, warp reduction, rank-1 update); the owner of column j+1 updates it first
-// and forms reflector j+1 at once (look-ahead), while the other warps are still updating their
-// columns, so the reflector's serial FP64 chain (norm, square root, reciprocal) stays off the
-// critical path.  One CTA barrier per step.
+// Householder reduction of the m x k column-major matrix S (leading dimension ld, in shared
+// memory or scratch) to its R factor: diag receives the diagonal, the strict upper triangle
+// stays in S.  Step j applies reflector j to every trailing column c > j: a dot product over the
+// rows the step touches, a reduction across the lanes that hold the column, a rank-1 update.
+// Warp 0 takes column j+1 alone and forms reflector j+1 at once (look-ahead), so the
+// reflector's serial FP64 chain (norm, square root, reciprocal) runs while warps 1.. update the
+// other columns.  Those hold a column in L = 32, 16 or 8 lanes (32 / L columns per warp), chosen
+// per step to minimise the FP64 instructions of the busiest warp: a warp instruction costs its
+// SM partition's FP64 pipe the same whatever its active lanes, so short columns (the banded
+// combine, late steps) pack several columns per instruction and pay log2 L reduction levels
+// instead of 5.  One CTA barrier per step.
 //
 // band > 0 declares that column c is zero below row (c+1) band - 1 (the interleaved stack of
 // triangular factors in the combine stage); reflectors then keep that pattern, and step j works
@@ -68,10 +72,28 @@ __device__ inline int band_rows(int m, int band, int j) {
   return band > 0 ? htg_min(m, (j + 1) * band) : m;
 }
 
-__device__ void householder_r(double* S, int m, int k, int band, double* diag, double* tau_sh) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = NT / 32;
+constexpr int QR_UPD_WARPS = NT / 32 - 1;   // warps 1.. update the columns after j+1
+
+// log2 of the lanes per column for a step with `rows` rows and nc columns to update: the busiest
+// warp issues passes x (2 ceil(rows / L) + log2 L) FP64 instructions, passes = ceil(nc / slots).
+__device__ inline int lanes_log2(int rows, int nc) {
+  int best = 5, best_cost = 0x7fffffff;
+#pragma unroll
+  for (int lg = 5; lg >= 3; --lg) {
+    const int L = 1 << lg, slots = QR_UPD_WARPS * (32 >> lg);
+    const int cost = ((nc + slots - 1) / slots) * (2 * ((rows + L - 1) / L) + lg);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = lg;
+    }
+  }
+  return best;
+}
+
+__device__ void householder_r(double* S, long long ld, int m, int k, int band, double* diag, double* tau_sh) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int rmax = htg_min(m, k);
-  // reflector 0 by the owner of column 0
+  // reflector 0 by warp 0
   if (wid == 0 && rmax > 0) {
     const int m0 = band_rows(m, band, 0);
     double s = 0.0;
@@ -82,33 +104,53 @@ __device__ void householder_r(double* S, int m, int k, int band, double* diag, d
   __syncthreads();
   for (int j = 0; j < rmax; ++j) {
     const double tau = tau_sh[j & 1];
-    const double* v = S + (long long)m * j;
+    const double* v = S + ld * j;
     const int mj = band_rows(m, band, j);
-    const int c0 = j + 1 + ((wid - (j + 1)) % nw + nw) % nw;   // this warp's first column > j
-    for (int c = c0; c < k; c += nw) {
-      double* cc = S + (long long)m * c;
-      double dot = 0.0;
-      for (int i = j + lane; i < mj; i += 32) dot = fma(v[i], cc[i], dot);
-      const double wgt = warp_sum(dot) * tau;
-      if (c == j + 1 && j + 1 < rmax) {
-        // update column j+1 and form reflector j+1 from its new entries (with band > 0 its
-        // support reaches rows [mj, m_{j+1}) that reflector j left untouched)
-        const int mj1 = band_rows(m, band, j + 1);
-        double ss = 0.0;
-        for (int i = j + lane; i < mj1; i += 32) {
-          double x = cc[i];
-          if (i < mj) {
-            x = fma(-wgt, v[i], x);
-            cc[i] = x;
+    if (wid == 0) {
+      if (j + 1 < k) {
+        double* cc = S + ld * (j + 1);
+        double dot = 0.0;
+        for (int i = j + lane; i < mj; i += 32) dot = fma(v[i], cc[i], dot);
+        const double wgt = warp_sum(dot) * tau;
+        if (j + 1 < rmax) {
+          // update column j+1 and form reflector j+1 from its new entries (with band > 0 its
+          // support reaches rows [mj, m_{j+1}) that reflector j left untouched)
+          const int mj1 = band_rows(m, band, j + 1);
+          double ss = 0.0;
+          for (int i = j + lane; i < mj1; i += 32) {
+            double x = cc[i];
+            if (i < mj) {
+              x = fma(-wgt, v[i], x);
+              cc[i] = x;
+            }
+            if (i > j + 1) ss = fma(x, x, ss);
           }
-          if (i > j + 1) ss = fma(x, x, ss);
+          ss = warp_sum(ss);
+          __syncwarp();
+          if (lane == 0) tau_sh[(j + 1) & 1] = reflector(cc, j + 1, ss, diag);
+          __syncwarp();
+        } else {
+          for (int i = j + lane; i < mj; i += 32) cc[i] = fma(-wgt, v[i], cc[i]);
         }
-        ss = warp_sum(ss);
-        __syncwarp();
-        if (lane == 0) tau_sh[(j + 1) & 1] = reflector(cc, j + 1, ss, diag);
-        __syncwarp();
-      } else {
-        for (int i = j + lane; i < mj; i += 32) cc[i] = fma(-wgt, v[i], cc[i]);
+      }
+    } else {
+      const int nc = k - j - 2;                            // columns j+2 .. k-1
+      const int lg = lanes_log2(mj - j, nc);               // uniform over the CTA
+      const int L = 1 << lg, grp = lane >> lg, gl = lane & (L - 1);
+      const int slots = QR_UPD_WARPS << (5 - lg);
+      const int passes = nc > 0 ? (nc + slots - 1) / slots : 0;
+      // slot = pass * slots + grp * QR_UPD_WARPS + (wid - 1): consecutive columns on different warps
+      for (int p = 0; p < passes; ++p) {
+        const int sl = p * slots + grp * QR_UPD_WARPS + (wid - 1);
+        const bool act = sl < nc;
+        double* cc = S + ld * (j + 2 + (act ? sl : 0));
+        double dot = 0.0;
+        if (act)
+          for (int i = j + gl; i < mj; i += L) dot = fma(v[i], cc[i], dot);
+        for (int o = L >> 1; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const double wgt = dot * tau;
+        if (act)
+          for (int i = j + gl; i < mj; i += L) cc[i] = fma(-wgt, v[i], cc[i]);
       }
     }
     __syncthreads();
@@ -134,11 +176,11 @@ __device__ double householder_flops(int m, int k, int band) {
 // Stage 1 costs about (m / ns) k^2 / 2 and the banded combine about ns k^3 / 6 element
 // updates, balanced at ns^2 = 3 m / k.
 __device__ inline int qr_splits(int m, int k, int gsplit, long long room) {
-  if (gsplit < 2 || m < 3 * k || (long long)m * k <= room) return 1;
+  if (gsplit < 2 || m < 3 * k || (long long)(m | 1) * k <= room) return 1;
   int ns = 1;
   while (ns < gsplit && (long long)(ns + 1) * (ns + 1) * k <= 3LL * m) ++ns;
-  while (ns > 1 && (long long)ns * k * k > room) --ns;                 // stack in shared memory
-  if (ns > 1 && (long long)((m + ns - 1) / ns) * k > room) ns = 1;     // row block in shared memory
+  while (ns > 1 && (long long)((ns * k) | 1) * k > room) --ns;              // stack in shared memory
+  if (ns > 1 && (long long)(((m + ns - 1) / ns) | 1) * k > room) ns = 1;    // row block in shared memory
   return ns;
 }
 
@@ -170,14 +212,17 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
   const int tid = threadIdx.x;
   double* S;
   int mw;                            // rows of the matrix this CTA reduces
+  long long ld;                      // its leading dimension (odd in shared memory)
   int band = 0;
   double f = 0.0;
   if (ns == 1) {
     mw = m;
-    S = ((long long)m * k <= room) ? diag + kd : q.scratch;
+    const bool fits = (long long)(m | 1) * k <= room;
+    S = fits ? diag + kd : q.scratch;
+    ld = fits ? (m | 1) : m;
     for (long long e = tid; e < (long long)m * k; e += NT) {
       const int i = (int)(e % m), c = (int)(e / m);
-      S[e] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
+      S[i + ld * c] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
     }
     __syncthreads();
   } else {
@@ -186,13 +231,14 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     const int r0 = part * mb;
     const int ms = htg_max(0, htg_min(mb, m - r0));
     S = diag + kd;
+    ld = ms | 1;
     for (long long e = tid; e < (long long)ms * k; e += NT) {
       const int i = (int)(e % ms), c = (int)(e / ms);
       const long long ig = r0 + i;
-      S[e] = q.tA ? q.A[c + (long long)q.lda * ig] : q.A[ig + (long long)q.lda * c];
+      S[i + ld * c] = q.tA ? q.A[c + (long long)q.lda * ig] : q.A[ig + (long long)q.lda * c];
     }
     __syncthreads();
-    householder_r(S, ms, k, 0, diag, tau_sh);
+    householder_r(S, ld, ms, k, 0, diag, tau_sh);
     if (tid == 0 && flops) f += householder_flops(ms, k, 0);
     // R_s into the interleaved stack (rows beyond min(ms, k) are zero)
     const int M2 = ns * k, rs = htg_min(ms, k);
@@ -200,7 +246,7 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     for (int e = tid; e < k * k; e += NT) {
       const int r = e % k, c = e / k;
       double val = 0.0;
-      if (r < rs) val = (c == r) ? diag[r] : (c > r ? S[r + (long long)ms * c] : 0.0);
+      if (r < rs) val = (c == r) ? diag[r] : (c > r ? S[r + ld * c] : 0.0);
       stack[(long long)(r * ns + part) + (long long)M2 * c] = val;
     }
     __threadfence();
@@ -214,12 +260,13 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     // ---- stage 2 (last CTA): the banded stack
     __threadfence();
     if (tid == 0) *q.ticket = 0u;    // ready for the next launch (stream ordered)
-    for (int e = tid; e < M2 * k; e += NT) S[e] = __ldcg(stack + e);
+    ld = M2 | 1;
+    for (int e = tid; e < M2 * k; e += NT) S[(e % M2) + ld * (e / M2)] = __ldcg(stack + e);
     __syncthreads();
     mw = M2;
     band = ns;
   }
-  householder_r(S, mw, k, band, diag, tau_sh);
+  householder_r(S, ld, mw, k, band, diag, tau_sh);
   // write R (rmax x k upper trapezoidal) or its transpose
   const int rmax = htg_min(mw, k);
   const long long rk = (long long)rmax * k;
@@ -227,7 +274,7 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     const int r = (int)(e % rmax), c = (int)(e / rmax);
     double val = 0.0;
     if (c == r) val = diag[r];
-    else if (c > r) val = S[r + (long long)mw * c];
+    else if (c > r) val = S[r + ld * c];
     if (q.tR) q.R[c + (long long)q.ldr * r] = val;
     else q.R[r + (long long)q.ldr * c] = val;
   }
