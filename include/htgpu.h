@@ -48,7 +48,8 @@ extern "C" {
 #define HT_MAXD 16
 #define HT_MAXNODES (2 * HT_MAXD - 1)
 #define HT_MAXTERMS 16   /* a Kronecker-sum operator has one term per dimension */
-#define HT_MAXBLOCKTERMS 8   /* terms of a general (block-diagonal) application */
+#define HT_MAXBLOCKTERMS 10  /* terms of a general (block-diagonal) application (the 3-D
+                                variable-coefficient advection operator has 9) */
 #define HT_MAXSTENCIL 9
 
 typedef enum ht_status {
@@ -90,14 +91,17 @@ typedef enum ht_factor_kind {
   HT_F_IDENTITY = 0,   /* identity */
   HT_F_STENCIL = 1,    /* periodic constant band: (A u)_j = sum_{s=-w}^{w} c_{s+w} u_{j+s mod n} */
   HT_F_DIAG = 2,       /* (A u)_j = v_j u_j, v a device vector of n values */
-  HT_F_RANK1 = 3       /* (A u)_j = m_j sum_l w_l u_l, m and w device vectors of n values */
+  HT_F_RANK1 = 3,      /* (A u)_j = m_j sum_l w_l u_l, m and w device vectors of n values */
+  HT_F_DIAG_STENCIL = 4   /* (A u)_j = v_j sum_{s=-w}^{w} c_{s+w} u_{j+s mod n}: a diagonal times a
+                             periodic band, e.g. z_k d/dz_k of the variable-coefficient advection
+                             operator (Section 4.1, Table tab:ordering0); v a device vector */
 } ht_factor_kind;
 
 typedef struct ht_factor {
   int kind;                        /* ht_factor_kind */
-  int half_width;                  /* STENCIL: w, 0 <= w <= (HT_MAXSTENCIL-1)/2 */
-  double stencil[HT_MAXSTENCIL];   /* STENCIL: 2w+1 coefficients (host values) */
-  const double* v;                 /* DIAG: device values; RANK1: device m */
+  int half_width;                  /* STENCIL, DIAG_STENCIL: w, 0 <= w <= (HT_MAXSTENCIL-1)/2 */
+  double stencil[HT_MAXSTENCIL];   /* STENCIL, DIAG_STENCIL: 2w+1 coefficients (host values) */
+  const double* v;                 /* DIAG, DIAG_STENCIL: device values; RANK1: device m */
   const double* w;                 /* RANK1: device w */
 } ht_factor;
 

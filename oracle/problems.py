@@ -10,8 +10,15 @@
     q = 4:    alpha = -nu,  identity;
     q = 5:    alpha = +nu,  (m w^T) on each v dimension (rho = sum_v w^3 f, M = m^{x3}).
 
+- Variable-coefficient advection f_t + sum_j (sum_k C_jk z_k) df/dz_j = 0 (Section 4.1, eq.
+  PDE-advR; Table tab:ordering0 orders its N^2 separable terms): term q = (j-1) N + k has
+  alpha_q = -C_jk, the derivative D on dimension j and multiplication by z on dimension k
+  (for k = j the single factor diag(z) D on dimension j), identity elsewhere.
+
 Parity: pinned by tests (dense Kronecker operator on tiny grids; exact conservation of
-the weighted mass; the Maxwellian is a fixed point of the collision terms).
+the weighted mass; the Maxwellian is a fixed point of the collision terms; the paper's
+term tables as golden files; the advection operator on exp(-|z|^2) against its closed form
+2 (z^T C z) exp(-|z|^2) within the central-difference error).
 """
 from __future__ import annotations
 
@@ -42,4 +49,24 @@ def kinetic_terms(kc):
     factors.append([None] * 6)
     alphas.append(kc.nu)
     factors.append([None, None, None, P1, P1, P1])
+    return alphas, factors
+
+
+def varcoef_terms(case):
+    """(alphas, factors) of -sum_j (C z)_j d/dz_j in the order of Table tab:ordering0:
+    q = (j-1) N + k (1-based j, k) carries -C_jk; None = identity."""
+    N, n = case.N, case.n
+    D = central_diff_matrix(n, case.h)
+    Z = np.diag(case.z())
+    alphas, factors = [], []
+    for j in range(N):
+        for k in range(N):
+            f = [None] * N
+            if k == j:
+                f[j] = Z @ D
+            else:
+                f[j] = D
+                f[k] = Z
+            alphas.append(-float(case.C[j, k]))
+            factors.append(f)
     return alphas, factors

@@ -68,6 +68,7 @@ struct Plan {
   GemmDesc g_T1[MAXLEV][NN];
   GemmDesc g_Epre[MAXLEV][2 * NN];
   GemmDesc g_XY[2 * NN];
+  GemmDesc g_bi[4][NN];     // two Newton steps restoring X_t Y_t = I (see rank_select_body)
   GemmDesc g_proj1[NN];
   GemmDesc g_proj2[NN];
   GemmDesc g_proj3[NN];
@@ -175,7 +176,7 @@ __device__ void fill_gemm(GemmDesc& g, const double* A, int lda, int tA, const d
   g.tA = tA; g.tB = tB;
   g.sA = g.sB = g.sC = 0;
   g.batch = 1;
-  g.alpha = 1.0; g.beta = 0.0;
+  g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0;
 }
 
 // skip_tol: the relative tolerance that sets the SVD discard level (SvdDesc::skip2), 0 when every
@@ -358,6 +359,20 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
     GemmDesc& y = P->g_XY[i++];
     fill_gemm(y, wn[t].E, P->K[t], 0, wn[t].Z, P->mE[t], 0, wn[t].Y, P->K[t], P->K[t], k, P->mE[t]);
     y.colscale = wn[t].invsig;
+    // X_t Y_t = W_k^T W_k S_k Z_k^T Z_k S_k^-1 = I_k in exact arithmetic; rounding in the SVD
+    // breaks it by about eps |u| / s_k (Y divides by the kept singular values), and the edge's
+    // projector Y X then moves T(u) by that much.  Two Newton steps for the inverse of X_t on
+    // the range of Y_t, Y <- Y (2I - X Y), square that error twice (N in SW, Y2 in P: both free
+    // once the SVD has run); with every direction kept, Y X = I and T(u) = u to rounding.
+    const int K = P->K[t];
+    GemmDesc& n1 = P->g_bi[0][t - 1];
+    fill_gemm(n1, wn[t].X, k, 0, wn[t].Y, K, 0, wn[t].SW, k, k, k, K);
+    n1.alpha = -1.0; n1.diag = 2.0;
+    fill_gemm(P->g_bi[1][t - 1], wn[t].Y, K, 0, wn[t].SW, k, 0, wn[t].P, K, K, k, k);
+    GemmDesc& n2 = P->g_bi[2][t - 1];
+    fill_gemm(n2, wn[t].X, k, 0, wn[t].P, K, 0, wn[t].SW, k, k, k, K);
+    n2.alpha = -1.0; n2.diag = 2.0;
+    fill_gemm(P->g_bi[3][t - 1], wn[t].P, K, 0, wn[t].SW, k, 0, wn[t].Y, K, K, k, k);
   }
   // projection
   for (int s = 0; s < L.n_proj1; ++s) {
@@ -451,6 +466,15 @@ __device__ double apply_factor_at(const ApplyFactor& F, const double* x, int n, 
     }
     case HT_F_DIAG: return F.v[j] * x[j];
     case HT_F_RANK1: return F.v[j] * xsum;
+    case HT_F_DIAG_STENCIL: {
+      double s = 0.0;
+      for (int o = -F.hw; o <= F.hw; ++o) {
+        int jj = (j + o) % n;
+        if (jj < 0) jj += n;
+        s = fma(F.c[o + F.hw], x[jj], s);
+      }
+      return F.v[j] * s;
+    }
   }
   return 0.0;
 }
@@ -612,6 +636,10 @@ __device__ void apply_xfer_body(const ApplyOp& op, const TreeInfo& T, const Leve
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && t != 0) out.rank[t] = ot[nb];
 }
+
+// the operator travels as a kernel parameter (at most 32764 bytes on this architecture)
+static_assert(sizeof(ApplyOp) + sizeof(TreeInfo) + sizeof(Levels) + 3 * sizeof(HtView) <= 32000,
+              "apply kernel parameters exceed the parameter space");
 
 __global__ void apply_leaf_kernel(ApplyOp op, TreeInfo T, Levels L, HtView in0, HtView in1, HtView out) {
   apply_leaf_body(op, T, L, in0, in1, out);
@@ -1000,6 +1028,8 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st));
   HTG_LAUNCH(c, KC_PLAN, s, sel());
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  for (int ph = 0; ph < 4; ++ph)
+    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_bi[ph], T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   if (L.n_proj3 > 0)
@@ -1073,10 +1103,12 @@ static bool build_apply(const ht_ctx* c, const ht_op* L, double dt, int mode, Ap
       o->c[0] = scale;
       return true;
     }
-    if (f.kind == HT_F_STENCIL) {
+    if (f.kind == HT_F_STENCIL || f.kind == HT_F_DIAG_STENCIL) {
       if (f.half_width < 0 || 2 * f.half_width + 1 > HT_MAXSTENCIL) return false;
+      if (f.kind == HT_F_DIAG_STENCIL && !f.v) return false;
       o->hw = f.half_width;
       for (int j = 0; j < 2 * f.half_width + 1; ++j) o->c[j] = scale * f.stencil[j];
+      o->v = f.v;
       return true;
     }
     if (f.kind == HT_F_DIAG || f.kind == HT_F_RANK1) {

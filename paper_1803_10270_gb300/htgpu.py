@@ -18,12 +18,12 @@ import numpy as np
 HT_MAXD = 16
 HT_MAXNODES = 2 * HT_MAXD - 1
 HT_MAXTERMS = 16
-HT_MAXBLOCKTERMS = 8
+HT_MAXBLOCKTERMS = 10
 HT_MAXSTENCIL = 9
 
 HT_OK, HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA, HT_ERR_NONFINITE, HT_ERR_TIMEOUT, HT_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 HT_PREC_FP64, HT_PREC_MIXED = 0, 1
-HT_F_IDENTITY, HT_F_STENCIL, HT_F_DIAG, HT_F_RANK1 = 0, 1, 2, 3
+HT_F_IDENTITY, HT_F_STENCIL, HT_F_DIAG, HT_F_RANK1, HT_F_DIAG_STENCIL = 0, 1, 2, 3, 4
 HT_APPLY_L, HT_APPLY_EULER, HT_APPLY_RK2POLY = 0, 1, 2
 HT_SCHEME_RK2POLY, HT_SCHEME_HEUN2 = 0, 1
 CP_ALS_GS, CP_ALS_JACOBI_DAMPED = 0, 1
@@ -167,7 +167,7 @@ def tree_info(d: int) -> TreeInfo:
 class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
-    def __init__(self, d: int, n, cap: int, max_terms: int = HT_MAXBLOCKTERMS - 2, precision: int = HT_PREC_FP64,
+    def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
                  device: int = 0):
         lib = load()
         cfg = ht_config()
@@ -392,6 +392,40 @@ class KineticOp:
                 f.v = self.m.data_ptr()
                 f.w = self.w.data_ptr()
             op.f[4][j] = f
+        self.op = op
+
+
+class VarCoefOp:
+    """-sum_j (C z)_j d/dz_j on (z_1..z_N) in the term order of Table tab:ordering0 (term
+    q = j N + k carries -C_jk: the derivative on z_j and z on z_k, or z d/dz_j when k = j);
+    keeps its device vector z alive."""
+
+    def __init__(self, case, device="cuda"):
+        import torch
+        self.z = torch.tensor(case.z(), dtype=torch.float64, device=device)
+        N = case.N
+        D = [-0.5 / case.h, 0.0, 0.5 / case.h]
+        op = ht_op()
+        op.d = N
+        op.n_terms = N * N
+        op.kron_sum = 0
+        for j in range(N):
+            for k in range(N):
+                q = j * N + k
+                op.alpha[q] = -float(case.C[j, k])
+                for i in range(N):
+                    op.f[q][i] = ht_factor()
+                if k == j:
+                    f = stencil_factor(D)
+                    f.kind = HT_F_DIAG_STENCIL
+                    f.v = self.z.data_ptr()
+                    op.f[q][j] = f
+                else:
+                    op.f[q][j] = stencil_factor(D)
+                    fz = ht_factor()
+                    fz.kind = HT_F_DIAG
+                    fz.v = self.z.data_ptr()
+                    op.f[q][k] = fz
         self.op = op
 
 

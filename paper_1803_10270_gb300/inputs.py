@@ -15,7 +15,9 @@ Workloads follow the paper's two problem classes:
   sum of separable products exp(sin(x_i + phi_{m,i})) as initial condition
   (Section 4.1 studies advection in six dimensions with a separable initial state);
 - the linearised kinetic (BGK-type) equation f_t + v . grad_x f = -nu (f - M(v) rho)
-  (Section 4.2, eq. BGK_LIN and Table tab:ordering give the separable operator).
+  (Section 4.2, eq. BGK_LIN and Table tab:ordering give the separable operator);
+- variable-coefficient advection f_t + sum_j (C z)_j df/dz_j = 0 (Section 4.1, eq. PDE-advR,
+  Table tab:ordering0) with the initial condition exp(-|z|^2).
 """
 from __future__ import annotations
 
@@ -212,3 +214,59 @@ def kinetic_case(n: int, nu: float = 1.0, seed: int | None = None, cfg_index: in
     if seed is None:
         seed = SEED_BASE + cfg_index
     return KineticCase(n=n, nu=nu, seed=seed)
+
+
+# the paper's evaluation point z* = (h, ..., h) of the pointwise error (Section 4.1)
+Z_STAR = 0.698835274542439
+
+
+@dataclass
+class VarCoefCase:
+    """Seeded variable-coefficient advection problem f_t + sum_j (C z)_j df/dz_j = 0 on the
+    periodic box [-zmax, zmax)^N (Section 4.1, eq. PDE-advR; the paper uses zmax = 60).
+
+    Grid: z_j = -zmax + j h, h = 2 zmax / n.  C = S + K with S = diag(s_i), s_i ~ U[0.5, 1],
+    and K skew, K_jk = (a_jk - a_kj) / 2 with a_jk ~ U[-1, 1] (draw order: s_1..s_N, then a row
+    by row): every eigenvalue of C has real part in [0.5, 1] (for a unit eigenvector x,
+    x^* K x is imaginary), so exp(-tC) contracts as in the paper's experiment.  Initial
+    condition exp(-|z|^2), separable of rank 1.  dt = cfl h / (zmax max_j sum_k |C_jk|), the
+    largest transport speed on the box.
+    """
+
+    N: int
+    n: int
+    zmax: float
+    seed: int
+    cfl: float
+    C: np.ndarray = field(repr=False)
+
+    @property
+    def h(self) -> float:
+        return 2.0 * self.zmax / self.n
+
+    @property
+    def dt(self) -> float:
+        vmax = self.zmax * float(np.abs(self.C).sum(axis=1).max())
+        return self.cfl * self.h / vmax
+
+    def z(self) -> np.ndarray:
+        return -self.zmax + np.arange(self.n, dtype=np.float64) * self.h
+
+    def ic_factors(self) -> list[np.ndarray]:
+        """Per dimension an n x 1 array exp(-z^2)."""
+        return [np.exp(-self.z() ** 2)[:, None] for _ in range(self.N)]
+
+    def star_index(self) -> int:
+        """Grid index nearest to the paper's evaluation coordinate h = 0.698835274542439."""
+        return int(np.argmin(np.abs(self.z() - Z_STAR)))
+
+
+def varcoef_case(N: int, n: int, zmax: float = 60.0, cfl: float = 0.2, seed: int | None = None,
+                 cfg_index: int = 5) -> VarCoefCase:
+    if seed is None:
+        seed = SEED_BASE + cfg_index
+    g = SplitMix64(seed)
+    s = [g.uniform_range(0.5, 1.0) for _ in range(N)]
+    a = np.array([[g.uniform_range(-1.0, 1.0) for _ in range(N)] for _ in range(N)])
+    C = np.diag(s) + 0.5 * (a - a.T)
+    return VarCoefCase(N=N, n=n, zmax=zmax, seed=seed, cfl=cfl, C=C)

@@ -56,3 +56,23 @@ def apply_node_projector(full: np.ndarray, dims: list, P: np.ndarray) -> np.ndar
     Y = (P @ M).reshape(shp, order="F")
     inv = np.argsort(perm)
     return Y.transpose(inv)
+
+
+def varcoef_L_shifted_gaussian(zs: list, C: np.ndarray, mu) -> np.ndarray:
+    """-sum_j (C z)_j d/dz_j applied to g(z) = exp(-|z - mu|^2) on the full grid of the 1-D
+    grids zs: d g / dz_j = -2 (z_j - mu_j) g, so L g = 2 g sum_j (C z)_j (z_j - mu_j)."""
+    Zs = np.meshgrid(*zs, indexing="ij")
+    g = np.exp(-sum((Z - m) ** 2 for Z, m in zip(Zs, mu)))
+    N = len(zs)
+    out = np.zeros_like(g)
+    for j in range(N):
+        a = sum(C[j, k] * Zs[k] for k in range(N))
+        out += a * (Zs[j] - mu[j])
+    return 2.0 * g * out
+
+
+def varcoef_exact(t: float, C: np.ndarray, z) -> float:
+    """Characteristic solution f(z, t) = f0(exp(-tC) z) with f0 = exp(-|z|^2) (Section 4.1)."""
+    from scipy.linalg import expm
+    y = expm(-t * C) @ np.asarray(z, dtype=np.float64)
+    return float(np.exp(-(y @ y)))

@@ -181,3 +181,45 @@ def test_twelve_dim_full_size_steps(G):
         m1 = float(m[0])
         assert abs(m1 - m0) <= math.sqrt(float(n) ** d) * 1e-8 * nrm * 1.01
         m0 = m1
+
+
+def test_truncate_tall_node_matrices_rank_deficient(G):
+    """ht_truncate of a d=4 HT with every rank 24: the interior node matrices (576 x 24) are
+    reduced in row blocks plus a banded combine step.  A duplicated leaf column and a zero
+    transfer slice make node matrices rank deficient.  Ranks and T(u) against the oracle."""
+    d, n, r = 4, 30, 24
+    u = random_ht(d, n, r, seed=11, scale_decay=0.7)
+    tree = u.tree
+    leaf = next(t for t in range(tree.n_nodes) if tree.is_leaf(t))
+    inner = next(t for t in range(1, tree.n_nodes) if not tree.is_leaf(t))
+    u.node[leaf][:, 1] = u.node[leaf][:, 0]
+    u.node[inner][:, :, 5] = 0.0
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    for rel_tol in (1e-6, 1e-10, 1e-13):
+        ref, rep = OH.truncate(u, rel_tol, r)
+        g = to_gpu(G, u, r)
+        out = G.HTTensor(d, [n] * d, r)
+        G.ht_truncate(ctx, g, rel_tol, r, out)
+        sync()
+        ctx.check()
+        assert out.ranks() == rep.ranks, f"tol {rel_tol}"
+        assert rel_err(from_gpu(out, tree), ref) < TOL64, f"tol {rel_tol}"
+
+
+def test_untruncated_graded_spectrum_reproduces_u(G):
+    """A truncation that keeps every direction returns u to rounding, even when node spectra
+    span ten decades (transfer tensors graded by 0.7^j, rank 24): the projectors Y_t X_t of the
+    R-factor form are refined to X_t Y_t = I, so no 1/s_k amplification of SVD rounding remains
+    (without the refinement this case moved u by 2.5e-7)."""
+    d, n, r = 4, 30, 24
+    u = random_ht(d, n, r, seed=11, scale_decay=0.7)
+    ref, rep = OH.truncate(u, 1e-13, r)
+    assert rep.ranks[1:] == [r] * (2 * d - 2)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    g = to_gpu(G, u, r)
+    out = G.HTTensor(d, [n] * d, r)
+    G.ht_truncate(ctx, g, 1e-13, r, out)
+    sync()
+    ctx.check()
+    assert out.ranks() == rep.ranks
+    assert rel_err(from_gpu(out, u.tree), u) < 1e-13
