@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
-    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched"],
+    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef"],
                    help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
@@ -248,6 +248,8 @@ def run_gpu(args):
             res = run_d12(G, torch, flush, args.steps, warm)
         elif args.line == "ab2":
             res = run_ab2(G, torch, flush, args.steps, warm)
+        elif args.line == "varcoef":
+            res = run_varcoef(G, torch, flush, args.steps, warm)
         else:
             res = run_batched(G, torch, flush, args.batched, args.steps, warm)
         if rank == 0:
@@ -327,6 +329,9 @@ def run_gpu(args):
     # ---- the 12-D workload (n = 128, r_max 64, depth-4 tree), HT route alone, 100 RK2 steps
     d12 = run_d12(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
 
+    # ---- variable-coefficient advection (eq. PDE-advR) on the paper's 2-D grid, HEUN2
+    varcoef = run_varcoef(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
+
     # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
     batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
         if args.batched > 0 else None
@@ -348,6 +353,8 @@ def run_gpu(args):
         out["ab2"] = ab2
         if d12 is not None:
             out["d12"] = d12
+        if varcoef is not None:
+            out["varcoef"] = varcoef
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -458,6 +465,62 @@ def run_d12(G, torch, flush, steps: int, warmup: int) -> dict:
     return {"workload": D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
             "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step,
             "ht_ranks_final": ranks, "cuda_graph": True}
+
+
+VC_WORKLOAD = ("variable-coefficient advection f_t + (C z).grad f = 0 (eq. PDE-advR), N=2 on the paper's "
+               "grid: [-60,60)^2 with 600 nodes per variable, seeded C (eigenvalue real parts in [0.5,1]), "
+               "f0 = exp(-|z|^2), 4-term operator of Table tab:ordering0, HEUN2 (truncation after each "
+               "stage), HT r_max 12, tol 1e-8, dt = 0.2 h / max speed, FP64")
+
+
+def run_varcoef(G, torch, flush, steps: int, warmup: int) -> dict:
+    """HT steps/s of HEUN2 with the 4-term variable-coefficient operator on the paper's 2-D grid;
+    graph-captured, L2 flushed between steps.  Also the paper's accuracy measure: the relative
+    pointwise error at the grid point nearest z* = (0.6988.., 0.6988..) against the
+    characteristic solution f0(exp(-tC) z) at the final time (outside the timed region)."""
+    import numpy as np
+    from scipy.linalg import expm
+    from paper_1803_10270_gb300.inputs import varcoef_case
+    N, n, cap = 2, 600, 12
+    case = varcoef_case(N, n)
+    ctx = G.Context(N, [n] * N, cap=cap, max_terms=N * N)
+    u = G.HTTensor(N, [n] * N, cap)
+    u.upload(ic_nodes(u.tree, case.ic_factors(), np))
+    vop = G.VarCoefOp(case)
+    for _ in range(warmup):
+        G.ht_step(ctx, u, vop.op, case.dt, TOL, cap, scheme=G.HT_SCHEME_HEUN2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    l0 = ctx.launches()
+    with torch.cuda.graph(graph):
+        G.ht_step(ctx, u, vop.op, case.dt, TOL, cap, scheme=G.HT_SCHEME_HEUN2,
+                  stream=torch.cuda.current_stream())
+    per_step = ctx.launches() - l0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max, value = aggregate_replicas(ms, steps)
+    ranks = u.ranks()
+    nodes = u.download()
+    del graph
+    ctx.close()
+    t_end = (warmup + steps) * case.dt
+    i = case.star_index()
+    a, b = u.tree.c1[0], u.tree.c2[0]          # the two leaves (z_1, z_2) of the 2-D tree
+    f_num = float(nodes[a][i, :] @ nodes[0] @ nodes[b][i, :])
+    zp = np.array([case.z()[i]] * N)
+    y = expm(-t_end * case.C) @ zp
+    f_ex = float(np.exp(-(y @ y)))
+    return {"workload": VC_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "ht_ranks_final": ranks,
+            "t_end": t_end, "pointwise_rel_err_at_z_star": abs(f_num - f_ex) / f_ex, "cuda_graph": True}
 
 
 def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:

@@ -33,9 +33,15 @@ constexpr int QR_SMEM_BYTES = 96 * 1024;
 // Largest number of row blocks (CTAs) per matrix in the two-stage form.
 constexpr int QR_MAXSPLIT = 8;
 
-// Householder reflector of column j from x0 = S[j, j] and t = sum_{i > j} S[i, j]^2 (lane 0):
-// v = x - alpha e1 with alpha = -sign(x0) |x| stored over S[j, j], alpha into diag[j], and
-// tau = 2 / (v.v) (0 when the column is already zero below and on the diagonal).
+// A launch whose matrices leave SMs idle runs one CTA per SM anyway: it takes 200 KB, so larger
+// matrices, row blocks and stacks of the two-stage form stay in shared memory.  Matrices above
+// the 96 KB size are the ones split (below it a single sweep is faster).
+constexpr int QR_SMEM_WIDE = 200 * 1024;
+constexpr long long QR_SPLIT_MIN = QR_SMEM_BYTES / sizeof(double);
+
+// Householder reflector of column j (rows [j, mend)) from x0 = S[j, j] and t = sum_{i > j}
+// S[i, j]^2 (lane 0): v = x - alpha e1 with alpha = -sign(x0) |x| stored over S[j, j], alpha into
+// diag[j], and tau = 2 / (v.v) (0 when the column is already zero below and on the diagonal).
 __device__ inline double reflector(double* colj, int j, double t, double* diag) {
   const double x0 = colj[j];
   const double n2 = fma(x0, x0, t);
@@ -50,6 +56,39 @@ __device__ inline double reflector(double* colj, int j, double t, double* diag) 
     colj[j] = v0;
   }
   diag[j] = alpha;
+  return tau;
+}
+
+// 2^k as a double (|k| <= 1000)
+__device__ inline double pow2(int k) { return __longlong_as_double((long long)(k + 1023) << 52); }
+
+// The reflector by the whole warp (every lane holds t; lane 0's return value is tau).  A column
+// whose squared norm leaves [2^-600, 2^600] (a row block holding only far tails of a Gaussian,
+// say: entries near 1e-160 have subnormal squares, v.v underflows and tau = 2 / (v.v)
+// overflows) is first scaled by an exact power of two, its squared sub-column norm recomputed,
+// and the diagonal entry of R scaled back; the scaled vector gives the same reflection.
+__device__ inline double warp_reflector(double* colj, int j, int mend, double t, double* diag, int lane) {
+  const double x0 = colj[j];
+  const double n2 = fma(x0, x0, t);
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(n2);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  int k = 0;
+  if ((bits << 1) != 0) {
+    const int e = (ex == 0) ? -1074 : ex - 1023;   // subnormal: the smallest exponent
+    if (e < -600 || e > 600) k = -(e / 2);
+  }
+  if (k == 0) return lane == 0 ? reflector(colj, j, t, diag) : 0.0;
+  const double sc = pow2(k);
+  for (int i = j + lane; i < mend; i += 32) colj[i] *= sc;
+  __syncwarp();
+  double tt = 0.0;
+  for (int i = j + 1 + lane; i < mend; i += 32) tt = fma(colj[i], colj[i], tt);
+  tt = warp_sum(tt);
+  double tau = 0.0;
+  if (lane == 0) {
+    tau = reflector(colj, j, tt, diag);
+    diag[j] *= pow2(-k);
+  }
   return tau;
 }
 
@@ -99,7 +138,8 @@ __device__ void householder_r(double* S, long long ld, int m, int k, int band, d
     double s = 0.0;
     for (int i = 1 + lane; i < m0; i += 32) s = fma(S[i], S[i], s);
     s = warp_sum(s);
-    if (lane == 0) tau_sh[0] = reflector(S, 0, s, diag);
+    const double t0 = warp_reflector(S, 0, m0, s, diag, lane);
+    if (lane == 0) tau_sh[0] = t0;
   }
   __syncthreads();
   for (int j = 0; j < rmax; ++j) {
@@ -127,7 +167,8 @@ __device__ void householder_r(double* S, long long ld, int m, int k, int band, d
           }
           ss = warp_sum(ss);
           __syncwarp();
-          if (lane == 0) tau_sh[(j + 1) & 1] = reflector(cc, j + 1, ss, diag);
+          const double tj = warp_reflector(cc, j + 1, mj1, ss, diag, lane);
+          if (lane == 0) tau_sh[(j + 1) & 1] = tj;
           __syncwarp();
         } else {
           for (int i = j + lane; i < mj; i += 32) cc[i] = fma(-wgt, v[i], cc[i]);
@@ -176,7 +217,7 @@ __device__ double householder_flops(int m, int k, int band) {
 // Stage 1 costs about (m / ns) k^2 / 2 and the banded combine about ns k^3 / 6 element
 // updates, balanced at ns^2 = 3 m / k.
 __device__ inline int qr_splits(int m, int k, int gsplit, long long room) {
-  if (gsplit < 2 || m < 3 * k || (long long)(m | 1) * k <= room) return 1;
+  if (gsplit < 2 || m < 3 * k || (long long)(m | 1) * k <= QR_SPLIT_MIN - ((k + 1) & ~1)) return 1;
   int ns = 1;
   while (ns < gsplit && (long long)(ns + 1) * (ns + 1) * k <= 3LL * m) ++ns;
   while (ns > 1 && (long long)((ns * k) | 1) * k > room) --ns;              // stack in shared memory
@@ -292,7 +333,7 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(qr_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(qr_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_WIDE);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
@@ -301,7 +342,8 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   if (dev >= 0 && dev < 64 && sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
   const int nsm = (dev >= 0 && dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
   const int gsplit = ((long long)ndesc * count < nsm) ? QR_MAXSPLIT : 1;
-  qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, QR_SMEM_BYTES, s>>>(
-      descs_dev, inst_stride, (long long)(QR_SMEM_BYTES / sizeof(double)), gsplit, flops);
+  const int smem = gsplit > 1 ? QR_SMEM_WIDE : QR_SMEM_BYTES;
+  qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, smem, s>>>(
+      descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, flops);
   return cudaGetLastError();
 }

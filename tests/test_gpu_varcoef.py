@@ -66,3 +66,25 @@ def test_varcoef_apply_matches_oracle(G):
     ref = OH.apply_separable(u, [1.0] + [0.3 * a for a in alphas], [[None] * N] + factors)
     got = OH.HT(u.tree, list(out.n), out.download())
     assert np.allclose(OH.to_full(got), OH.to_full(ref), rtol=0, atol=1e-12 * np.abs(OH.to_full(ref)).max())
+
+
+def test_varcoef_paper_grid_tiny_row_blocks(G):
+    """The paper's 2-D grid ([-60, 60)^2, 600 nodes): the leaf matrices (600 rows) are reduced
+    in row blocks, and the blocks far from the origin hold only the Gaussian's tails (entries
+    down to 1e-300, squares below the normal range), where an unscaled Householder vector would
+    overflow tau = 2 / (v.v).  Three HEUN2 steps against the oracle."""
+    N, n, cap = 2, 600, 12
+    case = varcoef_case(N, n)
+    alphas, factors = varcoef_terms(case)
+    u = OH.from_cp(np.ones(1), case.ic_factors())
+    vop = G.VarCoefOp(case)
+    ctx = G.Context(N, [n] * N, cap=cap, max_terms=N * N)
+    g = G.HTTensor(N, [n] * N, cap)
+    g.upload(u.node)
+    for step in range(3):
+        u, reps = OH.step_heun2(u, alphas, factors, case.dt, 1e-8, cap)
+        G.ht_step(ctx, g, vop.op, case.dt, 1e-8, cap, scheme=G.HT_SCHEME_HEUN2)
+        sync()
+        ctx.check()
+        assert g.ranks() == reps[1].ranks, f"step {step}"
+        assert rel_err(OH.HT(u.tree, list(g.n), g.download()), u) < TOL64, f"step {step}"
