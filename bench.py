@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
-    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef"],
+    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt"],
                    help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
@@ -250,6 +250,8 @@ def run_gpu(args):
             res = run_ab2(G, torch, flush, args.steps, warm)
         elif args.line == "varcoef":
             res = run_varcoef(G, torch, flush, args.steps, warm)
+        elif args.line == "tt":
+            res = run_tt(G, torch, flush, args.steps, warm)
         else:
             res = run_batched(G, torch, flush, args.batched, args.steps, warm)
         if rank == 0:
@@ -329,6 +331,9 @@ def run_gpu(args):
     # ---- the 12-D workload (n = 128, r_max 64, depth-4 tree), HT route alone, 100 RK2 steps
     d12 = run_d12(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
 
+    # ---- the same HT workload in tensor-train form (linear dimension tree)
+    tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
+
     # ---- variable-coefficient advection (eq. PDE-advR) on the paper's 2-D grid, HEUN2
     varcoef = run_varcoef(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
 
@@ -355,6 +360,8 @@ def run_gpu(args):
             out["d12"] = d12
         if varcoef is not None:
             out["varcoef"] = varcoef
+        if tt is not None:
+            out["tt"] = tt
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -429,15 +436,20 @@ D12_WORKLOAD = ("12-D advection n=128 (cfg5): depth-4 tree, seeded separable ran
                 "HT r_max 64, tol 1e-8, RK2 dt=0.2h, FP64 throughout")
 
 
-def run_d12(G, torch, flush, steps: int, warmup: int) -> dict:
+TT_WORKLOAD = ("6-D advection n=64 (cfg2) HT route in tensor-train form (the linear dimension tree, "
+               "Section 2.2), r_max 32, tol 1e-8, RK2 dt=0.2h, FP64")
+
+
+def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128, cap: int = 64,
+            n_terms: int = 3, cfg_index: int = 4, tree: int = 0, workload: str = None) -> dict:
     """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
-    64): the timed steps graph-captured, L2 flushed between them."""
+    64), or another advection workload and tree: the timed steps graph-captured, L2 flushed
+    between them."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
-    d, n, cap = 12, 128, 64
-    case = advection_case(d, n, n_terms=3, cfg_index=4)
-    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1)
-    u = G.HTTensor(d, [n] * d, cap)
+    case = advection_case(d, n, n_terms=n_terms, cfg_index=cfg_index)
+    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree)
+    u = G.HTTensor(d, [n] * d, cap, tree=tree)
     u.upload(ic_nodes(u.tree, case.ic_factors(), np))
     op = G.advection_op(case.c, case.h)
     for _ in range(warmup):
@@ -462,7 +474,7 @@ def run_d12(G, torch, flush, steps: int, warmup: int) -> dict:
     ranks = u.ranks()
     del graph
     ctx.close()
-    return {"workload": D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+    return {"workload": workload or D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
             "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step,
             "ht_ranks_final": ranks, "cuda_graph": True}
 
@@ -471,6 +483,12 @@ VC_WORKLOAD = ("variable-coefficient advection f_t + (C z).grad f = 0 (eq. PDE-a
                "grid: [-60,60)^2 with 600 nodes per variable, seeded C (eigenvalue real parts in [0.5,1]), "
                "f0 = exp(-|z|^2), 4-term operator of Table tab:ordering0, HEUN2 (truncation after each "
                "stage), HT r_max 12, tol 1e-8, dt = 0.2 h / max speed, FP64")
+
+
+def run_tt(G, torch, flush, steps: int, warmup: int) -> dict:
+    """The configuration-2 HT route on the linear (tensor-train) tree."""
+    return run_d12(G, torch, flush, steps, warmup, d=D, n=N, cap=RMAX, n_terms=2, cfg_index=1, tree=1,
+                   workload=TT_WORKLOAD)
 
 
 def run_varcoef(G, torch, flush, steps: int, warmup: int) -> dict:

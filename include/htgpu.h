@@ -25,10 +25,13 @@
  *    ht_ctx_check() reads (synchronising) and clears.
  *
  * Tree and node numbering
- *  The dimension range [a, b) of a node splits at a + floor((b-a)/2); for d = 6 this is
- *  {1,2,3}|{4,5,6}, then {1}|{2,3} and {4}|{5,6} (Section 2.2, eq. HTD).  Nodes are
+ *  HT_TREE_BALANCED: the dimension range [a, b) of a node splits at a + floor((b-a)/2); for
+ *  d = 6 this is {1,2,3}|{4,5,6}, then {1}|{2,3} and {4}|{5,6} (Section 2.2, eq. HTD).
+ *  HT_TREE_LINEAR: [a, b) splits at a + 1 ({a} | [a+1, b)), the degenerate tree of the
+ *  tensor-train format (Section 2.2 names TT as the special case of HT on such a tree): the
+ *  interior node [i, d) holds the TT core of dimension i, contracted with leaf i.  Nodes are
  *  numbered breadth first from the root (node 0); 2d-1 nodes, d leaves.  ht_tree_info()
- *  returns the numbering.
+ *  returns the numbering.  A tensor's buffers follow the tree of the context it is used with.
  *
  * Storage of an HT tensor (packed with the CURRENT ranks, first index fastest)
  *  leaf t of dimension i:  U[j + n_i * a],             0 <= a < k_t
@@ -121,6 +124,11 @@ typedef struct ht_op {
 /* ---------------------------------------------------------------- context --- */
 typedef struct ht_ctx ht_ctx;
 
+typedef enum ht_tree_kind {
+  HT_TREE_BALANCED = 0,    /* balanced binary dimension tree (eq. HTD) */
+  HT_TREE_LINEAR = 1       /* {a} | [a+1, b) at every node: the tensor-train tree */
+} ht_tree_kind;
+
 typedef struct ht_config {
   int d;                   /* dimensions of the tensors this context serves */
   int n[HT_MAXD];          /* grid points per dimension */
@@ -128,6 +136,7 @@ typedef struct ht_config {
   int max_terms;           /* largest operator term count used with ht_step/ht_apply */
   int precision;           /* ht_precision */
   int device;              /* CUDA device ordinal */
+  int tree;                /* ht_tree_kind */
 } ht_config;
 
 /* Workspace bytes a context with this configuration allocates (0 on bad config). */
@@ -164,7 +173,7 @@ const char* ht_status_string(int status);
 /* Node numbering of the balanced tree for d dimensions.  Each output array holds
  * 2d-1 ints: lo/hi = dimension range [lo, hi), c1/c2 = children (-1 for leaves),
  * parent (-1 for the root), depth.  Returns HT_ERR_ARG for d outside [2, HT_MAXD]. */
-int ht_tree_info(int d, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth);
+int ht_tree_info(int d, int kind, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth);
 
 /* ------------------------------------------------------------- HT calls ----- */
 typedef enum ht_apply_mode {

@@ -1,10 +1,13 @@
-"""Balanced binary dimension tree (Section 2.2, eq. HTD).
+"""Dimension trees (Section 2.2, eq. HTD).
 
-The paper splits the six variables {1..6} as {1,2,3}|{4,5,6} and then {1}|{2,3},
+Balanced: the paper splits the six variables {1..6} as {1,2,3}|{4,5,6} and then {1}|{2,3},
 {4}|{5,6} (eq. HTD / coreT).  Generalised: the index range [a, b) splits at
-a + floor((b - a)/2).  Nodes are numbered breadth first from the root (node 0).
+a + floor((b - a)/2).  Linear: [a, b) splits at a + 1 ({a} | [a+1, b)), the degenerate tree on
+which HT is the tensor-train format (Section 2.2).  Nodes are numbered breadth first from the
+root (node 0).
 
-Parity: pinned by tests (the d = 6 split reproduces the paper's grouping; 2d-1 nodes).
+Parity: pinned by tests (the d = 6 split reproduces the paper's grouping; 2d-1 nodes; on the
+linear tree the node singular values equal those of the TT unfoldings of the full tensor).
 """
 from __future__ import annotations
 
@@ -42,15 +45,17 @@ class Tree:
         return [[t for t in range(self.n_nodes) if self.depth[t] == k] for k in range(m + 1)]
 
 
-def build_tree(d: int) -> Tree:
+def build_tree(d: int, kind: str = "balanced") -> Tree:
     if d < 2:
         raise ValueError("HT needs d >= 2")
+    if kind not in ("balanced", "linear"):
+        raise ValueError(kind)
     lo, hi, children, parent, depth = [0], [d], [None], [-1], [0]
     t = 0
     while t < len(lo):
         a, b = lo[t], hi[t]
         if b - a > 1:
-            m = a + (b - a) // 2
+            m = a + 1 if kind == "linear" else a + (b - a) // 2
             c1 = len(lo)
             lo += [a, m]
             hi += [m, b]

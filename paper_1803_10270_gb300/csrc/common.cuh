@@ -22,7 +22,7 @@ struct TreeInfo {
   int parent[HT_MAXNODES], depth[HT_MAXNODES];
   int max_depth;
 };
-void htg_build_tree(int d, TreeInfo* t);
+void htg_build_tree(int d, int kind, TreeInfo* t);   // kind: ht_tree_kind
 
 // --------------------------------------------------------- work descriptors --
 // Batched GEMM: C[b] = alpha * op(A[b]) * op(B[b]) * diag(colscale) + beta * C[b],

@@ -23,7 +23,7 @@
 #include "common.cuh"
 
 // ------------------------------------------------------------------- tree -----
-void htg_build_tree(int d, TreeInfo* t) {
+void htg_build_tree(int d, int kind, TreeInfo* t) {
   memset(t, 0, sizeof(*t));
   t->d = d;
   int n = 1;
@@ -31,7 +31,7 @@ void htg_build_tree(int d, TreeInfo* t) {
   for (int i = 0; i < n; ++i) {
     const int a = t->lo[i], b = t->hi[i];
     if (b - a > 1) {
-      const int m = a + (b - a) / 2;
+      const int m = (kind == HT_TREE_LINEAR) ? a + 1 : a + (b - a) / 2;
       t->c1[i] = n; t->c2[i] = n + 1;
       t->lo[n] = a; t->hi[n] = m; t->lo[n + 1] = m; t->hi[n + 1] = b;
       t->parent[n] = t->parent[n + 1] = i;
@@ -51,7 +51,7 @@ void htg_build_tree(int d, TreeInfo* t) {
 namespace {
 
 constexpr int NN = HT_MAXNODES;
-constexpr int MAXLEV = 6;
+constexpr int MAXLEV = HT_MAXD;   // tree depth + 1 (the linear tree of d = 16 is 15 deep)
 
 // Device-side plan: dimensions derived from the device-resident ranks, plus every work
 // descriptor of one truncation.  Slots per level follow the host's level lists.
@@ -780,6 +780,7 @@ static bool cfg_valid(const ht_config* c) {
     return false;
   for (int i = 0; i < c->d; ++i)
     if (c->n[i] < 1) return false;
+  if (c->tree != HT_TREE_BALANCED && c->tree != HT_TREE_LINEAR) return false;
   return c->precision == HT_PREC_FP64 || c->precision == HT_PREC_MIXED;
 }
 
@@ -847,7 +848,7 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
 extern "C" size_t ht_workspace_bytes(const ht_config* cfg) {
   if (!cfg_valid(cfg)) return 0;
   TreeInfo T;
-  htg_build_tree(cfg->d, &T);
+  htg_build_tree(cfg->d, cfg->tree, &T);
   WsLayout W;
   layout(cfg, T, &W);
   return W.total;
@@ -860,7 +861,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   if (cudaSetDevice(cfg->device) != cudaSuccess) return HT_ERR_CUDA;
   ht_ctx* c = new ht_ctx();
   c->cfg = *cfg;
-  htg_build_tree(cfg->d, &c->tree);
+  htg_build_tree(cfg->d, cfg->tree, &c->tree);
   build_levels(c->tree, &c->lev);
   c->Kc = trunc_input_cap(cfg);
   c->cap = cfg->cap;
@@ -952,10 +953,10 @@ extern "C" const char* ht_status_string(int s) {
   return "HT_ERR_UNKNOWN";
 }
 
-extern "C" int ht_tree_info(int d, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth) {
-  if (d < 2 || d > HT_MAXD) return HT_ERR_ARG;
+extern "C" int ht_tree_info(int d, int kind, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth) {
+  if (d < 2 || d > HT_MAXD || (kind != HT_TREE_BALANCED && kind != HT_TREE_LINEAR)) return HT_ERR_ARG;
   TreeInfo T;
-  htg_build_tree(d, &T);
+  htg_build_tree(d, kind, &T);
   for (int t = 0; t < T.nn; ++t) {
     if (lo) lo[t] = T.lo[t];
     if (hi) hi[t] = T.hi[t];
@@ -1304,9 +1305,11 @@ extern "C" int ht_batch_create(ht_batch** out, int count, ht_ctx* const* ctxs, h
   if (count < 1 || count > 65535 || !ctxs || !us) return HT_ERR_ARG;
   const int d = ctxs[0] ? ctxs[0]->cfg.d : 0;
   const int dev = ctxs[0] ? ctxs[0]->cfg.device : 0;
+  const int tree = ctxs[0] ? ctxs[0]->cfg.tree : 0;
   for (int i = 0; i < count; ++i) {
     ht_ctx* c = ctxs[i];
-    if (!c || c->cfg.d != d || c->cfg.device != dev || c->batch || !tensor_matches(c, us[i])) return HT_ERR_ARG;
+    if (!c || c->cfg.d != d || c->cfg.device != dev || c->cfg.tree != tree || c->batch || !tensor_matches(c, us[i]))
+      return HT_ERR_ARG;
     if (us[i]->cap > c->cap) return HT_ERR_CAPACITY;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return HT_ERR_ARG;   // each instance needs its own workspace

@@ -26,6 +26,7 @@ HT_PREC_FP64, HT_PREC_MIXED = 0, 1
 HT_F_IDENTITY, HT_F_STENCIL, HT_F_DIAG, HT_F_RANK1, HT_F_DIAG_STENCIL = 0, 1, 2, 3, 4
 HT_APPLY_L, HT_APPLY_EULER, HT_APPLY_RK2POLY = 0, 1, 2
 HT_SCHEME_RK2POLY, HT_SCHEME_HEUN2 = 0, 1
+HT_TREE_BALANCED, HT_TREE_LINEAR = 0, 1
 CP_ALS_GS, CP_ALS_JACOBI_DAMPED = 0, 1
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libhtgpu.so")
@@ -53,7 +54,7 @@ class ht_op(C.Structure):
 
 class ht_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int * HT_MAXD), ("cap", C.c_int), ("max_terms", C.c_int),
-                ("precision", C.c_int), ("device", C.c_int)]
+                ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int)]
 
 
 _EXPORTS = {
@@ -66,7 +67,7 @@ _EXPORTS = {
     "ht_ctx_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "ht_ctx_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double)]),
-    "ht_tree_info": (C.c_int, [C.c_int] + [C.POINTER(C.c_int)] * 6),
+    "ht_tree_info": (C.c_int, [C.c_int, C.c_int] + [C.POINTER(C.c_int)] * 6),
     "ht_apply": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_op), C.c_double, C.c_int,
                            C.POINTER(ht_tensor), C.c_void_p]),
     "ht_truncate": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.c_double, C.c_int, C.POINTER(ht_tensor),
@@ -155,10 +156,10 @@ class TreeInfo:
         return self.c1[t] < 0
 
 
-def tree_info(d: int) -> TreeInfo:
+def tree_info(d: int, tree: int = 0) -> TreeInfo:
     lib = load()
     arrs = [(C.c_int * HT_MAXNODES)() for _ in range(6)]
-    _check(lib.ht_tree_info(d, *arrs), "ht_tree_info")
+    _check(lib.ht_tree_info(d, tree, *arrs), "ht_tree_info")
     nn = 2 * d - 1
     return TreeInfo(d, *[list(a)[:nn] for a in arrs])
 
@@ -168,7 +169,7 @@ class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
     def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
-                 device: int = 0):
+                 device: int = 0, tree: int = 0):
         lib = load()
         cfg = ht_config()
         cfg.d = d
@@ -178,6 +179,7 @@ class Context:
         cfg.max_terms = max_terms
         cfg.precision = precision
         cfg.device = device
+        cfg.tree = tree
         self.cfg = cfg
         self.d, self.n, self.cap, self.device = d, list(n), cap, device
         self.ptr = C.c_void_p()
@@ -222,10 +224,10 @@ class Context:
 class HTTensor:
     """Device buffers of an HT tensor (capacity `cap`) plus its ht_tensor struct."""
 
-    def __init__(self, d: int, n, cap: int, device="cuda"):
+    def __init__(self, d: int, n, cap: int, device="cuda", tree: int = 0):
         import torch
         self.d, self.n, self.cap = d, list(n), cap
-        self.tree = tree_info(d)
+        self.tree = tree_info(d, tree)
         # one device allocation (`blob`) holds every node buffer at 256-byte aligned offsets, so
         # the whole state moves between host and device in one copy
         sizes = []

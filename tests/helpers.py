@@ -8,9 +8,10 @@ from oracle.tree import build_tree
 from paper_1803_10270_gb300.inputs import normal_arrays
 
 
-def random_ht(d, ns, rank, seed, scale_decay=None):
-    """Random HT with every non-root rank = rank (leaves min(n, rank) not enforced)."""
-    tree = build_tree(d)
+def random_ht(d, ns, rank, seed, scale_decay=None, kind="balanced"):
+    """Random HT with every non-root rank = rank (leaves min(n, rank) not enforced), on the
+    balanced or the linear (tensor-train) tree."""
+    tree = build_tree(d, kind)
     ns = [ns] * d if np.isscalar(ns) else list(ns)
     rk = {t: (1 if t == 0 else rank) for t in range(tree.n_nodes)}
     shapes = []

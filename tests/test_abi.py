@@ -42,9 +42,9 @@ def test_exports_every_declared_symbol(lib):
 def test_tree_info_matches_oracle(lib):
     from oracle.tree import build_tree
     from paper_1803_10270_gb300 import htgpu as G
-    for d in (2, 3, 6, 7, 12, 16):
-        ti = G.tree_info(d)
-        to = build_tree(d)
+    for d, kind in [(d, k) for d in (2, 3, 6, 7, 12, 16) for k in ("balanced", "linear")]:
+        ti = G.tree_info(d, 0 if kind == "balanced" else 1)
+        to = build_tree(d, kind)
         assert ti.lo == to.lo and ti.hi == to.hi
         for t in range(to.n_nodes):
             ch = to.children[t]
@@ -55,8 +55,9 @@ def test_tree_info_matches_oracle(lib):
 def test_host_side_argument_errors(lib):
     from paper_1803_10270_gb300 import htgpu as G
     arrs = [(C.c_int * 31)() for _ in range(6)]
-    assert lib.ht_tree_info(1, *arrs) == G.HT_ERR_ARG
-    assert lib.ht_tree_info(17, *arrs) == G.HT_ERR_ARG
+    assert lib.ht_tree_info(1, 0, *arrs) == G.HT_ERR_ARG
+    assert lib.ht_tree_info(4, 2, *arrs) == G.HT_ERR_ARG
+    assert lib.ht_tree_info(17, 0, *arrs) == G.HT_ERR_ARG
     cfg = G.ht_config()
     cfg.d = 1
     assert lib.ht_workspace_bytes(C.byref(cfg)) == 0
