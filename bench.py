@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
-    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt"],
+    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn"],
                    help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
@@ -252,6 +252,8 @@ def run_gpu(args):
             res = run_varcoef(G, torch, flush, args.steps, warm)
         elif args.line == "tt":
             res = run_tt(G, torch, flush, args.steps, warm)
+        elif args.line == "cn":
+            res = run_cn(G, torch, flush, args.steps, warm)
         else:
             res = run_batched(G, torch, flush, args.batched, args.steps, warm)
         if rank == 0:
@@ -334,6 +336,9 @@ def run_gpu(args):
     # ---- the same HT workload in tensor-train form (linear dimension tree)
     tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
 
+    # ---- implicit Crank-Nicolson step in CP format (ALS), kinetic operator
+    cn = run_cn(G, torch, flush, 50, max(args.warmup, 3)) if args.d12 else None
+
     # ---- variable-coefficient advection (eq. PDE-advR) on the paper's 2-D grid, HEUN2
     varcoef = run_varcoef(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
 
@@ -362,6 +367,8 @@ def run_gpu(args):
             out["varcoef"] = varcoef
         if tt is not None:
             out["tt"] = tt
+        if cn is not None:
+            out["cn"] = cn
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -483,6 +490,59 @@ VC_WORKLOAD = ("variable-coefficient advection f_t + (C z).grad f = 0 (eq. PDE-a
                "grid: [-60,60)^2 with 600 nodes per variable, seeded C (eigenvalue real parts in [0.5,1]), "
                "f0 = exp(-|z|^2), 4-term operator of Table tab:ordering0, HEUN2 (truncation after each "
                "stage), HT r_max 12, tol 1e-8, dt = 0.2 h / max speed, FP64")
+
+
+CN_WORKLOAD = ("linearised 6-D kinetic equation (cfg3 operator, 5 separable terms), n=16 per variable, "
+               "Crank-Nicolson step solved in CP format by ALS (eqs. CNFDE, ALS2, ML, MR): CP rank 6 "
+               "(seeded kinetic initial condition), 5 Gauss-Seidel sweeps per step, dt = 5x the explicit "
+               "step, FP64")
+
+
+def run_cn(G, torch, flush, steps: int, warmup: int) -> dict:
+    """Implicit steps/s: each step copies x into x_n (the previous level and the initial guess)
+    and runs cp_cn_als_step; graph-captured, L2 flushed between steps."""
+    from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+    n, sweeps = 16, 5
+    kc = kinetic_case(n)
+    w0, F0 = kinetic_ic(kc)
+    r = len(w0)
+    ctx = G.Context(6, [n] * 6, cap=r, max_terms=5)
+    kop = G.KineticOp(kc)
+    x = G.CPTensor(6, [n] * 6, r)
+    xn = G.CPTensor(6, [n] * 6, r)
+    x.upload(w0, F0)
+    xn.upload(w0, F0)
+    dt = 5 * kc.dt
+
+    def step(stream=None):
+        xn.blob.copy_(x.blob)
+        G.cp_cn_als_step(ctx, xn, kop.op, dt, x, sweeps, stream=stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    l0 = ctx.launches()
+    with torch.cuda.graph(graph):
+        step(stream=torch.cuda.current_stream())
+    per_step = ctx.launches() - l0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max, value = aggregate_replicas(ms, steps)
+    del graph
+    ctx.close()
+    return {"workload": CN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "cp_rank": r, "sweeps": sweeps,
+            "cuda_graph": True}
 
 
 def run_tt(G, torch, flush, steps: int, warmup: int) -> dict:

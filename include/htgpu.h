@@ -315,6 +315,24 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
  * others wait out the bounded limit (about 0.2 s of SM clock) and report instead of hanging.
  * Synchronising (allocates and frees its own 2 KB).  Returns HT_OK when every CTA passed, the
  * device-reported HT_ERR_TIMEOUT when the barrier gave up, or HT_ERR_ARG / HT_ERR_CUDA. */
+/* One Crank-Nicolson step solved in CP format by alternating least squares (Section 3.3, eqs.
+ * CNFDE, BLs, rRr1, ALS2, ML, MR): x minimises |A x - B x_n| with A = I - dt/2 L and
+ * B = I + dt/2 L, over the factors of x at its current rank, Gauss-Seidel over the dimensions,
+ * `sweeps` sweeps (1..64).  Mode q solves the (n_q r) x (n_q r) normal equations
+ * M vec(X_q) = vec(R) (eq. ALS2 on the grid basis; M = sum_{e,z} eta_e eta_z Gamma^{ez} kron
+ * (E_q^e)^T E_q^z, eq. ML) by Cholesky.  x: the initial guess on entry (e.g. a copy of x_n),
+ * the result on return; its weights are folded into its first factor, so they are 1 on
+ * return.  x_n: read only, must not share factor buffers with x.  L: any separable operator
+ * (n_terms <= min(HT_MAXBLOCKTERMS, the context's max_terms); every factor kind).  eps_dev
+ * (optional, device): per sweep the largest |X_q^new - X_q^old|^2 (the paper's convergence
+ * measure).  Ranks <= the context's cap.  The first call on a context allocates its workspace
+ * (about (T^2 d + T d) n^2 + (n cap)^2 doubles, T = max_terms + 1): make it before capturing a
+ * graph (a capture that would allocate returns HT_ERR_ARG).  A system that is not positive
+ * definite sets HT_ERR_NONFINITE (ht_ctx_check) and leaves that factor unchanged.  Errors:
+ * HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_NOMEM, HT_ERR_CUDA. */
+int cp_cn_als_step(ht_ctx* ctx, const cp_tensor* x_n, const ht_op* L, double dt, cp_tensor* x, int sweeps,
+                   double* eps_dev, void* stream);
+
 int ht_selftest_grid_barrier(int nblocks, int absent, int device);
 
 #ifdef __cplusplus

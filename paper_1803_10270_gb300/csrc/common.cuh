@@ -203,6 +203,10 @@ int htg_ctx_d(const ht_ctx* c);
 const int* htg_ctx_n(const ht_ctx* c);
 int* htg_ctx_err(ht_ctx* c);
 int htg_ctx_grid(const ht_ctx* c);
+int htg_ctx_cap(const ht_ctx* c);
+int htg_ctx_max_terms(const ht_ctx* c);
+int htg_ctx_device(const ht_ctx* c);
+void** htg_ctx_cn_ws(ht_ctx* c, size_t** bytes);   // lazily allocated Crank-Nicolson ALS workspace
 void htg_ctx_count(ht_ctx* c, int launches, cudaStream_t s);
 int htg_cp_terms(int d);   // 1 + 2d + d(d-1)/2
 

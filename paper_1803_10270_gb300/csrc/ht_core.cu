@@ -163,6 +163,8 @@ struct ht_ctx {
   int gemm_grid = 0;
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
+  void* cn_ws = nullptr;       // Crank-Nicolson ALS workspace (allocated by its first call)
+  size_t cn_bytes = 0;
 };
 
 namespace {
@@ -925,6 +927,7 @@ extern "C" void ht_ctx_destroy(ht_ctx* ctx) {
   if (!ctx) return;
   for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->cn_ws) cudaFree(ctx->cn_ws);
   delete ctx;
 }
 
@@ -1516,6 +1519,13 @@ int htg_ctx_d(const ht_ctx* c) { return c->cfg.d; }
 const int* htg_ctx_n(const ht_ctx* c) { return c->cfg.n; }
 int* htg_ctx_err(ht_ctx* c) { return c->err; }
 int htg_ctx_grid(const ht_ctx* c) { return c->gemm_grid; }
+int htg_ctx_cap(const ht_ctx* c) { return c->cfg.cap; }
+int htg_ctx_max_terms(const ht_ctx* c) { return c->cfg.max_terms; }
+int htg_ctx_device(const ht_ctx* c) { return c->cfg.device; }
+void** htg_ctx_cn_ws(ht_ctx* c, size_t** bytes) {
+  *bytes = &c->cn_bytes;
+  return &c->cn_ws;
+}
 void htg_ctx_count(ht_ctx* c, int launches, cudaStream_t s) {
   c->launches += launches;
   c->last_stream = s;

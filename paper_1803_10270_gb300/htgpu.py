@@ -92,6 +92,8 @@ _EXPORTS = {
     "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
+    "cp_cn_als_step": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
+                                 C.POINTER(cp_tensor), C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -521,6 +523,13 @@ def cp_als_sweep_rk2(ctx: Context, x_old: CPTensor, op: ht_op, dt: float, x: CPT
     _check(load().cp_als_sweep_rk2(ctx.ptr, C.byref(x_old.struct), C.byref(op), dt, C.byref(x.struct), sweeps,
                                    variant, C.c_void_p(eps.data_ptr() if eps is not None else 0),
                                    _stream_ptr(stream)), "cp_als_sweep_rk2")
+
+
+def cp_cn_als_step(ctx: Context, x_n: CPTensor, op: ht_op, dt: float, x: CPTensor, sweeps: int, eps=None,
+                   stream=None):
+    _check(load().cp_cn_als_step(ctx.ptr, C.byref(x_n.struct), C.byref(op), dt, C.byref(x.struct), sweeps,
+                                 C.c_void_p(eps.data_ptr() if eps is not None else 0), _stream_ptr(stream)),
+           "cp_cn_als_step")
 
 
 def cp_als_sweep_noalloc(y: CPTensor, x: CPTensor, sweeps: int, variant: int = CP_ALS_GS, eps=None, status=None,
