@@ -416,6 +416,58 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
   }
 }
 
+// The two Newton steps Y <- Y (2I - X Y) of every node in one launch (one CTA per node,
+// blockIdx.y the instance): X (k x K, ld k) and Y (K x k, ld K) are those of the node's
+// descriptors in g_bi[0] (A, B); N = 2I - X Y and Y2 = Y N live in shared memory when
+// 3 k K + k^2 doubles fit, else in the node's SW and P buffers (the descriptors' outputs).
+constexpr int BIORTH_SMEM = 96 * 1024;
+__global__ void __launch_bounds__(256) biorth_kernel(const GemmDesc* d0, const GemmDesc* d1, long long inst_stride) {
+  const GemmDesc g0 = ((const GemmDesc*)((const char*)d0 + inst_stride * blockIdx.y))[blockIdx.x];
+  const GemmDesc g1 = ((const GemmDesc*)((const char*)d1 + inst_stride * blockIdx.y))[blockIdx.x];
+  const int k = g0.m, K = g0.k;
+  if (k <= 0 || K <= 0) return;
+  double* Yg = const_cast<double*>(g0.B);
+  extern __shared__ double sh[];
+  const long long need = 3LL * k * K + (long long)k * k;
+  const bool fits = need <= (long long)(BIORTH_SMEM / sizeof(double));
+  const double* X = g0.A;
+  const double* Y = Yg;
+  double* N = g0.C;
+  double* Y2 = g1.C;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (fits) {
+    double* Xs = sh;
+    double* Ys = Xs + (long long)k * K;
+    N = Ys + (long long)K * k;
+    Y2 = N + (long long)k * k;
+    for (int e = tid; e < k * K; e += nt) {
+      Xs[e] = g0.A[e];
+      Ys[e] = Yg[e];
+    }
+    X = Xs;
+    Y = Ys;
+    __syncthreads();
+  }
+  for (int it = 0; it < 2; ++it) {
+    const double* Yc = (it == 0) ? Y : Y2;
+    for (int e = tid; e < k * k; e += nt) {
+      const int a = e % k, b = e / k;
+      double acc = 0.0;
+      for (int c = 0; c < K; ++c) acc = fma(X[a + (long long)k * c], Yc[c + (long long)K * b], acc);
+      N[e] = (a == b ? 2.0 : 0.0) - acc;
+    }
+    __syncthreads();
+    double* out = (it == 0) ? Y2 : Yg;
+    for (int e = tid; e < K * k; e += nt) {
+      const int c = e % K, b = e / K;
+      double acc = 0.0;
+      for (int a = 0; a < k; ++a) acc = fma(Yc[c + (long long)K * a], N[a + (long long)k * b], acc);
+      out[e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtView out, const WsNode* wn,
                                    double rel_tol, int rmax, double* sigma_out, int sig_stride, double* norm_out,
                                    int* err) {
@@ -913,6 +965,11 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     delete c;
     return HT_ERR_CUDA;
   }
+  if (cudaFuncSetAttribute(biorth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BIORTH_SMEM) != cudaSuccess) {
+    cudaFree(c->ws);
+    delete c;
+    return HT_ERR_CUDA;
+  }
   // SVD working copy in shared memory when the capacity allows
   const size_t Kc = (size_t)c->Kc;
   c->svd_smem = ((2 * Kc * Kc + Kc) * sizeof(double) <= 200 * 1024) ? 1 : 0;
@@ -1032,8 +1089,9 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st));
   HTG_LAUNCH(c, KC_PLAN, s, sel());
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM), count, st));
-  for (int ph = 0; ph < 4; ++ph)
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_bi[ph], T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s,
+             (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
+              cudaGetLastError()));
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   if (L.n_proj3 > 0)

@@ -95,3 +95,17 @@ def test_cn_uniform_maxwellian_fixed_point(G):
     kop = G.KineticOp(kc)
     got, _ = run_gpu(G, 6, 8, kop.op, kc.dt, f, f, 2, cap=1, max_terms=5)
     assert rel(to_full(got), to_full(f)) < 1e-13
+
+
+def test_cn_large_system_in_global_memory(G):
+    """n r = 20 x 8 = 160 unknowns per mode: the 160 x 160 system no longer fits the solve's
+    shared memory and is factorised in its global buffer."""
+    case = varcoef_case(3, 20, zmax=5.0)
+    alphas, factors = varcoef_terms(case)
+    rng = np.random.default_rng(44)
+    xn = CP(np.ones(8), [rng.standard_normal((20, 8)) for _ in range(3)])
+    dt = 2 * case.dt
+    ref, _ = CN.cn_als_step(xn, xn, alphas, factors, dt, 2)
+    vop = G.VarCoefOp(case)
+    got, _ = run_gpu(G, 3, 20, vop.op, dt, xn, xn, 2, cap=8, max_terms=9)
+    assert rel(to_full(got), to_full(ref)) < 1e-10
