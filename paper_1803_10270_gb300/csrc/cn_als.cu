@@ -253,10 +253,12 @@ __global__ void __launch_bounds__(NT) cn_assemble_kernel(CnArgs a, CnWs w, CnDim
 // element threads packed the lanes better but its index arithmetic cost more: measured.)  Shared memory
 // when M fits (odd leading dimension), else the global buffer in place.  A pivot that is not
 // positive and finite sets HT_ERR_NONFINITE and leaves X_q unchanged.
-__global__ void __launch_bounds__(NT) cn_solve_kernel(CnArgs a, CnWs w, int q, int sweep, int* err,
-                                                      long long smem_doubles) {
+constexpr int NTS = 512;   // solve threads: 12 element warps hide the column loops' latency (1024: slower, measured)
+__global__ void __launch_bounds__(NTS) cn_solve_kernel(CnArgs a, CnWs w, int q, int sweep, int* err,
+                                                       long long smem_doubles) {
   const int n = a.n[q], r = a.r, N = n * r;
   const int tid = threadIdx.x, wid = tid >> 5;
+  constexpr int NT = NTS;
   constexpr int PIV = NT - 32;                     // lane 0 of the last warp (SM partition 3)
   constexpr int NE = (NT / 32) * 3 / 4 * 32;       // element threads: warps with wid % 4 != 3
   const int et = (wid % 4 != 3) ? (wid - wid / 4) * 32 + (tid & 31) : -1;
@@ -464,7 +466,7 @@ extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, do
       const int Nq = cn[q] * a.r;
       const int mblocks = (int)(((long long)Nq * Nq + NT - 1) / NT);
       CNL(KC_CPSMALL, (cn_assemble_kernel<<<mblocks + Nq, NT, 0, s>>>(a, w, mt, q, mblocks)));
-      CNL(KC_CPSOLVE, (cn_solve_kernel<<<1, NT, (size_t)solve_smem_doubles * sizeof(double), s>>>(
+      CNL(KC_CPSOLVE, (cn_solve_kernel<<<1, NTS, (size_t)solve_smem_doubles * sizeof(double), s>>>(
                           a, w, q, sw, htg_ctx_err(c), solve_smem_doubles)));
       CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1, 0)));
       CNL(KC_CPSMALL, (cn_gram_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1)));
