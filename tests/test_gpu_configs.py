@@ -223,3 +223,27 @@ def test_untruncated_graded_spectrum_reproduces_u(G):
     ctx.check()
     assert out.ranks() == rep.ranks
     assert rel_err(from_gpu(out, u.tree), u) < 1e-13
+
+
+def test_kinetic_config3_full_size_two_heun2_steps(G):
+    """The kinetic workload at full size: n = 64 per variable (64^6 grid points), HT r_max 64,
+    five operator terms (a 31 GB context), its seeded initial condition (rank 6), HEUN2 with
+    tol 1e-6: two steps against the oracle's HT-format steps (node ranks reach 42; the stage sums
+    put 3960 x 252 matrices through the QR and 252-column node factors through the SVD)."""
+    from oracle.problems import kinetic_terms
+    from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+    kc = kinetic_case(64)
+    w, F = kinetic_ic(kc)
+    u = OH.from_cp(w, F)
+    alphas, factors = kinetic_terms(kc)
+    kop = G.KineticOp(kc)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5)
+    g = to_gpu(G, u, 64)
+    for step in range(2):
+        u, reps = OH.step_heun2(u, alphas, factors, kc.dt, 1e-6, 64)
+        G.ht_step(ctx, g, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2)
+        sync()
+        ctx.check()
+        assert g.ranks() == reps[1].ranks, f"step {step}"
+        assert rel_err(from_gpu(g, u.tree), u) < TOL64, f"step {step}"
+    ctx.close()
