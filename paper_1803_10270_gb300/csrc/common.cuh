@@ -82,8 +82,24 @@ struct SvdDesc {
 // descs_dev + i * inst_stride bytes.
 cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr,
                             int count = 1, long long inst_stride = 0);
+// Workspace of the cooperative QR (matrices wider than 64 columns and above 2^17 entries, one
+// instance per launch): per descriptor d and CTA g of its group, partial dot products
+// part[(d G + g) kmax + c], totals tot[d kmax + c], the published row j in two buffers by step
+// parity rowj[(2 d + (j & 1)) kmax + c], the diagonal of R diag[d kmax + c], and barrier words
+// bar[d G + g] (zeroed by the launcher).
+struct QrCoopWs {
+  double* part;
+  double* tot;
+  double* rowj;
+  double* diag;
+  unsigned* bar;
+  int* err;
+  int kmax;     // largest k
+  int ndmax;    // largest descriptor count of one launch
+  int gmax;     // largest CTA group
+};
 cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops = nullptr, int count = 1,
-                          long long inst_stride = 0);
+                          long long inst_stride = 0, const QrCoopWs* coop = nullptr);
 cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
                            cudaStream_t s, double* flops = nullptr, int count = 1, long long inst_stride = 0);
 

@@ -51,6 +51,11 @@ void htg_build_tree(int d, int kind, TreeInfo* t) {
 namespace {
 
 constexpr int NN = HT_MAXNODES;
+// cooperative QR (k_qr.cu) for contexts whose truncation inputs reach this rank: descriptors
+// per launch (a level's complement QRs: 2 per interior node) and CTAs per matrix
+constexpr int QR_COOP_MIN_KC = 160;
+constexpr int QR_COOP_NDMAX = 2 * HT_MAXNODES;
+constexpr int QR_COOP_GMAX = 32;
 constexpr int MAXLEV = HT_MAXD;   // tree depth + 1 (the linear tree of d = 16 is 15 deep)
 
 // Device-side plan: dimensions derived from the device-resident ranks, plus every work
@@ -163,6 +168,8 @@ struct ht_ctx {
   int gemm_grid = 0;
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
+  QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
+  bool has_coop = false;
   void* cn_ws = nullptr;       // Crank-Nicolson ALS workspace (allocated by its first call)
   size_t cn_bytes = 0;
 };
@@ -845,6 +852,7 @@ static int trunc_input_cap(const ht_config* c) {
 
 struct WsLayout {
   size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
+  size_t off_coop[5];           // cooperative QR: part, tot, rowj, diag, bar (0 when not used)
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
   size_t total;
@@ -858,6 +866,16 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   W->off_plan = off; off = align_up(off + sizeof(Plan));
   W->off_err = off; off = align_up(off + 64);
   W->off_tick = off; off = align_up(off + 2 * NN * sizeof(unsigned));
+  for (int j = 0; j < 5; ++j) W->off_coop[j] = 0;
+  if ((size_t)Kc >= (size_t)QR_COOP_MIN_KC) {
+    const size_t nd = QR_COOP_NDMAX, gm = QR_COOP_GMAX;
+    const size_t sz[5] = {nd * gm * Kc * sizeof(double), nd * Kc * sizeof(double), 2 * nd * Kc * sizeof(double),
+                          nd * Kc * sizeof(double), nd * gm * sizeof(unsigned)};
+    for (int j = 0; j < 5; ++j) {
+      W->off_coop[j] = off;
+      off = align_up(off + sz[j]);
+    }
+  }
   W->off_app_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_stage_rank = off; off = align_up(off + NN * sizeof(int));
   W->off_wn = off; off = align_up(off + NN * sizeof(WsNode));
@@ -943,6 +961,18 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->stage[t] = (double*)(base + W.stage_off[t]);
   }
   c->wn_dev = (WsNode*)(base + W.off_wn);
+  if (W.off_coop[0]) {
+    c->has_coop = true;
+    c->qr_coop.part = (double*)(base + W.off_coop[0]);
+    c->qr_coop.tot = (double*)(base + W.off_coop[1]);
+    c->qr_coop.rowj = (double*)(base + W.off_coop[2]);
+    c->qr_coop.diag = (double*)(base + W.off_coop[3]);
+    c->qr_coop.bar = (unsigned*)(base + W.off_coop[4]);
+    c->qr_coop.err = c->err;
+    c->qr_coop.kmax = c->Kc;
+    c->qr_coop.ndmax = QR_COOP_NDMAX;
+    c->qr_coop.gmax = QR_COOP_GMAX;
+  }
   c->prof_flops = (double*)(base + W.off_prof);
   c->ptr_tbl = (const double**)(base + W.off_ptrs);
   {
@@ -1067,12 +1097,16 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   const int g = c->gemm_grid;
   const long long st = (long long)sizeof(Plan);
   HTG_LAUNCH(c, KC_PLAN, s, pre());
-  HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_leaf, L.n_leaf, s, htg_prof_flops(c, KC_QR), count, st));
+  const QrCoopWs* coop = (c->has_coop && count == 1) ? &c->qr_coop : nullptr;
+  const int coop_extra = coop ? 1 : 0;   // the cooperative QR launch beside each QR launch
+  HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_leaf, L.n_leaf, s, htg_prof_flops(c, KC_QR), count, st, coop));
+  c->launches += coop_extra;
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
     HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
     HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
-    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
+    c->launches += coop_extra;
   }
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   // top-down complement factors: E of a child needs only E, B and R of its parent, never the
@@ -1082,7 +1116,8 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
     HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
     HTG_LAUNCH(c, KC_GEMM, s,
                htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
-    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st));
+    HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
+    c->launches += coop_extra;
   }
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
   HTG_LAUNCH(c, KC_SVD, s,

@@ -233,8 +233,16 @@ __device__ inline int qr_splits(int m, int k, int gsplit, long long room) {
 // counter, no waiting) reduces the ns k x k stack, whose column c is zero below row
 // (c+1) ns - 1, with the banded sweep, and writes R.  Q = diag(Q_s) Q_stack, so R is the R
 // factor of op(A) up to an orthogonal factor on the left, which the truncation never sees.
+// Matrices the cooperative form takes (when the launch offers it): more than 2^16 entries and at
+// least twice as tall as wide.  One CTA sweeps such a matrix out of L2 for milliseconds to
+// seconds, and the two-stage form cannot hold its row blocks and stack on chip beyond about
+// 200 KB x 8 blocks; smaller matrices keep the one-CTA and two-stage forms.
+__device__ inline bool qr_coop_eligible(int m, int k) {
+  return (long long)m * k > (1LL << 16) && m >= 2 * k;
+}
+
 __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ descs, long long inst_stride,
-                                                 long long smem_doubles, int gsplit, double* flops) {
+                                                 long long smem_doubles, int gsplit, int coop, double* flops) {
   // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
   const QrDesc q = ((const QrDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x / gsplit];
   const int part = blockIdx.x % gsplit;
@@ -244,6 +252,7 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
     if (threadIdx.x == 0 && part == 0 && q.rows_out) *q.rows_out = 0;
     return;
   }
+  if (coop && qr_coop_eligible(m, k)) return;   // reduced by qr_coop_kernel
   const long long room = smem_doubles - kd;
   const int ns = q.ticket ? qr_splits(m, k, gsplit, room) : 1;
   if (part >= ns) return;
@@ -323,10 +332,150 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
   if (tid == 0 && flops) atomicAdd(flops, f + householder_flops(mw, k, band));
 }
 
+
+// ---------------------------------------------------------------- cooperative form ----
+// G CTAs per matrix, CTA g owning the rows [g mb, (g+1) mb) of the matrix in its scratch buffer.
+// Column j: (1) each CTA forms the partial dot products of column j with the columns c >= j
+// over its rows >= j (c = j gives the squared norm), and the owner of row j publishes that row;
+// (2) after a barrier of the matrix's CTAs, CTA g totals the columns c = j + g (mod G); (3)
+// after a second barrier every CTA forms the same reflector from the totals (alpha, and tau
+// split as (1 / |x|) (1 / (|x0| + |x|)) so that it does not overflow for tiny columns) and
+// updates its own rows: v.c = x.c - alpha c_j, c <- c - tau (v.c) v.  R is the rows j of the
+// updated matrix and the alphas.  Barriers are per matrix, by arrival words, each wait bounded
+// (HT_ERR_TIMEOUT, and the CTA returns).
+constexpr int QRC_NT = 256;
+constexpr long long QRC_TIMEOUT_CYCLES = 400000000LL;   // about 0.2 s
+
+__device__ bool coop_barrier(unsigned* flags, int G, int g, unsigned seq, int* err) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      *(volatile unsigned*)(flags + g) = seq;
+    }
+    __syncwarp();
+    int ok = 1;
+    const long long t0 = clock64();
+    for (int i = threadIdx.x; i < G && ok; i += 32) {
+      while (*(volatile unsigned*)(flags + i) < seq) {
+        if (clock64() - t0 > QRC_TIMEOUT_CYCLES) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && threadIdx.x == 0 && err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
+    __threadfence();
+    if (threadIdx.x == 0) ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+__global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int G, QrCoopWs w) {
+  const int d = blockIdx.x / G, g = blockIdx.x % G;
+  const QrDesc q = descs[d];
+  const int m = q.m, k = q.k;
+  if (m <= 0 || k <= 0 || !qr_coop_eligible(m, k)) return;   // uniform over the matrix's CTAs
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = QRC_NT / 32;
+  const int mb = (m + G - 1) / G, r0 = htg_min(m, g * mb), r1 = htg_min(m, r0 + mb);
+  double* S = q.scratch;                     // m x k, ld m
+  double* part = w.part + ((long long)d * G + g) * w.kmax;
+  double* part0 = w.part + (long long)d * G * w.kmax;
+  double* tot = w.tot + (long long)d * w.kmax;
+  // row j is published into one of two buffers by step parity: a CTA may publish row j+1 while
+  // a slower one still reads row j (no barrier between a step's update and the next step's
+  // dot products); two steps apart, the next step's first barrier separates them
+  double* rowj2 = w.rowj + (long long)d * 2 * w.kmax;
+  double* diag = w.diag + (long long)d * w.kmax;
+  unsigned* flags = w.bar + (long long)d * G;
+  __shared__ double wc[1024];                // (v.c) tau for the columns of one step
+  __shared__ double sh_v0, sh_alpha;
+  for (long long e = tid; e < (long long)(r1 - r0) * k; e += QRC_NT) {
+    const int i = r0 + (int)(e % (r1 - r0)), c = (int)(e / (r1 - r0));
+    S[i + (long long)m * c] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
+  }
+  unsigned seq = 0;
+  const int rmax = htg_min(m, k);
+  for (int j = 0; j < rmax; ++j) {
+    __syncthreads();
+    const int i0 = htg_max(j, r0);
+    const double* x = S + (long long)m * j;
+    for (int c = j + wid; c < k; c += nw) {
+      const double* cc = S + (long long)m * c;
+      double sdot = 0.0;
+      for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i], cc[i], sdot);
+      sdot = warp_sum(sdot);
+      if (lane == 0) part[c] = sdot;
+    }
+    double* rowj = rowj2 + (long long)(j & 1) * w.kmax;
+    if (j >= r0 && j < r1)
+      for (int c = j + tid; c < k; c += QRC_NT) rowj[c] = S[j + (long long)m * c];
+    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+    for (int c = j + g + G * wid; c < k; c += G * nw) {
+      double t = 0.0;
+      for (int h = lane; h < G; h += 32) t += __ldcg(part0 + (long long)h * w.kmax + c);
+      t = warp_sum(t);
+      if (lane == 0) tot[c] = t;
+    }
+    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+    // the reflector of column j (every CTA forms the same one)
+    const int nc = k - j - 1;
+    if (tid == 0) {
+      const double n2 = __ldcg(tot + j), x0 = __ldcg(rowj + j);
+      double alpha = 0.0, v0 = 0.0, ri = 0.0, rv = 0.0;
+      if (htg_dpos(n2)) {
+        const double nrm = sqrt(n2);
+        alpha = htg_dpos(x0) ? -nrm : nrm;
+        v0 = x0 - alpha;
+        ri = 1.0 / nrm;
+        rv = 1.0 / (fabs(x0) + nrm);      // tau = 2 / (v.v) = ri rv
+      }
+      sh_v0 = v0;
+      sh_alpha = alpha;
+      wc[0] = ri;
+      wc[1] = rv;
+      if (j >= r0 && j < r1) diag[j] = alpha;   // read back at the end by this CTA only
+    }
+    __syncthreads();
+    const double ri = wc[0], rv = wc[1], alpha = sh_alpha, v0 = sh_v0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nc; c0 += 1024) {
+      const int cn = htg_min(1024, nc - c0);
+      for (int t = tid; t < cn; t += QRC_NT) {
+        const int c = j + 1 + c0 + t;
+        const double vc = __ldcg(tot + c) - alpha * __ldcg(rowj + c);
+        wc[t] = (vc * ri) * rv;
+      }
+      __syncthreads();
+      for (long long e = tid; e < (long long)(r1 - i0) * cn; e += QRC_NT) {
+        const int i = i0 + (int)(e % (r1 - i0)), c = j + 1 + c0 + (int)(e / (r1 - i0));
+        const double vi = (i == j) ? v0 : x[i];
+        S[i + (long long)m * c] = fma(-wc[c - (j + 1 + c0)], vi, S[i + (long long)m * c]);
+      }
+      __syncthreads();
+    }
+  }
+  // R: rows r < rmax of this CTA (diag from the alphas, upper part from the updated rows)
+  __syncthreads();
+  for (long long e = tid; e < (long long)(r1 - r0) * k; e += QRC_NT) {
+    const int r = r0 + (int)(e % (r1 - r0)), c = (int)(e / (r1 - r0));
+    if (r >= rmax) continue;
+    double val = 0.0;
+    if (c == r) val = diag[r];
+    else if (c > r) val = S[r + (long long)m * c];
+    if (q.tR) q.R[c + (long long)q.ldr * r] = val;
+    else q.R[r + (long long)q.ldr * c] = val;
+  }
+  if (g == 0 && tid == 0 && q.rows_out) *q.rows_out = rmax;
+}
+
 }  // namespace
 
 cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops, int count,
-                          long long inst_stride) {
+                          long long inst_stride, const QrCoopWs* coop) {
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (count > 65535) return cudaErrorInvalidValue;
   static bool attr[64] = {false};
@@ -343,7 +492,24 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   const int nsm = (dev >= 0 && dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
   const int gsplit = ((long long)ndesc * count < nsm) ? QR_MAXSPLIT : 1;
   const int smem = gsplit > 1 ? QR_SMEM_WIDE : QR_SMEM_BYTES;
+  const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax;
   qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, smem, s>>>(
-      descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, flops);
-  return cudaGetLastError();
+      descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, use_coop ? 1 : 0, flops);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !use_coop) return e;
+  // the wide matrices: G CTAs each, all resident (cooperative launch)
+  const int G = htg_max(2, htg_min(coop->gmax, nsm / ndesc));
+  e = cudaMemsetAsync(coop->bar, 0, (size_t)ndesc * G * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ndesc * G);
+  cfg.blockDim = dim3(QRC_NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute lattr[1];
+  lattr[0].id = cudaLaunchAttributeCooperative;
+  lattr[0].val.cooperative = 1;
+  cfg.attrs = lattr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, G, *coop);
 }
