@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
-    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn"],
+    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn", "kinetic"],
                    help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
@@ -254,6 +254,8 @@ def run_gpu(args):
             res = run_tt(G, torch, flush, args.steps, warm)
         elif args.line == "cn":
             res = run_cn(G, torch, flush, args.steps, warm)
+        elif args.line == "kinetic":
+            res = run_kinetic(G, torch, flush, args.steps, warm)
         else:
             res = run_batched(G, torch, flush, args.batched, args.steps, warm)
         if rank == 0:
@@ -336,6 +338,9 @@ def run_gpu(args):
     # ---- the same HT workload in tensor-train form (linear dimension tree)
     tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
 
+    # ---- the full-size kinetic workload (cfg3), HEUN2, 5 steps after 3
+    kinetic = run_kinetic(G, torch, flush, 5, 3) if args.d12 else None
+
     # ---- implicit Crank-Nicolson step in CP format (ALS), kinetic operator
     cn = run_cn(G, torch, flush, 50, max(args.warmup, 3)) if args.d12 else None
 
@@ -369,6 +374,8 @@ def run_gpu(args):
             out["tt"] = tt
         if cn is not None:
             out["cn"] = cn
+        if kinetic is not None:
+            out["kinetic"] = kinetic
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -542,6 +549,50 @@ def run_cn(G, torch, flush, steps: int, warmup: int) -> dict:
     ctx.close()
     return {"workload": CN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
             "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "cp_rank": r, "sweeps": sweeps,
+            "cuda_graph": True}
+
+
+KIN_WORKLOAD = ("linearised 6-D kinetic equation (cfg3): n=64 per variable, x periodic [0,2pi)^3, v in [-6,6]^3, "
+                "nu=1, seeded initial condition M(v)(1 + 0.1 prod sin x_i) + rank-4 perturbation, 5-term operator, "
+                "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6, FP64; steps 4..3+K from t=0")
+
+
+def run_kinetic(G, torch, flush, steps: int, warmup: int) -> dict:
+    """HT HEUN2 steps/s of the full-size kinetic workload (node ranks grow to about 60 within ten
+    steps, so the step cost grows too: the line reports steps warmup+1 .. warmup+steps)."""
+    import numpy as np
+    from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+    kc = kinetic_case(64)
+    w0, F0 = kinetic_ic(kc)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5)
+    u = G.HTTensor(6, [64] * 6, 64)
+    u.upload(ic_nodes(u.tree, [F * (w0[None, :] if i == 0 else 1.0) for i, F in enumerate(F0)], np))
+    kop = G.KineticOp(kc)
+    for _ in range(warmup):
+        G.ht_step(ctx, u, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2)
+    torch.cuda.synchronize()
+    ctx.check()
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    l0 = ctx.launches()
+    with torch.cuda.graph(graph):
+        G.ht_step(ctx, u, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2, stream=torch.cuda.current_stream())
+    per_step = ctx.launches() - l0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        graph.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms_max, value = aggregate_replicas(ms, steps)
+    ranks = u.ranks()
+    del graph
+    ctx.close()
+    return {"workload": KIN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "ht_ranks_final": ranks,
             "cuda_graph": True}
 
 
