@@ -38,7 +38,6 @@ struct GemmDesc {
   int batch;
   int tA, tB;
   double alpha, beta;
-  double diag;              // added to the diagonal entries of C (C = alpha op(A) op(B) + beta C + diag I)
 };
 
 // Householder QR, R factor only.  Input op(A) is m x k (tA: A stored k x m, lda between

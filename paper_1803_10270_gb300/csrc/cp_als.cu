@@ -295,7 +295,6 @@ __global__ void cp_plan_kernel(CpArgs a, CpWs w) {
       g[q].batch = 1;
       g[q].alpha = 1.0;
       g[q].beta = 0.0;
-      g[q].diag = 0.0;
     }
     // RHS = Y_k (n x ry) * Hh (ry x r)
     g[0].A = a.Y[k]; g[0].lda = n; g[0].tA = 0;

@@ -73,7 +73,7 @@ struct Plan {
   GemmDesc g_T1[MAXLEV][NN];
   GemmDesc g_Epre[MAXLEV][2 * NN];
   GemmDesc g_XY[2 * NN];
-  GemmDesc g_bi[4][NN];     // two Newton steps restoring X_t Y_t = I (see rank_select_body)
+  GemmDesc g_bi[2][NN];     // operands of the X_t Y_t = I refinement (biorth_kernel)
   GemmDesc g_proj1[NN];
   GemmDesc g_proj2[NN];
   GemmDesc g_proj3[NN];
@@ -185,7 +185,7 @@ __device__ void fill_gemm(GemmDesc& g, const double* A, int lda, int tA, const d
   g.tA = tA; g.tB = tB;
   g.sA = g.sB = g.sC = 0;
   g.batch = 1;
-  g.alpha = 1.0; g.beta = 0.0; g.diag = 0.0;
+  g.alpha = 1.0; g.beta = 0.0;
 }
 
 // skip_tol: the relative tolerance that sets the SVD discard level (SvdDesc::skip2), 0 when every
@@ -371,17 +371,13 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
     // X_t Y_t = W_k^T W_k S_k Z_k^T Z_k S_k^-1 = I_k in exact arithmetic; rounding in the SVD
     // breaks it by about eps |u| / s_k (Y divides by the kept singular values), and the edge's
     // projector Y X then moves T(u) by that much.  Two Newton steps for the inverse of X_t on
-    // the range of Y_t, Y <- Y (2I - X Y), square that error twice (N in SW, Y2 in P: both free
-    // once the SVD has run); with every direction kept, Y X = I and T(u) = u to rounding.
+    // the range of Y_t, Y <- Y (2I - X Y) (biorth_kernel), square that error twice; with every
+    // direction kept, Y X = I and T(u) = u to rounding.  The descriptors carry the operands
+    // (X, Y: k x K and K x k) and the scratch used when they do not fit in shared memory
+    // (N = 2I - X Y in SW, Y2 in P: both free once the SVD has run).
     const int K = P->K[t];
-    GemmDesc& n1 = P->g_bi[0][t - 1];
-    fill_gemm(n1, wn[t].X, k, 0, wn[t].Y, K, 0, wn[t].SW, k, k, k, K);
-    n1.alpha = -1.0; n1.diag = 2.0;
+    fill_gemm(P->g_bi[0][t - 1], wn[t].X, k, 0, wn[t].Y, K, 0, wn[t].SW, k, k, k, K);
     fill_gemm(P->g_bi[1][t - 1], wn[t].Y, K, 0, wn[t].SW, k, 0, wn[t].P, K, K, k, k);
-    GemmDesc& n2 = P->g_bi[2][t - 1];
-    fill_gemm(n2, wn[t].X, k, 0, wn[t].P, K, 0, wn[t].SW, k, k, k, K);
-    n2.alpha = -1.0; n2.diag = 2.0;
-    fill_gemm(P->g_bi[3][t - 1], wn[t].P, K, 0, wn[t].SW, k, 0, wn[t].Y, K, K, k, k);
   }
   // projection
   for (int s = 0; s < L.n_proj1; ++s) {

@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     double* C = g.C + (long long)b * g.sC;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     const bool has_beta = htg_dnz(g.beta);   // bit test: an FP64 compare costs ~800 cycles here
-    const bool has_diag = htg_dnz(g.diag);
     for (int l0 = 0; l0 < g.k; l0 += BK) {
 #pragma unroll
       for (int p = 0; p < (BM * BK) / NT; ++p) {
@@ -106,7 +105,6 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
           if (g.colscale) v *= g.colscale[gj];
           double* cp = C + gi + (long long)g.ldc * gj;
           if (has_beta) v += g.beta * *cp;
-          if (has_diag && gi == gj) v += g.diag;
           *cp = v;
         }
       }
