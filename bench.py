@@ -221,6 +221,14 @@ class Workload:
         self.ev_join.record(self.side)
         main.wait_event(self.ev_join)
 
+    def step_route(self, route: str, stream=None):
+        """One route alone on the given stream ("ht" or "cp"), for the per-route timings."""
+        G = self.G
+        if route == "ht":
+            G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=stream)
+        else:
+            G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=stream)
+
     def first_step(self):
         """Step 1: the rank-2 state defines y; the iterate is that state padded to rank 24."""
         G = self.G
@@ -338,6 +346,27 @@ def run_gpu(args):
     e2e = run_e2e(W, G, torch, args.steps)
     ranks = W.u.ranks()
 
+    # ---- each route alone (same steps from t = 0, graph-captured, L2 flushed): the HT route's
+    #      steps/s is the metric's own reading; the combined step above runs both side by side
+    routes = {}
+    for route in ("ht", "cp"):
+        restart()
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1):
+            W.step_route(route, stream=torch.cuda.current_stream())
+        evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            evr[i][0].record(stream)
+            g1.replay()
+            evr[i][1].record(stream)
+        torch.cuda.synchronize()
+        W.ctx.check()
+        msr = sum(a.elapsed_time(b) for a, b in evr)
+        msr_max, vr = aggregate_replicas(msr, args.steps)
+        routes[route] = {"value": vr, "unit": "steps/s", "ms_per_step": msr_max / args.steps}
+        del g1
+
     # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
     ab2 = run_ab2(G, torch, flush, args.steps, args.warmup)
 
@@ -374,6 +403,7 @@ def run_gpu(args):
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_shares": shares,
         }
+        out["routes_alone"] = routes
         out["ab2"] = ab2
         if d12 is not None:
             out["d12"] = d12

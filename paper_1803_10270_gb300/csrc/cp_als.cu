@@ -1129,7 +1129,22 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   // stage Z_k in shared memory when it fits
   const size_t with_z = (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, true) * sizeof(double);
   const int zs_smem = (with_z <= 160 * 1024) ? 1 : 0;
-  const size_t smem = zs_smem ? with_z : (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, false) * sizeof(double);
+  size_t smem = zs_smem ? with_z : (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, false) * sizeof(double);
+  // Claim all of each SM's shared memory: the HT route's kernels, launched beside this one on
+  // another stream, then land on other SMs (an SM partition's FP64 pipe shared with their
+  // warps lengthens this kernel's latency-bound chains: measured 0.96 ms alone, 1.06 ms side by
+  // side before).  The launch has one CTA per factor column, far fewer than SMs.
+  {
+    int dev = 0, optin = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, cp_als_rk2_persistent) == cudaSuccess && nblk <= nsm && optin > 0) {
+      const size_t whole = (size_t)optin - fa.sharedSizeBytes;
+      if (whole > smem) smem = whole;
+    }
+  }
   if (smem > 48 * 1024) {
     if (cudaFuncSetAttribute(cp_als_rk2_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HT_ERR_CUDA;
