@@ -77,8 +77,13 @@ def mode_solve(X: list, xn: CP, eta, zeta, E, q: int) -> np.ndarray:
     return v.reshape(n, r, order="F")
 
 
-def cn_als_step(xn: CP, x0: CP, alphas: list, factors: list, dt: float, sweeps: int):
-    """x_{n+1} of rank x0.rank from the initial guess x0; returns (x, eps per sweep)."""
+def cn_als_step(xn: CP, x0: CP, alphas: list, factors: list, dt: float, sweeps: int, variant: str = "gs"):
+    """x_{n+1} of rank x0.rank from the initial guess x0; returns (x, eps per sweep).
+
+    variant "gs": Gauss-Seidel, each mode solved with the modes before it already updated.
+    variant "jacobi_damped": the parallel ALS of Appendix B (Algorithm 1): every mode solved from
+    the same iterate X^int, then X_q <- X_q^int + (V_q - X_q^int) / 4 for all q.  eps is the
+    largest |V_q - X_q^old|^2 of the sweep in both variants."""
     d = xn.d
     eta, zeta, E = cn_terms(alphas, factors, dt, d)
     X = [f.copy() for f in x0.factors]
@@ -86,10 +91,18 @@ def cn_als_step(xn: CP, x0: CP, alphas: list, factors: list, dt: float, sweeps: 
     eps = []
     for _ in range(sweeps):
         e_max = 0.0
-        for q in range(d):
-            V = mode_solve(X, xn, eta, zeta, E, q)
-            e_max = max(e_max, float(np.sum((V - X[q]) ** 2)))
-            X[q] = V
+        if variant == "gs":
+            for q in range(d):
+                V = mode_solve(X, xn, eta, zeta, E, q)
+                e_max = max(e_max, float(np.sum((V - X[q]) ** 2)))
+                X[q] = V
+        elif variant == "jacobi_damped":
+            Vs = [mode_solve(X, xn, eta, zeta, E, q) for q in range(d)]
+            for q in range(d):
+                e_max = max(e_max, float(np.sum((Vs[q] - X[q]) ** 2)))
+                X[q] = X[q] + 0.25 * (Vs[q] - X[q])
+        else:
+            raise ValueError(variant)
         eps.append(e_max)
     return CP(np.ones(x0.rank), X), eps
 

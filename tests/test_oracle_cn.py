@@ -87,3 +87,32 @@ def test_residual_never_increases():
             res = CN.cn_residual(CP(np.ones(2), X), xn, alphas, factors, kc.dt * 5)
             assert res <= prev * (1 + 1e-12) + 1e-15
             prev = res
+
+
+def test_damped_jacobi_reaches_the_relaxation_closed_form():
+    """The parallel variant (Appendix B, Algorithm 1: every mode from the same iterate, the
+    increment damped by 1/4) converges to the same step as Gauss-Seidel: for L = -nu I the
+    closed form (1 - nu dt/2)/(1 + nu dt/2) x_n; its increments shrink monotonically there."""
+    rng = np.random.default_rng(10)
+    d, n, nu, dt = 3, 5, 0.9, 0.3
+    xn = rand_cp(rng, d, n, 2)
+    x, eps = CN.cn_als_step(xn, xn, [-nu], [[None] * d], dt, 80, variant="jacobi_damped")
+    g = (1 - 0.5 * nu * dt) / (1 + 0.5 * nu * dt)
+    assert np.allclose(to_full(x), g * to_full(xn), rtol=0, atol=1e-10 * np.abs(to_full(xn)).max())
+    above = [e for e in eps[1:] if e > 1e-24 * eps[0]]      # above the rounding floor
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(above, above[1:]))
+    assert eps[-1] < 1e-24 * eps[0]
+
+
+def test_damped_jacobi_step_is_a_stationary_point():
+    """At convergence the parallel variant's iterate makes every mode's normal equations hold:
+    solving any mode again leaves it unchanged (kinetic operator, n = 4, rank 2)."""
+    kc = kinetic_case(4)
+    alphas, factors = kinetic_terms(kc)
+    rng = np.random.default_rng(11)
+    xn = CP(np.ones(2), [np.abs(rng.standard_normal((4, 2))) + 0.2 for _ in range(6)])
+    x, eps = CN.cn_als_step(xn, xn, alphas, factors, kc.dt, 400, variant="jacobi_damped")
+    eta, zeta, E = CN.cn_terms(alphas, factors, kc.dt, 6)
+    for q in range(6):
+        V = CN.mode_solve(x.factors, xn, eta, zeta, E, q)
+        assert np.allclose(V, x.factors[q], rtol=1e-10, atol=1e-12 * np.abs(V).max()), q
