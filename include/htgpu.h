@@ -318,7 +318,9 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
 /* One Crank-Nicolson step solved in CP format by alternating least squares (Section 3.3, eqs.
  * CNFDE, BLs, rRr1, ALS2, ML, MR): x minimises |A x - B x_n| with A = I - dt/2 L and
  * B = I + dt/2 L, over the factors of x at its current rank, Gauss-Seidel over the dimensions,
- * `sweeps` sweeps (1..64).  Mode q solves the (n_q r) x (n_q r) normal equations
+ * `sweeps` sweeps (1..64); variant CP_ALS_GS solves the dimensions in turn (Gauss-Seidel),
+ * CP_ALS_JACOBI_DAMPED solves all from the same iterate and moves each factor a quarter of the
+ * way (the parallel ALS of Appendix B, Algorithm 1).  Mode q solves the (n_q r) x (n_q r) normal equations
  * M vec(X_q) = vec(R) (eq. ALS2 on the grid basis; M = sum_{e,z} eta_e eta_z Gamma^{ez} kron
  * (E_q^e)^T E_q^z, eq. ML) by Cholesky.  x: the initial guess on entry (e.g. a copy of x_n),
  * the result on return; its weights are folded into its first factor, so they are 1 on
@@ -331,7 +333,7 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
  * definite sets HT_ERR_NONFINITE (ht_ctx_check) and leaves that factor unchanged.  Errors:
  * HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_NOMEM, HT_ERR_CUDA. */
 int cp_cn_als_step(ht_ctx* ctx, const cp_tensor* x_n, const ht_op* L, double dt, cp_tensor* x, int sweeps,
-                   double* eps_dev, void* stream);
+                   int variant, double* eps_dev, void* stream);
 
 int ht_selftest_grid_barrier(int nblocks, int absent, int device);
 

@@ -46,6 +46,7 @@ struct CnWs {
   double* M;     // (nmax R)^2          the system, column major, ld N
   double* Rh;    // nmax R              right-hand side, then the solution
   double* eps;   // 64                  increments per sweep
+  double* V;     // d x nmax x R         parallel variant: every mode's solution (ld n_k)
 };
 
 struct CnArgs {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(NT) cn_assemble_kernel(CnArgs a, CnWs w, CnDim
 // positive and finite sets HT_ERR_NONFINITE and leaves X_q unchanged.
 constexpr int NTS = 512;   // solve threads: 12 element warps hide the column loops' latency (1024: slower, measured)
 __global__ void __launch_bounds__(NTS) cn_solve_kernel(CnArgs a, CnWs w, int q, int sweep, int* err,
-                                                       long long smem_doubles) {
+                                                       long long smem_doubles, int to_v, long long vstride) {
   const int n = a.n[q], r = a.r, N = n * r;
   const int tid = threadIdx.x, wid = tid >> 5;
   constexpr int NT = NTS;
@@ -325,15 +326,29 @@ __global__ void __launch_bounds__(NTS) cn_solve_kernel(CnArgs a, CnWs w, int q, 
     __syncthreads();
   }
   double* Xq = a.X[q];
+  // Gauss-Seidel writes X_q; the parallel variant keeps V_q (offset q nmax R, ld n) for the
+  // damped update at the end of the sweep
+  double* dst = to_v ? w.V + (long long)q * vstride : Xq;
   double inc = 0.0;
   for (int e = tid; e < N; e += NT) {
     const double v = y[e];
     const double dlt = v - Xq[e];
     inc = fma(dlt, dlt, inc);
-    Xq[e] = v;
+    dst[e] = v;
   }
   const double tot = block_sum(inc, red);
   if (tid == 0 && htg_dgt_nn(tot, w.eps[sweep])) w.eps[sweep] = tot;
+}
+
+// parallel variant (Appendix B, Algorithm 1): X_q <- X_q + (V_q - X_q) / 4 for every q
+__global__ void cn_damp_kernel(CnArgs a, CnWs w, long long vstride) {
+  for (int k = 0; k < a.d; ++k) {
+    const int ne = a.n[k] * a.r;
+    const double* V = w.V + (long long)k * vstride;
+    double* X = a.X[k];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x)
+      X[e] = fma(0.25, V[e] - X[e], X[e]);
+  }
 }
 
 __global__ void cn_eps_out_kernel(CnWs w, int sweeps, double* out) {
@@ -356,8 +371,9 @@ bool factor_ok(const ht_factor& f) {
 }  // namespace
 
 extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, double dt, cp_tensor* x, int sweeps,
-                              double* eps_dev, void* stream) {
+                              int variant, double* eps_dev, void* stream) {
   if (!c || !xn || !L || !x || sweeps < 1 || sweeps > 64) return HT_ERR_ARG;
+  if (variant != CP_ALS_GS && variant != CP_ALS_JACOBI_DAMPED) return HT_ERR_ARG;
   const int d = htg_ctx_d(c);
   if (x->d != d || xn->d != d || L->d != d || !x->weight || !xn->weight) return HT_ERR_ARG;
   if (L->n_terms < 1 || L->n_terms > HT_MAXBLOCKTERMS) return HT_ERR_ARG;
@@ -379,8 +395,9 @@ extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, do
   // workspace for the context's capacities (allocated once; not while a graph is captured)
   const int Tm = htg_ctx_max_terms(c) + 1;
   const long long R = cap, nm = nmax, D = d, T2 = (long long)Tm * Tm;
-  const long long counts[11] = {Tm * D * nm * nm, T2 * D * nm * nm, Tm * D * nm * R, Tm * D * nm * R,
-                                D * T2 * R * R, D * T2 * R * R, T2 * R * R, T2 * R * R, (nm * R) * (nm * R), nm * R, 64};
+  const long long counts[12] = {Tm * D * nm * nm, T2 * D * nm * nm, Tm * D * nm * R, Tm * D * nm * R,
+                                D * T2 * R * R, D * T2 * R * R, T2 * R * R, T2 * R * R, (nm * R) * (nm * R), nm * R, 64,
+                                D * nm * R};
   size_t need = 0;
   for (long long v : counts) need += ((size_t)v * sizeof(double) + 255) & ~(size_t)255;
   size_t* have = nullptr;
@@ -405,8 +422,8 @@ extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, do
   CnWs w;
   {
     char* b = (char*)*slot;
-    double** ptrs[11] = {&w.Ed, &w.S, &w.Y, &w.Yn, &w.G, &w.Gn, &w.Gam, &w.Gamn, &w.M, &w.Rh, &w.eps};
-    for (int i = 0; i < 11; ++i) {
+    double** ptrs[12] = {&w.Ed, &w.S, &w.Y, &w.Yn, &w.G, &w.Gn, &w.Gam, &w.Gamn, &w.M, &w.Rh, &w.eps, &w.V};
+    for (int i = 0; i < 12; ++i) {
       *ptrs[i] = (double*)b;
       b += ((size_t)counts[i] * sizeof(double) + 255) & ~(size_t)255;
     }
@@ -460,6 +477,8 @@ extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, do
   CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, 0, d, 0)));
   CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, 0, d, 1)));
   CNL(KC_CPSMALL, (cn_gram_kernel<<<grid, NT, 0, s>>>(a, w, mt, 0, d)));
+  const bool gs = (variant == CP_ALS_GS);
+  const long long vstride = nm * R;
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int q = 0; q < d; ++q) {
       CNL(KC_CPSMALL, (cn_gamma_kernel<<<grid, NT, 0, s>>>(a, w, mt, q)));
@@ -467,9 +486,17 @@ extern "C" int cp_cn_als_step(ht_ctx* c, const cp_tensor* xn, const ht_op* L, do
       const int mblocks = (int)(((long long)Nq * Nq + NT - 1) / NT);
       CNL(KC_CPSMALL, (cn_assemble_kernel<<<mblocks + Nq, NT, 0, s>>>(a, w, mt, q, mblocks)));
       CNL(KC_CPSOLVE, (cn_solve_kernel<<<1, NTS, (size_t)solve_smem_doubles * sizeof(double), s>>>(
-                          a, w, q, sw, htg_ctx_err(c), solve_smem_doubles)));
-      CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1, 0)));
-      CNL(KC_CPSMALL, (cn_gram_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1)));
+                          a, w, q, sw, htg_ctx_err(c), solve_smem_doubles, gs ? 0 : 1, vstride)));
+      if (gs) {
+        CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1, 0)));
+        CNL(KC_CPSMALL, (cn_gram_kernel<<<grid, NT, 0, s>>>(a, w, mt, q, q + 1)));
+      }
+    }
+    if (!gs) {
+      // every mode was solved from the same iterate: damped update, then its applications and Grams
+      CNL(KC_CPSMALL, (cn_damp_kernel<<<grid, NT, 0, s>>>(a, w, vstride)));
+      CNL(KC_CPSMALL, (cn_apply_kernel<<<grid, NT, 0, s>>>(a, w, mt, 0, d, 0)));
+      CNL(KC_CPSMALL, (cn_gram_kernel<<<grid, NT, 0, s>>>(a, w, mt, 0, d)));
     }
   }
   if (eps_dev) CNL(KC_CPSMALL, (cn_eps_out_kernel<<<1, 64, 0, s>>>(w, sweeps, eps_dev)));

@@ -93,7 +93,7 @@ _EXPORTS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "cp_cn_als_step": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
-                                 C.POINTER(cp_tensor), C.c_int, C.c_void_p, C.c_void_p]),
+                                 C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -525,9 +525,9 @@ def cp_als_sweep_rk2(ctx: Context, x_old: CPTensor, op: ht_op, dt: float, x: CPT
                                    _stream_ptr(stream)), "cp_als_sweep_rk2")
 
 
-def cp_cn_als_step(ctx: Context, x_n: CPTensor, op: ht_op, dt: float, x: CPTensor, sweeps: int, eps=None,
-                   stream=None):
-    _check(load().cp_cn_als_step(ctx.ptr, C.byref(x_n.struct), C.byref(op), dt, C.byref(x.struct), sweeps,
+def cp_cn_als_step(ctx: Context, x_n: CPTensor, op: ht_op, dt: float, x: CPTensor, sweeps: int,
+                   variant: int = CP_ALS_GS, eps=None, stream=None):
+    _check(load().cp_cn_als_step(ctx.ptr, C.byref(x_n.struct), C.byref(op), dt, C.byref(x.struct), sweeps, variant,
                                  C.c_void_p(eps.data_ptr() if eps is not None else 0), _stream_ptr(stream)),
            "cp_cn_als_step")
 

@@ -25,7 +25,7 @@ def G():
     return htgpu
 
 
-def run_gpu(G, d, n, op, dt, xn: CP, x0: CP, sweeps, cap, max_terms):
+def run_gpu(G, d, n, op, dt, xn: CP, x0: CP, sweeps, cap, max_terms, variant=0):
     import torch
     ctx = G.Context(d, [n] * d, cap=cap, max_terms=max_terms)
     gn = G.CPTensor(d, [n] * d, cap)
@@ -33,7 +33,7 @@ def run_gpu(G, d, n, op, dt, xn: CP, x0: CP, sweeps, cap, max_terms):
     gx = G.CPTensor(d, [n] * d, cap)
     gx.upload(x0.weights, x0.factors)
     eps = torch.zeros(sweeps, dtype=torch.float64, device="cuda")
-    G.cp_cn_als_step(ctx, gn, op, dt, gx, sweeps, eps=eps)
+    G.cp_cn_als_step(ctx, gn, op, dt, gx, sweeps, variant=variant, eps=eps)
     torch.cuda.synchronize()
     ctx.check()
     w, f = gx.download()
@@ -109,3 +109,19 @@ def test_cn_large_system_in_global_memory(G):
     vop = G.VarCoefOp(case)
     got, _ = run_gpu(G, 3, 20, vop.op, dt, xn, xn, 2, cap=8, max_terms=9)
     assert rel(to_full(got), to_full(ref)) < 1e-10
+
+
+def test_cn_damped_jacobi_matches_oracle(G):
+    """The parallel variant (Appendix B, Algorithm 1): every mode from the same iterate, the
+    increment damped by 1/4; kinetic operator, n = 8, rank 3, 4 sweeps against the oracle."""
+    kc = kinetic_case(8)
+    alphas, factors = kinetic_terms(kc)
+    rng = np.random.default_rng(45)
+    xn = CP(np.array([1.0, 0.4, 0.2]), [np.abs(rng.standard_normal((8, 3))) + 0.1 for _ in range(6)])
+    x0 = CP(np.ones(3), [f * (1.0 + 0.05 * rng.standard_normal(f.shape)) for f in xn.factors])
+    dt = 5 * kc.dt
+    ref, eps_ref = CN.cn_als_step(xn, x0, alphas, factors, dt, 4, variant="jacobi_damped")
+    kop = G.KineticOp(kc)
+    got, eps = run_gpu(G, 6, 8, kop.op, dt, xn, x0, 4, cap=3, max_terms=5, variant=G.CP_ALS_JACOBI_DAMPED)
+    assert rel(to_full(got), to_full(ref)) < 1e-10
+    assert np.allclose(eps, eps_ref, rtol=1e-6, atol=1e-14 * max(eps_ref))
