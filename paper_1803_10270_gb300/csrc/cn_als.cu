@@ -246,12 +246,14 @@ __global__ void __launch_bounds__(NT) cn_assemble_kernel(CnArgs a, CnWs w, CnDim
 }
 
 // Cholesky M = L L^T (lower, in place) with y = L^-1 R fused in, then L^T v = y; X_q <- v.
-// Column j: (1) scale it by r_j = d_j^-1/2 (all threads) and y_j; (2) the trailing lower
-// triangle a_ic -= l_ij l_cj, i >= c > j (a warp per column on the element warps) with
-// y_i -= l_ij y_j; meanwhile one pivot thread, alone on its SM partition, forms
-// d_{j+1} = a_{j+1,j+1} - l_{j+1,j}^2 and r_{j+1} (look-ahead), so the pivot's serial FP64
-// chain overlaps the update.  Two barriers per column.  (Flattening the triangle over all
-// element threads packed the lanes better but its index arithmetic cost more: measured.)  Shared memory
+// Two columns per step: (1) columns j, j+1 below their 2 x 2 pivot block are scaled (r_j =
+// d_j^-1/2, and the second column corrected by l_{j+1,j} first), with y_j, y_{j+1}; (2) the
+// rank-2 update a_ic -= l_ij l_cj + l_{i,j+1} l_{c,j+1} of the trailing lower triangle (a warp
+// per column on the element warps) and of y; meanwhile one pivot thread, alone on its SM
+// partition, applies that update to the next pivot block itself and factors it (look-ahead),
+// so the pivots' serial FP64 chain overlaps the update.  Two barriers per two columns.
+// (Flattening the triangle over all element threads packed the lanes better but its index
+// arithmetic cost more; one column per step took twice the barriers: both measured.)  Shared memory
 // when M fits (odd leading dimension), else the global buffer in place.  A pivot that is not
 // positive and finite sets HT_ERR_NONFINITE and leaves X_q unchanged.
 constexpr int NTS = 512;   // solve threads: 12 element warps hide the column loops' latency (1024: slower, measured)
@@ -279,42 +281,90 @@ __global__ void __launch_bounds__(NTS) cn_solve_kernel(CnArgs a, CnWs w, int q, 
     for (int i = tid; i < N; i += NT) y[i] = w.Rh[i];
   }
   __syncthreads();
-  if (tid == 0) {
+  // two columns per step: the pivot pair (j, j+1) is factored ahead by the pivot thread
+  __shared__ double sh_l10;                        // l_{j+1,j} of the current pair
+  if (tid == PIV) {
     const double d0 = A[0];
-    const bool ok = htg_dpos_finite(d0);
-    const double r0 = ok ? htg_rsqrt_fast(d0) : 0.0;
+    const double r0 = htg_dpos_finite(d0) ? htg_rsqrt_fast(d0) : 0.0;
     rinv[0] = r0;
     A[0] = d0 * r0;
+    if (N > 1) {
+      const double l10 = A[1] * r0;
+      const double d1 = fma(-l10, l10, A[1 + ld]);
+      const double r1 = htg_dpos_finite(d1) ? htg_rsqrt_fast(d1) : 0.0;
+      rinv[1] = r1;
+      A[1 + ld] = d1 * r1;
+      sh_l10 = l10;
+    }
   }
   __syncthreads();
-  for (int j = 0; j < N; ++j) {
-    const double rj = rinv[j];
-    if (!htg_dnz(rj)) {                            // uniform: written before the last barrier
+  for (int j = 0; j < N; j += 2) {
+    const bool two = j + 1 < N;
+    const double r0 = rinv[j], r1 = two ? rinv[j + 1] : 1.0;
+    if (!htg_dnz(r0) || !htg_dnz(r1)) {            // uniform: written before the last barrier
       if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
       return;
     }
-    for (int i = j + 1 + tid; i < N; i += NT) A[i + ld * j] *= rj;
-    if (tid == 0) y[j] *= rj;
-    __syncthreads();
-    const int m = N - 1 - j;
-    if (et >= 0) {
-      // a warp per column c > j, its lanes down the rows i >= c ((j+1, j+1) is the pivot
-      // thread's); then y_i -= l_ij y_j
-      const int ew = et >> 5, lane = et & 31;
-      for (int c = j + 1 + ew; c < N; c += NE / 32) {
-        const double lc = A[c + ld * j];
-        for (int i = c + (c == j + 1 ? 1 : 0) + lane; i < N; i += 32)
-          A[i + ld * c] = fma(-A[i + ld * j], lc, A[i + ld * c]);
+    const double l10 = two ? sh_l10 : 0.0;
+    // (1) columns j, j+1 below the pair: l_ij = a_ij r_j, l_{i,j+1} = (a_{i,j+1} - l_ij l10) r_{j+1}
+    for (int i = j + 2 + tid; i < N; i += NT) {
+      const double lij = A[i + ld * j] * r0;
+      A[i + ld * j] = lij;
+      if (two) A[i + ld * (j + 1)] = fma(-lij, l10, A[i + ld * (j + 1)]) * r1;
+    }
+    if (tid == 0) {
+      const double y0 = y[j] * r0;
+      y[j] = y0;
+      if (two) {
+        A[(j + 1) + ld * j] = l10;
+        y[j + 1] = fma(-l10, y0, y[j + 1]) * r1;
       }
-      const double yj = y[j];
-      for (int i = j + 1 + et; i < N; i += NE) y[i] = fma(-A[i + ld * j], yj, y[i]);
-    } else if (tid == PIV && m > 0) {
-      const double l = A[(j + 1) + ld * j];
-      const double dn = fma(-l, l, A[(j + 1) + ld * (j + 1)]);
-      const bool ok = htg_dpos_finite(dn);
-      const double rn = ok ? htg_rsqrt_fast(dn) : 0.0;
-      rinv[j + 1] = rn;
-      A[(j + 1) + ld * (j + 1)] = dn * rn;
+    }
+    __syncthreads();
+    // (2) rank-2 update of the trailing lower triangle (a warp per column) and of y; the pivot
+    // thread updates the next pair's 2 x 2 block itself and factors it (look-ahead)
+    const int s0 = two ? j + 2 : j + 1;
+    if (et >= 0) {
+      const int ew = et >> 5, lane = et & 31;
+      for (int c = s0 + ew; c < N; c += NE / 32) {
+        const double lc0 = A[c + ld * j];
+        const double lc1 = two ? A[c + ld * (j + 1)] : 0.0;
+        const int i0 = (c <= s0 + 1) ? s0 + 2 : c;   // the pivot block (rows s0, s0+1) is the pivot thread's
+        for (int i = i0 + lane; i < N; i += 32) {
+          double v = fma(-A[i + ld * j], lc0, A[i + ld * c]);
+          if (two) v = fma(-A[i + ld * (j + 1)], lc1, v);
+          A[i + ld * c] = v;
+        }
+      }
+      const double y0 = y[j], y1 = two ? y[j + 1] : 0.0;
+      for (int i = s0 + et; i < N; i += NE) {
+        double v = fma(-A[i + ld * j], y0, y[i]);
+        if (two) v = fma(-A[i + ld * (j + 1)], y1, v);
+        y[i] = v;
+      }
+    } else if (tid == PIV && s0 < N) {
+      const int u = s0, w1 = s0 + 1;
+      const double luj = A[u + ld * j], luj1 = two ? A[u + ld * (j + 1)] : 0.0;
+      double duu = fma(-luj, luj, A[u + ld * u]);
+      if (two) duu = fma(-luj1, luj1, duu);
+      const double ru = htg_dpos_finite(duu) ? htg_rsqrt_fast(duu) : 0.0;
+      rinv[u] = ru;
+      A[u + ld * u] = duu * ru;
+      if (w1 < N) {
+        const double lwj = A[w1 + ld * j], lwj1 = two ? A[w1 + ld * (j + 1)] : 0.0;
+        double awu = fma(-lwj, luj, A[w1 + ld * u]);
+        double aww = fma(-lwj, lwj, A[w1 + ld * w1]);
+        if (two) {
+          awu = fma(-lwj1, luj1, awu);
+          aww = fma(-lwj1, lwj1, aww);
+        }
+        const double lwu = awu * ru;
+        const double dww = fma(-lwu, lwu, aww);
+        const double rw = htg_dpos_finite(dww) ? htg_rsqrt_fast(dww) : 0.0;
+        rinv[w1] = rw;
+        A[w1 + ld * w1] = dww * rw;
+        sh_l10 = lwu;
+      }
     }
     __syncthreads();
   }
