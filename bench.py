@@ -1,6 +1,6 @@
 """Benchmark: explicit time steps of 6-D advection held in HT and CP format on GB300.
 
-Workload (BASELINE config 2): u_t + c.grad u = 0 on [0,2pi)^6, n = 64 points per
+Workload: u_t + c.grad u = 0 on [0,2pi)^6, n = 64 points per
 dimension, central differences, RK2 with dt = 0.2 h, initial condition
 sum_{m=1,2} prod_i exp(sin(x_i + phi_{m,i})) (c, phi seeded).  One step runs the whole hot
 path once:
@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "HT steps/s (apply+truncate) vs FP64 plain form at rel err ≤1e-6; % roofline"
-WORKLOAD = ("6-D advection n=64 (cfg2): HT r_max=32 tol=1e-8 + CP rank<=24 with 5 ALS sweeps, "
+WORKLOAD = ("6-D advection n=64: HT r_max=32 tol=1e-8 + CP rank<=24 with 5 ALS sweeps, "
             "RK2 dt=0.2h; one step = HT apply+HSVD truncate and CP apply+ALS")
 D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
 # FP64 peak of GB300 derived from the nominal 1.25 TFLOP/s: 152 SMs x 2070 MHz x 4 FP64
@@ -74,7 +74,7 @@ def oracle_sample(seconds: float) -> dict:
     from oracle.problems import advection_A
     from paper_1803_10270_gb300.inputs import advection_case, cp_padding
 
-    case = advection_case(D, N, cfg_index=1)
+    case = advection_case(D, N, seed_offset=1)
     A = advection_A(case)
     u = OH.from_cp(np.ones(2), case.ic_factors())
     x = OC.CP(np.ones(2), case.ic_factors())
@@ -162,7 +162,7 @@ class Workload:
         from paper_1803_10270_gb300.inputs import advection_case, cp_padding
 
         self.G = G
-        self.case = advection_case(D, N, cfg_index=1)
+        self.case = advection_case(D, N, seed_offset=1)
         # Kronecker-sum RK2 steps raise ranks by 3: max_terms=1 sizes the workspace for that
         self.ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=1, precision=precision, device=device)
         self.op = G.advection_op(self.case.c, self.case.h)
@@ -376,7 +376,7 @@ def run_gpu(args):
     # ---- the same HT workload in tensor-train form (linear dimension tree)
     tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
 
-    # ---- the full-size kinetic workload (cfg3), HEUN2, 5 steps after 3
+    # ---- the full-size kinetic workload, HEUN2, 5 steps after 3
     kinetic = run_kinetic(G, torch, flush, 5, 3) if args.d12 else None
 
     # ---- implicit Crank-Nicolson step in CP format (ALS), kinetic operator
@@ -394,7 +394,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
-            "data": "synthetic (seeded advection, BASELINE config 2)",
+            "data": "synthetic (seeded 6-D advection, n=64)",
             "config": {"workload": WORKLOAD, "precision": args.precision, "ht_ranks_final": ranks,
                        "streams": "HT route and CP route on two streams (independent data)",
                        "cp_rank": CP_R, "l2": "flushed between timed steps (256 MB write)",
@@ -424,7 +424,7 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-BATCH_WORKLOAD = ("ragged batch (cfg4): independent 6-D advection instances, n in {32,48,64,96,128}, "
+BATCH_WORKLOAD = ("ragged batch: independent 6-D advection instances, n in {32,48,64,96,128}, "
                   "HT r_max in 8..48, seeded velocities, RK2 dt=0.2h, tol 1e-8, FP64; "
                   "one step = every instance's HT apply+HSVD truncate, each launch covering all instances")
 
@@ -451,7 +451,7 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
     RK2 start step, then AB2 steps, the timed ones graph-captured with L2 flushed between them."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
-    case = advection_case(D, N, cfg_index=1)
+    case = advection_case(D, N, seed_offset=1)
     ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=2)
     u = G.HTTensor(D, [N] * D, RMAX)
     up = G.HTTensor(D, [N] * D, RMAX)
@@ -480,27 +480,27 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
     ranks = u.ranks()
     del graph
     ctx.close()
-    return {"workload": "6-D advection n=64 (cfg2) HT route, AB2 (eq. AB2_) after one RK2 start step, "
+    return {"workload": "6-D advection n=64 HT route, AB2 (eq. AB2_) after one RK2 start step, "
                         "r_max 32, tol 1e-8", "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
             "steps": steps, "ht_ranks_final": ranks, "cuda_graph": True}
 
 
-D12_WORKLOAD = ("12-D advection n=128 (cfg5): depth-4 tree, seeded separable rank-3 initial condition, "
+D12_WORKLOAD = ("12-D advection n=128: depth-4 tree, seeded separable rank-3 initial condition, "
                 "HT r_max 64, tol 1e-8, RK2 dt=0.2h, FP64 throughout")
 
 
-TT_WORKLOAD = ("6-D advection n=64 (cfg2) HT route in tensor-train form (the linear dimension tree, "
+TT_WORKLOAD = ("6-D advection n=64 HT route in tensor-train form (the linear dimension tree, "
                "Section 2.2), r_max 32, tol 1e-8, RK2 dt=0.2h, FP64")
 
 
 def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128, cap: int = 64,
-            n_terms: int = 3, cfg_index: int = 4, tree: int = 0, workload: str = None) -> dict:
+            n_terms: int = 3, seed_offset: int = 4, tree: int = 0, workload: str = None) -> dict:
     """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
     64), or another advection workload and tree: the timed steps graph-captured, L2 flushed
     between them."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
-    case = advection_case(d, n, n_terms=n_terms, cfg_index=cfg_index)
+    case = advection_case(d, n, n_terms=n_terms, seed_offset=seed_offset)
     ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree)
     u = G.HTTensor(d, [n] * d, cap, tree=tree)
     u.upload(ic_nodes(u.tree, case.ic_factors(), np))
@@ -538,7 +538,7 @@ VC_WORKLOAD = ("variable-coefficient advection f_t + (C z).grad f = 0 (eq. PDE-a
                "stage), HT r_max 12, tol 1e-8, dt = 0.2 h / max speed, FP64")
 
 
-CN_WORKLOAD = ("linearised 6-D kinetic equation (cfg3 operator, 5 separable terms), n=16 per variable, "
+CN_WORKLOAD = ("linearised 6-D kinetic equation (its 5 separable terms), n=16 per variable, "
                "Crank-Nicolson step solved in CP format by ALS (eqs. CNFDE, ALS2, ML, MR): CP rank 6 "
                "(seeded kinetic initial condition), 5 Gauss-Seidel sweeps per step, dt = 5x the explicit "
                "step, FP64")
@@ -591,7 +591,7 @@ def run_cn(G, torch, flush, steps: int, warmup: int) -> dict:
             "cuda_graph": True}
 
 
-KIN_WORKLOAD = ("linearised 6-D kinetic equation (cfg3): n=64 per variable, x periodic [0,2pi)^3, v in [-6,6]^3, "
+KIN_WORKLOAD = ("linearised 6-D kinetic equation: n=64 per variable, x periodic [0,2pi)^3, v in [-6,6]^3, "
                 "nu=1, seeded initial condition M(v)(1 + 0.1 prod sin x_i) + rank-4 perturbation, 5-term operator, "
                 "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6, FP64; steps 4..3+K from t=0")
 
@@ -637,7 +637,7 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int) -> dict:
 
 def run_tt(G, torch, flush, steps: int, warmup: int) -> dict:
     """The configuration-2 HT route on the linear (tensor-train) tree."""
-    return run_d12(G, torch, flush, steps, warmup, d=D, n=N, cap=RMAX, n_terms=2, cfg_index=1, tree=1,
+    return run_d12(G, torch, flush, steps, warmup, d=D, n=N, cap=RMAX, n_terms=2, seed_offset=1, tree=1,
                    workload=TT_WORKLOAD)
 
 
@@ -762,8 +762,8 @@ def aggregate_replicas(ms_local: float, steps: int):
 
 def load_traffic() -> dict:
     """DRAM bytes per launch per kernel from the committed ncu summary
-    (profiles/traffic_cfg2_fp64.md, a `| kernel | bytes |` table)."""
-    p = os.path.join(ROOT, "profiles", "traffic_cfg2_fp64.md")
+    (profiles/traffic_adv6d_n64_fp64.md, a `| kernel | bytes |` table)."""
+    p = os.path.join(ROOT, "profiles", "traffic_adv6d_n64_fp64.md")
     out = {}
     try:
         with open(p) as f:
@@ -863,7 +863,7 @@ def run_reference(args):
     v = total_steps / total_s
     out = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": 0, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded advection, BASELINE config 2)",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 6-D advection, n=64)",
            "impl": "reference",
            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)"},
            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",

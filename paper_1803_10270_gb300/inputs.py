@@ -90,9 +90,9 @@ class AdvectionCase:
                 for i in range(self.d)]
 
 
-def advection_case(d: int, n: int, n_terms: int = 2, seed: int | None = None, cfg_index: int = 0) -> AdvectionCase:
+def advection_case(d: int, n: int, n_terms: int = 2, seed: int | None = None, seed_offset: int = 0) -> AdvectionCase:
     if seed is None:
-        seed = SEED_BASE + cfg_index
+        seed = SEED_BASE + seed_offset
     g = SplitMix64(seed)
     c = np.array([g.uniform_range(-1.0, 1.0) for _ in range(d)])
     phi = np.array([[g.uniform_range(0.0, 2.0 * math.pi) for _ in range(d)] for _ in range(n_terms)])
@@ -102,12 +102,12 @@ def advection_case(d: int, n: int, n_terms: int = 2, seed: int | None = None, cf
 BATCH_GRIDS = (32, 48, 64, 96, 128)
 
 
-def batched_advection_cases(count: int, d: int = 6, cfg_index: int = 3):
+def batched_advection_cases(count: int, d: int = 6, seed_offset: int = 3):
     """A ragged batch of independent advection problems: per instance (n, r_max, case) with n
-    drawn from BATCH_GRIDS and r_max from 8..48 (one splitmix64 stream, seed 0x5EED + cfg_index,
+    drawn from BATCH_GRIDS and r_max from 8..48 (one splitmix64 stream, seed 0x5EED + seed_offset,
     two draws per instance), and the velocity and phases of instance i from its own seed
     0x5EED + 1000 + i."""
-    g = SplitMix64(SEED_BASE + cfg_index)
+    g = SplitMix64(SEED_BASE + seed_offset)
     out = []
     for i in range(count):
         n = BATCH_GRIDS[int(g.uniform_range(0.0, float(len(BATCH_GRIDS)))) % len(BATCH_GRIDS)]
@@ -210,9 +210,9 @@ def kinetic_ic(kc: "KineticCase", seed: int | None = None, n_pert: int = 4, amp:
     return np.array(weights), F
 
 
-def kinetic_case(n: int, nu: float = 1.0, seed: int | None = None, cfg_index: int = 2) -> KineticCase:
+def kinetic_case(n: int, nu: float = 1.0, seed: int | None = None, seed_offset: int = 2) -> KineticCase:
     if seed is None:
-        seed = SEED_BASE + cfg_index
+        seed = SEED_BASE + seed_offset
     return KineticCase(n=n, nu=nu, seed=seed)
 
 
@@ -262,9 +262,9 @@ class VarCoefCase:
 
 
 def varcoef_case(N: int, n: int, zmax: float = 60.0, cfl: float = 0.2, seed: int | None = None,
-                 cfg_index: int = 5) -> VarCoefCase:
+                 seed_offset: int = 5) -> VarCoefCase:
     if seed is None:
-        seed = SEED_BASE + cfg_index
+        seed = SEED_BASE + seed_offset
     g = SplitMix64(seed)
     s = [g.uniform_range(0.5, 1.0) for _ in range(N)]
     a = np.array([[g.uniform_range(-1.0, 1.0) for _ in range(N)] for _ in range(N)])

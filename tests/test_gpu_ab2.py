@@ -38,7 +38,7 @@ def upload(G, u: OH.HT, cap):
 
 def test_ab2_steps_match_oracle(G):
     """6-D advection, n=16, r_max 8, tol 1e-8: RK2 start step, then 6 AB2 steps vs the oracle."""
-    case = advection_case(6, 16, cfg_index=0)
+    case = advection_case(6, 16, seed_offset=0)
     A = advection_A(case)
     u0 = OH.from_cp(np.ones(2), case.ic_factors())
     u1, _ = OH.step_rk2_poly(u0, A, 1e-8, 8)

@@ -32,9 +32,9 @@ def sync():
     torch.cuda.synchronize()
 
 
-def test_ab2_config2(G):
+def test_ab2_adv6d_n64(G):
     """AB2 on the 6-D n = 64 advection workload (r_max 32, tol 1e-8): RK2 start, 3 AB2 steps."""
-    case = advection_case(6, 64, cfg_index=1)
+    case = advection_case(6, 64, seed_offset=1)
     A = advection_A(case)
     u0 = OH.from_cp(np.ones(2), case.ic_factors())
     u1, _ = OH.step_rk2_poly(u0, A, 1e-8, 32)
@@ -55,9 +55,9 @@ def test_ab2_config2(G):
         assert rel_err(OH.HT(ref.tree, list(ref.n), gu.download()), ref) < TOL64, f"step {step}"
 
 
-def test_tensor_train_config2(G):
+def test_tensor_train_adv6d_n64(G):
     """The same workload on the linear (tensor-train) tree, 3 RK2 steps."""
-    case = advection_case(6, 64, cfg_index=1)
+    case = advection_case(6, 64, seed_offset=1)
     A = advection_A(case)
     u = OH.from_cp(np.ones(2), case.ic_factors(), tree=build_tree(6, "linear"))
     ctx = G.Context(6, [64] * 6, cap=32, max_terms=1, tree=1)

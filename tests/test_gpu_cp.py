@@ -74,10 +74,10 @@ def test_als_sweeps_match_oracle(G, variant):
     np.testing.assert_allclose(e.cpu().numpy(), eps, rtol=1e-6, atol=1e-14)
 
 
-def test_cp_step_config2_shape(G):
+def test_cp_step_adv6d_n64_shape(G):
     """n=64, d=6: y = p(dt L) x (rank 2*28), ALS to rank 24 from the padded iterate, 5 sweeps."""
     d, n = 6, 64
-    case = advection_case(d, n, cfg_index=1)
+    case = advection_case(d, n, seed_offset=1)
     A = advection_A(case)
     x = OC.CP(np.ones(2), case.ic_factors())
     pad = cp_padding([n] * d, 22, seed=0x5EED + 1, scale=1e-3)

@@ -131,9 +131,9 @@ def test_truncate_in_place_and_rank1(G):
     assert rel_err(from_gpu(g, pad.tree), u) < TOL64
 
 
-def test_step_rk2poly_config1_ten_steps(G):
+def test_step_rk2poly_adv6d_n16_ten_steps(G):
     """6-D advection, n=16, HT r_max=8, tol 1e-8, RK2, dt=0.2h, 10 steps, FP64."""
-    case = advection_case(6, 16, cfg_index=0)
+    case = advection_case(6, 16, seed_offset=0)
     A = advection_A(case)
     u = OH.from_cp(np.ones(2), case.ic_factors())
     ctx = G.Context(6, [16] * 6, cap=8, max_terms=6)
@@ -149,9 +149,9 @@ def test_step_rk2poly_config1_ten_steps(G):
         assert e < TOL64, f"step {step}: {e:.3e}"
 
 
-def test_step_rk2poly_config2_shape_three_steps(G):
+def test_step_rk2poly_adv6d_n64_shape_three_steps(G):
     """6-D advection at n=64, r_max=32 (the ranks settle near 6), 3 steps vs oracle."""
-    case = advection_case(6, 64, cfg_index=1)
+    case = advection_case(6, 64, seed_offset=1)
     A = advection_A(case)
     u = OH.from_cp(np.ones(2), case.ic_factors())
     ctx = G.Context(6, [64] * 6, cap=32, max_terms=6)

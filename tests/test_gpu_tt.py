@@ -66,7 +66,7 @@ def test_tt_truncate(G, rel_tol, rmax):
 
 def test_tt_rk2_advection_steps(G):
     d, n, cap = 6, 16, 8
-    case = advection_case(d, n, cfg_index=0)
+    case = advection_case(d, n, seed_offset=0)
     A = advection_A(case)
     u = OH.from_cp(np.ones(2), case.ic_factors(), tree=build_tree(d, "linear"))
     ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=LINEAR)
@@ -102,7 +102,7 @@ def test_tt_kinetic_heun2_steps(G):
 def test_tt_twelve_dim_deep_tree(G):
     """d = 12 on the linear tree: eleven levels of bottom-up QRs and top-down complements."""
     d, n, cap = 12, 6, 6
-    case = advection_case(d, n, n_terms=3, cfg_index=4)
+    case = advection_case(d, n, n_terms=3, seed_offset=4)
     A = advection_A(case)
     tree = build_tree(d, "linear")
     assert max(tree.depth) == 11

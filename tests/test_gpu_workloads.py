@@ -45,7 +45,7 @@ def test_twelve_dim_depth4_tree_steps(G):
     """12-D advection (the shape of the 12-D configuration: depth-4 tree, separable rank-3
     initial condition), n = 6, r_max 6, 3 RK2 steps against the oracle."""
     d, n = 12, 6
-    case = advection_case(d, n, n_terms=3, cfg_index=4)
+    case = advection_case(d, n, n_terms=3, seed_offset=4)
     A = advection_A(case)
     tree = build_tree(d)
     assert max(tree.depth) == 4
@@ -105,11 +105,11 @@ def test_zero_tensor_and_zero_tolerance(G):
     assert rel_err(ref, u) < 1e-12        # nothing was cut
 
 
-def test_config2_full_size_mass_bound(G):
+def test_adv6d_n64_full_size_mass_bound(G):
     """n=64, d=6 (64^6 grid points): the apply conserves the discrete mass exactly, the HSVD
     changes it by at most sqrt(N) |v - T(v)| <= sqrt(N) tol |v|; checked over 5 steps."""
     import torch
-    case = advection_case(6, 64, cfg_index=1)
+    case = advection_case(6, 64, seed_offset=1)
     u = OH.from_cp(np.ones(2), case.ic_factors())
     ctx = G.Context(6, [64] * 6, cap=32, max_terms=1)
     g = to_gpu(G, u, 32)
@@ -129,7 +129,7 @@ def test_config2_full_size_mass_bound(G):
         m0 = m1
 
 
-def test_kinetic_config3_shape_heun2(G):
+def test_kinetic6d_shape_heun2(G):
     """Linearised 6-D kinetic equation (x periodic, v in [-6, 6]) with its initial condition
     M(v)(1 + 0.1 prod sin x_i) plus a seeded rank-4 perturbation, n = 12, HEUN2 with a
     truncation after each stage, r_max 12, tol 1e-6: three steps against the oracle."""
@@ -158,7 +158,7 @@ def test_twelve_dim_full_size_steps(G):
     moves by at most sqrt(N) tol |v| per step."""
     import torch
     d, n, cap = 12, 128, 64
-    case = advection_case(d, n, n_terms=3, cfg_index=4)
+    case = advection_case(d, n, n_terms=3, seed_offset=4)
     A = advection_A(case)
     u = OH.from_cp(np.ones(3), case.ic_factors())
     ctx = G.Context(d, [n] * d, cap=cap, max_terms=1)
@@ -225,7 +225,7 @@ def test_untruncated_graded_spectrum_reproduces_u(G):
     assert rel_err(from_gpu(out, u.tree), u) < 1e-13
 
 
-def test_kinetic_config3_full_size_two_heun2_steps(G):
+def test_kinetic6d_n64_full_size_two_heun2_steps(G):
     """The kinetic workload at full size: n = 64 per variable (64^6 grid points), HT r_max 64,
     five operator terms (a 31 GB context), its seeded initial condition (rank 6), HEUN2 with
     tol 1e-6: two steps against the oracle's HT-format steps (node ranks reach 42; the stage sums
