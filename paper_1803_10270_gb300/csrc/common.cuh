@@ -99,8 +99,21 @@ struct QrCoopWs {
 };
 cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, double* flops = nullptr, int count = 1,
                           long long inst_stride = 0, const QrCoopWs* coop = nullptr);
+// Cluster form of the node SVD (wide node factors, one instance per launch): cl CTAs of one
+// thread-block cluster share a factor's columns in distributed shared memory.  cl = 0: not
+// available (no cluster of 8 or 16 CTAs with the shared memory it needs fits this device).
+struct SvdClusterCfg {
+  int cl = 0;
+  long long cap_doubles = 0;   // shared memory of one CTA of the cluster form, in doubles
+};
+SvdClusterCfg htg_svd_cluster_setup(int device);
+// whether htg_launch_svd adds the cluster launch (for the launch count)
+bool htg_svd_cluster_used(const SvdClusterCfg* clu, int count, int pmax);
+// With clu (count = 1 only), node factors the cluster form takes (p >= 128 and fitting its shared
+// memory) run in a second launch, one cluster each; the one-CTA kernel skips them.
 cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
-                           cudaStream_t s, double* flops = nullptr, int count = 1, long long inst_stride = 0);
+                           cudaStream_t s, double* flops = nullptr, int count = 1, long long inst_stride = 0,
+                           const SvdClusterCfg* clu = nullptr);
 
 // ------------------------------------------------------------ helpers -------
 __host__ __device__ inline int htg_min(int a, int b) { return a < b ? a : b; }

@@ -170,6 +170,7 @@ struct ht_ctx {
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
   QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
   bool has_coop = false;
+  SvdClusterCfg svd_clu;       // cluster form of the node SVD (contexts with Kc >= 128)
   void* cn_ws = nullptr;       // Crank-Nicolson ALS workspace (allocated by its first call)
   size_t cn_bytes = 0;
 };
@@ -996,6 +997,8 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     delete c;
     return HT_ERR_CUDA;
   }
+  // wide node factors: the cluster form of the SVD, when a cluster fits this device
+  if (c->Kc >= 128) c->svd_clu = htg_svd_cluster_setup(cfg->device);
   // SVD working copy in shared memory when the capacity allows
   const size_t Kc = (size_t)c->Kc;
   c->svd_smem = ((2 * Kc * Kc + Kc) * sizeof(double) <= 200 * 1024) ? 1 : 0;
@@ -1116,8 +1119,10 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
     c->launches += coop_extra;
   }
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  const SvdClusterCfg* clu = (count == 1) ? &c->svd_clu : nullptr;
   HTG_LAUNCH(c, KC_SVD, s,
-             htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st));
+             htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st, clu));
+  c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
   HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM), count, st));
   HTG_LAUNCH(c, KC_GEMM, s,

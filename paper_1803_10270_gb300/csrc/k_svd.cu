@@ -11,8 +11,13 @@
 // pair has |a.b| > tol |a||b|, tol = eps * max(m, 8).  Rotation: zeta = (|b|^2 - |a|^2) / (2 a.b),
 // t = sign(zeta) / (|zeta| + hypot(1, zeta)), c = 1/sqrt(1+t^2), s = c t.
 // One CTA per matrix; the working copy lives in shared memory when the capacity allows,
-// else in the descriptor's global work buffer (L2 resident).
+// else in the descriptor's global work buffer (L2 resident).  Factors of 128 columns and more
+// go to the cluster form further down (one thread-block cluster per matrix).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -74,12 +79,238 @@ __device__ void cta_gemm(double* dst, const double* A, int lda, const double* B,
   }
 }
 
+// ------------------------------------------------------------ cluster form -----
+// Wide node factors (p >= SVDC_MIN_P columns) are taken by one thread-block cluster of cl CTAs
+// (16, else 8): column j of N = M V (its q rows; the rows of M past q are zero and stay zero)
+// and of V (p rows) lives in the shared memory of CTA j mod cl, slot j / cl, with |N_j|^2 beside
+// it.  Every Brent-Luk round, pair pi goes to CTA pi mod cl, one warp per pair, which reads and
+// rotates both columns where they live (distributed shared memory) and writes their new squared
+// norms; a cluster barrier ends the round.  The rotations are the one-sided (Hestenes) ones of
+// the FP64 phase above, applied to N directly: no FP32 phase and no Gram matrix, so each sweep is
+// one pass over the column pairs, and its FP64 work is spread over cl SMs.
+constexpr int SVDC_MIN_P = 128;
+constexpr int CNT = 512;                 // threads per CTA
+constexpr int CNW = CNT / 32;            // warps per CTA = pairs one CTA rotates at a time
+constexpr int CREG = 15;                 // N entries a lane holds in registers: q <= 32 * CREG
+constexpr int SVDC_MAXQ = 32 * CREG;
+
+__host__ __device__ inline long long svdc_smem_doubles(int p, int q, int cl) {
+  const long long ncol = (p + cl - 1) / cl;
+  return ncol * (long long)(p + q) + ncol + p + 8;
+}
+
+// whether the cluster form takes a p x q node factor (the one-CTA kernel skips exactly these)
+__host__ __device__ inline bool svdc_takes(int p, int q, int cl, long long cap_doubles) {
+  return cl > 0 && p >= SVDC_MIN_P && p <= SVDC_MAXQ && q >= 1 && q <= SVDC_MAXQ &&
+         svdc_smem_doubles(p, q, cl) <= cap_doubles;
+}
+
+__device__ inline int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The sweeps, with the KQ = ceil(q / 32) N entries of a lane in registers (a compile-time count,
+// so no FP64 instruction is issued for rows past q: an FP64 warp instruction costs the same with
+// one lane active as with 32).
+template <int KQ>
+__device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm, double* flag, int p, int q, int cl,
+                            double floor2, double skip_abs, int sh2, double* myflops) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int me = (int)cluster.block_rank();
+  const int ld = q + p;
+  const int p2 = p + (p & 1), npairs = p2 / 2;
+  const float TOL64F = htg_d2f(EPS * (double)htg_max(htg_max(p, q), 8));
+  __shared__ int rot_sh;
+  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+    if (tid == 0) rot_sh = 0;
+    __syncthreads();
+    for (int round = 0; round < p2 - 1; ++round) {
+      for (int pi = me + cl * wid; pi < npairs; pi += cl * CNW) {
+        int a, b;
+        rr_pair(pi, round, p, p2, &a, &b);
+        if (a < 0) continue;
+        double* ca = cluster.map_shared_rank(col + (long long)(a / cl) * ld, a % cl);
+        double* cb = cluster.map_shared_rank(col + (long long)(b / cl) * ld, b % cl);
+        double* na = cluster.map_shared_rank(nrm + a / cl, a % cl);
+        double* nb = cluster.map_shared_rank(nrm + b / cl, b % cl);
+        const double al = *na, be = *nb;
+        // the rounding floor and the discard-level skip of the one-CTA kernel
+        if (!(htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
+              (htg_dgt_nn(al, skip_abs) || htg_dgt_nn(be, skip_abs))))
+          continue;
+        double xa[KQ], xb[KQ];
+        double ga = 0.0;
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) {
+          const int i = lane + 32 * k;
+          xa[k] = (i < q) ? ca[i] : 0.0;
+          xb[k] = (i < q) ? cb[i] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) ga = fma(xa[k], xb[k], ga);
+        ga = warp_sum(ga);   // the xor butterfly leaves the same value in every lane
+        if (lane == 0) *myflops += 2.0 * q;
+        // test and angle in FP32 on the values scaled by 2^sh2, c refined in FP64 (as above)
+        bool oka, okb, okg;
+        const float alf = htg_d2f_shift(al, sh2, &oka), bef = htg_d2f_shift(be, sh2, &okb);
+        const float gaf = htg_d2f_shift(ga, sh2, &okg);
+        if (!(oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef))) continue;
+        bool okd;
+        const float df = htg_d2f_shift(be - al, sh2, &okd);
+        const float zf = df / (2.0f * gaf);
+        const float azf = fabsf(zf);
+        const double t =
+            htg_f2d((azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f))));
+        const double c = htg_rsqrt_fast(fma(t, t, 1.0)), sn = c * t;
+        double sa = 0.0, sb = 0.0;
+#pragma unroll
+        for (int k = 0; k < KQ; ++k) {
+          const int i = lane + 32 * k;
+          const double x = c * xa[k] - sn * xb[k];
+          const double y = sn * xa[k] + c * xb[k];
+          sa = fma(x, x, sa);
+          sb = fma(y, y, sb);
+          if (i < q) {
+            ca[i] = x;
+            cb[i] = y;
+          }
+        }
+        // V columns, five entries per lane loaded ahead of their stores
+        double* va = ca + q;
+        double* vb = cb + q;
+        for (int i0 = 0; i0 < p; i0 += 160) {
+          double x[5], y[5];
+#pragma unroll
+          for (int u = 0; u < 5; ++u) {
+            const int i = i0 + lane + 32 * u;
+            x[u] = (i < p) ? va[i] : 0.0;
+            y[u] = (i < p) ? vb[i] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < 5; ++u) {
+            const int i = i0 + lane + 32 * u;
+            if (i < p) {
+              va[i] = c * x[u] - sn * y[u];
+              vb[i] = sn * x[u] + c * y[u];
+            }
+          }
+        }
+        sa = warp_sum(sa);
+        sb = warp_sum(sb);
+        if (lane == 0) {
+          *na = sa;
+          *nb = sb;
+          rot_sh = 1;
+          *myflops += 12.0 * q + 6.0 * p;
+        }
+      }
+      cluster.sync();   // the round's columns and norms are visible to every CTA
+    }
+    if (tid == 0) *flag = rot_sh ? 1.0 : 0.0;   // this CTA's flag of the sweep
+    cluster.sync();
+    const int any = __syncthreads_or(tid < cl ? (*cluster.map_shared_rank(flag, tid) != 0.0) : 0);
+    cluster.sync();   // every flag read before the next sweep rewrites it
+    if (!any) break;
+  }
+}
+
+__global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __restrict__ descs, long long cap_doubles,
+                                                             double* flops) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cl = (int)cluster.num_blocks();
+  const int me = (int)cluster.block_rank();
+  const SvdDesc D = descs[blockIdx.x / cl];
+  const int p = D.p, q = D.q;
+  // the same answer in every CTA of the cluster, so either all of them return here or none
+  if (!svdc_takes(p, q, cl, cap_doubles)) return;
+  extern __shared__ double smem[];
+  const int ncol = (p + cl - 1) / cl, ld = q + p;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // layout (doubles): red[0..7] | columns ncol * ld | nrm ncol | sig p
+  double* red = smem;             // [0] max |M| and [1] |M|_F^2 of this CTA's columns, [2] sweep flag
+  double* col = smem + 8;
+  double* nrm = col + (long long)ncol * ld;
+  double* sig = nrm + ncol;
+  for (int e = tid; e < ncol * ld; e += CNT) {
+    const int s = e / ld, i = e - s * ld, j = s * cl + me;
+    double v = 0.0;
+    if (j < p) v = (i < q) ? D.P[j + (long long)D.ldp * i] : ((i - q == j) ? 1.0 : 0.0);
+    col[e] = v;
+  }
+  __syncthreads();
+  __shared__ double wmax[CNW];
+  double am = 0.0;
+  for (int s = wid; s < ncol; s += CNW) {
+    const double* cc = col + (long long)s * ld;
+    double ss = 0.0;
+    for (int i = lane; i < q; i += 32) {
+      ss = fma(cc[i], cc[i], ss);
+      am = htg_dmax_nn(am, htg_dabs(cc[i]));
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) nrm[s] = ss;
+  }
+  for (int o = 16; o > 0; o >>= 1) am = htg_dmax_nn(am, __shfl_xor_sync(0xffffffffu, am, o));
+  if (lane == 0) wmax[wid] = am;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, f = 0.0;
+    for (int w = 0; w < CNW; ++w) a = htg_dmax_nn(a, wmax[w]);
+    for (int s = 0; s < ncol; ++s) f += nrm[s];
+    red[0] = a;
+    red[1] = f;
+  }
+  cluster.sync();
+  // cluster totals, summed in CTA order, so every CTA holds the same values
+  double amax = 0.0, fro = 0.0;
+  for (int r = 0; r < cl; ++r) {
+    const double* rr = cluster.map_shared_rank(red, r);
+    amax = htg_dmax_nn(amax, rr[0]);
+    fro += rr[1];
+  }
+  const int sh_e = (amax > 0.0) ? -ilogb(amax) : 0;
+  const double floor2 = EPS * EPS * fro;
+  const double skip_abs = D.skip2 * fro / (double)p;
+  double myflops = 0.0;
+  switch ((q + 31) / 32) {
+#define SVDC_CASE(K) \
+  case K: svdc_sweeps<K>(cluster, col, nrm, red + 2, p, q, cl, floor2, skip_abs, 2 * sh_e, &myflops); break;
+    SVDC_CASE(1) SVDC_CASE(2) SVDC_CASE(3) SVDC_CASE(4) SVDC_CASE(5) SVDC_CASE(6) SVDC_CASE(7) SVDC_CASE(8)
+    SVDC_CASE(9) SVDC_CASE(10) SVDC_CASE(11) SVDC_CASE(12) SVDC_CASE(13) SVDC_CASE(14) SVDC_CASE(15)
+#undef SVDC_CASE
+    default: break;
+  }
+  // singular values |N_j| of every column, gathered into every CTA
+  for (int j = tid; j < p; j += CNT) sig[j] = sqrt(*cluster.map_shared_rank(nrm + j / cl, j % cl));
+  cluster.sync();   // no CTA leaves while another still reads its norms
+  for (int s = wid; s < ncol; s += CNW) {
+    const int j = s * cl + me;
+    if (j >= p) continue;
+    const double sc = sig[j];
+    int rank = 0;
+    for (int o = lane; o < p; o += 32) {
+      const double so = sig[o];
+      rank += htg_dgt_nn(so, sc) || (__double_as_longlong(so) == __double_as_longlong(sc) && o < j);
+    }
+    rank = warp_sum_int(rank);
+    const double* cc = col + (long long)s * ld;
+    if (lane == 0) D.sigma[rank] = sc;
+    for (int i = lane; i < p; i += 32) D.V[i + (long long)p * rank] = cc[q + i];
+    const double inv = htg_dpos_finite(sc) ? 1.0 / sc : 0.0;
+    for (int i = lane; i < q; i += 32) D.U[i + (long long)q * rank] = cc[i] * inv;
+  }
+  if (flops && lane == 0 && myflops > 0.0) atomicAdd(flops, myflops);
+}
+
 __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ descs, long long inst_stride,
-                                                long long smem_doubles, double* flops) {
+                                                long long smem_doubles, double* flops, int cl, long long cl_cap) {
   // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
   const SvdDesc D = ((const SvdDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
   const int p = D.p, q = D.q;
   if (p <= 0) return;
+  if (svdc_takes(p, q, cl, cl_cap)) return;   // the cluster form's launch takes this factor
   const int mr = htg_max(p, q);
   extern __shared__ double smem[];
   // layout (doubles): M64 mr*p | N mr*p | G p*p | V p*p | T p*p | nrm p | M32 mr*p/2 | V32 p*p/2
@@ -361,11 +592,65 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
 
 }  // namespace
 
+bool htg_svd_cluster_used(const SvdClusterCfg* clu, int count, int pmax) {
+  return clu && clu->cl > 0 && count == 1 && pmax >= SVDC_MIN_P;
+}
+
+SvdClusterCfg htg_svd_cluster_setup(int device) {
+  SvdClusterCfg out;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, svd_cluster_kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  const long long dyn = (long long)optin - (long long)fa.sharedSizeBytes;
+  if (dyn < (long long)(8 * 1024)) return out;
+  if (cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess ||
+      cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  // the largest cluster (16 CTAs, else the portable 8) of which one fits the device with the
+  // full shared memory per CTA
+  const int sizes[2] = {16, 8};
+  for (int k = 0; k < 2; ++k) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sizes[k], 1, 1);
+    cfg.blockDim = dim3(CNT, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = sizes[k];
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, svd_cluster_kernel, &cfg) == cudaSuccess && n >= 1) {
+      out.cl = sizes[k];
+      out.cap_doubles = dyn / (long long)sizeof(double);
+      return out;
+    }
+    cudaGetLastError();
+  }
+  return out;
+}
+
 cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, int pmax, int qmax,
-                           cudaStream_t s, double* flops, int count, long long inst_stride) {
+                           cudaStream_t s, double* flops, int count, long long inst_stride, const SvdClusterCfg* clu) {
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (count > 65535) return cudaErrorInvalidValue;
   (void)use_smem;
+  // the cluster form's shared memory: enough for the widest factor it may be given
+  const bool use_cl = htg_svd_cluster_used(clu, count, pmax);
+  const int cl = use_cl ? clu->cl : 0;
+  long long cl_cap = 0;
+  if (use_cl) {
+    cl_cap = svdc_smem_doubles(htg_min(pmax, SVDC_MAXQ), htg_min(htg_max(qmax, 1), SVDC_MAXQ), cl);
+    if (cl_cap > clu->cap_doubles) cl_cap = clu->cap_doubles;
+  }
   // shared memory sized for p, q <= 40 (about 77 KB dynamic + 21 KB static: two CTAs per SM in
   // batched launches); larger node factors work in their global buffers
   pmax = htg_min(pmax, 40);
@@ -382,6 +667,21 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
-  svd_kernel<<<dim3(ndesc, count), NT, smem, s>>>(descs_dev, inst_stride, (long long)(smem / sizeof(double)), flops);
-  return cudaGetLastError();
+  svd_kernel<<<dim3(ndesc, count), NT, smem, s>>>(descs_dev, inst_stride, (long long)(smem / sizeof(double)), flops,
+                                                   cl, cl_cap);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !use_cl) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ndesc * cl), 1, 1);
+  cfg.blockDim = dim3(CNT, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)cl_cap * sizeof(double);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, svd_cluster_kernel, descs_dev, cl_cap, flops);
 }

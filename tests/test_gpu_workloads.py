@@ -206,6 +206,35 @@ def test_truncate_tall_node_matrices_rank_deficient(G):
         assert rel_err(from_gpu(out, tree), ref) < TOL64, f"tol {rel_tol}"
 
 
+@pytest.mark.parametrize("n,r,decay,deficient", [(150, 131, 0.85, True), (144, 140, 0.8, False)])
+def test_truncate_wide_node_factors(G, n, r, decay, deficient):
+    """ht_truncate of d=4 HT tensors of rank 131 (odd: a dummy player in every Jacobi round) and
+    140: every node factor is 131 / 140 columns wide, so the node SVDs run in the cluster form
+    (columns spread over the shared memory of one thread-block cluster).  Graded transfer tensors
+    make the root's children cut to ranks near 40 at tol 1e-8; the other nodes keep every
+    direction.  The deficient case duplicates a leaf column and zeroes a transfer slice (zero
+    singular values in the wide factors).  Ranks and T(u) against the oracle."""
+    d = 4
+    u = random_ht(d, n, r, seed=21, scale_decay=decay)
+    if deficient:
+        tree = u.tree
+        leaf = next(t for t in range(tree.n_nodes) if tree.is_leaf(t))
+        inner = next(t for t in range(1, tree.n_nodes) if not tree.is_leaf(t))
+        u.node[leaf][:, 1] = u.node[leaf][:, 0]
+        u.node[inner][:, :, 7] = 0.0
+    ref, rep = OH.truncate(u, 1e-8, r)
+    assert max(rep.ranks[1:]) == r and min(rep.ranks[1:]) < r
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    g = to_gpu(G, u, r)
+    out = G.HTTensor(d, [n] * d, r)
+    G.ht_truncate(ctx, g, 1e-8, r, out)
+    sync()
+    ctx.check()
+    assert out.ranks() == rep.ranks
+    assert rel_err(from_gpu(out, u.tree), ref) < TOL64
+    ctx.close()
+
+
 def test_untruncated_graded_spectrum_reproduces_u(G):
     """A truncation that keeps every direction returns u to rounding, even when node spectra
     span ten decades (transfer tensors graded by 0.7^j, rank 24): the projectors Y_t X_t of the
