@@ -55,7 +55,7 @@ constexpr int NN = HT_MAXNODES;
 // per launch (a level's complement QRs: 2 per interior node) and CTAs per matrix
 constexpr int QR_COOP_MIN_KC = 160;
 constexpr int QR_COOP_NDMAX = 2 * HT_MAXNODES;
-constexpr int QR_COOP_GMAX = 32;
+constexpr int QR_COOP_GMAX = 64;
 constexpr int MAXLEV = HT_MAXD;   // tree depth + 1 (the linear tree of d = 16 is 15 deep)
 
 // Device-side plan: dimensions derived from the device-resident ranks, plus every work
