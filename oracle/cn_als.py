@@ -21,7 +21,10 @@ measure of a sweep: max over q of |X_q^new - X_q^old|^2 (the paper's increment c
 Parity: pinned by tests -- a mode solve equals brute-force least squares over the full grid
 (library lstsq on the unfolded A); pure relaxation L = -nu I gives the closed form
 (1 - nu dt/2)/(1 + nu dt/2) x_n; a spatially uniform Maxwellian is a fixed point of the
-kinetic operator; the residual never increases from one mode solve to the next.
+kinetic operator; the residual never increases from one mode solve to the next; an x-uniform
+state relaxes to the rank-2 closed form g f0 + (1 - g) rho M; the exact full-grid step with
+these eta / zeta keeps the density and multiplies the momentum and E - 3 c2 rho by g; from the
+Maxwellian the density, velocity and temperature (Section 4.2, eqs. rho0, u0, T0) stay constant.
 """
 from __future__ import annotations
 

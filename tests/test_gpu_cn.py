@@ -125,3 +125,23 @@ def test_cn_damped_jacobi_matches_oracle(G):
     got, eps = run_gpu(G, 6, 8, kop.op, dt, xn, x0, 4, cap=3, max_terms=5, variant=G.CP_ALS_JACOBI_DAMPED)
     assert rel(to_full(got), to_full(ref)) < 1e-10
     assert np.allclose(eps, eps_ref, rtol=1e-6, atol=1e-14 * max(eps_ref))
+
+
+def test_cn_x_uniform_relaxation_closed_form(G):
+    """An x-uniform f0 sees no transport, so the exact Crank-Nicolson step of the kinetic
+    operator is f1 = g f0 + (1 - g) rho M (g = (1 - nu dt/2) / (1 + nu dt/2), rho = sum_v h^3 f0),
+    a rank-2 tensor: the rank-2 step from the guess [f0, 0.3 M] reaches it to rounding (x_n of
+    rank 1, x of rank 2; n = 8, 5 sweeps)."""
+    kc = kinetic_case(8)
+    v, m, ones = kc.vgrid(), kc.maxwellian(), np.ones(kc.n)
+    f0 = CP(np.ones(1), [ones[:, None]] * 3 +
+            [(m * (1 + 0.3 * v))[:, None], (m * (1 - 0.2 * v + 0.05 * v * v))[:, None], m[:, None]])
+    dt = 5 * kc.dt
+    g = (1 - 0.5 * kc.nu * dt) / (1 + 0.5 * kc.nu * dt)
+    rho = float(np.prod([kc.hv * f0.factors[3 + k][:, 0].sum() for k in range(3)]))
+    exact = g * to_full(f0) + (1 - g) * rho * to_full(CP(np.ones(1), [ones[:, None]] * 3 + [m[:, None]] * 3))
+    x0 = CP(np.array([1.0, 0.3]),
+            [np.concatenate([f0.factors[k], (ones if k < 3 else m)[:, None]], axis=1) for k in range(6)])
+    kop = G.KineticOp(kc)
+    got, _ = run_gpu(G, 6, 8, kop.op, dt, f0, x0, 5, cap=2, max_terms=5)
+    assert rel(to_full(got), exact) < 1e-12

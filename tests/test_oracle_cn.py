@@ -116,3 +116,89 @@ def test_damped_jacobi_step_is_a_stationary_point():
     for q in range(6):
         V = CN.mode_solve(x.factors, xn, eta, zeta, E, q)
         assert np.allclose(V, x.factors[q], rtol=1e-10, atol=1e-12 * np.abs(V).max()), q
+
+
+# ---- moments of the kinetic solution (Section 4.2: density, mean velocity, temperature) ----
+def grid_moments(f, kc):
+    """x-averaged density, momentum and second moment of a full-grid f on (x1,x2,x3,v1,v2,v3):
+    the discrete forms of the paper's <rho>, <rho><u> and sum_v |v|^2 f (eqs. rho0, u0, T0)."""
+    v = kc.vgrid()
+    w = (kc.hx / (2 * np.pi)) ** 3 * kc.hv ** 3
+    V = np.meshgrid(v, v, v, indexing="ij")
+    fv = f.reshape((kc.n ** 3,) + (kc.n,) * 3).sum(axis=0)      # sum over the x points
+    rho = w * fv.sum()
+    mom = np.array([w * (Vd * fv).sum() for Vd in V])
+    e2 = w * ((V[0] ** 2 + V[1] ** 2 + V[2] ** 2) * fv).sum()
+    return rho, mom, e2
+
+
+def test_exact_crank_nicolson_moment_recursions():
+    """The discrete kinetic operator keeps the x-averaged mass (periodic central differences sum
+    to zero over x, and sum_v h^3 M = 1), relaxes the momentum at rate nu (sum_v v M = 0 on the
+    symmetric grid) and the second moment E towards 3 c2 rho (c2 = sum_j h v_j^2 m_j).  Hence the
+    exact Crank-Nicolson step, A f1 = B f0 solved on the full grid with the oracle's eta / zeta,
+    keeps rho and multiplies the momentum and E - 3 c2 rho by g = (1 - nu dt/2) / (1 + nu dt/2),
+    for any f0 (here the x-dependent kinetic initial condition, n = 4).  A sign error in eta or
+    zeta, a transposed Maxwellian projector or a lost term breaks one of the three."""
+    from paper_1803_10270_gb300.inputs import kinetic_ic
+    kc = kinetic_case(4)
+    alphas, factors = kinetic_terms(kc)
+    dt = 5 * kc.dt
+    eta, zeta, E = CN.cn_terms(alphas, factors, dt, 6)
+    A = full_op(E, eta, 6, kc.n)
+    B = full_op(E, zeta, 6, kc.n)
+    w, F = kinetic_ic(kc)
+    f = to_full(CP(w, F)).reshape(-1)
+    g = (1 - 0.5 * kc.nu * dt) / (1 + 0.5 * kc.nu * dt)
+    c2 = kc.hv * float(np.sum(kc.vgrid() ** 2 * kc.maxwellian()))
+    rho0, mom0, e0 = grid_moments(f, kc)
+    assert np.abs(mom0).max() > 1e-3 * rho0          # a state away from equilibrium
+    for step in range(1, 4):
+        f = np.linalg.solve(A, B @ f)
+        rho, mom, e2 = grid_moments(f, kc)
+        assert abs(rho - rho0) <= 1e-13 * rho0, step
+        assert np.allclose(mom, g ** step * mom0, rtol=1e-11, atol=1e-13 * rho0), step
+        assert abs((e2 - 3 * c2 * rho) - g ** step * (e0 - 3 * c2 * rho0)) <= 1e-12 * e0, step
+
+
+def test_x_uniform_relaxation_reaches_the_closed_form():
+    """An x-uniform f0 = 1 x 1 x 1 x g1(v1) g2(v2) g3(v3) sees no transport, so the exact
+    Crank-Nicolson step is f1 = g f0 + (1 - g) rho M (rho = sum_v h^3 f0): rank 2.  The CP-ALS
+    step of rank 2 from the guess [f0, 0.3 M] reaches it to rounding, so its moments follow the
+    recursions above exactly (n = 8, dt = 5x the explicit step, 5 sweeps)."""
+    kc = kinetic_case(8)
+    alphas, factors = kinetic_terms(kc)
+    v, m, ones = kc.vgrid(), kc.maxwellian(), np.ones(kc.n)
+    f0 = CP(np.ones(1), [ones[:, None]] * 3 +
+            [(m * (1 + 0.3 * v))[:, None], (m * (1 - 0.2 * v + 0.05 * v * v))[:, None], m[:, None]])
+    dt = 5 * kc.dt
+    g = (1 - 0.5 * kc.nu * dt) / (1 + 0.5 * kc.nu * dt)
+    rho = float(np.prod([kc.hv * f0.factors[3 + k][:, 0].sum() for k in range(3)]))
+    Mx = to_full(CP(np.ones(1), [ones[:, None]] * 3 + [m[:, None]] * 3))
+    exact = g * to_full(f0) + (1 - g) * rho * Mx
+    x0 = CP(np.array([1.0, 0.3]),
+            [np.concatenate([f0.factors[k], (ones if k < 3 else m)[:, None]], axis=1) for k in range(6)])
+    x, _ = CN.cn_als_step(f0, x0, alphas, factors, dt, 5)
+    assert np.linalg.norm(to_full(x) - exact) <= 1e-13 * np.linalg.norm(exact)
+    r0, p0, _ = grid_moments(to_full(f0), kc)
+    r1, p1, _ = grid_moments(to_full(x), kc)
+    assert abs(r1 - r0) <= 1e-13 * r0
+    assert np.allclose(p1, g * p0, rtol=1e-11, atol=1e-13 * r0)
+
+
+def test_equilibrium_moments_stay_constant():
+    """The paper's steady-state check: from the Maxwellian f_eq, CP-ALS Crank-Nicolson steps keep
+    the average density, velocity and temperature (eqs. rho0, u0, T0) at their initial values."""
+    kc = kinetic_case(8)
+    alphas, factors = kinetic_terms(kc)
+    ones, m = np.ones(kc.n), kc.maxwellian()
+    f = CP(np.ones(1), [ones[:, None]] * 3 + [m[:, None]] * 3)
+    r0, p0, e0 = grid_moments(to_full(f), kc)
+    x = f
+    for _ in range(3):
+        x, _ = CN.cn_als_step(x, x, alphas, factors, 5 * kc.dt, 3)
+    r, p, e2 = grid_moments(to_full(x), kc)
+    assert abs(r - r0) <= 1e-13 * r0
+    assert np.abs(p).max() <= 1e-14 * r0 and np.abs(p0).max() <= 1e-14 * r0
+    t0, t = e0 / (3 * r0), (e2 - (p ** 2).sum() / r) / (3 * r)     # |v - <u>|^2 form of eq. T0
+    assert abs(t - t0) <= 1e-13 * t0
