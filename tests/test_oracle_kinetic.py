@@ -1,0 +1,75 @@
+"""The kinetic step pinned by its x-Fourier-mode closed form, independent of the operator's
+term list.
+
+The periodic central difference is circulant in x: on exp(i k x) it multiplies by
+i sin(k h) / h.  For an x-band-limited f (the kinetic initial condition carries x-modes |k| <= 2
+only) every x-mode K = (k1, k2, k3) therefore evolves on its own v-grid problem,
+    L_K g = -i (v1 s(k1) + v2 s(k2) + v3 s(k3)) g - nu g + nu M(v) sum_v h_v^3 g,   s(k) = sin(k h)/h,
+(the transport of the linearised kinetic equation, Section 4.2, eq. BGK_LIN, and the collision
+term with rho = sum_v h_v^3 f), and one untruncated HEUN2 step is p(dt L_K) g with
+p(z) = 1 + z + z^2/2 on each mode.  Nothing here uses the oracle's kinetic term list, so a wrong
+sign, a transport factor on the wrong dimension or a lost term in it fails the comparison.
+"""
+import numpy as np
+
+from oracle import ht as OH
+from oracle.problems import kinetic_terms
+from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+
+
+def mode_closed_form_step(kc, w, F, dt, kmax=2):
+    """Full-grid f after one step of p(dt L) on the band-limited CP f = sum_t w_t prod_j F_j[:, t]."""
+    n, hx, hv, nu = kc.n, kc.hx, kc.hv, kc.nu
+    x, v, m = kc.xgrid(), kc.vgrid(), kc.maxwellian()
+    ks = np.arange(-kmax, kmax + 1)
+    phase = np.exp(1j * np.outer(ks, x))                  # e^{i k x}, (modes, n)
+    # x-DFT coefficients of each x-factor; band-limited to |k| <= kmax (checked)
+    coef = []
+    for j in range(3):
+        c = np.conj(phase) @ F[j] / n                     # (modes, rank)
+        assert np.allclose(phase.T @ c, F[j], atol=1e-13 * max(1.0, np.abs(F[j]).max()))
+        coef.append(c)
+    M = np.einsum("a,b,c->abc", m, m, m)
+    V1, V2, V3 = np.meshgrid(v, v, v, indexing="ij")
+    s = np.sin(ks * hx) / hx
+    out = np.zeros((n,) * 6)
+    Ex = [phase[:, :, None, None] * np.ones((1, 1, n, n)),
+          phase[:, None, :, None] * np.ones((1, n, 1, n)),
+          phase[:, None, None, :] * np.ones((1, n, n, 1))]
+    for a, k1 in enumerate(ks):
+        for b, k2 in enumerate(ks):
+            for c, k3 in enumerate(ks):
+                amp = w * coef[0][a] * coef[1][b] * coef[2][c]          # (rank,)
+                if np.abs(amp).max() == 0.0:
+                    continue
+                g = np.einsum("t,it,jt,kt->ijk", amp, F[3], F[4], F[5])  # complex v array
+                sym = -1j * (V1 * s[a] + V2 * s[b] + V3 * s[c])
+
+                def L(h):
+                    return sym * h - nu * h + nu * M * (hv ** 3 * h.sum())
+                Lg = L(g)
+                gn = g + dt * Lg + 0.5 * dt * dt * L(Lg)
+                ex = np.exp(1j * (k1 * x[:, None, None] + k2 * x[None, :, None] + k3 * x[None, None, :]))
+                out += np.real(np.einsum("abc,ijk->abcijk", ex, gn))
+    return out
+
+
+def test_heun2_step_matches_x_fourier_mode_closed_form():
+    """The oracle's untruncated HT HEUN2 step of the kinetic operator (n = 12, the seeded kinetic
+    initial condition, dt = 5x the explicit step) equals the x-mode-wise closed form on the full
+    grid to rounding."""
+    kc = kinetic_case(12)
+    w, F = kinetic_ic(kc)
+    dt = 5 * kc.dt
+    alphas, factors = kinetic_terms(kc)
+    u = OH.from_cp(w, F)
+    u1, _ = OH.step_heun2(u, alphas, factors, dt, 0.0, 10 ** 6)
+    # the full grid as U_{t1} B_root U_{t2}^T (x dimensions fastest, as in eq. HTD), without the
+    # Kronecker product of the two root-child bases
+    c1, c2 = u1.tree.children[0]
+    full = OH.node_basis(u1, c1) @ u1.node[0] @ OH.node_basis(u1, c2).T
+    got = full.reshape((kc.n,) * 6, order="F")
+    ref = mode_closed_form_step(kc, w, F, dt)
+    f0 = OH.to_full(u)
+    assert np.abs(ref - f0).max() > 1e-3 * np.abs(f0).max()       # the step moves f
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
