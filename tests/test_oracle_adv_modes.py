@@ -1,0 +1,102 @@
+"""The 6-D advection steps at the bench's full size (n = 64) pinned by the fully discrete Fourier
+closed form on sampled modes, without a 64^6 grid.
+
+A single Fourier coefficient u^(q) = n^-d sum_x u(x) exp(-i q.x) of an HT tensor is a contraction
+of its leaves with one separable vector per dimension, so it is evaluated on the format.  The
+periodic central difference multiplies exp(i k x) by i sin(k h)/h, so K RK2 steps give
+u^_K(q) = R(dt lam(q))^K u^_0(q), lam(q) = -i sum_j c_j sin(q_j h)/h, R(z) = 1 + z + z^2/2, and the
+initial condition sum_m prod_i exp(sin(x_i + phi_mi)) has u^_0(q) = sum_m prod_i a^_mi(q_i) from
+1-D DFTs.  Untruncated steps must reach it to rounding; truncated steps (the bench's tol 1e-8,
+r_max 32) within n^-d/2 times the accumulated HSVD error bound (Parseval).
+"""
+import math
+
+import numpy as np
+
+from oracle import ht as OH
+from oracle.problems import advection_A
+from paper_1803_10270_gb300.inputs import advection_case
+
+
+def fourier_coefficient(u, q, x):
+    """u^(q) of an HT tensor: the leaves contracted with exp(-i q_i x)/n_i, then up the tree
+    (eq. HTD: B_t[a, b, c] couples basis a of the first child with b of the second)."""
+    tr = u.tree
+    val = {}
+    for t in sorted(range(tr.n_nodes), key=lambda t: -tr.depth[t]):
+        X = u.node[t]
+        if tr.is_leaf(t):
+            i = tr.lo[t]
+            val[t] = (np.exp(-1j * q[i] * x) / len(x)) @ X
+        else:
+            a, b = tr.children[t]
+            if t == 0:
+                return complex(val[a] @ X @ val[b])
+            val[t] = np.einsum("a,b,abc->c", val[a], val[b], X)
+    raise RuntimeError("unreachable")
+
+
+def closed_form(case, q, steps):
+    n, h, x = case.n, case.h, case.x()
+    ic = case.ic_factors()
+    u0 = 0.0
+    for m in range(case.n_terms):
+        term = 1.0 + 0.0j
+        for i in range(case.d):
+            term *= np.fft.fft(ic[i][:, m])[q[i] % n] / n
+        u0 += term
+    lam = -1j * sum(case.c[j] * math.sin(q[j] * h) / h for j in range(case.d))
+    z = case.dt * lam
+    return (1.0 + z + 0.5 * z * z) ** steps * u0
+
+
+def sample_modes(d, count, seed):
+    rng = np.random.default_rng(seed)
+    qs = [np.zeros(d, dtype=int)] + [np.eye(d, dtype=int)[i] * s for i in range(d) for s in (1, -2)]
+    qs += [rng.integers(-4, 5, d) for _ in range(count)]
+    return qs
+
+
+def test_untruncated_steps_match_fourier_modes_at_n64():
+    """Three exact RK2-polynomial applies (ranks 2 -> 6 -> 18 -> 54) of the bench workload."""
+    case = advection_case(6, 64, seed_offset=1)
+    A = advection_A(case)
+    u = OH.from_cp(np.ones(case.n_terms), case.ic_factors())
+    for _ in range(3):
+        u = OH.apply_kron_sum_rk2(u, A)
+    assert max(u.ranks()[1:]) == 54
+    x = case.x()
+    scale = abs(closed_form(case, np.zeros(6, dtype=int), 0))
+    for q in sample_modes(6, 24, seed=5):
+        got = fourier_coefficient(u, q, x)
+        ref = closed_form(case, q, 3)
+        assert abs(got - ref) <= 1e-13 * scale, q
+
+
+def test_truncated_bench_steps_within_the_hsvd_bound():
+    """Five steps of the bench's HT route (tol 1e-8, r_max 32): every sampled coefficient lies
+    within n^-d/2 sum_k g^(K-1-k) e_k of the exact one, e_k = sqrt(sum_t discarded_t^2) the HSVD
+    bound of step k's truncation and g = max_q |R(dt lam(q))| the growth of later steps."""
+    case = advection_case(6, 64, seed_offset=1)
+    A = advection_A(case)
+    u = OH.from_cp(np.ones(case.n_terms), case.ic_factors())
+    theta = case.dt * sum(abs(c) for c in case.c) / case.h
+    g = math.sqrt(1.0 + theta ** 4 / 4.0)           # |R(i s)| = sqrt(1 + s^4/4), |s| <= theta
+    K, bound = 5, 0.0
+    for _ in range(K):
+        u, rep = OH.step_rk2_poly(u, A, 1e-8, 32)
+        e_k = math.sqrt(sum(v * v for v in rep.discarded.values()))
+        # the rank rule: each of the 2d - 2 non-root nodes (the root's children counted twice)
+        # discards at most (tol |v|)^2 / (2d - 3) when r_max does not bind
+        assert max(rep.ranks) < 32
+        assert e_k <= 1e-8 * rep.norm * math.sqrt(10.0 / 9.0) * (1 + 1e-12)
+        bound = bound * g + e_k
+    assert 0.0 < bound
+    x = case.x()
+    tol = bound / 64.0 ** 3 * 1.01 + 1e-14 * abs(closed_form(case, np.zeros(6, dtype=int), 0))
+    worst = 0.0
+    for q in sample_modes(6, 24, seed=6):
+        err = abs(fourier_coefficient(u, q, x) - closed_form(case, q, K))
+        worst = max(worst, err)
+        assert err <= tol, q
+    assert worst > 0.0
