@@ -1,5 +1,5 @@
-"""The 6-D advection steps at the bench's full size (n = 64) pinned by the fully discrete Fourier
-closed form on sampled modes, without a 64^6 grid.
+"""The 6-D advection steps at the bench's full size (n = 64), HT and CP routes, pinned by the fully
+discrete Fourier closed form on sampled modes, without a 64^6 grid.
 
 A single Fourier coefficient u^(q) = n^-d sum_x u(x) exp(-i q.x) of an HT tensor is a contraction
 of its leaves with one separable vector per dimension, so it is evaluated on the format.  The
@@ -100,3 +100,42 @@ def test_truncated_bench_steps_within_the_hsvd_bound():
         worst = max(worst, err)
         assert err <= tol, q
     assert worst > 0.0
+
+
+def cp_fourier_coefficient(x, q):
+    """x^(q) of a CP tensor: sum_l w_l prod_i (DFT of factor column l of dimension i at q_i) / n."""
+    term = np.asarray(x.weights, dtype=np.complex128).copy()
+    for i, F in enumerate(x.factors):
+        n = F.shape[0]
+        term *= np.fft.fft(F, axis=0)[q[i] % n] / n
+    return complex(term.sum())
+
+
+def test_cp_route_at_n64_against_fourier_modes():
+    """The CP route at the bench size: the exact apply y = p(dt L) x (rank 2 (1 + 2d + d(d-1)/2)
+    = 56) has y^(q) = R(dt lam(q)) x^(q) to rounding, and the fitted rank-24 x after 5 Gauss-Seidel
+    sweeps lies within n^-d/2 (|y - x| + the Gram-difference rounding floor) of it on every
+    sampled mode, |y - x| the oracle's reported residual."""
+    from oracle import cp as OC
+    from paper_1803_10270_gb300.inputs import cp_padding
+    case = advection_case(6, 64, seed_offset=1)
+    A = advection_A(case)
+    x = OC.CP(np.ones(case.n_terms), case.ic_factors())
+    y = OC.apply_kron_sum_rk2(x, A)
+    assert y.rank == 56
+    h = case.h
+    scale = abs(cp_fourier_coefficient(x, np.zeros(6, dtype=int)))
+    qs = sample_modes(6, 24, seed=7)
+    for q in qs:
+        lam = -1j * sum(case.c[j] * math.sin(q[j] * h) / h for j in range(6))
+        z = case.dt * lam
+        ref = (1.0 + z + 0.5 * z * z) * cp_fourier_coefficient(x, q)
+        assert abs(cp_fourier_coefficient(y, q) - ref) <= 1e-13 * scale, q
+    pad = cp_padding([64] * 6, 22, seed=0x5EED + 1, scale=1e-3)
+    x1, _ = OC.step_rk2(x, A, 24, pad, 5)
+    res = OC.residual(y, x1)
+    ny = OC.residual(y, OC.CP(np.zeros(1), [np.zeros((64, 1))] * 6))
+    floor = 4.0 * math.sqrt(2.2e-16) * 2.0 * ny                 # |.|^2 formed from Gram sums
+    for q in qs:
+        err = abs(cp_fourier_coefficient(x1, q) - cp_fourier_coefficient(y, q))
+        assert err <= (res + floor) / 64.0 ** 3 * 1.01, q
