@@ -139,3 +139,31 @@ def test_cp_route_at_n64_against_fourier_modes():
     for q in qs:
         err = abs(cp_fourier_coefficient(x1, q) - cp_fourier_coefficient(y, q))
         assert err <= (res + floor) / 64.0 ** 3 * 1.01, q
+
+
+def test_twelve_dim_n128_steps_match_fourier_modes():
+    """The 12-D workload (n = 128, depth-4 tree, rank-3 initial condition): two untruncated
+    RK2-polynomial applies (ranks 3 -> 9 -> 27) reach the closed form to rounding, and five of the
+    bench's truncated steps (tol 1e-8, r_max 64) stay within the HSVD bound, on sampled modes."""
+    case = advection_case(12, 128, n_terms=3, seed_offset=4)
+    A = advection_A(case)
+    x = case.x()
+    u0 = OH.from_cp(np.ones(case.n_terms), case.ic_factors())
+    scale = abs(closed_form(case, np.zeros(12, dtype=int), 0))
+    u = u0
+    for _ in range(2):
+        u = OH.apply_kron_sum_rk2(u, A)
+    assert max(u.ranks()[1:]) == 27
+    qs = sample_modes(12, 24, seed=8)
+    for q in qs:
+        assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 2)) <= 1e-13 * scale, q
+    theta = case.dt * sum(abs(c) for c in case.c) / case.h
+    g = math.sqrt(1.0 + theta ** 4 / 4.0)
+    u, bound = u0, 0.0
+    for _ in range(5):
+        u, rep = OH.step_rk2_poly(u, A, 1e-8, 64)
+        assert max(rep.ranks) < 64
+        bound = bound * g + math.sqrt(sum(v * v for v in rep.discarded.values()))
+    tol = bound / 128.0 ** 6 * 1.01 + 1e-14 * scale
+    for q in qs:
+        assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 5)) <= tol, q
