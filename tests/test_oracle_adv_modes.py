@@ -167,3 +167,30 @@ def test_twelve_dim_n128_steps_match_fourier_modes():
     tol = bound / 128.0 ** 6 * 1.01 + 1e-14 * scale
     for q in qs:
         assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 5)) <= tol, q
+
+
+def test_tensor_train_route_at_n64_matches_fourier_modes():
+    """The same steps on the linear (tensor-train) dimension tree: three untruncated applies to
+    rounding and five truncated bench steps within the HSVD bound, on sampled modes."""
+    from oracle.tree import build_tree
+    case = advection_case(6, 64, seed_offset=1)
+    A = advection_A(case)
+    x = case.x()
+    u0 = OH.from_cp(np.ones(case.n_terms), case.ic_factors(), build_tree(6, "linear"))
+    scale = abs(closed_form(case, np.zeros(6, dtype=int), 0))
+    qs = sample_modes(6, 24, seed=9)
+    u = u0
+    for _ in range(3):
+        u = OH.apply_kron_sum_rk2(u, A)
+    for q in qs:
+        assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 3)) <= 1e-13 * scale, q
+    theta = case.dt * sum(abs(c) for c in case.c) / case.h
+    g = math.sqrt(1.0 + theta ** 4 / 4.0)
+    u, bound = u0, 0.0
+    for _ in range(5):
+        u, rep = OH.step_rk2_poly(u, A, 1e-8, 32)
+        assert max(rep.ranks) < 32
+        bound = bound * g + math.sqrt(sum(v * v for v in rep.discarded.values()))
+    tol = bound / 64.0 ** 3 * 1.01 + 1e-14 * scale
+    for q in qs:
+        assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 5)) <= tol, q
