@@ -73,3 +73,55 @@ def test_heun2_step_matches_x_fourier_mode_closed_form():
     f0 = OH.to_full(u)
     assert np.abs(ref - f0).max() > 1e-3 * np.abs(f0).max()       # the step moves f
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def contract(u, vecs):
+    """sum over the grid of u * prod_i vecs[i] (complex vectors), leaves to root (eq. HTD)."""
+    tr = u.tree
+    val = {}
+    for t in sorted(range(tr.n_nodes), key=lambda t: -tr.depth[t]):
+        X = u.node[t]
+        if tr.is_leaf(t):
+            val[t] = vecs[tr.lo[t]] @ X
+        else:
+            a, b = tr.children[t]
+            if t == 0:
+                return complex(val[a] @ X @ val[b])
+            val[t] = np.einsum("a,b,abc->c", val[a], val[b], X)
+    raise RuntimeError("unreachable")
+
+
+def test_full_size_heun2_step_matches_mode_closed_form_on_samples():
+    """The same closed form at the kinetic workload's full size (n = 64: no full grid): after
+    one untruncated HEUN2 step of the oracle (node ranks up to 222), the x-Fourier coefficient
+    f^(K; v) at sampled x-modes K and v-grid points equals p(dt L_K) applied to the mode's
+    v-array, to rounding."""
+    kc = kinetic_case(64)
+    w, F = kinetic_ic(kc)
+    dt = kc.dt
+    alphas, factors = kinetic_terms(kc)
+    u1, _ = OH.step_heun2(OH.from_cp(w, F), alphas, factors, dt, 0.0, 10 ** 6)
+    n, hx, hv, nu = kc.n, kc.hx, kc.hv, kc.nu
+    x, v, m = kc.xgrid(), kc.vgrid(), kc.maxwellian()
+    M = np.einsum("a,b,c->abc", m, m, m)
+    V1, V2, V3 = np.meshgrid(v, v, v, indexing="ij")
+    rng = np.random.default_rng(12)
+    modes = [(0, 0, 0), (1, 0, 0), (0, -1, 2), (2, 2, -1), (-1, 1, 1), (1, -2, 0)]
+    pts = [(32, 32, 32), (0, 63, 17)] + [tuple(rng.integers(0, n, 3)) for _ in range(10)]
+    scale = 0.0
+    for K in modes:
+        coef = [np.exp(-1j * K[j] * x) @ F[j] / n for j in range(3)]
+        g = np.einsum("t,it,jt,kt->ijk", w * coef[0] * coef[1] * coef[2], F[3], F[4], F[5])
+        s = [np.sin(k * hx) / hx for k in K]
+        sym = -1j * (V1 * s[0] + V2 * s[1] + V3 * s[2])
+
+        def L(h):
+            return sym * h - nu * h + nu * M * (hv ** 3 * h.sum())
+        Lg = L(g)
+        ref = g + dt * Lg + 0.5 * dt * dt * L(Lg)
+        scale = max(scale, np.abs(ref).max())
+        for p in pts:
+            vecs = [np.exp(-1j * K[j] * x) / n for j in range(3)]
+            vecs += [np.eye(n)[p[j]] for j in range(3)]
+            got = contract(u1, vecs)
+            assert abs(got - ref[p]) <= 1e-12 * scale, (K, p)
