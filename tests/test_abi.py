@@ -75,3 +75,57 @@ def test_host_side_argument_errors(lib):
     assert lib.ht_step(None, None, None, 0.1, 1e-8, 4, 0, None) == G.HT_ERR_ARG
     assert lib.cp_als_sweep(None, None, None, 1, 0, None, None) == G.HT_ERR_ARG
     assert lib.ht_status_string(G.HT_ERR_CAPACITY) == b"HT_ERR_CAPACITY"
+
+
+def test_every_entry_point_checks_its_arguments_before_the_gpu(lib):
+    """Each entry point answers null or malformed arguments with its status code, from host
+    checks made before any CUDA call (so this runs without a GPU); the destroy calls and the
+    launch counter accept a null handle."""
+    from paper_1803_10270_gb300 import htgpu as G
+    ARG, CAPY = G.HT_ERR_ARG, G.HT_ERR_CAPACITY
+    assert lib.ht_apply(None, None, None, 0.1, 0, None, None) == ARG
+    assert lib.ht_truncate(None, None, 1e-8, 4, None, None, 0, None, None) == ARG
+    assert lib.ht_step_ab2(None, None, None, None, 0.1, 1e-8, 4, None) == ARG
+    assert lib.ht_from_cp(None, None, None, None) == ARG
+    assert lib.ht_mass(None, None, None, None) == ARG
+    assert lib.ht_inner(None, None, None, None, None) == ARG
+    assert lib.cp_apply_rk2(None, None, None, 0.1, None, None) == ARG
+    assert lib.cp_als_sweep_rk2(None, None, None, 0.1, None, 5, 0, None, None) == ARG
+    assert lib.cp_cn_als_step(None, None, None, 0.1, None, 5, 0, None, None) == ARG
+    assert lib.ht_ctx_profile(None, 1) == ARG
+    assert lib.ht_ctx_profile_read(None, None, None, None) == ARG
+    assert lib.ht_ctx_check(None, None) == ARG
+    assert lib.ht_ctx_launches(None) == 0
+    lib.ht_ctx_destroy(None)
+    lib.ht_batch_destroy(None)
+    out = C.c_void_p()
+    assert lib.ht_batch_create(None, 1, None, None) == ARG
+    assert lib.ht_batch_create(C.byref(out), 0, None, None) == ARG and not out.value
+    assert lib.ht_batch_step(None, None, None, None, None, 0, None) == ARG
+    # the allocation-free sweep takes no context: its size checks are all on the host
+    dummy = (C.c_double * 1)()
+    addr = C.cast(dummy, C.c_void_p).value
+
+    def cp(d, n, rank, cap):
+        t = G.cp_tensor()
+        t.d, t.rank, t.cap, t.weight = d, rank, cap, addr
+        for k in range(d):
+            t.n[k] = n
+            t.factor[k] = addr
+        return t
+    call = lambda y, x, sweeps=5, variant=0: lib.cp_als_sweep_noalloc(C.byref(y), C.byref(x), sweeps, variant,
+                                                                      None, None, None)
+    assert lib.cp_als_sweep_noalloc(None, None, 5, 0, None, None, None) == ARG
+    assert call(cp(6, 16, 4, 4), cp(6, 16, 2, 2), sweeps=65) == ARG
+    assert call(cp(6, 16, 4, 4), cp(6, 16, 2, 2), variant=7) == ARG
+    assert call(cp(1, 16, 4, 4), cp(1, 16, 2, 2)) == ARG                 # d < 2
+    assert call(cp(6, 16, 4, 4), cp(5, 16, 2, 2)) == ARG                 # d mismatch
+    assert call(cp(6, 16, 4, 4), cp(6, 17, 2, 2)) == ARG                 # n mismatch
+    assert call(cp(6, 16, 4, 4), cp(6, 16, 3, 2)) == CAPY                # rank > cap
+    assert call(cp(9, 16, 4, 4), cp(9, 16, 2, 2)) == CAPY                # d > 8
+    assert call(cp(6, 257, 4, 4), cp(6, 257, 2, 2)) == CAPY              # n > 256
+    assert call(cp(6, 16, 4, 4), cp(6, 16, 33, 33)) == CAPY              # x rank > 32
+    assert call(cp(6, 16, 1025, 1025), cp(6, 16, 2, 2)) == CAPY          # y rank > 1024
+    y, x = cp(6, 16, 4, 4), cp(6, 16, 2, 2)
+    x.factor[3] = None
+    assert call(y, x) == ARG                                             # missing factor
