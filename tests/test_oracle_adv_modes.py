@@ -194,3 +194,28 @@ def test_tensor_train_route_at_n64_matches_fourier_modes():
     tol = bound / 64.0 ** 3 * 1.01 + 1e-14 * scale
     for q in qs:
         assert abs(fourier_coefficient(u, q, x) - closed_form(case, q, 5)) <= tol, q
+
+
+def test_ab2_route_at_n64_matches_fourier_modes():
+    """The AB2 scheme (eq. AB2_) of the bench's ab2 line at n = 64: started by one RK2 step, each
+    mode follows w_{k+1} = (1 + 3z/2) w_k - (z/2) w_{k-1}, z = dt lam(q).  Three AB2 steps with
+    the sums formed exactly and no truncation (node ranks 2 -> 6 -> 16 -> 44 -> 120) reach it to
+    rounding on sampled modes."""
+    case = advection_case(6, 64, seed_offset=1)
+    A = advection_A(case)
+    x = case.x()
+    h = case.h
+    u_prev = OH.from_cp(np.ones(case.n_terms), case.ic_factors())
+    u = OH.apply_kron_sum_rk2(u_prev, A)
+    for _ in range(3):
+        u, u_prev = OH.add(1.0, OH.apply_kron_sum_poly(u, A, (1.0, 1.5)), 1.0,
+                           OH.apply_kron_sum_poly(u_prev, A, (0.0, -0.5))), u
+    assert max(u.ranks()[1:]) == 120
+    scale = abs(closed_form(case, np.zeros(6, dtype=int), 0))
+    for q in sample_modes(6, 24, seed=10):
+        z = case.dt * (-1j) * sum(case.c[j] * math.sin(q[j] * h) / h for j in range(6))
+        w0 = closed_form(case, q, 0)
+        w1 = (1.0 + z + 0.5 * z * z) * w0
+        for _ in range(3):
+            w1, w0 = (1.0 + 1.5 * z) * w1 - 0.5 * z * w0, w1
+        assert abs(fourier_coefficient(u, q, x) - w1) <= 1e-13 * scale, q
