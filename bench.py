@@ -91,16 +91,24 @@ def oracle_sample(seconds: float) -> dict:
     return {"steps": steps, "seconds": el, "value": steps / el}
 
 
-def cpu_baseline(seconds: float) -> dict:
-    """Run the oracle sample in a fresh single-threaded process (BLAS pinned to 1 thread)."""
+def oracle_sample_process(seconds: float, threads: int):
+    """One oracle sample in a fresh process with its BLAS / OpenMP threads set to `threads`
+    (the count the sample may use); (result dict, None) or (None, stderr tail)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", "--cpu-seconds", str(seconds)],
                        capture_output=True, text=True, env=env, timeout=seconds * 10 + 120)
     if r.returncode != 0:
-        return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "error": r.stderr[-300:]}
-    res = json.loads(r.stdout.strip().splitlines()[-1])
+        return None, r.stderr[-300:]
+    return json.loads(r.stdout.strip().splitlines()[-1]), None
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """Run the oracle sample in a fresh single-threaded process (BLAS pinned to 1 thread)."""
+    res, err = oracle_sample_process(seconds, 1)
+    if res is None:
+        return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "error": err}
     return {"value": res["value"], "unit": "steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{res['steps']} consecutive steps of the same workload from t=0 "
                       f"(HT + CP routes) in {res['seconds']:.1f} s, FP64 numpy, 1 thread"}
@@ -851,24 +859,29 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     per = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    cores = os.cpu_count() or 1     # every sample may use all host cores (BLAS threads set so)
     for _ in range(args.warmup):
-        oracle_sample(per / 4)
-    vals = []
+        _, err = oracle_sample_process(per / 4, cores)
+        if err is not None:
+            raise RuntimeError(f"oracle sample failed: {err}")
     total_steps, total_s = 0, 0.0
     for _ in range(args.steps):
-        r = oracle_sample(per)
-        vals.append(r["value"])
+        r, err = oracle_sample_process(per, cores)
+        if err is not None:
+            raise RuntimeError(f"oracle sample failed: {err}")
         total_steps += r["steps"]
         total_s += r["seconds"]
     v = total_steps / total_s
-    out = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": 0, "steps": args.steps,
+    out = {"metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 6-D advection, n=64)",
            "impl": "reference",
-           "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)"},
-           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"{args.steps} samples of up to {per:.1f} s, each from t=0, "
-                                      f"FP64 numpy oracle ({total_steps} steps)"},
+           "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)",
+                      "device": "host cores (the oracle; no GPU used)"},
+           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{args.steps} samples of up to {per:.1f} s, each from t=0 in a fresh "
+                                      f"process with {cores} BLAS threads, FP64 numpy oracle "
+                                      f"({total_steps} steps)"},
            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
