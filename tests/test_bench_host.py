@@ -63,3 +63,30 @@ def test_reference_arm_only_rank0_works(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(argparse.Namespace(steps=1, warmup=0))
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_sample_process_runs_with_the_thread_count_set():
+    sys.path.insert(0, ROOT)
+    import bench
+    res, err = bench.oracle_sample_process(0.3, 1)
+    assert err is None and res["steps"] >= 1 and res["value"] > 0
+
+
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import argparse
+    import json
+
+    import bench
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.setattr(bench, "oracle_sample_process",
+                        lambda seconds, threads: ({"steps": 10, "seconds": 2.0, "value": 5.0}, None))
+    bench.run_reference(argparse.Namespace(steps=3, warmup=1, gpus=1))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] == 5.0 and line["unit"] == "steps/s"
+    assert line["n_gpus"] == 1 and line["steps"] == 3 and line["warmup"] == 1 and line["higher_is_better"]
+    assert line["metric"] == bench.METRIC and line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == 5.0 and cb["cores"] >= 1 and "sample" in cb
+    assert line["e2e"] == {"value": 5.0, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
