@@ -77,3 +77,24 @@ def test_pad_keeps_tensor_when_padding_zero():
     p = C.pad(x, 5, [np.zeros((n, 3))] * d)
     assert p.rank == 5
     assert np.abs(C.to_full(p) - C.to_full(x)).max() < 1e-12 * np.abs(C.to_full(x)).max()
+
+
+def test_singular_gram_takes_the_shift_and_keeps_the_fit():
+    """An initial guess with an all-zero column makes every Gamma_k exactly singular, so the
+    Cholesky factorisation fails and the shift by 1e-14 tr(Gamma_k)/r (Section 2.1: ill-conditioned
+    ALS systems are regularised, here only on failure) is taken.  The zero column then stays zero
+    (its right-hand side vanishes) and the fit equals the rank-3 fit without it to rounding."""
+    rng = np.random.default_rng(3)
+    d, n = 3, 6
+    y = C.CP(rng.uniform(0.5, 1.5, 5), [rng.standard_normal((n, 5)) for _ in range(d)])
+    base = [rng.standard_normal((n, 3)) for _ in range(d)]
+    x_zero = C.CP(np.ones(4), [np.hstack([b, np.zeros((n, 1))]) for b in base])
+    G = np.ones((4, 4))
+    for j in range(1, d):
+        G *= x_zero.factors[j].T @ x_zero.factors[j]
+    with pytest.raises(np.linalg.LinAlgError):
+        np.linalg.cholesky(G)
+    a, _ = C.als_sweeps(y, C.CP(np.ones(3), [b.copy() for b in base]), 4)
+    b, _ = C.als_sweeps(y, x_zero, 4)
+    assert b.weights[3] == 0.0
+    assert np.linalg.norm(C.to_full(a) - C.to_full(b)) <= 1e-12 * np.linalg.norm(C.to_full(a))
