@@ -34,7 +34,9 @@ from .cp import CP
 
 
 def cn_terms(alphas: list, factors: list, dt: float, d: int):
-    """(eta, zeta, E): E[e][k] the 1-D factor of term e on dimension k (None = identity)."""
+    """(eta, zeta, E): E[e][k] the 1-D factor of term e on dimension k (None = identity).
+    A = I - dt/2 L and B = I + dt/2 L as separable sums with the identity as term 0
+    (Section 3.3, eqs. CNFDE and BLs)."""
     eta = [1.0] + [-0.5 * dt * a for a in alphas]
     zeta = [1.0] + [0.5 * dt * a for a in alphas]
     E = [[None] * d] + [list(f) for f in factors]
@@ -42,11 +44,13 @@ def cn_terms(alphas: list, factors: list, dt: float, d: int):
 
 
 def _ap(F, X):
+    """F X for a 1-D factor F of eq. BLs (None = the identity), Section 3.3."""
     return X if F is None else F @ X
 
 
 def mode_system(X: list, xn: CP, eta, zeta, E, q: int):
-    """M ((n r) x (n r)) and R (n x r) of the normal equations of dimension q."""
+    """M ((n r) x (n r)) and R (n x r) of the normal equations of dimension q (Section 3.3,
+    eqs. ALS2, ML, MR, with eq:77's integrals as grid products)."""
     d = len(X)
     n, r = X[q].shape
     T = len(eta)
@@ -72,6 +76,8 @@ def mode_system(X: list, xn: CP, eta, zeta, E, q: int):
 
 
 def mode_solve(X: list, xn: CP, eta, zeta, E, q: int) -> np.ndarray:
+    """The new factor of dimension q: M vec(V) = vec(R) of eq. ALS2 solved by Cholesky
+    (Section 3.3)."""
     M, R = mode_system(X, xn, eta, zeta, E, q)
     n, r = X[q].shape
     Lc = np.linalg.cholesky(M)
@@ -111,7 +117,8 @@ def cn_als_step(xn: CP, x0: CP, alphas: list, factors: list, dt: float, sweeps: 
 
 
 def cn_residual(x: CP, xn: CP, alphas: list, factors: list, dt: float) -> float:
-    """|A x - B x_n| on the full grid (small grids only)."""
+    """|A x - B x_n| on the full grid (small grids only): the functional the ALS step of
+    Section 3.3 minimises (eqs. CNFDE, BLs)."""
     from .cp import to_full
     d = x.d
     eta, zeta, E = cn_terms(alphas, factors, dt, d)

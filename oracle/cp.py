@@ -32,6 +32,7 @@ import numpy as np
 
 @dataclass
 class CP:
+    """sum_l weights[l] prod_k factors[k][:, l] (Section 2.1, eq. functional-SSE)."""
     weights: np.ndarray        # (r,)
     factors: list              # d arrays n_k x r
 
@@ -48,6 +49,7 @@ class CP:
 
 
 def to_full(x: CP) -> np.ndarray:
+    """The grid values of eq. functional-SSE, term by term (small grids only)."""
     shape = tuple(f.shape[0] for f in x.factors)
     out = np.zeros(shape)
     for l in range(x.rank):
@@ -59,7 +61,8 @@ def to_full(x: CP) -> np.ndarray:
 
 
 def normalize(x: CP) -> CP:
-    """Unit factor columns, norms collected in the weights."""
+    """Unit factor columns, norms collected in the weights (the lambda_l of eq.
+    functional-SSE, Section 2.1)."""
     w = x.weights.copy()
     fs = []
     for f in x.factors:
@@ -94,7 +97,8 @@ def apply_kron_sum_rk2(x: CP, A: list) -> CP:
 
 
 def _mode_solve(y: CP, x_factors: list, k: int):
-    """Unnormalised minimiser X_k of |y - sum_l prod_j X_j[:, l]| (others fixed)."""
+    """Unnormalised minimiser X_k of |y - sum_l prod_j X_j[:, l]| (others fixed): the
+    normal equations of eqs. SSYSTEM and A^{ln}_{jhp} on the grid basis (Section 2.1)."""
     d = len(x_factors)
     r = x_factors[0].shape[1]
     Gam = np.ones((r, r))
@@ -115,7 +119,8 @@ def _mode_solve(y: CP, x_factors: list, k: int):
 
 
 def als_sweeps(y: CP, x0: CP, sweeps: int, variant: str = "gs"):
-    """ALS rank reduction of y starting from x0.  Returns (x, eps_conv per sweep).
+    """ALS rank reduction of y starting from x0 (Section 2.1, eq. als; Gauss-Seidel order of
+    Section 3.1; damped Jacobi of Appendix B, Algorithm 1).  Returns (x, eps_conv per sweep).
 
     Gauss-Seidel ('gs'): for k = 1..d, normalise the other factors, solve the mode-k
     normal equations, then split the solution into unit columns and weights.
@@ -153,7 +158,8 @@ def als_sweeps(y: CP, x0: CP, sweeps: int, variant: str = "gs"):
 
 
 def pad(x: CP, r_target: int, padding: list) -> CP:
-    """Append r_target - r columns (given seeded arrays, weight 1) to every factor."""
+    """Append r_target - r columns (given seeded arrays, weight 1) to every factor: the
+    initialisation the ALS rank reduction needs at every step (Section 4.1)."""
     r = x.rank
     if r >= r_target:
         return x.copy()
@@ -164,7 +170,7 @@ def pad(x: CP, r_target: int, padding: list) -> CP:
 
 
 def residual(y: CP, x: CP) -> float:
-    """|y - x| via factor Grams (no full grid)."""
+    """|y - x| via factor Grams (no full grid): the error the ALS of Section 2.1 minimises."""
     def gram(a: CP, b: CP):
         G = np.outer(a.weights, b.weights)
         for fa, fb in zip(a.factors, b.factors):

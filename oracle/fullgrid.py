@@ -18,10 +18,12 @@ import numpy as np
 
 
 def central_diff(u: np.ndarray, axis: int, h: float) -> np.ndarray:
+    """(u_{j+1} - u_{j-1}) / (2h) along `axis`, periodic (the FD reading of eq. PDE0)."""
     return (np.roll(u, -1, axis=axis) - np.roll(u, 1, axis=axis)) / (2.0 * h)
 
 
 def apply_L(u: np.ndarray, c, h) -> np.ndarray:
+    """L u = -sum_i c_i D_i u, the constant-coefficient case of eq. PDE-advR (Section 4.1)."""
     out = np.zeros_like(u)
     for i in range(u.ndim):
         hi = h[i] if np.ndim(h) else h
@@ -30,11 +32,14 @@ def apply_L(u: np.ndarray, c, h) -> np.ndarray:
 
 
 def rk2_step(u: np.ndarray, c, h, dt: float) -> np.ndarray:
+    """u + dt L u + dt^2/2 L(L u): a two-stage second-order explicit step of u' = L u
+    (Section 3.2)."""
     Lu = apply_L(u, c, h)
     return u + dt * Lu + 0.5 * dt * dt * apply_L(Lu, c, h)
 
 
 def rk2_steps(u: np.ndarray, c, h, dt: float, steps: int) -> np.ndarray:
+    """`steps` repetitions of rk2_step (Section 3.2)."""
     for _ in range(steps):
         u = rk2_step(u, c, h, dt)
     return u

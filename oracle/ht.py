@@ -40,6 +40,7 @@ from .tree import Tree, build_tree
 
 @dataclass
 class HT:
+    """Nodes of an HT tensor on a dimension tree (Section 2.2, eqs. HTD / coreT)."""
     tree: Tree
     n: list
     node: dict = field(default_factory=dict)   # t -> ndarray
@@ -101,11 +102,13 @@ def node_basis(ht: HT, t: int) -> np.ndarray:
 
 
 def to_full(ht: HT) -> np.ndarray:
+    """The grid values: the root basis of eq. HTD reshaped to the grid (small grids only)."""
     return node_basis(ht, 0).reshape(tuple(ht.n), order="F")
 
 
 def matricize(full: np.ndarray, dims: list) -> np.ndarray:
-    """Node matricisation: rows = dims (first fastest), columns = the rest."""
+    """Node matricisation: rows = dims (first fastest), columns = the rest (the t-unfolding
+    whose singular values the HSVD of Section 2.2 takes)."""
     rest = [i for i in range(full.ndim) if i not in dims]
     nr = int(np.prod([full.shape[i] for i in dims]))
     return full.transpose(dims + rest).reshape(nr, -1, order="F")
@@ -115,7 +118,8 @@ def matricize(full: np.ndarray, dims: list) -> np.ndarray:
 # 1-D operators
 # ---------------------------------------------------------------------------
 def central_diff_matrix(n: int, h: float) -> np.ndarray:
-    """(D u)_j = (u_{j+1} - u_{j-1}) / (2h), periodic."""
+    """(D u)_j = (u_{j+1} - u_{j-1}) / (2h), periodic: the 1-D derivative factor of eq. Lz
+    on the grid."""
     D = np.zeros((n, n))
     for j in range(n):
         D[j, (j + 1) % n] += 1.0 / (2.0 * h)
@@ -178,7 +182,7 @@ def apply_kron_sum_poly(ht: HT, A: list, coeffs) -> HT:
 
 def apply_kron_sum_rk2(ht: HT, A: list) -> HT:
     """v = p(S) u with p(z) = 1 + z + z^2/2 (every two-stage order-2 Runge-Kutta method on a
-    linear ODE): apply_kron_sum_poly with coefficients (1, 1, 1/2), rank 3k."""
+    linear ODE, Section 3.2): apply_kron_sum_poly with coefficients (1, 1, 1/2), rank 3k."""
     return apply_kron_sum_poly(ht, A, _POLY)
 
 
@@ -239,7 +243,8 @@ def add(a: float, u: HT, b: float, w: HT) -> HT:
 # mode products on transfer tensors
 # ---------------------------------------------------------------------------
 def mode_mult(B: np.ndarray, M: np.ndarray, mode: int) -> np.ndarray:
-    """B x_mode M: contracts axis `mode` of B with the columns of M (new = M @ old)."""
+    """B x_mode M: contracts axis `mode` of B with the columns of M (new = M @ old); the
+    mode product of the HT toolkit (Section 2.2)."""
     return np.moveaxis(np.tensordot(M, B, axes=(1, mode)), 0, mode)
 
 
@@ -247,7 +252,7 @@ def mode_mult(B: np.ndarray, M: np.ndarray, mode: int) -> np.ndarray:
 # orthogonalisation (bottom-up) and HSVD truncation (root to leaves)
 # ---------------------------------------------------------------------------
 def orthogonalize(ht: HT) -> HT:
-    """Orthonormal node bases for every non-root node.
+    """Orthonormal node bases for every non-root node (orthogonalisation, Section 2.2).
 
     Leaves: U = Q R (QR as a library step).  Interior nodes bottom-up: absorb the
     children's R factors, B <- B x1 R_t1 x2 R_t2, then QR of the (k1 k2) x k
@@ -277,7 +282,8 @@ def orthogonalize(ht: HT) -> HT:
 
 
 def node_svds(orth: HT) -> dict:
-    """Singular values and left singular vectors of every node matricisation.
+    """Singular values and left singular vectors of every node matricisation (the node SVDs
+    of the HSVD, Section 2.2).
 
     For an orthogonalised HT the t-matricisation of u is U_t F_t^... with U_t
     orthonormal, so its left singular pairs are those of the node factor F_t
@@ -309,6 +315,7 @@ def node_svds(orth: HT) -> dict:
 
 @dataclass
 class TruncReport:
+    """What the HSVD truncation (Section 2.2) chose and discarded, per node."""
     ranks: list
     sigma: dict          # t -> singular values of the node matricisation
     discarded: dict      # t -> sqrt(sum of discarded sigma^2)
@@ -382,7 +389,7 @@ def truncate(ht: HT, rel_tol: float, rmax: int):
 # scalar quantities
 # ---------------------------------------------------------------------------
 def _contract_vectors(ht: HT, vecs: list) -> float:
-    """sum over the grid of u * prod_i vecs[i] (leaf contraction up the tree)."""
+    """sum over the grid of u * prod_i vecs[i] (leaf contraction up the tree of eq. HTD)."""
     tr = ht.tree
     val = {}
     for t in sorted(range(tr.n_nodes), key=lambda t: -tr.depth[t]):
@@ -398,12 +405,14 @@ def _contract_vectors(ht: HT, vecs: list) -> float:
 
 
 def mass(ht: HT) -> float:
-    """sum of all grid values (the discrete mass up to the cell volume)."""
+    """sum of all grid values (the discrete mass up to the cell volume; Section 4.2 checks
+    the density moment)."""
     return _contract_vectors(ht, [np.ones(n) for n in ht.n])
 
 
 def inner(u: HT, w: HT) -> float:
-    """<u, w> over the grid via leaf Grams contracted up the tree."""
+    """<u, w> over the grid via leaf Grams contracted up the tree (scalar product of the HT
+    toolkit, Section 2.2)."""
     tr = u.tree
     G = {}
     for t in sorted(range(tr.n_nodes), key=lambda t: -tr.depth[t]):
@@ -419,6 +428,7 @@ def inner(u: HT, w: HT) -> float:
 
 
 def norm(u: HT) -> float:
+    """sqrt(<u, u>) (Section 2.2)."""
     return math.sqrt(max(inner(u, u), 0.0))
 
 
@@ -426,7 +436,8 @@ def norm(u: HT) -> float:
 # explicit steps (Section 3.2: apply, add, rank-reduce)
 # ---------------------------------------------------------------------------
 def step_rk2_poly(u: HT, A: list, rel_tol: float, rmax: int):
-    """One step u <- T(p(dt L) u) for a Kronecker-sum operator (single truncation)."""
+    """One step u <- T(p(dt L) u) for a Kronecker-sum operator (single truncation): apply
+    and rank reduction of Section 3.2."""
     return truncate(apply_kron_sum_rk2(u, A), rel_tol, rmax)
 
 

@@ -27,7 +27,8 @@ import numpy as np
 
 
 def _round_robin(k: int):
-    """Brent-Luk tournament: list of rounds, each a pair of index arrays (p, q)."""
+    """Brent-Luk tournament: list of rounds, each a pair of index arrays (p, q) (the pair order
+    of the node SVDs of the HSVD, Section 2.2)."""
     m = k + (k % 2)
     players = list(range(m))
     rounds = []
@@ -44,7 +45,8 @@ def _round_robin(k: int):
 
 
 def jacobi_svd(A: np.ndarray, tol: float | None = None, max_sweeps: int = 60):
-    """Return (U, s, V) with A = U diag(s) V^T, s descending; A is m x k with m >= k."""
+    """Return (U, s, V) with A = U diag(s) V^T, s descending; A is m x k with m >= k (a node
+    SVD of the HSVD, Section 2.2)."""
     A = np.array(A, dtype=np.float64, copy=True)
     m, k = A.shape
     if tol is None:
@@ -96,7 +98,7 @@ def jacobi_svd(A: np.ndarray, tol: float | None = None, max_sweeps: int = 60):
 
 
 def svd_left(F: np.ndarray):
-    """Left singular vectors and values of a (possibly wide) matrix F (k x m).
+    """Left singular vectors and values of a (possibly wide) matrix F (k x m) (Section 2.2).
 
     F^T = Q R (QR as a library step) reduces the problem to R^T (k x k'), whose SVD
     R^T = U S W^T gives F = U S (Q W)^T.  Returns (U, s) with U k x k (padded with an

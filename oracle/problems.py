@@ -28,12 +28,15 @@ from .ht import central_diff_matrix
 
 
 def advection_A(case) -> list:
+    """dt L_i = -dt c_i D on dimension i: the Kronecker-sum terms of eq. Lz for constant-
+    coefficient advection (Section 4.1)."""
     D = central_diff_matrix(case.n, case.h)
     return [case.dt * (-case.c[i]) * D for i in range(case.d)]
 
 
 def kinetic_terms(kc):
-    """(alphas, factors) of the kinetic operator on (x1,x2,x3,v1,v2,v3); None = identity."""
+    """(alphas, factors) of the kinetic operator on (x1,x2,x3,v1,v2,v3); None = identity
+    (Section 4.2, eq. BGK_LIN; terms of Table tab:ordering)."""
     n = kc.n
     D = central_diff_matrix(n, kc.hx)
     V = np.diag(kc.vgrid())

@@ -16,6 +16,7 @@ from dataclasses import dataclass
 
 @dataclass
 class Tree:
+    """A dimension tree (Section 2.2, eq. HTD): node ranges [lo, hi), children, depths."""
     d: int
     lo: list        # first dimension of each node
     hi: list        # one past the last dimension
@@ -46,6 +47,8 @@ class Tree:
 
 
 def build_tree(d: int, kind: str = "balanced") -> Tree:
+    """The balanced tree of eq. HTD / coreT, or the linear tree of the tensor-train format
+    (Section 2.2), numbered breadth first."""
     if d < 2:
         raise ValueError("HT needs d >= 2")
     if kind not in ("balanced", "linear"):
