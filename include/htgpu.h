@@ -139,7 +139,10 @@ typedef struct ht_config {
   int tree;                /* ht_tree_kind */
 } ht_config;
 
-/* Workspace bytes a context with this configuration allocates (0 on bad config). */
+/* Context management, status codes, the profiler and the tree query below are infrastructure
+ * around the method: no passage of the paper defines them.
+ *
+ * Workspace bytes a context with this configuration allocates (0 on bad config). */
 size_t ht_workspace_bytes(const ht_config* cfg);
 
 /* Create a context: allocates the workspace on cfg->device with cudaMalloc.
@@ -170,9 +173,11 @@ int ht_ctx_profile_read(ht_ctx* ctx, double* ms, long long* launches, double* fl
 /* Human-readable name of a status code. */
 const char* ht_status_string(int status);
 
-/* Node numbering of the balanced tree for d dimensions.  Each output array holds
+/* Node numbering of the dimension tree for d dimensions (Section 2.2, eq. HTD): kind
+ * HT_TREE_BALANCED, or HT_TREE_LINEAR for the tensor-train format.  Each output array holds
  * 2d-1 ints: lo/hi = dimension range [lo, hi), c1/c2 = children (-1 for leaves),
- * parent (-1 for the root), depth.  Returns HT_ERR_ARG for d outside [2, HT_MAXD]. */
+ * parent (-1 for the root), depth.  Returns HT_ERR_ARG for d outside [2, HT_MAXD] or an
+ * unknown kind. */
 int ht_tree_info(int d, int kind, int* lo, int* hi, int* c1, int* c2, int* parent, int* depth);
 
 /* ------------------------------------------------------------- HT calls ----- */
@@ -255,7 +260,9 @@ int ht_step_ab2(ht_ctx* ctx, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, do
  * leaves = factors, interior B = delta_abc, root = diag(weights).  out->cap >= x->rank. */
 int ht_from_cp(ht_ctx* ctx, const cp_tensor* x, ht_tensor* out, void* stream);
 
-/* Scalars: sum of all entries (discrete mass) and <u, w>, written to device doubles. */
+/* Scalars: sum of all entries (discrete mass) and <u, w>, written to device doubles (the
+ * scalar products of the HT toolkit, Section 2.2; the mass is the density moment Section 4.2
+ * checks).  Errors: HT_ERR_ARG, HT_ERR_CAPACITY (tensor capacity above the context's). */
 int ht_mass(ht_ctx* ctx, const ht_tensor* u, double* out_dev, void* stream);
 int ht_inner(ht_ctx* ctx, const ht_tensor* u, const ht_tensor* w, double* out_dev, void* stream);
 
@@ -274,7 +281,8 @@ typedef enum cp_variant {
 int cp_als_sweep(ht_ctx* ctx, const cp_tensor* y, cp_tensor* x, int sweeps, int variant,
                  double* eps_dev, void* stream);
 
-/* y = p(dt L) x exactly in CP form for a kron_sum operator: 1 + 2d + d(d-1)/2 rank-1
+/* y = p(dt L) x exactly in CP form for a kron_sum operator (the separable operator of eq. Lz
+ * applied in CP format, the explicit step of Section 3.2): 1 + 2d + d(d-1)/2 rank-1
  * terms per term of x (identity, dt A_i, dt^2 A_i^2 / 2, dt^2 A_i A_j for i < j).
  * y->cap >= x->rank * (1 + 2d + d(d-1)/2).  Sets y->rank on the host. */
 int cp_apply_rk2(ht_ctx* ctx, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y,
@@ -291,8 +299,9 @@ int cp_als_sweep_rk2(ht_ctx* ctx, const cp_tensor* x_old, const ht_op* L, double
                      int sweeps, int variant, double* eps_dev, void* stream);
 
 /* ----------------------------------------------------- allocation-free ---- */
-/* cp_als_sweep for callers that cannot allocate device memory (no ht_ctx needed).
- * The paper has no counterpart: this is a deployment variant of cp_als_sweep.
+/* cp_als_sweep (the ALS of Section 2.1, eqs. SSYSTEM, A^{ln}_{jhp}) for callers that cannot
+ * allocate device memory (no ht_ctx needed).  The paper has no counterpart for the memory
+ * discipline: this is a deployment variant of cp_als_sweep.
  * Who needs it: code running where cudaMalloc is unavailable or forbidden -- inside
  * host callbacks or plug-ins with a fixed memory budget, or processes whose device
  * memory is reserved up front by another framework.
