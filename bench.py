@@ -91,6 +91,26 @@ def oracle_sample(seconds: float) -> dict:
     return {"steps": steps, "seconds": el, "value": steps / el}
 
 
+def host_cpu() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer / part ids on
+    Arm), with the machine type and core count; "unknown" parts where it says nothing."""
+    import platform
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k and v and k not in fields:
+                    fields[k] = v
+    except OSError:
+        pass
+    name = fields.get("model name") or fields.get("Model") or ""
+    if not name and "CPU implementer" in fields:
+        name = f"implementer {fields['CPU implementer']} part {fields.get('CPU part', '?')}"
+    return f"{name or 'unknown'} ({platform.machine() or 'unknown'}, {os.cpu_count()} cores)"
+
+
 def oracle_sample_process(seconds: float, threads: int):
     """One oracle sample in a fresh process with its BLAS / OpenMP threads set to `threads`
     (the count the sample may use); (result dict, None) or (None, stderr tail)."""
@@ -109,7 +129,7 @@ def cpu_baseline(seconds: float) -> dict:
     res, err = oracle_sample_process(seconds, 1)
     if res is None:
         return {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle", "error": err}
-    return {"value": res["value"], "unit": "steps/s", "cores": 1, "kind": "oracle",
+    return {"value": res["value"], "unit": "steps/s", "cores": 1, "kind": "oracle", "cpu": host_cpu(),
             "sample": f"{res['steps']} consecutive steps of the same workload from t=0 "
                       f"(HT + CP routes) in {res['seconds']:.1f} s, FP64 numpy, 1 thread"}
 
@@ -878,7 +898,7 @@ def run_reference(args):
            "impl": "reference",
            "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)",
                       "device": "host cores (the oracle; no GPU used)"},
-           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                             "sample": f"{args.steps} samples of up to {per:.1f} s, each from t=0 in a fresh "
                                       f"process with {cores} BLAS threads, FP64 numpy oracle "
                                       f"({total_steps} steps)"},

@@ -89,4 +89,5 @@ def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
     assert line["metric"] == bench.METRIC and line["config"]["workload"] == bench.WORKLOAD
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == 5.0 and cb["cores"] >= 1 and "sample" in cb
+    assert isinstance(cb["cpu"], str) and "cores" in cb["cpu"]
     assert line["e2e"] == {"value": 5.0, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
