@@ -10,11 +10,25 @@ term with rho = sum_v h_v^3 f), and one untruncated HEUN2 step is p(dt L_K) g wi
 p(z) = 1 + z + z^2/2 on each mode.  Nothing here uses the oracle's kinetic term list, so a wrong
 sign, a transport factor on the wrong dimension or a lost term in it fails the comparison.
 """
+import functools
+
 import numpy as np
 
 from oracle import ht as OH
 from oracle.problems import kinetic_terms
 from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+
+
+@functools.lru_cache(maxsize=1)
+def full_size_step():
+    """(case, CP weights, CP factors, u0, u1): one untruncated HEUN2 step of the oracle at the
+    kinetic workload's full size (n = 64, dt the explicit step), shared by the tests below."""
+    kc = kinetic_case(64)
+    w, F = kinetic_ic(kc)
+    alphas, factors = kinetic_terms(kc)
+    u0 = OH.from_cp(w, F)
+    u1, _ = OH.step_heun2(u0, alphas, factors, kc.dt, 0.0, 10 ** 6)
+    return kc, w, F, u0, u1
 
 
 def mode_closed_form_step(kc, w, F, dt, kmax=2):
@@ -96,11 +110,8 @@ def test_full_size_heun2_step_matches_mode_closed_form_on_samples():
     one untruncated HEUN2 step of the oracle (node ranks up to 222), the x-Fourier coefficient
     f^(K; v) at sampled x-modes K and v-grid points equals p(dt L_K) applied to the mode's
     v-array, to rounding."""
-    kc = kinetic_case(64)
-    w, F = kinetic_ic(kc)
+    kc, w, F, _, u1 = full_size_step()
     dt = kc.dt
-    alphas, factors = kinetic_terms(kc)
-    u1, _ = OH.step_heun2(OH.from_cp(w, F), alphas, factors, dt, 0.0, 10 ** 6)
     n, hx, hv, nu = kc.n, kc.hx, kc.hv, kc.nu
     x, v, m = kc.xgrid(), kc.vgrid(), kc.maxwellian()
     M = np.einsum("a,b,c->abc", m, m, m)
@@ -125,3 +136,46 @@ def test_full_size_heun2_step_matches_mode_closed_form_on_samples():
             vecs += [np.eye(n)[p[j]] for j in range(3)]
             got = contract(u1, vecs)
             assert abs(got - ref[p]) <= 1e-12 * scale, (K, p)
+
+
+def moment_vectors(kc):
+    """Per dimension the vectors whose product is each moment functional: the x-average of the
+    density, the momentum components and the second moment |v|^2 (Section 4.2, eqs. rho0, u0,
+    T0 unnormalised)."""
+    n, v = kc.n, kc.vgrid()
+    a = np.full(n, kc.hx / (2 * np.pi))
+    b = np.full(n, kc.hv)
+    out = {"rho": [a, a, a, b, b, b]}
+    for d in range(3):
+        vv = [b, b, b]
+        vv[d] = kc.hv * v
+        out[f"p{d}"] = [a, a, a] + vv
+        vv = [b, b, b]
+        vv[d] = kc.hv * v * v
+        out[f"e{d}"] = [a, a, a] + vv
+    return out
+
+
+def moments(u, kc):
+    m = {k: contract(u, vecs).real for k, vecs in moment_vectors(kc).items()}
+    m["e"] = m.pop("e0") + m.pop("e1") + m.pop("e2")
+    return m
+
+
+def test_explicit_steps_relax_the_moments_at_rate_nu():
+    """Exponential relaxation at rate nu (Section 4.2), in the discrete form the explicit step
+    must reproduce: the kinetic operator keeps the density (l L = 0) and relaxes the momentum
+    and E - 3 c2 rho at rate nu (l L = -nu l; c2 = sum_j h v_j^2 m_j), so one untruncated HEUN2
+    step, p(dt L) with p(z) = 1 + z + z^2/2, keeps rho and multiplies those by p(-nu dt), to
+    rounding.  Full size n = 64, moments by contraction on the format."""
+    kc, _, _, u0, u1 = full_size_step()
+    dt = kc.dt
+    g = 1.0 - kc.nu * dt + 0.5 * (kc.nu * dt) ** 2
+    c2 = kc.hv * float(np.sum(kc.vgrid() ** 2 * kc.maxwellian()))
+    m0 = moments(u0, kc)
+    assert max(abs(m0[f"p{d}"]) for d in range(3)) > 1e-4 * m0["rho"]
+    m1 = moments(u1, kc)
+    assert abs(m1["rho"] - m0["rho"]) <= 1e-13 * m0["rho"]
+    for d in range(3):
+        assert abs(m1[f"p{d}"] - g * m0[f"p{d}"]) <= 1e-13 * m0["rho"], d
+    assert abs((m1["e"] - 3 * c2 * m1["rho"]) - g * (m0["e"] - 3 * c2 * m0["rho"])) <= 1e-13 * m0["e"]
