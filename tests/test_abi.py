@@ -129,3 +129,16 @@ def test_every_entry_point_checks_its_arguments_before_the_gpu(lib):
     y, x = cp(6, 16, 4, 4), cp(6, 16, 2, 2)
     x.factor[3] = None
     assert call(y, x) == ARG                                             # missing factor
+
+
+def test_product_path_fails_loudly_without_a_gpu_or_library(lib):
+    """No CPU fallback: without a GPU, creating a context raises the library's HT_ERR_CUDA, and a
+    library that was not built raises instead of substituting anything."""
+    import torch
+    from paper_1803_10270_gb300 import htgpu as G
+    with pytest.raises(RuntimeError, match="not built"):
+        G.load(os.path.join(ROOT, "no_such_dir", "libhtgpu.so"))
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: contexts are created normally")
+    with pytest.raises(G.HTError, match="HT_ERR_CUDA"):
+        G.Context(6, [16] * 6, cap=8, max_terms=1)
