@@ -186,6 +186,61 @@ def test_rank_rule():
     assert H.choose_rank(s, 0.0, 2) == 2
 
 
+def _orthogonal_diagonal(d, n, s, seed):
+    """u = sum_k s_k prod_i Q_i[:, k] with orthonormal Q_i: every node matricisation of u has the
+    singular values s (a diagonal tensor in orthonormal bases)."""
+    rng = np.random.default_rng(seed)
+    Q = [np.linalg.qr(rng.standard_normal((n, len(s))))[0] for _ in range(d)]
+    return H.from_cp(np.asarray(s, dtype=float), Q)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_rank_rule_splits_the_budget_over_2d_minus_3_edges(d):
+    """The rank rule's budget (tol |u|)^2 / (2d - 3): every node of an orthogonally diagonal
+    tensor has the spectrum s = (1, 0.1, 0.01, 0.001), and tol is set inside the window where
+    the tail after two values fits the budget with 2d - 3 edges but not with 2d - 2, so every
+    node keeps exactly two (d = 2 is the matrix case, a single edge)."""
+    s = np.array([1.0, 0.1, 0.01, 0.001])
+    u = _orthogonal_diagonal(d, 6, s, seed=70 + d)
+    e = 2 * d - 3
+    tail2 = float(np.sum(s[2:] ** 2)) / float(np.sum(s ** 2))
+    tol = math.sqrt(tail2 * (e + 0.5))          # tail2 <= tol^2 / e, tail2 > tol^2 / (e + 1)
+    t, rep = H.truncate(u, tol, 10)
+    assert rep.ranks[1:] == [2] * (2 * d - 2)
+    for t_ in range(1, 2 * d - 1):
+        assert np.allclose(rep.sigma[t_][:4], s, rtol=1e-12)
+
+
+def test_root_children_share_one_rank():
+    """The two children of the root share one spectrum, and the rank is chosen once for both:
+    with a 3-point leaf on one side and a rank-5 node on the other, tolerance 0 keeps three
+    directions on both sides (the other side's factor also carries two singular values at the
+    rounding level, which a separate choice at tolerance 0 would keep) and reproduces u."""
+    tree = build_tree(3)
+    c1, c2 = tree.children[0]
+    ns = [3, 6, 6]
+    ranks = {0: 1, c1: 3, c2: 5}
+    for t in range(tree.n_nodes):
+        if t not in ranks:
+            ranks[t] = 3
+    shapes = []
+    for t in range(tree.n_nodes):
+        if tree.is_leaf(t):
+            shapes.append((ns[tree.lo[t]], ranks[t]))
+        else:
+            a, b = tree.children[t]
+            shapes.append((ranks[a], ranks[b]) if t == 0 else (ranks[a], ranks[b], ranks[t]))
+    arrs = normal_arrays(shapes, 71)
+    u = H.HT(tree, ns)
+    for t in range(tree.n_nodes):
+        u.node[t] = arrs[t]
+    assert u.ranks()[c1] == 3 and u.ranks()[c2] == 5
+    t, rep = H.truncate(u, 0.0, 10)
+    assert rep.ranks[c1] == rep.ranks[c2] == 3
+    full = H.to_full(u)
+    assert np.abs(H.to_full(t) - full).max() <= 1e-12 * np.abs(full).max()
+
+
 def test_kinetic_operator_dense_and_conservation():
     from oracle.problems import kinetic_terms
     from paper_1803_10270_gb300.inputs import kinetic_case
