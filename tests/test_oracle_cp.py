@@ -98,3 +98,32 @@ def test_singular_gram_takes_the_shift_and_keeps_the_fit():
     b, _ = C.als_sweeps(y, x_zero, 4)
     assert b.weights[3] == 0.0
     assert np.linalg.norm(C.to_full(a) - C.to_full(b)) <= 1e-12 * np.linalg.norm(C.to_full(a))
+
+
+def test_damped_jacobi_sweep_is_a_quarter_step_from_one_iterate():
+    """The parallel variant (Appendix B, Algorithm 1): every mode's minimiser V_k is taken from
+    the same iterate (weights folded into the first factor) and each factor moves a quarter of
+    the way, X_k <- X_k + (V_k - X_k) / 4; Algorithm 5's measure is max_k |V_k - X_k| / |X_k|.
+    V_k by brute-force least squares on the unfolded full grid."""
+    d, n, r = 3, 4, 2
+    rng = np.random.default_rng(4)
+    y = C.CP(rng.uniform(0.5, 1.5, 5), [rng.standard_normal((n, 5)) for _ in range(d)])
+    x0 = C.CP(rng.uniform(0.5, 1.5, r), [rng.standard_normal((n, r)) for _ in range(d)])
+    # the iterate: unit columns for k >= 1, every norm and weight folded into the first factor
+    norms = [np.linalg.norm(f, axis=0) for f in x0.factors]
+    it = [x0.factors[0] * (x0.weights * np.prod(norms[1:], axis=0))[None, :]]
+    it += [x0.factors[k] / norms[k][None, :] for k in range(1, d)]
+    Yfull = C.to_full(y)
+    V = []
+    for k in range(d):
+        Z = np.ones((1, r))
+        for j in (j for j in range(d) if j != k):
+            Z = np.einsum("al,bl->abl", Z, it[j]).reshape(-1, r)
+        sol, *_ = np.linalg.lstsq(Z, np.moveaxis(Yfull, k, 0).reshape(n, -1).T, rcond=None)
+        V.append(sol.T)
+    want = [it[k] + (V[k] - it[k]) / 4.0 for k in range(d)]
+    x1, eps = C.als_sweeps(y, x0, 1, variant="jacobi_damped")
+    ref = C.to_full(C.CP(np.ones(r), want))
+    assert np.linalg.norm(C.to_full(x1) - ref) <= 1e-12 * np.linalg.norm(ref)
+    e_want = max(np.linalg.norm(V[k] - it[k]) / np.linalg.norm(it[k]) for k in range(d))
+    assert abs(eps[0] - e_want) <= 1e-10 * e_want
