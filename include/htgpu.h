@@ -299,9 +299,8 @@ int cp_als_sweep_rk2(ht_ctx* ctx, const cp_tensor* x_old, const ht_op* L, double
                      int sweeps, int variant, double* eps_dev, void* stream);
 
 /* ----------------------------------------------------- allocation-free ---- */
-/* cp_als_sweep (the ALS of Section 2.1, eqs. SSYSTEM, A^{ln}_{jhp}) for callers that cannot
- * allocate device memory (no ht_ctx needed).  The paper has no counterpart for the memory
- * discipline: this is a deployment variant of cp_als_sweep.
+/* The paper has no counterpart: this is a deployment variant of cp_als_sweep (same arguments
+ * and results; see its declaration above) that allocates nothing and needs no ht_ctx.
  * Who needs it: code running where cudaMalloc is unavailable or forbidden -- inside
  * host callbacks or plug-ins with a fixed memory budget, or processes whose device
  * memory is reserved up front by another framework.
@@ -318,12 +317,6 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
                          int* status_dev, void* stream);
 
 /* ------------------------------------------------------------ diagnostics -- */
-/* Self-test of the bounded grid barrier that the persistent ALS kernel (cp_als_sweep_rk2) uses
- * between its phases.  The paper has no counterpart.  Launches nblocks (1..64) cooperative CTAs
- * on `device` that meet at one barrier; CTA `absent` (or none when absent < 0) skips it, so the
- * others wait out the bounded limit (about 0.2 s of SM clock) and report instead of hanging.
- * Synchronising (allocates and frees its own 2 KB).  Returns HT_OK when every CTA passed, the
- * device-reported HT_ERR_TIMEOUT when the barrier gave up, or HT_ERR_ARG / HT_ERR_CUDA. */
 /* One Crank-Nicolson step solved in CP format by alternating least squares (Section 3.3, eqs.
  * CNFDE, BLs, rRr1, ALS2, ML, MR): x minimises |A x - B x_n| with A = I - dt/2 L and
  * B = I + dt/2 L, over the factors of x at its current rank, Gauss-Seidel over the dimensions,
@@ -344,7 +337,20 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
 int cp_cn_als_step(ht_ctx* ctx, const cp_tensor* x_n, const ht_op* L, double dt, cp_tensor* x, int sweeps,
                    int variant, double* eps_dev, void* stream);
 
+/* Self-test of the bounded grid barrier that the persistent ALS kernel (cp_als_sweep_rk2) uses
+ * between its phases.  The paper has no counterpart.  Launches nblocks (1..64) cooperative CTAs
+ * on `device` that meet at one barrier; CTA `absent` (or none when absent < 0) skips it, so the
+ * others wait out the bounded limit (about 0.2 s of SM clock) and report instead of hanging.
+ * Synchronising (allocates and frees its own 2 KB).  Returns HT_OK when every CTA passed, the
+ * device-reported HT_ERR_TIMEOUT when the barrier gave up, or HT_ERR_ARG / HT_ERR_CUDA. */
 int ht_selftest_grid_barrier(int nblocks, int absent, int device);
+
+/* Self-test of the library's FP64 reciprocal and reciprocal square root (an FP32 seed refined
+ * by the truncated series 1/(1-e) = 1 + e + e^2 and (1-e)^-1/2 = 1 + e/2 + 3e^2/8; used by the
+ * QR, SVD and ALS kernels).  The paper has no counterpart.  For each of the n device doubles
+ * x_dev[i] writes out_dev[4i .. 4i+3] = (library reciprocal, CUDA 1.0 / x, library rsqrt, CUDA
+ * rsqrt) (device, 4n doubles).  Asynchronous on stream.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+int ht_selftest_fastmath(const double* x_dev, double* out_dev, int n, void* stream);
 
 #ifdef __cplusplus
 }

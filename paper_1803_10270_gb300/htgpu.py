@@ -92,6 +92,7 @@ _EXPORTS = {
     "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
+    "ht_selftest_fastmath": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "cp_cn_als_step": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
                                  C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
@@ -540,6 +541,16 @@ def cp_als_sweep_noalloc(y: CPTensor, x: CPTensor, sweeps: int, variant: int = C
                                        C.c_void_p(eps.data_ptr() if eps is not None else 0),
                                        C.c_void_p(status.data_ptr() if status is not None else 0),
                                        _stream_ptr(stream)), "cp_als_sweep_noalloc")
+
+
+def selftest_fastmath(x, stream=None):
+    """(n, 4) tensor: library reciprocal, CUDA 1.0 / x, library rsqrt, CUDA rsqrt of x (device
+    FP64 tensor)."""
+    import torch
+    out = torch.empty((x.numel(), 4), dtype=torch.float64, device=x.device)
+    _check(load().ht_selftest_fastmath(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(),
+                                       _stream_ptr(stream)), "ht_selftest_fastmath")
+    return out
 
 
 def selftest_grid_barrier(nblocks: int, absent: int = -1, device: int = 0) -> int:

@@ -74,8 +74,39 @@ def test_als_sweeps_match_oracle(G, variant):
     np.testing.assert_allclose(e.cpu().numpy(), eps, rtol=1e-6, atol=1e-14)
 
 
+def _entries(x: OC.CP, idx: np.ndarray) -> np.ndarray:
+    """Grid values x(i_1, ..., i_d) at the rows of idx (eq. functional-SSE, term by term)."""
+    P = np.ones((idx.shape[0], x.rank)) * x.weights[None, :]
+    for k in range(x.d):
+        P = P * x.factors[k][idx[:, k], :]
+    return P.sum(1)
+
+
+def _sample_idx(d, n, count=4000, seed=5):
+    return np.random.default_rng(seed).integers(0, n, size=(count, d))
+
+
+def _one_step_conditioning(x, A, pad, r, sweeps, idx):
+    """Largest relative change of the sampled values of one oracle step when x is perturbed by
+    1e-15 relative (three seeded trials): the amplification any two FP64 evaluations of the
+    same step share.  The ALS of Section 2.1 with more columns than the target needs has
+    near-degenerate steps where this reaches 1e-10 and above."""
+    ref, _ = OC.step_rk2(x, A, r, pad, sweeps)
+    er = _entries(ref, idx)
+    worst = 0.0
+    for trial in range(3):
+        g = np.random.default_rng(100 + trial)
+        xp = OC.CP(x.weights * (1 + 1e-15 * g.standard_normal(x.rank)),
+                   [f * (1 + 1e-15 * g.standard_normal(f.shape)) for f in x.factors])
+        b, _ = OC.step_rk2(xp, A, r, pad, sweeps)
+        worst = max(worst, np.abs(_entries(b, idx) - er).max() / np.abs(er).max())
+    return ref, worst
+
+
 def test_cp_step_adv6d_n64_shape(G):
-    """n=64, d=6: y = p(dt L) x (rank 2*28), ALS to rank 24 from the padded iterate, 5 sweeps."""
+    """n=64, d=6: y = p(dt L) x formed explicitly (rank 2*28) by cp_apply_rk2, ALS to rank 24 from
+    the padded iterate, 5 sweeps with cp_als_sweep: sampled grid values against the oracle's
+    step at 1e-10 (a 1e-15 perturbation of this step's input moves them by about 3e-12)."""
     d, n = 6, 64
     case = advection_case(d, n, seed_offset=1)
     A = advection_A(case)
@@ -92,16 +123,50 @@ def test_cp_step_adv6d_n64_shape(G):
     G.cp_apply_rk2(ctx, X2, G.advection_op(case.c, case.h), case.dt, Y)
     G.cp_als_sweep(ctx, Y, X, 5)
     sync()
-    w, f = X.download()
-    # compare through factor Grams (the 64^6 grid is too large to form)
-    def gram(a, b):
-        g = np.outer(a.weights, b.weights)
-        for fa, fb in zip(a.factors, b.factors):
-            g = g * (fa.T @ fb)
-        return g.sum()
-    got = OC.CP(w, f)
-    num = gram(got, got) - 2 * gram(got, ref) + gram(ref, ref)
-    assert num <= (1e-7 * np.sqrt(gram(ref, ref))) ** 2   # Gram identity resolves ~1e-8 relative
+    ctx.check()
+    got = OC.CP(*X.download())
+    idx = _sample_idx(d, n)
+    er = _entries(ref, idx)
+    assert np.abs(_entries(got, idx) - er).max() <= 1e-10 * np.abs(er).max()
+
+
+def test_structured_rk2_als_bench_configuration(G):
+    """cp_als_sweep_rk2 in the launch configuration the benchmark times (d=6, n=64, rank 24, 5
+    Gauss-Seidel sweeps; one CTA per factor column): the padded first step (x_old = the rank-2
+    initial condition) and then steps 2..5 each taken from the oracle's own state (x_old aliasing
+    x, the benchmark's steady-state call).  Several chained ALS steps cannot be compared: from
+    the third step on a 1e-15 perturbation grows to 1e-5 (the fit's weights reach 1e7 and
+    cancel), so every FP64 evaluation order gives a different trajectory.  Each step is
+    compared on 4000 sampled grid values at 1e-10 relative, or at 100 times the step's
+    measured conditioning (see _one_step_conditioning) where that is larger."""
+    d, n, r, sweeps = 6, 64, 24, 5
+    case = advection_case(d, n, seed_offset=1)
+    A = advection_A(case)
+    op = G.advection_op(case.c, case.h)
+    pad = cp_padding([n] * d, r - 2, seed=0x5EED + 1, scale=1e-3)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    idx = _sample_idx(d, n)
+    x = OC.CP(np.ones(2), case.ic_factors())
+    X = G.CPTensor(d, [n] * d, r)
+    for step in range(5):
+        ref, cond = _one_step_conditioning(x, A, pad, r, sweeps, idx)
+        if step == 0:
+            xi = OC.pad(x, r, pad)
+            X.upload(xi.weights, xi.factors)
+            X2 = G.CPTensor(d, [n] * d, 2)
+            X2.upload(x.weights, x.factors)
+            G.cp_als_sweep_rk2(ctx, X2, op, case.dt, X, sweeps)
+        else:
+            X.upload(x.weights, x.factors)
+            G.cp_als_sweep_rk2(ctx, X, op, case.dt, X, sweeps)
+        sync()
+        ctx.check()
+        got = OC.CP(*X.download())
+        er = _entries(ref, idx)
+        tol = max(1e-10, 100 * cond)
+        err = np.abs(_entries(got, idx) - er).max() / np.abs(er).max()
+        assert err <= tol, f"step {step + 1}: {err:.3e} > {tol:.3e} (conditioning {cond:.2e})"
+        x = ref
 
 
 @pytest.mark.parametrize("variant", ["gs", "jacobi_damped"])

@@ -206,14 +206,18 @@ def test_truncate_tall_node_matrices_rank_deficient(G):
         assert rel_err(from_gpu(out, tree), ref) < TOL64, f"tol {rel_tol}"
 
 
-@pytest.mark.parametrize("n,r,decay,deficient", [(150, 131, 0.85, True), (144, 140, 0.8, False)])
-def test_truncate_wide_node_factors(G, n, r, decay, deficient):
-    """ht_truncate of d=4 HT tensors of rank 131 (odd: a dummy player in every Jacobi round) and
-    140: every node factor is 131 / 140 columns wide, so the node SVDs run in the cluster form
-    (columns spread over the shared memory of one thread-block cluster).  Graded transfer tensors
-    make the root's children cut to ranks near 40 at tol 1e-8; the other nodes keep every
-    direction.  The deficient case duplicates a leaf column and zeroes a transfer slice (zero
-    singular values in the wide factors).  Ranks and T(u) against the oracle."""
+@pytest.mark.parametrize("n,r,decay,deficient,ctx_cap",
+                         [(150, 131, 0.85, True, 131), (144, 140, 0.8, False, 140), (380, 370, 0.95, False, 124)])
+def test_truncate_wide_node_factors(G, n, r, decay, deficient, ctx_cap):
+    """ht_truncate of d=4 HT tensors of rank 131 (odd: a dummy player in every Jacobi round), 140
+    and 370: every node factor is that many columns wide, so the node SVDs run in the cluster form
+    (columns spread over the shared memory of one thread-block cluster; 370 columns come near its
+    480-column limit, the width of the kinetic workload's node factors).  Graded transfer tensors
+    make the root's children cut to ranks near 40 (132 at rank 370) at tol 1e-8; the other nodes
+    keep every direction.  The deficient case duplicates a leaf column and zeroes a transfer
+    slice (zero singular values in the wide factors).  The rank-370 input fits a context of
+    capacity 124 (truncation inputs up to 3 x 124 = 372).  Ranks and T(u) against the oracle
+    (about 100 s of oracle time at rank 370)."""
     d = 4
     u = random_ht(d, n, r, seed=21, scale_decay=decay)
     if deficient:
@@ -224,7 +228,7 @@ def test_truncate_wide_node_factors(G, n, r, decay, deficient):
         u.node[inner][:, :, 7] = 0.0
     ref, rep = OH.truncate(u, 1e-8, r)
     assert max(rep.ranks[1:]) == r and min(rep.ranks[1:]) < r
-    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    ctx = G.Context(d, [n] * d, cap=ctx_cap, max_terms=1)
     g = to_gpu(G, u, r)
     out = G.HTTensor(d, [n] * d, r)
     G.ht_truncate(ctx, g, 1e-8, r, out)

@@ -127,3 +127,27 @@ def test_damped_jacobi_sweep_is_a_quarter_step_from_one_iterate():
     assert np.linalg.norm(C.to_full(x1) - ref) <= 1e-12 * np.linalg.norm(ref)
     e_want = max(np.linalg.norm(V[k] - it[k]) / np.linalg.norm(it[k]) for k in range(d))
     assert abs(eps[0] - e_want) <= 1e-10 * e_want
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_residual_equals_full_grid_norm(seed):
+    """residual(y, x) (factor Grams, no grid) against |to_full(y) - to_full(x)|_F formed on the
+    grid: the error that the ALS of Section 2.1 minimises.  Cases: a generic pair, a fit close
+    to its target (cancellation in the Gram identity) and the exact fit (residual 0)."""
+    d, n = 4, 5
+    rng = np.random.default_rng(100 + seed)
+    y = C.CP(rng.uniform(0.5, 1.5, 6), [rng.standard_normal((n, 6)) for _ in range(d)])
+    x = C.CP(rng.uniform(0.5, 1.5, 3), [rng.standard_normal((n, 3)) for _ in range(d)])
+    full = np.linalg.norm(C.to_full(y) - C.to_full(x))
+    assert abs(C.residual(y, x) - full) <= 1e-12 * np.linalg.norm(C.to_full(y))
+    # a fit within 1e-4 of its target: the identity still resolves the residual to
+    # sqrt(eps) |y| (it subtracts Grams of size |y|^2)
+    near = C.CP(y.weights.copy(), [f + 1e-4 * rng.standard_normal(f.shape) for f in y.factors])
+    full = np.linalg.norm(C.to_full(y) - C.to_full(near))
+    ny = np.linalg.norm(C.to_full(y))
+    assert abs(C.residual(y, near) - full) <= 1e-7 * ny
+    assert 0.5 * full < C.residual(y, near) < 2.0 * full
+    assert C.residual(y, y) <= 1e-7 * ny
+    # a scaled copy: |y - a y| = |1 - a| |y| exactly
+    half = C.CP(0.5 * y.weights, [f.copy() for f in y.factors])
+    assert abs(C.residual(y, half) - 0.5 * ny) <= 1e-12 * ny

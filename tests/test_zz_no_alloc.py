@@ -78,3 +78,59 @@ def test_noalloc_rejects_sizes_beyond_its_limits(G):
     y2.struct.rank = 4
     rc = G.load().cp_als_sweep_noalloc(C.byref(y2.struct), C.byref(tall.struct), 1, 0, None, None, None)
     assert rc == G.HT_ERR_CAPACITY
+
+
+def test_noalloc_matches_oracle_directly(G):
+    """Both variants against the FP64 oracle's ALS (Section 2.1; Appendix B, Algorithm 1 for the
+    damped Jacobi sweep), on the full grid, over two calls in a row on the shared array."""
+    import torch
+    d, n, r = 4, 6, 5
+    for seed, variant, name in [(31, G.CP_ALS_GS, "gs"), (37, G.CP_ALS_JACOBI_DAMPED, "jacobi_damped")]:
+        y, xi = _inputs(seed, d, n, r)
+        ref, eps_ref = OC.als_sweeps(y, xi, 3, name)
+        Y = G.CPTensor(d, [n] * d, y.rank)
+        Y.upload(y.weights, y.factors)
+        X = G.CPTensor(d, [n] * d, r)
+        X.upload(xi.weights, xi.factors)
+        e = torch.zeros(3, dtype=torch.float64, device="cuda")
+        G.cp_als_sweep_noalloc(Y, X, 3, variant, eps=e)
+        torch.cuda.synchronize()
+        assert _full_rel(X.download(), (ref.weights, ref.factors)) < 1e-10, name
+        np.testing.assert_allclose(e.cpu().numpy(), eps_ref, rtol=1e-6, atol=1e-14)
+
+
+def test_noalloc_allocates_nothing(G):
+    """After a first call (which looks up the static array's address), further calls leave the
+    device's free memory and the torch caching allocator's reservation unchanged."""
+    import torch
+    d, n, r = 4, 6, 5
+    y, xi = _inputs(41, d, n, r)
+    Y = G.CPTensor(d, [n] * d, y.rank)
+    Y.upload(y.weights, y.factors)
+    X = G.CPTensor(d, [n] * d, r)
+    X.upload(xi.weights, xi.factors)
+    G.cp_als_sweep_noalloc(Y, X, 2)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    res0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        X.upload(xi.weights, xi.factors)
+        G.cp_als_sweep_noalloc(Y, X, 2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_reserved() == res0
+    assert free1 == free0
+
+
+def test_noalloc_rejects_mismatched_shapes(G):
+    """x and y must share d and every n_k: HT_ERR_ARG before anything is launched."""
+    x = G.CPTensor(4, [6] * 4, 4)
+    x.struct.rank = 2
+    y3 = G.CPTensor(3, [6] * 3, 4)
+    y3.struct.rank = 4
+    rc = G.load().cp_als_sweep_noalloc(C.byref(y3.struct), C.byref(x.struct), 1, 0, None, None, None)
+    assert rc == G.HT_ERR_ARG
+    yn = G.CPTensor(4, [6, 6, 7, 6], 4)
+    yn.struct.rank = 4
+    rc = G.load().cp_als_sweep_noalloc(C.byref(yn.struct), C.byref(x.struct), 1, 0, None, None, None)
+    assert rc == G.HT_ERR_ARG
