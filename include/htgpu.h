@@ -352,6 +352,18 @@ int ht_selftest_grid_barrier(int nblocks, int absent, int device);
  * rsqrt) (device, 4n doubles).  Asynchronous on stream.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 int ht_selftest_fastmath(const double* x_dev, double* out_dev, int n, void* stream);
 
+/* Self-test of the tensor-core contraction of HT_PREC_MIXED contexts: C[b] = alpha op(A[b])
+ * op(B[b]) diag(colscale) + beta C[b] for b < batch (column-major; op(A) m x k, op(B) k x n; tA/tB
+ * select the stored transposes; strides sA, sB, sC between batch entries; colscale: device, n
+ * values, or NULL), computed from `slices` (2..4) BF16 digit planes per operand with FP32
+ * accumulation in tensor memory.  Element (i, j) is within about 2^-(8 slices - 1) k
+ * max_l |op(A)_il| max_l |op(B)_lj| of the exact product.  The paper has no counterpart: the
+ * precision scheme is this library's.  Synchronising.  Returns HT_OK, HT_ERR_TIMEOUT (a bounded
+ * wait gave up), HT_ERR_ARG or HT_ERR_CUDA. */
+int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb, int tB,
+                           double* C, int ldc, double alpha, double beta, const double* colscale, int batch,
+                           long long sA, long long sB, long long sC, int slices, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,10 @@ _EXPORTS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "ht_selftest_fastmath": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ht_selftest_gemm_mixed": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                         C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double,
+                                         C.c_void_p, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
+                                         C.c_int, C.c_void_p]),
     "cp_cn_als_step": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
                                  C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
@@ -551,6 +555,19 @@ def selftest_fastmath(x, stream=None):
     _check(load().ht_selftest_fastmath(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(),
                                        _stream_ptr(stream)), "ht_selftest_fastmath")
     return out
+
+
+def selftest_gemm_mixed(A, B, C, m, n, k, lda, ldb, ldc, tA=0, tB=0, alpha=1.0, beta=0.0, colscale=None,
+                        batch=1, sA=0, sB=0, sC=0, slices=4, stream=None):
+    """The tensor-core contraction of the mixed form on device FP64 buffers (column-major views
+    given by leading dimensions and batch strides, in elements)."""
+    return int(load().ht_selftest_gemm_mixed(m, n, k, C_ptr(A), lda, tA, C_ptr(B), ldb, tB, C_ptr(C), ldc,
+                                             float(alpha), float(beta), C_ptr(colscale), batch, sA, sB, sC,
+                                             slices, _stream_ptr(stream)))
+
+
+def C_ptr(t):
+    return C.c_void_p(t.data_ptr() if t is not None else 0)
 
 
 def selftest_grid_barrier(nblocks: int, absent: int = -1, device: int = 0) -> int:
