@@ -67,8 +67,13 @@ typedef enum ht_status {
 
 typedef enum ht_precision {
   HT_PREC_FP64 = 0,   /* every operation in FP64 */
-  HT_PREC_MIXED = 1   /* accepted; runs the FP64 kernels (an FP32-contraction form drifted past a
-                         1e-6 relative error over 200 steps of the 6-D advection workload) */
+  HT_PREC_MIXED = 1   /* the dense contractions of the HSVD truncation (transfer-tensor absorption,
+                         the complement / square-root factors, the node factors P_t = R_t E_t, the
+                         projections) run on the tensor cores: each FP64 operand row / column is
+                         split into ht_config.mixed_slices BF16 digit planes, accumulated in FP32
+                         (tcgen05, tensor memory), normwise error about 2^-(8 slices - 1); the QR
+                         R factors, node SVDs, truncation thresholds, the X_t Y_t = I refinement
+                         of the kept subspaces, the apply and the CP route stay FP64 */
 } ht_precision;
 
 /* ---------------------------------------------------------------- tensors ---- */
@@ -137,6 +142,8 @@ typedef struct ht_config {
   int precision;           /* ht_precision */
   int device;              /* CUDA device ordinal */
   int tree;                /* ht_tree_kind */
+  int mixed_slices;        /* HT_PREC_MIXED: BF16 digit planes per contraction operand, 2..4 (0 = 4);
+                              ignored in HT_PREC_FP64 */
 } ht_config;
 
 /* Context management, status codes, the profiler and the tree query below are infrastructure
@@ -229,7 +236,8 @@ int ht_step(ht_ctx* ctx, ht_tensor* u, const ht_op* L, double dt, double rel_tol
  * every QR in one CTA where a lone step may reduce a large one in row blocks (the same R up to
  * rounding and an orthogonal factor the truncation does not see).
  *
- * ht_batch_create binds count contexts and tensors (caller-owned, distinct, same d and device;
+ * ht_batch_create binds count contexts and tensors (caller-owned, distinct, same d, device, tree and
+ * precision form (precision and mixed_slices);
  * us[i] must fit ctxs[i] as for ht_step).  A bound context's device plan lives in the batch
  * until ht_batch_destroy; the context may still be used alone in between, but not concurrently
  * with a batched step.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_NOMEM, HT_ERR_CUDA. */

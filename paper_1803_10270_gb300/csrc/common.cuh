@@ -81,6 +81,11 @@ struct SvdDesc {
 // descs_dev + i * inst_stride bytes.
 cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr,
                             int count = 1, long long inst_stride = 0);
+// Tensor-core form of the same descriptor lists (HT_PREC_MIXED): `slices` (2..4) BF16 digit planes
+// per operand row / column, FP32 accumulation in tensor memory, one CTA per SM (a batch spreads
+// them over its instances).  err (device, or nullptr): HT_ERR_TIMEOUT when a bounded wait gave up.
+cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, int slices, cudaStream_t s,
+                               double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr);
 // Workspace of the cooperative QR (matrices wider than 64 columns and above 2^17 entries, one
 // instance per launch): per descriptor d and CTA g of its group, partial dot products
 // part[(d G + g) kmax + c], totals tot[d kmax + c], the published row j in two buffers by step

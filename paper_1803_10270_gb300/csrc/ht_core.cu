@@ -166,6 +166,8 @@ struct ht_ctx {
   double* prof_flops = nullptr;     // device, KC_COUNT counters
   int svd_smem = 0;
   int gemm_grid = 0;
+  int sms = 1;                 // streaming multiprocessors of the device
+  int slices = 0;              // HT_PREC_MIXED: BF16 digit planes per operand (0: FP64 contractions)
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
   QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
@@ -839,7 +841,9 @@ static bool cfg_valid(const ht_config* c) {
   for (int i = 0; i < c->d; ++i)
     if (c->n[i] < 1) return false;
   if (c->tree != HT_TREE_BALANCED && c->tree != HT_TREE_LINEAR) return false;
-  return c->precision == HT_PREC_FP64 || c->precision == HT_PREC_MIXED;
+  if (c->precision == HT_PREC_MIXED)
+    return c->mixed_slices == 0 || (c->mixed_slices >= 2 && c->mixed_slices <= 4);
+  return c->precision == HT_PREC_FP64;
 }
 
 static int trunc_input_cap(const ht_config* c) {
@@ -1005,6 +1009,8 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
   c->gemm_grid = htg_max(1, sms) * 4;
+  c->sms = htg_max(1, sms);
+  c->slices = (cfg->precision == HT_PREC_MIXED) ? (cfg->mixed_slices ? cfg->mixed_slices : 4) : 0;
   *out = c;
   return HT_OK;
 }
@@ -1095,6 +1101,11 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   const Levels& L = c->lev;
   const int g = c->gemm_grid;
   const long long st = (long long)sizeof(Plan);
+  // the dense contractions: FP64 CUDA-core tiles, or the tensor-core split form (HT_PREC_MIXED)
+  auto gemm = [&](const GemmDesc* d, int nd) -> cudaError_t {
+    return c->slices ? htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMM), count, st, c->err)
+                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st);
+  };
   HTG_LAUNCH(c, KC_PLAN, s, pre());
   const QrCoopWs* coop = (c->has_coop && count == 1) ? &c->qr_coop : nullptr;
   const int coop_extra = coop ? 1 : 0;   // the cooperative QR launch beside each QR launch
@@ -1102,36 +1113,36 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   c->launches += coop_extra;
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_abs2[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_abs1[dep], L.n_int[dep]));
+    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_abs2[dep], L.n_int[dep]));
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_rootE, 2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_rootE, 2));
   // top-down complement factors: E of a child needs only E, B and R of its parent, never the
   // parent's SVD, so every node SVD runs afterwards in a single launch
   for (int dep = 1; dep < T.max_depth; ++dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_T1[dep], L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_T1[dep], L.n_int[dep]));
     HTG_LAUNCH(c, KC_GEMM, s,
-               htg_launch_gemm(P->g_Epre[dep], 2 * L.n_int[dep], g, s, htg_prof_flops(c, KC_GEMM), count, st));
+               gemm(P->g_Epre[dep], 2 * L.n_int[dep]));
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_Pall, T.nn - 1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_Pall, T.nn - 1));
   const SvdClusterCfg* clu = (count == 1) ? &c->svd_clu : nullptr;
   HTG_LAUNCH(c, KC_SVD, s,
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st, clu));
   c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_XY, 2 * (T.nn - 1), g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_XY, 2 * (T.nn - 1)));
   HTG_LAUNCH(c, KC_GEMM, s,
              (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
               cudaGetLastError()));
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj1, L.n_proj1, g, s, htg_prof_flops(c, KC_GEMM), count, st));
-  HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj2, L.n_proj2, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj1, L.n_proj1));
+  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj2, L.n_proj2));
   if (L.n_proj3 > 0)
-    HTG_LAUNCH(c, KC_GEMM, s, htg_launch_gemm(P->g_proj3, L.n_proj3, g, s, htg_prof_flops(c, KC_GEMM), count, st));
+    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj3, L.n_proj3));
   c->last_stream = s;
   return HT_OK;
 }
@@ -1407,6 +1418,7 @@ extern "C" int ht_batch_create(ht_batch** out, int count, ht_ctx* const* ctxs, h
     ht_ctx* c = ctxs[i];
     if (!c || c->cfg.d != d || c->cfg.device != dev || c->cfg.tree != tree || c->batch || !tensor_matches(c, us[i]))
       return HT_ERR_ARG;
+    if (c->slices != ctxs[0]->slices) return HT_ERR_ARG;   // one precision form per batch
     if (us[i]->cap > c->cap) return HT_ERR_CAPACITY;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return HT_ERR_ARG;   // each instance needs its own workspace

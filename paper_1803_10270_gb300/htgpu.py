@@ -54,7 +54,7 @@ class ht_op(C.Structure):
 
 class ht_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int * HT_MAXD), ("cap", C.c_int), ("max_terms", C.c_int),
-                ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int)]
+                ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int), ("mixed_slices", C.c_int)]
 
 
 _EXPORTS = {
@@ -176,7 +176,7 @@ class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
     def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
-                 device: int = 0, tree: int = 0):
+                 device: int = 0, tree: int = 0, mixed_slices: int = 0):
         lib = load()
         cfg = ht_config()
         cfg.d = d
@@ -187,6 +187,7 @@ class Context:
         cfg.precision = precision
         cfg.device = device
         cfg.tree = tree
+        cfg.mixed_slices = mixed_slices
         self.cfg = cfg
         self.d, self.n, self.cap, self.device = d, list(n), cap, device
         self.ptr = C.c_void_p()
