@@ -46,6 +46,12 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
+def config_keys(precision: str, l2: str, parallelism: str) -> dict:
+    """The workload identity, the same keys in both arms of the benchmark."""
+    return {"workload": WORKLOAD, "d": D, "n": N, "ht_r_max": RMAX, "tol": TOL, "cp_rank": CP_R,
+            "als_sweeps": SWEEPS, "precision": precision, "l2": l2, "parallelism": parallelism}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -58,9 +64,16 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
-    p.add_argument("--line", default="all", choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn", "kinetic"],
+    p.add_argument("--line", default="all",
+                   choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn", "kinetic", "mixed"],
                    help="run one side line alone (for profiling) and print its JSON object")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--record-counters", default=None, metavar="CSV",
+                   help="write the ncu counter record of --kernel from this CSV into profiles/counters.json")
+    p.add_argument("--kernel", default=None, help="kernel name for --record-counters")
+    p.add_argument("--record-workload", default="", help="workload of the capture (--record-counters)")
+    p.add_argument("--record-command", default="", help="the ncu command of the capture (--record-counters)")
+    p.add_argument("--record-sources", default="", help="comma-separated source files of the kernel")
     return p.parse_args()
 
 
@@ -289,8 +302,10 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
     if args.line != "all":
         warm = max(args.warmup, 3)
-        if args.line == "d12":
-            res = run_d12(G, torch, flush, args.steps, warm)
+        if args.line == "mixed":
+            res = run_mixed_lines(G, torch, flush, args)
+        elif args.line == "d12":
+            res = run_d12(G, torch, flush, args.steps, warm, precision=prec)
         elif args.line == "ab2":
             res = run_ab2(G, torch, flush, args.steps, warm)
         elif args.line == "varcoef":
@@ -300,9 +315,9 @@ def run_gpu(args):
         elif args.line == "cn":
             res = run_cn(G, torch, flush, args.steps, warm)
         elif args.line == "kinetic":
-            res = run_kinetic(G, torch, flush, args.steps, warm)
+            res = run_kinetic(G, torch, flush, args.steps, warm, precision=prec)
         else:
-            res = run_batched(G, torch, flush, args.batched, args.steps, warm)
+            res = run_batched(G, torch, flush, args.batched, args.steps, warm, precision=prec)
         if rank == 0:
             print(json.dumps({"line": args.line, **res}), flush=True)
         if world > 1:
@@ -398,14 +413,17 @@ def run_gpu(args):
     # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
     ab2 = run_ab2(G, torch, flush, args.steps, args.warmup)
 
-    # ---- the 12-D workload (n = 128, r_max 64, depth-4 tree), HT route alone, 100 RK2 steps
-    d12 = run_d12(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
+    # ---- FP64 against the tensor-core form: the HT route of this workload, the 12-D workload
+    #      (100 RK2 steps), the full-size kinetic workload and the ragged batch, each in both forms
+    #      from the same initial state; the FP64 halves are the d12 / kinetic / batched lines
+    mixed = run_mixed_lines(G, torch, flush, args) if args.d12 else None
+    d12 = mixed["d12"]["fp64"] if mixed else None
 
     # ---- the same HT workload in tensor-train form (linear dimension tree)
     tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
 
-    # ---- the full-size kinetic workload, HEUN2, 5 steps after 3
-    kinetic = run_kinetic(G, torch, flush, 5, 3) if args.d12 else None
+    # ---- the full-size kinetic workload, HEUN2, 5 steps after 3 (timed in run_mixed_lines)
+    kinetic = mixed["kinetic"]["fp64"] if mixed else None
 
     # ---- implicit Crank-Nicolson step in CP format (ALS), kinetic operator
     cn = run_cn(G, torch, flush, 50, max(args.warmup, 3)) if args.d12 else None
@@ -413,9 +431,13 @@ def run_gpu(args):
     # ---- variable-coefficient advection (eq. PDE-advR) on the paper's 2-D grid, HEUN2
     varcoef = run_varcoef(G, torch, flush, 100, max(args.warmup, 3)) if args.d12 else None
 
-    # ---- ragged batch of independent instances (ht_batch_step), its own throughput line
-    batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
-        if args.batched > 0 else None
+    # ---- ragged batch of independent instances (ht_batch_step), its own throughput line (timed
+    #      in run_mixed_lines when that ran)
+    if mixed and "batched" in mixed:
+        batched = mixed["batched"]["fp64"]
+    else:
+        batched = run_batched(G, torch, flush, args.batched, min(args.steps, 20), max(args.warmup, 3)) \
+            if args.batched > 0 else None
 
     if rank == 0:
         out = {
@@ -423,11 +445,10 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic (seeded 6-D advection, n=64)",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "ht_ranks_final": ranks,
-                       "streams": "HT route and CP route on two streams (independent data)",
-                       "cp_rank": CP_R, "l2": "flushed between timed steps (256 MB write)",
-                       "cuda_graph": graph is not None,
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": config_keys(args.precision, "flushed between timed steps (256 MB write)",
+                                  "replicas" if world > 1 else "single GPU"),
+            "run": {"ht_ranks_final": ranks, "streams": "HT route and CP route on two streams (independent data)",
+                    "cuda_graph": graph is not None},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_shares": shares,
         }
@@ -443,6 +464,10 @@ def run_gpu(args):
             out["cn"] = cn
         if kinetic is not None:
             out["kinetic"] = kinetic
+        if mixed is not None:
+            out["mixed"] = {k: {kk: vv for kk, vv in v.items() if kk != "fp64"} for k, v in mixed.items()}
+            for k, v in out["mixed"].items():
+                v["fp64_value"] = mixed[k]["fp64"]["value"]
         if batched is not None:
             out["batched"] = batched
         if not args.no_cpu_baseline:
@@ -452,8 +477,26 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_mixed_lines(G, torch, flush, args) -> dict:
+    """Each line in the FP64 and the mixed (tensor-core) form: steps/s, speedup and the relative
+    difference of the final states."""
+    warm = max(args.warmup, 3)
+    out = {"adv6d_ht": mixed_vs_fp64(G, torch, flush, run_d12, steps=args.steps, warmup=warm, d=D, n=N, cap=RMAX,
+                                     n_terms=2, seed_offset=1, workload=ADV_HT_WORKLOAD),
+           "d12": mixed_vs_fp64(G, torch, flush, run_d12, steps=100, warmup=warm),
+           "kinetic": mixed_vs_fp64(G, torch, flush, run_kinetic, steps=5, warmup=3)}
+    if args.batched > 0:
+        out["batched"] = mixed_vs_fp64(G, torch, flush, run_batched, count=args.batched,
+                                       steps=min(args.steps, 20), warmup=warm)
+    return out
+
+
+ADV_HT_WORKLOAD = ("6-D advection n=64 HT route alone: r_max 32, tol 1e-8, RK2 dt=0.2h (the headline "
+                   "workload's HT half)")
+
+
 BATCH_WORKLOAD = ("ragged batch: independent 6-D advection instances, n in {32,48,64,96,128}, "
-                  "HT r_max in 8..48, seeded velocities, RK2 dt=0.2h, tol 1e-8, FP64; "
+                  "HT r_max in 8..48, seeded velocities, RK2 dt=0.2h, tol 1e-8; "
                   "one step = every instance's HT apply+HSVD truncate, each launch covering all instances")
 
 
@@ -514,7 +557,7 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
 
 
 D12_WORKLOAD = ("12-D advection n=128: depth-4 tree, seeded separable rank-3 initial condition, "
-                "HT r_max 64, tol 1e-8, RK2 dt=0.2h, FP64 throughout")
+                "HT r_max 64, tol 1e-8, RK2 dt=0.2h")
 
 
 TT_WORKLOAD = ("6-D advection n=64 HT route in tensor-train form (the linear dimension tree, "
@@ -522,14 +565,17 @@ TT_WORKLOAD = ("6-D advection n=64 HT route in tensor-train form (the linear dim
 
 
 def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128, cap: int = 64,
-            n_terms: int = 3, seed_offset: int = 4, tree: int = 0, workload: str = None) -> dict:
+            n_terms: int = 3, seed_offset: int = 4, tree: int = 0, workload: str = None, precision: int = 0,
+            slices: int = 0, keep: bool = False, profile: bool = True):
     """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
     64), or another advection workload and tree: the timed steps graph-captured, L2 flushed
-    between them."""
+    between them; then a profiled stretch of the same length for the per-class roofline.  keep:
+    also return the context and the final state (steps warmup + steps, before the profiled
+    stretch) for a comparison between precision forms."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
     case = advection_case(d, n, n_terms=n_terms, seed_offset=seed_offset)
-    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree)
+    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree, precision=precision, mixed_slices=slices)
     u = G.HTTensor(d, [n] * d, cap, tree=tree)
     u.upload(ic_nodes(u.tree, case.ic_factors(), np))
     op = G.advection_op(case.c, case.h)
@@ -554,10 +600,22 @@ def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128,
     ms_max, value = aggregate_replicas(ms, steps)
     ranks = u.ranks()
     del graph
+    res = {"workload": workload or D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+           "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step,
+           "ht_ranks_final": ranks, "cuda_graph": True, "precision": precision_name(precision, slices)}
+    snap = None
+    if keep:
+        snap = G.HTTensor(d, [n] * d, cap, tree=tree)
+        snap.blob.copy_(u.blob)
+        snap.rank_buf.copy_(u.rank_buf)
+    if profile:
+        pst = min(steps, 10)
+        prof = profiled_steps(ctx, torch, flush, lambda: G.ht_step(ctx, u, op, case.dt, TOL, cap), pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+    if keep:
+        return res, ctx, snap
     ctx.close()
-    return {"workload": workload or D12_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
-            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step,
-            "ht_ranks_final": ranks, "cuda_graph": True}
+    return res
 
 
 VC_WORKLOAD = ("variable-coefficient advection f_t + (C z).grad f = 0 (eq. PDE-advR), N=2 on the paper's "
@@ -621,17 +679,19 @@ def run_cn(G, torch, flush, steps: int, warmup: int) -> dict:
 
 KIN_WORKLOAD = ("linearised 6-D kinetic equation: n=64 per variable, x periodic [0,2pi)^3, v in [-6,6]^3, "
                 "nu=1, seeded initial condition M(v)(1 + 0.1 prod sin x_i) + rank-4 perturbation, 5-term operator, "
-                "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6, FP64; steps 4..3+K from t=0")
+                "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6; steps 4..3+K from t=0")
 
 
-def run_kinetic(G, torch, flush, steps: int, warmup: int) -> dict:
+def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0,
+                keep: bool = False, profile: bool = True):
     """HT HEUN2 steps/s of the full-size kinetic workload (node ranks grow to about 60 within ten
-    steps, so the step cost grows too: the line reports steps warmup+1 .. warmup+steps)."""
+    steps, so the step cost grows too: the line reports steps warmup+1 .. warmup+steps); then a
+    profiled stretch for the per-class roofline; keep as in run_d12."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
     kc = kinetic_case(64)
     w0, F0 = kinetic_ic(kc)
-    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5, precision=precision, mixed_slices=slices)
     u = G.HTTensor(6, [64] * 6, 64)
     u.upload(ic_nodes(u.tree, [F * (w0[None, :] if i == 0 else 1.0) for i, F in enumerate(F0)], np))
     kop = G.KineticOp(kc)
@@ -657,10 +717,23 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int) -> dict:
     ms_max, value = aggregate_replicas(ms, steps)
     ranks = u.ranks()
     del graph
+    res = {"workload": KIN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+           "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "ht_ranks_final": ranks,
+           "cuda_graph": True, "precision": precision_name(precision, slices)}
+    snap = None
+    if keep:
+        snap = G.HTTensor(6, [64] * 6, 64)
+        snap.blob.copy_(u.blob)
+        snap.rank_buf.copy_(u.rank_buf)
+    if profile:
+        pst = min(steps, 2)
+        prof = profiled_steps(ctx, torch, flush,
+                              lambda: G.ht_step(ctx, u, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2), pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+    if keep:
+        return res, ctx, snap
     ctx.close()
-    return {"workload": KIN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
-            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "ht_ranks_final": ranks,
-            "cuda_graph": True}
+    return res
 
 
 def run_tt(G, torch, flush, steps: int, warmup: int) -> dict:
@@ -719,16 +792,19 @@ def run_varcoef(G, torch, flush, steps: int, warmup: int) -> dict:
             "t_end": t_end, "pointwise_rel_err_at_z_star": abs(f_num - f_ex) / f_ex, "cuda_graph": True}
 
 
-def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:
+def run_batched(G, torch, flush, count: int, steps: int, warmup: int, precision: int = 0, slices: int = 0,
+                keep: bool = False, profile: bool = True):
     """Throughput of ht_batch_step on a ragged batch: instance-steps/s over a graph-captured
-    step, L2 flushed between timed steps, slowest rank's time for replicas."""
+    step, L2 flushed between timed steps, slowest rank's time for replicas; then a profiled
+    stretch (the classes of the first instance's context carry the batch's launches); keep:
+    also return the contexts and the final states."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import batched_advection_cases
     cases = batched_advection_cases(count, D)
     ctxs, tens, ops = [], [], []
     ws = 0
     for n, rmax, case in cases:
-        c = G.Context(D, [n] * D, cap=rmax, max_terms=1)
+        c = G.Context(D, [n] * D, cap=rmax, max_terms=1, precision=precision, mixed_slices=slices)
         ws += c.workspace_bytes
         t = G.HTTensor(D, [n] * D, rmax)
         t.upload(ic_nodes(t.tree, case.ic_factors(), np))
@@ -764,15 +840,57 @@ def run_batched(G, torch, flush, count: int, steps: int, warmup: int) -> dict:
     ms_max, steps_per_s = aggregate_replicas(ms, steps)
     rk = [max(t.ranks()[1:]) for t in tens]
     ns = [n for n, _, _ in cases]
-    b.close()
     del graph
+    res = {"workload": BATCH_WORKLOAD, "instances": count, "value": steps_per_s * count,
+           "unit": "instance-steps/s", "ms_per_step": ms_max / steps, "steps": steps, "warmup": warmup,
+           "gpu_launches_per_step": per_step, "grids": {str(v): ns.count(v) for v in sorted(set(ns))},
+           "rank_max_final": max(rk), "rank_mean_final": sum(rk) / len(rk),
+           "workspace_gb": ws / 1e9, "l2": "flushed between timed steps (256 MB write)", "cuda_graph": True,
+           "precision": precision_name(precision, slices)}
+    snaps = None
+    if keep:
+        snaps = []
+        for (n, rmax, _), t in zip(cases, tens):
+            sn = G.HTTensor(D, [n] * D, rmax)
+            sn.blob.copy_(t.blob)
+            sn.rank_buf.copy_(t.rank_buf)
+            snaps.append(sn)
+    if profile:
+        pst = min(steps, 5)
+        prof = profiled_steps(ctxs[0], torch, flush, lambda: b.step(ops, dts, tols, rmaxs, stream=stream), pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+    b.close()
+    if keep:
+        return res, ctxs, snaps
     for c in ctxs:
         c.close()
-    return {"workload": BATCH_WORKLOAD, "instances": count, "value": steps_per_s * count,
-            "unit": "instance-steps/s", "ms_per_step": ms_max / steps, "steps": steps, "warmup": warmup,
-            "gpu_launches_per_step": per_step, "grids": {str(v): ns.count(v) for v in sorted(set(ns))},
-            "rank_max_final": max(rk), "rank_mean_final": sum(rk) / len(rk),
-            "workspace_gb": ws / 1e9, "l2": "flushed between timed steps (256 MB write)", "cuda_graph": True}
+    return res
+
+
+def precision_name(precision: int, slices: int) -> str:
+    return "fp64" if precision == 0 else f"mixed ({slices or 4} BF16 digit planes per operand, FP32 accumulation)"
+
+
+def mixed_vs_fp64(G, torch, flush, fn, **kw) -> dict:
+    """One line in both precision forms from the same initial state and for the same steps:
+    steps/s of each, their ratio and the relative difference of the final states (the FP64 GPU
+    form is within 1e-10 of the oracle, tests/test_gpu_workloads.py)."""
+    r64, c64, s64 = fn(G, torch, flush, precision=0, keep=True, **kw)
+    if isinstance(c64, list):     # a batch: free the FP64 workspaces before the mixed run
+        for c in c64:
+            c.close()
+    rmx, cmx, smx = fn(G, torch, flush, precision=1, slices=4, keep=True, **kw)
+    if isinstance(cmx, list):     # per instance, each against its FP64 twin
+        err = max(ht_rel_diff(G, torch, c, a, b) for c, a, b in zip(cmx, smx, s64))
+        for c in cmx:
+            c.close()
+    else:
+        err = ht_rel_diff(G, torch, c64, smx, s64)
+        c64.close()
+        cmx.close()
+    return {"workload": r64["workload"], "fp64": r64, "mixed": rmx, "speedup": rmx["value"] / r64["value"],
+            "rel_err_vs_fp64_final": err, "rel_err_resolution": 1.5e-8,
+            "steps_compared": r64["steps"] + r64["warmup"]}
 
 
 def aggregate_replicas(ms_local: float, steps: int):
@@ -788,50 +906,208 @@ def aggregate_replicas(ms_local: float, steps: int):
     return ms_max, world * steps / (ms_max * 1e-3)
 
 
-def load_traffic() -> dict:
-    """DRAM bytes per launch per kernel from the committed ncu summary
-    (profiles/traffic_adv6d_n64_fp64.md, a `| kernel | bytes |` table)."""
-    p = os.path.join(ROOT, "profiles", "traffic_adv6d_n64_fp64.md")
-    out = {}
+def ht_rel_diff(G, torch, ctx, a, b) -> float:
+    """|a - b| / |b| on the device from the three HT inner products <a,a>, <a,b>, <b,b> (the
+    identity resolves about sqrt(eps) = 1.5e-8 relative, ample for the 1e-6 bar)."""
+    out = torch.zeros(3, dtype=torch.float64, device="cuda")
+    G.ht_inner(ctx, a, a, out[0:1])
+    G.ht_inner(ctx, a, b, out[1:2])
+    G.ht_inner(ctx, b, b, out[2:3])
+    aa, ab, bb = (float(v) for v in out.cpu())
+    return math.sqrt(max(aa - 2.0 * ab + bb, 0.0) / bb) if bb > 0 else float("nan")
+
+
+def measured_peaks() -> dict:
+    """MEASURED_PEAKS.json of the GPU pool (copy bandwidth, cuBLAS bf16 burst and sustained)."""
     try:
-        with open(p) as f:
-            for line in f:
-                cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) == 2 and cells[1].isdigit():
-                    out[cells[0]] = int(cells[1])
-    except OSError:
-        pass
-    return out
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
-def profile_pass(W, torch, flush, steps: int):
-    """Event-time every kernel class over `steps` steps; roofline of the dominant class."""
-    W.ctx.profile(True)
-    for _ in range(steps):
-        flush.zero_()
-        W.step()
-    torch.cuda.synchronize()
-    prof = W.ctx.profile_read()
-    W.ctx.profile(False)
+def class_roofline(prof: dict, steps: int) -> tuple:
+    """Per-class shares of one profiled stretch, and the roofline of its dominant class: the
+    FP64 classes against the FP64 peak ("alu"), the tensor-core contractions against the
+    measured sustained BF16 tensor peak ("tensor", executed MMA flops)."""
     total = sum(v["ms"] for v in prof.values()) or 1.0
     shares = {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
                   "share": v["ms"] / total} for k, v in prof.items() if v["launches"]}
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    v = prof[dom]
-    roof = {"kernel": KERNEL_NAMES.get(dom, dom), "class": dom, "bound": "alu", "unit": "TFLOP/s",
-            "peak": FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM)",
-            "achieved": None, "frac": None, "traffic": None, "avg_launch_us": None, "steps": steps}
+    roof = roofline_of(prof, dom, steps)
+    out = {"dominant": roof}
+    if dom != "gemm_tc" and prof.get("gemm_tc", {}).get("launches"):
+        out["gemm_tc"] = roofline_of(prof, "gemm_tc", steps)
+    return out, shares
+
+
+def roofline_of(prof: dict, cls: str, steps: int) -> dict:
+    v = prof[cls]
+    if cls == "gemm_tc":
+        pk = measured_peaks()
+        peak = pk.get("bf16_tflops_sustained") or 1700.0
+        roof = {"kernel": "gemm_tc_kernel", "class": cls, "bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json" if pk else "fallback 1.7 PFLOP/s",
+                "flops": "executed BF16 MMA flops (digit-pair products over whole 128 x 128 tiles)"}
+    else:
+        roof = {"kernel": KERNEL_NAMES.get(cls, cls), "class": cls, "bound": "alu", "unit": "TFLOP/s",
+                "peak": FP64_PEAK_TFLOPS, "peak_source": "FP64 nominal (152 SMs x 2.07 GHz x 4 flop/clk/SM)",
+                "flops": "FP64 flops the kernel counts"}
+    roof.update({"achieved": None, "frac": None, "traffic": None, "avg_launch_us": None, "steps": steps})
     if v["launches"]:
         per_launch_s = v["ms"] * 1e-3 / v["launches"]
         roof["avg_launch_us"] = per_launch_s * 1e6
         if v["flops"] > 0:
             ach = v["flops"] / v["launches"] / per_launch_s / 1e12
             roof["achieved"] = ach
-            roof["frac"] = ach / FP64_PEAK_TFLOPS
+            roof["frac"] = ach / roof["peak"]
             roof["flops_per_launch"] = v["flops"] / v["launches"]
-    tr = load_traffic().get(roof["kernel"].split("/")[0])
-    if tr is not None:
-        roof["traffic"] = tr
+    rec = counter_record(roof["kernel"].split("/")[0])
+    if rec is not None:
+        roof["traffic"] = rec.get("dram_bytes_per_launch")
+        roof["traffic_record"] = {k: rec[k] for k in ("workload", "when") if k in rec}
+    return roof
+
+
+def profiled_steps(ctx, torch, flush, step, steps: int) -> dict:
+    """Per-class CUDA-event times of `steps` launches of step() (no graph, L2 flushed)."""
+    ctx.profile(True)
+    for _ in range(steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    return prof
+
+
+COUNTERS = os.path.join(ROOT, "profiles", "counters.json")
+# the ncu metrics a counter record keeps (dram bytes give roofline.traffic)
+RECORD_METRICS = ("gpu__time_duration.sum", "dram__bytes_read.sum", "dram__bytes_write.sum",
+                  "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active",
+                  "sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active",
+                  "sm__cycles_active.avg", "sm__cycles_elapsed.avg", "launch__grid_size",
+                  "launch__registers_per_thread", "gpu__dram_throughput.avg.pct_of_peak_sustained_elapsed")
+_UNIT = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "ns": 1e-3, "us": 1.0, "usecond": 1.0,
+         "msecond": 1e3, "ms": 1e3, "nsecond": 1e-3}
+
+
+def _sha256(path: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def counter_record(kernel: str):
+    """The committed ncu counter record of a kernel (profiles/counters.json, written by
+    --record-counters), or None.  A record whose kernel sources changed since the capture (their
+    SHA-256 differs from the one recorded) is returned with stale = True and no byte count."""
+    try:
+        with open(COUNTERS) as f:
+            recs = json.load(f).get("records", [])
+    except (OSError, ValueError):
+        return None
+    for r in recs:
+        if r.get("kernel") != kernel:
+            continue
+        try:
+            fresh = all(_sha256(p) == h for p, h in r.get("sources", {}).items())
+        except OSError:
+            fresh = False
+        if not fresh:
+            return {"stale": True, "workload": r.get("workload"), "when": r.get("when")}
+        return r
+    return None
+
+
+def parse_ncu_csv(path: str, kernel: str) -> list:
+    """Launches of `kernel` in an ncu CSV: the raw page (`ncu -i rep --page raw --csv`, one row per
+    launch, a units row under the header) or a --metrics --csv log (one row per metric).  Values
+    in bytes / microseconds / plain numbers."""
+    import csv
+    with open(path, newline="") as f:
+        rows = [r for r in csv.reader(f) if r and not r[0].startswith("==")]
+    hdr = rows[0]
+    out = []
+    if "Metric Name" in hdr:
+        ik, im, iu, iv, iid = (hdr.index(k) for k in ("Kernel Name", "Metric Name", "Metric Unit", "Metric Value", "ID"))
+        per = {}
+        for r in rows[1:]:
+            if kernel not in r[ik]:
+                continue
+            v = float(r[iv].replace(",", "")) * _UNIT.get(r[iu].strip().lower(), 1.0)
+            per.setdefault(r[iid], {})[r[im]] = v
+        return [per[k] for k in sorted(per, key=int)]
+    units = rows[1]
+    ik = hdr.index("Kernel Name")
+    for r in rows[2:]:
+        if kernel not in r[ik]:
+            continue
+        rec = {}
+        for m in RECORD_METRICS:
+            if m in hdr:
+                j = hdr.index(m)
+                try:
+                    rec[m] = float(r[j].replace(",", "")) * _UNIT.get(units[j].strip().lower(), 1.0)
+                except ValueError:
+                    pass
+        out.append(rec)
+    return out
+
+
+def record_counters(args) -> None:
+    """Write (or replace) the counter record of one kernel in profiles/counters.json from an ncu
+    CSV, with the SHA-256 of the kernel's source files so a later source change marks it stale."""
+    launches = parse_ncu_csv(args.record_counters, args.kernel)
+    if not launches:
+        raise SystemExit(f"no launch of {args.kernel} in {args.record_counters}")
+    last = launches[-1]
+    rec = {"kernel": args.kernel, "workload": args.record_workload, "command": args.record_command,
+           "when": time.strftime("%Y-%m-%d"), "launches_in_capture": len(launches),
+           "metrics": {k: v for k, v in last.items()},
+           "sources": {p: _sha256(p) for p in args.record_sources.split(",") if p}}
+    if "dram__bytes_read.sum" in last and "dram__bytes_write.sum" in last:
+        rec["dram_bytes_per_launch"] = int(round(last["dram__bytes_read.sum"] + last["dram__bytes_write.sum"]))
+    try:
+        with open(COUNTERS) as f:
+            doc = json.load(f)
+    except (OSError, ValueError):
+        doc = {"about": "ncu counters per kernel (bench.py --record-counters); bench.py reports "
+                        "roofline.traffic from dram_bytes_per_launch while every listed source is unchanged",
+               "records": []}
+    doc["records"] = [r for r in doc["records"] if r.get("kernel") != args.kernel] + [rec]
+    with open(COUNTERS, "w") as f:
+        json.dump(doc, f, indent=1)
+        f.write("\n")
+    print(json.dumps(rec, indent=1))
+
+
+def cp_survey_flops_per_launch(r: int = CP_R, d: int = D, n: int = N, sweeps: int = SWEEPS) -> float:
+    """The CP-ALS route's algorithmic flops per launch of cp_als_sweep_rk2 as the scope table counts
+    them for the explicit y = p(dt L) x (rank R_y = (1 + 2d + d(d-1)/2) r): per mode
+    2 d n r^2 (factor Grams) + 2 n R_y r (right-hand side) + r^3 / 3 (Cholesky), d modes a sweep."""
+    ry = (1 + 2 * d + d * (d - 1) // 2) * r
+    return sweeps * d * (2.0 * d * n * r * r + 2.0 * n * ry * r + r ** 3 / 3.0)
+
+
+def profile_pass(W, torch, flush, steps: int):
+    """Event-time every kernel class over `steps` steps; roofline of the dominant class.  For the
+    CP kernel `achieved` uses the scope table's algorithmic flops of the explicit form (75.3 MFLOP
+    per launch); the kernel itself never forms y and executes the fewer flops its counter reports
+    (`executed_*`)."""
+    prof = profiled_steps(W.ctx, torch, flush, W.step, steps)
+    rl, shares = class_roofline(prof, steps)
+    roof = rl["dominant"]
+    if roof["class"] == "cp_solve" and roof["avg_launch_us"]:
+        alg = cp_survey_flops_per_launch()
+        roof["executed_flops_per_launch"] = roof.get("flops_per_launch")
+        roof["executed_achieved"] = roof["achieved"]
+        roof["executed_frac"] = roof["frac"]
+        roof["flops_per_launch"] = alg
+        roof["flops"] = ("scope-table algorithmic flops of the explicit form: per mode 2 d n r^2 + 2 n R_y r "
+                         "+ r^3/3, R_y = 28 r, r = 24, 6 modes x 5 sweeps")
+        roof["achieved"] = alg / (roof["avg_launch_us"] * 1e-6) / 1e12
+        roof["frac"] = roof["achieved"] / roof["peak"]
     return roof, shares
 
 
@@ -896,8 +1172,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 6-D advection, n=64)",
            "impl": "reference",
-           "config": {"workload": WORKLOAD, "precision": "fp64", "l2": "n/a (host)",
-                      "device": "host cores (the oracle; no GPU used)"},
+           "config": config_keys("fp64", "n/a (host cores; the oracle uses no GPU)", "host cores"),
            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "cpu": host_cpu(),
                             "sample": f"{args.steps} samples of up to {per:.1f} s, each from t=0 in a fresh "
                                       f"process with {cores} BLAS threads, FP64 numpy oracle "
@@ -910,6 +1185,9 @@ def main():
     args = parse()
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.cpu_seconds)))
+        return
+    if args.record_counters:
+        record_counters(args)
         return
     if args.impl == "reference":
         run_reference(args)

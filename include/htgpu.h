@@ -172,8 +172,9 @@ long long ht_ctx_launches(const ht_ctx* ctx);
  * counter per kernel class.  on = 0 stops recording.  Not for use inside stream capture. */
 int ht_ctx_profile(ht_ctx* ctx, int on);
 
-/* Per kernel class (7 classes: apply, gemm, qr, svd, plan/rank, cp small kernels,
- * cp solve) the summed event time in ms, the launch count and the counted FP64 flops.
+/* Per kernel class (8 classes: apply, gemm, qr, svd, plan/rank, cp small kernels,
+ * cp solve, tensor-core gemm) the summed event time in ms, the launch count and the counted
+ * flops (FP64 flops; for the tensor-core class the executed BF16 MMA flops).
  * Synchronises on the recorded events.  Any output pointer may be NULL. */
 int ht_ctx_profile_read(ht_ctx* ctx, double* ms, long long* launches, double* flops);
 

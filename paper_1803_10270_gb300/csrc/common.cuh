@@ -83,7 +83,8 @@ cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cuda
                             int count = 1, long long inst_stride = 0);
 // Tensor-core form of the same descriptor lists (HT_PREC_MIXED): `slices` (2..4) BF16 digit planes
 // per operand row / column, FP32 accumulation in tensor memory, one CTA per SM (a batch spreads
-// them over its instances).  err (device, or nullptr): HT_ERR_TIMEOUT when a bounded wait gave up.
+// them over its instances).  flops (device, or nullptr) accumulates the executed MMA flops.
+// err (device, or nullptr): HT_ERR_TIMEOUT when a bounded wait gave up.
 cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, int slices, cudaStream_t s,
                                double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr);
 // Workspace of the cooperative QR (matrices wider than 64 columns and above 2^17 entries, one
@@ -245,8 +246,10 @@ int htg_cp_terms(int d);   // 1 + 2d + d(d-1)/2
 
 // ------------------------------------------------------------ profiling --------
 // Kernel classes of the opt-in event profiler (ht_ctx_profile / ht_ctx_profile_read).
+// KC_GEMMTC: the tensor-core contractions of HT_PREC_MIXED; their counter holds the executed MMA
+// flops (BF16 digit products over whole 128 x 128 tiles), not FP64-equivalent ones.
 enum HtgKernelClass { KC_APPLY = 0, KC_GEMM = 1, KC_QR = 2, KC_SVD = 3, KC_PLAN = 4, KC_CPSMALL = 5,
-                      KC_CPSOLVE = 6, KC_COUNT = 7 };
+                      KC_CPSOLVE = 6, KC_GEMMTC = 7, KC_COUNT = 8 };
 void htg_prof_begin(ht_ctx* c, cudaStream_t s);
 void htg_prof_end(ht_ctx* c, int cls, cudaStream_t s);
 double* htg_prof_flops(ht_ctx* c, int cls);   // device counter of a class, nullptr when off

@@ -1103,9 +1103,10 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   const long long st = (long long)sizeof(Plan);
   // the dense contractions: FP64 CUDA-core tiles, or the tensor-core split form (HT_PREC_MIXED)
   auto gemm = [&](const GemmDesc* d, int nd) -> cudaError_t {
-    return c->slices ? htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMM), count, st, c->err)
+    return c->slices ? htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMMTC), count, st, c->err)
                      : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st);
   };
+  const int gcls = c->slices ? KC_GEMMTC : KC_GEMM;
   HTG_LAUNCH(c, KC_PLAN, s, pre());
   const QrCoopWs* coop = (c->has_coop && count == 1) ? &c->qr_coop : nullptr;
   const int coop_extra = coop ? 1 : 0;   // the cooperative QR launch beside each QR launch
@@ -1113,36 +1114,36 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   c->launches += coop_extra;
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_abs1[dep], L.n_int[dep]));
-    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_abs2[dep], L.n_int[dep]));
+    HTG_LAUNCH(c, gcls, s, gemm(P->g_abs1[dep], L.n_int[dep]));
+    HTG_LAUNCH(c, gcls, s, gemm(P->g_abs2[dep], L.n_int[dep]));
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_rootE, 2));
+  HTG_LAUNCH(c, gcls, s, gemm(P->g_rootE, 2));
   // top-down complement factors: E of a child needs only E, B and R of its parent, never the
   // parent's SVD, so every node SVD runs afterwards in a single launch
   for (int dep = 1; dep < T.max_depth; ++dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_T1[dep], L.n_int[dep]));
-    HTG_LAUNCH(c, KC_GEMM, s,
+    HTG_LAUNCH(c, gcls, s, gemm(P->g_T1[dep], L.n_int[dep]));
+    HTG_LAUNCH(c, gcls, s,
                gemm(P->g_Epre[dep], 2 * L.n_int[dep]));
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_Pall, T.nn - 1));
+  HTG_LAUNCH(c, gcls, s, gemm(P->g_Pall, T.nn - 1));
   const SvdClusterCfg* clu = (count == 1) ? &c->svd_clu : nullptr;
   HTG_LAUNCH(c, KC_SVD, s,
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st, clu));
   c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
-  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_XY, 2 * (T.nn - 1)));
+  HTG_LAUNCH(c, gcls, s, gemm(P->g_XY, 2 * (T.nn - 1)));
   HTG_LAUNCH(c, KC_GEMM, s,
              (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
               cudaGetLastError()));
-  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj1, L.n_proj1));
-  HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj2, L.n_proj2));
+  HTG_LAUNCH(c, gcls, s, gemm(P->g_proj1, L.n_proj1));
+  HTG_LAUNCH(c, gcls, s, gemm(P->g_proj2, L.n_proj2));
   if (L.n_proj3 > 0)
-    HTG_LAUNCH(c, KC_GEMM, s, gemm(P->g_proj3, L.n_proj3));
+    HTG_LAUNCH(c, gcls, s, gemm(P->g_proj3, L.n_proj3));
   c->last_stream = s;
   return HT_OK;
 }

@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(NT, 1)
     const int b = (int)(loc / ((long long)tm * tn));
     const int i0 = (tile % tm) * TM, j0 = (tile / tm) * TN;
     const int nr = htg_min(TM, g.m - i0), nc = htg_min(TN, g.n - j0);
-    if (flops && tid == 0) atomicAdd(flops, 2.0 * nr * nc * (double)g.k);
+    // executed MMA flops: the digit pairs over the whole tile and every stage
+    if (flops && tid == 0)
+      atomicAdd(flops, (double)(S * (S + 1) / 2) * 2.0 * TM * TN * (double)(KC * htg_max(1, htg_cdiv(g.k, KC))));
     // op(A)(i0 + r, l) = Ab[r rsA + l ksA]; op(B)(l, j0 + c) = Bb[c rsB + l ksB]
     const double* Ab = g.A + (long long)b * g.sA + (g.tA ? (long long)g.lda * i0 : (long long)i0);
     const long long rsA = g.tA ? g.lda : 1, ksA = g.tA ? 1 : g.lda;

@@ -200,7 +200,7 @@ class Context:
     def launches(self) -> int:
         return int(load().ht_ctx_launches(self.ptr))
 
-    KERNEL_CLASSES = ["apply", "gemm", "qr", "svd", "plan", "cp_small", "cp_solve"]
+    KERNEL_CLASSES = ["apply", "gemm", "qr", "svd", "plan", "cp_small", "cp_solve", "gemm_tc"]
 
     def profile(self, on: bool):
         _check(load().ht_ctx_profile(self.ptr, 1 if on else 0), "ht_ctx_profile")
