@@ -144,6 +144,13 @@ typedef struct ht_config {
   int tree;                /* ht_tree_kind */
   int mixed_slices;        /* HT_PREC_MIXED: BF16 digit planes per contraction operand, 2..4 (0 = 4);
                               ignored in HT_PREC_FP64 */
+  /* Tuning (0 = the library default; the package's autotuner measures them per GPU): */
+  long long tc_min_work;   /* HT_PREC_MIXED: contractions of at least this many multiply-adds
+                              (m n k batch, decided on the device per contraction) run on the tensor
+                              cores, smaller ones on the FP64 CUDA cores; -1: all on the tensor cores */
+  int gemm_ctas_per_sm;    /* CTAs per SM of the FP64 contraction launches, 1..32 (default 4) */
+  int svd_cluster_min_cols;/* node factors at least this wide use the thread-block-cluster SVD,
+                              32..480 (default 128) */
 } ht_config;
 
 /* Context management, status codes, the profiler and the tree query below are infrastructure
@@ -369,6 +376,15 @@ int ht_selftest_fastmath(const double* x_dev, double* out_dev, int n, void* stre
  * max_l |op(A)_il| max_l |op(B)_lj| of the exact product.  The paper has no counterpart: the
  * precision scheme is this library's.  Synchronising.  Returns HT_OK, HT_ERR_TIMEOUT (a bounded
  * wait gave up), HT_ERR_ARG or HT_ERR_CUDA. */
+/* Tuning probe (used by the package's autotuner; the paper has no counterpart): mean CUDA-event
+ * time in ms of `reps` launches of one synthetic contraction (op(A) m x k, op(B) k x n, `batch`
+ * entries) through the FP64 CUDA-core kernel (route 0, ctas_per_sm CTAs per SM, 1..32) or the
+ * tensor-core split kernel (route 1, `slices` digit planes, 2..4), written to *ms_out.
+ * Synchronising; allocates and frees its own device buffers.  Errors: HT_ERR_ARG, HT_ERR_NOMEM,
+ * HT_ERR_CUDA, HT_ERR_TIMEOUT. */
+int ht_tune_time_gemm(int m, int n, int k, int batch, int route, int slices, int ctas_per_sm, int reps,
+                      double* ms_out);
+
 int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb, int tB,
                            double* C, int ldc, double alpha, double beta, const double* colscale, int batch,
                            long long sA, long long sB, long long sC, int slices, void* stream);

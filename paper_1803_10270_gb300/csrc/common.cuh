@@ -79,14 +79,18 @@ struct SvdDesc {
 // flops (device double, or nullptr): the kernels add the FP64 flops they execute.
 // Batched form (count > 1): instance i (blockIdx.y) reads its ndesc descriptors at
 // descs_dev + i * inst_stride bytes.
+// tc_min > 0 (HT_PREC_MIXED): the launch skips descriptors of at least tc_min multiply-adds
+// (m n k batch), which the tensor-core launch of the same list takes.
 cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr,
-                            int count = 1, long long inst_stride = 0);
+                            int count = 1, long long inst_stride = 0, long long tc_min = 0);
 // Tensor-core form of the same descriptor lists (HT_PREC_MIXED): `slices` (2..4) BF16 digit planes
 // per operand row / column, FP32 accumulation in tensor memory, one CTA per SM (a batch spreads
 // them over its instances).  flops (device, or nullptr) accumulates the executed MMA flops.
 // err (device, or nullptr): HT_ERR_TIMEOUT when a bounded wait gave up.
+// Only descriptors of at least tc_min multiply-adds are taken (0: all).
 cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, int slices, cudaStream_t s,
-                               double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr);
+                               double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr,
+                               long long tc_min = 0);
 // Workspace of the cooperative QR (matrices wider than 64 columns and above 2^17 entries, one
 // instance per launch): per descriptor d and CTA g of its group, partial dot products
 // part[(d G + g) kmax + c], totals tot[d kmax + c], the published row j in two buffers by step
@@ -111,6 +115,7 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
 struct SvdClusterCfg {
   int cl = 0;
   long long cap_doubles = 0;   // shared memory of one CTA of the cluster form, in doubles
+  int min_p = 128;             // node factors at least this wide take the cluster form
 };
 SvdClusterCfg htg_svd_cluster_setup(int device);
 // whether htg_launch_svd adds the cluster launch (for the launch count)
@@ -125,6 +130,11 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
 __host__ __device__ inline int htg_min(int a, int b) { return a < b ? a : b; }
 __host__ __device__ inline int htg_max(int a, int b) { return a > b ? a : b; }
 __host__ __device__ inline int htg_cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline long long htg_max_ll(long long a, long long b) { return a > b ? a : b; }
+
+// HT_PREC_MIXED: contractions of at least this many multiply-adds go to the tensor cores unless the
+// context is given a tuned threshold (ht_config.tc_min_work)
+#define HTG_TC_MIN_WORK_DEFAULT (1ll << 22)
 
 // ------------------------------------------------------- FP64 special values ---
 // Measured on GB300 (dependent chains): FP64 FMA 64 cycles, FP64 sqrt 674, divide / rsqrt

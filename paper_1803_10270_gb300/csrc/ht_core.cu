@@ -168,6 +168,9 @@ struct ht_ctx {
   int gemm_grid = 0;
   int sms = 1;                 // streaming multiprocessors of the device
   int slices = 0;              // HT_PREC_MIXED: BF16 digit planes per operand (0: FP64 contractions)
+  long long tc_min = 0;        // HT_PREC_MIXED: contractions of at least this many multiply-adds on the tensor cores
+  bool tc_reach = false;       // whether a contraction of this context can reach tc_min
+  int svd_min_cols = 128;      // node factors at least this wide take the cluster SVD
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
   QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
@@ -841,6 +844,8 @@ static bool cfg_valid(const ht_config* c) {
   for (int i = 0; i < c->d; ++i)
     if (c->n[i] < 1) return false;
   if (c->tree != HT_TREE_BALANCED && c->tree != HT_TREE_LINEAR) return false;
+  if (c->tc_min_work < -1 || c->gemm_ctas_per_sm < 0 || c->gemm_ctas_per_sm > 32) return false;
+  if (c->svd_cluster_min_cols != 0 && (c->svd_cluster_min_cols < 32 || c->svd_cluster_min_cols > 480)) return false;
   if (c->precision == HT_PREC_MIXED)
     return c->mixed_slices == 0 || (c->mixed_slices >= 2 && c->mixed_slices <= 4);
   return c->precision == HT_PREC_FP64;
@@ -938,6 +943,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   build_levels(c->tree, &c->lev);
   c->Kc = trunc_input_cap(cfg);
   c->cap = cfg->cap;
+  c->svd_min_cols = cfg->svd_cluster_min_cols ? cfg->svd_cluster_min_cols : 128;
   if (c->Kc > 2 * HTG_SVD_MAXP) { delete c; return HT_ERR_CAPACITY; }
   WsLayout W;
   layout(cfg, c->tree, &W);
@@ -1002,15 +1008,28 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     return HT_ERR_CUDA;
   }
   // wide node factors: the cluster form of the SVD, when a cluster fits this device
-  if (c->Kc >= 128) c->svd_clu = htg_svd_cluster_setup(cfg->device);
+  if (c->Kc >= c->svd_min_cols) {
+    c->svd_clu = htg_svd_cluster_setup(cfg->device);
+    c->svd_clu.min_p = c->svd_min_cols;
+  }
   // SVD working copy in shared memory when the capacity allows
   const size_t Kc = (size_t)c->Kc;
   c->svd_smem = ((2 * Kc * Kc + Kc) * sizeof(double) <= 200 * 1024) ? 1 : 0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
-  c->gemm_grid = htg_max(1, sms) * 4;
+  c->gemm_grid = htg_max(1, sms) * (cfg->gemm_ctas_per_sm ? cfg->gemm_ctas_per_sm : 4);
   c->sms = htg_max(1, sms);
   c->slices = (cfg->precision == HT_PREC_MIXED) ? (cfg->mixed_slices ? cfg->mixed_slices : 4) : 0;
+  if (c->slices) {
+    // the largest contraction a truncation of this context can issue: an absorbed or projected
+    // transfer tensor (Kc^4 multiply-adds) or a leaf projection (n Kc^2)
+    int nmax = 1;
+    for (int i = 0; i < cfg->d; ++i) nmax = htg_max(nmax, cfg->n[i]);
+    const double kc = (double)c->Kc;
+    const double wmax = kc * kc * kc * kc > (double)nmax * kc * kc ? kc * kc * kc * kc : (double)nmax * kc * kc;
+    c->tc_min = (cfg->tc_min_work == -1) ? 0 : (cfg->tc_min_work ? cfg->tc_min_work : HTG_TC_MIN_WORK_DEFAULT);
+    c->tc_reach = (double)c->tc_min <= wmax;
+  }
   *out = c;
   return HT_OK;
 }
@@ -1101,12 +1120,22 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   const Levels& L = c->lev;
   const int g = c->gemm_grid;
   const long long st = (long long)sizeof(Plan);
-  // the dense contractions: FP64 CUDA-core tiles, or the tensor-core split form (HT_PREC_MIXED)
-  auto gemm = [&](const GemmDesc* d, int nd) -> cudaError_t {
-    return c->slices ? htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMMTC), count, st, c->err)
-                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st);
+  // the dense contractions: FP64 CUDA-core tiles; in HT_PREC_MIXED those of at least tc_min
+  // multiply-adds (decided per descriptor on the device) on the tensor cores, the rest in FP64
+  const bool tc_on = c->slices && c->tc_reach;
+  const long long tcm = tc_on ? htg_max_ll(1, c->tc_min) : 0;
+  auto gemm64 = [&](const GemmDesc* d, int nd) -> cudaError_t {
+    return (tc_on && c->tc_min == 0) ? cudaSuccess
+                                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm);
   };
-  const int gcls = c->slices ? KC_GEMMTC : KC_GEMM;
+  auto gemmtc = [&](const GemmDesc* d, int nd) -> cudaError_t {
+    return htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMMTC), count, st, c->err, tcm);
+  };
+#define HTG_GEMM(DESCS, ND)                                                    \
+  do {                                                                         \
+    if (!(tc_on && c->tc_min == 0)) HTG_LAUNCH(c, KC_GEMM, s, gemm64(DESCS, ND)); \
+    if (tc_on) HTG_LAUNCH(c, KC_GEMMTC, s, gemmtc(DESCS, ND));                  \
+  } while (0)
   HTG_LAUNCH(c, KC_PLAN, s, pre());
   const QrCoopWs* coop = (c->has_coop && count == 1) ? &c->qr_coop : nullptr;
   const int coop_extra = coop ? 1 : 0;   // the cooperative QR launch beside each QR launch
@@ -1114,36 +1143,35 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   c->launches += coop_extra;
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, gcls, s, gemm(P->g_abs1[dep], L.n_int[dep]));
-    HTG_LAUNCH(c, gcls, s, gemm(P->g_abs2[dep], L.n_int[dep]));
+    HTG_GEMM(P->g_abs1[dep], L.n_int[dep]);
+    HTG_GEMM(P->g_abs2[dep], L.n_int[dep]);
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, gcls, s, gemm(P->g_rootE, 2));
+  HTG_GEMM(P->g_rootE, 2);
   // top-down complement factors: E of a child needs only E, B and R of its parent, never the
   // parent's SVD, so every node SVD runs afterwards in a single launch
   for (int dep = 1; dep < T.max_depth; ++dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_LAUNCH(c, gcls, s, gemm(P->g_T1[dep], L.n_int[dep]));
-    HTG_LAUNCH(c, gcls, s,
-               gemm(P->g_Epre[dep], 2 * L.n_int[dep]));
+    HTG_GEMM(P->g_T1[dep], L.n_int[dep]);
+    HTG_GEMM(P->g_Epre[dep], 2 * L.n_int[dep]);
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_LAUNCH(c, gcls, s, gemm(P->g_Pall, T.nn - 1));
+  HTG_GEMM(P->g_Pall, T.nn - 1);
   const SvdClusterCfg* clu = (count == 1) ? &c->svd_clu : nullptr;
   HTG_LAUNCH(c, KC_SVD, s,
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st, clu));
   c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
-  HTG_LAUNCH(c, gcls, s, gemm(P->g_XY, 2 * (T.nn - 1)));
+  HTG_GEMM(P->g_XY, 2 * (T.nn - 1));
   HTG_LAUNCH(c, KC_GEMM, s,
              (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
               cudaGetLastError()));
-  HTG_LAUNCH(c, gcls, s, gemm(P->g_proj1, L.n_proj1));
-  HTG_LAUNCH(c, gcls, s, gemm(P->g_proj2, L.n_proj2));
+  HTG_GEMM(P->g_proj1, L.n_proj1);
+  HTG_GEMM(P->g_proj2, L.n_proj2);
   if (L.n_proj3 > 0)
-    HTG_LAUNCH(c, gcls, s, gemm(P->g_proj3, L.n_proj3));
+    HTG_GEMM(P->g_proj3, L.n_proj3);
   c->last_stream = s;
   return HT_OK;
 }

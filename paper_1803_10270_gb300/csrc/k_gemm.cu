@@ -14,8 +14,13 @@ namespace {
 constexpr int BM = 16, BN = 16, BK = 16, NT = 64;
 constexpr int MAXD = 64;
 
+// work of a descriptor in multiply-adds, the quantity the FP64 / tensor-core split compares
+__device__ inline long long gemm_work(const GemmDesc& g) {
+  return (long long)g.m * g.n * (long long)g.k * g.batch;
+}
+
 __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ descs0, long long inst_stride, int ndesc,
-                                                  double* flops) {
+                                                  double* flops, long long tc_min) {
   // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
   const GemmDesc* __restrict__ descs = (const GemmDesc*)((const char*)descs0 + inst_stride * blockIdx.y);
   __shared__ long long prefix[MAXD + 1];
@@ -28,7 +33,8 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     for (int i = 0; i < ndesc; ++i) {
       const GemmDesc& g = descs[i];
       long long items = 0;
-      if (g.m > 0 && g.n > 0 && g.batch > 0)
+      // tc_min > 0: descriptors of at least tc_min multiply-adds belong to the tensor-core launch
+      if (g.m > 0 && g.n > 0 && g.batch > 0 && (tc_min <= 0 || gemm_work(g) < tc_min))
         items = (long long)g.batch * htg_cdiv(g.m, BM) * htg_cdiv(g.n, BN);
       acc += items;
       prefix[i + 1] = acc;
@@ -115,13 +121,13 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
 }  // namespace
 
 cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops, int count,
-                            long long inst_stride) {
+                            long long inst_stride, long long tc_min) {
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (ndesc > MAXD || count > 65535) return cudaErrorInvalidValue;
   // One instance: 2 x SMs 64-thread CTAs (grid = 4 x SMs), the grid-stride loop covers any
   // item count.  A batch: instances differ in size, so each gets up to 16 CTAs, as many as
   // stay resident together (32 CTAs of 64 threads per SM)
   const int gx = (count == 1) ? htg_max(1, grid / 2) : htg_max(2, htg_min(16, (grid * 8 + count - 1) / count));
-  gemm_kernel<<<dim3(gx, count), NT, 0, s>>>(descs_dev, inst_stride, ndesc, flops);
+  gemm_kernel<<<dim3(gx, count), NT, 0, s>>>(descs_dev, inst_stride, ndesc, flops, tc_min);
   return cudaGetLastError();
 }

@@ -200,7 +200,8 @@ struct TcShared {
 
 template <int S>
 __global__ void __launch_bounds__(NT, 1)
-    gemm_tc_kernel(const GemmDesc* __restrict__ descs0, long long inst_stride, int ndesc, double* flops, int* err) {
+    gemm_tc_kernel(const GemmDesc* __restrict__ descs0, long long inst_stride, int ndesc, double* flops, int* err,
+                   long long tc_min) {
   extern __shared__ __align__(1024) char smem_raw[];
   char* planes = (char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // stage st: A planes at planes + st (2 S PLANE), B planes after them
@@ -213,7 +214,9 @@ __global__ void __launch_bounds__(NT, 1)
     for (int i = 0; i < ndesc; ++i) {
       const GemmDesc& g = descs[i];
       long long items = 0;
-      if (g.m > 0 && g.n > 0 && g.batch > 0) items = (long long)g.batch * htg_cdiv(g.m, TM) * htg_cdiv(g.n, TN);
+      // descriptors below tc_min multiply-adds belong to the FP64 launch
+      if (g.m > 0 && g.n > 0 && g.batch > 0 && (long long)g.m * g.n * (long long)g.k * g.batch >= tc_min)
+        items = (long long)g.batch * htg_cdiv(g.m, TM) * htg_cdiv(g.n, TN);
       acc += items;
       sh.prefix[i + 1] = acc;
     }
@@ -376,7 +379,7 @@ constexpr int smem_bytes() {
 
 template <int S>
 cudaError_t launch_s(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops, int count,
-                     long long inst_stride, int* err) {
+                     long long inst_stride, int* err, long long tc_min) {
   static int configured[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
@@ -385,23 +388,23 @@ cudaError_t launch_s(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_
     if (e != cudaSuccess) return e;
     configured[dev] = 1;
   }
-  gemm_tc_kernel<S><<<dim3(grid, count), NT, smem_bytes<S>(), s>>>(descs_dev, inst_stride, ndesc, flops, err);
+  gemm_tc_kernel<S><<<dim3(grid, count), NT, smem_bytes<S>(), s>>>(descs_dev, inst_stride, ndesc, flops, err, tc_min);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, int slices, cudaStream_t s,
-                               double* flops, int count, long long inst_stride, int* err) {
+                               double* flops, int count, long long inst_stride, int* err, long long tc_min) {
   if (ndesc <= 0 || count <= 0) return cudaSuccess;
   if (ndesc > MAXD || count > 65535) return cudaErrorInvalidValue;
   // one CTA per SM (512 tensor-memory columns and 2 x 2 S planes of shared memory each); a batch
   // spreads the SMs over its instances
   const int grid = (count == 1) ? htg_max(1, sms) : htg_max(1, htg_min(16, htg_cdiv(sms * 2, count)));
   switch (slices) {
-    case 2: return launch_s<2>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err);
-    case 3: return launch_s<3>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err);
-    case 4: return launch_s<4>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err);
+    case 2: return launch_s<2>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err, tc_min);
+    case 3: return launch_s<3>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err, tc_min);
+    case 4: return launch_s<4>(descs_dev, ndesc, grid, s, flops, count, inst_stride, err, tc_min);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -441,4 +444,68 @@ extern "C" int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int 
   if (cudaMemcpyAsync(&h, ep, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HT_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return HT_ERR_CUDA;
   return h;
+}
+
+// ------------------------------------------------------------- tuning ------------
+// Mean CUDA-event time of `reps` launches of one synthetic contraction (m x k times k x n, batch
+// entries, seeded values) through the FP64 kernel (route 0, ctas_per_sm CTAs per SM) or the
+// tensor-core kernel (route 1, `slices` digit planes).  Allocates and frees its own buffers.
+extern "C" int ht_tune_time_gemm(int m, int n, int k, int batch, int route, int slices, int ctas_per_sm, int reps,
+                                 double* ms_out) {
+  if (m < 1 || n < 1 || k < 1 || batch < 1 || reps < 1 || !ms_out || (route != 0 && route != 1)) return HT_ERR_ARG;
+  if (route == 1 && (slices < 2 || slices > 4)) return HT_ERR_ARG;
+  if (route == 0 && (ctas_per_sm < 1 || ctas_per_sm > 32)) return HT_ERR_ARG;
+  const size_t na = (size_t)m * k * batch, nb = (size_t)k * n * batch, nc = (size_t)m * n * batch;
+  double *A = nullptr, *B = nullptr, *Cm = nullptr;
+  GemmDesc* dd = nullptr;
+  int* err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = HT_OK;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HT_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaMalloc(&A, na * sizeof(double)) != cudaSuccess || cudaMalloc(&B, nb * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Cm, nc * sizeof(double)) != cudaSuccess || cudaMalloc(&dd, sizeof(GemmDesc)) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    rc = HT_ERR_NOMEM;
+  } else {
+    // values in [-1, 1) from a byte pattern (their size does not change the timing)
+    if (cudaMemset(A, 0x3f, na * sizeof(double)) != cudaSuccess || cudaMemset(B, 0xbf, nb * sizeof(double)) != cudaSuccess ||
+        cudaMemset(err, 0, sizeof(int)) != cudaSuccess)
+      rc = HT_ERR_CUDA;
+    GemmDesc g;
+    g.A = A; g.B = B; g.C = Cm; g.colscale = nullptr;
+    g.sA = (long long)m * k; g.sB = (long long)k * n; g.sC = (long long)m * n;
+    g.m = m; g.n = n; g.k = k; g.lda = m; g.ldb = k; g.ldc = m;
+    g.batch = batch; g.tA = 0; g.tB = 0; g.alpha = 1.0; g.beta = 0.0;
+    if (rc == HT_OK && cudaMemcpy(dd, &g, sizeof(g), cudaMemcpyHostToDevice) != cudaSuccess) rc = HT_ERR_CUDA;
+    if (rc == HT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = HT_ERR_CUDA;
+    auto launch = [&]() -> cudaError_t {
+      return route == 1 ? htg_launch_gemm_tc(dd, 1, sms, slices, 0, nullptr, 1, 0, err, 0)
+                        : htg_launch_gemm(dd, 1, sms * ctas_per_sm, 0, nullptr, 1, 0, 0);
+    };
+    if (rc == HT_OK) {
+      for (int w = 0; w < 2 && rc == HT_OK; ++w)
+        if (launch() != cudaSuccess) rc = HT_ERR_CUDA;
+      if (rc == HT_OK && cudaEventRecord(e0, 0) != cudaSuccess) rc = HT_ERR_CUDA;
+      for (int r = 0; r < reps && rc == HT_OK; ++r)
+        if (launch() != cudaSuccess) rc = HT_ERR_CUDA;
+      float ms = 0.f;
+      if (rc == HT_OK && (cudaEventRecord(e1, 0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = HT_ERR_CUDA;
+      int h = 0;
+      if (rc == HT_OK && cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = HT_ERR_CUDA;
+      if (rc == HT_OK && h != 0) rc = h;
+      if (rc == HT_OK) *ms_out = (double)ms / reps;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(Cm);
+  cudaFree(dd);
+  cudaFree(err);
+  return rc;
 }

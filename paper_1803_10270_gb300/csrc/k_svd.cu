@@ -99,9 +99,10 @@ __host__ __device__ inline long long svdc_smem_doubles(int p, int q, int cl) {
   return ncol * (long long)(p + q) + ncol + p + 8;
 }
 
-// whether the cluster form takes a p x q node factor (the one-CTA kernel skips exactly these)
-__host__ __device__ inline bool svdc_takes(int p, int q, int cl, long long cap_doubles) {
-  return cl > 0 && p >= SVDC_MIN_P && p <= SVDC_MAXQ && q >= 1 && q <= SVDC_MAXQ &&
+// whether the cluster form takes a p x q node factor (the one-CTA kernel skips exactly these);
+// min_p: the width from which factors go to the cluster form (SVDC_MIN_P unless tuned)
+__host__ __device__ inline bool svdc_takes(int p, int q, int cl, long long cap_doubles, int min_p) {
+  return cl > 0 && p >= min_p && p <= SVDC_MAXQ && q >= 1 && q <= SVDC_MAXQ &&
          svdc_smem_doubles(p, q, cl) <= cap_doubles;
 }
 
@@ -216,135 +217,15 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
   }
 }
 
-// FP32 phase of the cluster form: the same round-robin one-sided rotations on an FP32 copy of the
-// columns (N32: q entries, V32: p entries, ld = q + p floats per column, CTA j mod cl holding
-// column j) scaled by 2^sh, with the FP32 rounding floor, the discard-level skip and the test
-// |a.b| > tol32 |a||b|.  FP32 instructions issue 60 times faster than FP64 ones on this GPU, so the
-// sweeps that take the columns from arbitrary to nearly orthogonal cost little; the FP64 sweeps
-// that follow start from off-diagonal couplings near tol32 and converge quadratically.
-template <int KQ>
-__device__ void svdc_sweeps32(cg::cluster_group& cluster, float* col, float* nrm, double* flag, int p, int q, int cl,
-                              float floor2, float skip_abs, float tol) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int me = (int)cluster.block_rank();
-  const int ld = q + p;
-  const int p2 = p + (p & 1), npairs = p2 / 2;
-  __shared__ int rot_sh32;
-  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-    if (tid == 0) rot_sh32 = 0;
-    __syncthreads();
-    for (int round = 0; round < p2 - 1; ++round) {
-      for (int pi = me + cl * wid; pi < npairs; pi += cl * CNW) {
-        int a, b;
-        rr_pair(pi, round, p, p2, &a, &b);
-        if (a < 0) continue;
-        float* ca = cluster.map_shared_rank(col + (long long)(a / cl) * ld, a % cl);
-        float* cb = cluster.map_shared_rank(col + (long long)(b / cl) * ld, b % cl);
-        float* na = cluster.map_shared_rank(nrm + a / cl, a % cl);
-        float* nb = cluster.map_shared_rank(nrm + b / cl, b % cl);
-        const float al = *na, be = *nb;
-        if (!(al > floor2 && be > floor2 && (al > skip_abs || be > skip_abs))) continue;
-        float xa[KQ], xb[KQ];
-        float ga = 0.f;
-#pragma unroll
-        for (int k = 0; k < KQ; ++k) {
-          const int i = lane + 32 * k;
-          xa[k] = (i < q) ? ca[i] : 0.f;
-          xb[k] = (i < q) ? cb[i] : 0.f;
-          ga = fmaf(xa[k], xb[k], ga);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        if (!(fabsf(ga) > (tol * sqrtf(al)) * sqrtf(be))) continue;
-        const float zf = (be - al) / (2.0f * ga);
-        const float azf = fabsf(zf);
-        const float t = (azf > 1e18f) ? 0.5f / zf : copysignf(1.0f, zf) / (azf + sqrtf(fmaf(zf, zf, 1.0f)));
-        const float c = rsqrtf(fmaf(t, t, 1.0f)), sn = c * t;
-        float sa = 0.f, sb = 0.f;
-#pragma unroll
-        for (int k = 0; k < KQ; ++k) {
-          const int i = lane + 32 * k;
-          const float x = c * xa[k] - sn * xb[k];
-          const float y = sn * xa[k] + c * xb[k];
-          sa = fmaf(x, x, sa);
-          sb = fmaf(y, y, sb);
-          if (i < q) {
-            ca[i] = x;
-            cb[i] = y;
-          }
-        }
-        float* va = ca + q;
-        float* vb = cb + q;
-        for (int i = lane; i < p; i += 32) {
-          const float x = va[i], y = vb[i];
-          va[i] = c * x - sn * y;
-          vb[i] = sn * x + c * y;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sa += __shfl_xor_sync(0xffffffffu, sa, o);
-          sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        }
-        if (lane == 0) {
-          *na = sa;
-          *nb = sb;
-          rot_sh32 = 1;
-        }
-      }
-      cluster.sync();
-    }
-    if (tid == 0) *flag = rot_sh32 ? 1.0 : 0.0;
-    cluster.sync();
-    const int any = __syncthreads_or(tid < cl ? (*cluster.map_shared_rank(flag, tid) != 0.0) : 0);
-    cluster.sync();
-    if (!any) break;
-  }
-}
-
-// One Newton-Schulz step V <- V (3 I - V^T V) / 2 on the FP64 V parts of the columns (p entries at
-// offset q of each column), which squares the departure of V from orthogonality: column s of the
-// result is 1.5 v_s - 0.5 sum_j v_j (v_j . v_s), every v_j read where it lives; the new columns go
-// to tmp (p doubles per local column) and replace V after a cluster barrier.  One warp per column.
-__device__ void svdc_newton_schulz(cg::cluster_group& cluster, double* col, double* tmp, int p, int q, int cl,
-                                   double* myflops) {
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int me = (int)cluster.block_rank();
-  const int ld = q + p, ncol = (p + cl - 1) / cl;
-  for (int s = wid; s < ncol; s += CNW) {
-    const int js = s * cl + me;
-    if (js >= p) continue;
-    const double* vs = col + (long long)s * ld + q;
-    double* out = tmp + (long long)s * p;
-    for (int i = lane; i < p; i += 32) out[i] = 1.5 * vs[i];
-    __syncwarp();
-    for (int j = 0; j < p; ++j) {
-      const double* vj = cluster.map_shared_rank(col + (long long)(j / cl) * ld + q, j % cl);
-      double d = 0.0;
-      for (int i = lane; i < p; i += 32) d = fma(vj[i], vs[i], d);
-      d = -0.5 * warp_sum(d);
-      for (int i = lane; i < p; i += 32) out[i] = fma(d, vj[i], out[i]);
-    }
-    if (lane == 0) *myflops += 4.0 * p * p;
-  }
-  cluster.sync();   // every column read before any is replaced
-  for (int s = wid; s < ncol; s += CNW) {
-    if (s * cl + me >= p) continue;
-    double* v = col + (long long)s * ld + q;
-    const double* src = tmp + (long long)s * p;
-    for (int i = lane; i < p; i += 32) v[i] = src[i];
-  }
-  cluster.sync();
-}
-
 __global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __restrict__ descs, long long cap_doubles,
-                                                             double* flops) {
+                                                             double* flops, int min_p) {
   cg::cluster_group cluster = cg::this_cluster();
   const int cl = (int)cluster.num_blocks();
   const int me = (int)cluster.block_rank();
   const SvdDesc D = descs[blockIdx.x / cl];
   const int p = D.p, q = D.q;
   // the same answer in every CTA of the cluster, so either all of them return here or none
-  if (!svdc_takes(p, q, cl, cap_doubles)) return;
+  if (!svdc_takes(p, q, cl, cap_doubles, min_p)) return;
   extern __shared__ double smem[];
   const int ncol = (p + cl - 1) / cl, ld = q + p;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -394,78 +275,6 @@ __global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __re
   const double floor2 = EPS * EPS * fro;
   const double skip_abs = D.skip2 * fro / (double)p;
   double myflops = 0.0;
-  // FP32 phase when its copy fits beside the FP64 columns (the same answer in every CTA): after
-  // it, V is made orthogonal in FP64 (two Newton-Schulz steps) and N = M V is formed in FP64, so
-  // the FP64 sweeps below start from nearly orthogonal columns
-  const long long need64 = svdc_smem_doubles(p, q, cl);
-  const long long reg32 = ((long long)ncol * ld + 1) / 2 > (long long)ncol * p ? ((long long)ncol * ld + 1) / 2
-                                                                                : (long long)ncol * p;
-  if (p > 1 && amax > 0.0 && need64 + reg32 + ncol + 2 <= cap_doubles) {
-    float* col32 = (float*)(smem + need64);          // later the Newton-Schulz buffer (doubles)
-    float* nrm32 = (float*)(smem + need64 + reg32);
-    for (int e = tid; e < ncol * ld; e += CNT) {
-      const int sc = e / ld, i = e - sc * ld, j = sc * cl + me;
-      float v = 0.f;
-      if (j < p) {
-        bool ok;
-        v = (i < q) ? htg_d2f_shift(col[e], sh_e, &ok) : ((i - q == j) ? 1.0f : 0.0f);
-      }
-      col32[e] = v;
-    }
-    __syncthreads();
-    for (int sc = wid; sc < ncol; sc += CNW) {
-      float ss = 0.f;
-      for (int i = lane; i < q; i += 32) ss = fmaf(col32[(long long)sc * ld + i], col32[(long long)sc * ld + i], ss);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-      if (lane == 0) nrm32[sc] = ss;
-    }
-    cluster.sync();
-    bool ok1, ok2;
-    const float fro32 = htg_d2f_shift(fro, 2 * sh_e, &ok1);
-    const float skip32 = htg_d2f_shift(skip_abs, 2 * sh_e, &ok2);
-    const float floor32 = 16.0f * 3.55e-15f * fro32;    // (4 eps32)^2 |M 2^sh|_F^2
-    const float tol32 = 4.0f * 5.96e-8f * (float)htg_max(htg_max(p, q), 8);
-    switch ((q + 31) / 32) {
-#define SVDC32_CASE(K) \
-  case K: svdc_sweeps32<K>(cluster, col32, nrm32, red + 2, p, q, cl, floor32, ok2 ? skip32 : 0.f, tol32); break;
-      SVDC32_CASE(1) SVDC32_CASE(2) SVDC32_CASE(3) SVDC32_CASE(4) SVDC32_CASE(5) SVDC32_CASE(6) SVDC32_CASE(7)
-      SVDC32_CASE(8) SVDC32_CASE(9) SVDC32_CASE(10) SVDC32_CASE(11) SVDC32_CASE(12) SVDC32_CASE(13)
-      SVDC32_CASE(14) SVDC32_CASE(15)
-#undef SVDC32_CASE
-      default: break;
-    }
-    // V in FP64 from V32, made orthogonal to FP64 accuracy
-    for (int e = tid; e < ncol * p; e += CNT) {
-      const int sc = e / p, i = e - sc * p;
-      if (sc * cl + me < p) col[(long long)sc * ld + q + i] = htg_f2d(col32[(long long)sc * ld + q + i]);
-    }
-    cluster.sync();
-    double* tmp = smem + need64;
-    svdc_newton_schulz(cluster, col, tmp, p, q, cl, &myflops);
-    svdc_newton_schulz(cluster, col, tmp, p, q, cl, &myflops);
-    // N = M V: row i of column s is P(:, i) . v_s (P column-major, rows contiguous)
-    for (int sc = wid; sc < ncol; sc += CNW) {
-      const int js = sc * cl + me;
-      if (js >= p) continue;
-      double* cs = col + (long long)sc * ld;
-      const double* vs = cs + q;
-      double ss = 0.0;
-      for (int i = 0; i < q; ++i) {
-        const double* Pi = D.P + (long long)D.ldp * i;
-        double d = 0.0;
-        for (int c = lane; c < p; c += 32) d = fma(Pi[c], vs[c], d);
-        d = warp_sum(d);
-        ss = fma(d, d, ss);
-        if (lane == 0) cs[i] = d;
-      }
-      if (lane == 0) {
-        nrm[sc] = ss;
-        myflops += 2.0 * p * q + 2.0 * q;
-      }
-    }
-    cluster.sync();
-  }
   switch ((q + 31) / 32) {
 #define SVDC_CASE(K) \
   case K: svdc_sweeps<K>(cluster, col, nrm, red + 2, p, q, cl, floor2, skip_abs, 2 * sh_e, &myflops); break;
@@ -497,12 +306,13 @@ __global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __re
 }
 
 __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ descs, long long inst_stride,
-                                                long long smem_doubles, double* flops, int cl, long long cl_cap) {
+                                                long long smem_doubles, double* flops, int cl, long long cl_cap,
+                                                int min_p) {
   // batched launches: instance blockIdx.y reads its own descriptor list, inst_stride bytes on
   const SvdDesc D = ((const SvdDesc*)((const char*)descs + inst_stride * blockIdx.y))[blockIdx.x];
   const int p = D.p, q = D.q;
   if (p <= 0) return;
-  if (svdc_takes(p, q, cl, cl_cap)) return;   // the cluster form's launch takes this factor
+  if (svdc_takes(p, q, cl, cl_cap, min_p)) return;   // the cluster form's launch takes this factor
   const int mr = htg_max(p, q);
   extern __shared__ double smem[];
   // layout (doubles): M64 mr*p | N mr*p | G p*p | V p*p | T p*p | nrm p | M32 mr*p/2 | V32 p*p/2
@@ -785,7 +595,7 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
 }  // namespace
 
 bool htg_svd_cluster_used(const SvdClusterCfg* clu, int count, int pmax) {
-  return clu && clu->cl > 0 && count == 1 && pmax >= SVDC_MIN_P;
+  return clu && clu->cl > 0 && count == 1 && pmax >= clu->min_p;
 }
 
 SvdClusterCfg htg_svd_cluster_setup(int device) {
@@ -840,8 +650,8 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
   const int cl = use_cl ? clu->cl : 0;
   long long cl_cap = 0;
   if (use_cl) {
-    // the whole opt-in shared memory: the FP64 columns plus, where it fits, their FP32 copy
-    cl_cap = clu->cap_doubles;
+    cl_cap = svdc_smem_doubles(htg_min(pmax, SVDC_MAXQ), htg_min(htg_max(qmax, 1), SVDC_MAXQ), cl);
+    if (cl_cap > clu->cap_doubles) cl_cap = clu->cap_doubles;
   }
   // shared memory sized for p, q <= 40 (about 77 KB dynamic + 21 KB static: two CTAs per SM in
   // batched launches); larger node factors work in their global buffers
@@ -859,8 +669,9 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr[dev] = true;
   }
+  const int min_p = clu ? clu->min_p : SVDC_MIN_P;
   svd_kernel<<<dim3(ndesc, count), NT, smem, s>>>(descs_dev, inst_stride, (long long)(smem / sizeof(double)), flops,
-                                                   cl, cl_cap);
+                                                   cl, cl_cap, min_p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !use_cl) return e;
   cudaLaunchConfig_t cfg = {};
@@ -875,5 +686,5 @@ cudaError_t htg_launch_svd(const SvdDesc* descs_dev, int ndesc, int use_smem, in
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, svd_cluster_kernel, descs_dev, cl_cap, flops);
+  return cudaLaunchKernelEx(&cfg, svd_cluster_kernel, descs_dev, cl_cap, flops, min_p);
 }

@@ -54,7 +54,8 @@ class ht_op(C.Structure):
 
 class ht_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int * HT_MAXD), ("cap", C.c_int), ("max_terms", C.c_int),
-                ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int), ("mixed_slices", C.c_int)]
+                ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int), ("mixed_slices", C.c_int),
+                ("tc_min_work", C.c_longlong), ("gemm_ctas_per_sm", C.c_int), ("svd_cluster_min_cols", C.c_int)]
 
 
 _EXPORTS = {
@@ -93,6 +94,7 @@ _EXPORTS = {
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
     "ht_selftest_fastmath": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ht_tune_time_gemm": (C.c_int, [C.c_int] * 8 + [C.POINTER(C.c_double)]),
     "ht_selftest_gemm_mixed": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                          C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double,
                                          C.c_void_p, C.c_int, C.c_longlong, C.c_longlong, C.c_longlong,
@@ -176,7 +178,10 @@ class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
     def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
-                 device: int = 0, tree: int = 0, mixed_slices: int = 0):
+                 device: int = 0, tree: int = 0, mixed_slices: int = 0, tuning: dict | None = None):
+        """tuning: values for the ht_config tuning fields (tc_min_work, gemm_ctas_per_sm,
+        svd_cluster_min_cols); None takes the tuning cache of this device when one exists
+        (paper_1803_10270_gb300.tune), {} the library defaults."""
         lib = load()
         cfg = ht_config()
         cfg.d = d
@@ -188,6 +193,13 @@ class Context:
         cfg.device = device
         cfg.tree = tree
         cfg.mixed_slices = mixed_slices
+        if tuning is None:
+            from paper_1803_10270_gb300 import tune as _tune
+            tuning = _tune.cached(device, max(3, max_terms + 2) * cap)
+        for k in ("tc_min_work", "gemm_ctas_per_sm", "svd_cluster_min_cols"):
+            if k in tuning:
+                setattr(cfg, k, int(tuning[k]))
+        self.tuning = dict(tuning)
         self.cfg = cfg
         self.d, self.n, self.cap, self.device = d, list(n), cap, device
         self.ptr = C.c_void_p()
@@ -565,6 +577,16 @@ def selftest_gemm_mixed(A, B, C, m, n, k, lda, ldb, ldc, tA=0, tB=0, alpha=1.0, 
     return int(load().ht_selftest_gemm_mixed(m, n, k, C_ptr(A), lda, tA, C_ptr(B), ldb, tB, C_ptr(C), ldc,
                                              float(alpha), float(beta), C_ptr(colscale), batch, sA, sB, sC,
                                              slices, _stream_ptr(stream)))
+
+
+def tune_time_gemm(m: int, n: int, k: int, batch: int = 1, route: int = 0, slices: int = 4, ctas_per_sm: int = 4,
+                   reps: int = 20) -> float:
+    """Mean time (ms) of one synthetic contraction through the FP64 (route 0) or the tensor-core
+    (route 1) kernel, for the autotuner."""
+    ms = C.c_double(0.0)
+    _check(load().ht_tune_time_gemm(m, n, k, batch, route, slices, ctas_per_sm, reps, C.byref(ms)),
+           "ht_tune_time_gemm")
+    return float(ms.value)
 
 
 def C_ptr(t):
