@@ -449,6 +449,30 @@ def step_ab2(u: HT, u_prev: HT, A: list, rel_tol: float, rmax: int):
     return truncate(v, rel_tol, rmax)
 
 
+def step_ab2_split(u: HT, u_prev: HT, A: list, rel_tol: float, rmax: int, variant: str = "argument"):
+    """eq. AB2_ evaluated as a sequence of simple tensor operations, each followed by a rank
+    reduction (Section 3.2, the paragraph after eq. AB2_), with S = dt L (A[i] = dt L_i):
+
+    'argument':   w = T(3 u - u_prev);  v = T(S w);  u_next = T(u + v/2)
+                  (the argument of L reduced first, then L w reduced again);
+    'difference': w = T(u - u_prev);  a = T(S u);  b = T(S w);  u_next = T(u + a + b/2)
+                  (the passage's literal w_{n+1} = f_{n+1} - f_n; dt/2 L (3u - u_prev) = S u + S w / 2).
+
+    Every T is the HSVD truncation with the same tolerance and cap.  Returns (u_next, reports)."""
+    if variant == "argument":
+        w, r1 = truncate(add(3.0, u, -1.0, u_prev), rel_tol, rmax)
+        v, r2 = truncate(apply_kron_sum_poly(w, A, (0.0, 1.0)), rel_tol, rmax)
+        un, r3 = truncate(add(1.0, u, 0.5, v), rel_tol, rmax)
+        return un, (r1, r2, r3)
+    if variant == "difference":
+        w, r1 = truncate(add(1.0, u, -1.0, u_prev), rel_tol, rmax)
+        a, r2 = truncate(apply_kron_sum_poly(u, A, (0.0, 1.0)), rel_tol, rmax)
+        b, r3 = truncate(apply_kron_sum_poly(w, A, (0.0, 1.0)), rel_tol, rmax)
+        un, r4 = truncate(add(1.0, u, 1.0, add(1.0, a, 0.5, b)), rel_tol, rmax)
+        return un, (r1, r2, r3, r4)
+    raise ValueError(variant)
+
+
 def step_heun2(u: HT, alphas: list, factors: list, dt: float, rel_tol: float, rmax: int):
     """Heun's two-stage RK2 with a truncation after each stage (general separable L):
 
