@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="launch every kernel per step instead of a CUDA graph")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-tune", dest="tune", action="store_false",
+                   help="skip the autotuner (contexts then use the library defaults or an earlier cache)")
     p.add_argument("--batched", type=int, default=256, help="instances of the ragged batched workload (0: skip)")
     p.add_argument("--no-d12", dest="d12", action="store_false", help="skip the 12-D n=128 line")
     p.add_argument("--line", default="all",
@@ -307,7 +309,7 @@ def run_gpu(args):
         elif args.line == "d12":
             res = run_d12(G, torch, flush, args.steps, warm, precision=prec)
         elif args.line == "ab2":
-            res = run_ab2(G, torch, flush, args.steps, warm)
+            res = run_ab2_all(G, torch, flush, args.steps, warm)
         elif args.line == "varcoef":
             res = run_varcoef(G, torch, flush, args.steps, warm)
         elif args.line == "tt":
@@ -323,6 +325,8 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
+    # ---- autotuner (launch parameters measured on this GPU, cached for every context below)
+    tuning = run_tuner(local) if args.tune else None
     W = Workload(G, local, prec)
     stream = torch.cuda.current_stream()
 
@@ -411,7 +415,7 @@ def run_gpu(args):
         del g1
 
     # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
-    ab2 = run_ab2(G, torch, flush, args.steps, args.warmup)
+    ab2 = run_ab2_all(G, torch, flush, args.steps, args.warmup)
 
     # ---- FP64 against the tensor-core form: the HT route of this workload, the 12-D workload
     #      (100 RK2 steps), the full-size kinetic workload and the ragged batch, each in both forms
@@ -464,6 +468,9 @@ def run_gpu(args):
             out["cn"] = cn
         if kinetic is not None:
             out["kinetic"] = kinetic
+        if tuning is not None:
+            out["tuning"] = tuning
+            out["tuning"]["tuned_vs_default"] = tuned_vs_default(G, torch, flush)
         if mixed is not None:
             out["mixed"] = {k: {kk: vv for kk, vv in v.items() if kk != "fp64"} for k, v in mixed.items()}
             for k, v in out["mixed"].items():
@@ -475,6 +482,26 @@ def run_gpu(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_tuner(device: int) -> dict:
+    """The package's autotuner (paper_1803_10270_gb300.tune): measured values, written to its cache."""
+    from paper_1803_10270_gb300 import tune
+    res = tune.tune(device, write=True)
+    return {k: res[k] for k in ("tc_min_work", "gemm_ctas_per_sm_by_kc", "svd_cluster_min_cols", "seconds")}
+
+
+def tuned_vs_default(G, torch, flush) -> dict:
+    """The kinetic line (both forms) and the 12-D line with the library defaults (tuning={}) beside
+    the tuned values (the cache the autotuner wrote)."""
+    out = {}
+    for name, fn, kw in (("kinetic_fp64", run_kinetic, dict(steps=5, warmup=3, precision=0)),
+                         ("kinetic_mixed", run_kinetic, dict(steps=5, warmup=3, precision=1, slices=4)),
+                         ("d12_fp64", run_d12, dict(steps=50, warmup=3))):
+        d = fn(G, torch, flush, tuning={}, profile=False, **kw)["value"]
+        t = fn(G, torch, flush, tuning=None, profile=False, **kw)["value"]
+        out[name] = {"default": d, "tuned": t, "unit": "steps/s", "speedup": t / d}
+    return out
 
 
 def run_mixed_lines(G, torch, flush, args) -> dict:
@@ -517,9 +544,26 @@ def ic_nodes(tree, fac, np):
     return nodes
 
 
-def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
-    """HT steps/s of the AB2 scheme (ht_step_ab2) on the configuration-2 advection workload: an
-    RK2 start step, then AB2 steps, the timed ones graph-captured with L2 flushed between them."""
+def run_ab2_all(G, torch, flush, steps: int, warmup: int) -> dict:
+    """The AB2 line: the exact-sum step (ht_step_ab2) and the two split evaluations of Section 3.2
+    (ht_step_ab2_split), each timed; the cancellation study is the relative distance of each split
+    result from the exact-sum result after the same steps (on the device, HT inner products)."""
+    res, c0, s0 = run_ab2(G, torch, flush, steps, warmup, keep=True)
+    res["split"] = {}
+    for variant, name in ((0, "argument"), (1, "difference")):
+        r, c, sv = run_ab2(G, torch, flush, steps, warmup, variant=variant, keep=True)
+        r["rel_dist_from_exact_sum_final"] = ht_rel_diff(G, torch, c0, sv, s0)
+        r["rel_dist_resolution"] = 1.5e-8
+        res["split"][name] = r
+        c.close()
+    c0.close()
+    return res
+
+
+def run_ab2(G, torch, flush, steps: int, warmup: int, variant: int | None = None, keep: bool = False):
+    """HT steps/s of the AB2 scheme on the configuration-2 advection workload (ht_step_ab2, or
+    ht_step_ab2_split with `variant`): an RK2 start step, then AB2 steps, the timed ones
+    graph-captured with L2 flushed between them.  keep: also return the context and the state."""
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
     case = advection_case(D, N, seed_offset=1)
@@ -530,14 +574,22 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
     u.upload(nodes)
     up.upload(nodes)
     op = G.advection_op(case.c, case.h)
+    def ab2(stream=None):
+        if variant is None:
+            G.ht_step_ab2(ctx, u, up, op, case.dt, TOL, RMAX, stream=stream)
+        else:
+            G.ht_step_ab2_split(ctx, u, up, op, case.dt, TOL, RMAX, variant, stream=stream)
+
     G.ht_step(ctx, u, op, case.dt, TOL, RMAX)       # u_1; u_prev = u_0
     for _ in range(max(warmup - 1, 0)):
-        G.ht_step_ab2(ctx, u, up, op, case.dt, TOL, RMAX)
+        ab2()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     graph = torch.cuda.CUDAGraph()
+    l0 = ctx.launches()
     with torch.cuda.graph(graph):
-        G.ht_step_ab2(ctx, u, up, op, case.dt, TOL, RMAX, stream=torch.cuda.current_stream())
+        ab2(stream=torch.cuda.current_stream())
+    per_step = ctx.launches() - l0
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for i in range(steps):
         flush.zero_()
@@ -550,10 +602,16 @@ def run_ab2(G, torch, flush, steps: int, warmup: int) -> dict:
     ms_max, value = aggregate_replicas(ms, steps)
     ranks = u.ranks()
     del graph
+    res = {"workload": "6-D advection n=64 HT route, AB2 (eq. AB2_) after one RK2 start step, "
+                       "r_max 32, tol 1e-8", "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
+           "steps": steps, "ht_ranks_final": ranks, "cuda_graph": True, "gpu_launches_per_step": per_step,
+           "form": "exact sum, one truncation" if variant is None else
+                   ("split: w = T(3u - u_prev), v = T(dt L w), T(u + v/2)" if variant == 0 else
+                    "split: w = T(u - u_prev), T(u + T(dt L u) + T(dt L w)/2)")}
+    if keep:
+        return res, ctx, u
     ctx.close()
-    return {"workload": "6-D advection n=64 HT route, AB2 (eq. AB2_) after one RK2 start step, "
-                        "r_max 32, tol 1e-8", "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
-            "steps": steps, "ht_ranks_final": ranks, "cuda_graph": True}
+    return res
 
 
 D12_WORKLOAD = ("12-D advection n=128: depth-4 tree, seeded separable rank-3 initial condition, "
@@ -566,7 +624,7 @@ TT_WORKLOAD = ("6-D advection n=64 HT route in tensor-train form (the linear dim
 
 def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128, cap: int = 64,
             n_terms: int = 3, seed_offset: int = 4, tree: int = 0, workload: str = None, precision: int = 0,
-            slices: int = 0, keep: bool = False, profile: bool = True):
+            slices: int = 0, keep: bool = False, profile: bool = True, tuning: dict | None = None):
     """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
     64), or another advection workload and tree: the timed steps graph-captured, L2 flushed
     between them; then a profiled stretch of the same length for the per-class roofline.  keep:
@@ -575,7 +633,8 @@ def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128,
     import numpy as np
     from paper_1803_10270_gb300.inputs import advection_case
     case = advection_case(d, n, n_terms=n_terms, seed_offset=seed_offset)
-    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree, precision=precision, mixed_slices=slices)
+    ctx = G.Context(d, [n] * d, cap=cap, max_terms=1, tree=tree, precision=precision, mixed_slices=slices,
+                    tuning=tuning)
     u = G.HTTensor(d, [n] * d, cap, tree=tree)
     u.upload(ic_nodes(u.tree, case.ic_factors(), np))
     op = G.advection_op(case.c, case.h)
@@ -683,7 +742,7 @@ KIN_WORKLOAD = ("linearised 6-D kinetic equation: n=64 per variable, x periodic 
 
 
 def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0,
-                keep: bool = False, profile: bool = True):
+                keep: bool = False, profile: bool = True, tuning: dict | None = None):
     """HT HEUN2 steps/s of the full-size kinetic workload (node ranks grow to about 60 within ten
     steps, so the step cost grows too: the line reports steps warmup+1 .. warmup+steps); then a
     profiled stretch for the per-class roofline; keep as in run_d12."""
@@ -691,7 +750,7 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
     from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
     kc = kinetic_case(64)
     w0, F0 = kinetic_ic(kc)
-    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5, precision=precision, mixed_slices=slices)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5, precision=precision, mixed_slices=slices, tuning=tuning)
     u = G.HTTensor(6, [64] * 6, 64)
     u.upload(ic_nodes(u.tree, [F * (w0[None, :] if i == 0 else 1.0) for i, F in enumerate(F0)], np))
     kop = G.KineticOp(kc)

@@ -148,7 +148,8 @@ typedef struct ht_config {
   long long tc_min_work;   /* HT_PREC_MIXED: contractions of at least this many multiply-adds
                               (m n k batch, decided on the device per contraction) run on the tensor
                               cores, smaller ones on the FP64 CUDA cores; -1: all on the tensor cores */
-  int gemm_ctas_per_sm;    /* CTAs per SM of the FP64 contraction launches, 1..32 (default 4) */
+  int gemm_ctas_per_sm;    /* CTAs per SM of the FP64 contraction launches, 1..32 (default 16, or 8
+                              for truncation inputs below rank 96) */
   int svd_cluster_min_cols;/* node factors at least this wide use the thread-block-cluster SVD,
                               32..480 (default 128) */
 } ht_config;
@@ -271,6 +272,27 @@ int ht_batch_step(ht_batch* b, const ht_op* const* Ls, const double* dts, const 
  * The context needs a truncation input of 4 cap (max_terms >= 2).  Errors as ht_step. */
 int ht_step_ab2(ht_ctx* ctx, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, double dt, double rel_tol,
                 int rmax, void* stream);
+
+/* Addition of HT tensors (one of the three operations an explicit step needs, Section 3.2):
+ * out = a u + b w exactly, ranks adding (k_u + k_w at every node), block-diagonal transfer
+ * tensors.  out->cap >= u->cap + w->cap; out must not share buffers or rank arrays with u or w.
+ * Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
+int ht_add(ht_ctx* ctx, double a, const ht_tensor* u, double b, const ht_tensor* w, ht_tensor* out, void* stream);
+
+typedef enum ht_ab2_split {
+  HT_AB2_SPLIT_ARGUMENT = 0,    /* w = T(3u - u_prev); v = T(dt L w); u_next = T(u + v/2) */
+  HT_AB2_SPLIT_DIFFERENCE = 1   /* w = T(u - u_prev); a = T(dt L u); b = T(dt L w); u_next = T(u + a + b/2) */
+} ht_ab2_split;
+
+/* The AB2 step (eq. AB2_) evaluated as a sequence of simple tensor operations, each followed by
+ * its own HSVD truncation (rel_tol, rmax), as the paragraph after eq. AB2_ (Section 3.2) proposes
+ * to save memory: HT_AB2_SPLIT_ARGUMENT reduces the argument 3u - u_prev of L, then L of it;
+ * HT_AB2_SPLIT_DIFFERENCE takes the passage's w = f_{n+1} - f_n literally (dt/2 L (3u - u_prev) =
+ * dt L u + dt L w / 2).  Kronecker-sum operators; in place, u_prev <- u and u <- u_next, as
+ * ht_step_ab2 (which forms the exact sum and truncates once).  The context needs a truncation
+ * input of 3 cap.  Errors as ht_step_ab2. */
+int ht_step_ab2_split(ht_ctx* ctx, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, double dt, double rel_tol,
+                      int rmax, int variant, void* stream);
 
 /* Exact HT form of a CP tensor (footnote to eq. HTD: a CP tensor is the diagonal case):
  * leaves = factors, interior B = delta_abc, root = diag(weights).  out->cap >= x->rank. */

@@ -134,7 +134,8 @@ __host__ __device__ inline long long htg_max_ll(long long a, long long b) { retu
 
 // HT_PREC_MIXED: contractions of at least this many multiply-adds go to the tensor cores unless the
 // context is given a tuned threshold (ht_config.tc_min_work)
-#define HTG_TC_MIN_WORK_DEFAULT (1ll << 22)
+// (the autotuner's crossover on GB300 against the FP64 kernel at 16 CTAs per SM: about 2^26)
+#define HTG_TC_MIN_WORK_DEFAULT (1ll << 26)
 
 // ------------------------------------------------------- FP64 special values ---
 // Measured on GB300 (dependent chains): FP64 FMA 64 cycles, FP64 sqrt 674, divide / rsqrt

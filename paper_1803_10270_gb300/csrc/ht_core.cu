@@ -1017,7 +1017,10 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   c->svd_smem = ((2 * Kc * Kc + Kc) * sizeof(double) <= 200 * 1024) ? 1 : 0;
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg->device);
-  c->gemm_grid = htg_max(1, sms) * (cfg->gemm_ctas_per_sm ? cfg->gemm_ctas_per_sm : 4);
+  // FP64 contraction CTAs per SM: the autotuner's measurement on GB300 (small tiles of 64 threads
+  // over many SMs hide the FP64 pipe's latency: 16 per SM were 1.4-2.4x faster than 4 on the
+  // contractions of contexts with Kc >= 96, 8 per SM best below)
+  c->gemm_grid = htg_max(1, sms) * (cfg->gemm_ctas_per_sm ? cfg->gemm_ctas_per_sm : (c->Kc >= 96 ? 16 : 8));
   c->sms = htg_max(1, sms);
   c->slices = (cfg->precision == HT_PREC_MIXED) ? (cfg->mixed_slices ? cfg->mixed_slices : 4) : 0;
   if (c->slices) {
@@ -1403,6 +1406,89 @@ extern "C" int ht_step_ab2(ht_ctx* c, ht_tensor* u, ht_tensor* u_prev, const ht_
   st = copy_tensor_to(c, u, u_prev->node, u_prev->rank, s);   // u_prev <- u (u is read no more)
   if (st != HT_OK) return st;
   return run_truncate(c, app, c->Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s);
+}
+
+// block-diagonal sum a * in0 + b * in1 (identity factors, root coefficients a, b)
+static void sum_op(const ht_ctx* c, double a, double b, ApplyOp* op) {
+  memset(op, 0, sizeof(*op));
+  op->mode = HT_APPLY_L;
+  op->nb = 2;
+  op->src[0] = 0;
+  op->src[1] = 1;
+  op->coef[0] = a;
+  op->coef[1] = b;
+  for (int blk = 0; blk < 2; ++blk)
+    for (int i = 0; i < c->cfg.d; ++i) {
+      op->f[blk][i].kind = HT_F_STENCIL;   // identity: a width-0 stencil
+      op->f[blk][i].hw = 0;
+      op->f[blk][i].c[0] = 1.0;
+    }
+}
+
+extern "C" int ht_add(ht_ctx* c, double a, const ht_tensor* u, double b, const ht_tensor* w, ht_tensor* out,
+                      void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, w) || !tensor_matches(c, out)) return HT_ERR_ARG;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (out->node[t] == u->node[t] || out->node[t] == w->node[t]) return HT_ERR_ARG;
+  if (out->rank == u->rank || out->rank == w->rank) return HT_ERR_ARG;
+  if ((long long)u->cap + w->cap > out->cap) return HT_ERR_CAPACITY;
+  ApplyOp op;
+  sum_op(c, a, b, &op);
+  return launch_apply(c, op, view_of(u), view_of(w), view_of(out), htg_max(u->cap, w->cap), (cudaStream_t)stream);
+}
+
+extern "C" int ht_step_ab2_split(ht_ctx* c, ht_tensor* u, ht_tensor* u_prev, const ht_op* L, double dt,
+                                 double rel_tol, int rmax, int variant, void* stream) {
+  if (!c || !tensor_matches(c, u) || !tensor_matches(c, u_prev) || u->cap != u_prev->cap) return HT_ERR_ARG;
+  for (int t = 0; t < c->tree.nn; ++t)
+    if (u->node[t] == u_prev->node[t]) return HT_ERR_ARG;
+  if (u->rank == u_prev->rank) return HT_ERR_ARG;
+  if (rmax < 1 || rmax > u->cap || !(rel_tol >= 0.0)) return HT_ERR_ARG;
+  if (variant != HT_AB2_SPLIT_ARGUMENT && variant != HT_AB2_SPLIT_DIFFERENCE) return HT_ERR_ARG;
+  if (u->cap > c->cap || 3LL * u->cap > c->Kc) return HT_ERR_CAPACITY;
+  ApplyOp opS;   // S x = dt L x exactly: the blocks [X, S X] with root coefficients (0, 1)
+  if (!build_apply(c, L, dt, HT_APPLY_RK2POLY, &opS)) return HT_ERR_ARG;
+  opS.npoly = 1;
+  opS.deg[0] = 1;
+  opS.pc[0][0] = 0.0;
+  opS.pc[0][1] = 1.0;
+  opS.pc[0][2] = 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const HtView uv = view_of(u), pv = view_of(u_prev);
+  const HtView app = view_ws(c, c->app, c->app_rank), stg = view_ws(c, c->stage, c->stage_rank);
+  const int cap = u->cap, Kc = c->Kc;
+  ApplyOp opA;
+  int st;
+#define HTG_TRY(x) do { st = (x); if (st != HT_OK) return st; } while (0)
+  if (variant == HT_AB2_SPLIT_ARGUMENT) {
+    // w = T(3u - u_prev) -> stage;  v = T(S w) -> u_prev;  u <- T(u + v/2), u_prev <- u
+    sum_op(c, 3.0, -1.0, &opA);
+    HTG_TRY(launch_apply(c, opA, uv, pv, app, cap, s));
+    HTG_TRY(run_truncate(c, app, Kc, stg, rel_tol, rmax, nullptr, 0, nullptr, s));
+    HTG_TRY(launch_apply(c, opS, stg, stg, app, cap, s));
+    HTG_TRY(run_truncate(c, app, Kc, pv, rel_tol, rmax, nullptr, 0, nullptr, s));
+    sum_op(c, 1.0, 0.5, &opA);
+    HTG_TRY(launch_apply(c, opA, uv, pv, app, cap, s));
+  } else {
+    // w = T(u - u_prev) -> u_prev;  a = T(S u) -> stage;  b = T(S w) -> u_prev;
+    // u <- T(u + (a + b/2)), u_prev <- u
+    sum_op(c, 1.0, -1.0, &opA);
+    HTG_TRY(launch_apply(c, opA, uv, pv, app, cap, s));
+    HTG_TRY(run_truncate(c, app, Kc, pv, rel_tol, rmax, nullptr, 0, nullptr, s));
+    HTG_TRY(launch_apply(c, opS, uv, uv, app, cap, s));
+    HTG_TRY(run_truncate(c, app, Kc, stg, rel_tol, rmax, nullptr, 0, nullptr, s));
+    HTG_TRY(launch_apply(c, opS, pv, pv, app, cap, s));
+    HTG_TRY(run_truncate(c, app, Kc, pv, rel_tol, rmax, nullptr, 0, nullptr, s));
+    sum_op(c, 1.0, 0.5, &opA);
+    HTG_TRY(launch_apply(c, opA, stg, pv, app, cap, s));      // a + b/2 (ranks <= 2 rmax)
+    sum_op(c, 1.0, 1.0, &opA);
+    HTG_TRY(launch_apply(c, opA, uv, app, stg, 2 * cap, s));  // u + (a + b/2) (ranks <= 3 rmax)
+  }
+  HTG_TRY(copy_tensor_to(c, u, u_prev->node, u_prev->rank, s));   // u_prev <- u
+  const HtView& fin = (variant == HT_AB2_SPLIT_ARGUMENT) ? app : stg;
+  HTG_TRY(run_truncate(c, fin, Kc, uv, rel_tol, rmax, nullptr, 0, nullptr, s));
+#undef HTG_TRY
+  return HT_OK;
 }
 
 // ---------------------------------------------------------------- batches -----

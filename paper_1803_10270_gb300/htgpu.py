@@ -82,6 +82,10 @@ _EXPORTS = {
     "ht_step_ab2": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.POINTER(ht_op), C.c_double,
                               C.c_double, C.c_int, C.c_void_p]),
     "ht_from_cp": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_tensor), C.c_void_p]),
+    "ht_add": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(ht_tensor), C.c_double, C.POINTER(ht_tensor),
+                         C.POINTER(ht_tensor), C.c_void_p]),
+    "ht_step_ab2_split": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.POINTER(ht_op),
+                                    C.c_double, C.c_double, C.c_int, C.c_int, C.c_void_p]),
     "ht_mass": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
     "ht_inner": (C.c_int, [C.c_void_p, C.POINTER(ht_tensor), C.POINTER(ht_tensor), C.c_void_p, C.c_void_p]),
     "cp_apply_rk2": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
@@ -509,6 +513,20 @@ def ht_step_ab2(ctx: Context, u: HTTensor, u_prev: HTTensor, op: ht_op, dt: floa
                 stream=None):
     _check(load().ht_step_ab2(ctx.ptr, C.byref(u.struct), C.byref(u_prev.struct), C.byref(op), dt, rel_tol, rmax,
                               _stream_ptr(stream)), "ht_step_ab2")
+
+
+HT_AB2_SPLIT_ARGUMENT, HT_AB2_SPLIT_DIFFERENCE = 0, 1
+
+
+def ht_add(ctx: Context, a: float, u: HTTensor, b: float, w: HTTensor, out: HTTensor, stream=None):
+    _check(load().ht_add(ctx.ptr, float(a), C.byref(u.struct), float(b), C.byref(w.struct), C.byref(out.struct),
+                         _stream_ptr(stream)), "ht_add")
+
+
+def ht_step_ab2_split(ctx: Context, u: HTTensor, u_prev: HTTensor, op: ht_op, dt: float, rel_tol: float, rmax: int,
+                      variant: int = HT_AB2_SPLIT_ARGUMENT, stream=None):
+    _check(load().ht_step_ab2_split(ctx.ptr, C.byref(u.struct), C.byref(u_prev.struct), C.byref(op), dt, rel_tol,
+                                    rmax, variant, _stream_ptr(stream)), "ht_step_ab2_split")
 
 
 def ht_from_cp(ctx: Context, x: CPTensor, out: HTTensor, stream=None):

@@ -88,7 +88,7 @@ def tune(device: int = 0, slices: int = 4, reps: int = 10, write: bool = True, v
     G.load()
     t0 = time.time()
     # ---- FP64 CTAs per SM, per capacity bucket
-    ctas_opts = (2, 4, 8, 16)
+    ctas_opts = (4, 8, 16, 32)
     by_kc = {}
     timings = {}
     for kc in KC_BUCKETS:
@@ -99,10 +99,11 @@ def tune(device: int = 0, slices: int = 4, reps: int = 10, write: bool = True, v
         best = min(tot, key=tot.get)
         by_kc[str(kc)] = best
         timings[f"fp64_ctas_kc{kc}"] = {str(c): tot[c] for c in ctas_opts}
-    # ---- tensor-core crossover (FP64 side at the default 4 CTAs per SM)
+    # ---- tensor-core crossover (FP64 side at its tuned CTA count of the largest bucket)
+    c_big = by_kc[str(KC_BUCKETS[-1])]
     pts = []
     for (m, n, k, b) in _shapes(384):
-        t64 = _time(G, m, n, k, b, 0, slices, 4, reps)
+        t64 = _time(G, m, n, k, b, 0, slices, c_big, reps)
         ttc = _time(G, m, n, k, b, 1, slices, 4, reps)
         pts.append((m * n * k * b, t64, ttc, (m, n, k, b)))
     pts.sort()
