@@ -342,8 +342,13 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
 // split as (1 / |x|) (1 / (|x0| + |x|)) so that it does not overflow for tiny columns) and
 // updates its own rows: v.c = x.c - alpha c_j, c <- c - tau (v.c) v.  R is the rows j of the
 // updated matrix and the alphas.  Barriers are per matrix, by arrival words, each wait bounded
-// (HT_ERR_TIMEOUT, and the CTA returns).
+// (HT_ERR_TIMEOUT, and the CTA returns).  A CTA whose row block (its rows x k doubles) fits the
+// launch's dynamic shared memory keeps it there for the whole reduction, so the column passes
+// (dot products and updates) never leave the SM; otherwise the block lives in the matrix's
+// scratch buffer in global memory (an ncu capture of that form measured 76x the matrix's bytes
+// of DRAM traffic: one pass over the trailing part per column).
 constexpr int QRC_NT = 256;
+constexpr int QRC_SMEM_BYTES = 200 * 1024;
 constexpr long long QRC_TIMEOUT_CYCLES = 400000000LL;   // about 0.2 s
 
 __device__ bool coop_barrier(unsigned* flags, int G, int g, unsigned seq, int* err) {
@@ -374,14 +379,20 @@ __device__ bool coop_barrier(unsigned* flags, int G, int g, unsigned seq, int* e
   return ok_sh != 0;
 }
 
-__global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int G, QrCoopWs w) {
+__global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int G, QrCoopWs w,
+                                                        int smem_doubles) {
   const int d = blockIdx.x / G, g = blockIdx.x % G;
   const QrDesc q = descs[d];
   const int m = q.m, k = q.k;
   if (m <= 0 || k <= 0 || !qr_coop_eligible(m, k)) return;   // uniform over the matrix's CTAs
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = QRC_NT / 32;
   const int mb = (m + G - 1) / G, r0 = htg_min(m, g * mb), r1 = htg_min(m, r0 + mb);
-  double* S = q.scratch;                     // m x k, ld m
+  // the CTA's rows [r0, r1): in shared memory (ld mb) when they fit, else in the scratch buffer
+  // (ld m); S points at row r0, so element (i, c) of the matrix is S[(i - r0) + ld c]
+  extern __shared__ double qsm[];
+  const bool local = (long long)mb * k <= (long long)smem_doubles;
+  const long long ld = local ? mb : m;
+  double* S = local ? qsm : q.scratch + r0;
   double* part = w.part + ((long long)d * G + g) * w.kmax;
   double* part0 = w.part + (long long)d * G * w.kmax;
   double* tot = w.tot + (long long)d * w.kmax;
@@ -395,24 +406,24 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   __shared__ double sh_v0, sh_alpha;
   for (long long e = tid; e < (long long)(r1 - r0) * k; e += QRC_NT) {
     const int i = r0 + (int)(e % (r1 - r0)), c = (int)(e / (r1 - r0));
-    S[i + (long long)m * c] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
+    S[(i - r0) + ld * c] = q.tA ? q.A[c + (long long)q.lda * i] : q.A[i + (long long)q.lda * c];
   }
   unsigned seq = 0;
   const int rmax = htg_min(m, k);
   for (int j = 0; j < rmax; ++j) {
     __syncthreads();
     const int i0 = htg_max(j, r0);
-    const double* x = S + (long long)m * j;
+    const double* x = S + ld * j;
     for (int c = j + wid; c < k; c += nw) {
-      const double* cc = S + (long long)m * c;
+      const double* cc = S + ld * c;
       double sdot = 0.0;
-      for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i], cc[i], sdot);
+      for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i - r0], cc[i - r0], sdot);
       sdot = warp_sum(sdot);
       if (lane == 0) part[c] = sdot;
     }
     double* rowj = rowj2 + (long long)(j & 1) * w.kmax;
     if (j >= r0 && j < r1)
-      for (int c = j + tid; c < k; c += QRC_NT) rowj[c] = S[j + (long long)m * c];
+      for (int c = j + tid; c < k; c += QRC_NT) rowj[c] = S[(j - r0) + ld * c];
     if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
     for (int c = j + g + G * wid; c < k; c += G * nw) {
       double t = 0.0;
@@ -452,8 +463,8 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
       __syncthreads();
       for (long long e = tid; e < (long long)(r1 - i0) * cn; e += QRC_NT) {
         const int i = i0 + (int)(e % (r1 - i0)), c = j + 1 + c0 + (int)(e / (r1 - i0));
-        const double vi = (i == j) ? v0 : x[i];
-        S[i + (long long)m * c] = fma(-wc[c - (j + 1 + c0)], vi, S[i + (long long)m * c]);
+        const double vi = (i == j) ? v0 : x[i - r0];
+        S[(i - r0) + ld * c] = fma(-wc[c - (j + 1 + c0)], vi, S[(i - r0) + ld * c]);
       }
       __syncthreads();
     }
@@ -465,7 +476,7 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
     if (r >= rmax) continue;
     double val = 0.0;
     if (c == r) val = diag[r];
-    else if (c > r) val = S[r + (long long)m * c];
+    else if (c > r) val = S[(r - r0) + ld * c];
     if (q.tR) q.R[c + (long long)q.ldr * r] = val;
     else q.R[r + (long long)q.ldr * c] = val;
   }
@@ -501,15 +512,21 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   const int G = htg_max(2, htg_min(coop->gmax, nsm / ndesc));
   e = cudaMemsetAsync(coop->bar, 0, (size_t)ndesc * G * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
+  static bool cattr[64] = {false};
+  if (dev < 0 || dev >= 64 || !cattr[dev]) {
+    e = cudaFuncSetAttribute(qr_coop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QRC_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) cattr[dev] = true;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ndesc * G);
   cfg.blockDim = dim3(QRC_NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = QRC_SMEM_BYTES;
   cfg.stream = s;
   cudaLaunchAttribute lattr[1];
   lattr[0].id = cudaLaunchAttributeCooperative;
   lattr[0].val.cooperative = 1;
   cfg.attrs = lattr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, G, *coop);
+  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, G, *coop, (int)(QRC_SMEM_BYTES / sizeof(double)));
 }
