@@ -431,7 +431,7 @@ def run_gpu(args):
     # ---- the same HT workload in tensor-train form (linear dimension tree)
     tt = run_tt(G, torch, flush, args.steps, max(args.warmup, 3)) if args.d12 else None
 
-    # ---- the full-size kinetic workload, HEUN2, 5 steps after 3 (timed in run_mixed_lines)
+    # ---- the full-size kinetic workload, HEUN2, steps 46-50 (timed in run_mixed_lines)
     kinetic = mixed["kinetic"]["fp64"] if mixed else None
 
     # ---- implicit Crank-Nicolson step in CP format (ALS), kinetic operator
@@ -579,7 +579,7 @@ def run_mixed_lines(G, torch, flush, args) -> dict:
     out = {"adv6d_ht": mixed_vs_fp64(G, torch, flush, run_d12, steps=args.steps, warmup=warm, d=D, n=N, cap=RMAX,
                                      n_terms=2, seed_offset=1, workload=ADV_HT_WORKLOAD),
            "d12": mixed_vs_fp64(G, torch, flush, run_d12, steps=100, warmup=warm),
-           "kinetic": mixed_vs_fp64(G, torch, flush, run_kinetic, steps=5, warmup=3)}
+           "kinetic": mixed_vs_fp64(G, torch, flush, run_kinetic, steps=5, warmup=45)}
     if args.batched > 0:
         out["batched"] = mixed_vs_fp64(G, torch, flush, run_batched, count=args.batched,
                                        steps=min(args.steps, 20), warmup=warm)
@@ -805,7 +805,7 @@ def run_cn(G, torch, flush, steps: int, warmup: int) -> dict:
 
 KIN_WORKLOAD = ("linearised 6-D kinetic equation: n=64 per variable, x periodic [0,2pi)^3, v in [-6,6]^3, "
                 "nu=1, seeded initial condition M(v)(1 + 0.1 prod sin x_i) + rank-4 perturbation, 5-term operator, "
-                "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6; steps 4..3+K from t=0")
+                "HEUN2 (truncation after each stage), HT r_max 64, tol 1e-6; steps W+1..W+K from t=0 (W warm-up steps)")
 
 
 def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0,

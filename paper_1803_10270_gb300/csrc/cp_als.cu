@@ -675,15 +675,18 @@ __device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const
 }
 
 // Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage is optional.
-__host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z) {
+// Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage and the Q_k / W stage are optional.
+__host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z,
+                                                             bool with_q) {
   const long long ld = nmax | 1, K = 3LL * r0;
   const long long base = 2LL * r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
                          (nmax > NT ? nmax : NT) + (long long)d * r * r + (long long)d * r + K + ld * r;
-  return base + (with_z ? ld * K : 0);
+  return base + (with_z ? ld * K : 0) + (with_q ? K * K + K * r : 0);
 }
 
 __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
-                                                            int sweeps, int* err, int zs_smem, double* flops) {
+                                                            int sweeps, int* err, int zs_smem, int qs_smem,
+                                                            double* flops) {
   const int b = blockIdx.x, tid = threadIdx.x;
   const unsigned int nb = gridDim.x;
   const int d = a.d, r = a.r, r0 = pa.r0, K = 3 * r0;
@@ -700,7 +703,9 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   double* Gs = pb + htg_max(NT, nmax);       // d x r x r: copy of the stored Grams Ghat_j
   double* Cs = Gs + (long long)d * r * r;    // d x r: copy of their row scales (G_j = diag(Cs_j) Ghat_j)
   double* Pb = Cs + (long long)d * r;        // 3 r0: Q_k w_b of this CTA's column
-  double* Xs = Pb + K;                       // odd_ld(nmax) x r: a staged factor
+  double* Qs = Pb + K;                       // 3 r0 x 3 r0: staged Q_k (phase B, when qs_smem)
+  double* Ws = Qs + (qs_smem ? (long long)K * K : 0);   // 3 r0 x r: staged W (phase B, when qs_smem)
+  double* Xs = Ws + (qs_smem ? (long long)K * r : 0);   // odd_ld(nmax) x r: a staged factor
   double* Zs = Xs + (long long)odd_ld(nmax) * r;   // odd_ld(nmax) x 3 r0: Z_k (when zs_smem)
   __shared__ unsigned short tri[TRI_MAX];
   __shared__ double red[HT_MAXD + 32];
@@ -878,10 +883,21 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         const double* Wb = w.Hh + (long long)K * b;
         for (int i = tid; i < K; i += blockDim.x) stage_async1(ys + i, Wb + i);
         asm volatile("cp.async.commit_group;" ::: "memory");
+        if (gs && qs_smem) {
+          // Q_k and W for the Gram column, in flight while X~_k[:, b] is formed
+          const double* Qg = w.Q + (long long)k * 9 * w.rcap * w.rcap;
+          for (int e = tid; e < K * K + K * r; e += blockDim.x) {
+            if (e < K * K) stage_async1(Qs + e, Qg + e);
+            else stage_async1(Ws + (e - K * K), w.Hh + (e - K * K));
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+          stage_wait();
+        }
         // the old column (convergence sums) is fetched now, consumed after the contraction
         double* col = a.X[k] + (long long)n * b;
         const double old_pre = (tid < n) ? col[tid] : 0.0;
-        stage_wait();
         __syncthreads();
         rows_dot(Zk, ldz, ys, n, K, pb, xs);
         const double lam_old = a.lam[b];
@@ -934,15 +950,17 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           // and X~_k^T X_k[:, b] = W^T P / |X~_b|, stored as column b of Ghat_k with the row scales
           // 1 / |X~_j| kept beside it (cinv), so the Gram G_k needs no pass over all of X_k
           double* Hc = w.H + (long long)k * w.rycap * w.rcap + (long long)K * b;
-          const double* Qk = w.Q + (long long)k * 9 * w.rcap * w.rcap;
           const double sc = scol;
+          stage_wait();
+          __syncthreads();
+          const double* Qk = qs_smem ? Qs : w.Q + (long long)k * 9 * w.rcap * w.rcap;
+          const double* Wk = qs_smem ? Ws : w.Hh;
           cols_dot([&](int o) { return Qk + (long long)K * o; }, ys, K, K, pb, [&](int o, double v) {
             Pb[o] = v;
             Hc[o] = v * sc;
           });
           double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
-          cols_dot([&](int o) { return (const double*)(w.Hh + (long long)K * o); }, Pb, K, r, pb,
-                   [&](int o, double v) { Gc[o] = v * sc; });
+          cols_dot([&](int o) { return Wk + (long long)K * o; }, Pb, K, r, pb, [&](int o, double v) { Gc[o] = v * sc; });
           if (tid == 0) w.cinv[(long long)k * w.rcap + b] = sc;
         } else {
           double* dst = w.Xold + (long long)k * nmax * w.rcap + (long long)n * b;
@@ -1153,10 +1171,13 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   // one cooperative launch: CTA b owns factor column b (and row b of the solve)
   const int nblk = htg_max(a.r, r0);
   const size_t nm = (size_t)w->nmax;
-  // stage Z_k in shared memory when it fits
-  const size_t with_z = (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, true) * sizeof(double);
-  const int zs_smem = (with_z <= 160 * 1024) ? 1 : 0;
-  size_t smem = zs_smem ? with_z : (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, false) * sizeof(double);
+  // stage Q_k and W (Gauss-Seidel), then Z_k, in shared memory as far as they fit
+  auto need = [&](bool z, bool q) { return (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, z, q) * sizeof(double); };
+  const size_t lim = 200 * 1024;
+  const bool gsv = (variant == CP_ALS_GS);
+  const int qs_smem = (gsv && need(false, true) <= lim) ? 1 : 0;
+  const int zs_smem = (need(true, qs_smem != 0) <= lim) ? 1 : 0;
+  size_t smem = need(zs_smem != 0, qs_smem != 0);
   // Claim all of each SM's shared memory: the HT route's kernels, launched beside this one on
   // another stream, then land on other SMs (an SM partition's FP64 pipe shared with their
   // warps lengthens this kernel's latency-bound chains: measured 0.96 ms alone, 1.06 ms side by
@@ -1190,7 +1211,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_persistent, a, pa, *w, (const double*)x_old->weight, sweeps,
-                                      htg_ctx_err(c), zs_smem, htg_prof_flops(c, KC_CPSOLVE));
+                                      htg_ctx_err(c), zs_smem, qs_smem, htg_prof_flops(c, KC_CPSOLVE));
   htg_prof_end(c, KC_CPSOLVE, s);
   ++launches;
   if (e0 != cudaSuccess || e1 != cudaSuccess) {

@@ -280,3 +280,32 @@ def test_kinetic6d_n64_full_size_two_heun2_steps(G):
         assert g.ranks() == reps[1].ranks, f"step {step}"
         assert rel_err(from_gpu(g, u.tree), u) < TOL64, f"step {step}"
     ctx.close()
+
+
+def test_kinetic6d_n64_late_window_one_step(G):
+    """The kinetic workload at full size after 45 HEUN2 steps on the GPU (node ranks near 61, node
+    factors 300-370 columns wide: the cluster SVD near its limit, the cooperative QR on the stage
+    sums): one more step from that state on the GPU and in the oracle, ranks and tensors compared
+    (the bench's kinetic window is steps 46-50)."""
+    from oracle.problems import kinetic_terms
+    from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
+    kc = kinetic_case(64)
+    w, F = kinetic_ic(kc)
+    u0 = OH.from_cp(w, F)
+    alphas, factors = kinetic_terms(kc)
+    kop = G.KineticOp(kc)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5)
+    g = to_gpu(G, u0, 64)
+    for _ in range(45):
+        G.ht_step(ctx, g, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2)
+    sync()
+    ctx.check()
+    state = from_gpu(g, u0.tree)
+    assert max(g.ranks()[1:]) >= 55
+    ref, reps = OH.step_heun2(state, alphas, factors, kc.dt, 1e-6, 64)
+    G.ht_step(ctx, g, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2)
+    sync()
+    ctx.check()
+    assert g.ranks() == reps[1].ranks
+    assert rel_err(from_gpu(g, u0.tree), ref) < TOL64
+    ctx.close()
