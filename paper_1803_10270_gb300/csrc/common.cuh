@@ -241,8 +241,6 @@ struct CpWs {
   double* Z;       // HT_MAXD x nmax x 3 rcap   powers [X, A X, A^2 X] of the step's input
   double* acc2;    // 2 doubles: per-mode sums of the convergence measure (persistent kernel)
   unsigned int* bar;   // 64 words: grid barrier arrival sequence numbers, one per CTA
-  double* Q;       // HT_MAXD x (3 rcap)^2   Z_k^T Z_k of the step's input (persistent kernel)
-  double* cinv;    // HT_MAXD x rcap         row scales of the stored G_k: G_k = diag(cinv_k) Ghat_k
   int rcap, rycap, nmax;
 };
 CpWs* htg_ctx_cp(ht_ctx* c);

@@ -336,13 +336,11 @@ struct PowArgs {
 // factor column b (row b of the r0 x r blocks in the solve phase); phases are separated by
 // a grid barrier:
 //   0a  powers Z_j^(p) of x_old (CTA b < r0), mu <- weights of x_old, normalise column b of x
-//   0b  column b of G_j = X_j^T X_j and M_j = Z_j^T X_j for every j; columns of Q_j = Z_j^T Z_j
+//   0b  column b of G_j = X_j^T X_j and M_j = Z_j^T X_j for every j
 //   per mode k:  A  Gamma_k (LDL^T) and row b of W = Hs Gamma_k^-1; CTA 0 records the
 //                   previous mode's convergence measure                      (CTA b < r0)
-//                B  column b of X~_k = Z_k W, convergence sums, X_k[:, b], lam_b, and from
-//                   P = Q_k w_b: M_k[:, b] = P / |X~_b| and column b of G_k up to the row
-//                   scales 1 / |X~_j| (W^T P / |X~_b|), so G_k needs no pass over all of X_k and
-//                   no third barrier
+//                B  column b of X~_k = Z_k W, convergence sums, X_k[:, b], lam_b and M_k[:, b]
+//                C  column b of G_k
 // The launch is cooperative (all CTAs resident), and every barrier wait is bounded: past the
 // limit the kernel records HT_ERR_TIMEOUT in the error word and returns.
 // ---------------------------------------------------------------------------
@@ -675,18 +673,15 @@ __device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const
 }
 
 // Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage is optional.
-// Shared memory (doubles) of cp_als_rk2_persistent; the Z_k stage and the Q_k / W stage are optional.
-__host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z,
-                                                             bool with_q) {
+__host__ __device__ inline long long persistent_smem_doubles(int r, int r0, int d, int nmax, bool with_z) {
   const long long ld = nmax | 1, K = 3LL * r0;
   const long long base = 2LL * r * r + 4LL * r + nmax + (nmax > K ? nmax : K) + 3LL * d * r +
-                         (nmax > NT ? nmax : NT) + (long long)d * r * r + (long long)d * r + K + ld * r;
-  return base + (with_z ? ld * K : 0) + (with_q ? K * K + K * r : 0);
+                         (nmax > NT ? nmax : NT) + (long long)d * r * r + ld * r;
+  return base + (with_z ? ld * K : 0);
 }
 
 __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
-                                                            int sweeps, int* err, int zs_smem, int qs_smem,
-                                                            double* flops) {
+                                                            int sweeps, int* err, int zs_smem, double* flops) {
   const int b = blockIdx.x, tid = threadIdx.x;
   const unsigned int nb = gridDim.x;
   const int d = a.d, r = a.r, r0 = pa.r0, K = 3 * r0;
@@ -700,12 +695,8 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   double* ys = xs + nmax;                    // max(nmax, 3 r0)
   double* Mv = ys + htg_max(nmax, K);        // d x 3 x r: copy of the M_j^(p) rows of this CTA's lp
   double* pb = Mv + 3 * d * r;               // max(NT, nmax): partial sums of split dot products
-  double* Gs = pb + htg_max(NT, nmax);       // d x r x r: copy of the stored Grams Ghat_j
-  double* Cs = Gs + (long long)d * r * r;    // d x r: copy of their row scales (G_j = diag(Cs_j) Ghat_j)
-  double* Pb = Cs + (long long)d * r;        // 3 r0: Q_k w_b of this CTA's column
-  double* Qs = Pb + K;                       // 3 r0 x 3 r0: staged Q_k (phase B, when qs_smem)
-  double* Ws = Qs + (qs_smem ? (long long)K * K : 0);   // 3 r0 x r: staged W (phase B, when qs_smem)
-  double* Xs = Ws + (qs_smem ? (long long)K * r : 0);   // odd_ld(nmax) x r: a staged factor
+  double* Gs = pb + htg_max(NT, nmax);       // d x r x r: copy of the Grams G_j
+  double* Xs = Gs + (long long)d * r * r;    // odd_ld(nmax) x r: a staged factor
   double* Zs = Xs + (long long)odd_ld(nmax) * r;   // odd_ld(nmax) x 3 r0: Z_k (when zs_smem)
   __shared__ unsigned short tri[TRI_MAX];
   __shared__ double red[HT_MAXD + 32];
@@ -755,23 +746,9 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
   if (b < r) normalise_column(a, b, !gs, red);
   if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
-  // ---------------- 0b: column b of G_j and M_j for every j (row scales 1: exact Grams), and the
-  //                   columns of Q_j = Z_j^T Z_j (K x K, ld K), spread over the CTAs
+  // ---------------- 0b: column b of G_j and M_j for every j
   if (b < r)
-    for (int j = 0; j < d; ++j) {
-      gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
-      if (tid == 0) w.cinv[(long long)j * w.rcap + b] = 1.0;
-    }
-  if (gs)
-    for (int idx = b; idx < d * K; idx += nb) {
-      const int j = idx / K, c = idx - (idx / K) * K, n = a.n[j];
-      const double* Zj = w.Z + (long long)j * nmax * 3 * w.rcap;
-      __syncthreads();
-      for (int i = tid; i < n; i += blockDim.x) xs[i] = Zj[i + (long long)n * c];
-      __syncthreads();
-      double* Qc = w.Q + (long long)j * 9 * w.rcap * w.rcap + (long long)K * c;
-      cols_dot([&](int o) { return Zj + (long long)n * o; }, xs, n, K, pb, [&](int o, double v) { Qc[o] = v; });
-    }
+    for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
   if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
   const double* mu = w.wold;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
@@ -790,15 +767,12 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         for (int j = j0; j < j1; ++j) {
           const double* Gg = w.G + (long long)j * w.rcap * w.rcap;
           const double* Hg = w.H + (long long)j * w.rycap * w.rcap + lp;
-          const double* Cg = w.cinv + (long long)j * w.rcap;
-          for (int e = tid; e < nG + nM + r; e += blockDim.x) {
+          for (int e = tid; e < nG + nM; e += blockDim.x) {
             if (e < nG) {
               stage_async1(Gs + j * nG + e, Gg + e);
-            } else if (e < nG + nM) {
+            } else {
               const int f = e - nG, pp = f / r, l = f - pp * r;
               stage_async1(Mv + (j * 3 + pp) * r + l, Hg + pp * r0 + (long long)K * l);
-            } else {
-              stage_async1(Cs + j * r + (e - nG - nM), Cg + (e - nG - nM));
             }
           }
         }
@@ -814,10 +788,9 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         } else if (wid % 4 != 3) {
           const int gt = (wid - wid / 4) * 32 + (tid & 31);
           for (int e = gt; e < nG; e += (NT / 32 - 2) * 32) {
-            const int i = e % r;
             double v = 1.0;
             for (int j = 0; j < d; ++j)
-              if (j != k) v *= Gs[j * nG + e] * Cs[j * r + i];
+              if (j != k) v *= Gs[j * nG + e];
             Lm[e] = v;
           }
         } else if (b == 0 && tid == 96) {
@@ -841,18 +814,17 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
             for (int i = 0; i < r; ++i) {
               double v = 1.0;
               for (int j = 0; j < d; ++j)
-                if (j != k) v *= Gs[j * nG + i + r * i] * Cs[j * r + i];
+                if (j != k) v *= Gs[j * nG + i + r * i];
               tr += v;
             }
             shift = 1e-14 * tr / r;
           }
           __syncthreads();
           for (int e = tid; e < nG; e += blockDim.x) {
-            const int i = e % r;
             double v = 1.0;
             for (int j = 0; j < d; ++j)
-              if (j != k) v *= Gs[j * nG + e] * Cs[j * r + i];
-            Lm[e] = v + ((i == e / r) ? shift : 0.0);
+              if (j != k) v *= Gs[j * nG + e];
+            Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
           }
           rk2_rhs_row(Mv, d, k, r, mu[lp], hs, tid, blockDim.x);
           __syncthreads();
@@ -883,21 +855,10 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         const double* Wb = w.Hh + (long long)K * b;
         for (int i = tid; i < K; i += blockDim.x) stage_async1(ys + i, Wb + i);
         asm volatile("cp.async.commit_group;" ::: "memory");
-        if (gs && qs_smem) {
-          // Q_k and W for the Gram column, in flight while X~_k[:, b] is formed
-          const double* Qg = w.Q + (long long)k * 9 * w.rcap * w.rcap;
-          for (int e = tid; e < K * K + K * r; e += blockDim.x) {
-            if (e < K * K) stage_async1(Qs + e, Qg + e);
-            else stage_async1(Ws + (e - K * K), w.Hh + (e - K * K));
-          }
-          asm volatile("cp.async.commit_group;" ::: "memory");
-          asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-          stage_wait();
-        }
         // the old column (convergence sums) is fetched now, consumed after the contraction
         double* col = a.X[k] + (long long)n * b;
         const double old_pre = (tid < n) ? col[tid] : 0.0;
+        stage_wait();
         __syncthreads();
         rows_dot(Zk, ldz, ys, n, K, pb, xs);
         const double lam_old = a.lam[b];
@@ -946,22 +907,10 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
             col[row] = v;
           }
           __syncthreads();
-          // With X~_k = Z_k W and Q_k = Z_k^T Z_k: P = Q_k w_b, M_k[:, b] = Z_k^T X_k[:, b] = P / |X~_b|
-          // and X~_k^T X_k[:, b] = W^T P / |X~_b|, stored as column b of Ghat_k with the row scales
-          // 1 / |X~_j| kept beside it (cinv), so the Gram G_k needs no pass over all of X_k
+          // M_k[:, b] = Z_k^T X_k[:, b]
           double* Hc = w.H + (long long)k * w.rycap * w.rcap + (long long)K * b;
-          const double sc = scol;
-          stage_wait();
-          __syncthreads();
-          const double* Qk = qs_smem ? Qs : w.Q + (long long)k * 9 * w.rcap * w.rcap;
-          const double* Wk = qs_smem ? Ws : w.Hh;
-          cols_dot([&](int o) { return Qk + (long long)K * o; }, ys, K, K, pb, [&](int o, double v) {
-            Pb[o] = v;
-            Hc[o] = v * sc;
-          });
-          double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
-          cols_dot([&](int o) { return Wk + (long long)K * o; }, Pb, K, r, pb, [&](int o, double v) { Gc[o] = v * sc; });
-          if (tid == 0) w.cinv[(long long)k * w.rcap + b] = sc;
+          cols_dot([&](int o) { return Zk + (long long)ldz * o; }, xs, n, K, pb,
+                   [&](int o, double v) { Hc[o] = v; });
         } else {
           double* dst = w.Xold + (long long)k * nmax * w.rcap + (long long)n * b;
           for (int row = tid; row < n; row += blockDim.x) dst[row] = xs[row];
@@ -969,6 +918,18 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
         }
       }
       if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
+      // ---------------- C: column b of G_k = X_k^T X_k (all columns of X_k are final)
+      if (gs && b < r) {
+        const int n = a.n[k];
+        const int ld = odd_ld(n);
+        stage_pad_async(Xs, ld, a.X[k], n, n, r);
+        stage_wait();
+        __syncthreads();
+        const double* xb = Xs + (long long)ld * b;
+        double* Gc = w.G + (long long)k * w.rcap * w.rcap + (long long)r * b;
+        cols_dot([&](int o) { return Xs + (long long)ld * o; }, xb, n, r, pb, [&](int o, double v) { Gc[o] = v; });
+      }
+      if (gs && !grid_barrier(w.bar, nb, ++bseq, err)) return;
     }
     if (!gs) {
       // damped Jacobi update of every column b, then refresh all Grams
@@ -982,27 +943,21 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
       }
       if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
       if (b < r)
-        for (int j = 0; j < d; ++j) {
-          gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
-          if (tid == 0) w.cinv[(long long)j * w.rcap + b] = 1.0;
-        }
+        for (int j = 0; j < d; ++j) gram_column(a, w, j, b, r0, true, xs, pb, zs_smem ? Xs : nullptr);
       if (!grid_barrier(w.bar, nb, ++bseq, err)) return;
     }
   }
   if (flops && b == 0 && tid == 0) {
-    // FP64 work of the structured algorithm per mode (each item once): Z_k W 2 n (3 r0) r, in the
-    // Gauss-Seidel form P = Q_k W 2 (3 r0)^2 r and W^T P 2 (3 r0) r^2 (the damped form: M_k
-    // 2 n (3 r0) r and the Grams 2 n r^2), right-hand sides 10 (d-1) r0 r, Gamma (d-2) r^2, LDL^T
-    // r^3 / 3, forward and back substitution for 3 r0 vectors 6 r0 r^2; once per launch Q_k
-    // 2 n (3 r0)^2 per dimension (Gauss-Seidel)
-    double f = 0.0, f0 = 0.0;
+    // FP64 work of the structured algorithm per mode (each item once): Gram of the new factor
+    // 2 n r^2, Z_k W and M_k 2 x 2 n (3 r0) r, right-hand sides 10 (d-1) r0 r, Gamma (d-2) r^2,
+    // LDL^T r^3 / 3, forward and back substitution for 3 r0 vectors 6 r0 r^2
+    double f = 0.0;
     for (int k = 0; k < d; ++k) {
-      const double n = a.n[k], rr = r, q0 = r0, K3 = 3.0 * r0;
-      f += 2.0 * n * K3 * rr + 10.0 * (d - 1) * q0 * rr + (d - 2) * rr * rr + rr * rr * rr / 3.0 + 6.0 * q0 * rr * rr;
-      f += gs ? (2.0 * K3 * K3 * rr + 2.0 * K3 * rr * rr) : (2.0 * n * K3 * rr + 2.0 * n * rr * rr);
-      if (gs) f0 += 2.0 * n * K3 * K3;
+      const double n = a.n[k], rr = r, q0 = r0;
+      f += 2.0 * n * rr * rr + 12.0 * n * q0 * rr + 10.0 * (d - 1) * q0 * rr + (d - 2) * rr * rr +
+           rr * rr * rr / 3.0 + 6.0 * q0 * rr * rr;
     }
-    atomicAdd(flops, f * sweeps + f0);
+    atomicAdd(flops, f * sweeps);
   }
   // the last mode's measure
   if (b == 0 && tid == 0 && sweeps > 0) {
@@ -1171,13 +1126,10 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   // one cooperative launch: CTA b owns factor column b (and row b of the solve)
   const int nblk = htg_max(a.r, r0);
   const size_t nm = (size_t)w->nmax;
-  // stage Q_k and W (Gauss-Seidel), then Z_k, in shared memory as far as they fit
-  auto need = [&](bool z, bool q) { return (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, z, q) * sizeof(double); };
-  const size_t lim = 200 * 1024;
-  const bool gsv = (variant == CP_ALS_GS);
-  const int qs_smem = (gsv && need(false, true) <= lim) ? 1 : 0;
-  const int zs_smem = (need(true, qs_smem != 0) <= lim) ? 1 : 0;
-  size_t smem = need(zs_smem != 0, qs_smem != 0);
+  // stage Z_k in shared memory when it fits
+  const size_t with_z = (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, true) * sizeof(double);
+  const int zs_smem = (with_z <= 160 * 1024) ? 1 : 0;
+  size_t smem = zs_smem ? with_z : (size_t)persistent_smem_doubles(a.r, r0, d, (int)nm, false) * sizeof(double);
   // Claim all of each SM's shared memory: the HT route's kernels, launched beside this one on
   // another stream, then land on other SMs (an SM partition's FP64 pipe shared with their
   // warps lengthens this kernel's latency-bound chains: measured 0.96 ms alone, 1.06 ms side by
@@ -1211,7 +1163,7 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_persistent, a, pa, *w, (const double*)x_old->weight, sweeps,
-                                      htg_ctx_err(c), zs_smem, qs_smem, htg_prof_flops(c, KC_CPSOLVE));
+                                      htg_ctx_err(c), zs_smem, htg_prof_flops(c, KC_CPSOLVE));
   htg_prof_end(c, KC_CPSOLVE, s);
   ++launches;
   if (e0 != cudaSuccess || e1 != cudaSuccess) {

@@ -857,7 +857,7 @@ static int trunc_input_cap(const ht_config* c) {
 }
 
 struct WsLayout {
-  size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[13], off_prof;
+  size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
   size_t off_coop[5];           // cooperative QR: part, tot, rowj, diag, bar (0 when not used)
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
@@ -891,11 +891,10 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
     const size_t rc = (size_t)c->cap, ry = rc * (size_t)htg_cp_terms(c->d);
     size_t nmax = 1;
     for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
-    const size_t cps[13] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
+    const size_t cps[11] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
                             HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1,
-                            HT_MAXD * nmax * 3 * rc, 4 + 32,    // acc2 (4 doubles) + 64 barrier words
-                            c->d * 9 * rc * rc, c->d * rc};     // Q_k = Z_k^T Z_k, row scales of G_k
-    for (int j = 0; j < 13; ++j) {
+                            HT_MAXD * nmax * 3 * rc, 4 + 32};   // acc2 (4 doubles) + 64 barrier words
+    for (int j = 0; j < 11; ++j) {
       W->off_cp[j] = off;
       off = align_up(off + cps[j] * sizeof(double));
     }
@@ -990,8 +989,6 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->cp.Z = (double*)(base + W.off_cp[9]);
     c->cp.acc2 = (double*)(base + W.off_cp[10]);
     c->cp.bar = (unsigned int*)(base + W.off_cp[10] + 4 * sizeof(double));
-    c->cp.Q = (double*)(base + W.off_cp[11]);
-    c->cp.cinv = (double*)(base + W.off_cp[12]);
     c->cp.rcap = cfg->cap;
     c->cp.rycap = cfg->cap * htg_cp_terms(cfg->d);
     int nmax = 1;
