@@ -117,7 +117,7 @@ __device__ inline int warp_sum_int(int v) {
 // one lane active as with 32).
 template <int KQ>
 __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm, double* flag, int p, int q, int cl,
-                            double floor2, double skip_abs, int sh2, double* myflops) {
+                            double floor2, double skip_abs, int sh2, float rnd2, double* myflops) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int me = (int)cluster.block_rank();
   const int ld = q + p;
@@ -158,6 +158,15 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
         const float alf = htg_d2f_shift(al, sh2, &oka), bef = htg_d2f_shift(be, sh2, &okb);
         const float gaf = htg_d2f_shift(ga, sh2, &okg);
         if (!(oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef))) continue;
+        // A pair with a column below the discard level (skip_abs > 0: ranks, not singular values,
+        // are wanted) moves T(u) by about |a.b| / max(|a|, |b|), the part of the small column along
+        // the large one; below 64 eps |P|_F (rnd2, squared and scaled) that is the rounding level of
+        // T(u), and the pair stops rotating.  Without this such pairs, coupled through the pairs of
+        // two sub-discard columns that never rotate, converged only linearly (a factor of about 0.7
+        // per sweep, up to the sweep limit, measured on the kinetic workload's factors).
+        if (rnd2 > 0.f && !(htg_dgt_nn(al, skip_abs) && htg_dgt_nn(be, skip_abs)) &&
+            gaf * gaf <= rnd2 * fmaxf(alf, bef))
+          continue;
         bool okd;
         const float df = htg_d2f_shift(be - al, sh2, &okd);
         const float zf = df / (2.0f * gaf);
@@ -274,10 +283,12 @@ __global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __re
   const int sh_e = (amax > 0.0) ? -ilogb(amax) : 0;
   const double floor2 = EPS * EPS * fro;
   const double skip_abs = D.skip2 * fro / (double)p;
+  bool okr;
+  const float rnd2 = (skip_abs > 0.0) ? htg_d2f_shift(4096.0 * EPS * EPS * fro, 2 * sh_e, &okr) : 0.f;
   double myflops = 0.0;
   switch ((q + 31) / 32) {
 #define SVDC_CASE(K) \
-  case K: svdc_sweeps<K>(cluster, col, nrm, red + 2, p, q, cl, floor2, skip_abs, 2 * sh_e, &myflops); break;
+  case K: svdc_sweeps<K>(cluster, col, nrm, red + 2, p, q, cl, floor2, skip_abs, 2 * sh_e, rnd2, &myflops); break;
     SVDC_CASE(1) SVDC_CASE(2) SVDC_CASE(3) SVDC_CASE(4) SVDC_CASE(5) SVDC_CASE(6) SVDC_CASE(7) SVDC_CASE(8)
     SVDC_CASE(9) SVDC_CASE(10) SVDC_CASE(11) SVDC_CASE(12) SVDC_CASE(13) SVDC_CASE(14) SVDC_CASE(15)
 #undef SVDC_CASE
