@@ -466,6 +466,8 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   __syncthreads();
   if (gl == 0 && gid == 0) myflops += 4.0 * p * p * p + 2.0 * mr * p * p + 2.0 * mr * p * p;
   // ---------------- phase 3: FP64 two-sided Jacobi on G (rotations also applied to V)
+  bool okr;
+  const float rnd2 = (skip_abs > 0.0) ? htg_d2f_shift(4096.0 * EPS * EPS * red2[0], sh2, &okr) : 0.f;
   const double TOL = EPS * (double)htg_max(mr, 8);
   const float TOL64F = htg_d2f(TOL);
   if (tid == 0) ract = 0;
@@ -498,7 +500,11 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
               // |ga| > TOL sqrt(al be), with the product formed so that it cannot underflow
               // before the floor test below rejects the pair
               const bool big = oka && okb && okg && fabsf(gaf) > (TOL64F * sqrtf(alf)) * sqrtf(bef);
-              if (big && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
+              // a pair with a column below the discard level also stops once its effect on T(u) is
+              // below the rounding level (the rule of the cluster form, svdc_sweeps)
+              const bool below = !(htg_dgt_nn(al, skip_abs) && htg_dgt_nn(be, skip_abs));
+              const bool moves = !(rnd2 > 0.f && below && gaf * gaf <= rnd2 * fmaxf(alf, bef));
+              if (big && moves && htg_dgt_nn(al, floor2) && htg_dgt_nn(be, floor2) &&
                   (htg_dgt_nn(al, skip_abs) || htg_dgt_nn(be, skip_abs))) {
                 bool okd;
                 const float df = htg_d2f_shift(be - al, sh2, &okd);   // 0 when below the range
