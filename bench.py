@@ -198,6 +198,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ GPU workload ---
+def cp_form_name(G, ctx) -> str:
+    """The form cp_als_sweep_rk2 takes for this workload's ranks on ctx."""
+    q = G.cp_als_rk2_cluster_ctas(ctx, CP_R, CP_R)
+    return f"thread-block cluster of {q} CTAs" if q else "cooperative grid, one CTA per factor column"
+
+
 class Workload:
     def __init__(self, G, device: int, precision: int):
         import numpy as np
@@ -209,6 +215,8 @@ class Workload:
         self.case = advection_case(D, N, seed_offset=1)
         # Kronecker-sum RK2 steps raise ranks by 3: max_terms=1 sizes the workspace for that
         self.ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=1, precision=precision, device=device)
+        # the CP route's context (its cp_form selects the cluster or the grid form of the ALS kernel)
+        self.cp_ctx = self.ctx
         self.op = G.advection_op(self.case.c, self.case.h)
         self.u = G.HTTensor(D, [N] * D, RMAX)
         self.X = G.CPTensor(D, [N] * D, CP_R)
@@ -261,7 +269,7 @@ class Workload:
         self.side.wait_event(self.ev_fork)
         G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=main)
         # CP route: ALS towards y = p(dt L) x_n with x_n as warm start (y never formed)
-        G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=self.side)
+        G.cp_als_sweep_rk2(self.cp_ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=self.side)
         self.ev_join.record(self.side)
         main.wait_event(self.ev_join)
 
@@ -271,7 +279,7 @@ class Workload:
         if route == "ht":
             G.ht_step(self.ctx, self.u, self.op, self.case.dt, TOL, RMAX, stream=stream)
         else:
-            G.cp_als_sweep_rk2(self.ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=stream)
+            G.cp_als_sweep_rk2(self.cp_ctx, self.X, self.op, self.case.dt, self.X, SWEEPS, stream=stream)
 
     def first_step(self):
         """Step 1: the rank-2 state defines y; the iterate is that state padded to rank 24."""
@@ -281,7 +289,7 @@ class Workload:
         X2 = G.CPTensor(D, [N] * D, 2)
         w, f = self.X.download()
         X2.upload(w[:2], [F[:, :2] for F in f])
-        G.cp_als_sweep_rk2(self.ctx, X2, self.op, self.case.dt, self.X, SWEEPS)
+        G.cp_als_sweep_rk2(self.cp_ctx, X2, self.op, self.case.dt, self.X, SWEEPS)
 
 
 def run_gpu(args):
@@ -401,11 +409,15 @@ def run_gpu(args):
     # ---- each route alone (same steps from t = 0, graph-captured, L2 flushed): the HT route's
     #      steps/s is the metric's own reading; the combined step above runs both side by side
     routes = {}
-    for route in ("ht", "cp"):
+    grid_ctx = G.Context(D, [N] * D, cap=RMAX, max_terms=1, precision=prec, device=local, cp_form=G.CP_FORM_GRID)
+    for route in ("ht", "cp", "cp_grid"):
+        # cp_grid: the CP route in the cooperative grid form (one CTA per factor column), for
+        # comparison with the cluster form the step uses
+        W.cp_ctx = grid_ctx if route == "cp_grid" else W.ctx
         restart()
         g1 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g1):
-            W.step_route(route, stream=torch.cuda.current_stream())
+            W.step_route(route[:2], stream=torch.cuda.current_stream())
         evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for i in range(args.steps):
             flush.zero_()
@@ -414,10 +426,15 @@ def run_gpu(args):
             evr[i][1].record(stream)
         torch.cuda.synchronize()
         W.ctx.check()
+        W.cp_ctx.check()
         msr = sum(a.elapsed_time(b) for a, b in evr)
         msr_max, vr = aggregate_replicas(msr, args.steps)
         routes[route] = {"value": vr, "unit": "steps/s", "ms_per_step": msr_max / args.steps}
         del g1
+    W.cp_ctx = W.ctx
+    grid_ctx.close()
+    routes["cp"]["form"] = cp_form_name(G, W.ctx)
+    routes["cp_grid"]["form"] = "cooperative grid, one CTA per factor column"
 
     # ---- the paper's two-step scheme (eq. AB2_) on the same HT workload, HT route alone
     ab2 = run_ab2_all(G, torch, flush, args.steps, args.warmup)
@@ -457,7 +474,7 @@ def run_gpu(args):
             "config": config_keys(args.precision, "flushed between timed steps (256 MB write)",
                                   "replicas" if world > 1 else "single GPU"),
             "run": {"ht_ranks_final": ranks, "streams": "HT route and CP route on two streams (independent data)",
-                    "cuda_graph": graph is not None},
+                    "cuda_graph": graph is not None, "cp_form": cp_form_name(G, W.ctx)},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_shares": shares,
         }

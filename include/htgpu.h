@@ -152,6 +152,9 @@ typedef struct ht_config {
                               for truncation inputs below rank 96) */
   int svd_cluster_min_cols;/* node factors at least this wide use the thread-block-cluster SVD,
                               32..480 (default 128) */
+  int cp_form;             /* cp_als_sweep_rk2 (Gauss-Seidel): 0 = one thread-block cluster of up to
+                              16 CTAs whenever the problem fits its shared memory (ranks <= 64), else
+                              the cooperative grid form; 1 = always the cooperative grid form */
 } ht_config;
 
 /* Context management, status codes, the profiler and the tree query below are infrastructure
@@ -332,9 +335,20 @@ int cp_apply_rk2(ht_ctx* ctx, const cp_tensor* x, const ht_op* L, double dt, cp_
  * from the powers A_j^p X_old,j (p <= 2), so the right-hand side of mode k contracts
  * over 3 r0 columns instead of r0 (1 + 2d + d(d-1)/2).  x holds the initial iterate
  * (rank x->rank) and receives the fit; x_old (rank r0) may alias x (it is read first).
+ * One launch runs every sweep: Gauss-Seidel sweeps on one thread-block cluster when the
+ * problem fits its shared memory (ht_config.cp_form), else on a cooperative grid with
+ * one CTA per factor column.  The two forms compute the same quantities in different
+ * summation orders (they agree to rounding).
  * Errors: HT_ERR_ARG, HT_ERR_CAPACITY (x rank > 64 or above the context capacity). */
 int cp_als_sweep_rk2(ht_ctx* ctx, const cp_tensor* x_old, const ht_op* L, double dt, cp_tensor* x,
                      int sweeps, int variant, double* eps_dev, void* stream);
+
+/* Which form cp_als_sweep_rk2 takes on this context for ranks r (x) and r0 (x_old) in the
+ * Gauss-Seidel variant: *ctas receives the CTAs of its thread-block cluster, or 0 for the
+ * cooperative grid form (ht_config.cp_form = 1, ranks above 64, a layout beyond one CTA's
+ * shared memory, or no cluster of that size placeable on the device).  The damped Jacobi
+ * variant always takes the grid form.  Errors: HT_ERR_ARG. */
+int cp_als_rk2_cluster_ctas(const ht_ctx* ctx, int r, int r0, int* ctas);
 
 /* ----------------------------------------------------- allocation-free ---- */
 /* The paper has no counterpart: this is a deployment variant of cp_als_sweep (same arguments

@@ -118,6 +118,13 @@ struct SvdClusterCfg {
   int min_p = 128;             // node factors at least this wide take the cluster form
 };
 SvdClusterCfg htg_svd_cluster_setup(int device);
+// Cluster form of the persistent CP-ALS kernel: the largest cluster (up to 16 CTAs, each with
+// its SM's whole shared memory) one of which fits the device, 0 when none does.
+struct CpClusterCfg {
+  int max_q = 0;
+  long long cap_doubles = 0;   // dynamic shared memory of one CTA, in doubles
+};
+CpClusterCfg htg_cp_cluster_setup(int device);
 // whether htg_launch_svd adds the cluster launch (for the launch count)
 bool htg_svd_cluster_used(const SvdClusterCfg* clu, int count, int pmax);
 // With clu (count = 1 only), node factors the cluster form takes (p >= 128 and fitting its shared
@@ -241,6 +248,7 @@ struct CpWs {
   double* Z;       // HT_MAXD x nmax x 3 rcap   powers [X, A X, A^2 X] of the step's input
   double* acc2;    // 2 doubles: per-mode sums of the convergence measure (persistent kernel)
   unsigned int* bar;   // 64 words: grid barrier arrival sequence numbers, one per CTA
+  double* ZT;      // HT_MAXD x 3 rcap x nmax   the powers transposed (the cluster form's M_k rows)
   int rcap, rycap, nmax;
 };
 CpWs* htg_ctx_cp(ht_ctx* c);
@@ -248,6 +256,8 @@ int htg_ctx_d(const ht_ctx* c);
 const int* htg_ctx_n(const ht_ctx* c);
 int* htg_ctx_err(ht_ctx* c);
 int htg_ctx_grid(const ht_ctx* c);
+int htg_ctx_cp_form(const ht_ctx* c);   // ht_config.cp_form
+const CpClusterCfg* htg_ctx_cp_cluster(const ht_ctx* c);
 int htg_ctx_cap(const ht_ctx* c);
 int htg_ctx_max_terms(const ht_ctx* c);
 int htg_ctx_device(const ht_ctx* c);

@@ -11,9 +11,12 @@
 //
 // Per mode update: hadamard kernel -> GEMM (RHS) -> solve kernel (Cholesky, substitution,
 // column normalisation, convergence measure) -> GEMM (refresh X_k^T X_k and Y_k^T X_k).
+#include <cooperative_groups.h>
 #include <cstring>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -582,16 +585,22 @@ constexpr int TRI_MAX = 64 * 65 / 2;   // lower-triangle pairs of the largest ra
 __device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 2; }
 
 // LDL^T factorisation (D diagonal, L unit lower) of the SPD r x r matrix in Lm (column-major,
-// lower part) with the unit-lower forward solve of the three right-hand sides in hs fused in.
+// lower part) with the unit-lower forward solve of the nrhs right-hand sides in hs (vector v at
+// hs + v r) fused in.
 // Right-looking, one CTA barrier per pivot: step j applies a_ic -= (a_ij / d_j) a_cj to the
 // trailing lower triangle (pairs from tri, i >= c > j) and z_i -= (a_ij / d_j) z_j to the
 // right-hand sides.  The next pivot a_{j+1,j+1} and its reciprocal are formed by one thread of
 // the last warp, and the warps on that warp's SM partition (warp index 3 mod 4) take no other
 // work: the pivot chain (two FP64 operations, the reciprocal's seed and its correction) then
 // never waits behind other warps' FP64 instructions (anything else that runs meanwhile, even
-// loads, lengthens the steps).  Column j keeps a_ij = L_ij d_j, Lsc receives L_ij.  A pivot that is not positive and
-// finite leaves dinv = 0 there; every thread sees it after the barrier and the result is false.
-__device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, const unsigned short* tri, int r) {
+// loads, lengthens the steps: asynchronous copies issued by the element threads during the
+// steps measured 1.4k cycles per step against 1.05k; so does more FP64 work on the pivot thread
+// itself: a look-ahead that formed the next pivot's entries there, one FMA off the chain,
+// measured 1.5k).  Column j keeps a_ij = L_ij d_j, Lsc receives L_ij.  A pivot that is
+// not positive and finite leaves dinv = 0 there; every thread sees it after the barrier and
+// the result is false.
+__device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, const unsigned short* tri, int r,
+                             int nrhs) {
   const int tid = threadIdx.x, wid = tid >> 5;
   constexpr int PIV = NT - 32;              // the pivot thread: lane 0 of the last warp
   constexpr int NE = (NT / 32) * 3 / 4 * 32;   // element threads: the warps with wid % 4 != 3
@@ -608,7 +617,7 @@ __device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, 
     const int m = r - 1 - j;
     const int s0 = tri_offset(j + 1, r) + 1;   // the pairs after (j+1, j+1)
     const int ntri = T - s0;
-    const int nall = ntri + 3 * m;
+    const int nall = ntri + nrhs * m;
     if (et >= 0) {
       for (int e = et; e < nall; e += NE) {
         if (e < ntri) {
@@ -636,15 +645,15 @@ __device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, 
   return true;
 }
 
-// Back substitution D L^T w = z for the three right-hand sides (z in hs, overwritten by w):
-// w_i = z_i / d_i - sum_{c > i} L_ci w_c.  For r <= 32 warp p takes side p with lane i holding
-// w_i's running value and column i of L (from Lsc) in registers: no CTA barrier inside.
+// Back substitution D L^T w = z for the nrhs right-hand sides (z in hs, overwritten by w):
+// w_i = z_i / d_i - sum_{c > i} L_ci w_c.  For r <= 32 warp p takes sides p, p + 8, ... with lane
+// i holding w_i's running value and column i of L (from Lsc) in registers: no CTA barrier inside.
 // Otherwise a CTA-wide substitution on the unscaled columns: w_i = (z_i - sum a_ci w_c) / d_i.
-__device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const double* dinv, int r) {
+__device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const double* dinv, int r, int nrhs) {
   const int tid = threadIdx.x;
   if (r <= 32) {
-    const int wp = tid >> 5, lane = tid & 31;
-    if (wp < 3) {
+    const int lane = tid & 31;
+    for (int wp = tid >> 5; wp < nrhs; wp += NT / 32) {
       double s = (lane < r) ? hs[wp * r + lane] * dinv[lane] : 0.0;
       double col[32];
 #pragma unroll
@@ -662,9 +671,9 @@ __device__ void ldlt_back(const double* Lm, const double* Lsc, double* hs, const
     return;
   }
   for (int j = r - 1; j >= 0; --j) {
-    if (tid < 3) hs[tid * r + j] *= dinv[j];
+    if (tid < nrhs) hs[tid * r + j] *= dinv[j];
     __syncthreads();
-    for (int e = tid; e < 3 * j; e += NT) {
+    for (int e = tid; e < nrhs * j; e += NT) {
       const int p = e / j, i = e % j;
       hs[p * r + i] = fma(-Lm[j + r * i], hs[p * r + j], hs[p * r + i]);
     }
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           w.acc2[1] = 0.0;
         }
         __syncthreads();
-        bool ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r);
+        bool ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r, 3);
         if (!ok) {
           // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation (Section 2.1
           // regularisation of ill-conditioned ALS systems), and start over
@@ -828,12 +837,12 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
           }
           rk2_rhs_row(Mv, d, k, r, mu[lp], hs, tid, blockDim.x);
           __syncthreads();
-          ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r);
+          ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r, 3);
         }
         if (!ok) {
           if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
         } else {
-          ldlt_back(Lm, Lsc, hs, dinv, r);
+          ldlt_back(Lm, Lsc, hs, dinv, r, 3);
         }
         for (int e = tid; e < 3 * r; e += blockDim.x) {
           const int pp = e / r, l = e % r;
@@ -968,6 +977,623 @@ __global__ void __launch_bounds__(NT) cp_als_rk2_persistent(CpArgs a, PowArgs pa
   if (!gs && b < r) normalise_column(a, b, false, red);
 }
 
+// ---------------------------------------------------------------------------
+// Thread-block-cluster form of the Gauss-Seidel cp_als_sweep_rk2, for problems whose operands
+// fit in shared memory: one cluster of Q <= 16 CTAs (one per SM) runs every sweep.  CTA q owns
+// the factor columns b = q, q + Q, ... < r and the solve rows lp = q, q + Q, ... < r0.  What a
+// phase hands to the next goes straight into the shared memory of the CTAs that read it
+// (distributed shared memory stores), and hardware cluster barriers (release / acquire)
+// separate the phases:
+//   A  Gamma_k (LDL^T) and the owned rows of W = Hs Gamma_k^-1; W[:, b] to the owner of column
+//      b.  Z_k and the owned old columns of X_k are fetched meanwhile, under the pivot chain
+//   B  owned columns of X~_k = Z_k W, the convergence sums, X_k[:, b] and lam_b; X_k[:, b] to
+//      every CTA
+//   C  owned columns of G_k = X_k^T X_k to every CTA; M_k[(p, lp), b] = Z_k[:, p r0 + lp] .
+//      X_k[:, b] to the owner of row lp (only the next mode's phase A reads M_k)
+// Every CTA holds all Grams G_j (d r^2), the M_j rows of its solve rows, the W columns of its
+// factor columns, the current X_k and a staged Z_k.  Against the cooperative form: cluster
+// barriers instead of grid barriers, and no L2 round trip between phases.
+// ---------------------------------------------------------------------------
+constexpr int CLU_MAX = 16;   // CTAs per cluster (the non-portable maximum)
+
+// Cluster size for ranks r, r0: the fewest columns per CTA (ceil(max(r, r0) / 16)), then as few
+// CTAs as carry them.
+__host__ __device__ inline int clu_ctas(int r, int r0) {
+  const int R = r > r0 ? r : r0;
+  const int C = (R + CLU_MAX - 1) / CLU_MAX;
+  return (R + C - 1) / C;
+}
+
+// Shared-memory layout of cp_als_rk2_cluster (offsets in doubles).
+struct CluLayout {
+  int C, Cr, ldx, K;
+  long long gs, lm, lsc, dinv, hs, mv, wc, xk, zs, zt, xo, xn, pb, go, total;
+};
+__host__ __device__ inline CluLayout clu_layout(int d, int r, int r0, int nmax, int Q) {
+  CluLayout L;
+  L.C = (r + Q - 1) / Q;      // factor columns per CTA (at most)
+  L.Cr = (r0 + Q - 1) / Q;    // solve rows per CTA (at most)
+  L.ldx = nmax | 1;           // odd: lanes walking columns of X_k hit distinct banks
+  L.K = 3 * r0;
+  long long o = 0;
+  L.gs = o;   o += (long long)d * r * r;         // G_j, j < d
+  L.lm = o;   o += (long long)r * r;             // Gamma_k, then its LDL^T factor
+  L.lsc = o;  o += (long long)r * r;             // L
+  L.dinv = o; o += r;                            // reciprocal pivots
+  L.hs = o;   o += 3LL * r * L.Cr;               // right-hand sides / W rows of the solve rows
+  L.mv = o;   o += (long long)L.Cr * d * 3 * r;  // M_j rows (p, lp) of the solve rows
+  L.wc = o;   o += (long long)L.C * L.K;         // W columns of the owned factor columns
+  L.xk = o;   o += (long long)L.ldx * r;         // X_k
+  o += o & 1;                                    // 16-byte starts: bulk-copy destinations
+  L.zs = o;   o += (long long)nmax * L.K;        // Z_k (n x K, leading dimension n)
+  o += o & 1;
+  L.zt = o;   o += (long long)nmax * L.K;        // Z_k^T (K x n, leading dimension K)
+  L.xo = o;   o += (long long)nmax * L.C;        // owned columns of X_k before the update
+  L.xn = o;   o += (long long)nmax * L.C;        // owned columns after it
+  const long long items = htg_max(htg_max(nmax, L.K), r) * L.C;
+  L.pb = o;   o += 8 * htg_max((long long)NT, items);   // partial sums (up to 8 parts)
+  L.go = o;   o += (long long)(r + L.K) * L.C;   // dot products before they are pushed
+  L.total = o;
+  return L;
+}
+
+// Parts per output of a split dot product of `len` terms over `items` outputs on nthr threads:
+// the count (1..8, at most len) that minimises a thread's FP64 instructions,
+// ceil(items P / nthr) ceil(len / P).
+__device__ inline int balanced_parts(int items, int len, int nthr = NT) {
+  int best = 1;
+  long long bc = (long long)((items + nthr - 1) / nthr) * len;
+  for (int P = 2; P <= 8 && P <= len; ++P) {
+    const long long c = (long long)((items * P + nthr - 1) / nthr) * ((len + P - 1) / P);
+    if (c < bc) { bc = c; best = P; }
+  }
+  return best;
+}
+
+// sum_{i0 <= i < i1} a[i sa] b[i sb] with four independent partial sums (FP64 latency)
+__device__ inline double dot4(const double* a, long long sa, const double* b, int i0, int i1) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int i = i0;
+  for (; i + 3 < i1; i += 4) {
+    s0 = fma(a[sa * i], b[i], s0);
+    s1 = fma(a[sa * (i + 1)], b[i + 1], s1);
+    s2 = fma(a[sa * (i + 2)], b[i + 2], s2);
+    s3 = fma(a[sa * (i + 3)], b[i + 3], s3);
+  }
+  for (; i < i1; ++i) s0 = fma(a[sa * i], b[i], s0);
+  return (s0 + s1) + (s2 + s3);
+}
+
+// out[o + nout c] = col(o) . xv[:, c] (length n; xv column-major, leading dimension n) for
+// o < nout, c < nc, each split into P parts (balanced_parts, computed once per launch):
+// consecutive lanes take consecutive outputs, partial sums added in part order.  Work item e =
+// f + items part, f = o + nout c; the indices advance without divisions.
+template <class Col>
+__device__ void cols_dot_multi(Col col, const double* xv, int n, int nout, int nc, int P, double* pb, double* out) {
+  const int items = nout * nc;
+  const int chunk = (n + P - 1) / P;
+  int f = threadIdx.x, part = 0;
+  while (f >= items) { f -= items; ++part; }
+  for (int e = threadIdx.x; e < items * P; e += NT) {
+    int o = f, c = 0;
+    while (o >= nout) { o -= nout; ++c; }
+    const int q0 = part * chunk;
+    pb[e] = dot4(col(o), 1, xv + (long long)n * c, q0, htg_min(n, q0 + chunk));
+    f += NT;
+    while (f >= items) { f -= items; ++part; }
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < items; g += NT) {
+    double v = pb[g];
+    for (int pp = 1; pp < P; ++pp) v += pb[g + items * pp];
+    out[g] = v;
+  }
+  __syncthreads();
+}
+
+// out[row + n c] = sum_i S[row + ld i] Y[i + ldy c] for row < n, c < nc, i < m, each split into P
+// parts: consecutive lanes take consecutive rows, partial sums added in part order.
+__device__ void rows_dot_multi(const double* S, int ld, const double* Y, int ldy, int n, int m, int nc, int P,
+                               double* pb, double* out) {
+  const int items = n * nc;
+  const int chunk = (m + P - 1) / P;
+  int f = threadIdx.x, part = 0;
+  while (f >= items) { f -= items; ++part; }
+  for (int e = threadIdx.x; e < items * P; e += NT) {
+    int row = f, c = 0;
+    while (row >= n) { row -= n; ++c; }
+    const int i0 = part * chunk;
+    pb[e] = dot4(S + row, ld, Y + (long long)ldy * c, i0, htg_min(m, i0 + chunk));
+    f += NT;
+    while (f >= items) { f -= items; ++part; }
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < items; g += NT) {
+    double v = pb[g];
+    for (int pp = 1; pp < P; ++pp) v += pb[g + items * pp];
+    out[g] = v;
+  }
+  __syncthreads();
+}
+
+// The first half of cols_dot_multi on threads t0 .. t0 + nthr - 1 only (no barrier): the P
+// partial sums of every output into pb[f + items part], items = nout nc.
+template <class Col>
+__device__ void cols_dot_parts(Col col, const double* xv, int n, int nout, int nc, int P, double* pb, int t0,
+                               int nthr) {
+  const int items = nout * nc;
+  const int chunk = (n + P - 1) / P;
+  const int t = threadIdx.x - t0;
+  int f = t, part = 0;
+  while (f >= items) { f -= items; ++part; }
+  for (int e = t; e < items * P; e += nthr) {
+    int o = f, c = 0;
+    while (o >= nout) { o -= nout; ++c; }
+    const int q0 = part * chunk;
+    pb[e] = dot4(col(o), 1, xv + (long long)n * c, q0, htg_min(n, q0 + chunk));
+    f += nthr;
+    while (f >= items) { f -= items; ++part; }
+  }
+}
+
+// The first half of rows_dot_multi on threads t0 .. t0 + nthr - 1 only (no barrier): the P
+// partial sums of every output into pb[f + items part], items = n nc.
+__device__ void rows_dot_parts(const double* S, int ld, const double* Y, int ldy, int n, int m, int nc, int P,
+                               double* pb, int t0, int nthr) {
+  const int items = n * nc;
+  const int chunk = (m + P - 1) / P;
+  const int t = threadIdx.x - t0;
+  int f = t, part = 0;
+  while (f >= items) { f -= items; ++part; }
+  for (int e = t; e < items * P; e += nthr) {
+    int row = f, c = 0;
+    while (row >= n) { row -= n; ++c; }
+    const int i0 = part * chunk;
+    pb[e] = dot4(S + row, ld, Y + (long long)ldy * c, i0, htg_min(m, i0 + chunk));
+    f += nthr;
+    while (f >= items) { f -= items; ++part; }
+  }
+}
+
+// n x cols column-major copy (leading dimensions lds, ldd) through L2 (data other CTAs of this
+// launch wrote: an L1 line may hold parts of several CTAs' columns), 8 loads in flight per thread
+__device__ void stage_cg(double* dst, int ldd, const double* src, int lds, int n, int cols) {
+  const int total = n * cols;
+  int base = 0;
+  for (; base + 8 * NT <= total; base += 8 * NT) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT + (int)threadIdx.x;
+      v[u] = __ldcg(src + (e % n) + (long long)lds * (e / n));
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * NT + (int)threadIdx.x;
+      dst[(e % n) + (long long)ldd * (e / n)] = v[u];
+    }
+  }
+  for (int e = base + (int)threadIdx.x; e < total; e += NT)
+    dst[(e % n) + (long long)ldd * (e / n)] = __ldcg(src + (e % n) + (long long)lds * (e / n));
+}
+
+__device__ inline unsigned clu_smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// one-dimensional bulk copy global -> shared, completing on the mbarrier's transaction count
+__device__ inline void clu_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   clu_smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(clu_smem_u32(bar))
+               : "memory");
+}
+constexpr long long CLU_WAIT_CYCLES = 1ll << 31;   // bounded mbarrier wait (about 1 s at 2 GHz)
+// bounded wait for the mbarrier phase of the given parity; false when it gave up
+__device__ inline bool clu_mbar_wait(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(clu_smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > CLU_WAIT_CYCLES) return false;
+  }
+}
+
+// (a_n / a_d > b_n / b_d) for non-negative numerators and positive denominators, by cross
+// multiplication (no division) and a bit-pattern compare of the non-negative products
+__device__ inline bool ratio_gt(double an, double ad, double bn, double bd) { return htg_dgt_nn(an * bd, bn * ad); }
+
+__global__ void __launch_bounds__(NT, 1) cp_als_rk2_cluster(CpArgs a, PowArgs pa, CpWs w, const double* mu_src,
+                                                         int sweeps, int* err, double* flops) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int q = (int)cluster.block_rank(), Q = (int)cluster.num_blocks();
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int d = a.d, r = a.r, r0 = pa.r0, K = 3 * r0, nmax = w.nmax;
+  const CluLayout L = clu_layout(d, r, r0, nmax, Q);
+  const int ldx = L.ldx;
+  extern __shared__ double sh[];
+  double* Gs = sh + L.gs;
+  double* Lm = sh + L.lm;
+  double* Lsc = sh + L.lsc;
+  double* dinv = sh + L.dinv;
+  double* hs = sh + L.hs;
+  double* Mv = sh + L.mv;
+  double* Wc = sh + L.wc;
+  double* Xk = sh + L.xk;
+  double* Zs = sh + L.zs;
+  double* ZTs = sh + L.zt;
+  double* xo = sh + L.xo;
+  double* xn = sh + L.xn;
+  double* pb = sh + L.pb;
+  double* go = sh + L.go;
+  __shared__ unsigned short tri[TRI_MAX];
+  __shared__ double red[HT_MAXD + 32];
+  __shared__ double part[2 * CLU_MAX];   // CTA 0: every CTA's convergence sums of the last mode
+  __shared__ double best[2 * 64];        // CTA 0: per sweep, the largest measure as (num, den)
+  __shared__ double mu_own[CLU_MAX];     // weights of x_old at the solve rows
+  __shared__ double lamo[CLU_MAX];       // lam of the owned columns before the update
+  __shared__ double csum[2 * CLU_MAX];   // per owned column: the convergence sums
+  __shared__ double cinv[CLU_MAX];       // per owned column: 1 / |x~|
+  __shared__ int Pb[HT_MAXD], Pg[HT_MAXD], Pg2[HT_MAXD], Pm[HT_MAXD], Pm2[HT_MAXD];   // dot-product parts
+  __shared__ __align__(8) unsigned long long zbar;        // completion of a mode's bulk prefetch
+  const int nc = (q < r) ? (r - q + Q - 1) / Q : 0;      // owned factor columns
+  const int nrw = (q < r0) ? (r0 - q + Q - 1) / Q : 0;   // owned solve rows
+  for (int c = tid; c < r; c += NT) {
+    const int o = tri_offset(c, r);
+    for (int i = c; i < r; ++i) tri[o + i - c] = (unsigned short)(i | (c << 8));
+  }
+  for (int i = tid; i < 2 * CLU_MAX; i += NT) part[i] = 0.0;
+  for (int i = tid; i < 64; i += NT) {
+    best[2 * i] = 0.0;
+    best[2 * i + 1] = 1.0;
+  }
+  for (int i = tid; i < nrw; i += NT) mu_own[i] = mu_src[q + Q * i];
+  for (int k = tid; k < d; k += NT) {
+    Pb[k] = balanced_parts(a.n[k] * htg_max(nc, 1), K);
+    Pg[k] = balanced_parts(r * htg_max(nc, 1), a.n[k]);
+    Pm[k] = balanced_parts(K * htg_max(nc, 1), a.n[k]);
+    Pm2[k] = balanced_parts(K * htg_max(nc, 1), a.n[k], NT - 32 * htg_max(nc, 1));
+    Pg2[k] = balanced_parts(r * htg_max(nc, 1), a.n[k], NT - 64);
+  }
+  // Z_k and Z_k^T arrive by two bulk copies per mode when every block is 16-byte aligned and a
+  // multiple of 16 bytes (else by 8-byte asynchronous copies)
+  const long long zstride = (long long)nmax * 3 * w.rcap;
+  bool bulk = (zstride % 2 == 0) && (((unsigned long long)w.Z | (unsigned long long)w.ZT) % 16 == 0);
+  for (int k = 0; k < d; ++k) bulk = bulk && ((long long)a.n[k] * K % 2 == 0) && (2LL * a.n[k] * K * 8 < (1 << 20));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(clu_smem_u32(&zbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (q == 0)
+    for (int i = tid; i < r0; i += NT) w.wold[i] = mu_src[i];
+  // ---------------- 0a: powers of x_old at the solve rows, all rows of a mode at once (scratch:
+  // the Z_k buffer, 2 nrw n <= 3 r0 n doubles)
+  for (int k = 0; k < d && nrw > 0; ++k) {
+    const int n = pa.n[k], hw = pa.hw[k];
+    double* xs = Zs;               // column i: x_old,k[:, q + Q i]
+    double* ys = Zs + nrw * n;     // A x
+    double* Zk = w.Z + (long long)k * zstride;
+    double* ZTk = w.ZT + (long long)k * zstride;   // Z_k^T: K x n, leading dimension K
+    for (int e = tid; e < nrw * n; e += NT) xs[e] = pa.X[k][(e % n) + (long long)n * (q + Q * (e / n))];
+    __syncthreads();
+    for (int e = tid; e < nrw * n; e += NT) {
+      const int j = e % n, i = e / n, lp = q + Q * i;
+      const double* x = xs + (long long)n * i;
+      double s = 0.0;
+      for (int o = -hw; o <= hw; ++o) {
+        int jj = (j + o) % n;
+        if (jj < 0) jj += n;
+        s = fma(pa.c[k][o + hw], x[jj], s);
+      }
+      ys[e] = s;
+      Zk[j + (long long)n * lp] = x[j];
+      Zk[j + (long long)n * (r0 + lp)] = s;
+      ZTk[lp + (long long)K * j] = x[j];
+      ZTk[r0 + lp + (long long)K * j] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < nrw * n; e += NT) {
+      const int j = e % n, i = e / n, lp = q + Q * i;
+      const double* y = ys + (long long)n * i;
+      double s = 0.0;
+      for (int o = -hw; o <= hw; ++o) {
+        int jj = (j + o) % n;
+        if (jj < 0) jj += n;
+        s = fma(pa.c[k][o + hw], y[jj], s);
+      }
+      Zk[j + (long long)n * (2 * r0 + lp)] = s;
+      ZTk[2 * r0 + lp + (long long)K * j] = s;
+    }
+    __syncthreads();
+  }
+  // owned columns of G_j, from X_j in Xk and its owned columns in xn (columns of Xk), to every CTA
+  auto gram_push = [&](int j, int n) {
+    cols_dot_multi([&](int o) { return Xk + (long long)ldx * o; }, xn, n, r, nc, Pg[j], pb, go);
+    for (int f = tid; f < r * nc; f += NT) {
+      const int o = f % r, c = f / r;
+      const double v = go[f];
+      double* dst = Gs + (long long)j * r * r + (long long)r * (q + Q * c) + o;
+      for (int t = 0; t < Q; ++t) *cluster.map_shared_rank(dst, t) = v;
+    }
+  };
+  // M_j[(p, lp), b] = value f = (p r0 + lp) + K c (b = q + Q c) to the owner of solve row lp
+  auto m_push = [&](int j, int f, double v) {
+    const int oo = f % K, c = f / K, p = oo / r0, lp = oo - p * r0;
+    *cluster.map_shared_rank(Mv + ((long long)((lp / Q) * d + j) * 3 + p) * r + (q + Q * c), lp % Q) = v;
+  };
+  cluster.sync();   // Z complete; all of x_old read (x may alias it)
+  for (int i = 0; i < nc; ++i) normalise_column(a, q + Q * i, false, red);
+  cluster.sync();   // X normalised
+  // ---------------- 0b: owned columns of G_j and M_j for every j (X_j by asynchronous copies, Z_j^T
+  // by one bulk copy when aligned)
+  unsigned zphase = 0;     // parity of the bulk prefetch's mbarrier phase
+  bool waited_ok = true;   // false once a bounded wait gave up
+  for (int j = 0; j < d; ++j) {
+    const int n = a.n[j];
+    if (nc > 0) {
+      const double* ZTj = w.ZT + (long long)j * zstride;
+      if (bulk) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const unsigned bytes = (unsigned)((long long)n * K * sizeof(double));
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(clu_smem_u32(&zbar)),
+                       "r"(bytes)
+                       : "memory");
+          clu_bulk_g2s(ZTs, ZTj, bytes, &zbar);
+        }
+      } else {
+        stage_cg(ZTs, K, ZTj, K, K, n);
+      }
+      stage_cg(Xk, ldx, a.X[j], n, n, r);
+      if (bulk) {
+        if (!clu_mbar_wait(&zbar, zphase)) waited_ok = false;
+        zphase ^= 1u;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * nc; e += NT) xn[e] = Xk[(e % n) + (long long)ldx * (q + Q * (e / n))];
+      __syncthreads();
+      gram_push(j, n);
+      rows_dot_multi(ZTs, K, xn, n, K, n, nc, Pm[j], pb, go);   // M_j columns, by rows of Z_j^T
+      for (int f = tid; f < K * nc; f += NT) m_push(j, f, go[f]);
+      __syncthreads();   // Xk, ZTs and go are rewritten for the next j
+    }
+  }
+  cluster.sync();   // every G_j and M_j row in place
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int k = 0; k < d; ++k) {
+      const int n = a.n[k];
+      const bool record = !(sweep == 0 && k == 0);   // the previous mode's sums are complete
+      // ---------------- A: Gamma_k (LDL^T) and the solve rows of W = Hs Gamma_k^-1
+      // Z_k and Z_k^T for phases B and C: two bulk copies issued by one thread (or 8-byte
+      // asynchronous copies), and the owned old columns of X_k; all land under the LDL^T pivot
+      // chain (nothing may run beside it)
+      if (nc > 0) {
+        const double* Zk = w.Z + (long long)k * zstride;
+        const double* ZTk = w.ZT + (long long)k * zstride;
+        if (bulk) {
+          if (tid == 0) {
+            // the generic-proxy reads of Zs and ZTs (the last phase C) before the async writes
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const unsigned bytes = (unsigned)((long long)n * K * sizeof(double));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(clu_smem_u32(&zbar)),
+                         "r"(2 * bytes)
+                         : "memory");
+            clu_bulk_g2s(Zs, Zk, bytes, &zbar);
+            clu_bulk_g2s(ZTs, ZTk, bytes, &zbar);
+          }
+        } else {
+          for (int e = tid; e < n * K; e += NT) {
+            stage_async1(Zs + e, Zk + e);
+            stage_async1(ZTs + e, ZTk + e);
+          }
+        }
+        for (int e = tid; e < n * nc; e += NT)
+          stage_async1(xo + e, a.X[k] + (e % n) + (long long)n * (q + Q * (e / n)));
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (tid < nc) lamo[tid] = a.lam[q + Q * tid];
+      }
+      if (nrw > 0) {
+        const int nG = r * r;
+        // side by side: Gamma_k (warps 0-2, 4-5), at the first mode the right-hand sides (row i on
+        // warp 7 - i % 2; later modes formed them in the previous phase C), CTA 0's record of the
+        // previous mode's convergence measure (warp 3).  (Gamma_k on every idle warp, with the
+        // factors multiplied as two interleaved partial products, measured slower: 5.4k cycles
+        // against 3.4k.)
+        if (wid >= NT / 32 - 2) {
+          if (sweep == 0 && k == 0)
+            for (int i = NT / 32 - 1 - wid; i < nrw; i += 2)
+              rk2_rhs_row(Mv + (long long)i * d * 3 * r, d, k, r, mu_own[i], hs + 3LL * r * i, lane, 32);
+        } else if (wid % 4 != 3) {
+          const int gt = (wid - wid / 4) * 32 + lane;
+          for (int e = gt; e < nG; e += (NT / 32 - 3) * 32) {
+            double v = 1.0;
+            for (int j = 0; j < d; ++j)
+              if (j != k) v *= Gs[j * nG + e];
+            Lm[e] = v;
+          }
+        } else if (q == 0 && record) {
+          // warp 3: the sums over CTAs (a shuffle tree), then the running maximum of num / den
+          double tn = (lane < Q) ? part[2 * lane] : 0.0, td = (lane < Q) ? part[2 * lane + 1] : 0.0;
+          for (int o = 16; o > 0; o >>= 1) {
+            tn += __shfl_xor_sync(0xffffffffu, tn, o);
+            td += __shfl_xor_sync(0xffffffffu, td, o);
+          }
+          if (lane == 0) {
+            if (!htg_dpos_finite(td)) td = 1.0;
+            const int sw = (k == 0) ? sweep - 1 : sweep;
+            if (ratio_gt(tn, td, best[2 * sw], best[2 * sw + 1])) {
+              best[2 * sw] = tn;
+              best[2 * sw + 1] = td;
+            }
+          }
+        }
+        __syncthreads();
+        bool ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r, 3 * nrw);
+        if (!ok) {
+          // shift by 1e-14 tr(Gamma)/r, only after a failed factorisation (Section 2.1
+          // regularisation of ill-conditioned ALS systems), and start over
+          __shared__ double shift;
+          if (tid == 0) {
+            double tr = 0.0;
+            for (int i = 0; i < r; ++i) {
+              double v = 1.0;
+              for (int j = 0; j < d; ++j)
+                if (j != k) v *= Gs[j * nG + i + r * i];
+              tr += v;
+            }
+            shift = 1e-14 * tr / r;
+          }
+          __syncthreads();
+          for (int e = tid; e < nG; e += NT) {
+            double v = 1.0;
+            for (int j = 0; j < d; ++j)
+              if (j != k) v *= Gs[j * nG + e];
+            Lm[e] = v + ((e % r == e / r) ? shift : 0.0);
+          }
+          for (int i = 0; i < nrw; ++i)
+            rk2_rhs_row(Mv + (long long)i * d * 3 * r, d, k, r, mu_own[i], hs + 3LL * r * i, tid, NT);
+          __syncthreads();
+          ok = ldlt_forward(Lm, Lsc, hs, dinv, tri, r, 3 * nrw);
+        }
+        if (!ok) {
+          if (tid == 0 && err) atomicCAS(err, 0, (int)HT_ERR_NONFINITE);
+        } else {
+          ldlt_back(Lm, Lsc, hs, dinv, r, 3 * nrw);
+        }
+        // W^(p)[lp, l] to the owner of column l
+        for (int e = tid; e < 3 * r * nrw; e += NT) {
+          const int i = e / (3 * r), f = e - i * 3 * r, p = f / r, l = f - p * r;
+          *cluster.map_shared_rank(Wc + (long long)(l / Q) * K + p * r0 + (q + Q * i), l % Q) = hs[e];
+        }
+      }
+      stage_wait();
+      if (nc > 0 && bulk) {
+        if (!clu_mbar_wait(&zbar, zphase)) waited_ok = false;
+        zphase ^= 1u;
+      }
+      cluster.sync();
+      // ---------------- B: owned columns of X~_k = Z_k W, X_k[:, b] and lam_b; M_k[:, b] to the
+      //                  owners of the solve rows
+      if (nc > 0) {
+        rows_dot_multi(Zs, n, Wc, K, n, K, nc, Pb[k], pb, xn);
+        // side by side: warp c < nc reduces column c (convergence sums, |x~|); the other warps form
+        // the partial sums of M~_k = Z_k^T X~_k (by rows of Z_k^T), scaled by 1 / |x~| below
+        if (wid >= nc) {
+          rows_dot_parts(ZTs, K, xn, n, K, n, nc, Pm2[k], pb, 32 * nc, NT - 32 * nc);
+        } else {
+          const int c = wid;
+          const double lam_old = lamo[c];
+          double num = 0.0, den = 0.0, nrm2 = 0.0;
+          for (int row = lane; row < n; row += 32) {
+            const double v = xn[row + n * c];
+            const double old = xo[row + n * c] * lam_old;
+            const double df = v - old;
+            num = fma(df, df, num);
+            den = fma(old, old, den);
+            nrm2 = fma(v, v, nrm2);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_xor_sync(0xffffffffu, num, o);
+            den += __shfl_xor_sync(0xffffffffu, den, o);
+            nrm2 += __shfl_xor_sync(0xffffffffu, nrm2, o);
+          }
+          if (lane == 0) {
+            double nr = 0.0, inv = 1.0;
+            if (htg_dpos_finite(nrm2)) {
+              inv = htg_rsqrt_fast(nrm2);
+              nr = nrm2 * inv;
+            } else {
+              nr = sqrt(nrm2);
+            }
+            a.lam[q + Q * c] = nr;
+            csum[2 * c] = num;
+            csum[2 * c + 1] = den;
+            cinv[c] = inv;
+          }
+        }
+        __syncthreads();
+        {
+          const int items = K * nc, P = Pm2[k];
+          for (int f = tid; f < items; f += NT) {
+            double v = pb[f];
+            for (int pp = 1; pp < P; ++pp) v += pb[f + items * pp];
+            m_push(k, f, v * cinv[f / K]);
+          }
+        }
+        double* Xg = a.X[k];
+        for (int f = tid; f < n * nc; f += NT) {
+          const int row = f % n, c = f / n;
+          const double v = xn[f] * cinv[c];
+          xn[f] = v;
+          Xg[row + (long long)n * (q + Q * c)] = v;
+          double* dst = Xk + row + (long long)ldx * (q + Q * c);
+          for (int t = 0; t < Q; ++t) *cluster.map_shared_rank(dst, t) = v;
+        }
+        if (tid == 0) {
+          double tn = 0.0, td = 0.0;
+          for (int c = 0; c < nc; ++c) { tn += csum[2 * c]; td += csum[2 * c + 1]; }
+          double* p0 = cluster.map_shared_rank(part, 0);
+          p0[2 * q] = tn;
+          p0[2 * q + 1] = td;
+        }
+      }
+      cluster.sync();
+      // ---------------- C: owned columns of G_k (to every CTA, warps 0-5) and, beside them, the next
+      // mode's right-hand sides (warps 6-7: every M_j row they read is in place)
+      {
+        const bool more = !(sweep == sweeps - 1 && k == d - 1);
+        const int kn = (k + 1 == d) ? 0 : k + 1;
+        if (wid >= NT / 32 - 2) {
+          if (more)
+            for (int i = NT / 32 - 1 - wid; i < nrw; i += 2)
+              rk2_rhs_row(Mv + (long long)i * d * 3 * r, d, kn, r, mu_own[i], hs + 3LL * r * i, lane, 32);
+        } else if (nc > 0) {
+          cols_dot_parts([&](int o) { return Xk + (long long)ldx * o; }, xn, n, r, nc, Pg2[k], pb, 0, NT - 64);
+        }
+        __syncthreads();
+        if (nc > 0) {
+          const int items = r * nc, P = Pg2[k];
+          for (int f = tid; f < items; f += NT) {
+            double v = pb[f];
+            for (int pp = 1; pp < P; ++pp) v += pb[f + items * pp];
+            const int o = f % r, c = f / r;
+            double* dst = Gs + (long long)k * r * r + (long long)r * (q + Q * c) + o;
+            for (int t = 0; t < Q; ++t) *cluster.map_shared_rank(dst, t) = v;
+          }
+        }
+      }
+      cluster.sync();
+    }
+  }
+  if (!waited_ok && err) atomicCAS(err, 0, (int)HT_ERR_TIMEOUT);
+  if (flops && q == 0 && tid == 0) {
+    // the structured algorithm's FP64 work, as counted by the cooperative form
+    double f = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double n = a.n[k], rr = r, q0 = r0;
+      f += 2.0 * n * rr * rr + 12.0 * n * q0 * rr + 10.0 * (d - 1) * q0 * rr + (d - 2) * rr * rr +
+           rr * rr * rr / 3.0 + 6.0 * q0 * rr * rr;
+    }
+    atomicAdd(flops, f * sweeps);
+  }
+  // the last mode's sums (arrived before the last cluster barrier), then the per-sweep measures
+  if (q == 0 && tid == 0 && sweeps > 0) {
+    double tn = 0.0, td = 0.0;
+    for (int t = 0; t < Q; ++t) { tn += part[2 * t]; td += part[2 * t + 1]; }
+    if (!htg_dpos_finite(td)) td = 1.0;
+    const int sw = sweeps - 1;
+    if (ratio_gt(tn, td, best[2 * sw], best[2 * sw + 1])) {
+      best[2 * sw] = tn;
+      best[2 * sw + 1] = td;
+    }
+    for (int s = 0; s < sweeps && s < 64; ++s) w.epsacc[s] = sqrt(best[2 * s] / best[2 * s + 1]);
+  }
+}
+
 // dynamic shared memory of cp_solve_kernel: L (r x r), norms (r), staged rows (n x r)
 static cudaError_t solve_smem_for(int r, const int* n, int d, size_t* out) {
   int nmax = 1;
@@ -979,6 +1605,64 @@ static cudaError_t solve_smem_for(int r, const int* n, int d, size_t* out) {
 }
 
 }  // namespace
+
+CpClusterCfg htg_cp_cluster_setup(int device) {
+  CpClusterCfg out;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, cp_als_rk2_cluster) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  // every CTA claims its SM's whole shared memory (the HT route's kernels, launched beside this
+  // one, then land on other SMs)
+  const long long dyn = (long long)optin - (long long)fa.sharedSizeBytes;
+  if (dyn < (long long)(16 * 1024)) return out;
+  if (cudaFuncSetAttribute(cp_als_rk2_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess ||
+      cudaFuncSetAttribute(cp_als_rk2_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return out;
+  }
+  // the largest cluster (up to 16 CTAs) of which one fits the device: smaller ones fit as well
+  for (int q = CLU_MAX; q >= 1; --q) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(q, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)dyn;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = q;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, cp_als_rk2_cluster, &cfg) == cudaSuccess && n >= 1) {
+      out.max_q = q;
+      out.cap_doubles = dyn / (long long)sizeof(double);
+      return out;
+    }
+    cudaGetLastError();
+  }
+  return out;
+}
+
+// CTAs of the cluster form for ranks (r, r0) on this context, 0 when the cooperative form runs
+static int cluster_form_ctas(const ht_ctx* c, int r, int r0) {
+  const CpClusterCfg* clu = htg_ctx_cp_cluster(c);
+  if (htg_ctx_cp_form(c) != 0 || clu->max_q <= 0 || r < 1 || r0 < 1 || r > 64 || r0 > 64) return 0;
+  if (r * (r + 1) / 2 > TRI_MAX) return 0;
+  const int Q = clu_ctas(r, r0);
+  const CluLayout lay = clu_layout(htg_ctx_d(c), r, r0, htg_ctx_cp((ht_ctx*)c)->nmax, Q);
+  return (Q <= clu->max_q && lay.total <= clu->cap_doubles) ? Q : 0;
+}
+
+extern "C" int cp_als_rk2_cluster_ctas(const ht_ctx* c, int r, int r0, int* ctas) {
+  if (!c || !ctas || r < 1 || r0 < 1) return HT_ERR_ARG;
+  *ctas = cluster_form_ctas(c, r, r0);
+  return HT_OK;
+}
 
 extern "C" int cp_apply_rk2(ht_ctx* c, const cp_tensor* x, const ht_op* L, double dt, cp_tensor* y, void* stream) {
   if (!c || !x || !y || !L) return HT_ERR_ARG;
@@ -1123,6 +1807,38 @@ extern "C" int cp_als_sweep_rk2(ht_ctx* c, const cp_tensor* x_old, const ht_op* 
   const int r0 = x_old->rank;
   cudaStream_t s = (cudaStream_t)stream;
   (void)nmax;
+  // the cluster form: Gauss-Seidel, and its layout within one CTA's shared memory on a cluster
+  // size this device can place (htg_cp_cluster_setup, at context creation)
+  const CpClusterCfg* clu = htg_ctx_cp_cluster(c);
+  if (variant == CP_ALS_GS) {
+    const int Q = cluster_form_ctas(c, a.r, r0);
+    if (Q > 0) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(Q);
+      cfg.blockDim = dim3(NT);
+      cfg.dynamicSmemBytes = (size_t)clu->cap_doubles * sizeof(double);
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = Q;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int launches = 0;
+      htg_prof_begin(c, s);
+      const cudaError_t e1 = cudaLaunchKernelEx(&cfg, cp_als_rk2_cluster, a, pa, *w, (const double*)x_old->weight,
+                                                sweeps, htg_ctx_err(c), htg_prof_flops(c, KC_CPSOLVE));
+      htg_prof_end(c, KC_CPSOLVE, s);
+      ++launches;
+      if (e1 == cudaSuccess && eps_dev && sweeps > 0) {
+        cp_eps_out_kernel<<<1, 64, 0, s>>>(*w, sweeps, eps_dev);
+        ++launches;
+      }
+      htg_ctx_count(c, launches, s);
+      return (e1 == cudaSuccess && cudaGetLastError() == cudaSuccess) ? HT_OK : HT_ERR_CUDA;
+    }
+  }
   // one cooperative launch: CTA b owns factor column b (and row b of the solve)
   const int nblk = htg_max(a.r, r0);
   const size_t nm = (size_t)w->nmax;

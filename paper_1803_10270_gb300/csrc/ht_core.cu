@@ -176,6 +176,7 @@ struct ht_ctx {
   QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
   bool has_coop = false;
   SvdClusterCfg svd_clu;       // cluster form of the node SVD (contexts with Kc >= 128)
+  CpClusterCfg cp_clu;         // cluster form of the persistent CP-ALS kernel
   void* cn_ws = nullptr;       // Crank-Nicolson ALS workspace (allocated by its first call)
   size_t cn_bytes = 0;
 };
@@ -846,6 +847,7 @@ static bool cfg_valid(const ht_config* c) {
   if (c->tree != HT_TREE_BALANCED && c->tree != HT_TREE_LINEAR) return false;
   if (c->tc_min_work < -1 || c->gemm_ctas_per_sm < 0 || c->gemm_ctas_per_sm > 32) return false;
   if (c->svd_cluster_min_cols != 0 && (c->svd_cluster_min_cols < 32 || c->svd_cluster_min_cols > 480)) return false;
+  if (c->cp_form != 0 && c->cp_form != 1) return false;
   if (c->precision == HT_PREC_MIXED)
     return c->mixed_slices == 0 || (c->mixed_slices >= 2 && c->mixed_slices <= 4);
   return c->precision == HT_PREC_FP64;
@@ -857,7 +859,7 @@ static int trunc_input_cap(const ht_config* c) {
 }
 
 struct WsLayout {
-  size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[11], off_prof;
+  size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[12], off_prof;
   size_t off_coop[5];           // cooperative QR: part, tot, rowj, diag, bar (0 when not used)
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
@@ -891,10 +893,11 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
     const size_t rc = (size_t)c->cap, ry = rc * (size_t)htg_cp_terms(c->d);
     size_t nmax = 1;
     for (int i = 0; i < c->d; ++i) nmax = nmax > (size_t)c->n[i] ? nmax : (size_t)c->n[i];
-    const size_t cps[11] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
+    const size_t cps[12] = {c->d * rc * rc, c->d * ry * rc, ry * rc, rc * rc, nmax * rc,
                             HT_MAXD * nmax * rc, rc, 64, (4 * HT_MAXD * sizeof(GemmDesc)) / sizeof(double) + 1,
-                            HT_MAXD * nmax * 3 * rc, 4 + 32};   // acc2 (4 doubles) + 64 barrier words
-    for (int j = 0; j < 11; ++j) {
+                            HT_MAXD * nmax * 3 * rc, 4 + 32,   // acc2 (4 doubles) + 64 barrier words
+                            HT_MAXD * nmax * 3 * rc};          // ZT
+    for (int j = 0; j < 12; ++j) {
       W->off_cp[j] = off;
       off = align_up(off + cps[j] * sizeof(double));
     }
@@ -989,6 +992,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->cp.Z = (double*)(base + W.off_cp[9]);
     c->cp.acc2 = (double*)(base + W.off_cp[10]);
     c->cp.bar = (unsigned int*)(base + W.off_cp[10] + 4 * sizeof(double));
+    c->cp.ZT = (double*)(base + W.off_cp[11]);
     c->cp.rcap = cfg->cap;
     c->cp.rycap = cfg->cap * htg_cp_terms(cfg->d);
     int nmax = 1;
@@ -1007,6 +1011,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     delete c;
     return HT_ERR_CUDA;
   }
+  c->cp_clu = htg_cp_cluster_setup(cfg->device);
   // wide node factors: the cluster form of the SVD, when a cluster fits this device
   if (c->Kc >= c->svd_min_cols) {
     c->svd_clu = htg_svd_cluster_setup(cfg->device);
@@ -1740,6 +1745,8 @@ int htg_ctx_d(const ht_ctx* c) { return c->cfg.d; }
 const int* htg_ctx_n(const ht_ctx* c) { return c->cfg.n; }
 int* htg_ctx_err(ht_ctx* c) { return c->err; }
 int htg_ctx_grid(const ht_ctx* c) { return c->gemm_grid; }
+int htg_ctx_cp_form(const ht_ctx* c) { return c->cfg.cp_form; }
+const CpClusterCfg* htg_ctx_cp_cluster(const ht_ctx* c) { return &c->cp_clu; }
 int htg_ctx_cap(const ht_ctx* c) { return c->cfg.cap; }
 int htg_ctx_max_terms(const ht_ctx* c) { return c->cfg.max_terms; }
 int htg_ctx_device(const ht_ctx* c) { return c->cfg.device; }

@@ -23,6 +23,7 @@ HT_MAXSTENCIL = 9
 
 HT_OK, HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA, HT_ERR_NONFINITE, HT_ERR_TIMEOUT, HT_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 HT_PREC_FP64, HT_PREC_MIXED = 0, 1
+CP_FORM_AUTO, CP_FORM_GRID = 0, 1   # ht_config.cp_form
 HT_F_IDENTITY, HT_F_STENCIL, HT_F_DIAG, HT_F_RANK1, HT_F_DIAG_STENCIL = 0, 1, 2, 3, 4
 HT_APPLY_L, HT_APPLY_EULER, HT_APPLY_RK2POLY = 0, 1, 2
 HT_SCHEME_RK2POLY, HT_SCHEME_HEUN2 = 0, 1
@@ -55,7 +56,8 @@ class ht_op(C.Structure):
 class ht_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int * HT_MAXD), ("cap", C.c_int), ("max_terms", C.c_int),
                 ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int), ("mixed_slices", C.c_int),
-                ("tc_min_work", C.c_longlong), ("gemm_ctas_per_sm", C.c_int), ("svd_cluster_min_cols", C.c_int)]
+                ("tc_min_work", C.c_longlong), ("gemm_ctas_per_sm", C.c_int), ("svd_cluster_min_cols", C.c_int),
+                ("cp_form", C.c_int)]
 
 
 _EXPORTS = {
@@ -94,6 +96,7 @@ _EXPORTS = {
                                C.c_void_p, C.c_void_p]),
     "cp_als_sweep_rk2": (C.c_int, [C.c_void_p, C.POINTER(cp_tensor), C.POINTER(ht_op), C.c_double,
                                    C.POINTER(cp_tensor), C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    "cp_als_rk2_cluster_ctas": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "cp_als_sweep_noalloc": (C.c_int, [C.POINTER(cp_tensor), C.POINTER(cp_tensor), C.c_int, C.c_int,
                                        C.c_void_p, C.c_void_p, C.c_void_p]),
     "ht_selftest_grid_barrier": (C.c_int, [C.c_int, C.c_int, C.c_int]),
@@ -182,10 +185,12 @@ class Context:
     """Owns an ht_ctx (workspace on the device)."""
 
     def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
-                 device: int = 0, tree: int = 0, mixed_slices: int = 0, tuning: dict | None = None):
+                 device: int = 0, tree: int = 0, mixed_slices: int = 0, tuning: dict | None = None,
+                 cp_form: int = 0):
         """tuning: values for the ht_config tuning fields (tc_min_work, gemm_ctas_per_sm,
         svd_cluster_min_cols); None takes the tuning cache of this device when one exists
-        (paper_1803_10270_gb300.tune), {} the library defaults."""
+        (paper_1803_10270_gb300.tune), {} the library defaults.  cp_form: CP_FORM_AUTO (the
+        cluster form of cp_als_sweep_rk2 where it fits) or CP_FORM_GRID."""
         lib = load()
         cfg = ht_config()
         cfg.d = d
@@ -197,6 +202,7 @@ class Context:
         cfg.device = device
         cfg.tree = tree
         cfg.mixed_slices = mixed_slices
+        cfg.cp_form = cp_form
         if tuning is None:
             from paper_1803_10270_gb300 import tune as _tune
             tuning = _tune.cached(device, max(3, max_terms + 2) * cap)
@@ -559,6 +565,14 @@ def cp_als_sweep_rk2(ctx: Context, x_old: CPTensor, op: ht_op, dt: float, x: CPT
     _check(load().cp_als_sweep_rk2(ctx.ptr, C.byref(x_old.struct), C.byref(op), dt, C.byref(x.struct), sweeps,
                                    variant, C.c_void_p(eps.data_ptr() if eps is not None else 0),
                                    _stream_ptr(stream)), "cp_als_sweep_rk2")
+
+
+def cp_als_rk2_cluster_ctas(ctx: Context, r: int, r0: int) -> int:
+    """CTAs of the thread-block cluster cp_als_sweep_rk2 (Gauss-Seidel) runs on for ranks r and r0
+    on this context, 0 when it takes the cooperative grid form."""
+    out = C.c_int(0)
+    _check(load().cp_als_rk2_cluster_ctas(ctx.ptr, int(r), int(r0), C.byref(out)), "cp_als_rk2_cluster_ctas")
+    return int(out.value)
 
 
 def cp_cn_als_step(ctx: Context, x_n: CPTensor, op: ht_op, dt: float, x: CPTensor, sweeps: int,

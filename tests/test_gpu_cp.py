@@ -130,9 +130,19 @@ def test_cp_step_adv6d_n64_shape(G):
     assert np.abs(_entries(got, idx) - er).max() <= 1e-10 * np.abs(er).max()
 
 
-def test_structured_rk2_als_bench_configuration(G):
+FORMS = ["cluster", "grid"]
+
+
+def _form(G, name):
+    return G.CP_FORM_AUTO if name == "cluster" else G.CP_FORM_GRID
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_structured_rk2_als_bench_configuration(G, form):
     """cp_als_sweep_rk2 in the launch configuration the benchmark times (d=6, n=64, rank 24, 5
-    Gauss-Seidel sweeps; one CTA per factor column): the padded first step (x_old = the rank-2
+    Gauss-Seidel sweeps), in both forms: one thread-block cluster of 12 CTAs with two factor
+    columns each (the default here), and the cooperative grid of one CTA per factor column.
+    The padded first step (x_old = the rank-2
     initial condition) and then steps 2..5 each taken from the oracle's own state (x_old aliasing
     x, the benchmark's steady-state call).  Several chained ALS steps cannot be compared: from
     the third step on a 1e-15 perturbation grows to 1e-5 (the fit's weights reach 1e7 and
@@ -144,7 +154,9 @@ def test_structured_rk2_als_bench_configuration(G):
     A = advection_A(case)
     op = G.advection_op(case.c, case.h)
     pad = cp_padding([n] * d, r - 2, seed=0x5EED + 1, scale=1e-3)
-    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1, cp_form=_form(G, form))
+    want = 12 if form == "cluster" else 0
+    assert G.cp_als_rk2_cluster_ctas(ctx, r, r) == want and G.cp_als_rk2_cluster_ctas(ctx, r, 2) == want
     idx = _sample_idx(d, n)
     x = OC.CP(np.ones(2), case.ic_factors())
     X = G.CPTensor(d, [n] * d, r)
@@ -169,8 +181,9 @@ def test_structured_rk2_als_bench_configuration(G):
         x = ref
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("variant", ["gs", "jacobi_damped"])
-def test_structured_rk2_als_matches_oracle_step(G, variant):
+def test_structured_rk2_als_matches_oracle_step(G, variant, form):
     """cp_als_sweep_rk2 (y never formed) == oracle: ALS on y = p(dt L) x from the padded x."""
     import torch
     d, n, r = 5, 7, 6
@@ -180,7 +193,9 @@ def test_structured_rk2_als_matches_oracle_step(G, variant):
     pad = cp_padding([n] * d, r - 2, seed=5, scale=1e-3)
     ref, eps = OC.step_rk2(x, A, r, pad, 3, variant)
     xi = OC.pad(x, r, pad)
-    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1, cp_form=_form(G, form))
+    if form == "cluster":
+        assert G.cp_als_rk2_cluster_ctas(ctx, r, 2) == 6
     X = G.CPTensor(d, [n] * d, r)
     X.upload(xi.weights, xi.factors)
     Xold = G.CPTensor(d, [n] * d, r)
@@ -195,13 +210,14 @@ def test_structured_rk2_als_matches_oracle_step(G, variant):
     np.testing.assert_allclose(e.cpu().numpy(), eps, rtol=1e-6, atol=1e-14)
 
 
-def test_structured_rk2_als_aliased_state(G):
+@pytest.mark.parametrize("form", FORMS)
+def test_structured_rk2_als_aliased_state(G, form):
     """x_old aliasing x (the steady-state call of a time loop): two steps vs the oracle."""
     d, n, r = 4, 6, 4
     case = advection_case(d, n, seed=33)
     A = advection_A(case)
     x = OC.CP(np.ones(r), cp_random_factors([n] * d, r, seed=6))
-    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1, cp_form=_form(G, form))
     X = G.CPTensor(d, [n] * d, r)
     X.upload(x.weights, x.factors)
     op = G.advection_op(case.c, case.h)
