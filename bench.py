@@ -40,7 +40,8 @@ D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel", "qr": "qr_r_kernel",
                 "svd": "svd_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
-                "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...", "cp_solve": "cp_als_rk2_persistent"}
+                "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...",
+                "cp_solve": "cp_als_rk2_cluster/cp_als_rk2_persistent"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -1244,6 +1245,16 @@ def profile_pass(W, torch, flush, steps: int):
     prof = profiled_steps(W.ctx, torch, flush, W.step, steps)
     rl, shares = class_roofline(prof, steps)
     roof = rl["dominant"]
+    if roof["class"] == "cp_solve":
+        # the form cp_als_sweep_rk2 took on this context names the kernel and its counter record
+        kern = "cp_als_rk2_cluster" if W.G.cp_als_rk2_cluster_ctas(W.ctx, CP_R, CP_R) else "cp_als_rk2_persistent"
+        roof["kernel"] = kern
+        roof["traffic"] = None
+        roof.pop("traffic_record", None)
+        rec = counter_record(kern)
+        if rec is not None:
+            roof["traffic"] = rec.get("dram_bytes_per_launch")
+            roof["traffic_record"] = {k: rec[k] for k in ("workload", "when") if k in rec}
     if roof["class"] == "cp_solve" and roof["avg_launch_us"]:
         alg = cp_survey_flops_per_launch()
         roof["executed_flops_per_launch"] = roof.get("flops_per_launch")
