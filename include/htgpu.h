@@ -389,8 +389,8 @@ int cp_als_sweep_noalloc(const cp_tensor* y, cp_tensor* x, int sweeps, int varia
 int cp_cn_als_step(ht_ctx* ctx, const cp_tensor* x_n, const ht_op* L, double dt, cp_tensor* x, int sweeps,
                    int variant, double* eps_dev, void* stream);
 
-/* Self-test of the bounded grid barrier that the persistent ALS kernel (cp_als_sweep_rk2) uses
- * between its phases.  The paper has no counterpart.  Launches nblocks (1..64) cooperative CTAs
+/* Self-test of the bounded grid barrier that the cooperative grid form of the persistent ALS
+ * kernel (cp_als_sweep_rk2) uses between its phases.  The paper has no counterpart.  Launches nblocks (1..64) cooperative CTAs
  * on `device` that meet at one barrier; CTA `absent` (or none when absent < 0) skips it, so the
  * others wait out the bounded limit (about 0.2 s of SM clock) and report instead of hanging.
  * Synchronising (allocates and frees its own 2 KB).  Returns HT_OK when every CTA passed, the
