@@ -334,7 +334,10 @@ __global__ void __launch_bounds__(NT) qr_r_kernel(const QrDesc* __restrict__ des
 
 
 // ---------------------------------------------------------------- cooperative form ----
-// G CTAs per matrix, CTA g owning the rows [g mb, (g+1) mb) of the matrix in its scratch buffer.
+// One CTA per SM, shared out over the launch's wide matrices in proportion to their work m k^2
+// (an equal share per matrix left the largest matrix of a level setting the launch time: 33 ms
+// for a level whose work split by weight takes about half); CTA g of a matrix's G owns the rows
+// [g mb, (g+1) mb).
 // Column j: (1) each CTA forms the partial dot products of column j with the columns c >= j
 // over its rows >= j (c = j gives the squared norm), and the owner of row j publishes that row;
 // (2) after a barrier of the matrix's CTAs, CTA g totals the columns c = j + g (mod G); (3)
@@ -379,12 +382,48 @@ __device__ bool coop_barrier(unsigned* flags, int G, int g, unsigned seq, int* e
   return ok_sh != 0;
 }
 
-__global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int G, QrCoopWs w,
+__global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int ndesc, QrCoopWs w,
                                                         int smem_doubles) {
-  const int d = blockIdx.x / G, g = blockIdx.x % G;
+  // The launch's CTAs are shared out over the eligible matrices in proportion to their work
+  // m k^2: two each, and the rest of the grid by those weights (the same computation in every
+  // CTA, so all agree).  Against an equal share of at most 64 CTAs per matrix: the kinetic
+  // workload's QR went from 122 to 100 ms per step (its largest matrices got 64-84 CTAs instead
+  // of 38); two equal 36864 x 192 matrices (76 CTAs each instead of 64) within run-to-run
+  // spread.  CTA g of matrix d's group of G sits at grid position base + g; barrier
+  // words and partial sums are indexed by grid position.
+  __shared__ int s_d, s_g, s_G, s_base;
+  if (threadIdx.x == 0) {
+    double wsum = 0.0;
+    int ne = 0;
+    for (int i = 0; i < ndesc; ++i) {
+      const QrDesc qi = descs[i];
+      if (qi.m > 0 && qi.k > 0 && qr_coop_eligible(qi.m, qi.k)) {
+        wsum += (double)qi.m * qi.k * qi.k;
+        ++ne;
+      }
+    }
+    const int spare = htg_max(0, (int)gridDim.x - 2 * ne);
+    int base = 0;
+    s_d = -1;
+    for (int i = 0; i < ndesc; ++i) {
+      const QrDesc qi = descs[i];
+      int Gi = 0;
+      if (qi.m > 0 && qi.k > 0 && qr_coop_eligible(qi.m, qi.k))
+        Gi = htg_min(qi.m, 2 + (int)(spare * ((double)qi.m * qi.k * qi.k / wsum)));
+      if ((int)blockIdx.x >= base && (int)blockIdx.x < base + Gi) {
+        s_d = i;
+        s_g = (int)blockIdx.x - base;
+        s_G = Gi;
+        s_base = base;
+      }
+      base += Gi;
+    }
+  }
+  __syncthreads();
+  if (s_d < 0) return;   // a CTA beyond the shares (uniform over the CTA)
+  const int d = s_d, g = s_g, G = s_G, gbase = s_base;
   const QrDesc q = descs[d];
   const int m = q.m, k = q.k;
-  if (m <= 0 || k <= 0 || !qr_coop_eligible(m, k)) return;   // uniform over the matrix's CTAs
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = QRC_NT / 32;
   const int mb = (m + G - 1) / G, r0 = htg_min(m, g * mb), r1 = htg_min(m, r0 + mb);
   // the CTA's rows [r0, r1): in shared memory (ld mb) when they fit, else in the scratch buffer
@@ -393,15 +432,15 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   const bool local = (long long)mb * k <= (long long)smem_doubles;
   const long long ld = local ? mb : m;
   double* S = local ? qsm : q.scratch + r0;
-  double* part = w.part + ((long long)d * G + g) * w.kmax;
-  double* part0 = w.part + (long long)d * G * w.kmax;
+  double* part = w.part + ((long long)gbase + g) * w.kmax;
+  double* part0 = w.part + (long long)gbase * w.kmax;
   double* tot = w.tot + (long long)d * w.kmax;
   // row j is published into one of two buffers by step parity: a CTA may publish row j+1 while
   // a slower one still reads row j (no barrier between a step's update and the next step's
   // dot products); two steps apart, the next step's first barrier separates them
   double* rowj2 = w.rowj + (long long)d * 2 * w.kmax;
   double* diag = w.diag + (long long)d * w.kmax;
-  unsigned* flags = w.bar + (long long)d * G;
+  unsigned* flags = w.bar + gbase;
   __shared__ double wc[1024];                // (v.c) tau for the columns of one step
   __shared__ double sh_v0, sh_alpha;
   for (long long e = tid; e < (long long)(r1 - r0) * k; e += QRC_NT) {
@@ -503,14 +542,17 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   const int nsm = (dev >= 0 && dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
   const int gsplit = ((long long)ndesc * count < nsm) ? QR_MAXSPLIT : 1;
   const int smem = gsplit > 1 ? QR_SMEM_WIDE : QR_SMEM_BYTES;
-  const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax;
+  // the cooperative form gives every wide matrix at least two CTAs of a one-per-SM grid
+  const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax && 2 * ndesc <= htg_min(nsm, coop->ndmax * coop->gmax);
   qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, smem, s>>>(
       descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, use_coop ? 1 : 0, flops);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !use_coop) return e;
-  // the wide matrices: G CTAs each, all resident (cooperative launch)
-  const int G = htg_max(2, htg_min(coop->gmax, nsm / ndesc));
-  e = cudaMemsetAsync(coop->bar, 0, (size_t)ndesc * G * sizeof(unsigned), s);
+  // the wide matrices: one CTA per SM (all resident, cooperative launch), shared out over the
+  // matrices by their work inside the kernel; barrier words and partial sums by grid position
+  // (the workspace holds ndmax x gmax of each)
+  const int grid = htg_min(nsm, coop->ndmax * coop->gmax);
+  e = cudaMemsetAsync(coop->bar, 0, (size_t)grid * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   static bool cattr[64] = {false};
   if (dev < 0 || dev >= 64 || !cattr[dev]) {
@@ -519,7 +561,7 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
     if (dev >= 0 && dev < 64) cattr[dev] = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ndesc * G);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(QRC_NT);
   cfg.dynamicSmemBytes = QRC_SMEM_BYTES;
   cfg.stream = s;
@@ -528,5 +570,5 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   lattr[0].val.cooperative = 1;
   cfg.attrs = lattr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, G, *coop, (int)(QRC_SMEM_BYTES / sizeof(double)));
+  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, ndesc, *coop, (int)(QRC_SMEM_BYTES / sizeof(double)));
 }
