@@ -91,17 +91,23 @@ cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cuda
 cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, int slices, cudaStream_t s,
                                double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr,
                                long long tc_min = 0);
-// Workspace of the cooperative QR (matrices wider than 64 columns and above 2^17 entries, one
-// instance per launch): per descriptor d and CTA g of its group, partial dot products
-// part[(d G + g) kmax + c], totals tot[d kmax + c], the published row j in two buffers by step
-// parity rowj[(2 d + (j & 1)) kmax + c], the diagonal of R diag[d kmax + c], and barrier words
-// bar[d G + g] (zeroed by the launcher).
+// Workspace of the cooperative QR (one instance per launch): per grid position s (the CTAs of a
+// matrix sit at consecutive positions) partial dot products part[s kmax + c] and, after the
+// QR_COOP_SLOTS such rows, the partial Gram blocks of the panels' trailing updates
+// part[QR_COOP_SLOTS kmax + s QR_COOP_QB (QR_COOP_QB + kmax) + ...];
+// per descriptor d totals tot[d kmax + c], the published row j in two buffers by step parity
+// rowj[(2 d + (j & 1)) kmax + c], the diagonal of R diag[d kmax + c], the panel's reduced Gram
+// block and W wtot[d QR_COOP_QB (QR_COOP_QB + kmax) + ...]; barrier words bar[s] (zeroed by the
+// launcher).
+constexpr int QR_COOP_QB = 16;       // panel width (columns whose reflectors are applied together)
+constexpr int QR_COOP_SLOTS = 256;   // grid positions the workspace serves (at least the SMs)
 struct QrCoopWs {
   double* part;
   double* tot;
   double* rowj;
   double* diag;
   unsigned* bar;
+  double* wtot;
   int* err;
   int kmax;     // largest k
   int ndmax;    // largest descriptor count of one launch

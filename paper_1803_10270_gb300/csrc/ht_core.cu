@@ -860,7 +860,7 @@ static int trunc_input_cap(const ht_config* c) {
 
 struct WsLayout {
   size_t off_plan, off_err, off_tick, off_app_rank, off_stage_rank, off_wn, off_ptrs, off_cp[12], off_prof;
-  size_t off_coop[5];           // cooperative QR: part, tot, rowj, diag, bar (0 when not used)
+  size_t off_coop[6];           // cooperative QR: part, tot, rowj, diag, bar, wtot (0 when not used)
   size_t node_off[NN][16];
   size_t app_off[NN], stage_off[NN];
   size_t total;
@@ -874,12 +874,13 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   W->off_plan = off; off = align_up(off + sizeof(Plan));
   W->off_err = off; off = align_up(off + 64);
   W->off_tick = off; off = align_up(off + 2 * NN * sizeof(unsigned));
-  for (int j = 0; j < 5; ++j) W->off_coop[j] = 0;
+  for (int j = 0; j < 6; ++j) W->off_coop[j] = 0;
   if ((size_t)Kc >= (size_t)QR_COOP_MIN_KC) {
-    const size_t nd = QR_COOP_NDMAX, gm = QR_COOP_GMAX;
-    const size_t sz[5] = {nd * gm * Kc * sizeof(double), nd * Kc * sizeof(double), 2 * nd * Kc * sizeof(double),
-                          nd * Kc * sizeof(double), nd * gm * sizeof(unsigned)};
-    for (int j = 0; j < 5; ++j) {
+    const size_t nd = QR_COOP_NDMAX, sl = QR_COOP_SLOTS, qb = QR_COOP_QB;
+    const size_t slot = qb * (qb + Kc);   // a panel's partial block
+    const size_t sz[6] = {sl * (Kc + slot) * sizeof(double), nd * Kc * sizeof(double), 2 * nd * Kc * sizeof(double),
+                          nd * Kc * sizeof(double), sl * sizeof(unsigned), nd * slot * sizeof(double)};
+    for (int j = 0; j < 6; ++j) {
       W->off_coop[j] = off;
       off = align_up(off + sz[j]);
     }
@@ -978,6 +979,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     c->qr_coop.rowj = (double*)(base + W.off_coop[2]);
     c->qr_coop.diag = (double*)(base + W.off_coop[3]);
     c->qr_coop.bar = (unsigned*)(base + W.off_coop[4]);
+    c->qr_coop.wtot = (double*)(base + W.off_coop[5]);
     c->qr_coop.err = c->err;
     c->qr_coop.kmax = c->Kc;
     c->qr_coop.ndmax = QR_COOP_NDMAX;

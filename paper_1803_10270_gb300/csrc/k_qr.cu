@@ -429,7 +429,8 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   // the CTA's rows [r0, r1): in shared memory (ld mb) when they fit, else in the scratch buffer
   // (ld m); S points at row r0, so element (i, c) of the matrix is S[(i - r0) + ld c]
   extern __shared__ double qsm[];
-  const bool local = (long long)mb * k <= (long long)smem_doubles;
+  // ... together with the QB x max(k, QRC_NT) staging area of the panel updates
+  const bool local = (long long)mb * k + (long long)QR_COOP_QB * htg_max(k, QRC_NT) <= (long long)smem_doubles;
   const long long ld = local ? mb : m;
   double* S = local ? qsm : q.scratch + r0;
   double* part = w.part + ((long long)gbase + g) * w.kmax;
@@ -449,63 +450,174 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   }
   unsigned seq = 0;
   const int rmax = htg_min(m, k);
-  for (int j = 0; j < rmax; ++j) {
-    __syncthreads();
-    const int i0 = htg_max(j, r0);
-    const double* x = S + ld * j;
-    for (int c = j + wid; c < k; c += nw) {
-      const double* cc = S + ld * c;
-      double sdot = 0.0;
-      for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i - r0], cc[i - r0], sdot);
-      sdot = warp_sum(sdot);
-      if (lane == 0) part[c] = sdot;
-    }
-    double* rowj = rowj2 + (long long)(j & 1) * w.kmax;
-    if (j >= r0 && j < r1)
-      for (int c = j + tid; c < k; c += QRC_NT) rowj[c] = S[(j - r0) + ld * c];
-    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
-    for (int c = j + g + G * wid; c < k; c += G * nw) {
-      double t = 0.0;
-      for (int h = lane; h < G; h += 32) t += __ldcg(part0 + (long long)h * w.kmax + c);
-      t = warp_sum(t);
-      if (lane == 0) tot[c] = t;
-    }
-    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
-    // the reflector of column j (every CTA forms the same one)
-    const int nc = k - j - 1;
-    if (tid == 0) {
-      const double n2 = __ldcg(tot + j), x0 = __ldcg(rowj + j);
-      double alpha = 0.0, v0 = 0.0, ri = 0.0, rv = 0.0;
-      if (htg_dpos(n2)) {
-        const double nrm = sqrt(n2);
-        alpha = htg_dpos(x0) ? -nrm : nrm;
-        v0 = x0 - alpha;
-        ri = 1.0 / nrm;
-        rv = 1.0 / (fabs(x0) + nrm);      // tau = 2 / (v.v) = ri rv
+  constexpr int QB = QR_COOP_QB;
+  const long long slotsz = (long long)QB * (QB + w.kmax);
+  // the panels' partial blocks after the column steps' partial sums (QR_COOP_SLOTS x kmax): the
+  // launch's matrices run independently, so the two kinds must not share memory
+  double* slots = w.part + (long long)QR_COOP_SLOTS * w.kmax;
+  double* wtot = w.wtot + (long long)d * slotsz;   // the panel's reduced [V^T V | V^T C], then W
+  double* wsm = local ? qsm + (long long)mb * k : qsm;   // QB x max(k, QRC_NT) staging
+  __shared__ double v0s[QB], taus[QB];
+  // V(i, p) of the current panel (rows i >= j0): 0 above its diagonal, v0 on it, the reduced
+  // column below
+  auto vval = [&](int i, int p, int j0) -> double {
+    const int jd = j0 + p;
+    return (i < jd) ? 0.0 : (i == jd ? v0s[p] : S[(i - r0) + ld * jd]);
+  };
+  for (int j0 = 0; j0 < rmax; j0 += QB) {
+    const int j1 = htg_min(rmax, j0 + QB), pb = j1 - j0;
+    // ---- the panel: columns j0 .. j1-1 one at a time, restricted to the panel's columns
+    for (int j = j0; j < j1; ++j) {
+      __syncthreads();
+      const int i0 = htg_max(j, r0);
+      const double* x = S + ld * j;
+      for (int c = j + wid; c < j1; c += nw) {
+        const double* cc = S + ld * c;
+        double sdot = 0.0;
+        for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i - r0], cc[i - r0], sdot);
+        sdot = warp_sum(sdot);
+        if (lane == 0) part[c] = sdot;
       }
-      sh_v0 = v0;
-      sh_alpha = alpha;
-      wc[0] = ri;
-      wc[1] = rv;
-      if (j >= r0 && j < r1) diag[j] = alpha;   // read back at the end by this CTA only
-    }
-    __syncthreads();
-    const double ri = wc[0], rv = wc[1], alpha = sh_alpha, v0 = sh_v0;
-    __syncthreads();
-    for (int c0 = 0; c0 < nc; c0 += 1024) {
-      const int cn = htg_min(1024, nc - c0);
-      for (int t = tid; t < cn; t += QRC_NT) {
-        const int c = j + 1 + c0 + t;
+      double* rowj = rowj2 + (long long)(j & 1) * w.kmax;
+      if (j >= r0 && j < r1)
+        for (int c = j + tid; c < j1; c += QRC_NT) rowj[c] = S[(j - r0) + ld * c];
+      if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+      for (int c = j + g + G * wid; c < j1; c += G * nw) {
+        double t = 0.0;
+        for (int h = lane; h < G; h += 32) t += __ldcg(part0 + (long long)h * w.kmax + c);
+        t = warp_sum(t);
+        if (lane == 0) tot[c] = t;
+      }
+      if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+      // the reflector of column j (every CTA forms the same one)
+      const int nc = j1 - j - 1;
+      if (tid == 0) {
+        const double n2 = __ldcg(tot + j), x0 = __ldcg(rowj + j);
+        double alpha = 0.0, v0 = 0.0, ri = 0.0, rv = 0.0;
+        if (htg_dpos(n2)) {
+          const double nrm = sqrt(n2);
+          alpha = htg_dpos(x0) ? -nrm : nrm;
+          v0 = x0 - alpha;
+          ri = 1.0 / nrm;
+          rv = 1.0 / (fabs(x0) + nrm);      // tau = 2 / (v.v) = ri rv
+        }
+        sh_v0 = v0;
+        sh_alpha = alpha;
+        wc[0] = ri;
+        wc[1] = rv;
+        v0s[j - j0] = v0;
+        taus[j - j0] = ri * rv;
+        if (j >= r0 && j < r1) diag[j] = alpha;   // read back at the end by this CTA only
+      }
+      __syncthreads();
+      const double ri = wc[0], rv = wc[1], alpha = sh_alpha, v0 = sh_v0;
+      __syncthreads();
+      for (int t = tid; t < nc; t += QRC_NT) {
+        const int c = j + 1 + t;
         const double vc = __ldcg(tot + c) - alpha * __ldcg(rowj + c);
         wc[t] = (vc * ri) * rv;
       }
       __syncthreads();
-      for (long long e = tid; e < (long long)(r1 - i0) * cn; e += QRC_NT) {
-        const int i = i0 + (int)(e % (r1 - i0)), c = j + 1 + c0 + (int)(e / (r1 - i0));
+      for (long long e = tid; e < (long long)(r1 - i0) * nc; e += QRC_NT) {
+        const int i = i0 + (int)(e % (r1 - i0)), c = j + 1 + (int)(e / (r1 - i0));
         const double vi = (i == j) ? v0 : x[i - r0];
-        S[(i - r0) + ld * c] = fma(-wc[c - (j + 1 + c0)], vi, S[(i - r0) + ld * c]);
+        S[(i - r0) + ld * c] = fma(-wc[c - (j + 1)], vi, S[(i - r0) + ld * c]);
       }
-      __syncthreads();
+    }
+    if (j1 >= k) continue;
+    // ---- the panel's reflectors applied to the trailing columns at once:
+    // H_{j1-1} ... H_{j0} = I - V T^T V^T (T upper triangular, T^-1 = diag(1 / tau) + the strictly
+    // upper part of V^T V), so C <- C - V W with (diag(1 / tau) + strict lower of V^T V) W = V^T C
+    const int nct = k - j1, ncol = pb + nct;
+    const int i0 = htg_max(j0, r0);
+    __syncthreads();
+    {
+      // partial [V^T V | V^T C] over this CTA's rows i >= j0: entry (p, q) at slot[p + QB q];
+      // thread -> column q (and a part of the rows when the columns are fewer than the threads)
+      const int nrow = htg_max(0, r1 - i0);
+      const int P = (ncol < QRC_NT) ? htg_max(1, htg_min(8, QRC_NT / ncol)) : 1;
+      const int chunk = (nrow + P - 1) / P;
+      double* slot = slots + ((long long)gbase + g) * slotsz;
+      for (int t = tid; t < ncol * P; t += QRC_NT) {
+        const int qc = t % ncol, rp = t / ncol;
+        double acc[QB];
+#pragma unroll
+        for (int p = 0; p < QB; ++p) acc[p] = 0.0;
+        const int ia = i0 + rp * chunk, ib = htg_min(r1, ia + chunk);
+        for (int i = ia; i < ib; ++i) {
+          const double xq = (qc < pb) ? vval(i, qc, j0) : S[(i - r0) + ld * (j1 + qc - pb)];
+#pragma unroll
+          for (int p = 0; p < QB; ++p)
+            if (p < pb) acc[p] = fma(vval(i, p, j0), xq, acc[p]);
+        }
+        if (P == 1) {
+#pragma unroll
+          for (int p = 0; p < QB; ++p) slot[p + (long long)QB * qc] = acc[p];
+        } else {
+#pragma unroll
+          for (int p = 0; p < QB; ++p) wsm[((long long)rp * QB + p) * ncol + qc] = acc[p];
+        }
+      }
+      if (P > 1) {
+        __syncthreads();
+        for (int t = tid; t < QB * ncol; t += QRC_NT) {
+          const int p = t % QB, qc = t / QB;
+          double v = 0.0;
+          for (int rp = 0; rp < P; ++rp) v += wsm[((long long)rp * QB + p) * ncol + qc];
+          slot[p + (long long)QB * qc] = v;
+        }
+      }
+    }
+    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+    // the totals: CTA g sums the columns q = g, g + G, ... over the G slots
+    for (int t = tid; t < QB * ((ncol - g + G - 1) / G); t += QRC_NT) {
+      const int p = t % QB, qc = g + G * (t / QB);
+      const double* src = slots + (long long)gbase * slotsz + p + (long long)QB * qc;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int h = 0;
+      for (; h + 3 < G; h += 4) {
+        s0 += __ldcg(src + (long long)h * slotsz);
+        s1 += __ldcg(src + (long long)(h + 1) * slotsz);
+        s2 += __ldcg(src + (long long)(h + 2) * slotsz);
+        s3 += __ldcg(src + (long long)(h + 3) * slotsz);
+      }
+      for (; h < G; ++h) s0 += __ldcg(src + (long long)h * slotsz);
+      wtot[p + (long long)QB * qc] = (s0 + s1) + (s2 + s3);
+    }
+    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+    // W for this CTA's trailing columns, in place: W_p = tau_p (Y_p - sum_{s<p} (V^T V)_{sp} W_s)
+    for (int qc = g + G * tid; qc < ncol; qc += G * QRC_NT) {
+      if (qc < pb) continue;
+      double wv[QB];
+#pragma unroll
+      for (int p = 0; p < QB; ++p) {
+        if (p < pb) {
+          double y = wtot[p + (long long)QB * qc];
+          for (int s2 = 0; s2 < p; ++s2) y = fma(-__ldcg(wtot + s2 + (long long)QB * p), wv[s2], y);
+          wv[p] = taus[p] * y;
+          wtot[p + (long long)QB * qc] = wv[p];
+        }
+      }
+    }
+    if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+    // C <- C - V W on this CTA's rows i >= j0: W staged in shared memory, a row's V in registers
+    for (int t = tid; t < QB * nct; t += QRC_NT) wsm[t] = __ldcg(wtot + (long long)QB * pb + t);
+    __syncthreads();
+    for (int i = i0 + tid; i < r1; i += QRC_NT) {
+      double vr[QB];
+#pragma unroll
+      for (int p = 0; p < QB; ++p) vr[p] = (p < pb) ? vval(i, p, j0) : 0.0;
+      double* srow = S + (i - r0);
+      for (int c = 0; c < nct; ++c) {
+        const double* wcol = wsm + (long long)QB * c;
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int p = 0; p < QB; p += 2) {
+          a0 = fma(vr[p], wcol[p], a0);
+          a1 = fma(vr[p + 1], wcol[p + 1], a1);
+        }
+        srow[ld * (j1 + c)] -= a0 + a1;
+      }
     }
   }
   // R: rows r < rmax of this CTA (diag from the alphas, upper part from the updated rows)
@@ -543,15 +655,16 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   const int gsplit = ((long long)ndesc * count < nsm) ? QR_MAXSPLIT : 1;
   const int smem = gsplit > 1 ? QR_SMEM_WIDE : QR_SMEM_BYTES;
   // the cooperative form gives every wide matrix at least two CTAs of a one-per-SM grid
-  const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax && 2 * ndesc <= htg_min(nsm, coop->ndmax * coop->gmax);
+  const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax && 2 * ndesc <= htg_min(nsm, QR_COOP_SLOTS) &&
+                        (long long)QR_COOP_QB * htg_max(coop->kmax, QRC_NT) * (long long)sizeof(double) <= QRC_SMEM_BYTES;
   qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, smem, s>>>(
       descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, use_coop ? 1 : 0, flops);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !use_coop) return e;
   // the wide matrices: one CTA per SM (all resident, cooperative launch), shared out over the
   // matrices by their work inside the kernel; barrier words and partial sums by grid position
-  // (the workspace holds ndmax x gmax of each)
-  const int grid = htg_min(nsm, coop->ndmax * coop->gmax);
+  // (the workspace holds QR_COOP_SLOTS of each)
+  const int grid = htg_min(nsm, QR_COOP_SLOTS);
   e = cudaMemsetAsync(coop->bar, 0, (size_t)grid * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   static bool cattr[64] = {false};
