@@ -272,6 +272,13 @@ __device__ void plan_pre_body(Plan* P, const TreeInfo& T, const Levels& L, const
       // |P_t|_F = |u|: with p columns, those with sigma^2 below (tol |u|)^2 / (2p (2d-3)) are
       // discarded by the rank rule whatever their mutual rotation (see SvdDesc::skip2)
       v.skip2 = 0.5 * skip_tol * skip_tol / (double)htg_max(2 * T.d - 3, 1);
+      // The root's children have P_t2 = R_t2 B^T R_t1^T = P_t1^T: one SVD serves both (t2's left
+      // singular vectors are t1's right ones and vice versa, the singular values shared), so
+      // neither P_t2 nor its SVD is formed
+      if (t == rb) {
+        P->g_Pall[t - 1].m = 0;
+        v.p = 0;
+      }
     }
     for (int s = 0; s < L.n_int[dep]; ++s) {
       const int t = L.inter[dep][s], a = T.c1[t], b = T.c2[t];
@@ -347,12 +354,12 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
     P->knew[t] = k;
     out.rank[t] = k;
     for (int j = 0; j < P->Rp[t]; ++j) {
-      const double sj = wn[t].sig[j];
+      const double sj = (j < p) ? s[j] : 0.0;   // the root's second child: its sibling's values
       wn[t].invsig[j] = (j < k && htg_dpos_finite(sj)) ? 1.0 / sj : 0.0;
     }
     if (sigma_out) {
       for (int j = 0; j < sig_stride; ++j)
-        sigma_out[(long long)t * sig_stride + j] = (j < P->Rp[t]) ? wn[t].sig[j] : 0.0;
+        sigma_out[(long long)t * sig_stride + j] = (j < P->Rp[t] && j < p) ? s[j] : 0.0;
     }
   }
   if (threadIdx.x == 0) out.rank[0] = 1;
@@ -371,9 +378,13 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
   int i = 0;
   for (int t = 1; t < T.nn; ++t) {
     const int k = P->knew[t];
-    fill_gemm(P->g_XY[i++], wn[t].W, P->Rp[t], 1, wn[t].Rf, P->Rp[t], 0, wn[t].X, k, k, P->K[t], P->Rp[t]);
+    // the root's second child: left singular vectors = its sibling's right ones (Rp[rb] rows,
+    // leading dimension mE[ra] = Rp[rb]), right ones = the sibling's left ones (Rp[ra] = mE[rb])
+    const double* Wt = (t == rb) ? wn[ra].Z : wn[t].W;
+    const double* Zt = (t == rb) ? wn[ra].W : wn[t].Z;
+    fill_gemm(P->g_XY[i++], Wt, P->Rp[t], 1, wn[t].Rf, P->Rp[t], 0, wn[t].X, k, k, P->K[t], P->Rp[t]);
     GemmDesc& y = P->g_XY[i++];
-    fill_gemm(y, wn[t].E, P->K[t], 0, wn[t].Z, P->mE[t], 0, wn[t].Y, P->K[t], P->K[t], k, P->mE[t]);
+    fill_gemm(y, wn[t].E, P->K[t], 0, Zt, P->mE[t], 0, wn[t].Y, P->K[t], P->K[t], k, P->mE[t]);
     y.colscale = wn[t].invsig;
     // X_t Y_t = W_k^T W_k S_k Z_k^T Z_k S_k^-1 = I_k in exact arithmetic; rounding in the SVD
     // breaks it by about eps |u| / s_k (Y divides by the kept singular values), and the edge's
