@@ -92,9 +92,9 @@ cudaError_t htg_launch_gemm_tc(const GemmDesc* descs_dev, int ndesc, int sms, in
                                double* flops = nullptr, int count = 1, long long inst_stride = 0, int* err = nullptr,
                                long long tc_min = 0);
 // Workspace of the cooperative QR (one instance per launch): per grid position s (the CTAs of a
-// matrix sit at consecutive positions) partial dot products part[s kmax + c] and, after the
-// QR_COOP_SLOTS such rows, the partial Gram blocks of the panels' trailing updates
-// part[QR_COOP_SLOTS kmax + s QR_COOP_QB (QR_COOP_QB + kmax) + ...];
+// matrix sit at consecutive positions) partial dot products in two buffers by column parity
+// part[((j & 1) QR_COOP_SLOTS + s) kmax + c] and, after them, the partial Gram blocks of the
+// panels' trailing updates part[2 QR_COOP_SLOTS kmax + s QR_COOP_QB (QR_COOP_QB + kmax) + ...];
 // per descriptor d totals tot[d kmax + c], the published row j in two buffers by step parity
 // rowj[(2 d + (j & 1)) kmax + c], the diagonal of R diag[d kmax + c], the panel's reduced Gram
 // block and W wtot[d QR_COOP_QB (QR_COOP_QB + kmax) + ...]; barrier words bar[s] (zeroed by the

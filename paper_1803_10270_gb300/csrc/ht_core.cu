@@ -889,7 +889,7 @@ static void layout(const ht_config* c, const TreeInfo& T, WsLayout* W) {
   if ((size_t)Kc >= (size_t)QR_COOP_MIN_KC) {
     const size_t nd = QR_COOP_NDMAX, sl = QR_COOP_SLOTS, qb = QR_COOP_QB;
     const size_t slot = qb * (qb + Kc);   // a panel's partial block
-    const size_t sz[6] = {sl * (Kc + slot) * sizeof(double), nd * Kc * sizeof(double), 2 * nd * Kc * sizeof(double),
+    const size_t sz[6] = {sl * (2 * Kc + slot) * sizeof(double), nd * Kc * sizeof(double), 2 * nd * Kc * sizeof(double),
                           nd * Kc * sizeof(double), sl * sizeof(unsigned), nd * slot * sizeof(double)};
     for (int j = 0; j < 6; ++j) {
       W->off_coop[j] = off;

@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
       const QrDesc qi = descs[i];
       int Gi = 0;
       if (qi.m > 0 && qi.k > 0 && qr_coop_eligible(qi.m, qi.k))
-        Gi = htg_min(qi.m, 2 + (int)(spare * ((double)qi.m * qi.k * qi.k / wsum)));
+        Gi = htg_min(htg_max(2, qi.m / 64), 2 + (int)(spare * ((double)qi.m * qi.k * qi.k / wsum)));
       if ((int)blockIdx.x >= base && (int)blockIdx.x < base + Gi) {
         s_d = i;
         s_g = (int)blockIdx.x - base;
@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   const long long slotsz = (long long)QB * (QB + w.kmax);
   // the panels' partial blocks after the column steps' partial sums (QR_COOP_SLOTS x kmax): the
   // launch's matrices run independently, so the two kinds must not share memory
-  double* slots = w.part + (long long)QR_COOP_SLOTS * w.kmax;
+  double* slots = w.part + 2LL * QR_COOP_SLOTS * w.kmax;
   double* wtot = w.wtot + (long long)d * slotsz;   // the panel's reduced [V^T V | V^T C], then W
   double* wsm = local ? qsm + (long long)mb * k : qsm;   // QB x max(k, QRC_NT) staging
   __shared__ double v0s[QB], taus[QB];
@@ -466,33 +466,38 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   };
   for (int j0 = 0; j0 < rmax; j0 += QB) {
     const int j1 = htg_min(rmax, j0 + QB), pb = j1 - j0;
-    // ---- the panel: columns j0 .. j1-1 one at a time, restricted to the panel's columns
+    // ---- the panel: columns j0 .. j1-1 one at a time, restricted to the panel's columns, one
+    // barrier per column: the partial dot products go to one of two buffers by step parity (as
+    // row j does), and after the barrier every CTA sums the panel's few columns itself
+    __shared__ double ptot[QB];
     for (int j = j0; j < j1; ++j) {
       __syncthreads();
       const int i0 = htg_max(j, r0);
       const double* x = S + ld * j;
+      double* partj = part + (long long)(j & 1) * QR_COOP_SLOTS * w.kmax;
+      const double* part0j = part0 + (long long)(j & 1) * QR_COOP_SLOTS * w.kmax;
       for (int c = j + wid; c < j1; c += nw) {
         const double* cc = S + ld * c;
         double sdot = 0.0;
         for (int i = i0 + lane; i < r1; i += 32) sdot = fma(x[i - r0], cc[i - r0], sdot);
         sdot = warp_sum(sdot);
-        if (lane == 0) part[c] = sdot;
+        if (lane == 0) partj[c] = sdot;
       }
       double* rowj = rowj2 + (long long)(j & 1) * w.kmax;
       if (j >= r0 && j < r1)
         for (int c = j + tid; c < j1; c += QRC_NT) rowj[c] = S[(j - r0) + ld * c];
       if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
-      for (int c = j + g + G * wid; c < j1; c += G * nw) {
+      for (int c = j + wid; c < j1; c += nw) {
         double t = 0.0;
-        for (int h = lane; h < G; h += 32) t += __ldcg(part0 + (long long)h * w.kmax + c);
+        for (int h = lane; h < G; h += 32) t += __ldcg(part0j + (long long)h * w.kmax + c);
         t = warp_sum(t);
-        if (lane == 0) tot[c] = t;
+        if (lane == 0) ptot[c - j0] = t;
       }
-      if (!coop_barrier(flags, G, g, ++seq, w.err)) return;
+      __syncthreads();
       // the reflector of column j (every CTA forms the same one)
       const int nc = j1 - j - 1;
       if (tid == 0) {
-        const double n2 = __ldcg(tot + j), x0 = __ldcg(rowj + j);
+        const double n2 = ptot[j - j0], x0 = __ldcg(rowj + j);
         double alpha = 0.0, v0 = 0.0, ri = 0.0, rv = 0.0;
         if (htg_dpos(n2)) {
           const double nrm = sqrt(n2);
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
       __syncthreads();
       for (int t = tid; t < nc; t += QRC_NT) {
         const int c = j + 1 + t;
-        const double vc = __ldcg(tot + c) - alpha * __ldcg(rowj + c);
+        const double vc = ptot[c - j0] - alpha * __ldcg(rowj + c);
         wc[t] = (vc * ri) * rv;
       }
       __syncthreads();
