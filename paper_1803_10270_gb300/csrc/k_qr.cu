@@ -537,39 +537,80 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
     const int i0 = htg_max(j0, r0);
     __syncthreads();
     {
-      // partial [V^T V | V^T C] over this CTA's rows i >= j0: entry (p, q) at slot[p + QB q];
-      // thread -> column q (and a part of the rows when the columns are fewer than the threads)
+      // partial [V^T V | V^T C] over this CTA's rows i >= j0: entry (p, q) at slot[p + QB q].
+      // Columns in passes of at most QRC_NT (a thread's QB accumulators stay in registers); a pass
+      // with fewer columns than threads splits the rows into P parts.  A row block in L2 goes
+      // through shared memory in chunks of rc rows: V's QB columns and the pass's columns, loaded
+      // with lanes over rows (coalesced), read with lanes over columns (odd stride: no bank
+      // conflicts) and V broadcast.
       const int nrow = htg_max(0, r1 - i0);
-      const int P = (ncol < QRC_NT) ? htg_max(1, htg_min(8, QRC_NT / ncol)) : 1;
-      const int chunk = (nrow + P - 1) / P;
       double* slot = slots + ((long long)gbase + g) * slotsz;
-      for (int t = tid; t < ncol * P; t += QRC_NT) {
-        const int qc = t % ncol, rp = t / ncol;
+      double* stg = wsm + (long long)QB * htg_max(k, QRC_NT);
+      for (int qa = 0; qa < ncol; qa += QRC_NT) {
+        const int nq = htg_min(QRC_NT, ncol - qa);
+        const int P = (nq < QRC_NT) ? htg_max(1, htg_min(8, QRC_NT / nq)) : 1;
+        const int qc = qa + tid % nq, rp = tid / nq;
+        const bool mine = tid < nq * P;
         double acc[QB];
 #pragma unroll
         for (int p = 0; p < QB; ++p) acc[p] = 0.0;
-        const int ia = i0 + rp * chunk, ib = htg_min(r1, ia + chunk);
-        for (int i = ia; i < ib; ++i) {
-          const double xq = (qc < pb) ? vval(i, qc, j0) : S[(i - r0) + ld * (j1 + qc - pb)];
+        if (local) {
+          if (mine) {
+            const int chunk = (nrow + P - 1) / P;
+            const int ia = i0 + rp * chunk, ib = htg_min(r1, ia + chunk);
+            for (int i = ia; i < ib; ++i) {
+              const double xq = (qc < pb) ? vval(i, qc, j0) : S[(i - r0) + ld * (j1 + qc - pb)];
 #pragma unroll
-          for (int p = 0; p < QB; ++p)
-            if (p < pb) acc[p] = fma(vval(i, p, j0), xq, acc[p]);
+              for (int p = 0; p < QB; ++p)
+                if (p < pb) acc[p] = fma(vval(i, p, j0), xq, acc[p]);
+            }
+          }
+        } else {
+          const int nqp = nq | 1;
+          const int avail = smem_doubles - QB * htg_max(k, QRC_NT);
+          const int RC = htg_max(1, htg_min(nrow, avail / (nqp + QB)));
+          double* Xs = stg;
+          double* Vs = stg + (long long)RC * nqp;
+          for (int c0 = i0; c0 < r1; c0 += RC) {
+            const int rc = htg_min(RC, r1 - c0);
+            __syncthreads();   // the previous chunk is consumed
+            for (int q = wid; q < nq; q += nw) {
+              const int qq = qa + q;
+              for (int ri = lane; ri < rc; ri += 32)
+                Xs[(long long)ri * nqp + q] = (qq < pb) ? vval(c0 + ri, qq, j0) : S[(c0 + ri - r0) + ld * (j1 + qq - pb)];
+            }
+            for (int p = wid; p < QB; p += nw)
+              for (int ri = lane; ri < rc; ri += 32) Vs[ri * QB + p] = (p < pb) ? vval(c0 + ri, p, j0) : 0.0;
+            __syncthreads();
+            if (mine) {
+              for (int ri = rp; ri < rc; ri += P) {
+                const double xq = Xs[(long long)ri * nqp + (qc - qa)];
+                const double* vrow = Vs + ri * QB;
+#pragma unroll
+                for (int p = 0; p < QB; ++p) acc[p] = fma(vrow[p], xq, acc[p]);
+              }
+            }
+          }
         }
         if (P == 1) {
+          if (mine) {
 #pragma unroll
-          for (int p = 0; p < QB; ++p) slot[p + (long long)QB * qc] = acc[p];
+            for (int p = 0; p < QB; ++p) slot[p + (long long)QB * qc] = acc[p];
+          }
         } else {
+          __syncthreads();
+          if (mine) {
 #pragma unroll
-          for (int p = 0; p < QB; ++p) wsm[((long long)rp * QB + p) * ncol + qc] = acc[p];
-        }
-      }
-      if (P > 1) {
-        __syncthreads();
-        for (int t = tid; t < QB * ncol; t += QRC_NT) {
-          const int p = t % QB, qc = t / QB;
-          double v = 0.0;
-          for (int rp = 0; rp < P; ++rp) v += wsm[((long long)rp * QB + p) * ncol + qc];
-          slot[p + (long long)QB * qc] = v;
+            for (int p = 0; p < QB; ++p) wsm[((long long)rp * QB + p) * nq + (qc - qa)] = acc[p];
+          }
+          __syncthreads();
+          for (int t = tid; t < QB * nq; t += QRC_NT) {
+            const int p = t % QB, q = t / QB;
+            double v = 0.0;
+            for (int r2 = 0; r2 < P; ++r2) v += wsm[((long long)r2 * QB + p) * nq + q];
+            slot[p + (long long)QB * (qa + q)] = v;
+          }
+          __syncthreads();
         }
       }
     }
@@ -608,12 +649,19 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
     // C <- C - V W on this CTA's rows i >= j0: W staged in shared memory, a row's V in registers
     for (int t = tid; t < QB * nct; t += QRC_NT) wsm[t] = __ldcg(wtot + (long long)QB * pb + t);
     __syncthreads();
-    for (int i = i0 + tid; i < r1; i += QRC_NT) {
+    // thread -> (row, part of the columns): rows by consecutive threads (coalesced), the columns
+    // split in CP parts when the rows are fewer than the threads
+    const int rows_cnt = htg_max(0, r1 - i0);
+    const int CP = (rows_cnt > 0 && rows_cnt < QRC_NT) ? htg_max(1, htg_min(8, QRC_NT / rows_cnt)) : 1;
+    const int cch = (nct + CP - 1) / CP;
+    for (int t = tid; t < rows_cnt * CP; t += QRC_NT) {
+      const int i = i0 + t % rows_cnt, cpi = t / rows_cnt;
+      const int ca = cpi * cch, cb = htg_min(nct, ca + cch);
       double vr[QB];
 #pragma unroll
       for (int p = 0; p < QB; ++p) vr[p] = (p < pb) ? vval(i, p, j0) : 0.0;
       double* srow = S + (i - r0);
-      for (int c = 0; c < nct; ++c) {
+      for (int c = ca; c < cb; ++c) {
         const double* wcol = wsm + (long long)QB * c;
         double a0 = 0.0, a1 = 0.0;
 #pragma unroll
@@ -661,7 +709,8 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   const int smem = gsplit > 1 ? QR_SMEM_WIDE : QR_SMEM_BYTES;
   // the cooperative form gives every wide matrix at least two CTAs of a one-per-SM grid
   const bool use_coop = coop && count == 1 && ndesc <= coop->ndmax && 2 * ndesc <= htg_min(nsm, QR_COOP_SLOTS) &&
-                        (long long)QR_COOP_QB * htg_max(coop->kmax, QRC_NT) * (long long)sizeof(double) <= QRC_SMEM_BYTES;
+                        ((long long)QR_COOP_QB * htg_max(coop->kmax, QRC_NT) + QRC_NT + 1 + QR_COOP_QB) *
+                                (long long)sizeof(double) <= QRC_SMEM_BYTES;
   qr_r_kernel<<<dim3(ndesc * gsplit, count), NT, smem, s>>>(
       descs_dev, inst_stride, (long long)(smem / sizeof(double)), gsplit, use_coop ? 1 : 0, flops);
   cudaError_t e = cudaGetLastError();
