@@ -71,7 +71,11 @@ typedef enum ht_precision {
                          the complement / square-root factors, the node factors P_t = R_t E_t, the
                          projections) run on the tensor cores: each FP64 operand row / column is
                          split into ht_config.mixed_slices BF16 digit planes, accumulated in FP32
-                         (tcgen05, tensor memory), normwise error about 2^-(8 slices - 1); the QR
+                         (tcgen05, tensor memory), normwise error about 2^-(8 slices - 1); those
+                         below ht_config.tc_min_work multiply-adds in a split-FP32 form on the CUDA
+                         cores (FP32 hi / lo operand parts, the compensated dot product of Ogita,
+                         Rump and Oishi: error at most about (k^2 + 5k + 10) 2^-47, in practice
+                         about (k/2 + 10) 2^-47, of the sum of |products|); the QR
                          R factors, node SVDs, truncation thresholds, the X_t Y_t = I refinement
                          of the kept subspaces, the apply and the CP route stay FP64 */
 } ht_precision;
@@ -404,12 +408,16 @@ int ht_selftest_grid_barrier(int nblocks, int absent, int device);
  * rsqrt) (device, 4n doubles).  Asynchronous on stream.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 int ht_selftest_fastmath(const double* x_dev, double* out_dev, int n, void* stream);
 
-/* Self-test of the tensor-core contraction of HT_PREC_MIXED contexts: C[b] = alpha op(A[b])
+/* Self-test of the contraction kernels of HT_PREC_MIXED contexts: C[b] = alpha op(A[b])
  * op(B[b]) diag(colscale) + beta C[b] for b < batch (column-major; op(A) m x k, op(B) k x n; tA/tB
  * select the stored transposes; strides sA, sB, sC between batch entries; colscale: device, n
- * values, or NULL), computed from `slices` (2..4) BF16 digit planes per operand with FP32
- * accumulation in tensor memory.  Element (i, j) is within about 2^-(8 slices - 1) k
- * max_l |op(A)_il| max_l |op(B)_lj| of the exact product.  The paper has no counterpart: the
+ * values, or NULL).  slices 2..4: the tensor-core kernel of the large contractions, from that many
+ * BF16 digit planes per operand with FP32 accumulation in tensor memory; element (i, j) is within
+ * about 2^-(8 slices - 1) k max_l |op(A)_il| max_l |op(B)_lj| of the exact product.  slices 1: the
+ * split-FP32 CUDA-core kernel of the small ones (FP32 hi / lo parts, double-float accumulation);
+ * element (i, j) is within about (k^2 + 5k + 10) 2^-47 sum_l |op(A)_il op(B)_lj| of the exact
+ * product (about (k/2 + 10) 2^-47 of it with rounding errors of random sign; operands of magnitude
+ * 2^128 or more are outside its range).  The paper has no counterpart: the
  * precision scheme is this library's.  Synchronising.  Returns HT_OK, HT_ERR_TIMEOUT (a bounded
  * wait gave up), HT_ERR_ARG or HT_ERR_CUDA. */
 /* Tuning probe (used by the package's autotuner; the paper has no counterpart): mean CUDA-event

@@ -83,6 +83,12 @@ struct SvdDesc {
 // (m n k batch), which the tensor-core launch of the same list takes.
 cudaError_t htg_launch_gemm(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops = nullptr,
                             int count = 1, long long inst_stride = 0, long long tc_min = 0);
+// The same descriptor lists in HT_PREC_MIXED's split-FP32 form (the contractions below tc_min
+// multiply-adds, all when tc_min <= 0): FP64 operands split into FP32 hi / lo parts, a
+// double-float accumulation on the FP32 pipe, at most about 2^-47 (k^2 + 5k + 10) sum |a_i b_i| of
+// error, about 2^-47 (k/2 + 10) sum |a_i b_i| in practice.
+cudaError_t htg_launch_gemm_f32x2(const GemmDesc* descs_dev, int ndesc, int grid, cudaStream_t s, double* flops,
+                                  int count, long long inst_stride, long long tc_min);
 // Tensor-core form of the same descriptor lists (HT_PREC_MIXED): `slices` (2..4) BF16 digit planes
 // per operand row / column, FP32 accumulation in tensor memory, one CTA per SM (a batch spreads
 // them over its instances).  flops (device, or nullptr) accumulates the executed MMA flops.

@@ -1142,12 +1142,14 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   const int g = c->gemm_grid;
   const long long st = (long long)sizeof(Plan);
   // the dense contractions: FP64 CUDA-core tiles; in HT_PREC_MIXED those of at least tc_min
-  // multiply-adds (decided per descriptor on the device) on the tensor cores, the rest in FP64
+  // multiply-adds (decided per descriptor on the device) on the tensor cores, the rest in the
+  // split-FP32 form on the CUDA cores (the same tiles, FP64-like accuracy on the FP32 pipe)
   const bool tc_on = c->slices && c->tc_reach;
   const long long tcm = tc_on ? htg_max_ll(1, c->tc_min) : 0;
   auto gemm64 = [&](const GemmDesc* d, int nd) -> cudaError_t {
-    return (tc_on && c->tc_min == 0) ? cudaSuccess
-                                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm);
+    if (tc_on && c->tc_min == 0) return cudaSuccess;
+    return c->slices ? htg_launch_gemm_f32x2(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm)
+                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm);
   };
   auto gemmtc = [&](const GemmDesc* d, int nd) -> cudaError_t {
     return htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMMTC), count, st, c->err, tcm);

@@ -418,7 +418,7 @@ __device__ int g_tc_selftest_err[1];
 extern "C" int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int lda, int tA, const double* B, int ldb,
                                       int tB, double* C, int ldc, double alpha, double beta, const double* colscale,
                                       int batch, long long sA, long long sB, long long sC, int slices, void* stream) {
-  if (m < 0 || n < 0 || k < 0 || batch < 1 || slices < 2 || slices > 4) return HT_ERR_ARG;
+  if (m < 0 || n < 0 || k < 0 || batch < 1 || slices < 1 || slices > 4) return HT_ERR_ARG;
   if (!A || !B || !C || lda < 1 || ldb < 1 || ldc < htg_max(1, m)) return HT_ERR_ARG;
   if (lda < (tA ? htg_max(1, k) : htg_max(1, m)) || ldb < (tB ? htg_max(1, n) : htg_max(1, k))) return HT_ERR_ARG;
   GemmDesc g;
@@ -438,8 +438,9 @@ extern "C" int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int 
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HT_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (htg_launch_gemm_tc((const GemmDesc*)dp, 1, sms, slices, s, nullptr, 1, 0, (int*)ep) != cudaSuccess)
-    return HT_ERR_CUDA;
+  const cudaError_t le = (slices == 1) ? htg_launch_gemm_f32x2((const GemmDesc*)dp, 1, 2 * sms, s, nullptr, 1, 0, 0)
+                                        : htg_launch_gemm_tc((const GemmDesc*)dp, 1, sms, slices, s, nullptr, 1, 0, (int*)ep);
+  if (le != cudaSuccess) return HT_ERR_CUDA;
   int h = 0;
   if (cudaMemcpyAsync(&h, ep, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HT_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return HT_ERR_CUDA;

@@ -604,8 +604,9 @@ def selftest_fastmath(x, stream=None):
 
 def selftest_gemm_mixed(A, B, C, m, n, k, lda, ldb, ldc, tA=0, tB=0, alpha=1.0, beta=0.0, colscale=None,
                         batch=1, sA=0, sB=0, sC=0, slices=4, stream=None):
-    """The tensor-core contraction of the mixed form on device FP64 buffers (column-major views
-    given by leading dimensions and batch strides, in elements)."""
+    """A contraction of the mixed form on device FP64 buffers (column-major views given by leading
+    dimensions and batch strides, in elements): slices 2..4 the tensor-core kernel, slices 1 the
+    split-FP32 CUDA-core kernel."""
     return int(load().ht_selftest_gemm_mixed(m, n, k, C_ptr(A), lda, tA, C_ptr(B), ldb, tB, C_ptr(C), ldc,
                                              float(alpha), float(beta), C_ptr(colscale), batch, sA, sB, sC,
                                              slices, _stream_ptr(stream)))

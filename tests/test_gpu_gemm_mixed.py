@@ -1,5 +1,6 @@
-"""The tensor-core contraction of the mixed-precision form (tcgen05, BF16 digit planes, FP32
-accumulators in tensor memory) against FP64 products formed on the host.
+"""The contraction kernels of the mixed-precision form against FP64 products formed on the host:
+the tensor-core one (tcgen05, BF16 digit planes, FP32 accumulators in tensor memory; slices 2..4)
+and the split-FP32 CUDA-core one of the small contractions (slices 1).
 
 The split writes each row of op(A) and column of op(B), scaled by its own power of two, as S
 balanced base-256 digits; integer-valued inputs that fit in 8S-1 bits are therefore represented
@@ -49,11 +50,12 @@ def _op(X, t):
     return X.T if t else X
 
 
-@pytest.mark.parametrize("slices", [2, 3, 4])
+@pytest.mark.parametrize("slices", [1, 2, 3, 4])
 @pytest.mark.parametrize("tA,tB", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_integer_inputs_are_exact(G, slices, tA, tB):
     """m = 200, n = 150 (two ragged tiles each way), k = 70 (three ragged stages of 32):
-    integers in [-100, 100] fit every split, so C must equal the integer product exactly."""
+    integers in [-100, 100] fit every split (and their sums, below 2^24, the FP32 high part of the
+    split-FP32 form), so C must equal the integer product exactly."""
     rng = np.random.default_rng(10 * slices + 2 * tA + tB)
     m, n, k = 200, 150, 70
     A = rng.integers(-100, 101, (m, k)).astype(np.float64)
@@ -126,3 +128,53 @@ def test_empty_inner_dimension_and_empty_output(G):
     rc = G.selftest_gemm_mixed(_dev(A), _dev(B), Cd, 0, 4, 1, 3, 1, 3, 0, 0, 1.0, 0.0, None, slices=4)
     assert rc == G.HT_OK
     np.testing.assert_array_equal(Cd.cpu().numpy().reshape(3, 4, order="F"), 2.0 * C0)
+
+
+def test_split_fp32_within_bound(G):
+    """The split-FP32 kernel (slices 1): values spanning 10 decades, k = 500 (32 ragged stages of
+    16).  Per element the error must stay within the compensated dot product's worst-case bound
+    (k^2 + 5k + 10) 2^-47 sum_l |a_il b_lj|, and within 2 (k/2 + 10) 2^-47 sum_l |a_il b_lj| (the
+    size rounding errors of random sign give; a plain FP32 accumulation misses it by about 2^20)."""
+    rng = np.random.default_rng(41)
+    m, n, k = 70, 45, 500
+    A = rng.standard_normal((m, k)) * np.exp(rng.uniform(-11.5, 11.5, (m, k)))
+    B = rng.standard_normal((k, n)) * np.exp(rng.uniform(-3, 3, (k, n)))
+    absAB = np.abs(A) @ np.abs(B)
+    for tA, tB in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        got = _run(G, _op(A, tA).copy(), _op(B, tB).copy(), tA, tB, 1)
+        err = np.abs(got - A @ B)
+        worst = (k * k + 5 * k + 10) * 2.0 ** -47 * absAB
+        typical = (k / 2 + 10) * 2.0 ** -47 * absAB
+        print(f"split FP32, tA={tA} tB={tB}: max error / typical bound = {(err / typical).max():.3f}")
+        assert (err <= worst).all()
+        assert (err / typical).max() <= 2.0
+
+
+def test_split_fp32_alpha_beta_colscale_and_batch(G):
+    """The split-FP32 kernel on the projection form C[b] = alpha A[b] B[b] diag(s) + beta C[b]
+    over a strided batch; rows past m and entries past the last stride untouched."""
+    import torch
+    rng = np.random.default_rng(22)
+    m, n, k, nb = 37, 21, 19, 4
+    lda, ldb, ldc = m + 3, k + 1, m + 2
+    sA, sB, sC = lda * k + 7, ldb * n + 5, ldc * n + 1
+    Ab = rng.standard_normal(sA * nb)
+    Bb = rng.standard_normal(sB * nb)
+    Cb = rng.standard_normal(sC * nb)
+    s = rng.uniform(0.5, 2.0, n) * 1e3
+    alpha, beta = -0.75, 0.5
+    Ad, Bd, Cd = (torch.from_numpy(x.copy()).cuda() for x in (Ab, Bb, Cb))
+    rc = G.selftest_gemm_mixed(Ad, Bd, Cd, m, n, k, lda, ldb, ldc, 0, 0, alpha, beta, torch.from_numpy(s).cuda(),
+                               batch=nb, sA=sA, sB=sB, sC=sC, slices=1)
+    assert rc == G.HT_OK
+    got = Cd.cpu().numpy()
+    for b in range(nb):
+        A = Ab[b * sA: b * sA + lda * k].reshape(lda, k, order="F")[:m]
+        B = Bb[b * sB: b * sB + ldb * n].reshape(ldb, n, order="F")[:k]
+        C0 = Cb[b * sC: b * sC + ldc * n].reshape(ldc, n, order="F")
+        ref = alpha * (A @ B) * s[None, :] + beta * C0[:m]
+        G_ = got[b * sC: b * sC + ldc * n].reshape(ldc, n, order="F")
+        bound = (k / 2 + 10) * 2.0 ** -47 * (np.abs(A) @ np.abs(B)) * abs(alpha) * s[None, :] + 4e-16 * np.abs(ref)
+        assert (np.abs(G_[:m] - ref) / bound).max() <= 2.0
+        np.testing.assert_array_equal(G_[m:], C0[m:])
+    np.testing.assert_array_equal(got[nb * sC:], Cb[nb * sC:])
