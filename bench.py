@@ -38,6 +38,12 @@ D, N, RMAX, TOL, CP_R, SWEEPS = 6, 64, 32, 1e-8, 24, 5
 # FP64 peak of GB300 derived from the nominal 1.25 TFLOP/s: 152 SMs x 2070 MHz x 4 FP64
 # flop/clk/SM (2 FMA/clk/SM).  An FMA-chain probe measured 1.196 TFLOP/s.
 FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
+# The split-FP32 contraction of the mixed form (gemm_f32x2_kernel) issues 10 FP32 operations per
+# FP64 multiply-add (3 FMA, 1 MUL, 6 ADD/SUB: the product, its error, two cross terms, TwoSum and
+# the low-part sum) on 128 FP32 lanes per SM: 152 x 2.07 GHz x 128 / 10 multiply-adds per second,
+# x 2 flops, in FP64-equivalent flops of the contraction.
+F32X2_PEAK_TFLOPS = 152 * 2.070e9 * 128 / 10 * 2 / 1e12
+HT_PREC_MIXED = 1   # ht_precision of the C ABI
 KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel", "qr": "qr_r_kernel",
                 "svd": "svd_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
                 "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...",
@@ -755,7 +761,7 @@ def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128,
     if profile:
         pst = min(steps, 10)
         prof = profiled_steps(ctx, torch, flush, lambda: G.ht_step(ctx, u, op, case.dt, TOL, cap), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx)
     if keep:
         return res, ctx, snap
     ctx.close()
@@ -873,7 +879,7 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
         pst = min(steps, 2)
         prof = profiled_steps(ctx, torch, flush,
                               lambda: G.ht_step(ctx, u, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx)
     if keep:
         return res, ctx, snap
     ctx.close()
@@ -1002,7 +1008,7 @@ def run_batched(G, torch, flush, count: int, steps: int, warmup: int, precision:
     if profile:
         pst = min(steps, 5)
         prof = profiled_steps(ctxs[0], torch, flush, lambda: b.step(ops, dts, tols, rmaxs, stream=stream), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctxs[0])
     b.close()
     if keep:
         return res, ctxs, snaps
@@ -1073,24 +1079,33 @@ def measured_peaks() -> dict:
         return {}
 
 
-def class_roofline(prof: dict, steps: int) -> tuple:
+def class_roofline(prof: dict, steps: int, ctx=None) -> tuple:
     """Per-class shares of one profiled stretch, and the roofline of its dominant class: the
     FP64 classes against the FP64 peak ("alu"), the tensor-core contractions against the
-    measured sustained BF16 tensor peak ("tensor", executed MMA flops)."""
+    measured sustained BF16 tensor peak ("tensor", executed MMA flops); in a mixed-form context
+    (ctx.cfg.precision) the gemm class is the split-FP32 kernel, against its FP32-pipe bound."""
+    split = ctx is not None and ctx.cfg.precision == HT_PREC_MIXED
     total = sum(v["ms"] for v in prof.values()) or 1.0
     shares = {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
-                  "share": v["ms"] / total} for k, v in prof.items() if v["launches"]}
+                  "share": v["ms"] / total,
+                  "counted_tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None}
+              for k, v in prof.items() if v["launches"]}
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    roof = roofline_of(prof, dom, steps)
+    roof = roofline_of(prof, dom, steps, split)
     out = {"dominant": roof}
     if dom != "gemm_tc" and prof.get("gemm_tc", {}).get("launches"):
         out["gemm_tc"] = roofline_of(prof, "gemm_tc", steps)
     return out, shares
 
 
-def roofline_of(prof: dict, cls: str, steps: int) -> dict:
+def roofline_of(prof: dict, cls: str, steps: int, split: bool = False) -> dict:
     v = prof[cls]
-    if cls == "gemm_tc":
+    if cls == "gemm" and split:
+        roof = {"kernel": "gemm_f32x2_kernel", "class": cls, "bound": "alu", "unit": "TFLOP/s",
+                "peak": F32X2_PEAK_TFLOPS,
+                "peak_source": "FP32 pipe (152 SMs x 2.07 GHz x 128 lanes) / 10 FP32 ops per FP64 multiply-add",
+                "flops": "FP64-equivalent flops of the contractions (2 m n k)"}
+    elif cls == "gemm_tc":
         pk = measured_peaks()
         peak = pk.get("bf16_tflops_sustained") or 1700.0
         roof = {"kernel": "gemm_tc_kernel", "class": cls, "bound": "tensor", "unit": "TFLOP/s", "peak": peak,
@@ -1243,7 +1258,7 @@ def profile_pass(W, torch, flush, steps: int):
     per launch); the kernel itself never forms y and executes the fewer flops its counter reports
     (`executed_*`)."""
     prof = profiled_steps(W.ctx, torch, flush, W.step, steps)
-    rl, shares = class_roofline(prof, steps)
+    rl, shares = class_roofline(prof, steps, W.ctx)
     roof = rl["dominant"]
     if roof["class"] == "cp_solve":
         # the form cp_als_sweep_rk2 took on this context names the kernel and its counter record

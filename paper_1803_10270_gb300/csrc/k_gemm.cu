@@ -59,24 +59,34 @@ __global__ void __launch_bounds__(NT) gemm_kernel(const GemmDesc* __restrict__ d
     double* C = g.C + (long long)b * g.sC;
     double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
     const bool has_beta = htg_dnz(g.beta);   // bit test: an FP64 compare costs ~800 cycles here
-    for (int l0 = 0; l0 < g.k; l0 += BK) {
+    // the next k-slice is read from global memory into registers while the current one is
+    // multiplied out of shared memory (its loads overlap the FP64 work of the slice)
+    constexpr int PER = (BM * BK) / NT;
+    double ra[PER], rb[PER];
+    auto gload = [&](int l0) {
 #pragma unroll
-      for (int p = 0; p < (BM * BK) / NT; ++p) {
+      for (int p = 0; p < PER; ++p) {
         const int e = tid + NT * p;
         int i, l;
         if (!g.tA) { i = e % BM; l = e / BM; } else { l = e % BK; i = e / BK; }
         const int gi = i0 + i, gl = l0 + l;
-        double v = 0.0;
-        if (gi < g.m && gl < g.k) v = g.tA ? A[gl + (long long)g.lda * gi] : A[gi + (long long)g.lda * gl];
-        As[l][i] = v;
+        ra[p] = (gi < g.m && gl < g.k) ? (g.tA ? A[gl + (long long)g.lda * gi] : A[gi + (long long)g.lda * gl]) : 0.0;
         int j, l2;
         if (!g.tB) { l2 = e % BK; j = e / BK; } else { j = e % BN; l2 = e / BN; }
         const int gj = j0 + j, gl2 = l0 + l2;
-        double u = 0.0;
-        if (gj < g.n && gl2 < g.k) u = g.tB ? B[gj + (long long)g.ldb * gl2] : B[gl2 + (long long)g.ldb * gj];
-        Bs[l2][j] = u;
+        rb[p] = (gj < g.n && gl2 < g.k) ? (g.tB ? B[gj + (long long)g.ldb * gl2] : B[gl2 + (long long)g.ldb * gj]) : 0.0;
+      }
+    };
+    gload(0);
+    for (int l0 = 0; l0 < g.k; l0 += BK) {
+#pragma unroll
+      for (int p = 0; p < PER; ++p) {
+        const int e = tid + NT * p;
+        if (!g.tA) As[e / BM][e % BM] = ra[p]; else As[e % BK][e / BK] = ra[p];
+        if (!g.tB) Bs[e % BK][e / BK] = rb[p]; else Bs[e / BN][e % BN] = rb[p];
       }
       __syncthreads();
+      if (l0 + BK < g.k) gload(l0 + BK);
       if (l0 + BK <= g.k) {
 #pragma unroll
         for (int l = 0; l < BK; ++l) {

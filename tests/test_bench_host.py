@@ -91,3 +91,24 @@ def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
     assert cb["kind"] == "oracle" and cb["value"] == 5.0 and cb["cores"] >= 1 and "sample" in cb
     assert isinstance(cb["cpu"], str) and "cores" in cb["cpu"]
     assert line["e2e"] == {"value": 5.0, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_class_roofline_labels_the_split_fp32_contraction():
+    """Per-class shares and the dominant class's roofline from a profiler read-out: in a mixed-form
+    context the gemm class is the split-FP32 kernel against its FP32-pipe bound, in an FP64
+    context the FP64 kernel against the FP64 peak."""
+    import types
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    prof = {"gemm": {"ms": 4.0, "launches": 8, "flops": 2e9}, "qr": {"ms": 1.0, "launches": 4, "flops": 1e8},
+            "gemm_tc": {"ms": 0.0, "launches": 0, "flops": 0.0}}
+    for prec, kernel, peak in ((1, "gemm_f32x2_kernel", bench.F32X2_PEAK_TFLOPS),
+                               (0, "gemm_kernel", bench.FP64_PEAK_TFLOPS)):
+        ctx = types.SimpleNamespace(cfg=types.SimpleNamespace(precision=prec))
+        roof, shares = bench.class_roofline(prof, 2, ctx)
+        dom = roof["dominant"]
+        assert dom["kernel"] == kernel and dom["peak"] == peak
+        assert abs(dom["achieved"] - 2e9 / 4e-3 / 1e12) < 1e-12
+        assert abs(shares["gemm"]["share"] - 0.8) < 1e-12 and shares["gemm"]["ms_per_step"] == 2.0
+        assert abs(shares["qr"]["counted_tflops"] - 1e8 / 1e-3 / 1e12) < 1e-12
+        assert "gemm_tc" not in shares
