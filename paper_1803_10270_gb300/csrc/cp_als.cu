@@ -587,18 +587,21 @@ __device__ inline int tri_offset(int c, int r) { return c * r - (c * (c - 1)) / 
 // LDL^T factorisation (D diagonal, L unit lower) of the SPD r x r matrix in Lm (column-major,
 // lower part) with the unit-lower forward solve of the nrhs right-hand sides in hs (vector v at
 // hs + v r) fused in.
-// Right-looking, one CTA barrier per pivot: step j applies a_ic -= (a_ij / d_j) a_cj to the
-// trailing lower triangle (pairs from tri, i >= c > j) and z_i -= (a_ij / d_j) z_j to the
-// right-hand sides.  The next pivot a_{j+1,j+1} and its reciprocal are formed by one thread of
-// the last warp, and the warps on that warp's SM partition (warp index 3 mod 4) take no other
-// work: the pivot chain (two FP64 operations, the reciprocal's seed and its correction) then
-// never waits behind other warps' FP64 instructions (anything else that runs meanwhile, even
-// loads, lengthens the steps: asynchronous copies issued by the element threads during the
-// steps measured 1.4k cycles per step against 1.05k; so does more FP64 work on the pivot thread
-// itself: a look-ahead that formed the next pivot's entries there, one FMA off the chain,
-// measured 1.5k).  Column j keeps a_ij = L_ij d_j, Lsc receives L_ij.  A pivot that is
-// not positive and finite leaves dinv = 0 there; every thread sees it after the barrier and
-// the result is false.
+// Right-looking, two CTA barriers per pivot.  Step j first forms the multipliers L_ij = a_ij / d_j
+// of column j once (into Lsc), then applies a_ic -= L_ij a_cj to the trailing lower triangle
+// (pairs from tri, i >= c > j) and z_i -= L_ij z_j to the right-hand sides, one FMA per element.
+// Meanwhile one thread of the last warp forms the next pivot a_{j+1,j+1} and its reciprocal, and
+// the warps on that warp's SM partition (warp index 3 mod 4) take no element work: the pivot
+// chain (an FMA, the reciprocal's seed and its correction) never waits behind other warps' FP64
+// instructions.  Measured per step (clock64 in CTA 0 at the bench configuration): the pivot
+// chain about 650 cycles after the multipliers' barrier, the element threads 300-700; variants
+// measured slower: the multiplier formed per element (one product more per element), the pivot
+// chain started beside the multipliers behind a named barrier, a division-free scaled
+// elimination (no reciprocal on the chain, but a product more per element) with and without the
+// trailing entries held in registers, asynchronous copies issued by the element threads during the
+// steps, and a look-ahead of the next pivot's entries on the pivot thread.  Column j keeps
+// a_ij = L_ij d_j.  A pivot that is not positive and finite leaves dinv = 0 there; every thread
+// sees it after the barrier and the result is false.
 __device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, const unsigned short* tri, int r,
                              int nrhs) {
   const int tid = threadIdx.x, wid = tid >> 5;
@@ -615,6 +618,8 @@ __device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, 
     const double dj = dinv[j];
     if (!htg_dnz(dj)) return false;   // uniform: written before the last barrier
     const int m = r - 1 - j;
+    for (int i = j + 1 + tid; i < r; i += NT) Lsc[i + r * j] = Lm[i + r * j] * dj;
+    __syncthreads();
     const int s0 = tri_offset(j + 1, r) + 1;   // the pairs after (j+1, j+1)
     const int ntri = T - s0;
     const int nall = ntri + nrhs * m;
@@ -623,20 +628,15 @@ __device__ bool ldlt_forward(double* Lm, double* Lsc, double* hs, double* dinv, 
         if (e < ntri) {
           const unsigned int pr = tri[s0 + e];
           const int i = pr & 0xff, c = pr >> 8;
-          const double t = Lm[i + r * j] * dj;   // L_ij
-          Lm[i + r * c] = fma(-t, Lm[c + r * j], Lm[i + r * c]);
-          if (e < m - 1) Lsc[i + r * j] = t;    // the pairs of column j+1 come first
+          Lm[i + r * c] = fma(-Lsc[i + r * j], Lm[c + r * j], Lm[i + r * c]);
         } else {
           const int f = e - ntri, p = f / m, i = j + 1 + f % m;
-          hs[p * r + i] = fma(-(Lm[i + r * j] * dj), hs[p * r + j], hs[p * r + i]);
+          hs[p * r + i] = fma(-Lsc[i + r * j], hs[p * r + j], hs[p * r + i]);
         }
       }
     } else if (tid == PIV && m > 0) {
       const int i = j + 1;
-      const double a = Lm[i + r * j];
-      const double t = a * dj;
-      Lsc[i + r * j] = t;
-      const double v = fma(-t, a, Lm[i + r * i]);
+      const double v = fma(-Lsc[i + r * j], Lm[i + r * j], Lm[i + r * i]);
       Lm[i + r * i] = v;
       dinv[i] = htg_dpos_finite(v) ? htg_rcp_fast(v) : 0.0;
     }
