@@ -422,8 +422,10 @@ int ht_selftest_fastmath(const double* x_dev, double* out_dev, int n, void* stre
  * wait gave up), HT_ERR_ARG or HT_ERR_CUDA. */
 /* Tuning probe (used by the package's autotuner; the paper has no counterpart): mean CUDA-event
  * time in ms of `reps` launches of one synthetic contraction (op(A) m x k, op(B) k x n, `batch`
- * entries) through the FP64 CUDA-core kernel (route 0, ctas_per_sm CTAs per SM, 1..32) or the
- * tensor-core split kernel (route 1, `slices` digit planes, 2..4), written to *ms_out.
+ * entries) through the FP64 CUDA-core kernel (route 0, ctas_per_sm CTAs per SM, 1..32), the
+ * tensor-core split kernel (route 1, `slices` digit planes, 2..4) or the split-FP32 CUDA-core
+ * kernel of the mixed form's small contractions (route 2, ctas_per_sm as route 0), written to
+ * *ms_out.
  * Synchronising; allocates and frees its own device buffers.  Errors: HT_ERR_ARG, HT_ERR_NOMEM,
  * HT_ERR_CUDA, HT_ERR_TIMEOUT. */
 int ht_tune_time_gemm(int m, int n, int k, int batch, int route, int slices, int ctas_per_sm, int reps,

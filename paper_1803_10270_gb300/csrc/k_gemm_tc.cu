@@ -453,9 +453,9 @@ extern "C" int ht_selftest_gemm_mixed(int m, int n, int k, const double* A, int 
 // tensor-core kernel (route 1, `slices` digit planes).  Allocates and frees its own buffers.
 extern "C" int ht_tune_time_gemm(int m, int n, int k, int batch, int route, int slices, int ctas_per_sm, int reps,
                                  double* ms_out) {
-  if (m < 1 || n < 1 || k < 1 || batch < 1 || reps < 1 || !ms_out || (route != 0 && route != 1)) return HT_ERR_ARG;
+  if (m < 1 || n < 1 || k < 1 || batch < 1 || reps < 1 || !ms_out || route < 0 || route > 2) return HT_ERR_ARG;
   if (route == 1 && (slices < 2 || slices > 4)) return HT_ERR_ARG;
-  if (route == 0 && (ctas_per_sm < 1 || ctas_per_sm > 32)) return HT_ERR_ARG;
+  if (route != 1 && (ctas_per_sm < 1 || ctas_per_sm > 32)) return HT_ERR_ARG;
   const size_t na = (size_t)m * k * batch, nb = (size_t)k * n * batch, nc = (size_t)m * n * batch;
   double *A = nullptr, *B = nullptr, *Cm = nullptr;
   GemmDesc* dd = nullptr;
@@ -482,8 +482,9 @@ extern "C" int ht_tune_time_gemm(int m, int n, int k, int batch, int route, int 
     if (rc == HT_OK && cudaMemcpy(dd, &g, sizeof(g), cudaMemcpyHostToDevice) != cudaSuccess) rc = HT_ERR_CUDA;
     if (rc == HT_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = HT_ERR_CUDA;
     auto launch = [&]() -> cudaError_t {
-      return route == 1 ? htg_launch_gemm_tc(dd, 1, sms, slices, 0, nullptr, 1, 0, err, 0)
-                        : htg_launch_gemm(dd, 1, sms * ctas_per_sm, 0, nullptr, 1, 0, 0);
+      if (route == 1) return htg_launch_gemm_tc(dd, 1, sms, slices, 0, nullptr, 1, 0, err, 0);
+      if (route == 2) return htg_launch_gemm_f32x2(dd, 1, sms * ctas_per_sm, 0, nullptr, 1, 0, 0);
+      return htg_launch_gemm(dd, 1, sms * ctas_per_sm, 0, nullptr, 1, 0, 0);
     };
     if (rc == HT_OK) {
       for (int w = 0; w < 2 && rc == HT_OK; ++w)

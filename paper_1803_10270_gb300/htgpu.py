@@ -614,8 +614,8 @@ def selftest_gemm_mixed(A, B, C, m, n, k, lda, ldb, ldc, tA=0, tB=0, alpha=1.0, 
 
 def tune_time_gemm(m: int, n: int, k: int, batch: int = 1, route: int = 0, slices: int = 4, ctas_per_sm: int = 4,
                    reps: int = 20) -> float:
-    """Mean time (ms) of one synthetic contraction through the FP64 (route 0) or the tensor-core
-    (route 1) kernel, for the autotuner."""
+    """Mean time (ms) of one synthetic contraction through the FP64 (route 0), the tensor-core
+    (route 1) or the split-FP32 (route 2) kernel, for the autotuner."""
     ms = C.c_double(0.0)
     _check(load().ht_tune_time_gemm(m, n, k, batch, route, slices, ctas_per_sm, reps, C.byref(ms)),
            "ht_tune_time_gemm")

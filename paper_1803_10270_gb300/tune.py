@@ -3,10 +3,10 @@
 It measures, through the library's own entry points:
 
 * tc_min_work: the work (multiply-adds m n k batch) from which a contraction of the mixed form
-  runs faster on the tensor-core split kernel than on the FP64 CUDA-core kernel.  Square and
-  batched shapes of the truncation's contractions are timed through both kernels
-  (ht_tune_time_gemm); the threshold is the smallest measured work from which the tensor cores
-  win at that work and every larger one.
+  runs faster on the tensor-core split kernel than on the split-FP32 CUDA-core kernel that takes
+  the mixed form's smaller contractions.  Square and batched shapes of the truncation's
+  contractions are timed through both kernels (ht_tune_time_gemm); the threshold is the smallest
+  measured work from which the tensor cores win at that work and every larger one.
 * gemm_ctas_per_sm: CTAs per SM of the FP64 contraction launches, chosen by the summed time of
   the same shapes, per capacity bucket of the context (the largest truncation input rank Kc).
 * svd_cluster_min_cols: the node-factor width from which the thread-block-cluster SVD beats the
@@ -99,11 +99,12 @@ def tune(device: int = 0, slices: int = 4, reps: int = 10, write: bool = True, v
         best = min(tot, key=tot.get)
         by_kc[str(kc)] = best
         timings[f"fp64_ctas_kc{kc}"] = {str(c): tot[c] for c in ctas_opts}
-    # ---- tensor-core crossover (FP64 side at its tuned CTA count of the largest bucket)
+    # ---- tensor-core crossover against the split-FP32 kernel (at the CUDA-core launches' tuned
+    # CTA count of the largest bucket)
     c_big = by_kc[str(KC_BUCKETS[-1])]
     pts = []
     for (m, n, k, b) in _shapes(384):
-        t64 = _time(G, m, n, k, b, 0, slices, c_big, reps)
+        t64 = _time(G, m, n, k, b, 2, slices, c_big, reps)
         ttc = _time(G, m, n, k, b, 1, slices, 4, reps)
         pts.append((m * n * k * b, t64, ttc, (m, n, k, b)))
     pts.sort()
@@ -113,7 +114,7 @@ def tune(device: int = 0, slices: int = 4, reps: int = 10, write: bool = True, v
             thr = w
             break
     tc_min = thr if thr is not None else (pts[-1][0] * 2 if pts else 1 << 40)
-    timings["gemm_crossover"] = [{"work": w, "shape": list(sh), "fp64_ms": a, "tc_ms": c} for (w, a, c, sh) in pts]
+    timings["gemm_crossover"] = [{"work": w, "shape": list(sh), "f32x2_ms": a, "tc_ms": c} for (w, a, c, sh) in pts]
     # ---- cluster SVD switch width
     svd_min, svd_t = _tune_svd_switch(G, torch, device)
     timings["svd_switch"] = svd_t

@@ -25,7 +25,7 @@ def G():
 
 
 def test_tune_time_gemm_probe(G):
-    for route in (0, 1):
+    for route in (0, 1, 2):   # FP64, tensor-core split, split-FP32
         t = G.tune_time_gemm(64, 64, 64, 2, route=route, reps=3)
         assert 0.0 < t < 1000.0
 
