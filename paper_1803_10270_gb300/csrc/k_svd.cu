@@ -87,7 +87,11 @@ __device__ void cta_gemm(double* dst, const double* A, int lda, const double* B,
 // rotates both columns where they live (distributed shared memory) and writes their new squared
 // norms; a cluster barrier ends the round.  The rotations are the one-sided (Hestenes) ones of
 // the FP64 phase above, applied to N directly: no FP32 phase and no Gram matrix, so each sweep is
-// one pass over the column pairs, and its FP64 work is spread over cl SMs.
+// one pass over the column pairs, and its FP64 work is spread over cl SMs.  A rotated pair's V
+// columns (rows q .. q + p - 1, which no dot product reads) are rotated one round late, by the
+// same warp at the start of the next round: the round barrier that follows orders them before
+// any later rotation of those columns, and a round's critical path is one pair's N work plus at
+// most one earlier V update instead of both halves of a rotation.
 constexpr int SVDC_MIN_P = 128;
 constexpr int CNT = 512;                 // threads per CTA
 constexpr int CNW = CNT / 32;            // warps per CTA = pairs one CTA rotates at a time
@@ -124,10 +128,36 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
   const int p2 = p + (p & 1), npairs = p2 / 2;
   const float TOL64F = htg_d2f(EPS * (double)htg_max(htg_max(p, q), 8));
   __shared__ int rot_sh;
+  // this warp's rotation of the previous round whose V columns are still to rotate
+  double* pva = nullptr;
+  double* pvb = nullptr;
+  double pc = 1.0, ps = 0.0;
+  auto rotate_v = [&]() {
+    if (!pva) return;
+    for (int i0 = 0; i0 < p; i0 += 160) {
+      double x[5], y[5];
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        const int i = i0 + lane + 32 * u;
+        x[u] = (i < p) ? pva[i] : 0.0;
+        y[u] = (i < p) ? pvb[i] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 5; ++u) {
+        const int i = i0 + lane + 32 * u;
+        if (i < p) {
+          pva[i] = pc * x[u] - ps * y[u];
+          pvb[i] = ps * x[u] + pc * y[u];
+        }
+      }
+    }
+    pva = pvb = nullptr;
+  };
   for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
     if (tid == 0) rot_sh = 0;
     __syncthreads();
     for (int round = 0; round < p2 - 1; ++round) {
+      rotate_v();
       for (int pi = me + cl * wid; pi < npairs; pi += cl * CNW) {
         int a, b;
         rr_pair(pi, round, p, p2, &a, &b);
@@ -187,26 +217,14 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
             cb[i] = y;
           }
         }
-        // V columns, five entries per lane loaded ahead of their stores
-        double* va = ca + q;
-        double* vb = cb + q;
-        for (int i0 = 0; i0 < p; i0 += 160) {
-          double x[5], y[5];
-#pragma unroll
-          for (int u = 0; u < 5; ++u) {
-            const int i = i0 + lane + 32 * u;
-            x[u] = (i < p) ? va[i] : 0.0;
-            y[u] = (i < p) ? vb[i] : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < 5; ++u) {
-            const int i = i0 + lane + 32 * u;
-            if (i < p) {
-              va[i] = c * x[u] - sn * y[u];
-              vb[i] = sn * x[u] + c * y[u];
-            }
-          }
-        }
+        // V columns (five entries per lane loaded ahead of their stores) at the next round's start;
+        // a warp with a second pair in this round (8-CTA clusters) first rotates the first pair's,
+        // whose columns no other warp touches in this round
+        rotate_v();
+        pva = ca + q;
+        pvb = cb + q;
+        pc = c;
+        ps = sn;
         sa = warp_sum(sa);
         sb = warp_sum(sb);
         if (lane == 0) {
@@ -224,6 +242,8 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
     cluster.sync();   // every flag read before the next sweep rewrites it
     if (!any) break;
   }
+  rotate_v();
+  cluster.sync();   // every V column final
 }
 
 __global__ void __launch_bounds__(CNT, 1) svd_cluster_kernel(const SvdDesc* __restrict__ descs, long long cap_doubles,
