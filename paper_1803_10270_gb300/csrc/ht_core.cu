@@ -16,6 +16,7 @@
 // node, i.e. the HSVD projections, expressed through R_t, E_t and the small SVDs only.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <cmath>
 #include <vector>
@@ -170,6 +171,11 @@ struct ht_ctx {
   int slices = 0;              // HT_PREC_MIXED: BF16 digit planes per operand (0: FP64 contractions)
   long long tc_min = 0;        // HT_PREC_MIXED: contractions of at least this many multiply-adds on the tensor cores
   bool tc_reach = false;       // whether a contraction of this context can reach tc_min
+  // per contraction list of a single truncation: whether one of its contractions can reach tc_min
+  // (bounds from the capacities; a list without a tensor-core launch runs wholly on the CUDA cores)
+  enum { TL_ABS1, TL_ABS2, TL_T1, TL_EPRE, TL_LEVEL };   // per depth
+  bool tc_lvl[MAXLEV][TL_LEVEL] = {};
+  bool tc_rootE = false, tc_Pall = false, tc_XY = false, tc_proj[3] = {false, false, false};
   int svd_min_cols = 128;      // node factors at least this wide take the cluster SVD
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
@@ -947,6 +953,60 @@ extern "C" size_t ht_workspace_bytes(const ht_config* cfg) {
   return W.total;
 }
 
+// Upper bounds of the work (multiply-adds m n k batch) of every contraction list a truncation of
+// this context issues, from the planner's shapes with every input rank at the capacity Kc, the
+// R-factor rows Rp bounded by the grid and by the children's Rp, the complement columns mE by the
+// sibling's Rp, and the new ranks by cap; a list whose bound stays below tc_min never reaches
+// the tensor cores, so its tensor-core launch (which would find no work) is left out.
+static void tc_list_bounds(ht_ctx* c, const ht_config* cfg) {
+  const TreeInfo& T = c->tree;
+  const double Kc = c->Kc, cap = c->cap, tcm = (double)c->tc_min;
+  double Rp[NN] = {0}, mE[NN] = {0}, kn[NN] = {0};
+  for (int dep = T.max_depth; dep >= 1; --dep)
+    for (int t = 1; t < T.nn; ++t) {
+      if (T.depth[t] != dep) continue;
+      Rp[t] = (T.c1[t] < 0) ? std::min(Kc, (double)cfg->n[T.lo[t]]) : std::min(Kc, Rp[T.c1[t]] * Rp[T.c2[t]]);
+    }
+  const int ra = T.c1[0], rb = T.c2[0];
+  mE[ra] = Rp[rb];
+  mE[rb] = Rp[ra];
+  for (int dep = 1; dep < T.max_depth; ++dep)
+    for (int t = 1; t < T.nn; ++t) {
+      if (T.depth[t] != dep || T.c1[t] < 0) continue;
+      mE[T.c1[t]] = std::min(Kc, Rp[T.c2[t]] * mE[t]);
+      mE[T.c2[t]] = std::min(Kc, Rp[T.c1[t]] * mE[t]);
+    }
+  for (int t = 1; t < T.nn; ++t) kn[t] = std::min(cap, Rp[t]);
+  double w_rootE = std::max(Kc * Rp[rb] * Kc, Kc * Rp[ra] * Kc), w_Pall = 0, w_XY = 0, w_p1 = 0, w_p2 = 0, w_p3 = 0;
+  for (int dep = 0; dep < MAXLEV; ++dep)
+    for (int j = 0; j < ht_ctx::TL_LEVEL; ++j) c->tc_lvl[dep][j] = false;
+  w_p1 = kn[ra] * Kc * Kc;            // the root's projection
+  w_p2 = kn[ra] * kn[rb] * Kc;
+  for (int t = 1; t < T.nn; ++t) {
+    w_Pall = std::max(w_Pall, Rp[t] * mE[t] * Kc);
+    w_XY = std::max(w_XY, std::max(kn[t] * Kc * Rp[t], Kc * kn[t] * mE[t]));
+    if (T.c1[t] < 0) {
+      w_p1 = std::max(w_p1, (double)cfg->n[T.lo[t]] * kn[t] * Kc);
+      continue;
+    }
+    const int a = T.c1[t], b = T.c2[t], dep = T.depth[t];
+    w_p1 = std::max(w_p1, Kc * Kc * kn[t] * Kc);
+    w_p2 = std::max(w_p2, kn[a] * Kc * kn[t] * Kc);
+    w_p3 = std::max(w_p3, kn[a] * kn[b] * Kc * kn[t]);
+    bool* f = c->tc_lvl[dep];
+    f[ht_ctx::TL_ABS1] = f[ht_ctx::TL_ABS1] || Rp[a] * Kc * Kc * Kc >= tcm;
+    f[ht_ctx::TL_ABS2] = f[ht_ctx::TL_ABS2] || Rp[a] * Rp[b] * Kc * Kc >= tcm;
+    f[ht_ctx::TL_T1] = f[ht_ctx::TL_T1] || Kc * Kc * mE[t] * Kc >= tcm;
+    f[ht_ctx::TL_EPRE] = f[ht_ctx::TL_EPRE] || std::max(Rp[a], Rp[b]) * Kc * Kc * mE[t] >= tcm;
+  }
+  c->tc_rootE = w_rootE >= tcm;
+  c->tc_Pall = w_Pall >= tcm;
+  c->tc_XY = w_XY >= tcm;
+  c->tc_proj[0] = w_p1 >= tcm;
+  c->tc_proj[1] = w_p2 >= tcm;
+  c->tc_proj[2] = w_p3 >= tcm;
+}
+
 extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
   if (!out) return HT_ERR_ARG;
   *out = nullptr;
@@ -1050,6 +1110,7 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     const double wmax = kc * kc * kc * kc > (double)nmax * kc * kc ? kc * kc * kc * kc : (double)nmax * kc * kc;
     c->tc_min = (cfg->tc_min_work == -1) ? 0 : (cfg->tc_min_work ? cfg->tc_min_work : HTG_TC_MIN_WORK_DEFAULT);
     c->tc_reach = (double)c->tc_min <= wmax;
+    tc_list_bounds(c, cfg);
   }
   *out = c;
   return HT_OK;
@@ -1146,18 +1207,21 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   // split-FP32 form on the CUDA cores (the same tiles, FP64-like accuracy on the FP32 pipe)
   const bool tc_on = c->slices && c->tc_reach;
   const long long tcm = tc_on ? htg_max_ll(1, c->tc_min) : 0;
-  auto gemm64 = [&](const GemmDesc* d, int nd) -> cudaError_t {
-    if (tc_on && c->tc_min == 0) return cudaSuccess;
-    return c->slices ? htg_launch_gemm_f32x2(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm)
-                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, tcm);
+  auto gemm64 = [&](const GemmDesc* d, int nd, bool tc_here) -> cudaError_t {
+    const long long cut = tc_here ? tcm : 0;   // 0: every descriptor on the CUDA cores
+    return c->slices ? htg_launch_gemm_f32x2(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, cut)
+                     : htg_launch_gemm(d, nd, g, s, htg_prof_flops(c, KC_GEMM), count, st, cut);
   };
   auto gemmtc = [&](const GemmDesc* d, int nd) -> cudaError_t {
     return htg_launch_gemm_tc(d, nd, c->sms, c->slices, s, htg_prof_flops(c, KC_GEMMTC), count, st, c->err, tcm);
   };
-#define HTG_GEMM(DESCS, ND)                                                    \
-  do {                                                                         \
-    if (!(tc_on && c->tc_min == 0)) HTG_LAUNCH(c, KC_GEMM, s, gemm64(DESCS, ND)); \
-    if (tc_on) HTG_LAUNCH(c, KC_GEMMTC, s, gemmtc(DESCS, ND));                  \
+  // FLAG: whether the list can reach the tensor cores (single truncations; a batch launches both
+  // kernels for every list); without them the CUDA-core kernel takes every descriptor
+#define HTG_GEMM(DESCS, ND, FLAG)                                                            \
+  do {                                                                                       \
+    const bool tc_here = tc_on && (count > 1 || (FLAG));                                     \
+    if (!(tc_here && c->tc_min == 0)) HTG_LAUNCH(c, KC_GEMM, s, gemm64(DESCS, ND, tc_here)); \
+    if (tc_here) HTG_LAUNCH(c, KC_GEMMTC, s, gemmtc(DESCS, ND));                             \
   } while (0)
   HTG_LAUNCH(c, KC_PLAN, s, pre());
   const QrCoopWs* coop = (c->has_coop && count == 1) ? &c->qr_coop : nullptr;
@@ -1166,35 +1230,35 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   c->launches += coop_extra;
   for (int dep = T.max_depth - 1; dep >= 1; --dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_GEMM(P->g_abs1[dep], L.n_int[dep]);
-    HTG_GEMM(P->g_abs2[dep], L.n_int[dep]);
+    HTG_GEMM(P->g_abs1[dep], L.n_int[dep], c->tc_lvl[dep][ht_ctx::TL_ABS1]);
+    HTG_GEMM(P->g_abs2[dep], L.n_int[dep], c->tc_lvl[dep][ht_ctx::TL_ABS2]);
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_orth[dep], L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_GEMM(P->g_rootE, 2);
+  HTG_GEMM(P->g_rootE, 2, c->tc_rootE);
   // top-down complement factors: E of a child needs only E, B and R of its parent, never the
   // parent's SVD, so every node SVD runs afterwards in a single launch
   for (int dep = 1; dep < T.max_depth; ++dep) {
     if (L.n_int[dep] == 0) continue;
-    HTG_GEMM(P->g_T1[dep], L.n_int[dep]);
-    HTG_GEMM(P->g_Epre[dep], 2 * L.n_int[dep]);
+    HTG_GEMM(P->g_T1[dep], L.n_int[dep], c->tc_lvl[dep][ht_ctx::TL_T1]);
+    HTG_GEMM(P->g_Epre[dep], 2 * L.n_int[dep], c->tc_lvl[dep][ht_ctx::TL_EPRE]);
     HTG_LAUNCH(c, KC_QR, s, htg_launch_qr(P->qr_comp[dep], 2 * L.n_int[dep], s, htg_prof_flops(c, KC_QR), count, st, coop));
     c->launches += coop_extra;
   }
-  HTG_GEMM(P->g_Pall, T.nn - 1);
+  HTG_GEMM(P->g_Pall, T.nn - 1, c->tc_Pall);
   const SvdClusterCfg* clu = (count == 1) ? &c->svd_clu : nullptr;
   HTG_LAUNCH(c, KC_SVD, s,
              htg_launch_svd(P->svd_all, T.nn - 1, svd_smem, Kc, Kc, s, htg_prof_flops(c, KC_SVD), count, st, clu));
   c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
-  HTG_GEMM(P->g_XY, 2 * (T.nn - 1));
+  HTG_GEMM(P->g_XY, 2 * (T.nn - 1), c->tc_XY);
   HTG_LAUNCH(c, KC_GEMM, s,
              (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
               cudaGetLastError()));
-  HTG_GEMM(P->g_proj1, L.n_proj1);
-  HTG_GEMM(P->g_proj2, L.n_proj2);
+  HTG_GEMM(P->g_proj1, L.n_proj1, c->tc_proj[0]);
+  HTG_GEMM(P->g_proj2, L.n_proj2, c->tc_proj[1]);
   if (L.n_proj3 > 0)
-    HTG_GEMM(P->g_proj3, L.n_proj3);
+    HTG_GEMM(P->g_proj3, L.n_proj3, c->tc_proj[2]);
   c->last_stream = s;
   return HT_OK;
 }
