@@ -74,6 +74,17 @@ def _shapes(kc_max: int):
     return out
 
 
+def crossover(pts) -> int:
+    """The tensor-core threshold from timed points (work, CUDA-core ms, tensor-core ms, shape): the
+    smallest measured work from which the tensor cores are faster at that work and every larger
+    one; twice the largest measured work when they never are (1 << 40 without points)."""
+    pts = sorted(pts, key=lambda p: p[0])
+    for i, p in enumerate(pts):
+        if all(q[2] < q[1] for q in pts[i:]):
+            return int(p[0])
+    return int(pts[-1][0] * 2) if pts else 1 << 40
+
+
 def _time(G, m, n, k, b, route, slices, ctas, reps):
     """Mean ms of one contraction: one launch first, then up to `reps` more within about 20 ms."""
     t1 = G.tune_time_gemm(m, n, k, b, route, slices, ctas, 1)
@@ -107,13 +118,8 @@ def tune(device: int = 0, slices: int = 4, reps: int = 10, write: bool = True, v
         t64 = _time(G, m, n, k, b, 2, slices, c_big, reps)
         ttc = _time(G, m, n, k, b, 1, slices, 4, reps)
         pts.append((m * n * k * b, t64, ttc, (m, n, k, b)))
-    pts.sort()
-    thr = None
-    for i, (w, t64, ttc, _) in enumerate(pts):
-        if all(p[2] < p[1] for p in pts[i:]):
-            thr = w
-            break
-    tc_min = thr if thr is not None else (pts[-1][0] * 2 if pts else 1 << 40)
+    pts.sort(key=lambda p: p[0])
+    tc_min = crossover(pts)
     timings["gemm_crossover"] = [{"work": w, "shape": list(sh), "f32x2_ms": a, "tc_ms": c} for (w, a, c, sh) in pts]
     # ---- cluster SVD switch width
     svd_min, svd_t = _tune_svd_switch(G, torch, device)
