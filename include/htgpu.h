@@ -151,9 +151,11 @@ typedef struct ht_config {
   /* Tuning (0 = the library default; the package's autotuner measures them per GPU): */
   long long tc_min_work;   /* HT_PREC_MIXED: contractions of at least this many multiply-adds
                               (m n k batch, decided on the device per contraction) run on the tensor
-                              cores, smaller ones on the FP64 CUDA cores; -1: all on the tensor cores */
-  int gemm_ctas_per_sm;    /* CTAs per SM of the FP64 contraction launches, 1..32 (default 16, or 8
-                              for truncation inputs below rank 96) */
+                              cores, smaller ones in the split-FP32 form on the CUDA cores; a list of
+                              contractions that cannot reach it at the context's capacities makes no
+                              tensor-core launch; -1: all on the tensor cores */
+  int gemm_ctas_per_sm;    /* CTAs per SM of the CUDA-core contraction launches (FP64 or split-FP32),
+                              1..32 (default 16, or 8 for truncation inputs below rank 96) */
   int svd_cluster_min_cols;/* node factors at least this wide use the thread-block-cluster SVD,
                               32..480 (default 128) */
   int cp_form;             /* cp_als_sweep_rk2 (Gauss-Seidel): 0 = one thread-block cluster of up to
