@@ -178,3 +178,27 @@ def test_split_fp32_alpha_beta_colscale_and_batch(G):
         assert (np.abs(G_[:m] - ref) / bound).max() <= 2.0
         np.testing.assert_array_equal(G_[m:], C0[m:])
     np.testing.assert_array_equal(got[nb * sC:], Cb[nb * sC:])
+
+
+def test_split_fp32_exponent_ranges(G):
+    """The split's documented ranges: operands from 2^-74 up keep 48 significant bits (the
+    (k^2 + 5k + 10) 2^-47 bound), operands between 2^-120 and 2^-75 keep only their FP32 high part
+    (2^-23 relative per product), zeros stay exact; one matrix mixes all three."""
+    rng = np.random.default_rng(77)
+    m, n, k = 33, 29, 40
+    mag = rng.choice([0.0, 1.0, 1.0], size=(m, k))
+    expo = rng.uniform(-74.0, 100.0, (m, k))
+    tiny = rng.random((m, k)) < 0.2
+    expo[tiny] = rng.uniform(-120.0, -76.0, tiny.sum())
+    A = mag * rng.choice([-1.0, 1.0], (m, k)) * np.exp2(expo) * rng.uniform(1.0, 2.0, (m, k))
+    B = rng.standard_normal((k, n))
+    got = _run(G, A, B, 0, 0, 1)
+    ref = A @ B
+    big = np.where(tiny, 0.0, np.abs(A))
+    small = np.where(tiny, np.abs(A), 0.0)
+    bound = ((k * k + 5 * k + 10) * 2.0 ** -47 * (big @ np.abs(B)) + 2.0 ** -23 * (small @ np.abs(B))
+             + 2.0 ** -52 * np.abs(ref))
+    assert (np.abs(got - ref) <= bound).all()
+    zero_rows = (mag == 0.0).all(axis=1)
+    if zero_rows.any():
+        assert (got[zero_rows] == 0.0).all()
