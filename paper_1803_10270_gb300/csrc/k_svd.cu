@@ -126,7 +126,11 @@ __device__ void svdc_sweeps(cg::cluster_group& cluster, double* col, double* nrm
   const int me = (int)cluster.block_rank();
   const int ld = q + p;
   const int p2 = p + (p & 1), npairs = p2 / 2;
-  const float TOL64F = htg_d2f(EPS * (double)htg_max(htg_max(p, q), 8));
+  // the pair test |a.b| > tol |a| |b|: tol = eps max(p, q) when the singular values are reported,
+  // at least 1e-11 when only the truncation's ranks are wanted (skip_abs > 0): a pair left
+  // unrotated at that level moves T(u) by at most about 1e-11 of its smaller column
+  const float TOL64F = htg_d2f(skip_abs > 0.0 ? fmax(EPS * (double)htg_max(htg_max(p, q), 8), 1e-11)
+                                              : EPS * (double)htg_max(htg_max(p, q), 8));
   __shared__ int rot_sh;
   // this warp's rotation of the previous round whose V columns are still to rotate
   double* pva = nullptr;
