@@ -492,7 +492,8 @@ __global__ void __launch_bounds__(NT) svd_kernel(const SvdDesc* __restrict__ des
   // ---------------- phase 3: FP64 two-sided Jacobi on G (rotations also applied to V)
   bool okr;
   const float rnd2 = (skip_abs > 0.0) ? htg_d2f_shift(4096.0 * EPS * EPS * red2[0], sh2, &okr) : 0.f;
-  const double TOL = EPS * (double)htg_max(mr, 8);
+  // at least 1e-11 when only the truncation's ranks are wanted (as in the cluster form)
+  const double TOL = (skip_abs > 0.0) ? fmax(EPS * (double)htg_max(mr, 8), 1e-11) : EPS * (double)htg_max(mr, 8);
   const float TOL64F = htg_d2f(TOL);
   if (tid == 0) ract = 0;
   __syncthreads();
