@@ -44,8 +44,8 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # x 2 flops, in FP64-equivalent flops of the contraction.
 F32X2_PEAK_TFLOPS = 152 * 2.070e9 * 128 / 10 * 2 / 1e12
 HT_PREC_MIXED = 1   # ht_precision of the C ABI
-KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel", "qr": "qr_r_kernel",
-                "svd": "svd_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
+KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel",
+                "qr": "qr_r_kernel/qr_coop_kernel", "svd": "svd_kernel/svd_cluster_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
                 "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...",
                 "cp_solve": "cp_als_rk2_cluster/cp_als_rk2_persistent"}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--record-workload", default="", help="workload of the capture (--record-counters)")
     p.add_argument("--record-command", default="", help="the ncu command of the capture (--record-counters)")
     p.add_argument("--record-sources", default="", help="comma-separated source files of the kernel")
+    p.add_argument("--record-line", default="", help="the bench line whose workload the capture ran "
+                                                     "(adv6d, wide, kinetic, batched, gemm_tc, ...)")
     return p.parse_args()
 
 
@@ -601,7 +603,7 @@ def run_mixed_lines(G, torch, flush, args) -> dict:
     difference of the final states."""
     warm = max(args.warmup, 3)
     out = {"adv6d_ht": mixed_vs_fp64(G, torch, flush, run_d12, steps=args.steps, warmup=warm, d=D, n=N, cap=RMAX,
-                                     n_terms=2, seed_offset=1, workload=ADV_HT_WORKLOAD),
+                                     n_terms=2, seed_offset=1, workload=ADV_HT_WORKLOAD, line="adv6d"),
            "d12": mixed_vs_fp64(G, torch, flush, run_d12, steps=100, warmup=warm),
            "kinetic": mixed_vs_fp64(G, torch, flush, run_kinetic, steps=5, warmup=45)}
     if args.batched > 0:
@@ -715,7 +717,8 @@ TT_WORKLOAD = ("6-D advection n=64 HT route in tensor-train form (the linear dim
 
 def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128, cap: int = 64,
             n_terms: int = 3, seed_offset: int = 4, tree: int = 0, workload: str = None, precision: int = 0,
-            slices: int = 0, keep: bool = False, profile: bool = True, tuning: dict | None = None):
+            slices: int = 0, keep: bool = False, profile: bool = True, tuning: dict | None = None,
+            line: str = "d12"):
     """HT steps/s of the RK2 step on the 12-D advection workload (n = 128 per dimension, r_max
     64), or another advection workload and tree: the timed steps graph-captured, L2 flushed
     between them; then a profiled stretch of the same length for the per-class roofline.  keep:
@@ -761,7 +764,7 @@ def run_d12(G, torch, flush, steps: int, warmup: int, d: int = 12, n: int = 128,
     if profile:
         pst = min(steps, 10)
         prof = profiled_steps(ctx, torch, flush, lambda: G.ht_step(ctx, u, op, case.dt, TOL, cap), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx, line)
     if keep:
         return res, ctx, snap
     ctx.close()
@@ -879,7 +882,7 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
         pst = min(steps, 2)
         prof = profiled_steps(ctx, torch, flush,
                               lambda: G.ht_step(ctx, u, kop.op, kc.dt, 1e-6, 64, scheme=G.HT_SCHEME_HEUN2), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx)
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctx, "kinetic")
     if keep:
         return res, ctx, snap
     ctx.close()
@@ -889,7 +892,7 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
 def run_tt(G, torch, flush, steps: int, warmup: int) -> dict:
     """The configuration-2 HT route on the linear (tensor-train) tree."""
     return run_d12(G, torch, flush, steps, warmup, d=D, n=N, cap=RMAX, n_terms=2, seed_offset=1, tree=1,
-                   workload=TT_WORKLOAD)
+                   workload=TT_WORKLOAD, line="tt")
 
 
 def run_varcoef(G, torch, flush, steps: int, warmup: int) -> dict:
@@ -1008,7 +1011,7 @@ def run_batched(G, torch, flush, count: int, steps: int, warmup: int, precision:
     if profile:
         pst = min(steps, 5)
         prof = profiled_steps(ctxs[0], torch, flush, lambda: b.step(ops, dts, tols, rmaxs, stream=stream), pst)
-        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctxs[0])
+        res["roofline"], res["kernel_shares"] = class_roofline(prof, pst, ctxs[0], "batched")
     b.close()
     if keep:
         return res, ctxs, snaps
@@ -1079,11 +1082,13 @@ def measured_peaks() -> dict:
         return {}
 
 
-def class_roofline(prof: dict, steps: int, ctx=None) -> tuple:
+def class_roofline(prof: dict, steps: int, ctx=None, line: str | None = None) -> tuple:
     """Per-class shares of one profiled stretch, and the roofline of its dominant class: the
     FP64 classes against the FP64 peak ("alu"), the tensor-core contractions against the
     measured sustained BF16 tensor peak ("tensor", executed MMA flops); in a mixed-form context
-    (ctx.cfg.precision) the gemm class is the split-FP32 kernel, against its FP32-pipe bound."""
+    (ctx.cfg.precision) the gemm class is the split-FP32 kernel, against its FP32-pipe bound.
+    `traffic` comes from a committed counter record of the class's kernel taken on this line's
+    workload (`line`), else it is null: another workload's DRAM bytes say nothing of this one's."""
     split = ctx is not None and ctx.cfg.precision == HT_PREC_MIXED
     total = sum(v["ms"] for v in prof.values()) or 1.0
     shares = {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps,
@@ -1091,14 +1096,14 @@ def class_roofline(prof: dict, steps: int, ctx=None) -> tuple:
                   "counted_tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 and v["flops"] > 0 else None}
               for k, v in prof.items() if v["launches"]}
     dom = max(prof, key=lambda k: prof[k]["ms"])
-    roof = roofline_of(prof, dom, steps, split)
+    roof = roofline_of(prof, dom, steps, split, line)
     out = {"dominant": roof}
     if dom != "gemm_tc" and prof.get("gemm_tc", {}).get("launches"):
-        out["gemm_tc"] = roofline_of(prof, "gemm_tc", steps)
+        out["gemm_tc"] = roofline_of(prof, "gemm_tc", steps, line=line)
     return out, shares
 
 
-def roofline_of(prof: dict, cls: str, steps: int, split: bool = False) -> dict:
+def roofline_of(prof: dict, cls: str, steps: int, split: bool = False, line: str | None = None) -> dict:
     v = prof[cls]
     if cls == "gemm" and split:
         roof = {"kernel": "gemm_f32x2_kernel", "class": cls, "bound": "alu", "unit": "TFLOP/s",
@@ -1124,11 +1129,22 @@ def roofline_of(prof: dict, cls: str, steps: int, split: bool = False) -> dict:
             roof["achieved"] = ach
             roof["frac"] = ach / roof["peak"]
             roof["flops_per_launch"] = v["flops"] / v["launches"]
-    rec = counter_record(roof["kernel"].split("/")[0])
-    if rec is not None:
-        roof["traffic"] = rec.get("dram_bytes_per_launch")
-        roof["traffic_record"] = {k: rec[k] for k in ("workload", "when") if k in rec}
+    attach_traffic(roof, roof["kernel"].split("/"), line)
     return roof
+
+
+def attach_traffic(roof: dict, kernels, line: str | None) -> None:
+    """roof["traffic"] (DRAM bytes per launch) from the first of `kernels` whose committed counter
+    record is fresh and was taken on the workload of `line`; null when none is."""
+    roof["traffic"] = None
+    roof.pop("traffic_record", None)
+    for kern in kernels:
+        rec = counter_record(kern)
+        if rec is None or rec.get("stale") or line is None or rec.get("line") != line:
+            continue
+        roof["traffic"] = rec.get("dram_bytes_per_launch")
+        roof["traffic_record"] = {k: rec[k] for k in ("kernel", "workload", "when") if k in rec}
+        return
 
 
 def profiled_steps(ctx, torch, flush, step, steps: int) -> dict:
@@ -1225,7 +1241,7 @@ def record_counters(args) -> None:
         raise SystemExit(f"no launch of {args.kernel} in {args.record_counters}")
     last = launches[-1]
     rec = {"kernel": args.kernel, "workload": args.record_workload, "command": args.record_command,
-           "when": time.strftime("%Y-%m-%d"), "launches_in_capture": len(launches),
+           "line": args.record_line, "when": time.strftime("%Y-%m-%d"), "launches_in_capture": len(launches),
            "metrics": {k: v for k, v in last.items()},
            "sources": {p: _sha256(p) for p in args.record_sources.split(",") if p}}
     if "dram__bytes_read.sum" in last and "dram__bytes_write.sum" in last:
@@ -1258,18 +1274,13 @@ def profile_pass(W, torch, flush, steps: int):
     per launch); the kernel itself never forms y and executes the fewer flops its counter reports
     (`executed_*`)."""
     prof = profiled_steps(W.ctx, torch, flush, W.step, steps)
-    rl, shares = class_roofline(prof, steps, W.ctx)
+    rl, shares = class_roofline(prof, steps, W.ctx, line="adv6d")
     roof = rl["dominant"]
     if roof["class"] == "cp_solve":
         # the form cp_als_sweep_rk2 took on this context names the kernel and its counter record
         kern = "cp_als_rk2_cluster" if W.G.cp_als_rk2_cluster_ctas(W.ctx, CP_R, CP_R) else "cp_als_rk2_persistent"
         roof["kernel"] = kern
-        roof["traffic"] = None
-        roof.pop("traffic_record", None)
-        rec = counter_record(kern)
-        if rec is not None:
-            roof["traffic"] = rec.get("dram_bytes_per_launch")
-            roof["traffic_record"] = {k: rec[k] for k in ("workload", "when") if k in rec}
+        attach_traffic(roof, [kern], "adv6d")
     if roof["class"] == "cp_solve" and roof["avg_launch_us"]:
         alg = cp_survey_flops_per_launch()
         roof["executed_flops_per_launch"] = roof.get("flops_per_launch")

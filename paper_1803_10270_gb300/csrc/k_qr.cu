@@ -383,7 +383,7 @@ __device__ bool coop_barrier(unsigned* flags, int G, int g, unsigned seq, int* e
 }
 
 __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restrict__ descs, int ndesc, QrCoopWs w,
-                                                        int smem_doubles) {
+                                                        int smem_doubles, double* flops) {
   // The launch's CTAs are shared out over the eligible matrices in proportion to their work
   // m k^2: two each, and the rest of the grid by those weights (the same computation in every
   // CTA, so all agree).  Against an equal share of at most 64 CTAs per matrix: the kinetic
@@ -425,6 +425,8 @@ __global__ void __launch_bounds__(QRC_NT) qr_coop_kernel(const QrDesc* __restric
   const QrDesc q = descs[d];
   const int m = q.m, k = q.k;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = QRC_NT / 32;
+  // the matrix's Householder flops, counted once (by its group's first CTA) as the one-CTA form counts them
+  if (g == 0 && tid == 0 && flops) atomicAdd(flops, householder_flops(m, k, 0));
   const int mb = (m + G - 1) / G, r0 = htg_min(m, g * mb), r1 = htg_min(m, r0 + mb);
   // the CTA's rows [r0, r1): in shared memory (ld mb) when they fit, else in the scratch buffer
   // (ld m); S points at row r0, so element (i, c) of the matrix is S[(i - r0) + ld c]
@@ -737,5 +739,5 @@ cudaError_t htg_launch_qr(const QrDesc* descs_dev, int ndesc, cudaStream_t s, do
   lattr[0].val.cooperative = 1;
   cfg.attrs = lattr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, ndesc, *coop, (int)(QRC_SMEM_BYTES / sizeof(double)));
+  return cudaLaunchKernelEx(&cfg, qr_coop_kernel, descs_dev, ndesc, *coop, (int)(QRC_SMEM_BYTES / sizeof(double)), flops);
 }

@@ -1,5 +1,6 @@
 """Host-side logic of bench.py on CPU: replica aggregation over gloo ranks and the reference
 arm's rank gating (no GPU involved)."""
+import json
 import os
 import socket
 import sys
@@ -75,7 +76,6 @@ def test_oracle_sample_process_runs_with_the_thread_count_set():
 def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
     sys.path.insert(0, ROOT)
     import argparse
-    import json
 
     import bench
     monkeypatch.delenv("WORLD_SIZE", raising=False)
@@ -112,3 +112,31 @@ def test_class_roofline_labels_the_split_fp32_contraction():
         assert abs(shares["gemm"]["share"] - 0.8) < 1e-12 and shares["gemm"]["ms_per_step"] == 2.0
         assert abs(shares["qr"]["counted_tflops"] - 1e8 / 1e-3 / 1e12) < 1e-12
         assert "gemm_tc" not in shares
+
+
+def test_roofline_traffic_only_from_a_capture_of_the_same_line(tmp_path, monkeypatch):
+    """roofline.traffic comes from a counter record of the class's kernel taken on the line's own
+    workload; a record of another line, or a stale one, leaves it null.  The qr and svd classes
+    name both of their kernels."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source\n")
+    recs = [{"kernel": "qr_r_kernel", "line": "adv6d", "workload": "w1", "when": "d", "sources": {},
+             "dram_bytes_per_launch": 1000},
+            {"kernel": "qr_coop_kernel", "line": "wide", "workload": "w2", "when": "d",
+             "sources": {str(src): "0" * 64}, "dram_bytes_per_launch": 5000}]
+    f = tmp_path / "counters.json"
+    f.write_text(json.dumps({"records": recs}))
+    monkeypatch.setattr(bench, "COUNTERS", str(f))
+    prof = {"qr": {"ms": 3.0, "launches": 6, "flops": 3e8}, "gemm": {"ms": 1.0, "launches": 2, "flops": 1e8}}
+    roof, _ = bench.class_roofline(prof, 2, None, "adv6d")
+    assert roof["dominant"]["kernel"] == "qr_r_kernel/qr_coop_kernel"
+    assert roof["dominant"]["traffic"] == 1000 and roof["dominant"]["traffic_record"]["kernel"] == "qr_r_kernel"
+    for line in ("kinetic", None):
+        roof, _ = bench.class_roofline(prof, 2, None, line)
+        assert roof["dominant"]["traffic"] is None and "traffic_record" not in roof["dominant"]
+    # the coop record's source hash does not match: stale, so the wide line gets no traffic either
+    roof, _ = bench.class_roofline(prof, 2, None, "wide")
+    assert roof["dominant"]["traffic"] is None
+    assert bench.KERNEL_NAMES["svd"] == "svd_kernel/svd_cluster_kernel"

@@ -239,6 +239,30 @@ def test_truncate_wide_node_factors(G, n, r, decay, deficient, ctx_cap):
     ctx.close()
 
 
+def test_profiler_counts_the_cooperative_qr_flops(G):
+    """The event profiler's QR class counts the Householder flops of every matrix it reduces,
+    those of the cooperative form too: in the truncation of a d=4 HT tensor of rank 96 the two
+    interior node matrices (96^2 x 96, over 2^16 entries and twice as tall as wide) go to the
+    cooperative kernel, so the class must count at least their 2 sum_j (m - j)(2 + 4 (k - j - 1))
+    flops (about 339 M; the leaves' 100 x 96 matrices add about 5 M)."""
+    d, n, r = 4, 100, 96
+    u = random_ht(d, n, r, seed=5, scale_decay=0.9)
+    ctx = G.Context(d, [n] * d, cap=r, max_terms=1)
+    g = to_gpu(G, u, r)
+    out = G.HTTensor(d, [n] * d, r)
+    ctx.profile(True)
+    G.ht_truncate(ctx, g, 1e-8, r, out)
+    sync()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check()
+    m, k = r * r, r
+    interior = sum((m - j) * (2.0 + 4.0 * (k - j - 1)) for j in range(k))
+    assert prof["qr"]["launches"] > 0
+    assert prof["qr"]["flops"] >= 2 * interior, (prof["qr"]["flops"], 2 * interior)
+    ctx.close()
+
+
 def test_untruncated_graded_spectrum_reproduces_u(G):
     """A truncation that keeps every direction returns u to rounding, even when node spectra
     span ten decades (transfer tensors graded by 0.7^j, rank 24): the projectors Y_t X_t of the
