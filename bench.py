@@ -44,6 +44,7 @@ FP64_PEAK_TFLOPS = 152 * 2.070e9 * 4 / 1e12
 # x 2 flops, in FP64-equivalent flops of the contraction.
 F32X2_PEAK_TFLOPS = 152 * 2.070e9 * 128 / 10 * 2 / 1e12
 HT_PREC_MIXED = 1   # ht_precision of the C ABI
+BIORTH_FORMS = {"cta": 0, "cluster": 1}   # ht_config.biorth_form
 KERNEL_NAMES = {"apply": "apply_leaf_kernel/apply_xfer_kernel", "gemm": "gemm_kernel",
                 "qr": "qr_r_kernel/qr_coop_kernel", "svd": "svd_kernel/svd_cluster_kernel", "plan": "plan_pre_kernel/rank_select_kernel",
                 "cp_small": "cp_hadamard_kernel/cp_normalize_kernel/...",
@@ -77,6 +78,8 @@ def parse():
     p.add_argument("--line", default="all",
                    choices=["all", "d12", "ab2", "batched", "varcoef", "tt", "cn", "kinetic", "mixed", "wide", "gemm_tc"],
                    help="run one side line alone (for profiling) and print its JSON object")
+    p.add_argument("--biorth-form", default="cta", choices=["cta", "cluster"],
+                   help="form of the X_t Y_t = I refinement on the kinetic and wide lines (ht_config.biorth_form)")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--record-counters", default=None, metavar="CSV",
                    help="write the ncu counter record of --kernel from this CSV into profiles/counters.json")
@@ -335,9 +338,11 @@ def run_gpu(args):
         elif args.line == "cn":
             res = run_cn(G, torch, flush, args.steps, warm)
         elif args.line == "kinetic":
-            res = run_kinetic(G, torch, flush, args.steps, warm, precision=prec)
+            res = run_kinetic(G, torch, flush, args.steps, warm, precision=prec,
+                              biorth_form=BIORTH_FORMS[args.biorth_form])
         elif args.line == "wide":
-            res = run_wide(G, torch, flush, args.steps, warm, precision=prec)
+            res = run_wide(G, torch, flush, args.steps, warm, precision=prec,
+                           biorth_form=BIORTH_FORMS[args.biorth_form])
         elif args.line == "gemm_tc":
             res = run_gemm_probe(G, args)
         else:
@@ -556,7 +561,8 @@ WIDE_WORKLOAD = ("HSVD truncation of a random d=4 HT tensor, n=200, every rank 1
                  "cooperative QR), tol 1e-8")
 
 
-def run_wide(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0) -> dict:
+def run_wide(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0,
+             biorth_form: int = 0) -> dict:
     """Truncations per second of one wide-factor case (the shape class of the kinetic workload's
     node factors at a size a profiler capture can hold), graph-captured, L2 flushed between."""
     import numpy as np
@@ -569,7 +575,8 @@ def run_wide(G, torch, flush, steps: int, warmup: int, precision: int = 0, slice
     g = 0.9 ** np.arange(w)
     u.upload({t: (arrs[t] * g.reshape((1,) * (arrs[t].ndim - 1) + (-1,)) if t else arrs[t])
               for t in range(tr.n_nodes)})
-    ctx = G.Context(d, [n] * d, cap=w // 3, max_terms=1, precision=precision, mixed_slices=slices)
+    ctx = G.Context(d, [n] * d, cap=w // 3, max_terms=1, precision=precision, mixed_slices=slices,
+                    biorth_form=biorth_form)
     out = G.HTTensor(d, [n] * d, w)
     for _ in range(warmup):
         G.ht_truncate(ctx, u, TOL, w, out)
@@ -591,11 +598,13 @@ def run_wide(G, torch, flush, steps: int, warmup: int, precision: int = 0, slice
     ms = sum(a.elapsed_time(b) for a, b in ev)
     ms_max, value = aggregate_replicas(ms, steps)
     ranks = out.ranks()
+    ctx_bi = ctx.biorth_cluster_ctas()
     del graph
     ctx.close()
     return {"workload": WIDE_WORKLOAD, "value": value, "unit": "truncations/s", "ms_per_step": ms_max / steps,
             "steps": steps, "warmup": warmup, "gpu_launches_per_step": per, "ranks_out": ranks,
-            "precision": precision_name(precision, slices), "cuda_graph": True}
+            "precision": precision_name(precision, slices), "cuda_graph": True,
+            "biorth_form": "cluster" if ctx_bi else "cta"}
 
 
 def run_mixed_lines(G, torch, flush, args) -> dict:
@@ -836,7 +845,7 @@ KIN_WORKLOAD = ("linearised 6-D kinetic equation: n=64 per variable, x periodic 
 
 
 def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, slices: int = 0,
-                keep: bool = False, profile: bool = True, tuning: dict | None = None):
+                keep: bool = False, profile: bool = True, tuning: dict | None = None, biorth_form: int = 0):
     """HT HEUN2 steps/s of the full-size kinetic workload (node ranks grow to about 60 within ten
     steps, so the step cost grows too: the line reports steps warmup+1 .. warmup+steps); then a
     profiled stretch for the per-class roofline; keep as in run_d12."""
@@ -844,7 +853,8 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
     from paper_1803_10270_gb300.inputs import kinetic_case, kinetic_ic
     kc = kinetic_case(64)
     w0, F0 = kinetic_ic(kc)
-    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5, precision=precision, mixed_slices=slices, tuning=tuning)
+    ctx = G.Context(6, [64] * 6, cap=64, max_terms=5, precision=precision, mixed_slices=slices, tuning=tuning,
+                    biorth_form=biorth_form)
     u = G.HTTensor(6, [64] * 6, 64)
     u.upload(ic_nodes(u.tree, [F * (w0[None, :] if i == 0 else 1.0) for i, F in enumerate(F0)], np))
     kop = G.KineticOp(kc)
@@ -872,7 +882,8 @@ def run_kinetic(G, torch, flush, steps: int, warmup: int, precision: int = 0, sl
     del graph
     res = {"workload": KIN_WORKLOAD, "value": value, "unit": "steps/s", "ms_per_step": ms_max / steps,
            "steps": steps, "warmup": warmup, "gpu_launches_per_step": per_step, "ht_ranks_final": ranks,
-           "cuda_graph": True, "precision": precision_name(precision, slices)}
+           "cuda_graph": True, "precision": precision_name(precision, slices),
+           "biorth_form": "cluster" if ctx.biorth_cluster_ctas() else "cta"}
     snap = None
     if keep:
         snap = G.HTTensor(6, [64] * 6, 64)

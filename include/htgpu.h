@@ -161,6 +161,14 @@ typedef struct ht_config {
   int cp_form;             /* cp_als_sweep_rk2 (Gauss-Seidel): 0 = one thread-block cluster of up to
                               16 CTAs whenever the problem fits its shared memory (ranks <= 64), else
                               the cooperative grid form; 1 = always the cooperative grid form */
+  int biorth_form;         /* the refinement X_t Y_t = I of the projections (two Newton steps, four
+                              products of 2 k^2 K flops per node): 0 = one CTA per node; 1 = one
+                              thread-block cluster of 16 (else 8) CTAs per node in contexts whose
+                              truncation inputs reach rank 160 (one CTA per node below that).  Both
+                              forms sum every element in the same order: the results agree bit for
+                              bit.  Measured on GB300: the cluster form takes the rank-192 wide-factor
+                              truncation from 93 to 86 ms, but the kinetic HEUN2 step (rank 64,
+                              5 terms) from 105.9 to 106.9 ms, so it is not the default */
 } ht_config;
 
 /* Context management, status codes, the profiler and the tree query below are infrastructure
@@ -182,6 +190,12 @@ int ht_ctx_check(ht_ctx* ctx, void* stream);
 
 /* Number of kernel launches the context issued since creation (host counter). */
 long long ht_ctx_launches(const ht_ctx* ctx);
+
+/* CTAs per node of the cluster form of the X_t Y_t = I refinement on this context (16 or 8),
+ * or 0 when it runs one CTA per node (ht_config.biorth_form = 0, truncation inputs below rank
+ * 160, or no cluster placeable on the device; batched steps always take one CTA per node and
+ * instance).  Errors: HT_ERR_ARG. */
+int ht_biorth_cluster_ctas(const ht_ctx* ctx, int* ctas);
 
 /* Opt-in event profiler (off by default).  on = 1 clears the accumulators and starts
  * recording a CUDA event pair on the launching stream around every kernel launch of the

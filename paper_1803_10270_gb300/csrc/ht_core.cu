@@ -21,7 +21,11 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------- tree -----
 void htg_build_tree(int d, int kind, TreeInfo* t) {
@@ -55,6 +59,8 @@ constexpr int NN = HT_MAXNODES;
 // cooperative QR (k_qr.cu) for contexts whose truncation inputs reach this rank: descriptors
 // per launch (a level's complement QRs: 2 per interior node) and CTAs per matrix
 constexpr int QR_COOP_MIN_KC = 160;
+// contexts whose truncation inputs reach this rank refine X_t Y_t = I in the cluster form
+constexpr int BIORTH_CLUSTER_MIN_KC = 160;
 constexpr int QR_COOP_NDMAX = 2 * HT_MAXNODES;
 constexpr int QR_COOP_GMAX = 64;
 constexpr int MAXLEV = HT_MAXD;   // tree depth + 1 (the linear tree of d = 16 is 15 deep)
@@ -177,6 +183,7 @@ struct ht_ctx {
   bool tc_lvl[MAXLEV][TL_LEVEL] = {};
   bool tc_rootE = false, tc_Pall = false, tc_XY = false, tc_proj[3] = {false, false, false};
   int svd_min_cols = 128;      // node factors at least this wide take the cluster SVD
+  int bi_cl = 0;               // CTAs per node of the cluster form of biorth (0: one CTA per node)
   cudaStream_t last_stream = nullptr;
   ht_batch* batch = nullptr;   // the batch this context is bound to, if any
   QrCoopWs qr_coop;            // cooperative QR workspace (contexts with Kc >= QR_COOP_MIN_KC)
@@ -448,11 +455,14 @@ __device__ void rank_select_body(Plan* P, const TreeInfo& T, const Levels& L, co
 // descriptors in g_bi[0] (A, B); N = 2I - X Y and Y2 = Y N live in shared memory when
 // 3 k K + k^2 doubles fit, else in the node's SW and P buffers (the descriptors' outputs).
 constexpr int BIORTH_SMEM = 96 * 1024;
-__global__ void __launch_bounds__(256) biorth_kernel(const GemmDesc* d0, const GemmDesc* d1, long long inst_stride) {
+__global__ void __launch_bounds__(256) biorth_kernel(const GemmDesc* d0, const GemmDesc* d1, long long inst_stride,
+                                                     double* flops) {
   const GemmDesc g0 = ((const GemmDesc*)((const char*)d0 + inst_stride * blockIdx.y))[blockIdx.x];
   const GemmDesc g1 = ((const GemmDesc*)((const char*)d1 + inst_stride * blockIdx.y))[blockIdx.x];
   const int k = g0.m, K = g0.k;
   if (k <= 0 || K <= 0) return;
+  // four products of 2 k^2 K flops each
+  if (threadIdx.x == 0 && flops) atomicAdd(flops, 8.0 * k * k * K);
   double* Yg = const_cast<double*>(g0.B);
   extern __shared__ double sh[];
   const long long need = 3LL * k * K + (long long)k * k;
@@ -493,6 +503,104 @@ __global__ void __launch_bounds__(256) biorth_kernel(const GemmDesc* d0, const G
     }
     __syncthreads();
   }
+}
+
+// The same two Newton steps for contexts with wide node factors (ht_config.biorth_form = 1),
+// where one CTA per node spends milliseconds on a node's 8 k^2 K flops (k = 64, K = 448: 7.3 M
+// multiply-adds, 2.4 ms): each node takes one thread-block cluster of CL CTAs, every product's
+// output elements are dealt out over the cluster's threads, and the four products are joined by
+// cluster barriers.  Each
+// element is summed in the same order as in biorth_kernel, so the results agree bit for bit.
+// The operands stay in global memory (L2 resident); N and Y2, written inside the launch, are
+// stored and read at L2 (st/ld .cg), so that no CTA reads a line of another CTA's output from
+// its own (non-coherent) L1.  One node per cluster: the early return and the barriers are
+// uniform over the cluster.
+__global__ void __launch_bounds__(256) biorth_cluster_kernel(const GemmDesc* d0, const GemmDesc* d1,
+                                                             double* flops) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cl = (int)cluster.num_blocks(), r = (int)cluster.block_rank();
+  const int node = (int)blockIdx.x / cl;
+  const GemmDesc g0 = d0[node];
+  const GemmDesc g1 = d1[node];
+  const int k = g0.m, K = g0.k;
+  if (k <= 0 || K <= 0) return;
+  if (r == 0 && threadIdx.x == 0 && flops) atomicAdd(flops, 8.0 * k * k * K);
+  const double* X = g0.A;
+  double* Yg = const_cast<double*>(g0.B);
+  double* N = g0.C;
+  double* Y2 = g1.C;
+  const int stride = cl * (int)blockDim.x, e0 = r * (int)blockDim.x + (int)threadIdx.x;
+  for (int it = 0; it < 2; ++it) {
+    const double* Yc = (it == 0) ? Yg : Y2;
+    for (int e = e0; e < k * k; e += stride) {
+      const int a = e % k, b = e / k;
+      double acc = 0.0;
+      // unrolled so that eight iterations' loads are in flight ahead of the (ordered) FMA chain
+#pragma unroll 8
+      for (int c = 0; c < K; ++c) acc = fma(X[a + (long long)k * c], __ldcg(Yc + c + (long long)K * b), acc);
+      __stcg(N + e, (a == b ? 2.0 : 0.0) - acc);
+    }
+    __threadfence();
+    cluster.sync();
+    double* out = (it == 0) ? Y2 : Yg;
+    for (int e = e0; e < K * k; e += stride) {
+      const int c = e % K, b = e / K;
+      double acc = 0.0;
+#pragma unroll 8
+      for (int a = 0; a < k; ++a) acc = fma(__ldcg(Yc + c + (long long)K * a), __ldcg(N + a + (long long)k * b), acc);
+      __stcg(out + e, acc);
+    }
+    __threadfence();
+    cluster.sync();
+  }
+}
+
+// The largest cluster (16 CTAs, else the portable 8) of biorth_cluster_kernel one of which fits
+// the device; 0 when none does (biorth_kernel then serves).
+static int biorth_cluster_setup() {
+  if (cudaFuncSetAttribute(biorth_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int sizes[2] = {16, 8};
+  for (int i = 0; i < 2; ++i) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(sizes[i], 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = sizes[i];
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, biorth_cluster_kernel, &cfg) == cudaSuccess && n >= 1) return sizes[i];
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+static cudaError_t launch_biorth(const ht_ctx* c, const Plan* P, int nodes, int count, long long st, double* flops,
+                                 cudaStream_t s) {
+  if (nodes <= 0 || count <= 0) return cudaSuccess;
+  if (c->bi_cl > 0 && count == 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nodes * c->bi_cl), 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = c->bi_cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, biorth_cluster_kernel, (const GemmDesc*)P->g_bi[0], (const GemmDesc*)P->g_bi[1],
+                              flops);
+  }
+  biorth_kernel<<<dim3(nodes, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st, flops);
+  return cudaGetLastError();
 }
 
 __global__ void rank_select_kernel(Plan* P, TreeInfo T, Levels L, HtView in, HtView out, const WsNode* wn,
@@ -865,6 +973,7 @@ static bool cfg_valid(const ht_config* c) {
   if (c->tc_min_work < -1 || c->gemm_ctas_per_sm < 0 || c->gemm_ctas_per_sm > 32) return false;
   if (c->svd_cluster_min_cols != 0 && (c->svd_cluster_min_cols < 32 || c->svd_cluster_min_cols > 480)) return false;
   if (c->cp_form != 0 && c->cp_form != 1) return false;
+  if (c->biorth_form != 0 && c->biorth_form != 1) return false;
   if (c->precision == HT_PREC_MIXED)
     return c->mixed_slices == 0 || (c->mixed_slices >= 2 && c->mixed_slices <= 4);
   return c->precision == HT_PREC_FP64;
@@ -1085,6 +1194,8 @@ extern "C" int ht_ctx_create(ht_ctx** out, const ht_config* cfg) {
     return HT_ERR_CUDA;
   }
   c->cp_clu = htg_cp_cluster_setup(cfg->device);
+  // wide node factors, on request: the cluster form of the X_t Y_t = I refinement
+  if (cfg->biorth_form == 1 && c->Kc >= BIORTH_CLUSTER_MIN_KC) c->bi_cl = biorth_cluster_setup();
   // wide node factors: the cluster form of the SVD, when a cluster fits this device
   if (c->Kc >= c->svd_min_cols) {
     c->svd_clu = htg_svd_cluster_setup(cfg->device);
@@ -1125,6 +1236,12 @@ extern "C" void ht_ctx_destroy(ht_ctx* ctx) {
 }
 
 extern "C" long long ht_ctx_launches(const ht_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" int ht_biorth_cluster_ctas(const ht_ctx* ctx, int* ctas) {
+  if (!ctx || !ctas) return HT_ERR_ARG;
+  *ctas = ctx->bi_cl;
+  return HT_OK;
+}
 
 extern "C" int ht_ctx_check(ht_ctx* ctx, void* stream) {
   if (!ctx) return HT_ERR_ARG;
@@ -1252,9 +1369,7 @@ static int truncate_launches(ht_ctx* c, Plan* P, int count, int Kc, int svd_smem
   c->launches += htg_svd_cluster_used(clu, count, Kc) ? 1 : 0;
   HTG_LAUNCH(c, KC_PLAN, s, sel());
   HTG_GEMM(P->g_XY, 2 * (T.nn - 1), c->tc_XY);
-  HTG_LAUNCH(c, KC_GEMM, s,
-             (biorth_kernel<<<dim3(T.nn - 1, count), 256, BIORTH_SMEM, s>>>(P->g_bi[0], P->g_bi[1], st),
-              cudaGetLastError()));
+  HTG_LAUNCH(c, KC_GEMM, s, launch_biorth(c, P, T.nn - 1, count, st, htg_prof_flops(c, KC_GEMM), s));
   HTG_GEMM(P->g_proj1, L.n_proj1, c->tc_proj[0]);
   HTG_GEMM(P->g_proj2, L.n_proj2, c->tc_proj[1]);
   if (L.n_proj3 > 0)

@@ -24,6 +24,7 @@ HT_MAXSTENCIL = 9
 HT_OK, HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA, HT_ERR_NONFINITE, HT_ERR_TIMEOUT, HT_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 HT_PREC_FP64, HT_PREC_MIXED = 0, 1
 CP_FORM_AUTO, CP_FORM_GRID = 0, 1   # ht_config.cp_form
+BIORTH_FORM_CTA, BIORTH_FORM_CLUSTER = 0, 1   # ht_config.biorth_form
 HT_F_IDENTITY, HT_F_STENCIL, HT_F_DIAG, HT_F_RANK1, HT_F_DIAG_STENCIL = 0, 1, 2, 3, 4
 HT_APPLY_L, HT_APPLY_EULER, HT_APPLY_RK2POLY = 0, 1, 2
 HT_SCHEME_RK2POLY, HT_SCHEME_HEUN2 = 0, 1
@@ -57,7 +58,7 @@ class ht_config(C.Structure):
     _fields_ = [("d", C.c_int), ("n", C.c_int * HT_MAXD), ("cap", C.c_int), ("max_terms", C.c_int),
                 ("precision", C.c_int), ("device", C.c_int), ("tree", C.c_int), ("mixed_slices", C.c_int),
                 ("tc_min_work", C.c_longlong), ("gemm_ctas_per_sm", C.c_int), ("svd_cluster_min_cols", C.c_int),
-                ("cp_form", C.c_int)]
+                ("cp_form", C.c_int), ("biorth_form", C.c_int)]
 
 
 _EXPORTS = {
@@ -66,6 +67,7 @@ _EXPORTS = {
     "ht_ctx_destroy": (None, [C.c_void_p]),
     "ht_ctx_check": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ht_ctx_launches": (C.c_longlong, [C.c_void_p]),
+    "ht_biorth_cluster_ctas": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "ht_status_string": (C.c_char_p, [C.c_int]),
     "ht_ctx_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "ht_ctx_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
@@ -186,11 +188,13 @@ class Context:
 
     def __init__(self, d: int, n, cap: int, max_terms: int = 6, precision: int = HT_PREC_FP64,
                  device: int = 0, tree: int = 0, mixed_slices: int = 0, tuning: dict | None = None,
-                 cp_form: int = 0):
+                 cp_form: int = 0, biorth_form: int = 0):
         """tuning: values for the ht_config tuning fields (tc_min_work, gemm_ctas_per_sm,
         svd_cluster_min_cols); None takes the tuning cache of this device when one exists
         (paper_1803_10270_gb300.tune), {} the library defaults.  cp_form: CP_FORM_AUTO (the
-        cluster form of cp_als_sweep_rk2 where it fits) or CP_FORM_GRID."""
+        cluster form of cp_als_sweep_rk2 where it fits) or CP_FORM_GRID.  biorth_form:
+        BIORTH_FORM_CTA (one CTA per node) or BIORTH_FORM_CLUSTER (a thread-block cluster per
+        node in contexts of truncation rank 160 and above); the two give the same bits."""
         lib = load()
         cfg = ht_config()
         cfg.d = d
@@ -203,6 +207,7 @@ class Context:
         cfg.tree = tree
         cfg.mixed_slices = mixed_slices
         cfg.cp_form = cp_form
+        cfg.biorth_form = biorth_form
         if tuning is None:
             from paper_1803_10270_gb300 import tune as _tune
             tuning = _tune.cached(device, max(3, max_terms + 2) * cap)
@@ -221,6 +226,12 @@ class Context:
 
     def launches(self) -> int:
         return int(load().ht_ctx_launches(self.ptr))
+
+    def biorth_cluster_ctas(self) -> int:
+        """CTAs per node of the cluster form of the X_t Y_t = I refinement, 0 for one CTA per node."""
+        out = C.c_int(0)
+        _check(load().ht_biorth_cluster_ctas(self.ptr, C.byref(out)), "ht_biorth_cluster_ctas")
+        return int(out.value)
 
     KERNEL_CLASSES = ["apply", "gemm", "qr", "svd", "plan", "cp_small", "cp_solve", "gemm_tc"]
 

@@ -70,6 +70,12 @@ def test_host_side_argument_errors(lib):
     assert lib.ht_workspace_bytes(C.byref(cfg)) > 0
     cfg.precision = 7
     assert lib.ht_workspace_bytes(C.byref(cfg)) == 0
+    cfg.precision = 0
+    cfg.biorth_form = 2
+    assert lib.ht_workspace_bytes(C.byref(cfg)) == 0
+    cfg.biorth_form = 1
+    assert lib.ht_workspace_bytes(C.byref(cfg)) > 0
+    cfg.precision = 7
     out = C.c_void_p()
     assert lib.ht_ctx_create(C.byref(out), C.byref(cfg)) == G.HT_ERR_ARG
     assert lib.ht_step(None, None, None, 0.1, 1e-8, 4, 0, None) == G.HT_ERR_ARG
@@ -96,6 +102,7 @@ def test_every_entry_point_checks_its_arguments_before_the_gpu(lib):
     assert lib.ht_ctx_profile_read(None, None, None, None) == ARG
     assert lib.ht_ctx_check(None, None) == ARG
     assert lib.ht_ctx_launches(None) == 0
+    assert lib.ht_biorth_cluster_ctas(None, None) == ARG
     lib.ht_ctx_destroy(None)
     lib.ht_batch_destroy(None)
     out = C.c_void_p()
@@ -142,3 +149,32 @@ def test_product_path_fails_loudly_without_a_gpu_or_library(lib):
         pytest.skip("a GPU is present: contexts are created normally")
     with pytest.raises(G.HTError, match="HT_ERR_CUDA"):
         G.Context(6, [16] * 6, cap=8, max_terms=1)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes mirrors of the header's structs have the header's field offsets and
+    sizes: a C program compiled against include/htgpu.h prints them (gcc, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_1803_10270_gb300 import htgpu as G
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    structs = [("ht_config", G.ht_config), ("cp_tensor", G.cp_tensor), ("ht_factor", G.ht_factor), ("ht_op", G.ht_op)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "htgpu.h"', "int main(void) {"]
+    for name, py in structs:
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, py in structs:
+        assert got[(name, "sizeof")] == C.sizeof(py), name
+        for f, _ in py._fields_:
+            assert got[(name, f)] == getattr(py, f).offset, (name, f)

@@ -263,6 +263,31 @@ def test_profiler_counts_the_cooperative_qr_flops(G):
     ctx.close()
 
 
+def test_biorth_cluster_form_matches_the_one_cta_form_bitwise(G):
+    """The cluster form of the X_t Y_t = I refinement (each node's four products dealt out over
+    the CTAs of a thread-block cluster) sums every element in the order of the one-CTA form:
+    ht_truncate of a d=4 tensor of rank 131 (k^2 and K k above the cluster's threads) returns
+    the same ranks and the same bits with either form, and matches the oracle."""
+    d, n, r = 4, 150, 131
+    u = random_ht(d, n, r, seed=21, scale_decay=0.85)
+    ref, rep = OH.truncate(u, 1e-8, r)
+    outs = []
+    for form in (G.BIORTH_FORM_CLUSTER, G.BIORTH_FORM_CTA):
+        ctx = G.Context(d, [n] * d, cap=r, max_terms=1, biorth_form=form)
+        assert (ctx.biorth_cluster_ctas() in (8, 16)) == (form == G.BIORTH_FORM_CLUSTER)
+        out = G.HTTensor(d, [n] * d, r)
+        G.ht_truncate(ctx, to_gpu(G, u, r), 1e-8, r, out)
+        sync()
+        ctx.check()
+        outs.append((out.ranks(), from_gpu(out, u.tree)))
+        ctx.close()
+    (ra, a), (rb, b) = outs
+    assert ra == rb == rep.ranks
+    for t in range(u.tree.n_nodes):
+        assert np.array_equal(a.node[t], b.node[t]), t
+    assert rel_err(a, ref) < TOL64
+
+
 def test_untruncated_graded_spectrum_reproduces_u(G):
     """A truncation that keeps every direction returns u to rounding, even when node spectra
     span ten decades (transfer tensors graded by 0.7^j, rank 24): the projectors Y_t X_t of the
