@@ -25,7 +25,10 @@ rank reduction):
 Parity: pinned by tests -- to_full vs brute-force CP evaluation; apply vs the
 Fourier closed form of the fully discrete scheme; truncate vs Eckart-Young (d = 2),
 exact recovery of separable inputs, brute-force projector products built from full
-matricisation SVDs, the HSVD error bounds and idempotence.
+matricisation SVDs, the HSVD error bounds and idempotence; add, inner, norm and mass
+vs the same operations on the full grid; step_rk2_poly, step_ab2 and step_heun2 vs the
+full-grid steppers and the Fourier / kinetic x-mode closed forms; step_ab2_split,
+untruncated, vs the full-grid AB2 step and, truncated, within the propagated HSVD bound.
 """
 from __future__ import annotations
 
