@@ -140,3 +140,15 @@ def test_roofline_traffic_only_from_a_capture_of_the_same_line(tmp_path, monkeyp
     roof, _ = bench.class_roofline(prof, 2, None, "wide")
     assert roof["dominant"]["traffic"] is None
     assert bench.KERNEL_NAMES["svd"] == "svd_kernel/svd_cluster_kernel"
+
+
+def test_biorth_form_switch_matches_the_binding(monkeypatch):
+    """`--biorth-form` names the binding's ht_config.biorth_form values; cta is the default."""
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_1803_10270_gb300 import htgpu as G
+    assert bench.BIORTH_FORMS == {"cta": G.BIORTH_FORM_CTA, "cluster": G.BIORTH_FORM_CLUSTER}
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert bench.parse().biorth_form == "cta"
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--line", "wide", "--biorth-form", "cluster"])
+    assert bench.BIORTH_FORMS[bench.parse().biorth_form] == G.BIORTH_FORM_CLUSTER
